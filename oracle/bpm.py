@@ -1,0 +1,204 @@
+"""Split-step z-march of the DEC NLSE, FP64, plain and slow.
+
+TEST INFRASTRUCTURE ONLY (see the package docstring).
+
+The equation (Eq. 1 in normalized form, discretized as Eqs. 10-12) is read as
+
+    i dPsi/dz = -sum_n p_n (-A)^n Psi - v Psi - chib |Psi|^2 Psi  (- i sigma Psi)
+
+with A = *0^{-1} d0^T *1 d0, so that the transverse Laplacian is -A (Table I).
+This follows Eq. 1 and Table I; Eq. 11 as printed puts the stiffness and the
+potential under one minus sign, which would flip the relative sign of
+diffraction against the potential and the Kerr term (the exact sech soliton
+is stationary only with the reading used here).  sigma >= 0 is the absorber
+(a damping rate per vertex; the paper names absorbing layers but gives no
+formula).
+
+One step of length h is the Strang composition D_{h/2} E_h D_{h/2}:
+  E_h  exact action of exp(i h sum_n p_n (-A)^n)       (linear diffraction)
+  D_h  exact flow of dpsi/dz = i (v + N(|psi|^2)) psi - sigma psi per vertex
+The oracle applies every half step as written (no merging of adjacent half
+steps), so that a fused implementation can be checked against it.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+import scipy.sparse as sp
+
+from .dec import Operators
+
+
+# --------------------------------------------------------------------------
+# linear operator of the diffraction part
+# --------------------------------------------------------------------------
+def apply_Ldiff(ops: Operators, p, psi: np.ndarray) -> np.ndarray:
+    """L_diff psi = -sum_n p_n (-A)^n psi: the higher-order terms are the
+    cascaded powers of the DEC Laplacian (Table I, 'Higher-order' row)."""
+    out = np.zeros_like(psi)
+    term = psi
+    for n, pn in enumerate(p, start=1):
+        term = -(ops.A @ term)            # (-A)^n psi
+        if pn != 0.0:
+            out = out - pn * term
+    return out
+
+
+def Ldiff_norm_bound(ops: Operators, p) -> float:
+    """Bound on the infinity norm of L_diff: sum_n |p_n| ||A||_inf^n."""
+    return float(sum(abs(pn) * ops.rho ** n for n, pn in enumerate(p, start=1)))
+
+
+def linear_step(ops: Operators, p, psi: np.ndarray, h: float, tol: float = 1e-18) -> np.ndarray:
+    """E_h psi = exp(-i h L_diff) psi by its Taylor series, with the step
+    split into s substeps so that ||(h/s) L_diff||_inf <= 1; each series is
+    summed until the last term is below tol times the partial sum (both in
+    the infinity norm).  This is a different algorithm from the library's
+    Chebyshev expansion on purpose."""
+    bound = Ldiff_norm_bound(ops, p) * abs(h)
+    s = max(1, int(math.ceil(bound)))
+    hs = h / s
+    psi = np.array(psi, dtype=np.complex128, copy=True)
+    for _ in range(s):
+        acc = psi.copy()
+        term = psi
+        k = 0
+        while True:
+            k += 1
+            term = (-1j * hs / k) * apply_Ldiff(ops, p, term)
+            acc = acc + term
+            if np.max(np.abs(term)) <= tol * max(np.max(np.abs(acc)), 1e-300) or k > 200:
+                break
+        psi = acc
+    return psi
+
+
+# --------------------------------------------------------------------------
+# diagonal (potential + Kerr + absorber) flow
+# --------------------------------------------------------------------------
+def _phi(sigma: np.ndarray, h: float) -> np.ndarray:
+    """int_0^h exp(-2 sigma z) dz = (1 - exp(-2 sigma h)) / (2 sigma), -> h as sigma -> 0."""
+    sigma = np.asarray(sigma, dtype=np.float64)
+    out = np.full(sigma.shape, float(h))
+    nz = sigma > 0
+    out[nz] = -np.expm1(-2.0 * sigma[nz] * h) / (2.0 * sigma[nz])
+    return out
+
+
+def diagonal_flow(ops: Operators, psi: np.ndarray, h: float, sigma: np.ndarray | None = None,
+                  kerr: str = "lumped") -> np.ndarray:
+    """Exact flow over h of dpsi_p/dz = i (v_p + N_p) psi_p - sigma_p psi_p.
+
+    |psi_p|^2 decays as exp(-2 sigma_p z) and the phase is the integral of
+    the rate:  theta_p = v_p h + sum_q c_pq |psi_q(0)|^2 phi(sigma_q, h).
+    kerr="lumped":  N_p = chib_p |psi_p|^2 (c = diag(chib)).
+    kerr="element": N_p = [*0^{-1} Q^T D Q |psi|^2]_p, the triangle-averaged
+                    intensity of Eq. 14 (the phase flow stays exact because
+                    every |psi_q| only decays at its own rate).
+    """
+    n0 = ops.n0
+    sigma = np.zeros(n0) if sigma is None else np.asarray(sigma, dtype=np.float64)
+    psi = np.asarray(psi, dtype=np.complex128)
+    I0 = np.abs(psi) ** 2
+    ph = _phi(sigma, h)
+    if psi.ndim == 2:
+        ph2 = ph[:, None]
+        v = ops.v[:, None]
+        sig = sigma[:, None]
+    else:
+        ph2, v, sig = ph, ops.v, sigma
+    if kerr == "lumped":
+        chib = ops.chib[:, None] if psi.ndim == 2 else ops.chib
+        theta = v * h + chib * I0 * ph2
+    elif kerr == "element":
+        C = sp.diags(1.0 / ops.H0) @ ops.QtDQ
+        theta = v * h + C @ (I0 * ph2)
+    else:
+        raise ValueError(kerr)
+    return psi * np.exp(-sig * h) * np.exp(1j * theta)
+
+
+# --------------------------------------------------------------------------
+# Strang split-step march
+# --------------------------------------------------------------------------
+def strang_step(ops, p, psi, h, sigma=None, kerr="lumped"):
+    psi = diagonal_flow(ops, psi, 0.5 * h, sigma, kerr)
+    psi = linear_step(ops, p, psi, h)
+    return diagonal_flow(ops, psi, 0.5 * h, sigma, kerr)
+
+
+def propagate(ops: Operators, p, psi0: np.ndarray, h: float, n_steps: int, sigma=None, kerr="lumped",
+              callback=None) -> np.ndarray:
+    """n_steps Strang steps of length h.  psi0 is [N0] or [N0, B] (fields
+    are independent).  callback(step, psi) runs after every step if given."""
+    psi = np.array(psi0, dtype=np.complex128, copy=True)
+    for n in range(n_steps):
+        psi = strang_step(ops, p, psi, h, sigma, kerr)
+        if callback is not None:
+            callback(n + 1, psi)
+    return psi
+
+
+# --------------------------------------------------------------------------
+# diagnostics
+# --------------------------------------------------------------------------
+def power(ops: Operators, psi: np.ndarray) -> np.ndarray:
+    """P = Psi^H *0 Psi = sum_p m_p |psi_p|^2 (conserved without absorber)."""
+    w = ops.H0 if psi.ndim == 1 else ops.H0[:, None]
+    return np.sum(w * np.abs(psi) ** 2, axis=0)
+
+
+def hamiltonian(ops: Operators, p, psi: np.ndarray) -> np.ndarray:
+    """H = Psi^H *0 L_diff Psi - sum_p m_p v_p |psi_p|^2 - (1/2) sum_p m_p chib_p |psi_p|^4,
+    the conserved energy of the lumped DEC system (i *0 dPsi/dz = dH/dPsi^*)."""
+    psi2 = psi if psi.ndim == 2 else psi[:, None]
+    Lpsi = apply_Ldiff(ops, p, psi2)
+    m = ops.H0[:, None]
+    lin = np.real(np.sum(np.conj(psi2) * m * Lpsi, axis=0))
+    I = np.abs(psi2) ** 2
+    pot = np.sum(m * ops.v[:, None] * I, axis=0)
+    kerr = 0.5 * np.sum(m * ops.chib[:, None] * I * I, axis=0)
+    out = lin - pot - kerr
+    return out if psi.ndim == 2 else out[0]
+
+
+def relative_error(ops: Operators, psi: np.ndarray, ref: np.ndarray) -> float:
+    """*0-weighted relative L2 error of the complex field."""
+    w = ops.H0 if psi.ndim == 1 else ops.H0[:, None]
+    return float(math.sqrt(np.sum(w * np.abs(psi - ref) ** 2) / np.sum(w * np.abs(ref) ** 2)))
+
+
+def intensity_error(ops: Operators, psi: np.ndarray, ref: np.ndarray) -> float:
+    """E_rel of Eq. 15 on intensities, with the L2 norm taken *0-weighted
+    over the mesh (the paper does not state the quadrature)."""
+    w = ops.H0 if psi.ndim == 1 else ops.H0[:, None]
+    a, b = np.abs(psi) ** 2, np.abs(ref) ** 2
+    return float(math.sqrt(np.sum(w * (a - b) ** 2) / np.sum(w * b * b)))
+
+
+# --------------------------------------------------------------------------
+# the paper's own integrator (cross-check of the split-step march)
+# --------------------------------------------------------------------------
+def rk45_reference(ops: Operators, p, psi0: np.ndarray, z: float, rtol=1e-11, atol=1e-13,
+                   kerr="lumped") -> np.ndarray:
+    """Integrate the DEC ODE of Eq. 10, i dPsi/dz = L Psi + N(|psi|^2) Psi,
+    with adaptive Dormand-Prince RK45 (scipy's solve_ivp, as in the paper,
+    which used rtol 1e-9 / atol 1e-11).  L = L_diff - diag(v) and
+    N = -diag(chib |psi|^2) (lumped) or -*0^{-1} diag(Q^T D Q |psi|^2) (Eq. 14).
+    No absorber: the paper's runs have none."""
+    from scipy.integrate import solve_ivp
+
+    C = sp.diags(1.0 / ops.H0) @ ops.QtDQ if kerr == "element" else None
+
+    def rhs(_z, y):
+        psi = y[: ops.n0] + 1j * y[ops.n0:]
+        I = np.abs(psi) ** 2
+        Nterm = ops.chib * I if kerr == "lumped" else C @ I
+        dpsi = -1j * (apply_Ldiff(ops, p, psi) - ops.v * psi - Nterm * psi)
+        return np.concatenate([dpsi.real, dpsi.imag])
+
+    y0 = np.concatenate([np.real(psi0), np.imag(psi0)])
+    sol = solve_ivp(rhs, (0.0, z), y0, method="RK45", rtol=rtol, atol=atol)
+    y = sol.y[:, -1]
+    return y[: ops.n0] + 1j * y[ops.n0:]
