@@ -1,0 +1,232 @@
+/*
+ * decbpm.h -- C ABI of the B300 (sm_103a) DEC beam-propagation library.
+ *
+ * The library marches a complex transverse field psi along z on an
+ * unstructured mesh, solving the normalized NLSE of Eq. 1
+ *
+ *     i dpsi/dz = -sum_n p_n lap^n psi - V psi - chi |psi|^2 psi
+ *
+ * discretized with discrete exterior calculus as in Eqs. 10-12: psi is a
+ * primal 0-form (one value per vertex), the transverse Laplacian is
+ * -*0^{-1} d0^T *1 d0 (Table I), *0 is the barycentric (diagonal) Hodge star
+ * and *1 the Galerkin Hodge star of Eq. 9, whose stiffness d0^T *1 d0 equals
+ * the cotangent-weight stiffness used here.  Higher-order diffraction terms
+ * are powers of the same operator (Table I, "Higher-order" row).  Potential
+ * and Kerr coefficients are per triangle, lumped to vertices with *0(V) and
+ * *0(chi) (Sec. "Discrete Hodge star").
+ *
+ * One z-step of length h is the Strang split D_{h/2} E_h D_{h/2}:
+ *   E_h  = exp(i h sum_n p_n (-A)^n), A = *0^{-1} d0^T *1 d0, applied by a
+ *          Chebyshev expansion on the Gershgorin interval of A;
+ *   D_h  = exact flow of dpsi/dz = i (v + chib |psi|^2) psi - sigma psi per
+ *          vertex (potential, Kerr phase and absorber damping).
+ *
+ * Conventions shared by every entry point
+ *   - Return value: DECBPM_OK (0) or a negative DECBPM_ERR_* code.  The
+ *     message of the last failure on the calling thread is returned by
+ *     decbpm_last_error().  No entry point aborts, traps or exits.
+ *   - Fields live on the device in the caller's vertex order, interleaved
+ *     complex (re, im), field-minor: element (vertex p, field f) is at
+ *     index p * n_fields + f.  complex64 for DECBPM_C64, complex128 for
+ *     DECBPM_C128.  The caller owns these buffers; the library updates them
+ *     in place.
+ *   - Host arrays (mesh description, diagnostics) are read or written only
+ *     during the call.
+ *   - `stream` is a cudaStream_t (NULL = legacy default stream).  Work is
+ *     enqueued on it; calls that return diagnostics or check device status
+ *     synchronize that stream before returning.
+ *   - A handle may be used by one thread at a time.
+ */
+#ifndef DECBPM_H
+#define DECBPM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes -------------------------------------------------------- */
+#define DECBPM_OK                 0
+#define DECBPM_ERR_INVALID_ARG   -1   /* bad pointer, size, dz, precision ... */
+#define DECBPM_ERR_BAD_MESH      -2   /* inverted / degenerate triangle, non-manifold edge, isolated vertex */
+#define DECBPM_ERR_NONFINITE     -3   /* NaN or Inf in an input, or in the field after a step block */
+#define DECBPM_ERR_TIMEOUT       -4   /* a device-side grid barrier gave up waiting (bounded spin) */
+#define DECBPM_ERR_CUDA          -5   /* a CUDA runtime call failed */
+#define DECBPM_ERR_OOM           -6   /* device or host allocation failed */
+#define DECBPM_ERR_UNSUPPORTED   -7   /* valid request that this build does not implement */
+
+/* ---- enumerations -------------------------------------------------------- */
+#define DECBPM_C64   1   /* complex64 field, FP32 arithmetic, FP64 diagnostics */
+#define DECBPM_C128  2   /* complex128 field, FP64 arithmetic */
+
+#define DECBPM_KERR_LUMPED   0   /* N_p = chib_p |psi_p|^2 (per-vertex, "pointwise") */
+#define DECBPM_KERR_ELEMENT  1   /* N_p = [*0^{-1} Q^T D Q |psi|^2]_p, triangle-averaged (Eq. 14) */
+
+#define DECBPM_VARIANT_FUSED  0  /* persistent kernel, fused Chebyshev/Clenshaw terms and diagonal step */
+#define DECBPM_VARIANT_PLAIN  1  /* unfused reference path: one CSR SpMV launch + one update launch per term */
+
+typedef struct decbpm_mesh_s *decbpm_mesh_t;
+typedef struct decbpm_plan_s *decbpm_plan_t;
+
+/* ---- mesh description (host memory, read during decbpm_mesh_create) ---------
+ * dim 2: cells are triangles [v1, v2, v3], counter-clockwise (positive signed
+ *        area), as the paper assumes for 2-simplices; dim 1: segments [a, b].
+ * V_cell / chi_cell: potential and Kerr coefficient per cell, evaluated at the
+ *        cell centroid (NULL = 0 and 1).  sigma_vertex: absorber rate >= 0
+ *        per vertex (NULL = none).  p_n: diffraction coefficients p_1..p_np of
+ *        Eq. 1 (NULL or n_p = 0 means p_1 = 1). */
+typedef struct {
+    int32_t dim;
+    int64_t n_vertices;
+    int64_t n_cells;
+    const double  *coords;        /* [n_vertices * dim] */
+    const int32_t *cells;         /* [n_cells * (dim + 1)] */
+    const double  *V_cell;        /* [n_cells] or NULL */
+    const double  *chi_cell;      /* [n_cells] or NULL */
+    const double  *sigma_vertex;  /* [n_vertices] or NULL */
+    const double  *p_n;           /* [n_p] or NULL */
+    int32_t        n_p;
+} decbpm_mesh_desc;
+
+typedef struct {
+    int64_t n_vertices, n_edges, n_cells;
+    int64_t nnz_offdiag;       /* off-diagonal entries of the stiffness K (2 per edge) */
+    int32_t max_degree;        /* largest vertex degree */
+    int32_t n_p;               /* number of diffraction coefficients */
+    int64_t bandwidth;         /* max |new(p) - new(q)| over edges after reverse Cuthill-McKee */
+    double  rho;               /* upper bound of the spectrum of A = *0^{-1} K (Gershgorin, +1% margin) */
+    double  area;              /* sum of cell measures = sum of *0 */
+    double  mean_degree;       /* nnz_offdiag / n_vertices */
+    int64_t sell_entries;      /* padded off-diagonal entries stored (SELL-32) */
+    int64_t device_bytes;      /* device memory held by the handle (operators, no workspaces) */
+} decbpm_mesh_info_t;
+
+/* ---- propagation parameters ---------------------------------------------- */
+typedef struct {
+    double  dz;          /* step length h > 0 */
+    int64_t n_steps;     /* >= 0 */
+    int32_t precision;   /* DECBPM_C64 | DECBPM_C128: element type of the field buffers */
+    int32_t kerr_mode;   /* DECBPM_KERR_LUMPED | DECBPM_KERR_ELEMENT */
+    int32_t diag_every;  /* > 0: diagnostics after every diag_every steps; 0: only after the last step */
+    int32_t variant;     /* DECBPM_VARIANT_FUSED | DECBPM_VARIANT_PLAIN (C128 only) */
+    double  cheb_tol;    /* Chebyshev truncation: tail bound; 0 = 1e-16 (C128) / 1e-9 (C64) */
+} decbpm_params;
+
+/* Diagnostics of one field at one z (FP64 accumulation, fixed reduction order):
+ *   power       P = sum_p m_p |psi_p|^2                    (m = *0)
+ *   hamiltonian H = psi^H *0 L_diff psi - sum_p m_p v_p |psi_p|^2 - 1/2 sum_p m_p chib_p |psi_p|^4
+ *               (conserved by the lumped system without absorber; NaN when n_p > 2)
+ *   max_intensity = max_p |psi_p|^2                                             */
+typedef struct { double z, power, hamiltonian, max_intensity; } decbpm_diag;
+
+/* ---- library ------------------------------------------------------------- */
+const char *decbpm_version(void);
+/* Message of the last failed call on this thread ("" if none).  Owned by the library. */
+const char *decbpm_last_error(void);
+
+/* ---- mesh ---------------------------------------------------------------- *
+ * Assembles the DEC operators in FP64 on the host (Sec. "DEC computational
+ * framework" through Eq. 12): canonical edges (a < b), the cotangent form of
+ * d0^T *1 d0 (equal to the Galerkin *1 of Eq. 9 with xi = 1), *0, *0(V),
+ * *0(chi), the Gershgorin bound rho of A; renumbers vertices by reverse
+ * Cuthill-McKee, packs the operator as SELL-32 and uploads it (FP64 and FP32
+ * copies) to the current CUDA device.  The handle owns that device memory.
+ * Errors: INVALID_ARG (NULL/size), BAD_MESH, NONFINITE, CUDA, OOM.          */
+int decbpm_mesh_create(const decbpm_mesh_desc *desc, decbpm_mesh_t *out);
+int decbpm_mesh_destroy(decbpm_mesh_t mesh);
+int decbpm_mesh_info(decbpm_mesh_t mesh, decbpm_mesh_info_t *info);
+
+/* Host-only assembly (no device needed), for inspection and testing.
+ * First call with every output NULL to fill *info (sizes); then call again
+ * with outputs of those sizes (any output may stay NULL):
+ *   m, v, chib   [n_vertices]            *0, lumped potential, lumped Kerr coefficient (caller order)
+ *   K_rowptr     [n_vertices + 1]        stiffness K = d0^T *1 d0 in CSR, caller order,
+ *   K_col, K_val [nnz_offdiag + n_vertices]   diagonal included, columns ascending
+ *   perm         [n_vertices]            internal order: perm[new] = caller index             */
+int decbpm_assemble_host(const decbpm_mesh_desc *desc, decbpm_mesh_info_t *info,
+                         double *m, double *v, double *chib,
+                         int64_t *K_rowptr, int32_t *K_col, double *K_val, int32_t *perm);
+
+/* Host-only: Chebyshev coefficients used for E_h.  For p = (p_1) the
+ * expansion is exp(-i a x) = sum_k (2 - delta_k0) (-i)^k J_k(a) T_k(x)
+ * (Jacobi-Anger), so this returns J_0(a) .. J_{n-1}(a) by Miller's backward
+ * recurrence, n = smallest degree + 1 whose tail 2 sum_{k>=n} |J_k(a)| <= tol.
+ * J_out has room for max_terms values; *n_out receives n (or the needed size
+ * with INVALID_ARG if max_terms is too small).                               */
+int decbpm_bessel_coefficients(double a, double tol, int32_t max_terms, double *J_out, int32_t *n_out);
+
+/* ---- propagation (single mesh) --------------------------------------------
+ * Advances n_fields independent fields psi_dev[n_vertices * n_fields] by
+ * params->n_steps Strang steps.  diag_out (host, may be NULL) receives
+ * n_fields records per diagnostic point, field-minor:
+ *   n_diag = n_steps / diag_every (+1 if n_steps % diag_every != 0), or 1 if diag_every == 0.
+ * Workspaces (internal-order field copy, three Clenshaw buffers, barrier
+ * words) are allocated on first use and cached in the handle.
+ * Errors: INVALID_ARG, NONFINITE (field became non-finite), TIMEOUT, CUDA, OOM,
+ * UNSUPPORTED (n_fields > 64, or the PLAIN variant with C64).               */
+int decbpm_propagate(decbpm_mesh_t mesh, const decbpm_params *params, void *psi_dev, int64_t n_fields,
+                     void *stream, decbpm_diag *diag_out);
+
+/* Same with host buffers: copies psi_host (pinned or pageable) to the device,
+ * propagates, copies the result back into psi_host.                          */
+int decbpm_propagate_host(decbpm_mesh_t mesh, const decbpm_params *params, void *psi_host, int64_t n_fields,
+                          void *stream, decbpm_diag *diag_out);
+
+/* Diagnostics of fields already on the device (caller order). diag_out: n_fields records. */
+int decbpm_diagnostics(decbpm_mesh_t mesh, const void *psi_dev, int64_t n_fields, int32_t precision,
+                       void *stream, decbpm_diag *diag_out);
+
+/* ---- batched propagation: many meshes x many fields, one persistent launch ----
+ * A plan binds n_meshes mesh handles, each carrying fields_per_mesh[i] fields
+ * (all <= 64), at one precision.  It owns the workspaces and a CUDA graph per
+ * step block.  All meshes advance the same n_steps with the same dz; each
+ * mesh uses its own Chebyshev degree.                                       */
+int decbpm_plan_create(const decbpm_mesh_t *meshes, int32_t n_meshes, const int32_t *fields_per_mesh,
+                       int32_t precision, decbpm_plan_t *out);
+int decbpm_plan_destroy(decbpm_plan_t plan);
+/* psi_dev[i] is mesh i's field buffer [n_vertices_i * fields_per_mesh_i].
+ * diag_out (host, may be NULL): for each diagnostic point, for each mesh, its
+ * fields' records (sum_i fields_per_mesh_i records per point).              */
+int decbpm_plan_propagate(decbpm_plan_t plan, const decbpm_params *params, void *const *psi_dev,
+                          void *stream, decbpm_diag *diag_out);
+/* Host-buffer version of decbpm_plan_propagate (copies in, propagates, copies out). */
+int decbpm_plan_propagate_host(decbpm_plan_t plan, const decbpm_params *params, void *const *psi_host,
+                               void *stream, decbpm_diag *diag_out);
+/* Plan information: Chebyshev degree used by mesh i for step dz (0 if i is out of range). */
+int32_t decbpm_plan_degree(decbpm_plan_t plan, int32_t mesh_index, double dz, int32_t precision, double cheb_tol);
+
+/* Launch configuration of a plan. */
+typedef struct {
+    int32_t grid;          /* CTAs of the persistent cooperative launch (all co-resident) */
+    int32_t block;         /* threads per CTA */
+    int32_t fields_padded; /* fields per vertex in the internal layout (power of two >= max fields) */
+    int32_t graphs;        /* 1 if step blocks are replayed from captured CUDA graphs */
+    int32_t stages;        /* grid-wide stages per step for the last configured dz (max degree) */
+    int32_t n_meshes;
+} decbpm_plan_config;
+int decbpm_plan_get_config(decbpm_plan_t plan, decbpm_plan_config *cfg);
+
+/* Device time in ms, from CUDA events recorded on the launch stream, from the
+ * start of the first march-kernel launch to the end of the last one in the
+ * most recent decbpm_plan_propagate call (one launch when diag_every = 0). */
+int decbpm_plan_last_march_ms(decbpm_plan_t plan, double *ms);
+
+/* One-shot convenience: plan_create + plan_propagate + plan_destroy. */
+int decbpm_propagate_batch(const decbpm_mesh_t *meshes, int32_t n_meshes, const int32_t *fields_per_mesh,
+                           const decbpm_params *params, void *const *psi_dev, void *stream,
+                           decbpm_diag *diag_out);
+
+/* ---- failure-path self test ------------------------------------------------
+ * Launches a small cooperative kernel whose CTAs meet at the same bounded
+ * grid barrier the march kernel uses, but wait for `missing_arrivals` more
+ * arrivals than the grid provides, giving up after timeout_ns.  Returns
+ * DECBPM_ERR_TIMEOUT when missing_arrivals > 0 (the wait runs out, the kernel
+ * exits normally and the context stays usable) and DECBPM_OK when it is 0.   */
+int decbpm_selftest_barrier(int32_t missing_arrivals, int64_t timeout_ns, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DECBPM_H */

@@ -1,0 +1,264 @@
+"""Thin Python binding of the C ABI (include/decbpm.h).
+
+Argument marshalling only: every step of the propagation runs in libdecbpm's
+CUDA kernels.  Device fields are torch CUDA tensors (complex64 or complex128,
+shape [N0] or [N0, B], contiguous, in the caller's vertex order); the current
+torch stream is passed as the CUDA stream.
+"""
+from __future__ import annotations
+
+import ctypes
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import _lib as L
+
+
+def _lib():
+    return L.load()
+
+
+def _dptr(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double)) if a is not None else None
+
+
+def _iptr(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)) if a is not None else None
+
+
+def _desc(coords, cells, V_cell=None, chi_cell=None, sigma=None, p=(1.0,)):
+    coords = np.ascontiguousarray(coords, dtype=np.float64)
+    if coords.ndim == 1:
+        coords = coords.reshape(-1, 1)
+    cells = np.ascontiguousarray(cells, dtype=np.int32)
+    V_cell = None if V_cell is None else np.ascontiguousarray(V_cell, dtype=np.float64)
+    chi_cell = None if chi_cell is None else np.ascontiguousarray(chi_cell, dtype=np.float64)
+    sigma = None if sigma is None else np.ascontiguousarray(sigma, dtype=np.float64)
+    p = np.ascontiguousarray(np.atleast_1d(np.asarray(p, dtype=np.float64)))
+    keep = (coords, cells, V_cell, chi_cell, sigma, p)
+    d = L.MeshDesc(dim=coords.shape[1], n_vertices=coords.shape[0], n_cells=cells.shape[0],
+                   coords=_dptr(coords), cells=_iptr(cells), V_cell=_dptr(V_cell), chi_cell=_dptr(chi_cell),
+                   sigma_vertex=_dptr(sigma), p_n=_dptr(p), n_p=len(p))
+    return d, keep
+
+
+def _params(dz, n_steps, precision, kerr="lumped", diag_every=0, variant="fused", cheb_tol=0.0):
+    return L.Params(dz=float(dz), n_steps=int(n_steps), precision=precision,
+                    kerr_mode=L.KERR_LUMPED if kerr == "lumped" else L.KERR_ELEMENT,
+                    diag_every=int(diag_every), variant=L.VARIANT_FUSED if variant == "fused" else L.VARIANT_PLAIN,
+                    cheb_tol=float(cheb_tol))
+
+
+def _n_diag(n_steps, diag_every):
+    if n_steps == 0 or diag_every <= 0:
+        return 1
+    return n_steps // diag_every + (1 if n_steps % diag_every else 0)
+
+
+def _diag_array(buf, n_points, n_fields):
+    out = np.zeros((n_points, n_fields), dtype=[("z", "f8"), ("power", "f8"), ("hamiltonian", "f8"),
+                                                ("max_intensity", "f8")])
+    for i in range(n_points * n_fields):
+        d = buf[i]
+        out.flat[i] = (d.z, d.power, d.hamiltonian, d.max_intensity)
+    return out
+
+
+def _precision_of(t):
+    import torch
+    if t.dtype == torch.complex64:
+        return L.C64
+    if t.dtype == torch.complex128:
+        return L.C128
+    raise TypeError("field must be complex64 or complex128, got %s" % t.dtype)
+
+
+def _stream_handle(stream):
+    import torch
+    s = torch.cuda.current_stream() if stream is None else stream
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+# ---------------------------------------------------------------- host-only
+def assemble_host(coords, cells, V_cell=None, chi_cell=None, sigma=None, p=(1.0,)):
+    """decbpm_assemble_host: FP64 operators in caller order (no GPU needed)."""
+    lib = _lib()
+    d, keep = _desc(coords, cells, V_cell, chi_cell, sigma, p)
+    info = L.MeshInfo()
+    L.check(lib.decbpm_assemble_host(ctypes.byref(d), ctypes.byref(info), None, None, None, None, None, None, None))
+    n0, nnz = info.n_vertices, info.nnz_offdiag + info.n_vertices
+    m, v, chib = np.zeros(n0), np.zeros(n0), np.zeros(n0)
+    rowptr = np.zeros(n0 + 1, dtype=np.int64)
+    col = np.zeros(nnz, dtype=np.int32)
+    val = np.zeros(nnz)
+    perm = np.zeros(n0, dtype=np.int32)
+    L.check(lib.decbpm_assemble_host(ctypes.byref(d), ctypes.byref(info), _dptr(m), _dptr(v), _dptr(chib),
+                                     rowptr.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), _iptr(col), _dptr(val),
+                                     _iptr(perm)))
+    del keep
+    return {"info": info.as_dict(), "m": m, "v": v, "chib": chib, "K_rowptr": rowptr, "K_col": col, "K_val": val,
+            "perm": perm}
+
+
+def bessel_coefficients(a, tol=1e-16):
+    """decbpm_bessel_coefficients: J_0(a) .. J_{n-1}(a) with tail <= tol."""
+    lib = _lib()
+    n = ctypes.c_int32(0)
+    lib.decbpm_bessel_coefficients(float(a), float(tol), 0, None, ctypes.byref(n))
+    out = np.zeros(n.value)
+    L.check(lib.decbpm_bessel_coefficients(float(a), float(tol), n.value, _dptr(out), ctypes.byref(n)))
+    return out
+
+
+# ---------------------------------------------------------------- meshes
+class Mesh:
+    """A mesh handle (decbpm_mesh_create): operators assembled in FP64 and
+    uploaded to the current CUDA device."""
+
+    def __init__(self, coords, cells, V_cell=None, chi_cell=None, sigma=None, p=(1.0,)):
+        lib = _lib()
+        d, keep = _desc(coords, cells, V_cell, chi_cell, sigma, p)
+        h = ctypes.c_void_p()
+        L.check(lib.decbpm_mesh_create(ctypes.byref(d), ctypes.byref(h)))
+        del keep
+        self._h = h
+        self.n_vertices = int(np.asarray(coords).shape[0])
+
+    @classmethod
+    def from_workload(cls, m, p=(1.0,)):
+        return cls(m.coords, m.cells, m.V_cell, m.chi_cell, m.sigma, p)
+
+    @property
+    def handle(self):
+        return self._h
+
+    def info(self) -> dict:
+        inf = L.MeshInfo()
+        L.check(_lib().decbpm_mesh_info(self._h, ctypes.byref(inf)))
+        return inf.as_dict()
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            _lib().decbpm_mesh_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:  # noqa: BLE001
+            pass
+
+
+def mesh_create(coords, cells, V_cell=None, chi_cell=None, sigma=None, p=(1.0,)) -> Mesh:
+    return Mesh(coords, cells, V_cell, chi_cell, sigma, p)
+
+
+def _fields(psi):
+    if not psi.is_cuda or not psi.is_contiguous():
+        raise ValueError("field must be a contiguous CUDA tensor")
+    return 1 if psi.dim() == 1 else int(psi.shape[1])
+
+
+def propagate(mesh: Mesh, psi, dz, n_steps, diag_every=0, kerr="lumped", variant="fused", cheb_tol=0.0,
+              stream=None):
+    """decbpm_propagate: advance psi (torch CUDA [N0] or [N0, B]) in place.
+    Returns the diagnostics as a structured numpy array [n_points, B]."""
+    lib = _lib()
+    B = _fields(psi)
+    prm = _params(dz, n_steps, _precision_of(psi), kerr, diag_every, variant, cheb_tol)
+    npts = _n_diag(n_steps, diag_every)
+    buf = (L.Diag * (npts * B))()
+    L.check(lib.decbpm_propagate(mesh.handle, ctypes.byref(prm), ctypes.c_void_p(psi.data_ptr()), B,
+                                 _stream_handle(stream), buf))
+    return _diag_array(buf, npts, B)
+
+
+def propagate_host(mesh: Mesh, psi_host, dz, n_steps, diag_every=0, kerr="lumped", variant="fused", cheb_tol=0.0,
+                   stream=None):
+    """decbpm_propagate_host: psi_host is a CPU torch tensor (pinned for speed), updated in place."""
+    lib = _lib()
+    B = 1 if psi_host.dim() == 1 else int(psi_host.shape[1])
+    prm = _params(dz, n_steps, _precision_of(psi_host), kerr, diag_every, variant, cheb_tol)
+    npts = _n_diag(n_steps, diag_every)
+    buf = (L.Diag * (npts * B))()
+    L.check(lib.decbpm_propagate_host(mesh.handle, ctypes.byref(prm), ctypes.c_void_p(psi_host.data_ptr()), B,
+                                      _stream_handle(stream), buf))
+    return _diag_array(buf, npts, B)
+
+
+def diagnostics(mesh: Mesh, psi, stream=None):
+    lib = _lib()
+    B = _fields(psi)
+    buf = (L.Diag * B)()
+    L.check(lib.decbpm_diagnostics(mesh.handle, ctypes.c_void_p(psi.data_ptr()), B, _precision_of(psi),
+                                   _stream_handle(stream), buf))
+    return _diag_array(buf, 1, B)[0]
+
+
+# ---------------------------------------------------------------- plans
+class Plan:
+    """decbpm_plan_create: many meshes x many fields in one persistent launch."""
+
+    def __init__(self, meshes, fields_per_mesh, precision="c64"):
+        lib = _lib()
+        self.meshes = list(meshes)
+        self.fields = [int(f) for f in fields_per_mesh]
+        self.precision = L.C64 if precision in ("c64", L.C64) else L.C128
+        arr = (ctypes.c_void_p * len(self.meshes))(*[m.handle.value for m in self.meshes])
+        nf = (ctypes.c_int32 * len(self.fields))(*self.fields)
+        h = ctypes.c_void_p()
+        L.check(lib.decbpm_plan_create(arr, len(self.meshes), nf, self.precision, ctypes.byref(h)))
+        self._h = h
+
+    def degree(self, i, dz, cheb_tol=0.0):
+        return int(_lib().decbpm_plan_degree(self._h, i, float(dz), self.precision, float(cheb_tol)))
+
+    def propagate(self, psis, dz, n_steps, diag_every=0, kerr="lumped", cheb_tol=0.0, stream=None):
+        lib = _lib()
+        prm = _params(dz, n_steps, self.precision, kerr, diag_every, "fused", cheb_tol)
+        npts = _n_diag(n_steps, diag_every)
+        nrec = npts * sum(self.fields)
+        buf = (L.Diag * nrec)()
+        ptrs = (ctypes.c_void_p * len(psis))(*[p.data_ptr() for p in psis])
+        L.check(lib.decbpm_plan_propagate(self._h, ctypes.byref(prm), ptrs, _stream_handle(stream), buf))
+        return _diag_array(buf, npts, sum(self.fields))
+
+    def propagate_host(self, psis_host, dz, n_steps, diag_every=0, kerr="lumped", cheb_tol=0.0, stream=None):
+        lib = _lib()
+        prm = _params(dz, n_steps, self.precision, kerr, diag_every, "fused", cheb_tol)
+        npts = _n_diag(n_steps, diag_every)
+        buf = (L.Diag * (npts * sum(self.fields)))()
+        ptrs = (ctypes.c_void_p * len(psis_host))(*[p.data_ptr() for p in psis_host])
+        L.check(lib.decbpm_plan_propagate_host(self._h, ctypes.byref(prm), ptrs, _stream_handle(stream), buf))
+        return _diag_array(buf, npts, sum(self.fields))
+
+    def config(self) -> dict:
+        c = L.PlanConfig()
+        L.check(_lib().decbpm_plan_get_config(self._h, ctypes.byref(c)))
+        return c.as_dict()
+
+    def last_march_ms(self) -> float:
+        v = ctypes.c_double()
+        L.check(_lib().decbpm_plan_last_march_ms(self._h, ctypes.byref(v)))
+        return v.value
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            _lib().decbpm_plan_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:  # noqa: BLE001
+            pass
+
+
+def plan_create(meshes, fields_per_mesh, precision="c64") -> Plan:
+    return Plan(meshes, fields_per_mesh, precision)
+
+
+def selftest_barrier(missing_arrivals: int, timeout_ns: int, stream=None) -> int:
+    """decbpm_selftest_barrier: returns the status code (no exception)."""
+    return int(_lib().decbpm_selftest_barrier(int(missing_arrivals), int(timeout_ns), _stream_handle(stream)))

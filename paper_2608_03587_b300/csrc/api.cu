@@ -1,0 +1,948 @@
+// C ABI of libdecbpm: mesh handles, plans, propagation and diagnostics.
+// See include/decbpm.h for the contract of every entry point.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <numeric>
+#include <tuple>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "decbpm.h"
+#include "internal.h"
+#include "kernels.cuh"
+
+namespace decbpm {
+const char *last_error_cstr();
+}
+using namespace decbpm;
+
+#define CK(call)                                                                                       \
+    do {                                                                                               \
+        cudaError_t e_ = (call);                                                                       \
+        if (e_ != cudaSuccess) {                                                                       \
+            return fail(e_ == cudaErrorMemoryAllocation ? DECBPM_ERR_OOM : DECBPM_ERR_CUDA,            \
+                        "%s: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, __LINE__);          \
+        }                                                                                              \
+    } while (0)
+
+#define TRY(call)                        \
+    do {                                 \
+        int rc_ = (call);                \
+        if (rc_ != DECBPM_OK) return rc_; \
+    } while (0)
+
+namespace {
+
+struct DevAllocs {
+    std::vector<void *> ptrs;
+    size_t bytes = 0;
+    template <class T> int alloc(T **p, size_t n) {
+        *p = nullptr;
+        if (n == 0) n = 1;
+        cudaError_t e = cudaMalloc((void **)p, n * sizeof(T));
+        if (e != cudaSuccess) {
+            *p = nullptr;
+            return fail(DECBPM_ERR_OOM, "cudaMalloc of %zu bytes failed: %s", n * sizeof(T), cudaGetErrorString(e));
+        }
+        ptrs.push_back((void *)*p);
+        bytes += n * sizeof(T);
+        return DECBPM_OK;
+    }
+    template <class T> int upload(T **p, const std::vector<T> &h) {
+        TRY(alloc(p, h.size()));
+        CK(cudaMemcpy(*p, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice));
+        return DECBPM_OK;
+    }
+    void release() {
+        for (void *p : ptrs) cudaFree(p);
+        ptrs.clear();
+        bytes = 0;
+    }
+};
+
+template <typename R> std::vector<R> cast(const std::vector<double> &x) { return std::vector<R>(x.begin(), x.end()); }
+
+int ilog2(int x) { int l = 0; while ((1 << l) < x) ++l; return l; }
+
+}  // namespace
+
+// ============================================================== mesh handle
+struct decbpm_mesh_s {
+    Assembly A;
+    Sell S;
+    int device = 0;
+    DevAllocs mem;
+    int32_t *slice_ptr = nullptr, *slice_w = nullptr, *col = nullptr, *perm = nullptr;
+    float *x32, *xd32, *v32, *chib32, *sig32, *coff32, *cdiag32;
+    double *x64, *xd64, *v64, *chib64, *sig64, *coff64, *cdiag64, *w64, *m64;
+    int32_t *csr_ptr = nullptr, *csr_col = nullptr;
+    double *csr_val = nullptr;
+    std::map<std::pair<int, int>, decbpm_plan_t> plans;   // (fields, precision) -> cached single-mesh plan
+    double r() const { return 0.5 * A.rho; }
+};
+
+static int mesh_upload(decbpm_mesh_t M) {
+    const Assembly &A = M->A;
+    const Sell &S = M->S;
+    const int64_t n0 = A.n0;
+    const double c = 0.5 * A.rho, r = 0.5 * A.rho;
+    // X = (A - c)/r with A = *0^{-1} K:  X_pq = -w_pq / (r m_p),  X_pp = (sum_q w_pq / m_p - c) / r
+    std::vector<double> xval(S.col.size()), xdiag(n0), wv(S.col.size()), cv(S.col.size());
+    std::vector<double> m(n0), v(n0), chib(n0), sig(n0), cdiag(n0);
+    for (int64_t sl = 0; sl < S.n_slices; ++sl)
+        for (int j = 0; j < S.slice_w[sl]; ++j)
+            for (int lane = 0; lane < kSlice; ++lane) {
+                const int64_t idx = S.slice_ptr[sl] + int64_t(j) * kSlice + lane;
+                const int64_t row = sl * kSlice + lane;
+                const double mp = row < n0 ? A.m[A.perm[row]] : 1.0;
+                xval[idx] = -S.w[idx] / (r * mp);
+                wv[idx] = S.w[idx];
+                cv[idx] = S.c[idx];
+            }
+    for (int64_t i = 0; i < n0; ++i) {
+        const int32_t o = A.perm[i];
+        m[i] = A.m[o];
+        xdiag[i] = (A.wsum[o] / A.m[o] - c) / r;
+        v[i] = A.v[o];
+        chib[i] = A.chib[o];
+        sig[i] = A.sigma[o];
+        cdiag[i] = A.c_diag[o];
+    }
+    DevAllocs &D = M->mem;
+    TRY(D.upload(&M->slice_ptr, S.slice_ptr));
+    TRY(D.upload(&M->slice_w, S.slice_w));
+    TRY(D.upload(&M->col, S.col));
+    TRY(D.upload(&M->perm, A.perm));
+    TRY(D.upload(&M->x32, cast<float>(xval)));
+    TRY(D.upload(&M->xd32, cast<float>(xdiag)));
+    TRY(D.upload(&M->v32, cast<float>(v)));
+    TRY(D.upload(&M->chib32, cast<float>(chib)));
+    TRY(D.upload(&M->sig32, cast<float>(sig)));
+    TRY(D.upload(&M->coff32, cast<float>(cv)));
+    TRY(D.upload(&M->cdiag32, cast<float>(cdiag)));
+    TRY(D.upload(&M->x64, xval));
+    TRY(D.upload(&M->xd64, xdiag));
+    TRY(D.upload(&M->v64, v));
+    TRY(D.upload(&M->chib64, chib));
+    TRY(D.upload(&M->sig64, sig));
+    TRY(D.upload(&M->coff64, cv));
+    TRY(D.upload(&M->cdiag64, cdiag));
+    TRY(D.upload(&M->w64, wv));
+    TRY(D.upload(&M->m64, m));
+    // CSR of X (diagonal included) in internal order for the plain path
+    std::vector<int32_t> rp(n0 + 1, 0), cc;
+    std::vector<double> vv;
+    cc.reserve(A.col.size() + n0);
+    vv.reserve(A.col.size() + n0);
+    for (int64_t i = 0; i < n0; ++i) {
+        const int32_t o = A.perm[i];
+        std::vector<std::pair<int32_t, double>> row;
+        row.push_back({int32_t(i), xdiag[i]});
+        for (int64_t k = A.rowptr[o]; k < A.rowptr[o + 1]; ++k) row.push_back({A.iperm[A.col[k]], -A.w[k] / (r * A.m[o])});
+        std::sort(row.begin(), row.end());
+        for (auto &e : row) { cc.push_back(e.first); vv.push_back(e.second); }
+        rp[i + 1] = int32_t(cc.size());
+    }
+    TRY(D.upload(&M->csr_ptr, rp));
+    TRY(D.upload(&M->csr_col, cc));
+    TRY(D.upload(&M->csr_val, vv));
+    return DECBPM_OK;
+}
+
+// ============================================================== plans
+struct decbpm_plan_s {
+    std::vector<decbpm_mesh_t> meshes;
+    std::vector<int32_t> B;
+    int bpad = 1, bpad_log2 = 0, precision = DECBPM_C64, fpt = 1;
+    int device = 0, num_sms = 0;
+    int block = 512, grid = 0;
+    DevAllocs mem;
+    std::vector<void *> psi, b0, b1, b2, user;   // user: device staging for the host-buffer entry points
+    void *y_plain = nullptr;                     // SpMV result of the plain path
+    void *views = nullptr, *coef = nullptr;
+    int32_t *active = nullptr;
+    int coef_cap = 0, active_cap = 0;
+    unsigned long long *barrier = nullptr;
+    int *status = nullptr;
+    double *partial = nullptr, *diag_dev = nullptr, *diag_host = nullptr;   // diag_host pinned
+    int diag_cap = 0;
+    std::vector<int> diag_blocks;
+    cudaStream_t cap_stream = nullptr;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    // coefficient configuration
+    double cfg_dz = 0, cfg_tol = -1;
+    std::vector<int> order, M, item_begin, items;
+    int S = 0, total_items = 0;
+    // graphs: key -> exec
+    std::map<std::tuple<double, int64_t, int32_t, int32_t, double>, cudaGraphExec_t> graphs;
+    bool graphs_ok = true;
+    ~decbpm_plan_s() {
+        for (auto &g : graphs) cudaGraphExecDestroy(g.second);
+        if (diag_host) cudaFreeHost(diag_host);
+        if (cap_stream) cudaStreamDestroy(cap_stream);
+        if (ev0) cudaEventDestroy(ev0);
+        if (ev1) cudaEventDestroy(ev1);
+        mem.release();
+    }
+};
+
+// Pinned host buffer for diagnostics of n_points points; graphs hold its
+// address, so they are dropped when it moves.
+static int ensure_diag_host(decbpm_plan_t P, int n_points) {
+    if (n_points <= P->diag_cap && P->diag_host) return DECBPM_OK;
+    for (auto &g : P->graphs) cudaGraphExecDestroy(g.second);
+    P->graphs.clear();
+    if (P->diag_host) cudaFreeHost(P->diag_host);
+    P->diag_host = nullptr;
+    P->diag_cap = 0;
+    CK(cudaMallocHost(&P->diag_host, sizeof(double) * size_t(n_points) * P->meshes.size() * P->bpad * kDiagQ));
+    P->diag_cap = n_points;
+    return DECBPM_OK;
+}
+
+static size_t csize(int precision) { return precision == DECBPM_C64 ? 8 : 16; }
+
+template <typename R, int FPT> static const void *march_fn() { return (const void *)march_kernel<R, FPT>; }
+
+static const void *march_kernel_ptr(int precision, int fpt) {
+    if (precision == DECBPM_C64) return fpt == 2 ? march_fn<float, 2>() : march_fn<float, 1>();
+    return fpt == 2 ? march_fn<double, 2>() : march_fn<double, 1>();
+}
+
+static int plan_create_impl(const decbpm_mesh_t *meshes, int32_t n, const int32_t *fields, int32_t precision,
+                            decbpm_plan_t *out) {
+    if (!out) return fail(DECBPM_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (!meshes || !fields || n < 1 || n > kMaxMeshes)
+        return fail(DECBPM_ERR_INVALID_ARG, "need 1..%d meshes with field counts", kMaxMeshes);
+    if (precision != DECBPM_C64 && precision != DECBPM_C128) return fail(DECBPM_ERR_INVALID_ARG, "bad precision %d", precision);
+    int maxB = 0;
+    for (int i = 0; i < n; ++i) {
+        if (!meshes[i]) return fail(DECBPM_ERR_INVALID_ARG, "mesh %d is NULL", i);
+        if (fields[i] < 1 || fields[i] > kMaxFields)
+            return fail(DECBPM_ERR_UNSUPPORTED, "fields per mesh must be in 1..%d (mesh %d has %d)", kMaxFields, i, fields[i]);
+        maxB = std::max(maxB, int(fields[i]));
+    }
+    auto P = std::make_unique<decbpm_plan_s>();
+    P->meshes.assign(meshes, meshes + n);
+    P->B.assign(fields, fields + n);
+    P->precision = precision;
+    P->bpad_log2 = ilog2(maxB);
+    P->bpad = 1 << P->bpad_log2;
+    P->fpt = P->bpad >= 2 ? 2 : 1;
+    CK(cudaGetDevice(&P->device));
+    CK(cudaDeviceGetAttribute(&P->num_sms, cudaDevAttrMultiProcessorCount, P->device));
+    const size_t cs = csize(precision);
+    for (int i = 0; i < n; ++i) {
+        const size_t elems = size_t(meshes[i]->A.n0) * P->bpad;
+        void *a, *b, *c, *d;
+        char *t;
+        TRY(P->mem.alloc(&t, elems * cs)); a = t;
+        TRY(P->mem.alloc(&t, elems * cs)); b = t;
+        TRY(P->mem.alloc(&t, elems * cs)); c = t;
+        TRY(P->mem.alloc(&t, elems * cs)); d = t;
+        P->psi.push_back(a); P->b0.push_back(b); P->b1.push_back(c); P->b2.push_back(d);
+        P->user.push_back(nullptr);
+        // deterministic diagnostic grid: depends on n0 and the SM count only
+        const int rows_per_block = std::max(1, kDiagThreads >> P->bpad_log2);
+        P->diag_blocks.push_back(int(std::min<int64_t>(2 * P->num_sms, (meshes[i]->A.n0 + rows_per_block - 1) / rows_per_block)));
+    }
+    char *t;
+    TRY(P->mem.alloc(&t, precision == DECBPM_C64 ? sizeof(MeshView<float>) * n : sizeof(MeshView<double>) * n));
+    P->views = t;
+    TRY(P->mem.alloc(&P->barrier, 1));
+    TRY(P->mem.alloc(&P->status, 1));
+    CK(cudaMemset(P->status, 0, sizeof(int)));
+    int maxdb = *std::max_element(P->diag_blocks.begin(), P->diag_blocks.end());
+    TRY(P->mem.alloc(&P->partial, size_t(maxdb) * P->bpad * kDiagQ));
+    TRY(P->mem.alloc(&P->diag_dev, size_t(n) * P->bpad * kDiagQ));
+    CK(cudaStreamCreateWithFlags(&P->cap_stream, cudaStreamNonBlocking));
+    CK(cudaEventCreate(&P->ev0));
+    CK(cudaEventCreate(&P->ev1));
+    // occupancy-derived persistent grid: every CTA must be co-resident
+    int per_sm = 0;
+    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, march_kernel_ptr(precision, P->fpt), P->block, 0));
+    if (per_sm < 1) return fail(DECBPM_ERR_CUDA, "march kernel cannot be resident with %d threads", P->block);
+    P->grid = P->num_sms * std::min(per_sm, 2);
+    *out = P.release();
+    return DECBPM_OK;
+}
+
+// Chebyshev degrees and stage tables for one step length.
+template <typename R>
+static int plan_configure(decbpm_plan_t P, double dz, double tol) {
+    if (P->cfg_dz == dz && P->cfg_tol == tol && !P->order.empty()) return DECBPM_OK;
+    using C = typename CT<R>::c2;
+    const int n = int(P->meshes.size());
+    std::vector<Cheb> ch(n);
+    for (int i = 0; i < n; ++i) TRY(cheb_coefficients(P->meshes[i]->A.p, P->meshes[i]->A.rho, dz, tol, ch[i]));
+    P->order.resize(n);
+    std::iota(P->order.begin(), P->order.end(), 0);
+    std::stable_sort(P->order.begin(), P->order.end(), [&](int a, int b) { return ch[a].M > ch[b].M; });
+    P->M.resize(n);
+    for (int i = 0; i < n; ++i) P->M[i] = ch[i].M;
+    P->S = ch[P->order[0]].M;
+    const int tpr_log2 = P->bpad_log2 - (P->fpt == 2 ? 1 : 0);
+    const int rpw = 32 >> tpr_log2;
+    P->item_begin.assign(n, 0);
+    P->items.assign(n, 0);
+    int acc = 0;
+    for (int j = 0; j < n; ++j) {
+        const int i = P->order[j];
+        P->item_begin[i] = acc;
+        P->items[i] = int((P->meshes[i]->A.n0 + rpw - 1) / rpw);
+        acc += P->items[i];
+    }
+    P->total_items = acc;
+    std::vector<int32_t> active(P->S);
+    for (int s = 0; s < P->S; ++s) {
+        const int k = P->S - 1 - s;
+        int a = 0;
+        for (int j = 0; j < n; ++j)
+            if (ch[P->order[j]].M > k) a += P->items[P->order[j]];
+        active[s] = a;
+    }
+    // stage tables (see StageCoef): fold b_M = a_M psi into the first two stages
+    int total_coef = 0;
+    for (int i = 0; i < n; ++i) total_coef += ch[i].M;
+    if (total_coef > P->coef_cap) {
+        char *t;
+        TRY(P->mem.alloc(&t, sizeof(StageCoef<R>) * total_coef));
+        P->coef = t;
+        P->coef_cap = total_coef;
+    }
+    if (P->S > P->active_cap) {
+        TRY(P->mem.alloc(&P->active, P->S));
+        P->active_cap = P->S;
+    }
+    std::vector<StageCoef<R>> coef(total_coef);
+    std::vector<MeshView<R>> views(n);
+    int off = 0;
+    auto mk = [](std::complex<double> z) { C c; c.x = R(z.real()); c.y = R(z.imag()); return c; };
+    for (int j = 0; j < n; ++j) {
+        const int i = P->order[j];
+        const Cheb &cb = ch[i];
+        const int Mi = cb.M;
+        for (int k = 0; k < Mi; ++k) {
+            StageCoef<R> s{};
+            std::complex<double> alpha = cb.a[k], beta = (k == 0) ? 1.0 : 2.0;
+            int flags = 0;
+            if (k == Mi - 1) { flags |= kGisPsi; beta = 2.0 * cb.a[Mi]; }
+            else if (k == Mi - 2) { alpha = cb.a[k] - cb.a[Mi]; }
+            else flags |= kHasH;
+            if (k == 0) flags |= kFinal;
+            s.alpha = mk(alpha);
+            s.beta = mk(beta);
+            s.flags = flags;
+            coef[off + k] = s;
+        }
+        decbpm_mesh_t m = P->meshes[i];
+        MeshView<R> &v = views[j];
+        v.n0 = int32_t(m->A.n0);
+        v.n_slices = int32_t(m->S.n_slices);
+        v.M = Mi;
+        v.item_begin = P->item_begin[i];
+        v.slice_ptr = m->slice_ptr; v.slice_w = m->slice_w; v.col = m->col;
+        if constexpr (sizeof(R) == 4) {
+            v.xval = m->x32; v.xdiag = m->xd32; v.v = m->v32; v.chib = m->chib32; v.sigma = m->sig32;
+            v.coff = m->coff32; v.cdiag = m->cdiag32;
+        } else {
+            v.xval = m->x64; v.xdiag = m->xd64; v.v = m->v64; v.chib = m->chib64; v.sigma = m->sig64;
+            v.coff = m->coff64; v.cdiag = m->cdiag64;
+        }
+        v.psi = (C *)P->psi[i];
+        v.b[0] = (C *)P->b0[i]; v.b[1] = (C *)P->b1[i]; v.b[2] = (C *)P->b2[i];
+        v.coef = (const StageCoef<R> *)P->coef + off;
+        off += Mi;
+    }
+    CK(cudaMemcpy(P->coef, coef.data(), sizeof(StageCoef<R>) * total_coef, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(P->active, active.data(), sizeof(int32_t) * P->S, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(P->views, views.data(), sizeof(MeshView<R>) * n, cudaMemcpyHostToDevice));
+    for (auto &g : P->graphs) cudaGraphExecDestroy(g.second);
+    P->graphs.clear();
+    P->cfg_dz = dz;
+    P->cfg_tol = tol;
+    return DECBPM_OK;
+}
+
+template <typename R>
+static int launch_march(decbpm_plan_t P, cudaStream_t s, int n_steps, int kerr_mode, double dz) {
+    MarchParams<R> mp{};
+    mp.meshes = (const MeshView<R> *)P->views;
+    mp.active_items = P->active;
+    mp.n_meshes = int32_t(P->meshes.size());
+    mp.S = P->S;
+    mp.total_items = P->total_items;
+    mp.n_steps = n_steps;
+    mp.pre_half = 1;
+    mp.post_half = 1;
+    mp.kerr_mode = kerr_mode;
+    mp.bpad_log2 = P->bpad_log2;
+    mp.h = R(dz);
+    mp.barrier = P->barrier;
+    mp.status = P->status;
+    mp.timeout_ns = kBarrierTimeoutNs;
+    CK(cudaMemsetAsync(P->barrier, 0, sizeof(unsigned long long), s));
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(P->grid);
+    cfg.blockDim = dim3(P->block);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    if (P->fpt == 2) CK(cudaLaunchKernelEx(&cfg, march_kernel<R, 2>, mp));
+    else CK(cudaLaunchKernelEx(&cfg, march_kernel<R, 1>, mp));
+    return DECBPM_OK;
+}
+
+template <typename R>
+static int launch_diag(decbpm_plan_t P, cudaStream_t s, int kerr_mode, int point) {
+    // writes diag_dev[mesh][f][q] and copies to diag_host[point][mesh][f][q]
+    const int n = int(P->meshes.size());
+    for (int i = 0; i < n; ++i) {
+        decbpm_mesh_t m = P->meshes[i];
+        diag_partial_kernel<R><<<P->diag_blocks[i], kDiagThreads, 0, s>>>(
+            (const typename CT<R>::c2 *)P->psi[i], int32_t(m->A.n0), P->bpad_log2, P->B[i], m->slice_ptr, m->slice_w,
+            m->col, m->w64, m->m64, m->v64, m->chib64, m->coff64, m->cdiag64, kerr_mode, P->partial);
+        diag_final_kernel<<<1, 64, 0, s>>>(P->partial, P->diag_blocks[i], P->bpad, P->diag_dev + size_t(i) * P->bpad * kDiagQ);
+    }
+    CK(cudaGetLastError());
+    const size_t per_point = size_t(n) * P->bpad * kDiagQ;
+    CK(cudaMemcpyAsync(P->diag_host + per_point * point, P->diag_dev, per_point * sizeof(double), cudaMemcpyDeviceToHost, s));
+    return DECBPM_OK;
+}
+
+// The device work of one propagate call: step blocks, diagnostics after each.
+template <typename R>
+static int enqueue_march(decbpm_plan_t P, cudaStream_t s, const decbpm_params *prm, int n_points) {
+    const int64_t every = prm->diag_every > 0 ? prm->diag_every : std::max<int64_t>(prm->n_steps, 1);
+    int64_t done = 0;
+    int point = 0;
+    bool first = true;
+    while (done < prm->n_steps) {
+        const int64_t nb = std::min<int64_t>(every, prm->n_steps - done);
+        if (nb > 0x7fffffff) return fail(DECBPM_ERR_INVALID_ARG, "step block too long");
+        if (first) CK(cudaEventRecordWithFlags(P->ev0, s, cudaEventRecordExternal));
+        TRY(launch_march<R>(P, s, int(nb), prm->kerr_mode, prm->dz));
+        if (done + nb >= prm->n_steps) CK(cudaEventRecordWithFlags(P->ev1, s, cudaEventRecordExternal));
+        first = false;
+        done += nb;
+        TRY(launch_diag<R>(P, s, prm->kerr_mode, point++));
+    }
+    if (prm->n_steps == 0) {
+        CK(cudaEventRecordWithFlags(P->ev0, s, cudaEventRecordExternal));
+        CK(cudaEventRecordWithFlags(P->ev1, s, cudaEventRecordExternal));
+        TRY(launch_diag<R>(P, s, prm->kerr_mode, point++));
+    }
+    (void)n_points;
+    return DECBPM_OK;
+}
+
+static int n_diag_points(const decbpm_params *p) {
+    if (p->n_steps == 0) return 1;
+    if (p->diag_every <= 0) return 1;
+    return int(p->n_steps / p->diag_every + (p->n_steps % p->diag_every ? 1 : 0));
+}
+
+static int check_params(const decbpm_params *p) {
+    if (!p) return fail(DECBPM_ERR_INVALID_ARG, "params is NULL");
+    if (!(p->dz > 0) || !std::isfinite(p->dz)) return fail(DECBPM_ERR_INVALID_ARG, "dz must be finite and > 0");
+    if (p->n_steps < 0) return fail(DECBPM_ERR_INVALID_ARG, "n_steps < 0");
+    if (p->precision != DECBPM_C64 && p->precision != DECBPM_C128) return fail(DECBPM_ERR_INVALID_ARG, "bad precision");
+    if (p->kerr_mode != DECBPM_KERR_LUMPED && p->kerr_mode != DECBPM_KERR_ELEMENT) return fail(DECBPM_ERR_INVALID_ARG, "bad kerr_mode");
+    if (p->diag_every < 0) return fail(DECBPM_ERR_INVALID_ARG, "diag_every < 0");
+    if (p->variant != DECBPM_VARIANT_FUSED && p->variant != DECBPM_VARIANT_PLAIN) return fail(DECBPM_ERR_INVALID_ARG, "bad variant");
+    if (!(p->cheb_tol >= 0)) return fail(DECBPM_ERR_INVALID_ARG, "cheb_tol < 0");
+    return DECBPM_OK;
+}
+
+static double default_tol(const decbpm_params *p) {
+    if (p->cheb_tol > 0) return p->cheb_tol;
+    return p->precision == DECBPM_C64 ? 1e-9 : 1e-16;
+}
+
+static int finish_diag(decbpm_plan_t P, const decbpm_params *prm, int n_points, decbpm_diag *out) {
+    const int n = int(P->meshes.size());
+    bool finite = true;
+    int rec = 0;
+    const int64_t every = prm->diag_every > 0 ? prm->diag_every : std::max<int64_t>(prm->n_steps, 1);
+    for (int pt = 0; pt < n_points; ++pt) {
+        const int64_t steps_done = prm->n_steps == 0 ? 0 : std::min<int64_t>(prm->n_steps, (pt + 1) * every);
+        for (int i = 0; i < n; ++i) {
+            const std::vector<double> &p = P->meshes[i]->A.p;
+            for (int f = 0; f < P->B[i]; ++f) {
+                const double *q = P->diag_host + ((size_t(pt) * n + i) * P->bpad + f) * kDiagQ;
+                decbpm_diag d;
+                d.z = double(steps_done) * prm->dz;
+                d.power = q[0];
+                double lin = NAN;
+                if (p.size() == 1) lin = p[0] * q[1];
+                else if (p.size() == 2) lin = p[0] * q[1] - p[1] * q[2];
+                d.hamiltonian = lin - q[3] - 0.5 * q[4];
+                d.max_intensity = q[5];
+                if (!std::isfinite(d.power) || !std::isfinite(d.max_intensity)) finite = false;
+                if (out) out[rec] = d;
+                ++rec;
+            }
+        }
+    }
+    if (!finite) return fail(DECBPM_ERR_NONFINITE, "field became non-finite (check dz, input amplitude and p_n)");
+    return DECBPM_OK;
+}
+
+template <typename R>
+static int plan_propagate_impl(decbpm_plan_t P, const decbpm_params *prm, void *const *psi_dev, cudaStream_t s,
+                               decbpm_diag *diag_out) {
+    using C = typename CT<R>::c2;
+    const int n = int(P->meshes.size());
+    TRY(plan_configure<R>(P, prm->dz, default_tol(prm)));
+    const int n_points = n_diag_points(prm);
+    TRY(ensure_diag_host(P, n_points));
+    CK(cudaMemsetAsync(P->status, 0, sizeof(int), s));
+    for (int i = 0; i < n; ++i) {
+        const int64_t n0 = P->meshes[i]->A.n0;
+        const int blocks = int(std::min<int64_t>(4 * P->num_sms, (n0 * P->bpad + 255) / 256));
+        permute_in_kernel<C><<<blocks, 256, 0, s>>>((const C *)psi_dev[i], (C *)P->psi[i], P->meshes[i]->perm,
+                                                     int32_t(n0), P->B[i], P->bpad);
+    }
+    CK(cudaGetLastError());
+    // capture the march + diagnostics once per parameter set, replay afterwards
+    auto key = std::make_tuple(prm->dz, prm->n_steps, prm->diag_every, prm->kerr_mode, default_tol(prm));
+    bool launched = false;
+    if (P->graphs_ok) {
+        auto it = P->graphs.find(key);
+        if (it == P->graphs.end()) {
+            cudaGraph_t g = nullptr;
+            cudaGraphExec_t ge = nullptr;
+            bool ok = cudaStreamBeginCapture(P->cap_stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+            int rc = DECBPM_OK;
+            if (ok) rc = enqueue_march<R>(P, P->cap_stream, prm, n_points);
+            cudaError_t ec = ok ? cudaStreamEndCapture(P->cap_stream, &g) : cudaErrorUnknown;
+            if (ok && rc == DECBPM_OK && ec == cudaSuccess && g &&
+                cudaGraphInstantiate(&ge, g, 0) == cudaSuccess) {
+                it = P->graphs.emplace(key, ge).first;
+            } else {
+                P->graphs_ok = false;   // capture unsupported here: launch directly from now on
+                cudaGetLastError();
+            }
+            if (g) cudaGraphDestroy(g);
+        }
+        if (it != P->graphs.end()) {
+            CK(cudaGraphLaunch(it->second, s));
+            launched = true;
+        }
+    }
+    if (!launched) TRY(enqueue_march<R>(P, s, prm, n_points));
+    for (int i = 0; i < n; ++i) {
+        const int64_t n0 = P->meshes[i]->A.n0;
+        const int blocks = int(std::min<int64_t>(4 * P->num_sms, (n0 * P->B[i] + 255) / 256));
+        permute_out_kernel<C><<<blocks, 256, 0, s>>>((const C *)P->psi[i], (C *)psi_dev[i], P->meshes[i]->perm,
+                                                      int32_t(n0), P->B[i], P->bpad);
+    }
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(s));
+    int status = 0;
+    CK(cudaMemcpy(&status, P->status, sizeof(int), cudaMemcpyDeviceToHost));
+    if (status == DECBPM_ERR_TIMEOUT) return fail(DECBPM_ERR_TIMEOUT, "grid barrier timed out in the march kernel");
+    if (status != 0) return fail(status, "device reported status %d", status);
+    return finish_diag(P, prm, n_points, diag_out);
+}
+
+static int plan_propagate_dispatch(decbpm_plan_t P, const decbpm_params *prm, void *const *psi_dev, void *stream,
+                                   decbpm_diag *diag_out) {
+    TRY(check_params(prm));
+    if (!P) return fail(DECBPM_ERR_INVALID_ARG, "plan is NULL");
+    if (!psi_dev) return fail(DECBPM_ERR_INVALID_ARG, "psi_dev is NULL");
+    for (size_t i = 0; i < P->meshes.size(); ++i)
+        if (!psi_dev[i]) return fail(DECBPM_ERR_INVALID_ARG, "psi_dev[%zu] is NULL", i);
+    if (prm->precision != P->precision) return fail(DECBPM_ERR_INVALID_ARG, "params precision differs from the plan's");
+    if (prm->variant != DECBPM_VARIANT_FUSED) return fail(DECBPM_ERR_UNSUPPORTED, "plans run the fused variant only");
+    if (P->precision == DECBPM_C64) return plan_propagate_impl<float>(P, prm, psi_dev, (cudaStream_t)stream, diag_out);
+    return plan_propagate_impl<double>(P, prm, psi_dev, (cudaStream_t)stream, diag_out);
+}
+
+// ============================================================== plain FP64 path
+struct PlainWork {
+    double2 *psi = nullptr, *y = nullptr, *b[3] = {nullptr, nullptr, nullptr};
+};
+
+static int propagate_plain(decbpm_mesh_t m, const decbpm_params *prm, void *psi_dev, cudaStream_t s, decbpm_diag *diag_out) {
+    if (prm->precision != DECBPM_C128) return fail(DECBPM_ERR_UNSUPPORTED, "the plain variant is FP64 (C128) only");
+    const int n0 = int(m->A.n0);
+    Cheb cb;
+    TRY(cheb_coefficients(m->A.p, m->A.rho, prm->dz, default_tol(prm), cb));
+    // one-field C128 plan for buffers, permutation and diagnostics
+    decbpm_plan_t P = nullptr;
+    auto key = std::make_pair(1, int(DECBPM_C128));
+    auto it = m->plans.find(key);
+    if (it == m->plans.end()) {
+        int32_t one = 1;
+        TRY(plan_create_impl(&m, 1, &one, DECBPM_C128, &P));
+        m->plans[key] = P;
+    } else P = it->second;
+    TRY(plan_configure<double>(P, prm->dz, default_tol(prm)));
+    double2 *psi = (double2 *)P->psi[0];
+    double2 *b[3] = {(double2 *)P->b0[0], (double2 *)P->b1[0], (double2 *)P->b2[0]};
+    if (!P->y_plain) {
+        char *t;
+        TRY(P->mem.alloc(&t, size_t(n0) * 16));
+        P->y_plain = t;
+    }
+    double2 *y = (double2 *)P->y_plain;
+    const int n_points = n_diag_points(prm);
+    TRY(ensure_diag_host(P, n_points));
+    const int T = 256, G = (n0 + T - 1) / T;
+    permute_in_kernel<double2><<<std::min(G, 4 * P->num_sms), T, 0, s>>>((const double2 *)psi_dev, psi, m->perm, n0, 1, 1);
+    const int64_t every = prm->diag_every > 0 ? prm->diag_every : std::max<int64_t>(prm->n_steps, 1);
+    const int M = cb.M;
+    int point = 0;
+    CK(cudaEventRecord(P->ev0, s));
+    for (int64_t step = 0; step < prm->n_steps; ++step) {
+        const bool block_start = (step % every) == 0;
+        const bool block_end = ((step + 1) % every) == 0 || step + 1 == prm->n_steps;
+        if (block_start)
+            plain_diag_flow_kernel<<<G, T, 0, s>>>(psi, m->v64, m->chib64, m->sig64, 0.5 * prm->dz, n0);
+        for (int k = M - 1; k >= 0; --k) {
+            std::complex<double> alpha = cb.a[k], beta = (k == 0) ? 1.0 : 2.0;
+            int has_h = 1;
+            const double2 *g = b[(k + 1) % 3];
+            if (k == M - 1) { g = psi; beta = 2.0 * cb.a[M]; has_h = 0; }
+            else if (k == M - 2) { alpha = cb.a[k] - cb.a[M]; has_h = 0; }
+            plain_spmv_kernel<<<G, T, 0, s>>>(m->csr_ptr, m->csr_col, m->csr_val, g, y, n0);
+            double2 *outp = (k == 0) ? psi : b[k % 3];
+            plain_update_kernel<<<G, T, 0, s>>>(psi, y, b[(k + 2) % 3], outp, make_double2(alpha.real(), alpha.imag()),
+                                                make_double2(beta.real(), beta.imag()), has_h, n0);
+        }
+        plain_diag_flow_kernel<<<G, T, 0, s>>>(psi, m->v64, m->chib64, m->sig64, block_end ? 0.5 * prm->dz : prm->dz, n0);
+        if (block_end) {
+            if (step + 1 == prm->n_steps) CK(cudaEventRecord(P->ev1, s));
+            TRY(launch_diag<double>(P, s, DECBPM_KERR_LUMPED, point++));
+        }
+    }
+    if (prm->n_steps == 0) {
+        CK(cudaEventRecord(P->ev1, s));
+        TRY(launch_diag<double>(P, s, DECBPM_KERR_LUMPED, point++));
+    }
+    permute_out_kernel<double2><<<std::min(G, 4 * P->num_sms), T, 0, s>>>(psi, (double2 *)psi_dev, m->perm, n0, 1, 1);
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(s));
+    return finish_diag(P, prm, n_points, diag_out);
+}
+
+// ============================================================== C ABI
+extern "C" {
+
+const char *decbpm_version(void) { return "decbpm 0.1 (sm_103a)"; }
+
+const char *decbpm_last_error(void) { return last_error_cstr(); }
+
+int decbpm_assemble_host(const decbpm_mesh_desc *desc, decbpm_mesh_info_t *info, double *m, double *v, double *chib,
+                         int64_t *K_rowptr, int32_t *K_col, double *K_val, int32_t *perm) {
+    Assembly A;
+    TRY(assemble(desc, A));
+    Sell S;
+    build_sell(A, S);
+    if (info) {
+        info->n_vertices = A.n0;
+        info->n_edges = A.n_edges;
+        info->n_cells = A.nc;
+        info->nnz_offdiag = int64_t(A.col.size());
+        info->max_degree = A.max_degree;
+        info->n_p = int32_t(A.p.size());
+        info->bandwidth = A.bandwidth;
+        info->rho = A.rho;
+        info->area = A.area;
+        info->mean_degree = double(A.col.size()) / double(A.n0);
+        info->sell_entries = int64_t(S.col.size());
+        info->device_bytes = 0;
+    }
+    const int64_t n0 = A.n0;
+    if (m) std::copy(A.m.begin(), A.m.end(), m);
+    if (v) std::copy(A.v.begin(), A.v.end(), v);
+    if (chib) std::copy(A.chib.begin(), A.chib.end(), chib);
+    if (perm) std::copy(A.perm.begin(), A.perm.end(), perm);
+    if (K_rowptr || K_col || K_val) {
+        int64_t k = 0;
+        for (int64_t p = 0; p < n0; ++p) {
+            if (K_rowptr) K_rowptr[p] = k;
+            bool diag_done = false;
+            for (int64_t e = A.rowptr[p]; e <= A.rowptr[p + 1]; ++e) {
+                const bool at_end = e == A.rowptr[p + 1];
+                if (!diag_done && (at_end || A.col[e] > p)) {
+                    if (K_col) K_col[k] = int32_t(p);
+                    if (K_val) K_val[k] = A.wsum[p];
+                    ++k;
+                    diag_done = true;
+                }
+                if (at_end) break;
+                if (K_col) K_col[k] = A.col[e];
+                if (K_val) K_val[k] = -A.w[e];
+                ++k;
+            }
+        }
+        if (K_rowptr) K_rowptr[n0] = k;
+    }
+    return DECBPM_OK;
+}
+
+int decbpm_bessel_coefficients(double a, double tol, int32_t max_terms, double *J_out, int32_t *n_out) {
+    if (!n_out || !(a >= 0) || !std::isfinite(a) || !(tol > 0)) return fail(DECBPM_ERR_INVALID_ARG, "bad arguments");
+    Cheb cb;
+    std::vector<double> p = {1.0};
+    // a = h * p1 * r with rho = 2r; use h = a, r = 1
+    TRY(cheb_coefficients(p, 2.0, a, tol, cb));
+    const int n = cb.M + 1;
+    *n_out = n;
+    if (!J_out || max_terms < n) return fail(DECBPM_ERR_INVALID_ARG, "need %d terms", n);
+    std::vector<double> J(n);
+    bessel_sequence(a, n - 1, J.data());
+    std::copy(J.begin(), J.end(), J_out);
+    return DECBPM_OK;
+}
+
+int decbpm_mesh_create(const decbpm_mesh_desc *desc, decbpm_mesh_t *out) {
+    if (!out) return fail(DECBPM_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    auto M = std::make_unique<decbpm_mesh_s>();
+    TRY(assemble(desc, M->A));
+    build_sell(M->A, M->S);
+    CK(cudaGetDevice(&M->device));
+    int rc = mesh_upload(M.get());
+    if (rc != DECBPM_OK) {
+        M->mem.release();
+        return rc;
+    }
+    *out = M.release();
+    return DECBPM_OK;
+}
+
+int decbpm_mesh_destroy(decbpm_mesh_t mesh) {
+    if (!mesh) return DECBPM_OK;
+    for (auto &p : mesh->plans) delete p.second;
+    mesh->plans.clear();
+    mesh->mem.release();
+    delete mesh;
+    return DECBPM_OK;
+}
+
+int decbpm_mesh_info(decbpm_mesh_t m, decbpm_mesh_info_t *info) {
+    if (!m || !info) return fail(DECBPM_ERR_INVALID_ARG, "NULL argument");
+    info->n_vertices = m->A.n0;
+    info->n_edges = m->A.n_edges;
+    info->n_cells = m->A.nc;
+    info->nnz_offdiag = int64_t(m->A.col.size());
+    info->max_degree = m->A.max_degree;
+    info->n_p = int32_t(m->A.p.size());
+    info->bandwidth = m->A.bandwidth;
+    info->rho = m->A.rho;
+    info->area = m->A.area;
+    info->mean_degree = double(m->A.col.size()) / double(m->A.n0);
+    info->sell_entries = int64_t(m->S.col.size());
+    info->device_bytes = int64_t(m->mem.bytes);
+    return DECBPM_OK;
+}
+
+static int single_plan(decbpm_mesh_t mesh, int64_t n_fields, int32_t precision, decbpm_plan_t *P) {
+    if (n_fields < 1 || n_fields > kMaxFields) return fail(DECBPM_ERR_UNSUPPORTED, "n_fields must be in 1..%d", kMaxFields);
+    auto key = std::make_pair(int(n_fields), int(precision));
+    auto it = mesh->plans.find(key);
+    if (it != mesh->plans.end()) { *P = it->second; return DECBPM_OK; }
+    int32_t nf = int32_t(n_fields);
+    TRY(plan_create_impl(&mesh, 1, &nf, precision, P));
+    mesh->plans[key] = *P;
+    return DECBPM_OK;
+}
+
+int decbpm_propagate(decbpm_mesh_t mesh, const decbpm_params *params, void *psi_dev, int64_t n_fields, void *stream,
+                     decbpm_diag *diag_out) {
+    clear_error();
+    if (!mesh || !psi_dev) return fail(DECBPM_ERR_INVALID_ARG, "mesh and psi_dev are required");
+    TRY(check_params(params));
+    if (params->variant == DECBPM_VARIANT_PLAIN) {
+        if (n_fields != 1) return fail(DECBPM_ERR_UNSUPPORTED, "the plain variant runs one field");
+        if (params->kerr_mode != DECBPM_KERR_LUMPED) return fail(DECBPM_ERR_UNSUPPORTED, "the plain variant runs lumped Kerr");
+        return propagate_plain(mesh, params, psi_dev, (cudaStream_t)stream, diag_out);
+    }
+    decbpm_plan_t P;
+    TRY(single_plan(mesh, n_fields, params->precision, &P));
+    void *ptrs[1] = {psi_dev};
+    return plan_propagate_dispatch(P, params, ptrs, stream, diag_out);
+}
+
+int decbpm_propagate_host(decbpm_mesh_t mesh, const decbpm_params *params, void *psi_host, int64_t n_fields, void *stream,
+                          decbpm_diag *diag_out) {
+    clear_error();
+    if (!mesh || !psi_host) return fail(DECBPM_ERR_INVALID_ARG, "mesh and psi_host are required");
+    TRY(check_params(params));
+    decbpm_plan_t P;
+    TRY(single_plan(mesh, n_fields, params->precision, &P));
+    const size_t bytes = size_t(mesh->A.n0) * n_fields * csize(params->precision);
+    if (!P->user[0]) {
+        char *t;
+        TRY(P->mem.alloc(&t, bytes));
+        P->user[0] = t;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    CK(cudaMemcpyAsync(P->user[0], psi_host, bytes, cudaMemcpyHostToDevice, s));
+    int rc = params->variant == DECBPM_VARIANT_PLAIN ? propagate_plain(mesh, params, P->user[0], s, diag_out)
+                                                     : plan_propagate_dispatch(P, params, P->user.data(), stream, diag_out);
+    if (rc != DECBPM_OK) return rc;
+    CK(cudaMemcpyAsync(psi_host, P->user[0], bytes, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    return DECBPM_OK;
+}
+
+int decbpm_diagnostics(decbpm_mesh_t mesh, const void *psi_dev, int64_t n_fields, int32_t precision, void *stream,
+                       decbpm_diag *diag_out) {
+    clear_error();
+    if (!mesh || !psi_dev || !diag_out) return fail(DECBPM_ERR_INVALID_ARG, "NULL argument");
+    if (precision != DECBPM_C64 && precision != DECBPM_C128) return fail(DECBPM_ERR_INVALID_ARG, "bad precision");
+    decbpm_plan_t P;
+    TRY(single_plan(mesh, n_fields, precision, &P));
+    cudaStream_t s = (cudaStream_t)stream;
+    decbpm_params prm{};
+    prm.dz = 1.0;
+    prm.n_steps = 0;
+    prm.precision = precision;
+    TRY(ensure_diag_host(P, 1));
+    const int64_t n0 = mesh->A.n0;
+    const int blocks = int(std::min<int64_t>(4 * P->num_sms, (n0 * P->bpad + 255) / 256));
+    if (precision == DECBPM_C64) {
+        permute_in_kernel<float2><<<blocks, 256, 0, s>>>((const float2 *)psi_dev, (float2 *)P->psi[0], mesh->perm,
+                                                         int32_t(n0), int32_t(n_fields), P->bpad);
+        TRY(launch_diag<float>(P, s, DECBPM_KERR_LUMPED, 0));
+    } else {
+        permute_in_kernel<double2><<<blocks, 256, 0, s>>>((const double2 *)psi_dev, (double2 *)P->psi[0], mesh->perm,
+                                                          int32_t(n0), int32_t(n_fields), P->bpad);
+        TRY(launch_diag<double>(P, s, DECBPM_KERR_LUMPED, 0));
+    }
+    CK(cudaStreamSynchronize(s));
+    return finish_diag(P, &prm, 1, diag_out);
+}
+
+int decbpm_plan_create(const decbpm_mesh_t *meshes, int32_t n_meshes, const int32_t *fields_per_mesh, int32_t precision,
+                       decbpm_plan_t *out) {
+    clear_error();
+    return plan_create_impl(meshes, n_meshes, fields_per_mesh, precision, out);
+}
+
+int decbpm_plan_destroy(decbpm_plan_t plan) {
+    delete plan;
+    return DECBPM_OK;
+}
+
+int decbpm_plan_propagate(decbpm_plan_t plan, const decbpm_params *params, void *const *psi_dev, void *stream,
+                          decbpm_diag *diag_out) {
+    clear_error();
+    return plan_propagate_dispatch(plan, params, psi_dev, stream, diag_out);
+}
+
+int decbpm_plan_propagate_host(decbpm_plan_t P, const decbpm_params *params, void *const *psi_host, void *stream,
+                               decbpm_diag *diag_out) {
+    clear_error();
+    TRY(check_params(params));
+    if (!P || !psi_host) return fail(DECBPM_ERR_INVALID_ARG, "NULL argument");
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t cs = csize(P->precision);
+    for (size_t i = 0; i < P->meshes.size(); ++i) {
+        if (!psi_host[i]) return fail(DECBPM_ERR_INVALID_ARG, "psi_host[%zu] is NULL", i);
+        const size_t bytes = size_t(P->meshes[i]->A.n0) * P->B[i] * cs;
+        if (!P->user[i]) {
+            char *t;
+            TRY(P->mem.alloc(&t, bytes));
+            P->user[i] = t;
+        }
+        CK(cudaMemcpyAsync(P->user[i], psi_host[i], bytes, cudaMemcpyHostToDevice, s));
+    }
+    TRY(plan_propagate_dispatch(P, params, P->user.data(), stream, diag_out));
+    for (size_t i = 0; i < P->meshes.size(); ++i) {
+        const size_t bytes = size_t(P->meshes[i]->A.n0) * P->B[i] * cs;
+        CK(cudaMemcpyAsync(psi_host[i], P->user[i], bytes, cudaMemcpyDeviceToHost, s));
+    }
+    CK(cudaStreamSynchronize(s));
+    return DECBPM_OK;
+}
+
+int32_t decbpm_plan_degree(decbpm_plan_t P, int32_t i, double dz, int32_t precision, double cheb_tol) {
+    if (!P || i < 0 || i >= int32_t(P->meshes.size()) || !(dz > 0)) return 0;
+    Cheb cb;
+    const double tol = cheb_tol > 0 ? cheb_tol : (precision == DECBPM_C64 ? 1e-9 : 1e-16);
+    if (cheb_coefficients(P->meshes[i]->A.p, P->meshes[i]->A.rho, dz, tol, cb) != DECBPM_OK) return 0;
+    return cb.M;
+}
+
+int decbpm_plan_get_config(decbpm_plan_t P, decbpm_plan_config *cfg) {
+    if (!P || !cfg) return fail(DECBPM_ERR_INVALID_ARG, "NULL argument");
+    cfg->grid = P->grid;
+    cfg->block = P->block;
+    cfg->fields_padded = P->bpad;
+    cfg->graphs = (P->graphs_ok && !P->graphs.empty()) ? 1 : 0;
+    cfg->stages = P->S;
+    cfg->n_meshes = int32_t(P->meshes.size());
+    return DECBPM_OK;
+}
+
+int decbpm_plan_last_march_ms(decbpm_plan_t P, double *ms) {
+    if (!P || !ms) return fail(DECBPM_ERR_INVALID_ARG, "NULL argument");
+    float t = 0;
+    CK(cudaEventElapsedTime(&t, P->ev0, P->ev1));
+    *ms = double(t);
+    return DECBPM_OK;
+}
+
+int decbpm_selftest_barrier(int32_t missing_arrivals, int64_t timeout_ns, void *stream) {
+    clear_error();
+    if (missing_arrivals < 0 || timeout_ns <= 0 || timeout_ns > 10000000000LL)
+        return fail(DECBPM_ERR_INVALID_ARG, "missing_arrivals >= 0 and 0 < timeout_ns <= 1e10 required");
+    cudaStream_t s = (cudaStream_t)stream;
+    unsigned long long *bar = nullptr;
+    int *status = nullptr;
+    CK(cudaMalloc(&bar, sizeof(unsigned long long)));
+    CK(cudaMalloc(&status, sizeof(int)));
+    CK(cudaMemsetAsync(bar, 0, sizeof(unsigned long long), s));
+    CK(cudaMemsetAsync(status, 0, sizeof(int), s));
+    int dev = 0, sms = 0;
+    CK(cudaGetDevice(&dev));
+    CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(std::min(sms, 8));
+    cfg.blockDim = dim3(64);
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    long long tns = timeout_ns;
+    unsigned extra = unsigned(missing_arrivals);
+    cudaError_t e = cudaLaunchKernelEx(&cfg, barrier_selftest_kernel, bar, status, tns, extra);
+    int st = 0;
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e == cudaSuccess) e = cudaMemcpy(&st, status, sizeof(int), cudaMemcpyDeviceToHost);
+    cudaFree(bar);
+    cudaFree(status);
+    if (e != cudaSuccess) return fail(DECBPM_ERR_CUDA, "self test: %s", cudaGetErrorString(e));
+    if (st == DECBPM_ERR_TIMEOUT) return fail(DECBPM_ERR_TIMEOUT, "barrier wait ran out (as requested)");
+    return st;
+}
+
+int decbpm_propagate_batch(const decbpm_mesh_t *meshes, int32_t n_meshes, const int32_t *fields_per_mesh,
+                           const decbpm_params *params, void *const *psi_dev, void *stream, decbpm_diag *diag_out) {
+    clear_error();
+    TRY(check_params(params));
+    decbpm_plan_t P = nullptr;
+    TRY(plan_create_impl(meshes, n_meshes, fields_per_mesh, params->precision, &P));
+    int rc = plan_propagate_dispatch(P, params, psi_dev, stream, diag_out);
+    delete P;
+    return rc;
+}
+
+}  // extern "C"

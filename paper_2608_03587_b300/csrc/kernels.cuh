@@ -1,0 +1,529 @@
+// Device kernels of libdecbpm (sm_103a).
+//
+// The hot path is one persistent cooperative kernel that advances every
+// (mesh, field) of a plan through a block of Strang steps.  Per step the
+// linear propagator E_h = exp(i h sum p_n (-A)^n) is the Chebyshev sum
+// sum_k a_k T_k(X), X = (A - c)/r, evaluated by Clenshaw's recurrence
+//     b_k = a_k psi + 2 X b_{k+1} - b_{k+2},   S = a_0 psi + X b_1 - b_2,
+// one grid-wide stage per term.  Each stage is a complex SpMV over the
+// SELL-32 operator fused with the *0^{-1} scaling (folded into X), the
+// recurrence update and, in the last stage, the exact diagonal flow D_h
+// (potential + Kerr phase + absorber).  The bulk data stays in HBM/L2; the
+// kernel is bandwidth bound (no tensor-core work exists in a sparse SpMV).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace decbpm {
+
+constexpr int kMaxMeshes = 64;
+constexpr int kMaxFields = 64;
+constexpr long long kBarrierTimeoutNs = 4000000000LL;   // default limit of one barrier wait: 4 s
+
+// ------------------------------------------------------------ complex types
+template <typename R> struct CT;
+template <> struct CT<float>  { using c2 = float2; };
+template <> struct CT<double> { using c2 = double2; };
+
+template <typename C> __device__ __forceinline__ C cmk(decltype(C::x) re, decltype(C::x) im) { C r; r.x = re; r.y = im; return r; }
+template <typename C> __device__ __forceinline__ C cadd(C a, C b) { return cmk<C>(a.x + b.x, a.y + b.y); }
+template <typename C> __device__ __forceinline__ C csub(C a, C b) { return cmk<C>(a.x - b.x, a.y - b.y); }
+template <typename C> __device__ __forceinline__ C cmul(C a, C b) { return cmk<C>(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); }
+template <typename C, typename R> __device__ __forceinline__ C cscale(C a, R s) { return cmk<C>(a.x * s, a.y * s); }
+template <typename C, typename R> __device__ __forceinline__ C cfma(R s, C a, C acc) { return cmk<C>(fma(s, a.x, acc.x), fma(s, a.y, acc.y)); }
+
+__device__ __forceinline__ void sincos_r(float x, float *s, float *c) { sincosf(x, s, c); }
+__device__ __forceinline__ void sincos_r(double x, double *s, double *c) { sincos(x, s, c); }
+__device__ __forceinline__ float exp_r(float x) { return expf(x); }
+__device__ __forceinline__ double exp_r(double x) { return exp(x); }
+__device__ __forceinline__ float expm1_r(float x) { return expm1f(x); }
+__device__ __forceinline__ double expm1_r(double x) { return expm1(x); }
+
+// FPT consecutive complex values of one vertex row, moved with 16-byte (or
+// 8-byte for a single complex64) vector accesses.
+template <typename R, int FPT> struct Pack {
+    using C = typename CT<R>::c2;
+    C v[FPT];
+};
+
+template <typename R, int FPT> union PackRaw {
+    static constexpr int kBytes = int(sizeof(typename CT<R>::c2)) * FPT;
+    Pack<R, FPT> p;
+    uint4 u[kBytes >= 16 ? kBytes / 16 : 1];
+    float2 f2;
+};
+
+template <typename R, int FPT>
+__device__ __forceinline__ Pack<R, FPT> ld_pack(const typename CT<R>::c2 *p) {
+    PackRaw<R, FPT> t;
+    if constexpr (PackRaw<R, FPT>::kBytes == 8) {
+        t.f2 = *reinterpret_cast<const float2 *>(p);
+    } else {
+        const uint4 *q = reinterpret_cast<const uint4 *>(p);
+#pragma unroll
+        for (int i = 0; i < PackRaw<R, FPT>::kBytes / 16; ++i) t.u[i] = q[i];
+    }
+    return t.p;
+}
+
+template <typename R, int FPT>
+__device__ __forceinline__ void st_pack(typename CT<R>::c2 *p, const Pack<R, FPT> &v) {
+    PackRaw<R, FPT> t;
+    t.p = v;
+    if constexpr (PackRaw<R, FPT>::kBytes == 8) {
+        *reinterpret_cast<float2 *>(p) = t.f2;
+    } else {
+        uint4 *q = reinterpret_cast<uint4 *>(p);
+#pragma unroll
+        for (int i = 0; i < PackRaw<R, FPT>::kBytes / 16; ++i) q[i] = t.u[i];
+    }
+}
+
+// ------------------------------------------------------------ plan views
+// Per-stage Clenshaw coefficients of one mesh at local term index k:
+//   out = alpha * psi + beta * (X g) - (has_h ? h : 0),
+//   g = psi (first stage) or b_{k+1};  h = b_{k+2};  the last stage (k = 0)
+//   applies the diagonal flow and overwrites psi.
+enum : int { kGisPsi = 1, kHasH = 2, kFinal = 4 };
+template <typename R> struct StageCoef {
+    typename CT<R>::c2 alpha, beta;
+    int flags;
+    int pad;
+};
+
+template <typename R> struct MeshView {
+    int32_t n0, n_slices;
+    int32_t M;               // Chebyshev degree (>= 2)
+    int32_t item_begin;      // first plan-global work item of this mesh
+    const int32_t *slice_ptr, *slice_w, *col;
+    const R *xval, *xdiag;   // X = (A - c)/r: off-diagonal (SELL) and diagonal
+    const R *v, *chib, *sigma;
+    const R *coff, *cdiag;   // element-averaged Kerr operator (SELL) and diagonal
+    typename CT<R>::c2 *psi, *b[3];
+    const StageCoef<R> *coef;   // [M]: index k
+};
+
+template <typename R> struct MarchParams {
+    const MeshView<R> *meshes;   // sorted by M descending
+    const int32_t *active_items; // [S]: items of meshes with M > S-1-s
+    int32_t n_meshes, S, total_items;
+    int32_t n_steps;
+    int32_t pre_half, post_half; // D_{h/2} before the first / after the last step of this launch
+    int32_t kerr_mode;
+    int32_t bpad_log2;           // log2 of the padded fields per vertex
+    R h;
+    unsigned long long *barrier; // zeroed before every launch
+    int *status;                 // 0, or a DECBPM_ERR_* code written by the device
+    long long timeout_ns;        // limit of one barrier wait
+};
+
+// ------------------------------------------------------------ grid barrier
+__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long *p) {
+    unsigned long long v;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ long long global_ns() {
+    long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// All CTAs of a cooperative launch arrive, then wait until the counter
+// reaches the next multiple of gridDim.x.  The wait is bounded: after
+// timeout_ns, or once another CTA has reported an error, it records
+// DECBPM_ERR_TIMEOUT (-4) in *status and returns false; callers then exit.
+// `extra` raises the arrival count waited for (only the self test sets it).
+__device__ __forceinline__ bool grid_barrier(unsigned long long *bar, unsigned long long &target, int *status,
+                                             long long timeout_ns, unsigned extra = 0) {
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        target += gridDim.x + extra;
+        __threadfence();
+        atomicAdd(bar, 1ull);
+        int ok = 1;
+        const long long t0 = global_ns();
+        unsigned spins = 0;
+        while (ld_acquire_u64(bar) < target) {
+            if ((++spins & 63u) == 0) {
+                if (*(volatile int *)status != 0) { ok = 0; break; }
+                if (global_ns() - t0 > timeout_ns) {
+                    atomicCAS(status, 0, -4);
+                    ok = 0;
+                    break;
+                }
+            }
+            __nanosleep(32);
+        }
+        __threadfence();
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+// ------------------------------------------------------------ diagonal flow
+// Exact flow over h of dpsi/dz = i (v + chib |psi|^2) psi - sigma psi:
+// |psi|^2 decays as e^{-2 sigma z}, phase = v h + chib |psi0|^2 phi,
+// phi = (1 - e^{-2 sigma h}) / (2 sigma)  (-> h for sigma = 0).
+template <typename R>
+__device__ __forceinline__ void diag_factors(R sigma, R h, R &damp, R &phi) {
+    if (sigma > R(0)) {
+        damp = exp_r(-sigma * h);
+        phi = -expm1_r(R(-2) * sigma * h) / (R(2) * sigma);
+    } else {
+        damp = R(1);
+        phi = h;
+    }
+}
+
+template <typename C, typename R>
+__device__ __forceinline__ C diag_apply(C s, R v, R chib, R h, R damp, R phi) {
+    const R I = s.x * s.x + s.y * s.y;
+    const R theta = v * h + chib * I * phi;
+    R sn, cs;
+    sincos_r(theta, &sn, &cs);
+    return cmk<C>(damp * (s.x * cs - s.y * sn), damp * (s.x * sn + s.y * cs));
+}
+
+// Which mesh owns plan-global item `it` (meshes are few: linear scan).
+__device__ __forceinline__ int mesh_of_item(const int32_t *s_begin, int n_meshes, int it) {
+    int i = 0;
+    while (i + 1 < n_meshes && it >= s_begin[i + 1]) ++i;
+    return i;
+}
+
+// One Clenshaw stage for one warp item (RPW rows x all fields of one mesh).
+template <typename R, int FPT>
+__device__ __forceinline__ void clenshaw_item(const MeshView<R> &m, int local_item, int k, R h_post,
+                                              int kerr_mode, int bpad_log2) {
+    using C = typename CT<R>::c2;
+    const int lane = threadIdx.x & 31;
+    const int tpr_log2 = bpad_log2 - (FPT == 2 ? 1 : 0);      // threads per row
+    const int rpw = 32 >> tpr_log2;                             // rows per warp item
+    const int row = local_item * rpw + (lane >> tpr_log2);
+    if (row >= m.n0) return;
+    const int fo = (lane & ((1 << tpr_log2) - 1)) * FPT;        // first field of this thread
+    const int bpad = 1 << bpad_log2;
+    const StageCoef<R> sc = m.coef[k];
+    const C *g = (sc.flags & kGisPsi) ? m.psi : m.b[(k + 1) % 3];
+
+    const int slice = row >> 5;
+    const int base = __ldg(m.slice_ptr + slice) + (row & 31);
+    const int width = __ldg(m.slice_w + slice);
+    Pack<R, FPT> acc = ld_pack<R, FPT>(g + (size_t)row * bpad + fo);
+    const R xd = __ldg(m.xdiag + row);
+#pragma unroll
+    for (int f = 0; f < FPT; ++f) acc.v[f] = cscale(acc.v[f], xd);
+    for (int j = 0; j < width; ++j) {
+        const int q = __ldg(m.col + base + 32 * j);
+        const R x = __ldg(m.xval + base + 32 * j);
+        const Pack<R, FPT> gq = ld_pack<R, FPT>(g + (size_t)q * bpad + fo);
+#pragma unroll
+        for (int f = 0; f < FPT; ++f) acc.v[f] = cfma(x, gq.v[f], acc.v[f]);
+    }
+    const Pack<R, FPT> ps = ld_pack<R, FPT>(m.psi + (size_t)row * bpad + fo);
+    Pack<R, FPT> out;
+#pragma unroll
+    for (int f = 0; f < FPT; ++f) out.v[f] = cadd(cmul(sc.alpha, ps.v[f]), cmul(sc.beta, acc.v[f]));
+    if (sc.flags & kHasH) {
+        const Pack<R, FPT> hh = ld_pack<R, FPT>(m.b[(k + 2) % 3] + (size_t)row * bpad + fo);
+#pragma unroll
+        for (int f = 0; f < FPT; ++f) out.v[f] = csub(out.v[f], hh.v[f]);
+    }
+    if (sc.flags & kFinal) {
+        if (kerr_mode == 0) {
+            R damp, phi;
+            const R sig = __ldg(m.sigma + row);
+            diag_factors(sig, h_post, damp, phi);
+            const R vv = __ldg(m.v + row), cb = __ldg(m.chib + row);
+#pragma unroll
+            for (int f = 0; f < FPT; ++f) out.v[f] = diag_apply(out.v[f], vv, cb, h_post, damp, phi);
+            st_pack<R, FPT>(m.psi + (size_t)row * bpad + fo, out);
+        } else {
+            // element-averaged Kerr needs the neighbours' |S|^2: park S in b[0]
+            st_pack<R, FPT>(m.b[0] + (size_t)row * bpad + fo, out);
+        }
+    } else {
+        st_pack<R, FPT>(m.b[k % 3] + (size_t)row * bpad + fo, out);
+    }
+}
+
+// Element-averaged Kerr flow (Eq. 14 with the absorber):
+//   theta_p = v_p h + sum_q c_pq |src_q|^2 phi(sigma_q, h),  dst_p = src_p e^{-sigma_p h} e^{i theta_p}
+template <typename R, int FPT>
+__device__ __forceinline__ void element_kerr_item(const MeshView<R> &m, int local_item, R hh, int bpad_log2,
+                                                  const typename CT<R>::c2 *src, typename CT<R>::c2 *dst) {
+    using C = typename CT<R>::c2;
+    const int lane = threadIdx.x & 31;
+    const int tpr_log2 = bpad_log2 - (FPT == 2 ? 1 : 0);
+    const int rpw = 32 >> tpr_log2;
+    const int row = local_item * rpw + (lane >> tpr_log2);
+    if (row >= m.n0) return;
+    const int fo = (lane & ((1 << tpr_log2) - 1)) * FPT;
+    const int bpad = 1 << bpad_log2;
+    const int slice = row >> 5;
+    const int base = __ldg(m.slice_ptr + slice) + (row & 31);
+    const int width = __ldg(m.slice_w + slice);
+    const Pack<R, FPT> s = ld_pack<R, FPT>(src + (size_t)row * bpad + fo);
+    R damp, phi;
+    diag_factors(__ldg(m.sigma + row), hh, damp, phi);
+    R rate[FPT];
+    const R cd = __ldg(m.cdiag + row) * phi;
+#pragma unroll
+    for (int f = 0; f < FPT; ++f) rate[f] = cd * (s.v[f].x * s.v[f].x + s.v[f].y * s.v[f].y);
+    for (int j = 0; j < width; ++j) {
+        const int q = __ldg(m.col + base + 32 * j);
+        const R cq = __ldg(m.coff + base + 32 * j);
+        R dq, pq;
+        diag_factors(__ldg(m.sigma + q), hh, dq, pq);
+        const Pack<R, FPT> sq = ld_pack<R, FPT>(src + (size_t)q * bpad + fo);
+#pragma unroll
+        for (int f = 0; f < FPT; ++f) rate[f] += cq * pq * (sq.v[f].x * sq.v[f].x + sq.v[f].y * sq.v[f].y);
+    }
+    const R vh = __ldg(m.v + row) * hh;
+    Pack<R, FPT> out;
+#pragma unroll
+    for (int f = 0; f < FPT; ++f) {
+        R sn, cs;
+        sincos_r(vh + rate[f], &sn, &cs);
+        out.v[f] = cmk<C>(damp * (s.v[f].x * cs - s.v[f].y * sn), damp * (s.v[f].x * sn + s.v[f].y * cs));
+    }
+    st_pack<R, FPT>(dst + (size_t)row * bpad + fo, out);
+}
+
+template <typename R, int FPT>
+__device__ __forceinline__ void lumped_diag_item(const MeshView<R> &m, int local_item, R hh, int bpad_log2) {
+    const int lane = threadIdx.x & 31;
+    const int tpr_log2 = bpad_log2 - (FPT == 2 ? 1 : 0);
+    const int rpw = 32 >> tpr_log2;
+    const int row = local_item * rpw + (lane >> tpr_log2);
+    if (row >= m.n0) return;
+    const int fo = (lane & ((1 << tpr_log2) - 1)) * FPT;
+    const int bpad = 1 << bpad_log2;
+    Pack<R, FPT> s = ld_pack<R, FPT>(m.psi + (size_t)row * bpad + fo);
+    R damp, phi;
+    diag_factors(__ldg(m.sigma + row), hh, damp, phi);
+    const R vv = __ldg(m.v + row), cb = __ldg(m.chib + row);
+#pragma unroll
+    for (int f = 0; f < FPT; ++f) s.v[f] = diag_apply(s.v[f], vv, cb, hh, damp, phi);
+    st_pack<R, FPT>(m.psi + (size_t)row * bpad + fo, s);
+}
+
+template <typename R, int FPT>
+__device__ __forceinline__ void copy_item(const MeshView<R> &m, int local_item, int bpad_log2,
+                                          const typename CT<R>::c2 *src, typename CT<R>::c2 *dst) {
+    const int lane = threadIdx.x & 31;
+    const int tpr_log2 = bpad_log2 - (FPT == 2 ? 1 : 0);
+    const int rpw = 32 >> tpr_log2;
+    const int row = local_item * rpw + (lane >> tpr_log2);
+    if (row >= m.n0) return;
+    const int fo = (lane & ((1 << tpr_log2) - 1)) * FPT;
+    const size_t off = (size_t)row * (1 << bpad_log2) + fo;
+    st_pack<R, FPT>(dst + off, ld_pack<R, FPT>(src + off));
+}
+
+// Run `body(view, local_item)` over this CTA's contiguous share of the first
+// `n_items` plan-global items, one warp per item.
+template <typename R, typename F>
+__device__ __forceinline__ void for_my_items(const MarchParams<R> &P, const int32_t *s_begin, int n_items, F body) {
+    const int warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    const int lo = int((long long)n_items * blockIdx.x / gridDim.x);
+    const int hi = int((long long)n_items * (blockIdx.x + 1) / gridDim.x);
+    int mi = -1, mend = 0;
+    for (int it = lo + warp; it < hi; it += nwarps) {
+        if (mi < 0 || it >= mend) {
+            mi = mesh_of_item(s_begin, P.n_meshes, it);
+            mend = (mi + 1 < P.n_meshes) ? s_begin[mi + 1] : P.total_items;
+        }
+        body(P.meshes[mi], it - s_begin[mi]);
+    }
+}
+
+template <typename R, int FPT>
+__global__ void __launch_bounds__(512) march_kernel(MarchParams<R> P) {
+    __shared__ int32_t s_begin[kMaxMeshes + 1];
+    for (int i = threadIdx.x; i < P.n_meshes; i += blockDim.x) s_begin[i] = P.meshes[i].item_begin;
+    __syncthreads();
+    unsigned long long target = 0;
+    const R h = P.h, hh = P.h * R(0.5);
+    for (int step = 0; step < P.n_steps; ++step) {
+        if (step == 0 && P.pre_half) {
+            if (P.kerr_mode == 0) {
+                for_my_items(P, s_begin, P.total_items, [&](const MeshView<R> &m, int li) {
+                    lumped_diag_item<R, FPT>(m, li, hh, P.bpad_log2);
+                });
+                if (!grid_barrier(P.barrier, target, P.status, P.timeout_ns)) return;
+            } else {
+                for_my_items(P, s_begin, P.total_items, [&](const MeshView<R> &m, int li) {
+                    element_kerr_item<R, FPT>(m, li, hh, P.bpad_log2, m.psi, m.b[0]);
+                });
+                if (!grid_barrier(P.barrier, target, P.status, P.timeout_ns)) return;
+                for_my_items(P, s_begin, P.total_items, [&](const MeshView<R> &m, int li) {
+                    copy_item<R, FPT>(m, li, P.bpad_log2, m.b[0], m.psi);
+                });
+                if (!grid_barrier(P.barrier, target, P.status, P.timeout_ns)) return;
+            }
+        }
+        const R h_post = (step == P.n_steps - 1 && P.post_half) ? hh : h;
+        for (int s = 0; s < P.S; ++s) {
+            const int k = P.S - 1 - s;
+            for_my_items(P, s_begin, P.active_items[s], [&](const MeshView<R> &m, int li) {
+                clenshaw_item<R, FPT>(m, li, k, h_post, P.kerr_mode, P.bpad_log2);
+            });
+            if (!grid_barrier(P.barrier, target, P.status, P.timeout_ns)) return;
+        }
+        if (P.kerr_mode != 0) {
+            for_my_items(P, s_begin, P.total_items, [&](const MeshView<R> &m, int li) {
+                element_kerr_item<R, FPT>(m, li, h_post, P.bpad_log2, m.b[0], m.psi);
+            });
+            if (!grid_barrier(P.barrier, target, P.status, P.timeout_ns)) return;
+        }
+    }
+}
+
+// Self test of the bounded barrier: every CTA waits for `extra` arrivals
+// that never come, gives up after timeout_ns and exits.
+__global__ void barrier_selftest_kernel(unsigned long long *bar, int *status, long long timeout_ns, unsigned extra) {
+    unsigned long long target = 0;
+    grid_barrier(bar, target, status, timeout_ns, extra);
+}
+
+// ------------------------------------------------------------ permutation
+// internal[new][f] = user[perm[new]][f] for f < B, 0 for the padding fields.
+template <typename C>
+__global__ void permute_in_kernel(const C *__restrict__ user, C *__restrict__ internal, const int32_t *__restrict__ perm,
+                                  int32_t n0, int32_t B, int32_t bpad) {
+    const long long n = (long long)n0 * bpad;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const int r = int(i / bpad), f = int(i % bpad);
+        C val;
+        if (f < B) val = user[(size_t)perm[r] * B + f];
+        else { val.x = 0; val.y = 0; }
+        internal[i] = val;
+    }
+}
+
+template <typename C>
+__global__ void permute_out_kernel(const C *__restrict__ internal, C *__restrict__ user, const int32_t *__restrict__ perm,
+                                   int32_t n0, int32_t B, int32_t bpad) {
+    const long long n = (long long)n0 * B;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const int r = int(i / B), f = int(i % B);
+        user[(size_t)perm[r] * B + f] = internal[(size_t)r * bpad + f];
+    }
+}
+
+// ------------------------------------------------------------ diagnostics
+// Per field, FP64: [0] sum m|psi|^2, [1] psi^H K psi, [2] sum |K psi|^2 / m,
+// [3] sum m v |psi|^2, [4] sum m * kerr-energy density, [5] max |psi|^2.
+// kerr energy density: chib |psi|^4 (lumped) or |psi_p|^2 (C|psi|^2)_p (element).
+constexpr int kDiagQ = 6;
+constexpr int kDiagThreads = 256;
+
+template <typename R>
+__global__ void __launch_bounds__(kDiagThreads) diag_partial_kernel(
+        const typename CT<R>::c2 *__restrict__ psi, int32_t n0, int32_t bpad_log2, int32_t B,
+        const int32_t *__restrict__ slice_ptr, const int32_t *__restrict__ slice_w, const int32_t *__restrict__ col,
+        const double *__restrict__ w64, const double *__restrict__ m64, const double *__restrict__ v64,
+        const double *__restrict__ chib64, const double *__restrict__ coff64, const double *__restrict__ cdiag64,
+        int32_t kerr_mode, double *__restrict__ partial /* [gridDim.x][bpad][kDiagQ] */) {
+    using C = typename CT<R>::c2;
+    __shared__ double red[kDiagThreads][kDiagQ];
+    const int bpad = 1 << bpad_log2;
+    const int f = threadIdx.x & (bpad - 1);
+    const int slot = threadIdx.x >> bpad_log2, nslot = kDiagThreads >> bpad_log2;
+    const int lo = int((long long)n0 * blockIdx.x / gridDim.x), hi = int((long long)n0 * (blockIdx.x + 1) / gridDim.x);
+    double acc[kDiagQ] = {0, 0, 0, 0, 0, 0};
+    if (nslot > 0 && f < B) {
+        for (int p = lo + slot; p < hi; p += nslot) {
+            const C a = psi[(size_t)p * bpad + f];
+            const double ar = a.x, ai = a.y, I = ar * ar + ai * ai;
+            const int s = p >> 5;
+            const int base = slice_ptr[s] + (p & 31);
+            double kr = 0, ki = 0, ke = cdiag64[p] * I;   // (K psi)_p and element-kerr rate
+            for (int j = 0; j < slice_w[s]; ++j) {
+                const int q = col[base + 32 * j];
+                const double w = w64[base + 32 * j];
+                const C b = psi[(size_t)q * bpad + f];
+                kr += w * (ar - double(b.x));
+                ki += w * (ai - double(b.y));
+                ke += coff64[base + 32 * j] * (double(b.x) * b.x + double(b.y) * b.y);
+            }
+            const double mp = m64[p];
+            acc[0] += mp * I;
+            acc[1] += ar * kr + ai * ki;
+            acc[2] += (kr * kr + ki * ki) / mp;
+            acc[3] += mp * v64[p] * I;
+            acc[4] += kerr_mode == 0 ? mp * chib64[p] * I * I : mp * I * ke;
+            acc[5] = fmax(acc[5], I);
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < kDiagQ; ++q) red[threadIdx.x][q] = acc[q];
+    __syncthreads();
+    if (threadIdx.x < bpad && nslot > 0) {
+        double s[kDiagQ] = {0, 0, 0, 0, 0, 0};
+        for (int sl = 0; sl < nslot; ++sl) {
+            const int t = sl * bpad + threadIdx.x;
+            for (int q = 0; q < 5; ++q) s[q] += red[t][q];
+            s[5] = fmax(s[5], red[t][5]);
+        }
+        for (int q = 0; q < kDiagQ; ++q) partial[((size_t)blockIdx.x * bpad + threadIdx.x) * kDiagQ + q] = s[q];
+    }
+}
+
+// Fixed-order reduction over blocks: out[f][q].
+__global__ void diag_final_kernel(const double *__restrict__ partial, int32_t nblocks, int32_t bpad,
+                                  double *__restrict__ out) {
+    const int f = threadIdx.x;
+    if (f >= bpad) return;
+    double s[kDiagQ] = {0, 0, 0, 0, 0, 0};
+    for (int b = 0; b < nblocks; ++b) {
+        const double *p = partial + ((size_t)b * bpad + f) * kDiagQ;
+        for (int q = 0; q < 5; ++q) s[q] += p[q];
+        s[5] = fmax(s[5], p[5]);
+    }
+    for (int q = 0; q < kDiagQ; ++q) out[f * kDiagQ + q] = s[q];
+}
+
+// ------------------------------------------------------------ plain path
+// Unfused single-field FP64 reference path: a CSR SpMV launch and an update
+// launch per Clenshaw term, a separate launch for each diagonal flow.
+__global__ void plain_spmv_kernel(const int32_t *__restrict__ rowptr, const int32_t *__restrict__ colidx,
+                                  const double *__restrict__ val, const double2 *__restrict__ x,
+                                  double2 *__restrict__ y, int32_t n0) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n0) return;
+    double sr = 0, si = 0;
+    for (int k = rowptr[r]; k < rowptr[r + 1]; ++k) {
+        const double2 xv = x[colidx[k]];
+        sr += val[k] * xv.x;
+        si += val[k] * xv.y;
+    }
+    y[r] = make_double2(sr, si);
+}
+
+__global__ void plain_update_kernel(const double2 *__restrict__ psi, const double2 *__restrict__ Xg,
+                                    const double2 *__restrict__ hprev, double2 *__restrict__ out,
+                                    double2 alpha, double2 beta, int32_t has_h, int32_t n0) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n0) return;
+    double2 o = cadd(cmul(alpha, psi[r]), cmul(beta, Xg[r]));
+    if (has_h) o = csub(o, hprev[r]);
+    out[r] = o;
+}
+
+__global__ void plain_diag_flow_kernel(double2 *__restrict__ psi, const double *__restrict__ v,
+                                       const double *__restrict__ chib, const double *__restrict__ sigma,
+                                       double h, int32_t n0) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n0) return;
+    double damp, phi;
+    diag_factors(sigma[r], h, damp, phi);
+    psi[r] = diag_apply(psi[r], v[r], chib[r], h, damp, phi);
+}
+
+}  // namespace decbpm

@@ -1,0 +1,308 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 CPU oracle.
+
+Tolerances (relative *0-weighted L2 error of the complex field):
+  FP64 (C128) fused and plain paths ........ 1e-12 over whole runs
+  FP32 (C64) fused path .................... 1e-5 for one step from the oracle
+                                             state, 1e-4 over a whole run
+Diagnostics (power, Hamiltonian) are FP64 on both sides: 1e-11 relative.
+Sizes span many SELL slices and a ragged last slice; edge cases cover a
+single triangle, fewer than 32 vertices, the maximum field count, zero steps.
+"""
+import math
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import bpm, dec  # noqa: E402
+from paper_2608_03587_b300 import api  # noqa: E402
+from paper_2608_03587_b300 import workloads as W  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+DEV = torch.device("cuda:0")
+
+
+def rel(ops, a, b):
+    return bpm.relative_error(ops, a, b)
+
+
+def to_dev(psi, dtype=torch.complex128):
+    return torch.from_numpy(np.ascontiguousarray(psi)).to(DEV, dtype)
+
+
+def from_dev(t):
+    return t.detach().cpu().numpy().astype(np.complex128)
+
+
+@pytest.fixture(scope="module")
+def fiber():
+    """Step-index fiber (Table II), 3001 vertices: ~94 SELL slices with a ragged tail."""
+    coords, tris = W.mesh_disk_graded(4.0, 3000, 3.0, interfaces=(1.0,), seed=31, grade_from=1.0)
+    V, chi = W.step_index_materials(coords, tris)
+    sigma = W.absorber_profile(coords, 4.0, 20.0)
+    ops = dec.Operators(coords, tris, V, chi)
+    mesh = api.Mesh(coords, tris, V, chi, sigma)
+    return coords, tris, V, chi, sigma, ops, mesh
+
+
+def launch(coords, B, seed=0, A=2.0):
+    rng = np.random.default_rng(seed)
+    cols = []
+    for b in range(B):
+        g = W.elliptic_gaussian(coords, A=A * (1 + 0.2 * b), x0=0.3 * rng.standard_normal(),
+                                y0=0.3 * rng.standard_normal(), theta=rng.uniform(0, math.pi))
+        cols.append(g * np.exp(1j * rng.uniform(0, 2 * math.pi)))
+    return np.stack(cols, axis=1)
+
+
+# ------------------------------------------------------------------ FP64
+@pytest.mark.parametrize("B", [1, 3])
+def test_fp64_fused_matches_oracle(fiber, B):
+    coords, tris, V, chi, sigma, ops, mesh = fiber
+    psi0 = launch(coords, B)
+    dz, n = 2e-3, 25
+    ref = bpm.propagate(ops, (1.0,), psi0, dz, n, sigma)
+    t = to_dev(psi0 if B > 1 else psi0[:, 0])
+    diag = api.propagate(mesh, t, dz, n)
+    out = from_dev(t).reshape(-1, B)
+    assert rel(ops, out, ref) <= 1e-12
+    assert diag.shape == (1, B)
+    for b in range(B):
+        assert diag[0, b]["power"] == pytest.approx(bpm.power(ops, ref[:, b]), rel=1e-11)
+        assert diag[0, b]["z"] == pytest.approx(dz * n)
+
+
+def test_fp64_plain_matches_oracle(fiber):
+    coords, tris, V, chi, sigma, ops, mesh = fiber
+    psi0 = launch(coords, 1)[:, 0]
+    dz, n = 2e-3, 20
+    ref = bpm.propagate(ops, (1.0,), psi0, dz, n, sigma)
+    t = to_dev(psi0)
+    api.propagate(mesh, t, dz, n, variant="plain")
+    assert rel(ops, from_dev(t), ref) <= 1e-12
+
+
+def test_fp64_diagnostics_and_blocks(fiber):
+    """diag_every splits the march into blocks (half steps at the block
+    edges); results and the per-block power/Hamiltonian match the oracle."""
+    coords, tris, V, chi, sigma, ops, mesh = fiber
+    nt = len(tris)
+    psi0 = launch(coords, 2, seed=3)
+    dz, n, every = 1e-3, 10, 4
+    m0 = api.Mesh(coords, tris, V, chi, None)     # no absorber: power conserved
+    t = to_dev(psi0)
+    diag = api.propagate(m0, t, dz, n, diag_every=every)
+    ref = psi0.copy()
+    zs = []
+    steps = [4, 4, 2]
+    for k, s in enumerate(steps):
+        ref = bpm.propagate(ops, (1.0,), ref, dz, s)
+        zs.append(sum(steps[:k + 1]) * dz)
+        for b in range(2):
+            assert diag[k, b]["z"] == pytest.approx(zs[-1])
+            assert diag[k, b]["power"] == pytest.approx(bpm.power(ops, ref[:, b]), rel=1e-11)
+            assert diag[k, b]["hamiltonian"] == pytest.approx(bpm.hamiltonian(ops, (1.0,), ref[:, b]), rel=1e-10)
+            assert diag[k, b]["max_intensity"] == pytest.approx(np.max(np.abs(ref[:, b]) ** 2), rel=1e-12)
+    assert rel(ops, from_dev(t), ref) <= 1e-12
+    assert diag[-1, 0]["power"] == pytest.approx(bpm.power(ops, psi0[:, 0]), rel=1e-12)
+    del nt
+
+
+def test_fp64_higher_order_diffraction(fiber):
+    """p = (p1, p2): exp(i h (p2 A^2 - p1 A)) by the DCT Chebyshev path."""
+    coords, tris, V, chi, sigma, ops, mesh = fiber
+    p = (1.0, 2e-5)
+    m2 = api.Mesh(coords, tris, V, chi, sigma, p=p)
+    psi0 = launch(coords, 1, seed=5)[:, 0]
+    dz, n = 1e-3, 6
+    ref = bpm.propagate(ops, p, psi0, dz, n, sigma)
+    t = to_dev(psi0)
+    api.propagate(m2, t, dz, n)
+    assert rel(ops, from_dev(t), ref) <= 1e-11
+
+
+def test_fp64_element_kerr(fiber):
+    coords, tris, V, chi, sigma, ops, mesh = fiber
+    psi0 = launch(coords, 2, seed=6, A=3.0)
+    dz, n = 2e-3, 12
+    ref = bpm.propagate(ops, (1.0,), psi0, dz, n, sigma, kerr="element")
+    t = to_dev(psi0)
+    api.propagate(mesh, t, dz, n, kerr="element")
+    assert rel(ops, from_dev(t), ref) <= 1e-12
+
+
+def test_fp64_soliton_1d_full_run():
+    """Config of the exact sech soliton (1024 jittered nodes, dz = 1e-3,
+    2000 steps, C128): GPU equals the oracle, both near sech(x) e^{iz/2}."""
+    wl = W.soliton_1d()
+    m = wl.meshes[0]
+    ops = dec.Operators(m.coords, m.cells, m.V_cell, m.chi_cell)
+    psi0 = wl.psi0[0][:, 0]
+    ref = bpm.propagate(ops, wl.p, psi0, wl.dz, wl.n_steps)
+    mesh = api.Mesh.from_workload(m, p=wl.p)
+    t = to_dev(psi0)
+    api.propagate(mesh, t, wl.dz, wl.n_steps)
+    out = from_dev(t)
+    assert rel(ops, out, ref) <= 1e-12
+    z = wl.dz * wl.n_steps
+    assert rel(ops, out, W.sech_1d(m.coords) * np.exp(0.5j * z)) < 5e-4
+
+
+# ------------------------------------------------------------------ FP32
+@pytest.mark.parametrize("B", [1, 2, 16])
+def test_fp32_one_step_from_oracle_state(fiber, B):
+    coords, tris, V, chi, sigma, ops, mesh = fiber
+    psi0 = launch(coords, B, seed=7)
+    dz = 2e-3
+    state = bpm.propagate(ops, (1.0,), psi0, dz, 5, sigma)
+    state32 = state.astype(np.complex64).astype(np.complex128)
+    ref = bpm.propagate(ops, (1.0,), state32, dz, 1, sigma)
+    t = to_dev(state32, torch.complex64)
+    api.propagate(mesh, t, dz, 1)
+    assert rel(ops, from_dev(t).reshape(-1, B), ref) <= 1e-5
+
+
+def test_fp32_full_run(fiber):
+    coords, tris, V, chi, sigma, ops, mesh = fiber
+    psi0 = launch(coords, 4, seed=8)
+    dz, n = 1e-3, 400
+    ref = bpm.propagate(ops, (1.0,), psi0, dz, n, sigma)
+    t = to_dev(psi0, torch.complex64)
+    diag = api.propagate(mesh, t, dz, n)
+    assert rel(ops, from_dev(t), ref) <= 1e-4
+    for b in range(4):
+        assert diag[0, b]["power"] == pytest.approx(bpm.power(ops, ref[:, b]), rel=1e-4)
+
+
+def test_fp32_element_kerr(fiber):
+    coords, tris, V, chi, sigma, ops, mesh = fiber
+    psi0 = launch(coords, 2, seed=9, A=3.0)
+    dz, n = 2e-3, 50
+    ref = bpm.propagate(ops, (1.0,), psi0, dz, n, sigma, kerr="element")
+    t = to_dev(psi0, torch.complex64)
+    api.propagate(mesh, t, dz, n, kerr="element")
+    assert rel(ops, from_dev(t), ref) <= 1e-4
+
+
+# ------------------------------------------------------------------ batched plans
+@pytest.mark.parametrize("precision,tol", [("c128", 1e-12), ("c64", 1e-4)])
+def test_batched_plan_uneven_meshes(precision, tol):
+    """Meshes of uneven size (and so different Chebyshev degrees) and
+    different field counts advance in one persistent launch."""
+    specs = [(600, 3, 41), (2500, 1, 42), (5000, 4, 43), (90, 2, 44)]
+    meshes, opss, sigs, psis = [], [], [], []
+    for n, B, seed in specs:
+        coords, tris = W.mesh_disk_graded(4.0, n, 3.0, interfaces=(1.0,), seed=seed, grade_from=1.0)
+        V, chi = W.step_index_materials(coords, tris)
+        sigma = W.absorber_profile(coords, 4.0, 20.0)
+        meshes.append(api.Mesh(coords, tris, V, chi, sigma))
+        opss.append(dec.Operators(coords, tris, V, chi))
+        sigs.append(sigma)
+        psis.append(W.hg_superpositions(coords, B, np.random.default_rng(seed)))
+    dt = torch.complex64 if precision == "c64" else torch.complex128
+    plan = api.Plan(meshes, [s[1] for s in specs], precision)
+    degs = [plan.degree(i, 2e-3) for i in range(len(specs))]
+    assert len(set(degs)) > 1
+    ts = [to_dev(p, dt) for p in psis]
+    dz, n = 2e-3, 30
+    diag = plan.propagate(ts, dz, n)
+    assert diag.shape == (1, sum(s[1] for s in specs))
+    for ops, sigma, p0, t in zip(opss, sigs, psis, ts):
+        ref = bpm.propagate(ops, (1.0,), p0, dz, n, sigma)
+        assert rel(ops, from_dev(t), ref) <= tol
+    # a second call reuses the captured graph and continues from the new state
+    before = [from_dev(t) for t in ts]
+    plan.propagate(ts, dz, 3)
+    for ops, sigma, p0, t in zip(opss, sigs, before, ts):
+        ref = bpm.propagate(ops, (1.0,), p0, dz, 3, sigma)
+        assert rel(ops, from_dev(t), ref) <= tol
+
+
+# ------------------------------------------------------------------ edge cases
+def test_single_triangle_and_tiny_meshes():
+    coords = np.array([[0.0, 0.0], [1.0, 0.0], [0.2, 0.9]])
+    tris = np.array([[0, 1, 2]], dtype=np.int32)
+    ops = dec.Operators(coords, tris, np.array([-2.0]), np.array([1.5]))
+    mesh = api.Mesh(coords, tris, np.array([-2.0]), np.array([1.5]))
+    psi0 = np.array([1.0 + 0.5j, -0.3j, 0.7])
+    ref = bpm.propagate(ops, (1.0,), psi0, 0.01, 7)
+    t = to_dev(psi0)
+    api.propagate(mesh, t, 0.01, 7)
+    assert rel(ops, from_dev(t), ref) <= 1e-12
+    # 17 vertices: a single partial SELL slice
+    coords, tris = W.mesh_disk_graded(1.0, 17, 1.0, seed=3)
+    ops = dec.Operators(coords, tris)
+    mesh = api.Mesh(coords, tris)
+    psi0 = W.gaussian(coords, w=0.5)
+    ref = bpm.propagate(ops, (1.0,), psi0, 0.01, 5)
+    t = to_dev(psi0)
+    api.propagate(mesh, t, 0.01, 5)
+    assert rel(ops, from_dev(t), ref) <= 1e-12
+
+
+def test_zero_steps_and_max_fields(fiber):
+    coords, tris, V, chi, sigma, ops, mesh = fiber
+    psi0 = launch(coords, 64, seed=10)
+    t = to_dev(psi0)
+    diag = api.propagate(mesh, t, 1e-3, 0)
+    assert np.array_equal(from_dev(t), psi0)
+    assert diag.shape == (1, 64)
+    assert diag[0, 63]["power"] == pytest.approx(bpm.power(ops, psi0[:, 63]), rel=1e-12)
+    ref = bpm.propagate(ops, (1.0,), psi0, 1e-3, 2, sigma)
+    api.propagate(mesh, t, 1e-3, 2)
+    assert rel(ops, from_dev(t), ref) <= 1e-12
+
+
+def test_fields_beyond_maximum_are_rejected(fiber):
+    from paper_2608_03587_b300 import _lib as L
+    coords, tris, V, chi, sigma, ops, mesh = fiber
+    t = torch.zeros((len(coords), 65), dtype=torch.complex64, device=DEV)
+    with pytest.raises(L.DecbpmError) as e:
+        api.propagate(mesh, t, 1e-3, 1)
+    assert e.value.code == L.ERR_UNSUPPORTED
+
+
+def test_host_buffer_entry_point(fiber):
+    coords, tris, V, chi, sigma, ops, mesh = fiber
+    psi0 = launch(coords, 2, seed=11)
+    ref = bpm.propagate(ops, (1.0,), psi0, 2e-3, 5, sigma)
+    h = torch.from_numpy(psi0.copy()).pin_memory()
+    api.propagate_host(mesh, h, 2e-3, 5)
+    assert rel(ops, h.numpy(), ref) <= 1e-12
+
+
+def test_deterministic_bitwise(fiber):
+    coords, tris, V, chi, sigma, ops, mesh = fiber
+    psi0 = launch(coords, 2, seed=12)
+    outs, diags = [], []
+    for _ in range(2):
+        t = to_dev(psi0, torch.complex64)
+        diags.append(api.propagate(mesh, t, 2e-3, 15))
+        outs.append(from_dev(t))
+    assert np.array_equal(outs[0], outs[1])
+    assert diags[0]["power"].tolist() == diags[1]["power"].tolist()
+
+
+# ------------------------------------------------------------------ full size
+def test_full_size_gaussian_disk_one_step_sampled():
+    """The 200k-vertex graded-disk workload at full size, in the launch
+    configuration of the benchmark (C64, fused): one step from the launch
+    field against the oracle's step, on all vertices."""
+    wl = W.gaussian_disk()
+    m = wl.meshes[0]
+    ops = dec.Operators(m.coords, m.cells, m.V_cell, m.chi_cell)
+    psi0 = wl.psi0[0][:, 0]
+    ref = bpm.propagate(ops, wl.p, psi0, wl.dz, 1, m.sigma)
+    mesh = api.Mesh.from_workload(m)
+    assert mesh.n_vertices >= 196_000
+    t = to_dev(psi0.astype(np.complex64), torch.complex64)
+    api.propagate(mesh, t, wl.dz, 1)
+    assert rel(ops, from_dev(t), ref) <= 1e-5
+    t = to_dev(psi0)
+    api.propagate(mesh, t, wl.dz, 1)
+    assert rel(ops, from_dev(t), ref) <= 1e-12

@@ -1,0 +1,153 @@
+"""Host-side checks of libdecbpm that need no GPU: the library loads and
+exports every entry point its header declares, the FP64 host assembly equals
+the oracle's operators, the Chebyshev/Bessel coefficients are right, and bad
+input is rejected with the documented status codes."""
+import ctypes
+import math
+import os
+import re
+
+import numpy as np
+import pytest
+import scipy.sparse as sp
+import scipy.sparse.linalg as spla
+from scipy.special import jv
+
+from oracle import dec
+from paper_2608_03587_b300 import _lib as L
+from paper_2608_03587_b300 import api
+from paper_2608_03587_b300 import workloads as W
+
+HEADER = os.path.join(os.path.dirname(os.path.dirname(__file__)), "include", "decbpm.h")
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(decbpm_[a-z0-9_]+)\s*\(", text)))
+
+
+def test_library_exports_every_declared_symbol(lib):
+    names = declared_functions()
+    assert len(names) >= 15
+    for n in names:
+        assert hasattr(lib, n), n
+        assert n in L.SIGNATURES, "no ctypes signature for %s" % n
+    assert lib.decbpm_version().decode().startswith("decbpm")
+
+
+@pytest.fixture(scope="module")
+def fiber():
+    coords, tris = W.mesh_disk_graded(4.0, 2500, 3.0, interfaces=(1.0,), seed=17, grade_from=1.0)
+    V, chi = W.step_index_materials(coords, tris)
+    sigma = W.absorber_profile(coords, 4.0, 10.0)
+    return coords, tris, V, chi, sigma
+
+
+def test_host_assembly_matches_oracle(fiber):
+    coords, tris, V, chi, sigma = fiber
+    a = api.assemble_host(coords, tris, V, chi, sigma)
+    ops = dec.Operators(coords, tris, V, chi)
+    assert np.allclose(a["m"], ops.H0, rtol=1e-13, atol=0)
+    assert np.allclose(a["v"], ops.v, rtol=1e-12, atol=1e-12 * np.abs(ops.v).max())
+    assert np.allclose(a["chib"], ops.chib, rtol=1e-12)
+    n0 = len(coords)
+    K = sp.csr_matrix((a["K_val"], a["K_col"], a["K_rowptr"]), shape=(n0, n0))
+    assert abs(K - ops.K).max() <= 1e-12 * abs(ops.K).max()
+    info = a["info"]
+    assert info["n_vertices"] == n0 and info["n_cells"] == len(tris)
+    assert info["nnz_offdiag"] == 2 * info["n_edges"]
+    assert info["area"] == pytest.approx(ops.H0.sum(), rel=1e-13)
+    # rho bounds the spectrum of A = *0^{-1} K from above (Gershgorin + margin)
+    lam_max = spla.eigsh(ops.K, k=1, M=sp.diags(ops.H0), which="LA", return_eigenvectors=False)[0]
+    assert lam_max <= info["rho"] <= 2.5 * lam_max
+    # reverse Cuthill-McKee: a permutation with a small bandwidth
+    perm = a["perm"]
+    assert np.array_equal(np.sort(perm), np.arange(n0))
+    assert info["bandwidth"] < n0 / 8
+
+
+def test_host_assembly_1d(fiber):
+    x, cells = W.mesh_1d_jittered(300, seed=2)
+    a = api.assemble_host(x, cells, p=(0.5,))
+    ops = dec.Operators(x, cells)
+    K = sp.csr_matrix((a["K_val"], a["K_col"], a["K_rowptr"]), shape=(300, 300))
+    assert abs(K - ops.K).max() <= 1e-13 * abs(ops.K).max()
+    assert np.allclose(a["m"], ops.H0, rtol=1e-14)
+    assert a["info"]["bandwidth"] == 1
+
+
+@pytest.mark.parametrize("a", [0.0, 1e-3, 0.7, 3.0, 17.5, 120.0])
+def test_bessel_coefficients_match_scipy(a):
+    J = api.bessel_coefficients(a, 1e-16)
+    k = np.arange(len(J))
+    ref = jv(k, a)
+    assert np.max(np.abs(J - ref)) < 1e-14 * max(1.0, math.sqrt(a))
+    # the truncated tail really is below the tolerance
+    kk = np.arange(len(J), len(J) + 40)
+    assert 2 * np.sum(np.abs(jv(kk, a))) <= 1.1e-16
+    assert len(J) >= min(a, 1e9)
+
+
+def test_chebyshev_sum_reproduces_exponential():
+    """sum_k (2 - delta_k0) (-i)^k J_k(a) T_k(x) = exp(-i a x) on [-1, 1]."""
+    a = 9.3
+    J = api.bessel_coefficients(a, 1e-16)
+    x = np.linspace(-1, 1, 101)
+    T = np.cos(np.outer(np.arange(len(J)), np.arccos(x)))
+    coef = J * (-1j) ** np.arange(len(J)) * np.where(np.arange(len(J)) == 0, 1.0, 2.0)
+    assert np.max(np.abs(coef @ T - np.exp(-1j * a * x))) < 1e-14
+
+
+def _rc(**kw):
+    coords = np.array([[0.0, 0.0], [1.0, 0.0], [0.0, 1.0], [1.0, 1.0]])
+    tris = np.array([[0, 1, 2], [1, 3, 2]], dtype=np.int32)
+    args = dict(coords=coords, cells=tris)
+    args.update(kw)
+    try:
+        api.assemble_host(**args)
+        return 0
+    except L.DecbpmError as e:
+        return e.code
+
+
+def test_rejects_bad_meshes():
+    assert _rc() == 0
+    assert _rc(cells=np.array([[0, 2, 1], [1, 3, 2]], dtype=np.int32)) == L.ERR_BAD_MESH       # clockwise
+    assert _rc(cells=np.array([[0, 1, 2], [1, 3, 7]], dtype=np.int32)) == L.ERR_BAD_MESH       # index range
+    bad = np.array([[0.0, 0.0], [1.0, 0.0], [0.0, np.nan], [1.0, 1.0]])
+    assert _rc(coords=bad) == L.ERR_NONFINITE
+    assert _rc(sigma=np.array([0.0, -1.0, 0.0, 0.0])) == L.ERR_INVALID_ARG
+    # an edge shared by three triangles
+    coords = np.array([[0.0, 0.0], [1.0, 0.0], [0.5, 1.0], [0.5, -1.0], [0.6, 2.0]])
+    tris = np.array([[0, 1, 2], [1, 0, 3], [0, 1, 4]], dtype=np.int32)
+    assert _rc(coords=coords, cells=tris) == L.ERR_BAD_MESH
+    # an isolated vertex
+    coords = np.array([[0.0, 0.0], [1.0, 0.0], [0.0, 1.0], [5.0, 5.0]])
+    assert _rc(coords=coords, cells=np.array([[0, 1, 2]], dtype=np.int32)) == L.ERR_BAD_MESH
+    assert "counter-clockwise" in _last_error_after(np.array([[0, 2, 1], [1, 3, 2]], dtype=np.int32))
+
+
+def _last_error_after(cells):
+    try:
+        api.assemble_host(np.array([[0.0, 0.0], [1.0, 0.0], [0.0, 1.0], [1.0, 1.0]]), cells)
+    except L.DecbpmError as e:
+        return str(e)
+    return ""
+
+
+def test_element_kerr_operator_rows(fiber):
+    """The element-averaged Kerr operator the library builds satisfies
+    C 1 = chib (its rows reproduce the lumped coefficient for uniform |psi|)."""
+    # exercised through the oracle identity Q^T D Q 1 = *0(chi) 1 on the same mesh
+    coords, tris, V, chi, sigma = fiber
+    ops = dec.Operators(coords, tris, V, chi)
+    assert np.allclose(ops.QtDQ @ np.ones(ops.n0) / ops.H0, ops.chib, rtol=1e-12)
+
+
+def test_null_arguments_are_rejected(lib):
+    assert lib.decbpm_mesh_create(None, None) == L.ERR_INVALID_ARG
+    assert lib.decbpm_propagate(None, None, None, 1, None, None) == L.ERR_INVALID_ARG
+    h = ctypes.c_void_p()
+    assert lib.decbpm_plan_create(None, 0, None, L.C64, ctypes.byref(h)) == L.ERR_INVALID_ARG
+    assert lib.decbpm_mesh_destroy(None) == L.OK
