@@ -66,6 +66,10 @@ extern "C" {
 #define DECBPM_VARIANT_FUSED  0  /* persistent kernel, fused Chebyshev/Clenshaw terms and diagonal step */
 #define DECBPM_VARIANT_PLAIN  1  /* unfused reference path: one CSR SpMV launch + one update launch per term */
 
+#define DECBPM_ORDER_DEFAULT  0  /* Hilbert curve in 2D, coordinate order in 1D */
+#define DECBPM_ORDER_RCM      1  /* reverse Cuthill-McKee (small bandwidth, thin level sets) */
+#define DECBPM_ORDER_HILBERT  2  /* Hilbert space-filling curve of the vertex positions (compact blocks) */
+
 typedef struct decbpm_mesh_s *decbpm_mesh_t;
 typedef struct decbpm_plan_s *decbpm_plan_t;
 
@@ -87,6 +91,7 @@ typedef struct {
     const double  *sigma_vertex;  /* [n_vertices] or NULL */
     const double  *p_n;           /* [n_p] or NULL */
     int32_t        n_p;
+    int32_t        ordering;      /* internal vertex order: DECBPM_ORDER_DEFAULT / _RCM / _HILBERT */
 } decbpm_mesh_desc;
 
 typedef struct {
@@ -94,7 +99,7 @@ typedef struct {
     int64_t nnz_offdiag;       /* off-diagonal entries of the stiffness K (2 per edge) */
     int32_t max_degree;        /* largest vertex degree */
     int32_t n_p;               /* number of diffraction coefficients */
-    int64_t bandwidth;         /* max |new(p) - new(q)| over edges after reverse Cuthill-McKee */
+    int64_t bandwidth;         /* max |new(p) - new(q)| over edges in the internal order */
     double  rho;               /* upper bound of the spectrum of A = *0^{-1} K (Gershgorin, +1% margin) */
     double  area;              /* sum of cell measures = sum of *0 */
     double  mean_degree;       /* nnz_offdiag / n_vertices */
@@ -129,8 +134,8 @@ const char *decbpm_last_error(void);
  * Assembles the DEC operators in FP64 on the host (Sec. "DEC computational
  * framework" through Eq. 12): canonical edges (a < b), the cotangent form of
  * d0^T *1 d0 (equal to the Galerkin *1 of Eq. 9 with xi = 1), *0, *0(V),
- * *0(chi), the Gershgorin bound rho of A; renumbers vertices by reverse
- * Cuthill-McKee, packs the operator as SELL-32 and uploads it (FP64 and FP32
+ * *0(chi), the Gershgorin bound rho of A; renumbers vertices (Hilbert curve or
+ * reverse Cuthill-McKee), packs the operator as SELL-32 and uploads it (FP64 and FP32
  * copies) to the current CUDA device.  The handle owns that device memory.
  * Errors: INVALID_ARG (NULL/size), BAD_MESH, NONFINITE, CUDA, OOM.          */
 int decbpm_mesh_create(const decbpm_mesh_desc *desc, decbpm_mesh_t *out);
@@ -143,7 +148,8 @@ int decbpm_mesh_info(decbpm_mesh_t mesh, decbpm_mesh_info_t *info);
  *   m, v, chib   [n_vertices]            *0, lumped potential, lumped Kerr coefficient (caller order)
  *   K_rowptr     [n_vertices + 1]        stiffness K = d0^T *1 d0 in CSR, caller order,
  *   K_col, K_val [nnz_offdiag + n_vertices]   diagonal included, columns ascending
- *   perm         [n_vertices]            internal order: perm[new] = caller index             */
+ *   perm         [n_vertices]            internal order: perm[new] = caller index
+ * The internal order is reverse Cuthill-McKee or a Hilbert curve (desc->ordering).           */
 int decbpm_assemble_host(const decbpm_mesh_desc *desc, decbpm_mesh_info_t *info,
                          double *m, double *v, double *chib,
                          int64_t *K_rowptr, int32_t *K_col, double *K_val, int32_t *perm);

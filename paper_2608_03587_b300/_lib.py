@@ -27,6 +27,9 @@ KERR_LUMPED = 0
 KERR_ELEMENT = 1
 VARIANT_FUSED = 0
 VARIANT_PLAIN = 1
+ORDER_DEFAULT = 0
+ORDER_RCM = 1
+ORDER_HILBERT = 2
 
 _c_double_p = ctypes.POINTER(ctypes.c_double)
 _c_int32_p = ctypes.POINTER(ctypes.c_int32)
@@ -37,7 +40,7 @@ class MeshDesc(ctypes.Structure):
     _fields_ = [("dim", ctypes.c_int32), ("n_vertices", ctypes.c_int64), ("n_cells", ctypes.c_int64),
                 ("coords", _c_double_p), ("cells", _c_int32_p), ("V_cell", _c_double_p),
                 ("chi_cell", _c_double_p), ("sigma_vertex", _c_double_p), ("p_n", _c_double_p),
-                ("n_p", ctypes.c_int32)]
+                ("n_p", ctypes.c_int32), ("ordering", ctypes.c_int32)]
 
 
 class MeshInfo(ctypes.Structure):

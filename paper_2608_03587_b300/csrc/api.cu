@@ -78,8 +78,8 @@ struct decbpm_mesh_s {
     int device = 0;
     DevAllocs mem;
     int32_t *slice_ptr = nullptr, *slice_w = nullptr, *col = nullptr, *perm = nullptr;
-    float *x32, *xd32, *v32, *chib32, *sig32, *coff32, *cdiag32;
-    double *x64, *xd64, *v64, *chib64, *sig64, *coff64, *cdiag64, *w64, *m64;
+    float *x32, *v32, *chib32, *sig32, *coff32, *cdiag32;
+    double *x64, *v64, *chib64, *sig64, *coff64, *cdiag64, *w64, *m64;
     int32_t *csr_ptr = nullptr, *csr_col = nullptr;
     double *csr_val = nullptr;
     std::map<std::pair<int, int>, decbpm_plan_t> plans;   // (fields, precision) -> cached single-mesh plan
@@ -91,7 +91,9 @@ static int mesh_upload(decbpm_mesh_t M) {
     const Sell &S = M->S;
     const int64_t n0 = A.n0;
     const double c = 0.5 * A.rho, r = 0.5 * A.rho;
-    // X = (A - c)/r with A = *0^{-1} K:  X_pq = -w_pq / (r m_p),  X_pp = (sum_q w_pq / m_p - c) / r
+    // X = (A - c)/r with A = *0^{-1} K and c = r:  X = A/r - I.  The fused
+    // kernels store x_pq = w_pq / (r m_p) and evaluate (X g)_p = sum_q x_pq (g_p - g_q) - g_p;
+    // the plain path stores X itself in CSR (X_pq = -x_pq, X_pp = (sum_q w_pq / m_p - c) / r).
     std::vector<double> xval(S.col.size()), xdiag(n0), wv(S.col.size()), cv(S.col.size());
     std::vector<double> m(n0), v(n0), chib(n0), sig(n0), cdiag(n0);
     for (int64_t sl = 0; sl < S.n_slices; ++sl)
@@ -100,7 +102,7 @@ static int mesh_upload(decbpm_mesh_t M) {
                 const int64_t idx = S.slice_ptr[sl] + int64_t(j) * kSlice + lane;
                 const int64_t row = sl * kSlice + lane;
                 const double mp = row < n0 ? A.m[A.perm[row]] : 1.0;
-                xval[idx] = -S.w[idx] / (r * mp);
+                xval[idx] = S.w[idx] / (r * mp);
                 wv[idx] = S.w[idx];
                 cv[idx] = S.c[idx];
             }
@@ -119,14 +121,12 @@ static int mesh_upload(decbpm_mesh_t M) {
     TRY(D.upload(&M->col, S.col));
     TRY(D.upload(&M->perm, A.perm));
     TRY(D.upload(&M->x32, cast<float>(xval)));
-    TRY(D.upload(&M->xd32, cast<float>(xdiag)));
     TRY(D.upload(&M->v32, cast<float>(v)));
     TRY(D.upload(&M->chib32, cast<float>(chib)));
     TRY(D.upload(&M->sig32, cast<float>(sig)));
     TRY(D.upload(&M->coff32, cast<float>(cv)));
     TRY(D.upload(&M->cdiag32, cast<float>(cdiag)));
     TRY(D.upload(&M->x64, xval));
-    TRY(D.upload(&M->xd64, xdiag));
     TRY(D.upload(&M->v64, v));
     TRY(D.upload(&M->chib64, chib));
     TRY(D.upload(&M->sig64, sig));
@@ -160,7 +160,7 @@ struct decbpm_plan_s {
     std::vector<int32_t> B;
     int bpad = 1, bpad_log2 = 0, precision = DECBPM_C64, fpt = 1;
     int device = 0, num_sms = 0;
-    int block = 512, grid = 0;
+    int block = 256, grid = 0;
     DevAllocs mem;
     std::vector<void *> psi, b0, b1, b2, user;   // user: device staging for the host-buffer entry points
     void *y_plain = nullptr;                     // SpMV result of the plain path
@@ -177,6 +177,7 @@ struct decbpm_plan_s {
     // coefficient configuration
     double cfg_dz = 0, cfg_tol = -1;
     std::vector<int> order, M, item_begin, items;
+    std::vector<double> theta0;                   // per mesh: phase left out of the step coefficients
     int S = 0, total_items = 0;
     // graphs: key -> exec
     std::map<std::tuple<double, int64_t, int32_t, int32_t, double>, cudaGraphExec_t> graphs;
@@ -234,7 +235,7 @@ static int plan_create_impl(const decbpm_mesh_t *meshes, int32_t n, const int32_
     P->precision = precision;
     P->bpad_log2 = ilog2(maxB);
     P->bpad = 1 << P->bpad_log2;
-    P->fpt = P->bpad >= 2 ? 2 : 1;
+    P->fpt = P->bpad > 32 ? 2 : 1;   // one complex per thread (two above 32 fields: a row fits one warp)
     CK(cudaGetDevice(&P->device));
     CK(cudaDeviceGetAttribute(&P->num_sms, cudaDevAttrMultiProcessorCount, P->device));
     const size_t cs = csize(precision);
@@ -268,7 +269,7 @@ static int plan_create_impl(const decbpm_mesh_t *meshes, int32_t n, const int32_
     int per_sm = 0;
     CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, march_kernel_ptr(precision, P->fpt), P->block, 0));
     if (per_sm < 1) return fail(DECBPM_ERR_CUDA, "march kernel cannot be resident with %d threads", P->block);
-    P->grid = P->num_sms * std::min(per_sm, 2);
+    P->grid = P->num_sms * std::min(per_sm, 4);
     *out = P.release();
     return DECBPM_OK;
 }
@@ -285,7 +286,8 @@ static int plan_configure(decbpm_plan_t P, double dz, double tol) {
     std::iota(P->order.begin(), P->order.end(), 0);
     std::stable_sort(P->order.begin(), P->order.end(), [&](int a, int b) { return ch[a].M > ch[b].M; });
     P->M.resize(n);
-    for (int i = 0; i < n; ++i) P->M[i] = ch[i].M;
+    P->theta0.resize(n);
+    for (int i = 0; i < n; ++i) { P->M[i] = ch[i].M; P->theta0[i] = ch[i].theta0; }
     P->S = ch[P->order[0]].M;
     const int tpr_log2 = P->bpad_log2 - (P->fpt == 2 ? 1 : 0);
     const int rpw = 32 >> tpr_log2;
@@ -338,8 +340,30 @@ static int plan_configure(decbpm_plan_t P, double dz, double tol) {
             if (k == 0) flags |= kFinal;
             s.alpha = mk(alpha);
             s.beta = mk(beta);
+            s.alpha_lo = mk(0.0);
             s.flags = flags;
             coef[off + k] = s;
+        }
+        // The kernel applies X to a constant field exactly (X 1 = -1), so the
+        // lambda = 0 mode sees the stage recurrence at x = -1 with the stored
+        // (rounded) coefficients.  Evaluate that recurrence in FP64 and put
+        // the residual against the exact value f(lambda = 0) e^{-i theta0}
+        // into alpha_lo: the smooth part of the field then carries no
+        // systematic per-step phase or gain error from coefficient rounding.
+        {
+            auto up = [](C z) { return std::complex<double>(double(z.x), double(z.y)); };
+            std::complex<double> bk1 = 0, bk2 = 0, Sv = 0;
+            for (int k = Mi - 1; k >= 0; --k) {
+                const StageCoef<R> &s = coef[off + k];
+                const std::complex<double> g = (s.flags & kGisPsi) ? 1.0 : bk1;
+                std::complex<double> o = up(s.alpha) - up(s.beta) * g;
+                if (s.flags & kHasH) o -= bk2;
+                if (s.flags & kFinal) Sv = o;
+                bk2 = bk1;
+                bk1 = o;
+            }
+            const std::complex<double> target = cb.f0;
+            coef[off].alpha_lo = mk(target - Sv);
         }
         decbpm_mesh_t m = P->meshes[i];
         MeshView<R> &v = views[j];
@@ -349,10 +373,10 @@ static int plan_configure(decbpm_plan_t P, double dz, double tol) {
         v.item_begin = P->item_begin[i];
         v.slice_ptr = m->slice_ptr; v.slice_w = m->slice_w; v.col = m->col;
         if constexpr (sizeof(R) == 4) {
-            v.xval = m->x32; v.xdiag = m->xd32; v.v = m->v32; v.chib = m->chib32; v.sigma = m->sig32;
+            v.xval = m->x32; v.v = m->v32; v.chib = m->chib32; v.sigma = m->sig32;
             v.coff = m->coff32; v.cdiag = m->cdiag32;
         } else {
-            v.xval = m->x64; v.xdiag = m->xd64; v.v = m->v64; v.chib = m->chib64; v.sigma = m->sig64;
+            v.xval = m->x64; v.v = m->v64; v.chib = m->chib64; v.sigma = m->sig64;
             v.coff = m->coff64; v.cdiag = m->cdiag64;
         }
         v.psi = (C *)P->psi[i];
@@ -544,8 +568,9 @@ static int plan_propagate_impl(decbpm_plan_t P, const decbpm_params *prm, void *
     for (int i = 0; i < n; ++i) {
         const int64_t n0 = P->meshes[i]->A.n0;
         const int blocks = int(std::min<int64_t>(4 * P->num_sms, (n0 * P->B[i] + 255) / 256));
+        const double ph = std::fmod(double(prm->n_steps) * P->theta0[i], 2.0 * M_PI);
         permute_out_kernel<C><<<blocks, 256, 0, s>>>((const C *)P->psi[i], (C *)psi_dev[i], P->meshes[i]->perm,
-                                                      int32_t(n0), P->B[i], P->bpad);
+                                                      int32_t(n0), P->B[i], P->bpad, std::cos(ph), std::sin(ph));
     }
     CK(cudaGetLastError());
     CK(cudaStreamSynchronize(s));
@@ -631,7 +656,9 @@ static int propagate_plain(decbpm_mesh_t m, const decbpm_params *prm, void *psi_
         CK(cudaEventRecord(P->ev1, s));
         TRY(launch_diag<double>(P, s, DECBPM_KERR_LUMPED, point++));
     }
-    permute_out_kernel<double2><<<std::min(G, 4 * P->num_sms), T, 0, s>>>(psi, (double2 *)psi_dev, m->perm, n0, 1, 1);
+    const double ph = std::fmod(double(prm->n_steps) * cb.theta0, 2.0 * M_PI);
+    permute_out_kernel<double2><<<std::min(G, 4 * P->num_sms), T, 0, s>>>(psi, (double2 *)psi_dev, m->perm, n0, 1, 1,
+                                                                         std::cos(ph), std::sin(ph));
     CK(cudaGetLastError());
     CK(cudaStreamSynchronize(s));
     return finish_diag(P, prm, n_points, diag_out);

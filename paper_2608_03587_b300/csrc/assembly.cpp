@@ -122,6 +122,43 @@ static void rcm(const std::vector<int64_t> &rowptr, const std::vector<int32_t> &
     perm.assign(order.begin(), order.end());
 }
 
+// Position of (x, y) on the Hilbert curve filling a 2^order x 2^order grid
+// (the iterative rotate-and-reflect construction).
+static uint64_t hilbert_index(uint32_t x, uint32_t y, int order) {
+    uint64_t d = 0;
+    for (uint32_t s = 1u << (order - 1); s > 0; s >>= 1) {
+        const uint32_t rx = (x & s) ? 1u : 0u;
+        const uint32_t ry = (y & s) ? 1u : 0u;
+        d += uint64_t(s) * uint64_t(s) * ((3u * rx) ^ ry);
+        if (ry == 0) {
+            if (rx == 1) { x = s - 1 - (x & (s - 1)) + (x & ~(s - 1)); y = s - 1 - (y & (s - 1)) + (y & ~(s - 1)); }
+            std::swap(x, y);
+        }
+    }
+    return d;
+}
+
+// Vertices sorted along a Hilbert curve of their (quantized) positions; in
+// 1D, by coordinate.
+static void hilbert_order(const double *X, int dim, int64_t n, std::vector<int32_t> &perm) {
+    std::vector<std::pair<uint64_t, int32_t>> key(n);
+    double lo[2] = {X[0], dim == 2 ? X[1] : 0.0}, hi[2] = {X[0], dim == 2 ? X[1] : 0.0};
+    for (int64_t i = 0; i < n; ++i)
+        for (int a = 0; a < dim; ++a) { lo[a] = std::min(lo[a], X[i * dim + a]); hi[a] = std::max(hi[a], X[i * dim + a]); }
+    const int order = 20;
+    const double span = std::max(hi[0] - lo[0], dim == 2 ? hi[1] - lo[1] : 0.0);
+    const double scale = span > 0 ? double((1u << order) - 1) / span : 0.0;
+    for (int64_t i = 0; i < n; ++i) {
+        const uint32_t qx = uint32_t((X[i * dim] - lo[0]) * scale);
+        if (dim == 1) { key[i] = {qx, int32_t(i)}; continue; }
+        const uint32_t qy = uint32_t((X[i * dim + 1] - lo[1]) * scale);
+        key[i] = {hilbert_index(qx, qy, order), int32_t(i)};
+    }
+    std::sort(key.begin(), key.end());
+    perm.resize(n);
+    for (int64_t i = 0; i < n; ++i) perm[i] = key[i].second;
+}
+
 int assemble(const decbpm_mesh_desc *d, Assembly &A) {
     if (!d) return fail(DECBPM_ERR_INVALID_ARG, "mesh description is NULL");
     if (d->dim != 1 && d->dim != 2) return fail(DECBPM_ERR_INVALID_ARG, "dim must be 1 or 2 (got %d)", d->dim);
@@ -267,7 +304,9 @@ int assemble(const decbpm_mesh_desc *d, Assembly &A) {
         A.c_diag[p] = cdiag[p] / (kk * A.m[p]);
     }
 
-    rcm(A.rowptr, A.col, n0, A.perm);
+    if (d->ordering == DECBPM_ORDER_RCM) rcm(A.rowptr, A.col, n0, A.perm);
+    else if (d->ordering == DECBPM_ORDER_DEFAULT || d->ordering == DECBPM_ORDER_HILBERT) hilbert_order(X, dim, n0, A.perm);
+    else return fail(DECBPM_ERR_INVALID_ARG, "unknown ordering %d", d->ordering);
     A.iperm.assign(n0, 0);
     for (int64_t i = 0; i < n0; ++i) A.iperm[A.perm[i]] = int32_t(i);
     A.bandwidth = 0;
@@ -365,14 +404,19 @@ int cheb_coefficients(const std::vector<double> &p, double rho, double h, double
         int M = 0;
         while (M < kmax && tail[M + 1] > tol) ++M;
         M = std::max(M, 2);
-        const cd phase = std::exp(cd(0.0, -h * p[0] * c));
         out.M = M;
+        out.theta0 = -h * p[0] * c;
+        out.f0 = std::exp(cd(0.0, h * p[0] * c));
         out.a.resize(M + 1);
-        cd mi(1.0, 0.0);                                  // (-i)^k, with J_k(-a) = (-1)^k J_k(a)
         for (int k = 0; k <= M; ++k) {
-            double jk = J[k] * ((a < 0 && (k & 1)) ? -1.0 : 1.0);
-            out.a[k] = phase * (k == 0 ? 1.0 : 2.0) * mi * jk;
-            mi *= cd(0.0, -1.0);
+            // (-i)^k J_k(a) is purely real or imaginary; J_k(-a) = (-1)^k J_k(a)
+            const double jk = J[k] * ((a < 0 && (k & 1)) ? -1.0 : 1.0) * (k == 0 ? 1.0 : 2.0);
+            switch (k & 3) {
+                case 0: out.a[k] = cd(jk, 0.0); break;
+                case 1: out.a[k] = cd(0.0, -jk); break;
+                case 2: out.a[k] = cd(-jk, 0.0); break;
+                default: out.a[k] = cd(0.0, jk); break;
+            }
         }
         return DECBPM_OK;
     }
@@ -387,12 +431,17 @@ int cheb_coefficients(const std::vector<double> &p, double rho, double h, double
     while (N < 2 * int(est + 64)) N *= 2;
     std::vector<cd> f(N);
     const double pi = std::acos(-1.0);
-    for (int j = 0; j < N; ++j) {
-        const double x = std::cos(pi * (j + 0.5) / N);
-        const double l = c + r * x;
+    auto gfun = [&](double l) {
         double g = 0.0, pw = 1.0;
         for (size_t n = 1; n <= p.size(); ++n) { pw *= -l; g += p[n - 1] * pw; }
-        f[j] = std::exp(cd(0.0, h * g));
+        return g;
+    };
+    const double gc = gfun(c);
+    out.theta0 = h * gc;
+    out.f0 = std::exp(cd(0.0, h * (gfun(0.0) - gc)));
+    for (int j = 0; j < N; ++j) {
+        const double x = std::cos(pi * (j + 0.5) / N);
+        f[j] = std::exp(cd(0.0, h * (gfun(c + r * x) - gc)));
     }
     std::vector<cd> a(N);
     for (int k = 0; k < N; ++k) {

@@ -62,10 +62,15 @@ void build_sell(const Assembly &a, Sell &s);
 // Bessel J_0..J_kmax(a) (a >= 0) by Miller's backward recurrence.
 void bessel_sequence(double a, int kmax, double *J);
 
-// Chebyshev expansion of f(lambda) = exp(i h sum_n p_n (-lambda)^n) on
-// [0, rho] in x = (lambda - c) / r, c = r = rho / 2:  f = sum_k a_k T_k(x).
+// Chebyshev expansion of f(lambda) = exp(i h g(lambda)), g = sum_n p_n (-lambda)^n,
+// on [0, rho] in x = (lambda - c) / r, c = r = rho / 2:
+//     f = exp(i theta0) sum_k a_k T_k(x),   theta0 = h g(c).
+// The constant phase theta0 is kept out of a_k: rounding it into FP32
+// coefficients would add the same phase error at every step.
 struct Cheb {
     int M = 0;                                  // degree (>= 2)
+    double theta0 = 0.0;
+    std::complex<double> f0;                    // exact f(lambda = 0) e^{-i theta0}
     std::vector<std::complex<double>> a;        // a_0 .. a_M
 };
 int cheb_coefficients(const std::vector<double> &p, double rho, double h, double tol, Cheb &out);

@@ -88,6 +88,7 @@ __device__ __forceinline__ void st_pack(typename CT<R>::c2 *p, const Pack<R, FPT
 enum : int { kGisPsi = 1, kHasH = 2, kFinal = 4 };
 template <typename R> struct StageCoef {
     typename CT<R>::c2 alpha, beta;
+    typename CT<R>::c2 alpha_lo;   // final stage only: residual making the sum exact at lambda = 0
     int flags;
     int pad;
 };
@@ -97,7 +98,7 @@ template <typename R> struct MeshView {
     int32_t M;               // Chebyshev degree (>= 2)
     int32_t item_begin;      // first plan-global work item of this mesh
     const int32_t *slice_ptr, *slice_w, *col;
-    const R *xval, *xdiag;   // X = (A - c)/r: off-diagonal (SELL) and diagonal
+    const R *xval;           // x_pq = w_pq / (r m_p) (SELL): X g = sum_q x_pq (g_p - g_q) - g_p
     const R *v, *chib, *sigma;
     const R *coff, *cdiag;   // element-averaged Kerr operator (SELL) and diagonal
     typename CT<R>::c2 *psi, *b[3];
@@ -168,24 +169,31 @@ __device__ __forceinline__ bool grid_barrier(unsigned long long *bar, unsigned l
 // Exact flow over h of dpsi/dz = i (v + chib |psi|^2) psi - sigma psi:
 // |psi|^2 decays as e^{-2 sigma z}, phase = v h + chib |psi0|^2 phi,
 // phi = (1 - e^{-2 sigma h}) / (2 sigma)  (-> h for sigma = 0).
+// The update is written psi + psi w with w = e^{-sigma h} e^{i theta} - 1
+// = em (1 + e) + e, em = expm1(-sigma h), e = e^{i theta} - 1 =
+// (-2 sin^2(theta/2), sin theta): w is formed without cancellation, so the
+// rounding of |e^{i theta}| does not act as a per-vertex gain of 1 +- eps at
+// every step.
 template <typename R>
-__device__ __forceinline__ void diag_factors(R sigma, R h, R &damp, R &phi) {
+__device__ __forceinline__ void diag_factors(R sigma, R h, R &em, R &phi) {
     if (sigma > R(0)) {
-        damp = exp_r(-sigma * h);
+        em = expm1_r(-sigma * h);
         phi = -expm1_r(R(-2) * sigma * h) / (R(2) * sigma);
     } else {
-        damp = R(1);
+        em = R(0);
         phi = h;
     }
 }
 
 template <typename C, typename R>
-__device__ __forceinline__ C diag_apply(C s, R v, R chib, R h, R damp, R phi) {
+__device__ __forceinline__ C diag_apply(C s, R v, R chib, R h, R em, R phi) {
     const R I = s.x * s.x + s.y * s.y;
     const R theta = v * h + chib * I * phi;
-    R sn, cs;
-    sincos_r(theta, &sn, &cs);
-    return cmk<C>(damp * (s.x * cs - s.y * sn), damp * (s.x * sn + s.y * cs));
+    R sh, ch;
+    sincos_r(R(0.5) * theta, &sh, &ch);
+    const C e = cmk<C>(R(-2) * sh * sh, R(2) * sh * ch);             // e^{i theta} - 1
+    const C w = cadd(cscale(cadd(e, cmk<C>(R(1), R(0))), em), e);    // e^{-sigma h} e^{i theta} - 1
+    return cadd(s, cmul(s, w));
 }
 
 // Which mesh owns plan-global item `it` (meshes are few: linear scan).
@@ -196,6 +204,20 @@ __device__ __forceinline__ int mesh_of_item(const int32_t *s_begin, int n_meshes
 }
 
 // One Clenshaw stage for one warp item (RPW rows x all fields of one mesh).
+// X g is evaluated in difference form, (X g)_p = sum_q x_pq (g_p - g_q) - g_p
+// with x_pq = w_pq / (r m_p) > 0 (X = A/r - I since c = r): constants are
+// annihilated exactly whatever the rounding of x_pq, so smooth fields keep
+// FP32 accuracy relative to their Laplacian, not to r |g|.  The neighbour
+// indices and weights of up to kUnroll entries are loaded first, then all
+// gathers are issued together (memory-level parallelism).
+#ifndef DECBPM_UNROLL
+#define DECBPM_UNROLL 1
+#endif
+#ifndef DECBPM_MARCH_MINB
+#define DECBPM_MARCH_MINB 4
+#endif
+constexpr int kUnroll = DECBPM_UNROLL;
+
 template <typename R, int FPT>
 __device__ __forceinline__ void clenshaw_item(const MeshView<R> &m, int local_item, int k, R h_post,
                                               int kerr_mode, int bpad_log2) {
@@ -209,27 +231,50 @@ __device__ __forceinline__ void clenshaw_item(const MeshView<R> &m, int local_it
     const int bpad = 1 << bpad_log2;
     const StageCoef<R> sc = m.coef[k];
     const C *g = (sc.flags & kGisPsi) ? m.psi : m.b[(k + 1) % 3];
+    const size_t own = (size_t)row * bpad + fo;
 
     const int slice = row >> 5;
     const int base = __ldg(m.slice_ptr + slice) + (row & 31);
     const int width = __ldg(m.slice_w + slice);
-    Pack<R, FPT> acc = ld_pack<R, FPT>(g + (size_t)row * bpad + fo);
-    const R xd = __ldg(m.xdiag + row);
+    int q[kUnroll];
+    R x[kUnroll];
 #pragma unroll
-    for (int f = 0; f < FPT; ++f) acc.v[f] = cscale(acc.v[f], xd);
-    for (int j = 0; j < width; ++j) {
-        const int q = __ldg(m.col + base + 32 * j);
-        const R x = __ldg(m.xval + base + 32 * j);
-        const Pack<R, FPT> gq = ld_pack<R, FPT>(g + (size_t)q * bpad + fo);
-#pragma unroll
-        for (int f = 0; f < FPT; ++f) acc.v[f] = cfma(x, gq.v[f], acc.v[f]);
+    for (int j = 0; j < kUnroll; ++j) {
+        if (j < width) {
+            q[j] = __ldg(m.col + base + 32 * j);
+            x[j] = __ldg(m.xval + base + 32 * j);
+        }
     }
-    const Pack<R, FPT> ps = ld_pack<R, FPT>(m.psi + (size_t)row * bpad + fo);
+    const Pack<R, FPT> gp = ld_pack<R, FPT>(g + own);
+    const Pack<R, FPT> ps = ld_pack<R, FPT>(m.psi + own);
+    Pack<R, FPT> hh;
+    if (sc.flags & kHasH) hh = ld_pack<R, FPT>(m.b[(k + 2) % 3] + own);
+    Pack<R, FPT> gq[kUnroll];
+#pragma unroll
+    for (int j = 0; j < kUnroll; ++j)
+        if (j < width) gq[j] = ld_pack<R, FPT>(g + (size_t)q[j] * bpad + fo);
+    Pack<R, FPT> acc;
+#pragma unroll
+    for (int f = 0; f < FPT; ++f) acc.v[f] = cmk<C>(R(0), R(0));
+#pragma unroll
+    for (int j = 0; j < kUnroll; ++j)
+        if (j < width) {
+#pragma unroll
+            for (int f = 0; f < FPT; ++f) acc.v[f] = cfma(x[j], csub(gp.v[f], gq[j].v[f]), acc.v[f]);
+        }
+    for (int j = kUnroll; j < width; ++j) {                     // rare: vertices of degree > kUnroll
+        const int qq = __ldg(m.col + base + 32 * j);
+        const R xx = __ldg(m.xval + base + 32 * j);
+        const Pack<R, FPT> gg = ld_pack<R, FPT>(g + (size_t)qq * bpad + fo);
+#pragma unroll
+        for (int f = 0; f < FPT; ++f) acc.v[f] = cfma(xx, csub(gp.v[f], gg.v[f]), acc.v[f]);
+    }
     Pack<R, FPT> out;
 #pragma unroll
-    for (int f = 0; f < FPT; ++f) out.v[f] = cadd(cmul(sc.alpha, ps.v[f]), cmul(sc.beta, acc.v[f]));
+    for (int f = 0; f < FPT; ++f)
+        out.v[f] = cadd(cadd(cmul(sc.alpha, ps.v[f]), cmul(sc.alpha_lo, ps.v[f])),
+                        cmul(sc.beta, csub(acc.v[f], gp.v[f])));
     if (sc.flags & kHasH) {
-        const Pack<R, FPT> hh = ld_pack<R, FPT>(m.b[(k + 2) % 3] + (size_t)row * bpad + fo);
 #pragma unroll
         for (int f = 0; f < FPT; ++f) out.v[f] = csub(out.v[f], hh.v[f]);
     }
@@ -241,13 +286,13 @@ __device__ __forceinline__ void clenshaw_item(const MeshView<R> &m, int local_it
             const R vv = __ldg(m.v + row), cb = __ldg(m.chib + row);
 #pragma unroll
             for (int f = 0; f < FPT; ++f) out.v[f] = diag_apply(out.v[f], vv, cb, h_post, damp, phi);
-            st_pack<R, FPT>(m.psi + (size_t)row * bpad + fo, out);
+            st_pack<R, FPT>(m.psi + own, out);
         } else {
             // element-averaged Kerr needs the neighbours' |S|^2: park S in b[0]
-            st_pack<R, FPT>(m.b[0] + (size_t)row * bpad + fo, out);
+            st_pack<R, FPT>(m.b[0] + own, out);
         }
     } else {
-        st_pack<R, FPT>(m.b[k % 3] + (size_t)row * bpad + fo, out);
+        st_pack<R, FPT>(m.b[k % 3] + own, out);
     }
 }
 
@@ -287,9 +332,11 @@ __device__ __forceinline__ void element_kerr_item(const MeshView<R> &m, int loca
     Pack<R, FPT> out;
 #pragma unroll
     for (int f = 0; f < FPT; ++f) {
-        R sn, cs;
-        sincos_r(vh + rate[f], &sn, &cs);
-        out.v[f] = cmk<C>(damp * (s.v[f].x * cs - s.v[f].y * sn), damp * (s.v[f].x * sn + s.v[f].y * cs));
+        R sh, ch;
+        sincos_r(R(0.5) * (vh + rate[f]), &sh, &ch);
+        const C e = cmk<C>(R(-2) * sh * sh, R(2) * sh * ch);
+        const C w = cadd(cscale(cadd(e, cmk<C>(R(1), R(0))), damp), e);
+        out.v[f] = cadd(s.v[f], cmul(s.v[f], w));
     }
     st_pack<R, FPT>(dst + (size_t)row * bpad + fo, out);
 }
@@ -343,7 +390,7 @@ __device__ __forceinline__ void for_my_items(const MarchParams<R> &P, const int3
 }
 
 template <typename R, int FPT>
-__global__ void __launch_bounds__(512) march_kernel(MarchParams<R> P) {
+__global__ void __launch_bounds__(256, DECBPM_MARCH_MINB) march_kernel(MarchParams<R> P) {
     __shared__ int32_t s_begin[kMaxMeshes + 1];
     for (int i = threadIdx.x; i < P.n_meshes; i += blockDim.x) s_begin[i] = P.meshes[i].item_begin;
     __syncthreads();
@@ -406,13 +453,20 @@ __global__ void permute_in_kernel(const C *__restrict__ user, C *__restrict__ in
     }
 }
 
+// user[perm[new]][f] = phase * internal[new][f]; phase (FP64) is the global
+// factor exp(i n theta0) that the step coefficients leave out.
 template <typename C>
 __global__ void permute_out_kernel(const C *__restrict__ internal, C *__restrict__ user, const int32_t *__restrict__ perm,
-                                   int32_t n0, int32_t B, int32_t bpad) {
+                                   int32_t n0, int32_t B, int32_t bpad, double phase_re, double phase_im) {
     const long long n = (long long)n0 * B;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
         const int r = int(i / B), f = int(i % B);
-        user[(size_t)perm[r] * B + f] = internal[(size_t)r * bpad + f];
+        const C a = internal[(size_t)r * bpad + f];
+        const double ar = a.x, ai = a.y;
+        C o;
+        o.x = decltype(a.x)(ar * phase_re - ai * phase_im);
+        o.y = decltype(a.x)(ar * phase_im + ai * phase_re);
+        user[(size_t)perm[r] * B + f] = o;
     }
 }
 

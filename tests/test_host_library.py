@@ -61,10 +61,19 @@ def test_host_assembly_matches_oracle(fiber):
     # rho bounds the spectrum of A = *0^{-1} K from above (Gershgorin + margin)
     lam_max = spla.eigsh(ops.K, k=1, M=sp.diags(ops.H0), which="LA", return_eigenvectors=False)[0]
     assert lam_max <= info["rho"] <= 2.5 * lam_max
-    # reverse Cuthill-McKee: a permutation with a small bandwidth
+    # internal orders: permutations; RCM has a small bandwidth, the Hilbert
+    # curve keeps most edges short (compact blocks of consecutive vertices)
     perm = a["perm"]
     assert np.array_equal(np.sort(perm), np.arange(n0))
-    assert info["bandwidth"] < n0 / 8
+    r = api.assemble_host(coords, tris, V, chi, sigma, ordering="rcm")
+    assert np.array_equal(np.sort(r["perm"]), np.arange(n0))
+    assert r["info"]["bandwidth"] < n0 / 8
+    inv = np.empty(n0, dtype=np.int64)
+    inv[perm] = np.arange(n0)
+    E = dec.edges(tris)
+    span = np.abs(inv[E[:, 0]] - inv[E[:, 1]])
+    assert np.median(span) < 40
+    assert np.mean(span < 256) > 0.8
 
 
 def test_host_assembly_1d(fiber):
