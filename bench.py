@@ -1,0 +1,367 @@
+"""Benchmark: vertex-steps/s of the DEC split-step march on one B300 (or N
+independent replicas under torchrun), with the HBM roofline of the march
+kernel, an end-to-end number through the host-buffer entry point, and the
+CPU oracle as a reported baseline.
+
+Workload (default): 16 step-index fibers of the paper's Table II (core radius
+1, DEC disk of radius 4, V = -V#^2 in the cladding, Kerr ratio 2.2/2.8) with
+20k..500k vertices, 16 launch fields each (seeded Hermite-Gauss
+superpositions), dz = 5e-4, complex64 (FP32 arithmetic, FP64 diagnostics),
+all advanced by one persistent launch per call.  A "step" is one z-step of
+all 256 fields.  Its working set (~1.4 GB) is far larger than the 126 MB L2,
+so no L2 flush is needed between steps.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+PEAKS_PATH = os.path.join(ROOT, "MEASURED_PEAKS.json")
+FALLBACK_HBM_GBS = 6400.0
+METRIC = "vertex-steps/s (complex field) + % HBM roofline, FP32/batched vs plain FP64 on GPU"
+UNIT = "vertex-steps/s"
+
+# DRAM bytes per algorithmic byte of the march kernel, from the ncu capture
+# summarized in profiles/march_kernel_fiber500k_b16.md, valid for the kernel
+# source whose hash is recorded with it (traffic is reported as null otherwise).
+TRAFFIC_RATIO = None
+TRAFFIC_SRC_HASH = None
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    for f in ("kernels.cuh", "api.cu"):
+        with open(os.path.join(ROOT, "paper_2608_03587_b300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def hbm_peak():
+    try:
+        with open(PEAKS_PATH) as fh:
+            return float(json.load(fh)["hbm_gbs"]), "measured"
+    except Exception:  # noqa: BLE001
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during a region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, local_rank: int):
+        # nvidia-smi indexes physical GPUs: map through CUDA_VISIBLE_DEVICES
+        vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+        ids = [v.strip() for v in vis.split(",")] if vis else []
+        self.gpu = ids[local_rank] if local_rank < len(ids) else str(local_rank)
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.Q, "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:  # noqa: BLE001
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:  # noqa: BLE001
+                self.proc.kill()
+
+    def summary(self):
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        try:
+            for line in open(self.path):
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    smax.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for n, v in zip(names, parts[5:9]):
+                    if v.lower() in ("active", "1", "yes"):
+                        reasons.add(n)
+        finally:
+            try:
+                os.unlink(self.path)
+            except OSError:
+                pass
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ workload
+def build_workload(args, rank: int):
+    from paper_2608_03587_b300 import workloads as W
+    return W.batched_fibers(n_meshes=args.meshes, fields_per_mesh=args.fields, seed=shard_seed(rank))
+
+
+def algorithmic_bytes_per_step(mesh_infos, fields, degrees, scalar_bytes=8):
+    """Bytes the degree-M Clenshaw chain must move per z-step (all meshes):
+    per vertex-field, M * (S_op / B + 4 s) + 12 / B with S_op = 8 d + 8
+    (column index and weight per off-diagonal entry, diagonal, row pointer),
+    s = 8 (complex64) and 12 B of per-vertex epilogue data (v, chib, sigma)."""
+    total = 0.0
+    for info, B, M in zip(mesh_infos, fields, degrees):
+        s_op = 8.0 * info["mean_degree"] + 8.0
+        per_vf = M * (s_op / B + 4 * scalar_bytes) + 12.0 / B
+        total += per_vf * info["n_vertices"] * B
+    return total
+
+
+def max_over_ranks(values, world, device=None):
+    """Element-wise maximum of per-rank timings (all ranks get the result)."""
+    if world <= 1:
+        return [float(v) for v in values]
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64,
+                     device=device if dist.get_backend() == "nccl" else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(x) for x in t.cpu().tolist()]
+
+
+def shard_seed(rank: int) -> int:
+    """Replicas (weak scaling): every rank advances its own independent batch
+    of the same shape; the launch-field seed differs per rank."""
+    return 4 + 1000 * rank
+
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+    from paper_2608_03587_b300 import api
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    t0 = time.time()
+    wl = build_workload(args, rank)
+    meshes = [api.Mesh.from_workload(m, p=wl.p) for m in wl.meshes]
+    fields = [int(p.shape[1]) for p in wl.psi0]
+    plan = api.Plan(meshes, fields, "c64")
+    setup_s = time.time() - t0
+    psis = [torch.from_numpy(p).to(dev, torch.complex64).contiguous() for p in wl.psi0]
+    infos = [m.info() for m in meshes]
+    degrees = [plan.degree(i, wl.dz) for i in range(len(meshes))]
+    units_per_step = sum(inf["n_vertices"] * B for inf, B in zip(infos, fields))
+
+    def sync_all():
+        torch.cuda.synchronize()
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    # warm-up: W untimed steps (also captures the CUDA graph of this step count)
+    plan.propagate(psis, wl.dz, args.warmup)
+    plan.propagate(psis, wl.dz, args.steps)          # graph for K steps captured outside the timed region
+    sync_all()
+    stream = torch.cuda.current_stream()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local_rank) as clk:
+        sync_all()
+        ev0.record(stream)
+        plan.propagate(psis, wl.dz, args.steps)
+        ev1.record(stream)
+        sync_all()
+    ms = ev0.elapsed_time(ev1)
+    march_ms = plan.last_march_ms()
+    cfg = plan.config()
+    clocks = clk.summary()
+
+    # end to end through the host-buffer entry point (pinned host fields;
+    # H2D of every field, the K-step march, D2H of every field and the diagnostics)
+    host = [torch.from_numpy(p.astype(np.complex64)).pin_memory() for p in wl.psi0]
+    plan.propagate_host(host, wl.dz, args.steps)
+    sync_all()
+    t_e2e = time.perf_counter()
+    plan.propagate_host(host, wl.dz, args.steps)
+    sync_all()
+    e2e_s = time.perf_counter() - t_e2e
+    io_bytes = sum(h.numel() * 8 for h in host)
+
+    ms, march_ms, e2e_ms = max_over_ranks([ms, march_ms, e2e_s * 1e3], world, dev)
+
+    alg_step = algorithmic_bytes_per_step(infos, fields, degrees)
+    peak, peak_kind = hbm_peak()
+    achieved = alg_step * args.steps / (march_ms * 1e-3) / 1e9
+    traffic = None
+    if TRAFFIC_RATIO is not None and TRAFFIC_SRC_HASH == kernel_source_hash():
+        traffic = TRAFFIC_RATIO * alg_step * args.steps
+    value = units_per_step * args.steps * world / (ms * 1e-3)
+    e2e_value = units_per_step * args.steps * world / (e2e_ms * 1e-3)
+    # kernels of ours per timed call: permute in / out per mesh, the march
+    # kernel, two diagnostic kernels per mesh
+    launches = 1 + 4 * len(meshes)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {
+            "workload": "batched step-index fibers: %d meshes (%d..%d vertices) x %d fields, dz=%g, c64"
+                        % (len(meshes), min(i["n_vertices"] for i in infos), max(i["n_vertices"] for i in infos),
+                           fields[0], wl.dz),
+            "vertices_total": int(sum(i["n_vertices"] for i in infos)), "fields_per_mesh": fields[0],
+            "cheb_degree_min": int(min(degrees)), "cheb_degree_max": int(max(degrees)),
+            "ordering": "hilbert", "parallelism": "replicas" if world > 1 else "single",
+            "grid": cfg["grid"], "block": cfg["block"], "cuda_graph": bool(cfg["graphs"]),
+            "l2": "working set %.2f GB > 126 MB L2; no flush" % (units_per_step * 8 * 4 / 1e9),
+            "setup_s": round(setup_s, 2),
+        },
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": traffic,
+                     "peak_kind": peak_kind, "kernel": "march_kernel<float,16>",
+                     "kernel_ms": march_ms, "alg_bytes_per_launch": alg_step * args.steps},
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": io_bytes / args.steps,
+                "d2h_bytes_per_step": io_bytes / args.steps},
+        "gpu_launches": launches,
+        "clocks": clocks,
+    }
+    if rank == 0 and not args.no_plain:
+        line["fp64_plain"] = plain_fp64_reference(wl, meshes, api, torch, dev)
+        line["fp64_plain"]["fp32_batched_speedup"] = value / world / line["fp64_plain"]["value"]
+    if rank == 0 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(args, wl)
+    return line
+
+
+def plain_fp64_reference(wl, meshes, api, torch, dev):
+    """The plain single-field FP64 GPU path (unfused CSR SpMV + update
+    launches per Chebyshev term) on the largest fiber, first field."""
+    i = int(np.argmax([m.n_vertices for m in meshes]))
+    psi = torch.from_numpy(np.ascontiguousarray(wl.psi0[i][:, 0])).to(dev, torch.complex128)
+    api.propagate(meshes[i], psi, wl.dz, 1, variant="plain")
+    torch.cuda.synchronize()
+    n = 5
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    api.propagate(meshes[i], psi, wl.dz, n, variant="plain")
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    return {"value": meshes[i].n_vertices * n / (ms * 1e-3), "unit": UNIT, "steps": n,
+            "sample": "largest fiber (%d vertices), 1 field, c128, %d steps" % (meshes[i].n_vertices, n)}
+
+
+# ------------------------------------------------------------------ CPU oracle
+def oracle_sample(wl, n_meshes, n_steps):
+    """Time the FP64 oracle (plain numpy/scipy) on the first field of the
+    n_meshes smallest fibers for n_steps steps; returns (vertex-steps, seconds)."""
+    from oracle import bpm, dec
+    order = np.argsort([m.n_vertices for m in wl.meshes])[:n_meshes]
+    units, secs = 0, 0.0
+    for i in order:
+        m = wl.meshes[i]
+        ops = dec.Operators(m.coords, m.cells, m.V_cell, m.chi_cell)
+        psi = wl.psi0[i][:, 0]
+        t = time.perf_counter()
+        bpm.propagate(ops, wl.p, psi, wl.dz, n_steps, m.sigma)
+        secs += time.perf_counter() - t
+        units += m.n_vertices * n_steps
+    return units, secs
+
+
+def cpu_baseline(args, wl):
+    units, secs = oracle_sample(wl, args.cpu_meshes, 1)
+    return {"value": units / secs, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "first field of the %d smallest fibers, 1 step each (%d vertex-steps, %.1f s); "
+                      "numpy/scipy single thread" % (args.cpu_meshes, units, secs)}
+
+
+def run_reference(args, rank, world):
+    """Reference arm: the CPU FP64 oracle, timed as it stands on the host."""
+    if rank != 0:
+        return None
+    wl = build_workload(args, 0)
+    per_step = []
+    tot_units, tot_s = 0, 0.0
+    for k in range(args.warmup + args.steps):
+        units, secs = oracle_sample(wl, args.ref_meshes, 1)
+        if k >= args.warmup:
+            per_step.append(secs)
+            tot_units += units
+            tot_s += secs
+    value = tot_units / tot_s
+    return {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * tot_s / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "batched step-index fibers (bounded sample: first field of the %d smallest "
+                               "fibers per step)" % args.ref_meshes},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": "first field of the %d smallest fibers, 1 z-step per timed step"
+                                   % args.ref_meshes},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--meshes", type=int, default=16)
+    ap.add_argument("--fields", type=int, default=16)
+    ap.add_argument("--cpu-meshes", type=int, default=8)
+    ap.add_argument("--ref-meshes", type=int, default=4)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-plain", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        line = run_reference(args, rank, world)
+        if line is not None:
+            print(json.dumps(line), flush=True)
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl")
+    line = run_ours(args, rank, world, local_rank)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

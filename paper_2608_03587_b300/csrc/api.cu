@@ -208,11 +208,21 @@ static int ensure_diag_host(decbpm_plan_t P, int n_points) {
 
 static size_t csize(int precision) { return precision == DECBPM_C64 ? 8 : 16; }
 
-template <typename R, int FPT> static const void *march_fn() { return (const void *)march_kernel<R, FPT>; }
+// The march kernel is instantiated per padded field count (1..64).
+template <typename R> static const void *march_ptr_for(int bpad) {
+    switch (bpad) {
+        case 1: return (const void *)march_kernel<R, 1>;
+        case 2: return (const void *)march_kernel<R, 2>;
+        case 4: return (const void *)march_kernel<R, 4>;
+        case 8: return (const void *)march_kernel<R, 8>;
+        case 16: return (const void *)march_kernel<R, 16>;
+        case 32: return (const void *)march_kernel<R, 32>;
+        default: return (const void *)march_kernel<R, 64>;
+    }
+}
 
-static const void *march_kernel_ptr(int precision, int fpt) {
-    if (precision == DECBPM_C64) return fpt == 2 ? march_fn<float, 2>() : march_fn<float, 1>();
-    return fpt == 2 ? march_fn<double, 2>() : march_fn<double, 1>();
+static const void *march_kernel_ptr(int precision, int bpad) {
+    return precision == DECBPM_C64 ? march_ptr_for<float>(bpad) : march_ptr_for<double>(bpad);
 }
 
 static int plan_create_impl(const decbpm_mesh_t *meshes, int32_t n, const int32_t *fields, int32_t precision,
@@ -235,7 +245,8 @@ static int plan_create_impl(const decbpm_mesh_t *meshes, int32_t n, const int32_
     P->precision = precision;
     P->bpad_log2 = ilog2(maxB);
     P->bpad = 1 << P->bpad_log2;
-    P->fpt = P->bpad > 32 ? 2 : 1;   // one complex per thread (two above 32 fields: a row fits one warp)
+    // complex values per thread; must match Geo<R, BPAD>::FPT of the kernel
+    P->fpt = precision == DECBPM_C64 ? (P->bpad >= 2 ? 2 : 1) : (P->bpad > 32 ? 2 : 1);
     CK(cudaGetDevice(&P->device));
     CK(cudaDeviceGetAttribute(&P->num_sms, cudaDevAttrMultiProcessorCount, P->device));
     const size_t cs = csize(precision);
@@ -267,7 +278,7 @@ static int plan_create_impl(const decbpm_mesh_t *meshes, int32_t n, const int32_
     CK(cudaEventCreate(&P->ev1));
     // occupancy-derived persistent grid: every CTA must be co-resident
     int per_sm = 0;
-    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, march_kernel_ptr(precision, P->fpt), P->block, 0));
+    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, march_kernel_ptr(precision, P->bpad), P->block, 0));
     if (per_sm < 1) return fail(DECBPM_ERR_CUDA, "march kernel cannot be resident with %d threads", P->block);
     P->grid = P->num_sms * std::min(per_sm, 4);
     *out = P.release();
@@ -422,8 +433,8 @@ static int launch_march(decbpm_plan_t P, cudaStream_t s, int n_steps, int kerr_m
     attr[0].val.cooperative = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    if (P->fpt == 2) CK(cudaLaunchKernelEx(&cfg, march_kernel<R, 2>, mp));
-    else CK(cudaLaunchKernelEx(&cfg, march_kernel<R, 1>, mp));
+    void *args[] = {&mp};
+    CK(cudaLaunchKernelExC(&cfg, march_ptr_for<R>(P->bpad), args));
     return DECBPM_OK;
 }
 

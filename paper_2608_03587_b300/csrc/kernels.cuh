@@ -17,6 +17,10 @@
 
 namespace decbpm {
 
+#ifndef DECBPM_MARCH_MINB
+#define DECBPM_MARCH_MINB 2     // CTAs of 256 threads per SM the march kernel is compiled for
+#endif
+
 constexpr int kMaxMeshes = 64;
 constexpr int kMaxFields = 64;
 constexpr long long kBarrierTimeoutNs = 4000000000LL;   // default limit of one barrier wait: 4 s
@@ -203,96 +207,164 @@ __device__ __forceinline__ int mesh_of_item(const int32_t *s_begin, int n_meshes
     return i;
 }
 
-// One Clenshaw stage for one warp item (RPW rows x all fields of one mesh).
-// X g is evaluated in difference form, (X g)_p = sum_q x_pq (g_p - g_q) - g_p
-// with x_pq = w_pq / (r m_p) > 0 (X = A/r - I since c = r): constants are
-// annihilated exactly whatever the rounding of x_pq, so smooth fields keep
-// FP32 accuracy relative to their Laplacian, not to r |g|.  The neighbour
-// indices and weights of up to kUnroll entries are loaded first, then all
-// gathers are issued together (memory-level parallelism).
-#ifndef DECBPM_UNROLL
-#define DECBPM_UNROLL 1
-#endif
-#ifndef DECBPM_MARCH_MINB
-#define DECBPM_MARCH_MINB 4
-#endif
-constexpr int kUnroll = DECBPM_UNROLL;
+// Compile-time geometry of a warp item for BPAD padded fields per vertex:
+// FPT complex values per thread, TPR threads per row, RPW rows per warp item.
+// A row's operator entries j < 8 live in registers of the row's lanes: entry j
+// in lane (j % TPR) of the row group, slot j / TPR (E slots per lane).
+template <typename R, int BPAD> struct Geo {
+    // complex64: two per thread (16-byte accesses) whenever there are two
+    // fields; complex128: one (already 16 bytes) unless a row needs more
+    // than a warp
+    static constexpr int FPT = sizeof(R) == 4 ? (BPAD >= 2 ? 2 : 1) : (BPAD > 32 ? 2 : 1);
+    static constexpr int TPR = BPAD / FPT;
+    static constexpr int TPR_LOG2 = TPR >= 32 ? 5 : TPR >= 16 ? 4 : TPR >= 8 ? 3 : TPR >= 4 ? 2 : TPR >= 2 ? 1 : 0;
+    static constexpr int RPW = 32 / TPR;
+    static constexpr int E = TPR >= 8 ? 1 : 8 / TPR;
+};
 
-template <typename R, int FPT>
-__device__ __forceinline__ void clenshaw_item(const MeshView<R> &m, int local_item, int k, R h_post,
-                                              int kerr_mode, int bpad_log2) {
-    using C = typename CT<R>::c2;
+template <typename R, int E> struct ItemMeta {
+    int row;        // vertex row of this lane (may be >= n0 in the last item of a mesh)
+    int mi;         // mesh index in the plan
+    int base;       // SELL offset of (row, j = 0)
+    int width;      // SELL width of the row's slice (uniform over the warp item)
+    int q[E];
+    R x[E];
+};
+
+// Metadata of plan-global item `it`: row, slice offsets and this lane's
+// share of the row's (column, weight) entries.
+template <typename R, int BPAD>
+__device__ __forceinline__ void load_meta(const MeshView<R> *sv, const int32_t *s_begin, int n_meshes, int it,
+                                          ItemMeta<R, Geo<R, BPAD>::E> &mt) {
+    using G = Geo<R, BPAD>;
     const int lane = threadIdx.x & 31;
-    const int tpr_log2 = bpad_log2 - (FPT == 2 ? 1 : 0);      // threads per row
-    const int rpw = 32 >> tpr_log2;                             // rows per warp item
-    const int row = local_item * rpw + (lane >> tpr_log2);
-    if (row >= m.n0) return;
-    const int fo = (lane & ((1 << tpr_log2) - 1)) * FPT;        // first field of this thread
-    const int bpad = 1 << bpad_log2;
-    const StageCoef<R> sc = m.coef[k];
-    const C *g = (sc.flags & kGisPsi) ? m.psi : m.b[(k + 1) % 3];
-    const size_t own = (size_t)row * bpad + fo;
-
-    const int slice = row >> 5;
-    const int base = __ldg(m.slice_ptr + slice) + (row & 31);
-    const int width = __ldg(m.slice_w + slice);
-    int q[kUnroll];
-    R x[kUnroll];
+    int mi = 0;
+    while (mi + 1 < n_meshes && it >= s_begin[mi + 1]) ++mi;
+    const MeshView<R> &m = sv[mi];
+    mt.mi = mi;
+    mt.row = (it - s_begin[mi]) * G::RPW + (lane >> G::TPR_LOG2);
+    const int slice = mt.row >> 5;          // always < n_slices: items never leave the last slice
+    mt.base = __ldg(m.slice_ptr + slice) + (mt.row & 31);
+    mt.width = __ldg(m.slice_w + slice);
+    const int lr = lane & (G::TPR - 1);
 #pragma unroll
-    for (int j = 0; j < kUnroll; ++j) {
-        if (j < width) {
-            q[j] = __ldg(m.col + base + 32 * j);
-            x[j] = __ldg(m.xval + base + 32 * j);
-        }
-    }
-    const Pack<R, FPT> gp = ld_pack<R, FPT>(g + own);
-    const Pack<R, FPT> ps = ld_pack<R, FPT>(m.psi + own);
-    Pack<R, FPT> hh;
-    if (sc.flags & kHasH) hh = ld_pack<R, FPT>(m.b[(k + 2) % 3] + own);
-    Pack<R, FPT> gq[kUnroll];
-#pragma unroll
-    for (int j = 0; j < kUnroll; ++j)
-        if (j < width) gq[j] = ld_pack<R, FPT>(g + (size_t)q[j] * bpad + fo);
-    Pack<R, FPT> acc;
-#pragma unroll
-    for (int f = 0; f < FPT; ++f) acc.v[f] = cmk<C>(R(0), R(0));
-#pragma unroll
-    for (int j = 0; j < kUnroll; ++j)
-        if (j < width) {
-#pragma unroll
-            for (int f = 0; f < FPT; ++f) acc.v[f] = cfma(x[j], csub(gp.v[f], gq[j].v[f]), acc.v[f]);
-        }
-    for (int j = kUnroll; j < width; ++j) {                     // rare: vertices of degree > kUnroll
-        const int qq = __ldg(m.col + base + 32 * j);
-        const R xx = __ldg(m.xval + base + 32 * j);
-        const Pack<R, FPT> gg = ld_pack<R, FPT>(g + (size_t)qq * bpad + fo);
-#pragma unroll
-        for (int f = 0; f < FPT; ++f) acc.v[f] = cfma(xx, csub(gp.v[f], gg.v[f]), acc.v[f]);
-    }
-    Pack<R, FPT> out;
-#pragma unroll
-    for (int f = 0; f < FPT; ++f)
-        out.v[f] = cadd(cadd(cmul(sc.alpha, ps.v[f]), cmul(sc.alpha_lo, ps.v[f])),
-                        cmul(sc.beta, csub(acc.v[f], gp.v[f])));
-    if (sc.flags & kHasH) {
-#pragma unroll
-        for (int f = 0; f < FPT; ++f) out.v[f] = csub(out.v[f], hh.v[f]);
-    }
-    if (sc.flags & kFinal) {
-        if (kerr_mode == 0) {
-            R damp, phi;
-            const R sig = __ldg(m.sigma + row);
-            diag_factors(sig, h_post, damp, phi);
-            const R vv = __ldg(m.v + row), cb = __ldg(m.chib + row);
-#pragma unroll
-            for (int f = 0; f < FPT; ++f) out.v[f] = diag_apply(out.v[f], vv, cb, h_post, damp, phi);
-            st_pack<R, FPT>(m.psi + own, out);
+    for (int e = 0; e < G::E; ++e) {
+        const int j = e * G::TPR + lr;
+        if (j < mt.width) {
+            mt.q[e] = __ldg(m.col + mt.base + 32 * j);
+            mt.x[e] = __ldg(m.xval + mt.base + 32 * j);
         } else {
-            // element-averaged Kerr needs the neighbours' |S|^2: park S in b[0]
-            st_pack<R, FPT>(m.b[0] + own, out);
+            mt.q[e] = 0;
+            mt.x[e] = R(0);
         }
-    } else {
-        st_pack<R, FPT>(m.b[k % 3] + own, out);
+    }
+}
+
+// One Clenshaw stage over this CTA's share of the active items.  X g is
+// evaluated in difference form, (X g)_p = sum_q x_pq (g_p - g_q) - g_p with
+// x_pq = w_pq / (r m_p) > 0 (X = A/r - I since c = r): constants are
+// annihilated exactly whatever the rounding of x_pq, so smooth fields keep
+// FP32 accuracy relative to their Laplacian, not to r |g|.
+// Each warp walks its items as a two-deep software pipeline: the next item's
+// operator metadata is requested while the current item's neighbour gathers
+// are in flight, so one memory latency (not three) is exposed per item.
+template <typename R, int BPAD>
+__device__ __forceinline__ void clenshaw_stage(const MeshView<R> *sv, const StageCoef<R> *scoef, const int32_t *s_begin,
+                                               int n_meshes, int n_active, int k, R h_post, int kerr_mode) {
+    using G = Geo<R, BPAD>;
+    using C = typename CT<R>::c2;
+    constexpr int FPT = G::FPT;
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    const int lo = int((long long)n_active * blockIdx.x / gridDim.x);
+    const int hi = int((long long)n_active * (blockIdx.x + 1) / gridDim.x);
+    const int fo = (lane & (G::TPR - 1)) * FPT;
+    const int row_lane0 = lane & ~(G::TPR - 1);
+    int it = lo + warp;
+    ItemMeta<R, G::E> cur;
+    if (it < hi) load_meta<R, BPAD>(sv, s_begin, n_meshes, it, cur);
+    while (it < hi) {
+        const int nxt = it + nwarps;
+        const MeshView<R> &m = sv[cur.mi];
+        const StageCoef<R> sc = scoef[cur.mi];
+        const C *g = (sc.flags & kGisPsi) ? m.psi : m.b[(k + 1) % 3];
+        const bool live = cur.row < m.n0;
+        const size_t own = (size_t)cur.row * BPAD + fo;
+        Pack<R, FPT> gp, ps, hh;
+        if (live) {
+            gp = ld_pack<R, FPT>(g + own);
+            ps = ld_pack<R, FPT>(m.psi + own);
+            if (sc.flags & kHasH) hh = ld_pack<R, FPT>(m.b[(k + 2) % 3] + own);
+        }
+        Pack<R, FPT> gq[8];
+        R xs[8];
+#pragma unroll
+        for (int jj = 0; jj < 8; ++jj) {
+            if (jj < cur.width) {
+                int qj;
+                R xj;
+                if constexpr (G::TPR == 1) {
+                    qj = cur.q[jj];
+                    xj = cur.x[jj];
+                } else {
+                    const int src = row_lane0 + (jj % G::TPR);
+                    qj = __shfl_sync(0xffffffffu, cur.q[jj / G::TPR], src);
+                    xj = __shfl_sync(0xffffffffu, cur.x[jj / G::TPR], src);
+                }
+                xs[jj] = xj;
+                gq[jj] = ld_pack<R, FPT>(g + (size_t)qj * BPAD + fo);
+            }
+        }
+        ItemMeta<R, G::E> nm;
+        if (nxt < hi) load_meta<R, BPAD>(sv, s_begin, n_meshes, nxt, nm);
+        Pack<R, FPT> acc;
+#pragma unroll
+        for (int f = 0; f < FPT; ++f) acc.v[f] = cmk<C>(R(0), R(0));
+#pragma unroll
+        for (int jj = 0; jj < 8; ++jj)
+            if (jj < cur.width) {
+#pragma unroll
+                for (int f = 0; f < FPT; ++f) acc.v[f] = cfma(xs[jj], csub(gp.v[f], gq[jj].v[f]), acc.v[f]);
+            }
+        for (int j = 8; j < cur.width; ++j) {               // rare: slices wider than 8
+            const int qq = __ldg(m.col + cur.base + 32 * j);
+            const R xx = __ldg(m.xval + cur.base + 32 * j);
+            const Pack<R, FPT> gg = ld_pack<R, FPT>(g + (size_t)qq * BPAD + fo);
+#pragma unroll
+            for (int f = 0; f < FPT; ++f) acc.v[f] = cfma(xx, csub(gp.v[f], gg.v[f]), acc.v[f]);
+        }
+        if (live) {
+            Pack<R, FPT> out;
+#pragma unroll
+            for (int f = 0; f < FPT; ++f) {
+                // the lambda = 0 residual joins alpha*psi, where it is about one
+                // ulp; added to the full sum it would round away
+                C t = cmul(sc.alpha, ps.v[f]);
+                if (sc.flags & kFinal) t = cadd(t, cmul(sc.alpha_lo, ps.v[f]));
+                out.v[f] = cadd(t, cmul(sc.beta, csub(acc.v[f], gp.v[f])));
+            }
+            if (sc.flags & kHasH) {
+#pragma unroll
+                for (int f = 0; f < FPT; ++f) out.v[f] = csub(out.v[f], hh.v[f]);
+            }
+            if (sc.flags & kFinal) {
+                if (kerr_mode == 0) {
+                    R em, phi;
+                    diag_factors(__ldg(m.sigma + cur.row), h_post, em, phi);
+                    const R vv = __ldg(m.v + cur.row), cb = __ldg(m.chib + cur.row);
+#pragma unroll
+                    for (int f = 0; f < FPT; ++f) out.v[f] = diag_apply(out.v[f], vv, cb, h_post, em, phi);
+                    st_pack<R, FPT>(m.psi + own, out);
+                } else {
+                    // element-averaged Kerr needs the neighbours' |S|^2: park S in b[0]
+                    st_pack<R, FPT>(m.b[0] + own, out);
+                }
+            } else {
+                st_pack<R, FPT>(m.b[k % 3] + own, out);
+            }
+        }
+        cur = nm;
+        it = nxt;
     }
 }
 
@@ -389,27 +461,34 @@ __device__ __forceinline__ void for_my_items(const MarchParams<R> &P, const int3
     }
 }
 
-template <typename R, int FPT>
+template <typename R, int BPAD>
 __global__ void __launch_bounds__(256, DECBPM_MARCH_MINB) march_kernel(MarchParams<R> P) {
+    constexpr int FPT = Geo<R, BPAD>::FPT;
     __shared__ int32_t s_begin[kMaxMeshes + 1];
-    for (int i = threadIdx.x; i < P.n_meshes; i += blockDim.x) s_begin[i] = P.meshes[i].item_begin;
+    __shared__ MeshView<R> s_view[kMaxMeshes];
+    __shared__ StageCoef<R> s_coef[kMaxMeshes];
+    for (int i = threadIdx.x; i < P.n_meshes; i += blockDim.x) {
+        s_begin[i] = P.meshes[i].item_begin;
+        s_view[i] = P.meshes[i];
+    }
     __syncthreads();
     unsigned long long target = 0;
     const R h = P.h, hh = P.h * R(0.5);
+    const int bl = Geo<R, BPAD>::TPR_LOG2 + (FPT == 2 ? 1 : 0);
     for (int step = 0; step < P.n_steps; ++step) {
         if (step == 0 && P.pre_half) {
             if (P.kerr_mode == 0) {
                 for_my_items(P, s_begin, P.total_items, [&](const MeshView<R> &m, int li) {
-                    lumped_diag_item<R, FPT>(m, li, hh, P.bpad_log2);
+                    lumped_diag_item<R, FPT>(m, li, hh, bl);
                 });
                 if (!grid_barrier(P.barrier, target, P.status, P.timeout_ns)) return;
             } else {
                 for_my_items(P, s_begin, P.total_items, [&](const MeshView<R> &m, int li) {
-                    element_kerr_item<R, FPT>(m, li, hh, P.bpad_log2, m.psi, m.b[0]);
+                    element_kerr_item<R, FPT>(m, li, hh, bl, m.psi, m.b[0]);
                 });
                 if (!grid_barrier(P.barrier, target, P.status, P.timeout_ns)) return;
                 for_my_items(P, s_begin, P.total_items, [&](const MeshView<R> &m, int li) {
-                    copy_item<R, FPT>(m, li, P.bpad_log2, m.b[0], m.psi);
+                    copy_item<R, FPT>(m, li, bl, m.b[0], m.psi);
                 });
                 if (!grid_barrier(P.barrier, target, P.status, P.timeout_ns)) return;
             }
@@ -417,14 +496,15 @@ __global__ void __launch_bounds__(256, DECBPM_MARCH_MINB) march_kernel(MarchPara
         const R h_post = (step == P.n_steps - 1 && P.post_half) ? hh : h;
         for (int s = 0; s < P.S; ++s) {
             const int k = P.S - 1 - s;
-            for_my_items(P, s_begin, P.active_items[s], [&](const MeshView<R> &m, int li) {
-                clenshaw_item<R, FPT>(m, li, k, h_post, P.kerr_mode, P.bpad_log2);
-            });
+            for (int i = threadIdx.x; i < P.n_meshes; i += blockDim.x)
+                if (s_view[i].M > k) s_coef[i] = s_view[i].coef[k];
+            __syncthreads();
+            clenshaw_stage<R, BPAD>(s_view, s_coef, s_begin, P.n_meshes, P.active_items[s], k, h_post, P.kerr_mode);
             if (!grid_barrier(P.barrier, target, P.status, P.timeout_ns)) return;
         }
         if (P.kerr_mode != 0) {
             for_my_items(P, s_begin, P.total_items, [&](const MeshView<R> &m, int li) {
-                element_kerr_item<R, FPT>(m, li, h_post, P.bpad_log2, m.b[0], m.psi);
+                element_kerr_item<R, FPT>(m, li, h_post, bl, m.b[0], m.psi);
             });
             if (!grid_barrier(P.barrier, target, P.status, P.timeout_ns)) return;
         }

@@ -1,0 +1,55 @@
+"""Host-side logic of bench.py: the algorithmic-byte model, the replica
+sharding and the max-over-ranks timing reduction (world size 2, gloo, CPU)."""
+import os
+import socket
+
+import pytest
+import torch.multiprocessing as mp
+
+import bench
+
+
+def test_algorithmic_bytes_model():
+    info = {"n_vertices": 1000, "mean_degree": 6.0}
+    # M = 10, B = 16: per vertex-field 10 * (56/16 + 32) + 12/16 bytes
+    b = bench.algorithmic_bytes_per_step([info], [16], [10])
+    assert b == pytest.approx(1000 * 16 * (10 * (56 / 16 + 32) + 12 / 16))
+    # B = 1 single field: the operator is not amortized
+    assert bench.algorithmic_bytes_per_step([info], [1], [10]) == pytest.approx(1000 * (10 * (56 + 32) + 12))
+
+
+def test_replica_seeds_are_distinct():
+    assert len({bench.shard_seed(r) for r in range(8)}) == 8
+
+
+def _free_port():
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    port = s.getsockname()[1]
+    s.close()
+    return port
+
+
+def _worker(rank, world, port, out):
+    import torch.distributed as dist
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    vals = bench.max_over_ranks([1.0 + rank, 5.0 - rank, 3.0], world)
+    out[rank] = vals
+    dist.destroy_process_group()
+
+
+def test_max_over_ranks_gloo_two_ranks():
+    ctx = mp.get_context("spawn")
+    mgr = ctx.Manager()
+    out = mgr.dict()
+    port = _free_port()
+    procs = [ctx.Process(target=_worker, args=(r, 2, port, out)) for r in range(2)]
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(60)
+        assert p.exitcode == 0
+    assert out[0] == [2.0, 5.0, 3.0]
+    assert out[1] == [2.0, 5.0, 3.0]
+    assert bench.max_over_ranks([7.0], 1) == [7.0]
