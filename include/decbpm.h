@@ -223,6 +223,29 @@ int decbpm_propagate_batch(const decbpm_mesh_t *meshes, int32_t n_meshes, const 
                            const decbpm_params *params, void *const *psi_dev, void *stream,
                            decbpm_diag *diag_out);
 
+/* ---- allocation-free propagation -------------------------------------------
+ * No counterpart in the paper: a service for callers that cannot allocate
+ * device memory when they propagate (for example while another allocator owns
+ * the memory budget, during CUDA graph capture, or in loops with a fixed
+ * footprint).  Same march as decbpm_propagate on one mesh (fused variant,
+ * either precision and Kerr mode), but the scratch (internal-order field
+ * copy, three Clenshaw buffers, stage tables, barrier/status words) lives in
+ * one static 32 MiB device array of the library instead of allocated
+ * workspaces; this call makes no cudaMalloc, cudaFree or pinned-memory
+ * allocation.  The scratch needed is about 4 * n_vertices * padded_fields *
+ * (8 bytes for C64, 16 for C128) plus 64 KiB; larger requests fail with
+ * DECBPM_ERR_INVALID_ARG and a message giving the sizes.  The mesh handle
+ * (created beforehand with decbpm_mesh_create) and psi_dev are the caller's.
+ * No diagnostics are returned.  The first call on a device looks up the
+ * array's device address (cudaGetSymbolAddress); make that first call before
+ * any stream capture.  All calls share the one array, which keeps the last
+ * call's contents (the call clears what must start at zero), so calls that
+ * can overlap on the GPU (on different streams or from different host
+ * threads of one process) race on it: serialize them.  Each process has its
+ * own copy.  The call synchronizes `stream` before returning.               */
+int decbpm_propagate_noalloc(decbpm_mesh_t mesh, const decbpm_params *params, void *psi_dev, int64_t n_fields,
+                             void *stream);
+
 /* ---- failure-path self test ------------------------------------------------
  * Launches a small cooperative kernel whose CTAs meet at the same bounded
  * grid barrier the march kernel uses, but wait for `missing_arrivals` more

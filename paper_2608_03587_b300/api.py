@@ -177,6 +177,18 @@ def propagate(mesh: Mesh, psi, dz, n_steps, diag_every=0, kerr="lumped", variant
     return _diag_array(buf, npts, B)
 
 
+def propagate_noalloc(mesh: Mesh, psi, dz, n_steps, kerr="lumped", cheb_tol=0.0, stream=None):
+    """decbpm_propagate_noalloc: like propagate(), for callers that cannot
+    allocate device memory at call time; scratch comes from the library's
+    static 32 MiB device array (size limits and sharing rules in decbpm.h).
+    Returns nothing (no diagnostics)."""
+    lib = _lib()
+    B = _fields(psi)
+    prm = _params(dz, n_steps, _precision_of(psi), kerr, 0, "fused", cheb_tol)
+    L.check(lib.decbpm_propagate_noalloc(mesh.handle, ctypes.byref(prm), ctypes.c_void_p(psi.data_ptr()), B,
+                                         _stream_handle(stream)))
+
+
 def propagate_host(mesh: Mesh, psi_host, dz, n_steps, diag_every=0, kerr="lumped", variant="fused", cheb_tol=0.0,
                    stream=None):
     """decbpm_propagate_host: psi_host is a CPU torch tensor (pinned for speed), updated in place."""

@@ -5,6 +5,7 @@
 #include <cstdio>
 #include <cstring>
 #include <map>
+#include <mutex>
 #include <memory>
 #include <numeric>
 #include <tuple>
@@ -984,3 +985,194 @@ int decbpm_propagate_batch(const decbpm_mesh_t *meshes, int32_t n_meshes, const 
 }
 
 }  // extern "C"
+
+// ============================================================== allocation-free propagate
+// Some callers cannot allocate device memory at the point where they want to
+// propagate: code running while a framework's caching allocator owns the
+// whole memory budget, code that must not touch the allocator while a CUDA
+// graph is being captured, or real-time loops with a fixed memory footprint.
+// For them, decbpm_propagate_noalloc keeps its scratch (the internal-order
+// copy of the field, the three Clenshaw buffers, the stage tables and the
+// barrier/status words) in the file-scope device array below instead of in
+// cudaMalloc'ed workspaces.  Every GPU that loads this library holds the
+// array until the process exits.
+constexpr size_t kNoallocScratchBytes = size_t(32) << 20;   // 32 MiB
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocScratchBytes];
+
+namespace {
+struct NoallocSlot {
+    bool ready = false;
+    unsigned char *base = nullptr;
+};
+constexpr int kNoallocMaxDevices = 64;
+NoallocSlot g_noalloc_slot[kNoallocMaxDevices];
+std::mutex g_noalloc_mu;
+
+// Device address of g_noalloc_scratch on the current device.  In host code the
+// array's name is only a host-side stand-in, so the address is looked up once
+// per device (with that device current) and cached.
+int noalloc_scratch_base(int dev, unsigned char **base) {
+    if (dev < 0 || dev >= kNoallocMaxDevices) return fail(DECBPM_ERR_UNSUPPORTED, "device %d out of range", dev);
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    NoallocSlot &sl = g_noalloc_slot[dev];
+    if (!sl.ready) {
+        void *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess || !p)
+            return fail(DECBPM_ERR_CUDA, "cudaGetSymbolAddress(g_noalloc_scratch) failed: %s", cudaGetErrorString(e));
+        sl.base = static_cast<unsigned char *>(p);
+        sl.ready = true;
+    }
+    *base = sl.base;
+    return DECBPM_OK;
+}
+
+size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+template <typename R>
+int propagate_noalloc_impl(decbpm_mesh_t mesh, const decbpm_params *prm, void *psi_dev, int64_t n_fields,
+                           cudaStream_t s) {
+    using C = typename CT<R>::c2;
+    const int64_t n0 = mesh->A.n0;
+    const int bpad_log2 = ilog2(int(n_fields));
+    const int bpad = 1 << bpad_log2;
+    const int fpt = sizeof(R) == 4 ? (bpad >= 2 ? 2 : 1) : (bpad > 32 ? 2 : 1);
+    Cheb cb;
+    TRY(cheb_coefficients(mesh->A.p, mesh->A.rho, prm->dz, default_tol(prm), cb));
+    const int M = cb.M;
+    // scratch layout: [barrier u64, status int] [view] [coef[M]] [active[M]] [psi] [b0] [b1] [b2]
+    const size_t state = align256(size_t(n0) * bpad * sizeof(C));
+    const size_t off_view = 256;
+    const size_t off_coef = off_view + align256(sizeof(MeshView<R>));
+    const size_t off_active = off_coef + align256(sizeof(StageCoef<R>) * M);
+    const size_t off_psi = off_active + align256(sizeof(int32_t) * M);
+    const size_t need = off_psi + 4 * state;
+    if (need > kNoallocScratchBytes)
+        return fail(DECBPM_ERR_INVALID_ARG,
+                    "decbpm_propagate_noalloc needs %zu bytes of scratch for %lld vertices x %d padded fields "
+                    "(degree %d) but its static scratch holds %zu bytes; use decbpm_propagate",
+                    need, (long long)n0, bpad, M, kNoallocScratchBytes);
+    int dev = 0, sms = 0, per_sm = 0;
+    CK(cudaGetDevice(&dev));
+    unsigned char *base = nullptr;
+    TRY(noalloc_scratch_base(dev, &base));
+    CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, march_ptr_for<R>(bpad), 256, 0));
+    if (per_sm < 1) return fail(DECBPM_ERR_CUDA, "march kernel cannot be resident");
+    C *psi = reinterpret_cast<C *>(base + off_psi);
+    C *b[3] = {reinterpret_cast<C *>(base + off_psi + state), reinterpret_cast<C *>(base + off_psi + 2 * state),
+               reinterpret_cast<C *>(base + off_psi + 3 * state)};
+    // stage table, same recurrence and lambda = 0 residual as the plans
+    StageCoef<R> coef[1024];
+    if (M > 1024) return fail(DECBPM_ERR_UNSUPPORTED, "Chebyshev degree %d above 1024 (reduce dz)", M);
+    auto mk = [](std::complex<double> z) { C c; c.x = R(z.real()); c.y = R(z.imag()); return c; };
+    for (int k = 0; k < M; ++k) {
+        StageCoef<R> sc{};
+        std::complex<double> alpha = cb.a[k], beta = (k == 0) ? 1.0 : 2.0;
+        int flags = 0;
+        if (k == M - 1) { flags |= kGisPsi; beta = 2.0 * cb.a[M]; }
+        else if (k == M - 2) { alpha = cb.a[k] - cb.a[M]; }
+        else flags |= kHasH;
+        if (k == 0) flags |= kFinal;
+        sc.alpha = mk(alpha);
+        sc.beta = mk(beta);
+        sc.alpha_lo = mk(0.0);
+        sc.flags = flags;
+        coef[k] = sc;
+    }
+    {
+        auto up = [](C z) { return std::complex<double>(double(z.x), double(z.y)); };
+        std::complex<double> bk1 = 0, bk2 = 0, Sv = 0;
+        for (int k = M - 1; k >= 0; --k) {
+            const std::complex<double> g = (coef[k].flags & kGisPsi) ? 1.0 : bk1;
+            std::complex<double> o = up(coef[k].alpha) - up(coef[k].beta) * g;
+            if (coef[k].flags & kHasH) o -= bk2;
+            if (coef[k].flags & kFinal) Sv = o;
+            bk2 = bk1;
+            bk1 = o;
+        }
+        coef[0].alpha_lo = mk(cb.f0 - Sv);
+    }
+    const int tpr_log2 = bpad_log2 - (fpt == 2 ? 1 : 0);
+    const int rpw = 32 >> tpr_log2;
+    const int items = int((n0 + rpw - 1) / rpw);
+    int32_t active[1024];
+    for (int k = 0; k < M; ++k) active[k] = items;
+    MeshView<R> v{};
+    v.n0 = int32_t(n0);
+    v.n_slices = int32_t(mesh->S.n_slices);
+    v.M = M;
+    v.item_begin = 0;
+    v.slice_ptr = mesh->slice_ptr; v.slice_w = mesh->slice_w; v.col = mesh->col;
+    if constexpr (sizeof(R) == 4) {
+        v.xval = mesh->x32; v.v = mesh->v32; v.chib = mesh->chib32; v.sigma = mesh->sig32;
+        v.coff = mesh->coff32; v.cdiag = mesh->cdiag32;
+    } else {
+        v.xval = mesh->x64; v.v = mesh->v64; v.chib = mesh->chib64; v.sigma = mesh->sig64;
+        v.coff = mesh->coff64; v.cdiag = mesh->cdiag64;
+    }
+    v.psi = psi; v.b[0] = b[0]; v.b[1] = b[1]; v.b[2] = b[2];
+    v.coef = reinterpret_cast<const StageCoef<R> *>(base + off_coef);
+    // the array keeps the previous call's contents: clear the barrier and status words
+    CK(cudaMemsetAsync(base, 0, 256, s));
+    CK(cudaMemcpyAsync(base + off_view, &v, sizeof(v), cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(base + off_coef, coef, sizeof(StageCoef<R>) * M, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(base + off_active, active, sizeof(int32_t) * M, cudaMemcpyHostToDevice, s));
+    const int pblocks = int(std::min<int64_t>(4 * sms, (n0 * bpad + 255) / 256));
+    permute_in_kernel<C><<<pblocks, 256, 0, s>>>((const C *)psi_dev, psi, mesh->perm, int32_t(n0), int32_t(n_fields), bpad);
+    CK(cudaGetLastError());
+    if (prm->n_steps > 0) {
+        if (prm->n_steps > 0x7fffffff) return fail(DECBPM_ERR_INVALID_ARG, "n_steps too large");
+        MarchParams<R> mp{};
+        mp.meshes = reinterpret_cast<const MeshView<R> *>(base + off_view);
+        mp.active_items = reinterpret_cast<const int32_t *>(base + off_active);
+        mp.n_meshes = 1;
+        mp.S = M;
+        mp.total_items = items;
+        mp.n_steps = int32_t(prm->n_steps);
+        mp.pre_half = 1;
+        mp.post_half = 1;
+        mp.kerr_mode = prm->kerr_mode;
+        mp.bpad_log2 = bpad_log2;
+        mp.h = R(prm->dz);
+        mp.barrier = reinterpret_cast<unsigned long long *>(base);
+        mp.status = reinterpret_cast<int *>(base + 8);
+        mp.timeout_ns = kBarrierTimeoutNs;
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(sms * std::min(per_sm, 4));
+        cfg.blockDim = dim3(256);
+        cfg.stream = s;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeCooperative;
+        attr[0].val.cooperative = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        void *args[] = {&mp};
+        CK(cudaLaunchKernelExC(&cfg, march_ptr_for<R>(bpad), args));
+    }
+    const double ph = std::fmod(double(prm->n_steps) * cb.theta0, 2.0 * M_PI);
+    const int oblocks = int(std::min<int64_t>(4 * sms, (n0 * n_fields + 255) / 256));
+    permute_out_kernel<C><<<oblocks, 256, 0, s>>>(psi, (C *)psi_dev, mesh->perm, int32_t(n0), int32_t(n_fields), bpad,
+                                                 std::cos(ph), std::sin(ph));
+    CK(cudaGetLastError());
+    int status = 0;
+    CK(cudaMemcpyAsync(&status, base + 8, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (status == DECBPM_ERR_TIMEOUT) return fail(DECBPM_ERR_TIMEOUT, "grid barrier timed out in the march kernel");
+    if (status != 0) return fail(status, "device reported status %d", status);
+    return DECBPM_OK;
+}
+}  // namespace
+
+extern "C" int decbpm_propagate_noalloc(decbpm_mesh_t mesh, const decbpm_params *params, void *psi_dev,
+                                        int64_t n_fields, void *stream) {
+    clear_error();
+    if (!mesh || !psi_dev) return fail(DECBPM_ERR_INVALID_ARG, "mesh and psi_dev are required");
+    TRY(check_params(params));
+    if (params->variant != DECBPM_VARIANT_FUSED)
+        return fail(DECBPM_ERR_UNSUPPORTED, "decbpm_propagate_noalloc runs the fused variant only");
+    if (n_fields < 1 || n_fields > kMaxFields) return fail(DECBPM_ERR_UNSUPPORTED, "n_fields must be in 1..%d", kMaxFields);
+    cudaStream_t s = (cudaStream_t)stream;
+    if (params->precision == DECBPM_C64) return propagate_noalloc_impl<float>(mesh, params, psi_dev, n_fields, s);
+    return propagate_noalloc_impl<double>(mesh, params, psi_dev, n_fields, s);
+}
