@@ -40,7 +40,7 @@ class MeshDesc(ctypes.Structure):
     _fields_ = [("dim", ctypes.c_int32), ("n_vertices", ctypes.c_int64), ("n_cells", ctypes.c_int64),
                 ("coords", _c_double_p), ("cells", _c_int32_p), ("V_cell", _c_double_p),
                 ("chi_cell", _c_double_p), ("sigma_vertex", _c_double_p), ("p_n", _c_double_p),
-                ("n_p", ctypes.c_int32), ("ordering", ctypes.c_int32)]
+                ("n_p", ctypes.c_int32), ("ordering", ctypes.c_int32), ("spectral_bound", ctypes.c_int32)]
 
 
 class MeshInfo(ctypes.Structure):

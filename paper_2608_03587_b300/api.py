@@ -28,9 +28,10 @@ def _iptr(a):
 
 
 _ORDERS = {"default": 0, "rcm": 1, "hilbert": 2}
+_BOUNDS = {"default": 0, "lanczos": 1, "gershgorin": 2}
 
 
-def _desc(coords, cells, V_cell=None, chi_cell=None, sigma=None, p=(1.0,), ordering="default"):
+def _desc(coords, cells, V_cell=None, chi_cell=None, sigma=None, p=(1.0,), ordering="default", bound="default"):
     coords = np.ascontiguousarray(coords, dtype=np.float64)
     if coords.ndim == 1:
         coords = coords.reshape(-1, 1)
@@ -42,7 +43,8 @@ def _desc(coords, cells, V_cell=None, chi_cell=None, sigma=None, p=(1.0,), order
     keep = (coords, cells, V_cell, chi_cell, sigma, p)
     d = L.MeshDesc(dim=coords.shape[1], n_vertices=coords.shape[0], n_cells=cells.shape[0],
                    coords=_dptr(coords), cells=_iptr(cells), V_cell=_dptr(V_cell), chi_cell=_dptr(chi_cell),
-                   sigma_vertex=_dptr(sigma), p_n=_dptr(p), n_p=len(p), ordering=_ORDERS[ordering])
+                   sigma_vertex=_dptr(sigma), p_n=_dptr(p), n_p=len(p), ordering=_ORDERS[ordering],
+                   spectral_bound=_BOUNDS[bound])
     return d, keep
 
 
@@ -84,10 +86,11 @@ def _stream_handle(stream):
 
 
 # ---------------------------------------------------------------- host-only
-def assemble_host(coords, cells, V_cell=None, chi_cell=None, sigma=None, p=(1.0,), ordering="default"):
+def assemble_host(coords, cells, V_cell=None, chi_cell=None, sigma=None, p=(1.0,), ordering="default",
+                  bound="default"):
     """decbpm_assemble_host: FP64 operators in caller order (no GPU needed)."""
     lib = _lib()
-    d, keep = _desc(coords, cells, V_cell, chi_cell, sigma, p, ordering)
+    d, keep = _desc(coords, cells, V_cell, chi_cell, sigma, p, ordering, bound)
     info = L.MeshInfo()
     L.check(lib.decbpm_assemble_host(ctypes.byref(d), ctypes.byref(info), None, None, None, None, None, None, None))
     n0, nnz = info.n_vertices, info.nnz_offdiag + info.n_vertices
@@ -119,9 +122,10 @@ class Mesh:
     """A mesh handle (decbpm_mesh_create): operators assembled in FP64 and
     uploaded to the current CUDA device."""
 
-    def __init__(self, coords, cells, V_cell=None, chi_cell=None, sigma=None, p=(1.0,), ordering="default"):
+    def __init__(self, coords, cells, V_cell=None, chi_cell=None, sigma=None, p=(1.0,), ordering="default",
+                 bound="default"):
         lib = _lib()
-        d, keep = _desc(coords, cells, V_cell, chi_cell, sigma, p, ordering)
+        d, keep = _desc(coords, cells, V_cell, chi_cell, sigma, p, ordering, bound)
         h = ctypes.c_void_p()
         L.check(lib.decbpm_mesh_create(ctypes.byref(d), ctypes.byref(h)))
         del keep
@@ -129,8 +133,8 @@ class Mesh:
         self.n_vertices = int(np.asarray(coords).shape[0])
 
     @classmethod
-    def from_workload(cls, m, p=(1.0,), ordering="default"):
-        return cls(m.coords, m.cells, m.V_cell, m.chi_cell, m.sigma, p, ordering)
+    def from_workload(cls, m, p=(1.0,), ordering="default", bound="default"):
+        return cls(m.coords, m.cells, m.V_cell, m.chi_cell, m.sigma, p, ordering, bound)
 
     @property
     def handle(self):
@@ -153,8 +157,9 @@ class Mesh:
             pass
 
 
-def mesh_create(coords, cells, V_cell=None, chi_cell=None, sigma=None, p=(1.0,), ordering="default") -> Mesh:
-    return Mesh(coords, cells, V_cell, chi_cell, sigma, p, ordering)
+def mesh_create(coords, cells, V_cell=None, chi_cell=None, sigma=None, p=(1.0,), ordering="default",
+                bound="default") -> Mesh:
+    return Mesh(coords, cells, V_cell, chi_cell, sigma, p, ordering, bound)
 
 
 def _fields(psi):

@@ -159,6 +159,82 @@ static void hilbert_order(const double *X, int dim, int64_t n, std::vector<int32
     for (int64_t i = 0; i < n; ++i) perm[i] = key[i].second;
 }
 
+// Largest eigenvalue of the symmetric tridiagonal matrix (diag a, off b) by
+// bisection on the Sturm count.
+static double tridiag_max_eig(const std::vector<double> &a, const std::vector<double> &b) {
+    const int k = int(a.size());
+    double lo = 1e300, hi = -1e300;
+    for (int i = 0; i < k; ++i) {
+        const double r = (i > 0 ? std::fabs(b[i - 1]) : 0.0) + (i + 1 < k ? std::fabs(b[i]) : 0.0);
+        lo = std::min(lo, a[i] - r);
+        hi = std::max(hi, a[i] + r);
+    }
+    auto count_above = [&](double x) {      // eigenvalues > x
+        int neg = 0;
+        double q = a[0] - x;
+        if (q < 0) ++neg;
+        for (int i = 1; i < k; ++i) {
+            const double qq = q == 0.0 ? 1e-300 : q;
+            q = a[i] - x - b[i - 1] * b[i - 1] / qq;
+            if (q < 0) ++neg;
+        }
+        return k - neg;
+    };
+    for (int it = 0; it < 200 && hi - lo > 1e-14 * std::max(1.0, std::fabs(hi)); ++it) {
+        const double mid = 0.5 * (lo + hi);
+        if (count_above(mid) >= 1) lo = mid;
+        else hi = mid;
+    }
+    return hi;
+}
+
+// Lanczos estimate of lambda_max(*0^{-1} K) = lambda_max(S), S = *0^{-1/2} K *0^{-1/2}
+// symmetric, from a fixed pseudo-random start (no reorthogonalization: the
+// largest Ritz value still converges to lambda_max from below).
+static double lanczos_lambda_max(const Assembly &A, int steps) {
+    const int64_t n = A.n0;
+    std::vector<double> isq(n), v(n), vprev(n, 0.0), w(n), tmp(n);
+    for (int64_t i = 0; i < n; ++i) isq[i] = 1.0 / std::sqrt(A.m[i]);
+    uint64_t st = 0x9E3779B97F4A7C15ull;
+    double nrm = 0.0;
+    for (int64_t i = 0; i < n; ++i) {
+        st ^= st << 13; st ^= st >> 7; st ^= st << 17;                  // xorshift64
+        v[i] = double(st >> 11) * (1.0 / 9007199254740992.0) - 0.5;
+        nrm += v[i] * v[i];
+    }
+    nrm = std::sqrt(nrm);
+    for (auto &x : v) x /= nrm;
+    std::vector<double> alpha, beta;
+    double bprev = 0.0;
+    const int k = int(std::min<int64_t>(steps, n));
+    for (int j = 0; j < k; ++j) {
+        for (int64_t i = 0; i < n; ++i) tmp[i] = isq[i] * v[i];
+        for (int64_t p = 0; p < n; ++p) {                               // w = S v
+            double acc = A.wsum[p] * tmp[p];
+            for (int64_t e = A.rowptr[p]; e < A.rowptr[p + 1]; ++e) acc -= A.w[e] * tmp[A.col[e]];
+            w[p] = isq[p] * acc;
+        }
+        double a = 0.0;
+        for (int64_t i = 0; i < n; ++i) a += w[i] * v[i];
+        double b = 0.0;
+        for (int64_t i = 0; i < n; ++i) {
+            w[i] -= a * v[i] + bprev * vprev[i];
+            b += w[i] * w[i];
+        }
+        b = std::sqrt(b);
+        alpha.push_back(a);
+        if (j + 1 == k || b < 1e-300) break;
+        beta.push_back(b);
+        for (int64_t i = 0; i < n; ++i) {
+            vprev[i] = v[i];
+            v[i] = w[i] / b;
+        }
+        bprev = b;
+    }
+    beta.resize(alpha.size() > 0 ? alpha.size() - 1 : 0);
+    return tridiag_max_eig(alpha, beta);
+}
+
 int assemble(const decbpm_mesh_desc *d, Assembly &A) {
     if (!d) return fail(DECBPM_ERR_INVALID_ARG, "mesh description is NULL");
     if (d->dim != 1 && d->dim != 2) return fail(DECBPM_ERR_INVALID_ARG, "dim must be 1 or 2 (got %d)", d->dim);
@@ -197,6 +273,10 @@ int assemble(const decbpm_mesh_desc *d, Assembly &A) {
     recs.reserve(size_t(nc) * (dim == 2 ? 3 : 1));
     const double *X = d->coords;
     double area = 0.0;
+    // element eigenvalue bound: with K = sum_t K_t and *0 = sum_t M_t (M_t the
+    // lumped element mass |t|/(d+1) on each vertex of t),
+    // x^T K x = sum_t x_t^T K_t x_t <= max_t lambda_max(K_t, M_t) x^T *0 x.
+    double rho_elem = 0.0;
     for (int64_t t = 0; t < nc; ++t) {
         const int32_t *c = d->cells + t * kv;
         const double Vt = d->V_cell ? d->V_cell[t] : 0.0;
@@ -206,6 +286,7 @@ int assemble(const decbpm_mesh_desc *d, Assembly &A) {
             meas = std::fabs(X[c[1]] - X[c[0]]);
             if (!(meas > 0)) return fail(DECBPM_ERR_BAD_MESH, "degenerate segment %lld", (long long)t);
             recs.push_back({std::min<int64_t>(c[0], c[1]), std::max<int64_t>(c[0], c[1]), 1.0 / meas, chit * meas});
+            rho_elem = std::max(rho_elem, 4.0 / (meas * meas));      // K_e = [1 -1; -1 1]/L, M_e = L/2
         } else {
             const double *p0 = X + 2 * c[0], *p1 = X + 2 * c[1], *p2 = X + 2 * c[2];
             const double cross = (p1[0] - p0[0]) * (p2[1] - p0[1]) - (p1[1] - p0[1]) * (p2[0] - p0[0]);
@@ -213,6 +294,7 @@ int assemble(const decbpm_mesh_desc *d, Assembly &A) {
                 return fail(DECBPM_ERR_BAD_MESH, "triangle %lld is %s (cells must be counter-clockwise)",
                             (long long)t, cross < 0 ? "clockwise" : "degenerate");
             meas = 0.5 * cross;
+            double wsum_t = 0.0, wprod_t = 0.0, wopp[3];
             for (int i = 0; i < 3; ++i) {
                 const int32_t vi = c[i], vj = c[(i + 1) % 3], vk = c[(i + 2) % 3];
                 const double *pi = X + 2 * vi, *pj = X + 2 * vj, *pk = X + 2 * vk;
@@ -220,7 +302,14 @@ int assemble(const decbpm_mesh_desc *d, Assembly &A) {
                 const double wx = pk[0] - pi[0], wy = pk[1] - pi[1];
                 const double cot = (ux * wx + uy * wy) / cross;   // |u x w| = cross for CCW
                 recs.push_back({std::min<int64_t>(vj, vk), std::max<int64_t>(vj, vk), 0.5 * cot, chit * meas});
+                wopp[i] = 0.5 * cot;
+                wsum_t += 0.5 * cot;
             }
+            // K_t has zero row sums and off-diagonals -w: its nonzero eigenvalues are
+            // s +- sqrt(s^2 - 3 (w0 w1 + w1 w2 + w2 w0)), s = w0 + w1 + w2; M_t = |t|/3 I
+            wprod_t = wopp[0] * wopp[1] + wopp[1] * wopp[2] + wopp[2] * wopp[0];
+            const double disc = std::max(0.0, wsum_t * wsum_t - 3.0 * wprod_t);
+            rho_elem = std::max(rho_elem, (wsum_t + std::sqrt(disc)) * 3.0 / meas);
         }
         area += meas;
         for (int i = 0; i < kv; ++i) {
@@ -296,7 +385,20 @@ int assemble(const decbpm_mesh_desc *d, Assembly &A) {
         // A_pp = sum_q w_pq / m_p, R_p = sum_q |w_pq| / m_p
         rho = std::max(rho, (ws + wabs) / A.m[p]);
     }
-    A.rho = 1.01 * rho;
+    // Gershgorin and the element bound are rigorous; the margin covers rounding
+    A.rho_gershgorin = rho;
+    A.rho_element = rho_elem;
+    A.rho = (1.0 + 1e-6) * std::min(rho, rho_elem);
+    if (d->spectral_bound == DECBPM_BOUND_DEFAULT || d->spectral_bound == DECBPM_BOUND_LANCZOS) {
+        // Kuczynski-Wozniakowski: for k Lanczos steps from a random start,
+        // P(lambda_max > theta_k / (1 - eps)) <= 1.648 sqrt(n) exp(-sqrt(eps) (2k - 1)).
+        // k = 200, 1 / (1 - eps) = 1.01 gives < 1e-12 for n < 2^30.
+        const double theta = lanczos_lambda_max(A, 200);
+        A.rho_lanczos = theta;
+        if (theta > 0) A.rho = std::min(A.rho, 1.01 * theta);
+    } else if (d->spectral_bound != DECBPM_BOUND_GERSHGORIN) {
+        return fail(DECBPM_ERR_INVALID_ARG, "unknown spectral_bound %d", d->spectral_bound);
+    }
     A.v.resize(n0); A.chib.resize(n0); A.c_diag.resize(n0);
     for (int64_t p = 0; p < n0; ++p) {
         A.v[p] = mV[p] / A.m[p];

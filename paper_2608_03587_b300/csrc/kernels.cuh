@@ -21,6 +21,16 @@ namespace decbpm {
 #define DECBPM_MARCH_MINB 2     // CTAs of 256 threads per SM the march kernel is compiled for
 #endif
 
+#ifndef DECBPM_REVERSE_ODD
+#define DECBPM_REVERSE_ODD 1    // odd stages walk the CTA's items backwards (L2 reuse between stages)
+#endif
+#ifndef DECBPM_HINTS
+#define DECBPM_HINTS 0          // cache hints: b_{k+2} read as last use, psi bypasses L1
+#endif
+#ifndef DECBPM_PREFETCH
+#define DECBPM_PREFETCH 0       // L2 prefetch of the own rows this many items ahead (0 = off)
+#endif
+
 constexpr int kMaxMeshes = 64;
 constexpr int kMaxFields = 64;
 constexpr long long kBarrierTimeoutNs = 4000000000LL;   // default limit of one barrier wait: 4 s
@@ -69,6 +79,31 @@ __device__ __forceinline__ Pack<R, FPT> ld_pack(const typename CT<R>::c2 *p) {
         for (int i = 0; i < PackRaw<R, FPT>::kBytes / 16; ++i) t.u[i] = q[i];
     }
     return t.p;
+}
+
+// Loads with a cache policy: kLastUse for data dead after this read (the
+// b_{k+2} operand), kL2Only for data re-read next stage but not gathered (psi).
+enum : int { kLdDefault = 0, kLdLastUse = 1, kLdL2Only = 2 };
+template <typename R, int FPT, int POLICY>
+__device__ __forceinline__ Pack<R, FPT> ld_pack_hint(const typename CT<R>::c2 *p) {
+    if constexpr (POLICY == kLdDefault || !DECBPM_HINTS) {
+        return ld_pack<R, FPT>(p);
+    } else {
+        PackRaw<R, FPT> t;
+        if constexpr (PackRaw<R, FPT>::kBytes == 8) {
+            t.f2 = POLICY == kLdLastUse ? __ldlu(reinterpret_cast<const float2 *>(p))
+                                        : __ldcg(reinterpret_cast<const float2 *>(p));
+        } else {
+            const uint4 *q = reinterpret_cast<const uint4 *>(p);
+#pragma unroll
+            for (int i = 0; i < PackRaw<R, FPT>::kBytes / 16; ++i) t.u[i] = POLICY == kLdLastUse ? __ldlu(q + i) : __ldcg(q + i);
+        }
+        return t.p;
+    }
+}
+
+__device__ __forceinline__ void prefetch_l2(const void *p) {
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
 }
 
 template <typename R, int FPT>
@@ -280,11 +315,16 @@ __device__ __forceinline__ void clenshaw_stage(const MeshView<R> *sv, const Stag
     const int hi = int((long long)n_active * (blockIdx.x + 1) / gridDim.x);
     const int fo = (lane & (G::TPR - 1)) * FPT;
     const int row_lane0 = lane & ~(G::TPR - 1);
-    int it = lo + warp;
+    // items of this CTA in walk order: forward on even stages, backward on odd
+    // ones, so a stage starts on the rows the previous stage wrote last
+    const bool rev = DECBPM_REVERSE_ODD && (k & 1);
+    const int n_mine = hi - lo;
+    auto item_at = [&](int i) { return rev ? hi - 1 - i : lo + i; };
+    int idx = warp;
     ItemMeta<R, G::E> cur;
-    if (it < hi) load_meta<R, BPAD>(sv, s_begin, n_meshes, it, cur);
-    while (it < hi) {
-        const int nxt = it + nwarps;
+    if (idx < n_mine) load_meta<R, BPAD>(sv, s_begin, n_meshes, item_at(idx), cur);
+    while (idx < n_mine) {
+        const int nidx = idx + nwarps;
         const MeshView<R> &m = sv[cur.mi];
         const StageCoef<R> sc = scoef[cur.mi];
         const C *g = (sc.flags & kGisPsi) ? m.psi : m.b[(k + 1) % 3];
@@ -293,8 +333,18 @@ __device__ __forceinline__ void clenshaw_stage(const MeshView<R> *sv, const Stag
         Pack<R, FPT> gp, ps, hh;
         if (live) {
             gp = ld_pack<R, FPT>(g + own);
-            ps = ld_pack<R, FPT>(m.psi + own);
-            if (sc.flags & kHasH) hh = ld_pack<R, FPT>(m.b[(k + 2) % 3] + own);
+            ps = ld_pack_hint<R, FPT, kLdL2Only>(m.psi + own);
+            if (sc.flags & kHasH) hh = ld_pack_hint<R, FPT, kLdLastUse>(m.b[(k + 2) % 3] + own);
+        }
+        if (DECBPM_PREFETCH > 0 && idx + DECBPM_PREFETCH * nwarps < n_mine) {
+            // own rows of a later item of the same mesh (a guess across mesh edges is harmless)
+            const int pr = cur.row + (rev ? -1 : 1) * DECBPM_PREFETCH * nwarps * G::RPW;
+            if (pr >= 0 && pr < m.n0) {
+                const size_t po = (size_t)pr * BPAD + fo;
+                prefetch_l2(m.psi + po);
+                prefetch_l2(g + po);
+                if (sc.flags & kHasH) prefetch_l2(m.b[(k + 2) % 3] + po);
+            }
         }
         Pack<R, FPT> gq[8];
         R xs[8];
@@ -316,7 +366,7 @@ __device__ __forceinline__ void clenshaw_stage(const MeshView<R> *sv, const Stag
             }
         }
         ItemMeta<R, G::E> nm;
-        if (nxt < hi) load_meta<R, BPAD>(sv, s_begin, n_meshes, nxt, nm);
+        if (nidx < n_mine) load_meta<R, BPAD>(sv, s_begin, n_meshes, item_at(nidx), nm);
         Pack<R, FPT> acc;
 #pragma unroll
         for (int f = 0; f < FPT; ++f) acc.v[f] = cmk<C>(R(0), R(0));
@@ -364,7 +414,7 @@ __device__ __forceinline__ void clenshaw_stage(const MeshView<R> *sv, const Stag
             }
         }
         cur = nm;
-        it = nxt;
+        idx = nidx;
     }
 }
 

@@ -76,6 +76,27 @@ def test_host_assembly_matches_oracle(fiber):
     assert np.mean(span < 256) > 0.8
 
 
+@pytest.mark.parametrize("n", [300, 6000])
+def test_spectral_bounds_contain_the_spectrum(n):
+    """rho must bound lambda_max(*0^{-1} K) from above (the Chebyshev series
+    diverges outside its interval): the Lanczos-certified default within 1%
+    above it, the deterministic Gershgorin / element bound anywhere above."""
+    coords, tris = W.mesh_disk_graded(4.0, n, 3.0, interfaces=(1.0,), seed=n, grade_from=1.0)
+    ops = dec.Operators(coords, tris)
+    lam = spla.eigsh(ops.K, k=1, M=sp.diags(ops.H0), which="LA", return_eigenvectors=False)[0]
+    rho = api.assemble_host(coords, tris)["info"]["rho"]
+    rho_g = api.assemble_host(coords, tris, bound="gershgorin")["info"]["rho"]
+    assert lam <= rho <= 1.0101 * lam
+    assert lam <= rho_g
+    assert rho_g == pytest.approx(min(rho_g, ops.rho * (1 + 1e-6)), rel=1e-12)   # never above Gershgorin
+    # 1D: the element bound 4/L_min^2 and the exact spectrum
+    x, cells = W.mesh_1d_jittered(200, seed=5)
+    o1 = dec.Operators(x, cells)
+    lam1 = np.linalg.eigvals(o1.A.toarray()).real.max()
+    r1 = api.assemble_host(x, cells)["info"]["rho"]
+    assert lam1 <= r1 <= 1.0101 * lam1
+
+
 def test_host_assembly_1d(fiber):
     x, cells = W.mesh_1d_jittered(300, seed=2)
     a = api.assemble_host(x, cells, p=(0.5,))
