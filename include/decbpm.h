@@ -232,6 +232,26 @@ int decbpm_plan_get_config(decbpm_plan_t plan, decbpm_plan_config *cfg);
  * most recent decbpm_plan_propagate call (one launch when diag_every = 0). */
 int decbpm_plan_last_march_ms(decbpm_plan_t plan, double *ms);
 
+/* ---- potential and adjoint --------------------------------------------------
+ * Replace the per-vertex potential v_p used by the diagonal flow (host array
+ * in caller order; NULL restores the lumped *0^{-1} *0(V) 1 of the mesh).  A
+ * per-vertex refractive-index perturbation enters as dv_p = (k0 L)^2 d(n^2)_p. */
+int decbpm_mesh_set_potential(decbpm_mesh_t mesh, const double *v_vertex);
+
+/* Vector-Jacobian product of the whole march psi_N = (D_{h/2} E_h D_{h/2})^N psi_0
+ * (lumped Kerr, fused variant) for n_fields fields on one mesh:
+ *   gN_dev         [n_vertices * n_fields] Euclidean cotangent of psi_N (dJ = Re sum conj(gN) dpsi_N),
+ *   grad_psi0_dev  out: dJ/dpsi_0 in the same convention (the gradient torch uses for complex inputs),
+ *   grad_v_dev     out (may be NULL): FP64 [n_vertices] dJ/dv_p for the per-vertex potential,
+ *   psiN_dev       out (may be NULL): the forward result.
+ * The E-step adjoint in the *0 inner product is E_{-h} (same Chebyshev kernel,
+ * conjugate coefficients); the diagonal-flow adjoint is its real-pair
+ * linearization.  Memory: checkpoints every checkpoint_every steps (0 =
+ * ceil(sqrt(n_steps))) plus one segment of states are kept on the device.     */
+int decbpm_vjp(decbpm_mesh_t mesh, const decbpm_params *params, const void *psi0_dev, const void *gN_dev,
+               void *psiN_dev, void *grad_psi0_dev, double *grad_v_dev, int64_t n_fields, int32_t checkpoint_every,
+               void *stream);
+
 /* One-shot convenience: plan_create + plan_propagate + plan_destroy. */
 int decbpm_propagate_batch(const decbpm_mesh_t *meshes, int32_t n_meshes, const int32_t *fields_per_mesh,
                            const decbpm_params *params, void *const *psi_dev, void *stream,

@@ -100,6 +100,8 @@ SIGNATURES = {
     "decbpm_plan_get_config": (_i32, [_vp, ctypes.POINTER(PlanConfig)]),
     "decbpm_plan_last_march_ms": (_i32, [_vp, ctypes.POINTER(ctypes.c_double)]),
     "decbpm_selftest_barrier": (_i32, [_i32, _i64, _vp]),
+    "decbpm_mesh_set_potential": (_i32, [_vp, _c_double_p]),
+    "decbpm_vjp": (_i32, [_vp, ctypes.POINTER(Params), _vp, _vp, _vp, _vp, _vp, _i64, _i32, _vp]),
     "decbpm_propagate_noalloc": (_i32, [_vp, ctypes.POINTER(Params), _vp, _i64, _vp]),
     "decbpm_propagate_batch": (_i32, [ctypes.POINTER(_vp), _i32, _c_int32_p, ctypes.POINTER(Params),
                                       ctypes.POINTER(_vp), _vp, ctypes.POINTER(Diag)]),

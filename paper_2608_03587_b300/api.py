@@ -131,6 +131,8 @@ class Mesh:
         del keep
         self._h = h
         self.n_vertices = int(np.asarray(coords).shape[0])
+        self._inputs = (coords, cells, V_cell, chi_cell, sigma, p)
+        self._v_base = None
 
     @classmethod
     def from_workload(cls, m, p=(1.0,), ordering="default", bound="default"):
@@ -282,3 +284,71 @@ def plan_create(meshes, fields_per_mesh, precision="c64") -> Plan:
 def selftest_barrier(missing_arrivals: int, timeout_ns: int, stream=None) -> int:
     """decbpm_selftest_barrier: returns the status code (no exception)."""
     return int(_lib().decbpm_selftest_barrier(int(missing_arrivals), int(timeout_ns), _stream_handle(stream)))
+
+
+# ---------------------------------------------------------------- adjoint
+def set_potential(mesh: Mesh, v_vertex=None):
+    """decbpm_mesh_set_potential: per-vertex potential v_p (numpy, caller
+    order) used by the diagonal flow; None restores the mesh's own."""
+    v = None if v_vertex is None else np.ascontiguousarray(v_vertex, dtype=np.float64)
+    L.check(_lib().decbpm_mesh_set_potential(mesh.handle, _dptr(v)))
+
+
+def vjp(mesh: Mesh, psi0, gN, dz, n_steps, checkpoint_every=0, want_grad_v=True, stream=None):
+    """decbpm_vjp: (psi_N, dJ/dpsi_0, dJ/dv) for a terminal cotangent gN
+    (torch CUDA tensors like psi0; gradients in torch's complex convention)."""
+    import torch
+    lib = _lib()
+    B = _fields(psi0)
+    prm = _params(dz, n_steps, _precision_of(psi0))
+    gN = gN.contiguous()
+    psiN = torch.empty_like(psi0)
+    g0 = torch.empty_like(psi0)
+    gv = torch.zeros(psi0.shape[0], dtype=torch.float64, device=psi0.device) if want_grad_v else None
+    L.check(lib.decbpm_vjp(mesh.handle, ctypes.byref(prm), ctypes.c_void_p(psi0.data_ptr()),
+                           ctypes.c_void_p(gN.data_ptr()), ctypes.c_void_p(psiN.data_ptr()),
+                           ctypes.c_void_p(g0.data_ptr()),
+                           ctypes.c_void_p(gv.data_ptr()) if gv is not None else None, B,
+                           int(checkpoint_every), _stream_handle(stream)))
+    return psiN, g0, gv
+
+
+def _base_potential(mesh: Mesh):
+    if getattr(mesh, "_v_base", None) is None:
+        a = assemble_host(*mesh._inputs)
+        mesh._v_base = a["v"]
+    return mesh._v_base
+
+
+def _march_function():
+    import torch
+
+    class MarchFunction(torch.autograd.Function):
+        """psi_N = march(psi_0; v + dv): forward through decbpm_propagate,
+        backward through the hand-written adjoint decbpm_vjp (checkpointed)."""
+
+        @staticmethod
+        def forward(ctx, psi0, dv, mesh, dz, n_steps, checkpoint_every):
+            v = _base_potential(mesh) + dv.detach().double().cpu().numpy()
+            set_potential(mesh, v)
+            out = psi0.detach().clone().contiguous()
+            propagate(mesh, out, dz, n_steps)
+            ctx.save_for_backward(psi0.detach(), dv.detach())
+            ctx.mesh, ctx.dz, ctx.n_steps, ctx.ck = mesh, dz, n_steps, checkpoint_every
+            return out
+
+        @staticmethod
+        def backward(ctx, grad_out):
+            psi0, dv = ctx.saved_tensors
+            mesh = ctx.mesh
+            set_potential(mesh, _base_potential(mesh) + dv.double().cpu().numpy())
+            _, g0, gv = vjp(mesh, psi0, grad_out.contiguous(), ctx.dz, ctx.n_steps, ctx.ck)
+            return g0, gv.to(dv.dtype), None, None, None, None
+
+    return MarchFunction
+
+
+def march(mesh: Mesh, psi0, dv, dz, n_steps, checkpoint_every=0):
+    """Differentiable march: gradients flow to psi0 (complex) and to the
+    per-vertex potential offset dv (real, [N0])."""
+    return _march_function().apply(psi0, dv, mesh, dz, n_steps, checkpoint_every)

@@ -165,6 +165,8 @@ struct decbpm_plan_s {
     DevAllocs mem;
     std::vector<void *> psi, b0, b1, b2, user;   // user: device staging for the host-buffer entry points
     void *y_plain = nullptr;                     // SpMV result of the plain path
+    char *adj_ws = nullptr;                      // adjoint workspace (checkpoints, segment states, cotangent)
+    size_t adj_ws_bytes = 0;
     void *views = nullptr, *coef = nullptr;
     int32_t *active = nullptr;
     int coef_cap = 0, active_cap = 0;
@@ -189,6 +191,7 @@ struct decbpm_plan_s {
         if (cap_stream) cudaStreamDestroy(cap_stream);
         if (ev0) cudaEventDestroy(ev0);
         if (ev1) cudaEventDestroy(ev1);
+        if (adj_ws) cudaFree(adj_ws);
         mem.release();
     }
 };
@@ -676,6 +679,167 @@ static int propagate_plain(decbpm_mesh_t m, const decbpm_params *prm, void *psi_
     return finish_diag(P, prm, n_points, diag_out);
 }
 
+
+// ============================================================== adjoint (vector-Jacobian product)
+// Reverse-mode derivative of psi_N = (D_{h/2} E_h D_{h/2})^N psi_0 (lumped Kerr):
+// forward march with a checkpoint every C steps; backward segment by
+// segment: recompute the segment's states one step at a time (each stored),
+// then for every step, last first: adjoint of the trailing D_{h/2}, E_h^{-1}
+// (the march kernel with -dz coefficients and the diagonal flow switched
+// off: D_0 is the identity), adjoint of the leading D_{h/2}.
+template <typename R>
+static int vjp_impl(decbpm_mesh_t mesh, decbpm_plan_t P, const decbpm_params *prm, const void *psi0_dev,
+                    const void *gN_dev, void *psiN_dev, void *grad_psi0_dev, double *grad_v_dev, int64_t n_fields,
+                    int32_t ck_every, cudaStream_t s) {
+    using C = typename CT<R>::c2;
+    const int64_t N = prm->n_steps;
+    const int64_t n0 = mesh->A.n0;
+    const int bpad = P->bpad;
+    const double tol = default_tol(prm);
+    TRY(plan_configure<R>(P, prm->dz, tol));
+    Cheb cb_fwd, cb_bwd;
+    TRY(cheb_coefficients(mesh->A.p, mesh->A.rho, prm->dz, tol, cb_fwd));
+    TRY(cheb_coefficients(mesh->A.p, mesh->A.rho, -prm->dz, tol, cb_bwd));
+    if (cb_bwd.M != cb_fwd.M) return fail(DECBPM_ERR_CUDA, "internal: backward degree differs");
+    const int64_t Cs = ck_every > 0 ? ck_every : std::max<int64_t>(1, int64_t(std::ceil(std::sqrt(double(std::max<int64_t>(N, 1))))));
+    const int64_t n_ck = N > 0 ? (N + Cs - 1) / Cs : 0;
+    const size_t state = size_t(n0) * bpad * sizeof(C);
+    const int M = cb_bwd.M;
+    // workspace: G | grad_v (double n0) | backward view | backward stage table | checkpoints | segment states (Cs + 1)
+    const size_t off_gv = (state + 255) & ~size_t(255);
+    const size_t off_view = off_gv + ((sizeof(double) * n0 + 255) & ~size_t(255));
+    const size_t off_coef = off_view + 256 * ((sizeof(MeshView<R>) + 255) / 256);
+    const size_t off_ck = off_coef + 256 * ((sizeof(StageCoef<R>) * M + 255) / 256);
+    const size_t off_seg = off_ck + state * size_t(n_ck);
+    const size_t need = off_seg + state * size_t(Cs + 1);
+    if (need > P->adj_ws_bytes) {
+        if (P->adj_ws) cudaFree(P->adj_ws);
+        P->adj_ws = nullptr;
+        P->adj_ws_bytes = 0;
+        cudaError_t e = cudaMalloc(&P->adj_ws, need);
+        if (e != cudaSuccess) return fail(DECBPM_ERR_OOM, "adjoint workspace of %zu bytes: %s", need, cudaGetErrorString(e));
+        P->adj_ws_bytes = need;
+    }
+    char *ws = P->adj_ws;
+    C *G = reinterpret_cast<C *>(ws);
+    double *gv = reinterpret_cast<double *>(ws + off_gv);
+    auto ck = [&](int64_t j) { return reinterpret_cast<C *>(ws + off_ck + state * size_t(j)); };
+    auto seg = [&](int64_t j) { return reinterpret_cast<C *>(ws + off_seg + state * size_t(j)); };
+    // backward view: the plan's mesh view with -dz coefficients, acting on G
+    {
+        std::vector<StageCoef<R>> coef(M);
+        auto mk = [](std::complex<double> z) { C c; c.x = R(z.real()); c.y = R(z.imag()); return c; };
+        for (int k = 0; k < M; ++k) {
+            StageCoef<R> sc{};
+            std::complex<double> alpha = cb_bwd.a[k], beta = (k == 0) ? 1.0 : 2.0;
+            int flags = 0;
+            if (k == M - 1) { flags |= kGisPsi; beta = 2.0 * cb_bwd.a[M]; }
+            else if (k == M - 2) { alpha = cb_bwd.a[k] - cb_bwd.a[M]; }
+            else flags |= kHasH;
+            if (k == 0) flags |= kFinal;
+            sc.alpha = mk(alpha); sc.beta = mk(beta); sc.alpha_lo = mk(0.0); sc.flags = flags;
+            coef[k] = sc;
+        }
+        auto up = [](C z) { return std::complex<double>(double(z.x), double(z.y)); };
+        std::complex<double> bk1 = 0, bk2 = 0, Sv = 0;
+        for (int k = M - 1; k >= 0; --k) {
+            const std::complex<double> g = (coef[k].flags & kGisPsi) ? 1.0 : bk1;
+            std::complex<double> o = up(coef[k].alpha) - up(coef[k].beta) * g;
+            if (coef[k].flags & kHasH) o -= bk2;
+            if (coef[k].flags & kFinal) Sv = o;
+            bk2 = bk1;
+            bk1 = o;
+        }
+        coef[0].alpha_lo = mk(cb_bwd.f0 - Sv);
+        MeshView<R> v{};
+        CK(cudaMemcpy(&v, P->views, sizeof(MeshView<R>), cudaMemcpyDeviceToHost));
+        v.psi = G;
+        v.coef = reinterpret_cast<const StageCoef<R> *>(ws + off_coef);
+        CK(cudaMemcpy(ws + off_coef, coef.data(), sizeof(StageCoef<R>) * M, cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(ws + off_view, &v, sizeof(v), cudaMemcpyHostToDevice));
+    }
+    const MeshView<R> *bwd_view = reinterpret_cast<const MeshView<R> *>(ws + off_view);
+    auto march = [&](const MeshView<R> *views, int steps, R h, int pre) -> int {
+        MarchParams<R> mp{};
+        mp.meshes = views;
+        mp.active_items = P->active;
+        mp.n_meshes = 1;
+        mp.S = P->S;
+        mp.total_items = P->total_items;
+        mp.n_steps = steps;
+        mp.pre_half = pre;
+        mp.post_half = 1;
+        mp.kerr_mode = DECBPM_KERR_LUMPED;
+        mp.bpad_log2 = P->bpad_log2;
+        mp.h = h;
+        mp.barrier = P->barrier;
+        mp.status = P->status;
+        mp.timeout_ns = kBarrierTimeoutNs;
+        CK(cudaMemsetAsync(P->barrier, 0, sizeof(unsigned long long), s));
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(P->grid);
+        cfg.blockDim = dim3(P->block);
+        cfg.stream = s;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeCooperative;
+        attr[0].val.cooperative = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        void *args[] = {&mp};
+        CK(cudaLaunchKernelExC(&cfg, march_ptr_for<R>(bpad), args));
+        return DECBPM_OK;
+    };
+    const MeshView<R> *fwd_view = reinterpret_cast<const MeshView<R> *>(P->views);
+    const R *vv = sizeof(R) == 4 ? (const R *)mesh->v32 : (const R *)mesh->v64;
+    const R *cb = sizeof(R) == 4 ? (const R *)mesh->chib32 : (const R *)mesh->chib64;
+    const R *sg = sizeof(R) == 4 ? (const R *)mesh->sig32 : (const R *)mesh->sig64;
+    C *psi = (C *)P->psi[0];
+    const int T = 256;
+    const int Gv = int((n0 + T - 1) / T);
+    const int Gs = int(std::min<int64_t>(4 * P->num_sms, (n0 * bpad + T - 1) / T));
+    CK(cudaMemsetAsync(P->status, 0, sizeof(int), s));
+    // forward with checkpoints
+    permute_in_kernel<C><<<Gs, T, 0, s>>>((const C *)psi0_dev, psi, mesh->perm, int32_t(n0), int32_t(n_fields), bpad);
+    for (int64_t j = 0; j < n_ck; ++j) {
+        CK(cudaMemcpyAsync(ck(j), psi, state, cudaMemcpyDeviceToDevice, s));
+        TRY(march(fwd_view, int(std::min<int64_t>(Cs, N - j * Cs)), R(prm->dz), 1));
+    }
+    const double phN = std::fmod(double(N) * cb_fwd.theta0, 2.0 * M_PI);
+    if (psiN_dev)
+        permute_out_kernel<C><<<Gs, T, 0, s>>>(psi, (C *)psiN_dev, mesh->perm, int32_t(n0), int32_t(n_fields), bpad,
+                                               std::cos(phN), std::sin(phN));
+    // terminal cotangent in the internal (phase-free, *0-weighted) frame
+    cotangent_in_kernel<C><<<Gs, T, 0, s>>>((const C *)gN_dev, G, mesh->perm, mesh->m64, int32_t(n0), int32_t(n_fields),
+                                            bpad, std::cos(phN), -std::sin(phN));
+    CK(cudaMemsetAsync(gv, 0, sizeof(double) * n0, s));
+    const R hh = R(0.5 * prm->dz);
+    for (int64_t j = n_ck - 1; j >= 0; --j) {
+        const int64_t len = std::min<int64_t>(Cs, N - j * Cs);
+        CK(cudaMemcpyAsync(psi, ck(j), state, cudaMemcpyDeviceToDevice, s));
+        for (int64_t t = 0; t < len; ++t) {
+            CK(cudaMemcpyAsync(seg(t), psi, state, cudaMemcpyDeviceToDevice, s));
+            TRY(march(fwd_view, 1, R(prm->dz), 1));
+        }
+        CK(cudaMemcpyAsync(seg(len), psi, state, cudaMemcpyDeviceToDevice, s));
+        for (int64_t t = len - 1; t >= 0; --t) {
+            adj_diag_kernel<R><<<Gv, T, 0, s>>>(G, seg(t + 1), 1, int32_t(n0), int32_t(n_fields), bpad, hh, vv, cb, sg,
+                                                mesh->m64, gv);
+            TRY(march(bwd_view, 1, R(0), 0));
+            adj_diag_kernel<R><<<Gv, T, 0, s>>>(G, seg(t), 0, int32_t(n0), int32_t(n_fields), bpad, hh, vv, cb, sg,
+                                                mesh->m64, gv);
+        }
+    }
+    gradient_out_kernel<C><<<Gs, T, 0, s>>>(G, (C *)grad_psi0_dev, mesh->perm, mesh->m64, int32_t(n0), int32_t(n_fields), bpad);
+    if (grad_v_dev) scatter_real_kernel<<<Gv, T, 0, s>>>(gv, grad_v_dev, mesh->perm, int32_t(n0));
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(s));
+    int status = 0;
+    CK(cudaMemcpy(&status, P->status, sizeof(int), cudaMemcpyDeviceToHost));
+    if (status == DECBPM_ERR_TIMEOUT) return fail(DECBPM_ERR_TIMEOUT, "grid barrier timed out in the march kernel");
+    if (status != 0) return fail(status, "device reported status %d", status);
+    return DECBPM_OK;
+}
+
 // ============================================================== C ABI
 extern "C" {
 
@@ -916,6 +1080,41 @@ int32_t decbpm_plan_degree(decbpm_plan_t P, int32_t i, double dz, int32_t precis
     const double tol = cheb_tol > 0 ? cheb_tol : (precision == DECBPM_C64 ? 1e-9 : 1e-16);
     if (cheb_coefficients(P->meshes[i]->A.p, P->meshes[i]->A.rho, dz, tol, cb) != DECBPM_OK) return 0;
     return cb.M;
+}
+
+int decbpm_mesh_set_potential(decbpm_mesh_t m, const double *v_vertex) {
+    clear_error();
+    if (!m) return fail(DECBPM_ERR_INVALID_ARG, "mesh is NULL");
+    const int64_t n0 = m->A.n0;
+    std::vector<double> v(n0);
+    for (int64_t i = 0; i < n0; ++i) {
+        const int32_t o = m->A.perm[i];
+        v[i] = v_vertex ? v_vertex[o] : m->A.v[o];
+        if (!std::isfinite(v[i])) return fail(DECBPM_ERR_NONFINITE, "v_vertex[%d] is not finite", o);
+    }
+    std::vector<float> v32(v.begin(), v.end());
+    CK(cudaMemcpy(m->v64, v.data(), sizeof(double) * n0, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(m->v32, v32.data(), sizeof(float) * n0, cudaMemcpyHostToDevice));
+    return DECBPM_OK;
+}
+
+int decbpm_vjp(decbpm_mesh_t mesh, const decbpm_params *params, const void *psi0_dev, const void *gN_dev,
+               void *psiN_dev, void *grad_psi0_dev, double *grad_v_dev, int64_t n_fields, int32_t checkpoint_every,
+               void *stream) {
+    clear_error();
+    if (!mesh || !psi0_dev || !gN_dev || !grad_psi0_dev) return fail(DECBPM_ERR_INVALID_ARG, "NULL argument");
+    TRY(check_params(params));
+    if (params->kerr_mode != DECBPM_KERR_LUMPED) return fail(DECBPM_ERR_UNSUPPORTED, "the adjoint supports lumped Kerr");
+    if (params->variant != DECBPM_VARIANT_FUSED) return fail(DECBPM_ERR_UNSUPPORTED, "the adjoint runs the fused variant");
+    if (checkpoint_every < 0) return fail(DECBPM_ERR_INVALID_ARG, "checkpoint_every < 0");
+    decbpm_plan_t P;
+    TRY(single_plan(mesh, n_fields, params->precision, &P));
+    cudaStream_t s = (cudaStream_t)stream;
+    if (params->precision == DECBPM_C64)
+        return vjp_impl<float>(mesh, P, params, psi0_dev, gN_dev, psiN_dev, grad_psi0_dev, grad_v_dev, n_fields,
+                               checkpoint_every, s);
+    return vjp_impl<double>(mesh, P, params, psi0_dev, gN_dev, psiN_dev, grad_psi0_dev, grad_v_dev, n_fields,
+                            checkpoint_every, s);
 }
 
 int decbpm_plan_get_config(decbpm_plan_t P, decbpm_plan_config *cfg) {

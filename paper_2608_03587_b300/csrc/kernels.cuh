@@ -511,8 +511,12 @@ __device__ __forceinline__ void for_my_items(const MarchParams<R> &P, const int3
     }
 }
 
+// CTAs per SM the march kernel is compiled for: the FP64 variants need
+// 150-220 registers per thread, so they get the whole register file.
+template <typename R> struct MarchMinBlocks { static constexpr int value = sizeof(R) == 8 ? 1 : DECBPM_MARCH_MINB; };
+
 template <typename R, int BPAD>
-__global__ void __launch_bounds__(256, DECBPM_MARCH_MINB) march_kernel(MarchParams<R> P) {
+__global__ void __launch_bounds__(256, MarchMinBlocks<R>::value) march_kernel(MarchParams<R> P) {
     constexpr int FPT = Geo<R, BPAD>::FPT;
     __shared__ int32_t s_begin[kMaxMeshes + 1];
     __shared__ MeshView<R> s_view[kMaxMeshes];
@@ -598,6 +602,96 @@ __global__ void permute_out_kernel(const C *__restrict__ internal, C *__restrict
         o.y = decltype(a.x)(ar * phase_im + ai * phase_re);
         user[(size_t)perm[r] * B + f] = o;
     }
+}
+
+// ------------------------------------------------------------ adjoint
+// Backward through the diagonal flow D_h (lumped Kerr) for every field of
+// every vertex (internal order, padded layout).  g holds the *0-weighted
+// cotangent of the flow's output and is overwritten with that of its input.
+// `state` is the flow's input (post = 0) or output (post = 1; the input is
+// recovered exactly: |psi|^2 = |psi'|^2 e^{2 sigma h}, psi = psi' e^{sigma h} e^{-i theta}).
+// With u = e^{-sigma h} e^{i theta}, theta = v h + chib |psi|^2 phi:
+//     ghat = conj(u) g,   g <- ghat - 2 chib phi Im(conj(ghat) psi) psi,
+//     dJ/dv_p += -h m_p sum_fields Im(conj(ghat) psi)   (one thread per vertex: fixed order).
+template <typename R>
+__global__ void adj_diag_kernel(typename CT<R>::c2 *__restrict__ g, const typename CT<R>::c2 *__restrict__ state,
+                                int32_t post, int32_t n0, int32_t B, int32_t bpad, R h, const R *__restrict__ v,
+                                const R *__restrict__ chib, const R *__restrict__ sigma, const double *__restrict__ m64,
+                                double *__restrict__ grad_v) {
+    using C = typename CT<R>::c2;
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n0) return;
+    R em, phi;
+    const R sg = sigma[p];
+    diag_factors(sg, h, em, phi);
+    const R damp = em + R(1);
+    double acc = 0.0;
+    for (int f = 0; f < B; ++f) {
+        const size_t i = (size_t)p * bpad + f;
+        C ps = state[i];
+        R I = ps.x * ps.x + ps.y * ps.y;
+        R sn, cs;
+        if (post) {
+            I = I / (damp * damp);
+            const R theta = v[p] * h + chib[p] * I * phi;
+            sincos_r(theta, &sn, &cs);
+            const R inv = R(1) / damp;
+            ps = cmk<C>(inv * (ps.x * cs + ps.y * sn), inv * (ps.y * cs - ps.x * sn));   // psi' e^{sigma h} e^{-i theta}
+        } else {
+            const R theta = v[p] * h + chib[p] * I * phi;
+            sincos_r(theta, &sn, &cs);
+        }
+        const C gg = g[i];
+        const C gh = cmk<C>(damp * (gg.x * cs + gg.y * sn), damp * (gg.y * cs - gg.x * sn));   // conj(u) g
+        const R im = gh.x * ps.y - gh.y * ps.x;                                                // Im(conj(gh) psi)
+        const R c2 = R(2) * chib[p] * phi * im;
+        g[i] = cmk<C>(gh.x - c2 * ps.x, gh.y - c2 * ps.y);
+        acc += double(im);
+    }
+    if (grad_v) grad_v[p] += -double(h) * m64[p] * acc;
+}
+
+// user cotangent (caller order, Euclidean) -> *0-weighted internal cotangent
+// with the global phase factor of the internal states: out = phase * g / m
+template <typename C>
+__global__ void cotangent_in_kernel(const C *__restrict__ user, C *__restrict__ internal, const int32_t *__restrict__ perm,
+                                    const double *__restrict__ m64, int32_t n0, int32_t B, int32_t bpad, double pr, double pi) {
+    const long long n = (long long)n0 * bpad;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const int r = int(i / bpad), f = int(i % bpad);
+        C o;
+        if (f < B) {
+            const C a = user[(size_t)perm[r] * B + f];
+            const double s = 1.0 / m64[r];
+            o.x = decltype(a.x)(s * (double(a.x) * pr - double(a.y) * pi));
+            o.y = decltype(a.x)(s * (double(a.x) * pi + double(a.y) * pr));
+        } else {
+            o.x = 0;
+            o.y = 0;
+        }
+        internal[i] = o;
+    }
+}
+
+// internal *0-weighted cotangent -> Euclidean gradient in caller order: user = m * g
+template <typename C>
+__global__ void gradient_out_kernel(const C *__restrict__ internal, C *__restrict__ user, const int32_t *__restrict__ perm,
+                                    const double *__restrict__ m64, int32_t n0, int32_t B, int32_t bpad) {
+    const long long n = (long long)n0 * B;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const int r = int(i / B), f = int(i % B);
+        const C a = internal[(size_t)r * bpad + f];
+        C o;
+        o.x = decltype(a.x)(m64[r] * double(a.x));
+        o.y = decltype(a.x)(m64[r] * double(a.y));
+        user[(size_t)perm[r] * B + f] = o;
+    }
+}
+
+__global__ void scatter_real_kernel(const double *__restrict__ internal, double *__restrict__ user,
+                                    const int32_t *__restrict__ perm, int32_t n0) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r < n0) user[perm[r]] = internal[r];
 }
 
 // ------------------------------------------------------------ diagnostics
