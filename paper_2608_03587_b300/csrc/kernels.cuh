@@ -21,14 +21,11 @@ namespace decbpm {
 #define DECBPM_MARCH_MINB 2     // CTAs of 256 threads per SM the march kernel is compiled for
 #endif
 
+#ifndef DECBPM_FPT4
+#define DECBPM_FPT4 4           // complex64 values per thread from four fields on (4 or 2)
+#endif
 #ifndef DECBPM_REVERSE_ODD
 #define DECBPM_REVERSE_ODD 1    // odd stages walk the CTA's items backwards (L2 reuse between stages)
-#endif
-#ifndef DECBPM_HINTS
-#define DECBPM_HINTS 0          // cache hints: b_{k+2} read as last use, psi bypasses L1
-#endif
-#ifndef DECBPM_PREFETCH
-#define DECBPM_PREFETCH 0       // L2 prefetch of the own rows this many items ahead (0 = off)
 #endif
 
 constexpr int kMaxMeshes = 64;
@@ -46,6 +43,44 @@ template <typename C> __device__ __forceinline__ C csub(C a, C b) { return cmk<C
 template <typename C> __device__ __forceinline__ C cmul(C a, C b) { return cmk<C>(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); }
 template <typename C, typename R> __device__ __forceinline__ C cscale(C a, R s) { return cmk<C>(a.x * s, a.y * s); }
 template <typename C, typename R> __device__ __forceinline__ C cfma(R s, C a, C acc) { return cmk<C>(fma(s, a.x, acc.x), fma(s, a.y, acc.y)); }
+
+// complex64 overloads on Blackwell's packed FP32x2 pipe: one instruction
+// for the (re, im) pair, rounding identical to the scalar FADD / FFMA.
+#ifndef DECBPM_F32X2
+#define DECBPM_F32X2 1
+#endif
+#if DECBPM_F32X2
+__device__ __forceinline__ unsigned long long f2_bits(float2 a) {
+    unsigned long long r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a.x), "f"(a.y));
+    return r;
+}
+__device__ __forceinline__ float2 bits_f2(unsigned long long r) {
+    float2 a;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(a.x), "=f"(a.y) : "l"(r));
+    return a;
+}
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) {
+    unsigned long long r;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(f2_bits(a)), "l"(f2_bits(b)));
+    return bits_f2(r);
+}
+__device__ __forceinline__ float2 csub(float2 a, float2 b) {
+    unsigned long long r;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(f2_bits(a)), "l"(f2_bits(b)));
+    return bits_f2(r);
+}
+__device__ __forceinline__ float2 cfma(float s, float2 a, float2 acc) {
+    unsigned long long r;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(f2_bits(make_float2(s, s))), "l"(f2_bits(a)), "l"(f2_bits(acc)));
+    return bits_f2(r);
+}
+__device__ __forceinline__ float2 cscale(float2 a, float s) {
+    unsigned long long r;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(f2_bits(a)), "l"(f2_bits(make_float2(s, s))));
+    return bits_f2(r);
+}
+#endif
 
 __device__ __forceinline__ void sincos_r(float x, float *s, float *c) { sincosf(x, s, c); }
 __device__ __forceinline__ void sincos_r(double x, double *s, double *c) { sincos(x, s, c); }
@@ -79,31 +114,6 @@ __device__ __forceinline__ Pack<R, FPT> ld_pack(const typename CT<R>::c2 *p) {
         for (int i = 0; i < PackRaw<R, FPT>::kBytes / 16; ++i) t.u[i] = q[i];
     }
     return t.p;
-}
-
-// Loads with a cache policy: kLastUse for data dead after this read (the
-// b_{k+2} operand), kL2Only for data re-read next stage but not gathered (psi).
-enum : int { kLdDefault = 0, kLdLastUse = 1, kLdL2Only = 2 };
-template <typename R, int FPT, int POLICY>
-__device__ __forceinline__ Pack<R, FPT> ld_pack_hint(const typename CT<R>::c2 *p) {
-    if constexpr (POLICY == kLdDefault || !DECBPM_HINTS) {
-        return ld_pack<R, FPT>(p);
-    } else {
-        PackRaw<R, FPT> t;
-        if constexpr (PackRaw<R, FPT>::kBytes == 8) {
-            t.f2 = POLICY == kLdLastUse ? __ldlu(reinterpret_cast<const float2 *>(p))
-                                        : __ldcg(reinterpret_cast<const float2 *>(p));
-        } else {
-            const uint4 *q = reinterpret_cast<const uint4 *>(p);
-#pragma unroll
-            for (int i = 0; i < PackRaw<R, FPT>::kBytes / 16; ++i) t.u[i] = POLICY == kLdLastUse ? __ldlu(q + i) : __ldcg(q + i);
-        }
-        return t.p;
-    }
-}
-
-__device__ __forceinline__ void prefetch_l2(const void *p) {
-    asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
 }
 
 template <typename R, int FPT>
@@ -247,10 +257,12 @@ __device__ __forceinline__ int mesh_of_item(const int32_t *s_begin, int n_meshes
 // A row's operator entries j < 8 live in registers of the row's lanes: entry j
 // in lane (j % TPR) of the row group, slot j / TPR (E slots per lane).
 template <typename R, int BPAD> struct Geo {
-    // complex64: two per thread (16-byte accesses) whenever there are two
-    // fields; complex128: one (already 16 bytes) unless a row needs more
-    // than a warp
-    static constexpr int FPT = sizeof(R) == 4 ? (BPAD >= 2 ? 2 : 1) : (BPAD > 32 ? 2 : 1);
+    // complex64: four per thread (32-byte accesses) from four fields on, two
+    // (16-byte) for two or three; complex128: one (already 16 bytes) unless a
+    // row needs more than a warp
+    static constexpr int FPT = sizeof(R) == 4 ? (BPAD >= 4 ? DECBPM_FPT4 : (BPAD >= 2 ? 2 : 1)) : (BPAD > 32 ? 2 : 1);
+    static constexpr int FPT_LOG2 = FPT == 4 ? 2 : FPT == 2 ? 1 : 0;
+    static constexpr int NB = FPT >= 4 ? 4 : 8;     // neighbour gathers in flight per batch
     static constexpr int TPR = BPAD / FPT;
     static constexpr int TPR_LOG2 = TPR >= 32 ? 5 : TPR >= 16 ? 4 : TPR >= 8 ? 3 : TPR >= 4 ? 2 : TPR >= 2 ? 1 : 0;
     static constexpr int RPW = 32 / TPR;
@@ -333,49 +345,43 @@ __device__ __forceinline__ void clenshaw_stage(const MeshView<R> *sv, const Stag
         Pack<R, FPT> gp, ps, hh;
         if (live) {
             gp = ld_pack<R, FPT>(g + own);
-            ps = ld_pack_hint<R, FPT, kLdL2Only>(m.psi + own);
-            if (sc.flags & kHasH) hh = ld_pack_hint<R, FPT, kLdLastUse>(m.b[(k + 2) % 3] + own);
+            ps = ld_pack<R, FPT>(m.psi + own);
+            if (sc.flags & kHasH) hh = ld_pack<R, FPT>(m.b[(k + 2) % 3] + own);
         }
-        if (DECBPM_PREFETCH > 0 && idx + DECBPM_PREFETCH * nwarps < n_mine) {
-            // own rows of a later item of the same mesh (a guess across mesh edges is harmless)
-            const int pr = cur.row + (rev ? -1 : 1) * DECBPM_PREFETCH * nwarps * G::RPW;
-            if (pr >= 0 && pr < m.n0) {
-                const size_t po = (size_t)pr * BPAD + fo;
-                prefetch_l2(m.psi + po);
-                prefetch_l2(g + po);
-                if (sc.flags & kHasH) prefetch_l2(m.b[(k + 2) % 3] + po);
-            }
-        }
-        Pack<R, FPT> gq[8];
-        R xs[8];
-#pragma unroll
-        for (int jj = 0; jj < 8; ++jj) {
-            if (jj < cur.width) {
-                int qj;
-                R xj;
-                if constexpr (G::TPR == 1) {
-                    qj = cur.q[jj];
-                    xj = cur.x[jj];
-                } else {
-                    const int src = row_lane0 + (jj % G::TPR);
-                    qj = __shfl_sync(0xffffffffu, cur.q[jj / G::TPR], src);
-                    xj = __shfl_sync(0xffffffffu, cur.x[jj / G::TPR], src);
-                }
-                xs[jj] = xj;
-                gq[jj] = ld_pack<R, FPT>(g + (size_t)qj * BPAD + fo);
-            }
-        }
-        ItemMeta<R, G::E> nm;
-        if (nidx < n_mine) load_meta<R, BPAD>(sv, s_begin, n_meshes, item_at(nidx), nm);
         Pack<R, FPT> acc;
 #pragma unroll
         for (int f = 0; f < FPT; ++f) acc.v[f] = cmk<C>(R(0), R(0));
+        ItemMeta<R, G::E> nm;
 #pragma unroll
-        for (int jj = 0; jj < 8; ++jj)
-            if (jj < cur.width) {
+        for (int j0 = 0; j0 < 8; j0 += G::NB) {
+            Pack<R, FPT> gq[G::NB];
+            R xs[G::NB];
 #pragma unroll
-                for (int f = 0; f < FPT; ++f) acc.v[f] = cfma(xs[jj], csub(gp.v[f], gq[jj].v[f]), acc.v[f]);
+            for (int jj = 0; jj < G::NB; ++jj) {
+                const int j = j0 + jj;
+                if (j < cur.width) {
+                    int qj;
+                    R xj;
+                    if constexpr (G::TPR == 1) {
+                        qj = cur.q[j];
+                        xj = cur.x[j];
+                    } else {
+                        const int src = row_lane0 + (j % G::TPR);
+                        qj = __shfl_sync(0xffffffffu, cur.q[j / G::TPR], src);
+                        xj = __shfl_sync(0xffffffffu, cur.x[j / G::TPR], src);
+                    }
+                    xs[jj] = xj;
+                    gq[jj] = ld_pack<R, FPT>(g + (size_t)qj * BPAD + fo);
+                }
             }
+            if (j0 == 0 && nidx < n_mine) load_meta<R, BPAD>(sv, s_begin, n_meshes, item_at(nidx), nm);
+#pragma unroll
+            for (int jj = 0; jj < G::NB; ++jj)
+                if (j0 + jj < cur.width) {
+#pragma unroll
+                    for (int f = 0; f < FPT; ++f) acc.v[f] = cfma(xs[jj], csub(gp.v[f], gq[jj].v[f]), acc.v[f]);
+                }
+        }
         for (int j = 8; j < cur.width; ++j) {               // rare: slices wider than 8
             const int qq = __ldg(m.col + cur.base + 32 * j);
             const R xx = __ldg(m.xval + cur.base + 32 * j);
@@ -425,7 +431,7 @@ __device__ __forceinline__ void element_kerr_item(const MeshView<R> &m, int loca
                                                   const typename CT<R>::c2 *src, typename CT<R>::c2 *dst) {
     using C = typename CT<R>::c2;
     const int lane = threadIdx.x & 31;
-    const int tpr_log2 = bpad_log2 - (FPT == 2 ? 1 : 0);
+    const int tpr_log2 = bpad_log2 - (FPT == 4 ? 2 : FPT == 2 ? 1 : 0);
     const int rpw = 32 >> tpr_log2;
     const int row = local_item * rpw + (lane >> tpr_log2);
     if (row >= m.n0) return;
@@ -466,7 +472,7 @@ __device__ __forceinline__ void element_kerr_item(const MeshView<R> &m, int loca
 template <typename R, int FPT>
 __device__ __forceinline__ void lumped_diag_item(const MeshView<R> &m, int local_item, R hh, int bpad_log2) {
     const int lane = threadIdx.x & 31;
-    const int tpr_log2 = bpad_log2 - (FPT == 2 ? 1 : 0);
+    const int tpr_log2 = bpad_log2 - (FPT == 4 ? 2 : FPT == 2 ? 1 : 0);
     const int rpw = 32 >> tpr_log2;
     const int row = local_item * rpw + (lane >> tpr_log2);
     if (row >= m.n0) return;
@@ -485,7 +491,7 @@ template <typename R, int FPT>
 __device__ __forceinline__ void copy_item(const MeshView<R> &m, int local_item, int bpad_log2,
                                           const typename CT<R>::c2 *src, typename CT<R>::c2 *dst) {
     const int lane = threadIdx.x & 31;
-    const int tpr_log2 = bpad_log2 - (FPT == 2 ? 1 : 0);
+    const int tpr_log2 = bpad_log2 - (FPT == 4 ? 2 : FPT == 2 ? 1 : 0);
     const int rpw = 32 >> tpr_log2;
     const int row = local_item * rpw + (lane >> tpr_log2);
     if (row >= m.n0) return;
@@ -528,7 +534,7 @@ __global__ void __launch_bounds__(256, MarchMinBlocks<R>::value) march_kernel(Ma
     __syncthreads();
     unsigned long long target = 0;
     const R h = P.h, hh = P.h * R(0.5);
-    const int bl = Geo<R, BPAD>::TPR_LOG2 + (FPT == 2 ? 1 : 0);
+    const int bl = Geo<R, BPAD>::TPR_LOG2 + Geo<R, BPAD>::FPT_LOG2;
     for (int step = 0; step < P.n_steps; ++step) {
         if (step == 0 && P.pre_half) {
             if (P.kerr_mode == 0) {
