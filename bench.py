@@ -125,7 +125,8 @@ class ClockSampler:
 # ------------------------------------------------------------------ workload
 def build_workload(args, rank: int):
     from paper_2608_03587_b300 import workloads as W
-    return W.batched_fibers(n_meshes=args.meshes, fields_per_mesh=args.fields, seed=shard_seed(rank))
+    return W.batched_fibers(n_meshes=args.meshes, fields_per_mesh=args.fields, n_min=args.fiber_min,
+                            ratio=args.fiber_ratio, seed=shard_seed(rank))
 
 
 def algorithmic_bytes_per_step(mesh_infos, fields, degrees, scalar_bytes=8):
@@ -335,6 +336,8 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--meshes", type=int, default=16)
     ap.add_argument("--fields", type=int, default=16)
+    ap.add_argument("--fiber-min", type=int, default=20_000, help="vertices of the smallest fiber")
+    ap.add_argument("--fiber-ratio", type=float, default=25.0, help="largest / smallest fiber size")
     ap.add_argument("--cpu-meshes", type=int, default=8)
     ap.add_argument("--ref-meshes", type=int, default=4)
     ap.add_argument("--no-cpu-baseline", action="store_true")

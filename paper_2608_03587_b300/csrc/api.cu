@@ -250,7 +250,7 @@ static int plan_create_impl(const decbpm_mesh_t *meshes, int32_t n, const int32_
     P->bpad_log2 = ilog2(maxB);
     P->bpad = 1 << P->bpad_log2;
     // complex values per thread; must match Geo<R, BPAD>::FPT of the kernel
-    P->fpt = precision == DECBPM_C64 ? (P->bpad >= 4 ? DECBPM_FPT4 : (P->bpad >= 2 ? 2 : 1)) : (P->bpad > 32 ? 2 : 1);
+    P->fpt = precision == DECBPM_C64 ? std::min(P->bpad, DECBPM_FPT4) : (P->bpad > 32 ? 2 : 1);
     CK(cudaGetDevice(&P->device));
     CK(cudaDeviceGetAttribute(&P->num_sms, cudaDevAttrMultiProcessorCount, P->device));
     const size_t cs = csize(precision);
@@ -304,7 +304,7 @@ static int plan_configure(decbpm_plan_t P, double dz, double tol) {
     P->theta0.resize(n);
     for (int i = 0; i < n; ++i) { P->M[i] = ch[i].M; P->theta0[i] = ch[i].theta0; }
     P->S = ch[P->order[0]].M;
-    const int tpr_log2 = P->bpad_log2 - (P->fpt == 4 ? 2 : P->fpt == 2 ? 1 : 0);
+    const int tpr_log2 = P->bpad_log2 - (P->fpt == 8 ? 3 : P->fpt == 4 ? 2 : P->fpt == 2 ? 1 : 0);
     const int rpw = 32 >> tpr_log2;
     P->item_begin.assign(n, 0);
     P->items.assign(n, 0);
@@ -451,7 +451,8 @@ static int launch_diag(decbpm_plan_t P, cudaStream_t s, int kerr_mode, int point
         diag_partial_kernel<R><<<P->diag_blocks[i], kDiagThreads, 0, s>>>(
             (const typename CT<R>::c2 *)P->psi[i], int32_t(m->A.n0), P->bpad_log2, P->B[i], m->slice_ptr, m->slice_w,
             m->col, m->w64, m->m64, m->v64, m->chib64, m->coff64, m->cdiag64, kerr_mode, P->partial);
-        diag_final_kernel<<<1, 64, 0, s>>>(P->partial, P->diag_blocks[i], P->bpad, P->diag_dev + size_t(i) * P->bpad * kDiagQ);
+        diag_final_kernel<<<P->B[i], kDiagThreads, 0, s>>>(P->partial, P->diag_blocks[i], P->bpad,
+                                                            P->diag_dev + size_t(i) * P->bpad * kDiagQ);
     }
     CK(cudaGetLastError());
     const size_t per_point = size_t(n) * P->bpad * kDiagQ;
@@ -1235,7 +1236,7 @@ int propagate_noalloc_impl(decbpm_mesh_t mesh, const decbpm_params *prm, void *p
     const int64_t n0 = mesh->A.n0;
     const int bpad_log2 = ilog2(int(n_fields));
     const int bpad = 1 << bpad_log2;
-    const int fpt = sizeof(R) == 4 ? (bpad >= 4 ? DECBPM_FPT4 : (bpad >= 2 ? 2 : 1)) : (bpad > 32 ? 2 : 1);
+    const int fpt = sizeof(R) == 4 ? std::min(bpad, DECBPM_FPT4) : (bpad > 32 ? 2 : 1);
     Cheb cb;
     TRY(cheb_coefficients(mesh->A.p, mesh->A.rho, prm->dz, default_tol(prm), cb));
     const int M = cb.M;
@@ -1292,7 +1293,7 @@ int propagate_noalloc_impl(decbpm_mesh_t mesh, const decbpm_params *prm, void *p
         }
         coef[0].alpha_lo = mk(cb.f0 - Sv);
     }
-    const int tpr_log2 = bpad_log2 - (fpt == 4 ? 2 : fpt == 2 ? 1 : 0);
+    const int tpr_log2 = bpad_log2 - (fpt == 8 ? 3 : fpt == 4 ? 2 : fpt == 2 ? 1 : 0);
     const int rpw = 32 >> tpr_log2;
     const int items = int((n0 + rpw - 1) / rpw);
     int32_t active[1024];

@@ -22,7 +22,7 @@ namespace decbpm {
 #endif
 
 #ifndef DECBPM_FPT4
-#define DECBPM_FPT4 4           // complex64 values per thread from four fields on (4 or 2)
+#define DECBPM_FPT4 4           // most complex64 values per thread (2, 4 or 8)
 #endif
 #ifndef DECBPM_REVERSE_ODD
 #define DECBPM_REVERSE_ODD 1    // odd stages walk the CTA's items backwards (L2 reuse between stages)
@@ -260,9 +260,9 @@ template <typename R, int BPAD> struct Geo {
     // complex64: four per thread (32-byte accesses) from four fields on, two
     // (16-byte) for two or three; complex128: one (already 16 bytes) unless a
     // row needs more than a warp
-    static constexpr int FPT = sizeof(R) == 4 ? (BPAD >= 4 ? DECBPM_FPT4 : (BPAD >= 2 ? 2 : 1)) : (BPAD > 32 ? 2 : 1);
-    static constexpr int FPT_LOG2 = FPT == 4 ? 2 : FPT == 2 ? 1 : 0;
-    static constexpr int NB = FPT >= 4 ? 4 : 8;     // neighbour gathers in flight per batch
+    static constexpr int FPT = sizeof(R) == 4 ? (BPAD < DECBPM_FPT4 ? BPAD : DECBPM_FPT4) : (BPAD > 32 ? 2 : 1);
+    static constexpr int FPT_LOG2 = FPT == 8 ? 3 : FPT == 4 ? 2 : FPT == 2 ? 1 : 0;
+    static constexpr int NB = FPT >= 8 ? 2 : FPT >= 4 ? 4 : 8;     // neighbour gathers in flight per batch
     static constexpr int TPR = BPAD / FPT;
     static constexpr int TPR_LOG2 = TPR >= 32 ? 5 : TPR >= 16 ? 4 : TPR >= 8 ? 3 : TPR >= 4 ? 2 : TPR >= 2 ? 1 : 0;
     static constexpr int RPW = 32 / TPR;
@@ -431,7 +431,7 @@ __device__ __forceinline__ void element_kerr_item(const MeshView<R> &m, int loca
                                                   const typename CT<R>::c2 *src, typename CT<R>::c2 *dst) {
     using C = typename CT<R>::c2;
     const int lane = threadIdx.x & 31;
-    const int tpr_log2 = bpad_log2 - (FPT == 4 ? 2 : FPT == 2 ? 1 : 0);
+    const int tpr_log2 = bpad_log2 - (FPT == 8 ? 3 : FPT == 4 ? 2 : FPT == 2 ? 1 : 0);
     const int rpw = 32 >> tpr_log2;
     const int row = local_item * rpw + (lane >> tpr_log2);
     if (row >= m.n0) return;
@@ -472,7 +472,7 @@ __device__ __forceinline__ void element_kerr_item(const MeshView<R> &m, int loca
 template <typename R, int FPT>
 __device__ __forceinline__ void lumped_diag_item(const MeshView<R> &m, int local_item, R hh, int bpad_log2) {
     const int lane = threadIdx.x & 31;
-    const int tpr_log2 = bpad_log2 - (FPT == 4 ? 2 : FPT == 2 ? 1 : 0);
+    const int tpr_log2 = bpad_log2 - (FPT == 8 ? 3 : FPT == 4 ? 2 : FPT == 2 ? 1 : 0);
     const int rpw = 32 >> tpr_log2;
     const int row = local_item * rpw + (lane >> tpr_log2);
     if (row >= m.n0) return;
@@ -491,7 +491,7 @@ template <typename R, int FPT>
 __device__ __forceinline__ void copy_item(const MeshView<R> &m, int local_item, int bpad_log2,
                                           const typename CT<R>::c2 *src, typename CT<R>::c2 *dst) {
     const int lane = threadIdx.x & 31;
-    const int tpr_log2 = bpad_log2 - (FPT == 4 ? 2 : FPT == 2 ? 1 : 0);
+    const int tpr_log2 = bpad_log2 - (FPT == 8 ? 3 : FPT == 4 ? 2 : FPT == 2 ? 1 : 0);
     const int rpw = 32 >> tpr_log2;
     const int row = local_item * rpw + (lane >> tpr_log2);
     if (row >= m.n0) return;
@@ -759,18 +759,29 @@ __global__ void __launch_bounds__(kDiagThreads) diag_partial_kernel(
     }
 }
 
-// Fixed-order reduction over blocks: out[f][q].
-__global__ void diag_final_kernel(const double *__restrict__ partial, int32_t nblocks, int32_t bpad,
-                                  double *__restrict__ out) {
-    const int f = threadIdx.x;
-    if (f >= bpad) return;
+// Fixed-order reduction over blocks, one block of kDiagThreads per field:
+// out[f][q].  Thread t sums blocks t, t + kDiagThreads, ... in order, then a
+// fixed tree combines the threads (bitwise reproducible).
+__global__ void __launch_bounds__(kDiagThreads) diag_final_kernel(const double *__restrict__ partial, int32_t nblocks,
+                                                                  int32_t bpad, double *__restrict__ out) {
+    __shared__ double red[kDiagThreads][kDiagQ];
+    const int f = blockIdx.x;
     double s[kDiagQ] = {0, 0, 0, 0, 0, 0};
-    for (int b = 0; b < nblocks; ++b) {
+    for (int b = threadIdx.x; b < nblocks; b += blockDim.x) {
         const double *p = partial + ((size_t)b * bpad + f) * kDiagQ;
         for (int q = 0; q < 5; ++q) s[q] += p[q];
         s[5] = fmax(s[5], p[5]);
     }
-    for (int q = 0; q < kDiagQ; ++q) out[f * kDiagQ + q] = s[q];
+    for (int q = 0; q < kDiagQ; ++q) red[threadIdx.x][q] = s[q];
+    __syncthreads();
+    for (int half = kDiagThreads / 2; half > 0; half >>= 1) {
+        if (threadIdx.x < half) {
+            for (int q = 0; q < 5; ++q) red[threadIdx.x][q] += red[threadIdx.x + half][q];
+            red[threadIdx.x][5] = fmax(red[threadIdx.x][5], red[threadIdx.x + half][5]);
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x < kDiagQ) out[f * kDiagQ + threadIdx.x] = red[0][threadIdx.x];
 }
 
 // ------------------------------------------------------------ plain path
