@@ -36,11 +36,12 @@ FALLBACK_HBM_GBS = 6400.0
 METRIC = "vertex-steps/s (complex field) + % HBM roofline, FP32/batched vs plain FP64 on GPU"
 UNIT = "vertex-steps/s"
 
-# DRAM bytes per algorithmic byte of the march kernel, from the ncu capture
-# summarized in profiles/march_kernel_fiber500k_b16.md, valid for the kernel
-# source whose hash is recorded with it (traffic is reported as null otherwise).
-TRAFFIC_RATIO = None
-TRAFFIC_SRC_HASH = None
+# DRAM bytes (read + write) per algorithmic byte of the march kernel on this
+# workload, from the one-pass ncu capture of this bench's own launches
+# (profiles/launches_bench_batched_fibers.md), valid for the kernel source
+# whose hash is recorded with it; traffic is reported as null otherwise.
+TRAFFIC_RATIO = 0.967
+TRAFFIC_SRC_HASH = "d74759874ca68737"
 
 
 def kernel_source_hash() -> str:
