@@ -252,3 +252,105 @@ def vjp(ops: Operators, p, psi0: np.ndarray, gN: np.ndarray, h: float, n_steps: 
         gt, d2 = adjoint_diagonal(ops, pre[n], gt, 0.5 * h, sigma)
         gv += d1 + d2
     return ops.H0 * gt, gv
+
+
+# --------------------------------------------------------------------------
+# the paper's integrator: adaptive Dormand-Prince 5(4) on the DEC ODE
+# --------------------------------------------------------------------------
+# Butcher tableau of Dormand & Prince (1980), 5th-order solution with an
+# embedded 4th-order estimate, first-same-as-last.
+DP_C = [0.0, 1 / 5, 3 / 10, 4 / 5, 8 / 9, 1.0, 1.0]
+DP_A = [[],
+        [1 / 5],
+        [3 / 40, 9 / 40],
+        [44 / 45, -56 / 15, 32 / 9],
+        [19372 / 6561, -25360 / 2187, 64448 / 6561, -212 / 729],
+        [9017 / 3168, -355 / 33, 46732 / 5247, 49 / 176, -5103 / 18656],
+        [35 / 384, 0.0, 500 / 1113, 125 / 192, -2187 / 6784, 11 / 84]]
+DP_B4 = [5179 / 57600, 0.0, 7571 / 16695, 393 / 640, -92097 / 339200, 187 / 2100, 1 / 40]
+DP_E = [b5 - b4 for b5, b4 in zip(DP_A[6] + [0.0], DP_B4)]
+
+
+def dec_rhs(ops: Operators, p, psi: np.ndarray, sigma=None, kerr="lumped") -> np.ndarray:
+    """Right-hand side of Eq. 10, dPsi/dz = -i (L Psi + N Psi), with
+    L = L_diff - diag(v) (the potential inside L as in Eq. 11, sign per Eq. 1)
+    and N = -chib |psi|^2 (lumped) or -*0^{-1} Q^T D Q |psi|^2 (Eq. 14); the
+    absorber adds -sigma psi (zero for the paper's runs)."""
+    I = np.abs(psi) ** 2
+    if kerr == "lumped":
+        Nr = ops.chib * I
+    else:
+        Nr = (sp.diags(1.0 / ops.H0) @ ops.QtDQ) @ I
+    out = -1j * (apply_Ldiff(ops, p, psi) - ops.v * psi - Nr * psi)
+    if sigma is not None:
+        out = out - np.asarray(sigma) * psi
+    return out
+
+
+def _rms_error(err, y, y_new, rtol, atol):
+    """sqrt(mean((err / (atol + rtol max(|y|, |y_new|)))^2)) over the real and
+    imaginary components (the field viewed as a real vector of length 2 N0)."""
+    e = np.concatenate([err.real, err.imag])
+    a = np.concatenate([y.real, y.imag])
+    b = np.concatenate([y_new.real, y_new.imag])
+    sc = atol + rtol * np.maximum(np.abs(a), np.abs(b))
+    return float(np.sqrt(np.mean((e / sc) ** 2)))
+
+
+def dopri5(ops: Operators, p, psi0: np.ndarray, z_end: float, rtol=1e-9, atol=1e-11, h0=0.0, sigma=None,
+           kerr="lumped", max_steps=10_000_000):
+    """Adaptive Dormand-Prince integration of Eq. 10 from z = 0 to z_end.
+
+    Step control: accept when the RMS error norm E <= 1; the next step is
+    h * min(10, 0.9 E^(-1/5)) after an accept (no growth right after a
+    rejection) and h * max(0.2, 0.9 E^(-1/5)) after a reject.  h0 = 0 picks
+    the first step as 0.01 * ||y|| / ||f(y)|| (RMS norms scaled as above),
+    limited by the fifth-root rule on a trial Euler step.
+    Returns (psi(z_end), stats dict)."""
+    y = np.array(psi0, dtype=np.complex128, copy=True)
+    f = lambda v: dec_rhs(ops, p, v, sigma, kerr)
+    k1 = f(y)
+    n_rhs = 1
+    if h0 <= 0.0:
+        sc = atol + rtol * np.abs(np.concatenate([y.real, y.imag]))
+        d0 = float(np.sqrt(np.mean((np.concatenate([y.real, y.imag]) / sc) ** 2)))
+        d1 = float(np.sqrt(np.mean((np.concatenate([k1.real, k1.imag]) / sc) ** 2)))
+        h_try = 1e-6 if (d0 < 1e-5 or d1 < 1e-5) else 0.01 * d0 / d1
+        y1 = y + h_try * k1
+        k_try = f(y1)
+        n_rhs += 1
+        d2 = float(np.sqrt(np.mean((np.concatenate([(k_try - k1).real, (k_try - k1).imag]) / sc) ** 2))) / h_try
+        h1 = max(1e-6, h_try * 1e-3) if max(d1, d2) <= 1e-15 else (0.01 / max(d1, d2)) ** (1 / 5)
+        h = min(100 * h_try, h1)
+    else:
+        h = h0
+    z = 0.0
+    h_last = 0.0
+    n_acc = n_rej = 0
+    while z < z_end and n_acc + n_rej < max_steps:
+        h = min(h, z_end - z)
+        rejected = False
+        while True:
+            ks = [k1]
+            for s in range(1, 7):
+                ys = y + h * sum(a * k for a, k in zip(DP_A[s], ks))
+                ks.append(f(ys))
+                n_rhs += 1
+            y_new = ys                                   # stage 7 input is the 5th-order solution
+            err = h * sum(e * k for e, k in zip(DP_E, ks))
+            E = _rms_error(err, y, y_new, rtol, atol)
+            if E <= 1.0:
+                factor = 10.0 if E == 0.0 else min(10.0, 0.9 * E ** (-0.2))
+                if rejected:
+                    factor = min(1.0, factor)
+                z = z + h
+                y = y_new
+                k1 = ks[6]
+                n_acc += 1
+                h_last = h
+                h = h * factor
+                break
+            n_rej += 1
+            rejected = True
+            h = h * max(0.2, 0.9 * E ** (-0.2))
+    return y, {"n_accepted": n_acc, "n_rejected": n_rej, "n_rhs": n_rhs, "h_last": h_last}

@@ -440,3 +440,37 @@ def test_launch_fields_follow_paper_parameters():
     assert abs(psi[0]) == 0.0
     assert psi[1] == pytest.approx(math.exp(-1.0))            # rho = 1, Phi = 0
     assert psi[2] == pytest.approx(1j * math.exp(-1.0))       # rho = 1, Phi = pi/2
+
+
+# ------------------------------------------------------- the paper's RK45
+def test_dopri5_matches_scipy_rk45(tiny):
+    """The oracle's Dormand-Prince integration of Eq. 10 agrees with scipy's
+    solve_ivp RK45 (an independent implementation of the same method) to the
+    tolerance level, and with the split-step march at small dz."""
+    ops, _ = tiny
+    psi0 = W.elliptic_gaussian(ops.coords, A=2.0, wx=0.6, wy=0.3)
+    z = 0.01
+    out, st = bpm.dopri5(ops, (1.0,), psi0, z, rtol=1e-10, atol=1e-12)
+    ref = bpm.rk45_reference(ops, (1.0,), psi0, z, rtol=1e-10, atol=1e-12)
+    assert bpm.relative_error(ops, out, ref) < 1e-8
+    assert st["n_accepted"] > 10
+    split = bpm.propagate(ops, (1.0,), psi0, z / 64, 64)
+    assert bpm.relative_error(ops, out, split) < 1e-4
+    # the error estimate behaves as a 5th-order method: tighter tolerance, more steps
+    _, st2 = bpm.dopri5(ops, (1.0,), psi0, z, rtol=1e-12, atol=1e-14)
+    assert st2["n_accepted"] > st["n_accepted"]
+
+
+def test_dec_rhs_is_the_ode_of_the_split_step(tiny):
+    """dec_rhs is the generator of both split pieces: for small h,
+    (D_h E_h psi - psi)/h -> dec_rhs(psi)."""
+    ops, sigma = tiny
+    rng = np.random.default_rng(12)
+    psi = W.elliptic_gaussian(ops.coords, A=1.5) + 0.1 * rng.standard_normal(ops.n0)
+    f = bpm.dec_rhs(ops, (1.0,), psi, sigma)
+    errs = []
+    for h in (1e-5, 5e-6):
+        step = bpm.strang_step(ops, (1.0,), psi, h, sigma)
+        errs.append(np.linalg.norm((step - psi) / h - f) / np.linalg.norm(f))
+    # first-order difference quotient: the error halves with h
+    assert errs[1] < 2e-3 and 0.4 < errs[1] / errs[0] < 0.6
