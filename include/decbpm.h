@@ -252,6 +252,21 @@ int decbpm_vjp(decbpm_mesh_t mesh, const decbpm_params *params, const void *psi0
                void *psiN_dev, void *grad_psi0_dev, double *grad_v_dev, int64_t n_fields, int32_t checkpoint_every,
                void *stream);
 
+/* ---- the paper's integrator ---------------------------------------------------
+ * Adaptive Dormand-Prince 5(4) (the "RK45" the paper runs through scipy) on
+ * the full DEC ODE of Eq. 10, dPsi/dz = -i (L Psi + N(|psi|^2) Psi), with the
+ * potential inside L as in Eq. 11 (sign per Eq. 1) and the absorber as
+ * -sigma psi; FP64, one complex128 field in caller order on the device,
+ * integrated in place from z = 0 to z_end.  Step control: accept when the
+ * RMS of err / (atol + rtol max(|y|, |y_new|)) over real and imaginary parts
+ * is <= 1; next step h min(10, 0.9 E^-1/5) (no growth right after a
+ * rejection), or h max(0.2, 0.9 E^-1/5) after a rejection; h0 = 0 chooses
+ * the first step automatically.  p_n with n <= 2.                          */
+typedef struct { double rtol, atol, h0; int64_t max_steps; } decbpm_rk45_opts;
+typedef struct { int64_t n_accepted, n_rejected, n_rhs; double h_last, z; } decbpm_rk45_stats;
+int decbpm_rk45(decbpm_mesh_t mesh, double z_end, int32_t kerr_mode, const decbpm_rk45_opts *opts, void *psi_dev,
+                void *stream, decbpm_rk45_stats *stats);
+
 /* One-shot convenience: plan_create + plan_propagate + plan_destroy. */
 int decbpm_propagate_batch(const decbpm_mesh_t *meshes, int32_t n_meshes, const int32_t *fields_per_mesh,
                            const decbpm_params *params, void *const *psi_dev, void *stream,

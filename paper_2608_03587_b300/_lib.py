@@ -68,6 +68,19 @@ class PlanConfig(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class Rk45Opts(ctypes.Structure):
+    _fields_ = [("rtol", ctypes.c_double), ("atol", ctypes.c_double), ("h0", ctypes.c_double),
+                ("max_steps", ctypes.c_int64)]
+
+
+class Rk45Stats(ctypes.Structure):
+    _fields_ = [("n_accepted", ctypes.c_int64), ("n_rejected", ctypes.c_int64), ("n_rhs", ctypes.c_int64),
+                ("h_last", ctypes.c_double), ("z", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 class Diag(ctypes.Structure):
     _fields_ = [("z", ctypes.c_double), ("power", ctypes.c_double), ("hamiltonian", ctypes.c_double),
                 ("max_intensity", ctypes.c_double)]
@@ -102,6 +115,7 @@ SIGNATURES = {
     "decbpm_selftest_barrier": (_i32, [_i32, _i64, _vp]),
     "decbpm_mesh_set_potential": (_i32, [_vp, _c_double_p]),
     "decbpm_vjp": (_i32, [_vp, ctypes.POINTER(Params), _vp, _vp, _vp, _vp, _vp, _i64, _i32, _vp]),
+    "decbpm_rk45": (_i32, [_vp, _dbl, _i32, ctypes.POINTER(Rk45Opts), _vp, _vp, ctypes.POINTER(Rk45Stats)]),
     "decbpm_propagate_noalloc": (_i32, [_vp, ctypes.POINTER(Params), _vp, _i64, _vp]),
     "decbpm_propagate_batch": (_i32, [ctypes.POINTER(_vp), _i32, _c_int32_p, ctypes.POINTER(Params),
                                       ctypes.POINTER(_vp), _vp, ctypes.POINTER(Diag)]),

@@ -352,3 +352,17 @@ def march(mesh: Mesh, psi0, dv, dz, n_steps, checkpoint_every=0):
     """Differentiable march: gradients flow to psi0 (complex) and to the
     per-vertex potential offset dv (real, [N0])."""
     return _march_function().apply(psi0, dv, mesh, dz, n_steps, checkpoint_every)
+
+
+# ---------------------------------------------------------------- the paper's integrator
+def rk45(mesh: Mesh, psi, z_end, rtol=1e-9, atol=1e-11, h0=0.0, kerr="lumped", max_steps=0, stream=None):
+    """decbpm_rk45: adaptive Dormand-Prince integration of Eq. 10 in place on
+    a complex128 CUDA field [N0]; returns the step statistics."""
+    lib = _lib()
+    if psi.dtype.__str__() != "torch.complex128" or psi.dim() != 1:
+        raise TypeError("rk45 integrates one complex128 field [N0]")
+    o = L.Rk45Opts(rtol=float(rtol), atol=float(atol), h0=float(h0), max_steps=int(max_steps))
+    st = L.Rk45Stats()
+    L.check(lib.decbpm_rk45(mesh.handle, float(z_end), L.KERR_LUMPED if kerr == "lumped" else L.KERR_ELEMENT,
+                            ctypes.byref(o), ctypes.c_void_p(psi.data_ptr()), _stream_handle(stream), ctypes.byref(st)))
+    return st.as_dict()

@@ -167,6 +167,8 @@ struct decbpm_plan_s {
     void *y_plain = nullptr;                     // SpMV result of the plain path
     char *adj_ws = nullptr;                      // adjoint workspace (checkpoints, segment states, cotangent)
     size_t adj_ws_bytes = 0;
+    char *rk_ws = nullptr;                       // Dormand-Prince workspace (stages, states, norms)
+    size_t rk_ws_bytes = 0;
     void *views = nullptr, *coef = nullptr;
     int32_t *active = nullptr;
     int coef_cap = 0, active_cap = 0;
@@ -192,6 +194,7 @@ struct decbpm_plan_s {
         if (ev0) cudaEventDestroy(ev0);
         if (ev1) cudaEventDestroy(ev1);
         if (adj_ws) cudaFree(adj_ws);
+        if (rk_ws) cudaFree(rk_ws);
         mem.release();
     }
 };
@@ -841,6 +844,146 @@ static int vjp_impl(decbpm_mesh_t mesh, decbpm_plan_t P, const decbpm_params *pr
     return DECBPM_OK;
 }
 
+
+// ============================================================== the paper's integrator
+// Adaptive Dormand-Prince 5(4) on the DEC ODE of Eq. 10 (FP64, one field):
+// the stages, the error estimate and its RMS norm run on the device; the
+// step controller (same rules as the oracle's dopri5) runs on the host and
+// reads one double per attempted step.
+static const double kDpA[7][6] = {
+    {0, 0, 0, 0, 0, 0},
+    {1.0 / 5, 0, 0, 0, 0, 0},
+    {3.0 / 40, 9.0 / 40, 0, 0, 0, 0},
+    {44.0 / 45, -56.0 / 15, 32.0 / 9, 0, 0, 0},
+    {19372.0 / 6561, -25360.0 / 2187, 64448.0 / 6561, -212.0 / 729, 0, 0},
+    {9017.0 / 3168, -355.0 / 33, 46732.0 / 5247, 49.0 / 176, -5103.0 / 18656, 0},
+    {35.0 / 384, 0, 500.0 / 1113, 125.0 / 192, -2187.0 / 6784, 11.0 / 84}};
+static const double kDpB4[7] = {5179.0 / 57600, 0, 7571.0 / 16695, 393.0 / 640, -92097.0 / 339200, 187.0 / 2100, 1.0 / 40};
+
+static int rk45_impl(decbpm_mesh_t mesh, decbpm_plan_t P, double z_end, int kerr_mode, const decbpm_rk45_opts *o,
+                     void *psi_dev, cudaStream_t s, decbpm_rk45_stats *stats) {
+    const int n0 = int(mesh->A.n0);
+    const std::vector<double> &pp = mesh->A.p;
+    if (pp.size() > 2) return fail(DECBPM_ERR_UNSUPPORTED, "the RK45 path supports p_1 and p_2");
+    const double p1 = pp[0], p2 = pp.size() > 1 ? pp[1] : 0.0;
+    const double r = 0.5 * mesh->A.rho;
+    const int T = kRkThreads, G = (n0 + T - 1) / T;
+    const int NB = std::min(2 * P->num_sms, G);
+    const size_t vec = size_t(n0) * sizeof(double2);
+    const size_t need = 11 * vec + sizeof(double) * (NB + 1);
+    if (need > P->rk_ws_bytes) {
+        if (P->rk_ws) cudaFree(P->rk_ws);
+        P->rk_ws = nullptr;
+        P->rk_ws_bytes = 0;
+        cudaError_t e = cudaMalloc(&P->rk_ws, need);
+        if (e != cudaSuccess) return fail(DECBPM_ERR_OOM, "RK45 workspace of %zu bytes: %s", need, cudaGetErrorString(e));
+        P->rk_ws_bytes = need;
+    }
+    double2 *K[7], *y, *ys, *tmp, *tA;
+    for (int j = 0; j < 7; ++j) K[j] = reinterpret_cast<double2 *>(P->rk_ws + j * vec);
+    y = reinterpret_cast<double2 *>(P->rk_ws + 7 * vec);
+    ys = reinterpret_cast<double2 *>(P->rk_ws + 8 * vec);
+    tmp = reinterpret_cast<double2 *>(P->rk_ws + 9 * vec);
+    tA = reinterpret_cast<double2 *>(P->rk_ws + 10 * vec);
+    double *part = reinterpret_cast<double *>(P->rk_ws + 11 * vec);
+    double *nrm = part + NB;
+    MeshView<double> mv{};
+    CK(cudaMemcpy(&mv, P->views, sizeof(mv), cudaMemcpyDeviceToHost));
+    permute_in_kernel<double2><<<std::min(G, 4 * P->num_sms), T, 0, s>>>((const double2 *)psi_dev, y, mesh->perm, n0, 1, 1);
+    int64_t n_rhs = 0;
+    auto rhs = [&](const double2 *in, double2 *out) -> int {
+        if (pp.size() == 1) {
+            rk_rhs_kernel<<<G, T, 0, s>>>(mv, in, out, nullptr, 0, r, p1, p2, kerr_mode);
+        } else {
+            rk_rhs_kernel<<<G, T, 0, s>>>(mv, in, out, tA, 1, r, p1, p2, kerr_mode);
+            rk_rhs_kernel<<<G, T, 0, s>>>(mv, in, out, tA, 2, r, p1, p2, kerr_mode);
+        }
+        ++n_rhs;
+        CK(cudaGetLastError());
+        return DECBPM_OK;
+    };
+    auto combine = [&](double2 *out, const double2 *base, double h, const double *a, double2 *const *ks, int nk) {
+        RkCombine c{};
+        for (int j = 0; j < nk; ++j) { c.k[j] = ks[j]; c.a[j] = a[j]; }
+        c.nk = nk;
+        rk_combine_kernel<<<G, T, 0, s>>>(out, base, h, c, n0);
+    };
+    auto norm = [&](const double2 *u, const double2 *yy, const double2 *y2, double &out) -> int {
+        rk_norm_partial_kernel<<<NB, T, 0, s>>>(u, yy, y2, o->atol, o->rtol, n0, part);
+        rk_norm_final_kernel<<<1, T, 0, s>>>(part, NB, nrm);
+        double v = 0;
+        CK(cudaMemcpyAsync(&v, nrm, sizeof(double), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        out = std::sqrt(v / (2.0 * n0));
+        return DECBPM_OK;
+    };
+    TRY(rhs(y, K[0]));
+    double h = o->h0;
+    if (!(h > 0)) {
+        double d0, d1, d2;
+        TRY(norm(y, y, nullptr, d0));
+        TRY(norm(K[0], y, nullptr, d1));
+        const double h_try = (d0 < 1e-5 || d1 < 1e-5) ? 1e-6 : 0.01 * d0 / d1;
+        const double one = 1.0;
+        double2 *k0p[1] = {K[0]};
+        combine(ys, y, h_try, &one, k0p, 1);
+        TRY(rhs(ys, K[1]));
+        const double a2[2] = {1.0, -1.0};
+        double2 *kk[2] = {K[1], K[0]};
+        combine(tmp, nullptr, 1.0, a2, kk, 2);
+        TRY(norm(tmp, y, nullptr, d2));
+        d2 /= h_try;
+        const double h1 = std::max(d1, d2) <= 1e-15 ? std::max(1e-6, h_try * 1e-3) : std::pow(0.01 / std::max(d1, d2), 0.2);
+        h = std::min(100 * h_try, h1);
+    }
+    double z = 0.0, h_last = 0.0;
+    int64_t n_acc = 0, n_rej = 0;
+    const int64_t max_steps = o->max_steps > 0 ? o->max_steps : (int64_t(1) << 40);
+    double E_b[7];
+    for (int j = 0; j < 7; ++j) E_b[j] = (j < 6 ? kDpA[6][j] : 0.0) - kDpB4[j];
+    while (z < z_end && n_acc + n_rej < max_steps) {
+        h = std::min(h, z_end - z);
+        bool rejected = false;
+        while (true) {
+            for (int st = 1; st < 7; ++st) {
+                combine(ys, y, h, kDpA[st], K, st);
+                TRY(rhs(ys, K[st]));
+            }
+            combine(tmp, nullptr, h, E_b, K, 7);
+            double E;
+            TRY(norm(tmp, y, ys, E));
+            if (!std::isfinite(E)) return fail(DECBPM_ERR_NONFINITE, "RK45 error estimate is not finite");
+            if (E <= 1.0) {
+                double factor = E == 0.0 ? 10.0 : std::min(10.0, 0.9 * std::pow(E, -0.2));
+                if (rejected) factor = std::min(1.0, factor);
+                z += h;
+                std::swap(y, ys);
+                std::swap(K[0], K[6]);
+                ++n_acc;
+                h_last = h;
+                h *= factor;
+                break;
+            }
+            ++n_rej;
+            rejected = true;
+            h *= std::max(0.2, 0.9 * std::pow(E, -0.2));
+            if (h < 1e-300) return fail(DECBPM_ERR_NONFINITE, "RK45 step size underflow");
+        }
+    }
+    permute_out_kernel<double2><<<std::min(G, 4 * P->num_sms), T, 0, s>>>(y, (double2 *)psi_dev, mesh->perm, n0, 1, 1,
+                                                                         1.0, 0.0);
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(s));
+    if (stats) {
+        stats->n_accepted = n_acc;
+        stats->n_rejected = n_rej;
+        stats->n_rhs = n_rhs;
+        stats->h_last = h_last;
+        stats->z = z;
+    }
+    return DECBPM_OK;
+}
+
 // ============================================================== C ABI
 extern "C" {
 
@@ -1116,6 +1259,19 @@ int decbpm_vjp(decbpm_mesh_t mesh, const decbpm_params *params, const void *psi0
                                checkpoint_every, s);
     return vjp_impl<double>(mesh, P, params, psi0_dev, gN_dev, psiN_dev, grad_psi0_dev, grad_v_dev, n_fields,
                             checkpoint_every, s);
+}
+
+int decbpm_rk45(decbpm_mesh_t mesh, double z_end, int32_t kerr_mode, const decbpm_rk45_opts *opts, void *psi_dev,
+                void *stream, decbpm_rk45_stats *stats) {
+    clear_error();
+    if (!mesh || !opts || !psi_dev) return fail(DECBPM_ERR_INVALID_ARG, "NULL argument");
+    if (!(z_end >= 0) || !std::isfinite(z_end)) return fail(DECBPM_ERR_INVALID_ARG, "z_end must be finite and >= 0");
+    if (!(opts->rtol > 0) || !(opts->atol > 0)) return fail(DECBPM_ERR_INVALID_ARG, "rtol and atol must be > 0");
+    if (kerr_mode != DECBPM_KERR_LUMPED && kerr_mode != DECBPM_KERR_ELEMENT) return fail(DECBPM_ERR_INVALID_ARG, "bad kerr_mode");
+    decbpm_plan_t P;
+    TRY(single_plan(mesh, 1, DECBPM_C128, &P));
+    if (P->order.empty()) TRY(plan_configure<double>(P, 1e-3, 1e-16));   // only for the device view of the mesh
+    return rk45_impl(mesh, P, z_end, kerr_mode, opts, psi_dev, (cudaStream_t)stream, stats);
 }
 
 int decbpm_plan_get_config(decbpm_plan_t P, decbpm_plan_config *cfg) {

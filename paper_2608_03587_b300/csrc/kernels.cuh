@@ -784,6 +784,121 @@ __global__ void __launch_bounds__(kDiagThreads) diag_final_kernel(const double *
     if (threadIdx.x < kDiagQ) out[f * kDiagQ + threadIdx.x] = red[0][threadIdx.x];
 }
 
+// ------------------------------------------------------------ the paper's integrator
+// Right-hand side of Eq. 10 for one field in internal order (FP64):
+//   dpsi/dz = -i (p1 A y - p2 A^2 y - v y - N(y) y) - sigma y,
+// (A y)_p = r sum_q x_pq (y_p - y_q),  N = chib |y|^2 (lumped) or
+// cdiag |y_p|^2 + sum_q c_pq |y_q|^2 (element-averaged, Eq. 14).
+// pass 0: n_p = 1, k = F(y).  pass 1: t = A y only.  pass 2: k = F(y) using t = A y.
+__device__ __forceinline__ double2 a_row(const MeshView<double> &m, const double2 *__restrict__ y, int p, double r) {
+    const int s = p >> 5, base = m.slice_ptr[s] + (p & 31), w = m.slice_w[s];
+    const double2 yp = y[p];
+    double ar = 0, ai = 0;
+    for (int j = 0; j < w; ++j) {
+        const double x = m.xval[base + 32 * j];
+        const double2 yq = y[m.col[base + 32 * j]];
+        ar += x * (yp.x - yq.x);
+        ai += x * (yp.y - yq.y);
+    }
+    return make_double2(r * ar, r * ai);
+}
+
+__global__ void rk_rhs_kernel(MeshView<double> m, const double2 *__restrict__ y, double2 *__restrict__ k,
+                              double2 *__restrict__ t, int32_t pass, double r, double p1, double p2,
+                              int32_t kerr_mode) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= m.n0) return;
+    if (pass == 1) {
+        t[p] = a_row(m, y, p, r);
+        return;
+    }
+    const double2 yp = y[p];
+    double2 lin;
+    if (pass == 0) {
+        const double2 ay = a_row(m, y, p, r);
+        lin = make_double2(p1 * ay.x, p1 * ay.y);
+    } else {
+        const double2 ay = t[p], aay = a_row(m, t, p, r);
+        lin = make_double2(p1 * ay.x - p2 * aay.x, p1 * ay.y - p2 * aay.y);
+    }
+    double nr;
+    if (kerr_mode == 0) {
+        nr = m.chib[p] * (yp.x * yp.x + yp.y * yp.y);
+    } else {
+        const int s = p >> 5, base = m.slice_ptr[s] + (p & 31), w = m.slice_w[s];
+        nr = m.cdiag[p] * (yp.x * yp.x + yp.y * yp.y);
+        for (int j = 0; j < w; ++j) {
+            const double2 yq = y[m.col[base + 32 * j]];
+            nr += m.coff[base + 32 * j] * (yq.x * yq.x + yq.y * yq.y);
+        }
+    }
+    const double q = m.v[p] + nr;                          // L y - N y = lin - (v + N) y
+    const double gr = lin.x - q * yp.x, gi = lin.y - q * yp.y;
+    const double sg = m.sigma[p];
+    k[p] = make_double2(gi - sg * yp.x, -gr - sg * yp.y);  // -i (g) - sigma y
+}
+
+struct RkCombine {
+    const double2 *k[7];
+    double a[7];
+    int32_t nk;
+};
+
+// out = (y ? y : 0) + h sum_j a_j k_j
+__global__ void rk_combine_kernel(double2 *__restrict__ out, const double2 *__restrict__ y, double h, RkCombine c,
+                                  int32_t n) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n) return;
+    double2 acc = y ? y[p] : make_double2(0.0, 0.0);
+    for (int j = 0; j < c.nk; ++j) {
+        if (c.a[j] == 0.0) continue;
+        const double2 kk = c.k[j][p];
+        acc.x += h * c.a[j] * kk.x;
+        acc.y += h * c.a[j] * kk.y;
+    }
+    out[p] = acc;
+}
+
+// sum over real and imaginary components of (u / (atol + rtol max(|y|, |y2|)))^2,
+// per block (y2 may be NULL); fixed grid, fixed tree: reproducible
+constexpr int kRkThreads = 256;
+__global__ void __launch_bounds__(kRkThreads) rk_norm_partial_kernel(const double2 *__restrict__ u,
+                                                                      const double2 *__restrict__ y,
+                                                                      const double2 *__restrict__ y2, double atol,
+                                                                      double rtol, int32_t n, double *__restrict__ part) {
+    __shared__ double red[kRkThreads];
+    const int lo = int((long long)n * blockIdx.x / gridDim.x), hi = int((long long)n * (blockIdx.x + 1) / gridDim.x);
+    double acc = 0.0;
+    for (int p = lo + threadIdx.x; p < hi; p += blockDim.x) {
+        const double2 a = u[p], b = y[p];
+        double sx = fabs(b.x), sy = fabs(b.y);
+        if (y2) { sx = fmax(sx, fabs(y2[p].x)); sy = fmax(sy, fabs(y2[p].y)); }
+        const double ex = a.x / (atol + rtol * sx), ey = a.y / (atol + rtol * sy);
+        acc += ex * ex + ey * ey;
+    }
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int half = kRkThreads / 2; half > 0; half >>= 1) {
+        if (threadIdx.x < half) red[threadIdx.x] += red[threadIdx.x + half];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) part[blockIdx.x] = red[0];
+}
+
+__global__ void __launch_bounds__(kRkThreads) rk_norm_final_kernel(const double *__restrict__ part, int32_t nb,
+                                                                    double *__restrict__ out) {
+    __shared__ double red[kRkThreads];
+    double acc = 0.0;
+    for (int b = threadIdx.x; b < nb; b += blockDim.x) acc += part[b];
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int half = kRkThreads / 2; half > 0; half >>= 1) {
+        if (threadIdx.x < half) red[threadIdx.x] += red[threadIdx.x + half];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *out = red[0];
+}
+
 // ------------------------------------------------------------ plain path
 // Unfused single-field FP64 reference path: a CSR SpMV launch and an update
 // launch per Clenshaw term, a separate launch for each diagonal flow.
