@@ -186,8 +186,8 @@ def run_ours(args, rank, world, local_rank):
         torch.cuda.synchronize()
 
     # warm-up: W untimed steps (also captures the CUDA graph of this step count)
-    plan.propagate(psis, wl.dz, args.warmup)
-    plan.propagate(psis, wl.dz, args.steps)          # graph for K steps captured outside the timed region
+    plan.propagate(psis, wl.dz, args.warmup, variant=args.variant)
+    plan.propagate(psis, wl.dz, args.steps, variant=args.variant)   # graph for K steps captured outside the timed region
     sync_all()
     stream = torch.cuda.current_stream()
     ev0 = torch.cuda.Event(enable_timing=True)
@@ -195,7 +195,7 @@ def run_ours(args, rank, world, local_rank):
     with ClockSampler(local_rank) as clk:
         sync_all()
         ev0.record(stream)
-        plan.propagate(psis, wl.dz, args.steps)
+        plan.propagate(psis, wl.dz, args.steps, variant=args.variant)
         ev1.record(stream)
         sync_all()
     ms = ev0.elapsed_time(ev1)
@@ -206,10 +206,10 @@ def run_ours(args, rank, world, local_rank):
     # end to end through the host-buffer entry point (pinned host fields;
     # H2D of every field, the K-step march, D2H of every field and the diagnostics)
     host = [torch.from_numpy(p.astype(np.complex64)).pin_memory() for p in wl.psi0]
-    plan.propagate_host(host, wl.dz, args.steps)
+    plan.propagate_host(host, wl.dz, args.steps, variant=args.variant)
     sync_all()
     t_e2e = time.perf_counter()
-    plan.propagate_host(host, wl.dz, args.steps)
+    plan.propagate_host(host, wl.dz, args.steps, variant=args.variant)
     sync_all()
     e2e_s = time.perf_counter() - t_e2e
     io_bytes = sum(h.numel() * 8 for h in host)
@@ -227,6 +227,8 @@ def run_ours(args, rank, world, local_rank):
     # kernels of ours per timed call: permute in / out per mesh, the march
     # kernel, two diagnostic kernels per mesh
     launches = 1 + 4 * len(meshes)
+    tiled = cfg.get("tile_slots", 0) > 0 and args.variant == "fused"
+    kernel_name = "march_tile_kernel" if tiled else "march_kernel<float,%d>" % cfg["fields_padded"]
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
@@ -238,13 +240,15 @@ def run_ours(args, rank, world, local_rank):
             "vertices_total": int(sum(i["n_vertices"] for i in infos)), "fields_per_mesh": fields[0],
             "cheb_degree_min": int(min(degrees)), "cheb_degree_max": int(max(degrees)),
             "ordering": "hilbert", "parallelism": "replicas" if world > 1 else "single",
-            "grid": cfg["grid"], "block": cfg["block"], "cuda_graph": bool(cfg["graphs"]),
+            "grid": cfg["tile_grid"] if tiled else cfg["grid"], "block": 512 if tiled else cfg["block"],
+            "march_kernel": kernel_name, "tile_slots": cfg["tile_slots"] if tiled else 0,
+            "cuda_graph": bool(cfg["graphs"]),
             "l2": "working set %.2f GB > 126 MB L2; no flush" % (units_per_step * 8 * 4 / 1e9),
             "setup_s": round(setup_s, 2),
         },
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic,
-                     "peak_kind": peak_kind, "kernel": "march_kernel<float,16>",
+                     "peak_kind": peak_kind, "kernel": kernel_name,
                      "kernel_ms": march_ms, "alg_bytes_per_launch": alg_step * args.steps},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": io_bytes / args.steps,
                 "d2h_bytes_per_step": io_bytes / args.steps},
@@ -254,9 +258,38 @@ def run_ours(args, rank, world, local_rank):
     if rank == 0 and not args.no_plain:
         line["fp64_plain"] = plain_fp64_reference(wl, meshes, api, torch, dev)
         line["fp64_plain"]["fp32_batched_speedup"] = value / world / line["fp64_plain"]["value"]
+        line["rk45"] = rk45_comparison(wl, meshes, api, torch, dev, args.steps)
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args, wl)
     return line
+
+
+def rk45_comparison(wl, meshes, api, torch, dev, steps):
+    """The paper's own integrator (adaptive Dormand-Prince, rtol 1e-9,
+    atol 1e-11) on the GPU against the fused FP64 split-step march, both over
+    z = steps * dz on the largest fiber, first field."""
+    i = int(np.argmax([m.n_vertices for m in meshes]))
+    psi0 = torch.from_numpy(np.ascontiguousarray(wl.psi0[i][:, 0])).to(dev, torch.complex128)
+    z = steps * wl.dz
+    a = psi0.clone()
+    api.propagate(meshes[i], a, wl.dz, steps)
+    a = psi0.clone()
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    api.propagate(meshes[i], a, wl.dz, steps)
+    torch.cuda.synchronize()
+    split_ms = (time.perf_counter() - t) * 1e3
+    b = psi0.clone()
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    st = api.rk45(meshes[i], b, z, rtol=1e-9, atol=1e-11)
+    torch.cuda.synchronize()
+    rk_ms = (time.perf_counter() - t) * 1e3
+    diff = float(torch.linalg.vector_norm(a - b) / torch.linalg.vector_norm(b))
+    return {"sample": "largest fiber (%d vertices), 1 field, c128, z=%g" % (meshes[i].n_vertices, z),
+            "rk45_ms": rk_ms, "split_step_ms": split_ms, "split_step_speedup": rk_ms / split_ms,
+            "rk45_accepted": int(st["n_accepted"]), "rk45_rejected": int(st["n_rejected"]),
+            "rk45_rhs": int(st["n_rhs"]), "rel_l2_difference": diff}
 
 
 def plain_fp64_reference(wl, meshes, api, torch, dev):
@@ -343,6 +376,8 @@ def main():
     ap.add_argument("--ref-meshes", type=int, default=4)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--variant", choices=["fused", "rows"], default="fused",
+                    help="fused: tile-staged kernel where the plan allows it; rows: the row kernel")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

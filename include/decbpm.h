@@ -65,6 +65,8 @@ extern "C" {
 
 #define DECBPM_VARIANT_FUSED  0  /* persistent kernel, fused Chebyshev/Clenshaw terms and diagonal step */
 #define DECBPM_VARIANT_PLAIN  1  /* unfused reference path: one CSR SpMV launch + one update launch per term */
+#define DECBPM_VARIANT_ROWS   2  /* fused, operands read straight from global memory (never the tile-staged
+                                    kernel that FUSED selects for complex64 plans with 9..16 fields) */
 
 #define DECBPM_ORDER_DEFAULT  0  /* Hilbert curve in 2D, coordinate order in 1D */
 #define DECBPM_ORDER_RCM      1  /* reverse Cuthill-McKee (small bandwidth, thin level sets) */
@@ -128,7 +130,8 @@ typedef struct {
     int32_t precision;   /* DECBPM_C64 | DECBPM_C128: element type of the field buffers */
     int32_t kerr_mode;   /* DECBPM_KERR_LUMPED | DECBPM_KERR_ELEMENT */
     int32_t diag_every;  /* > 0: diagnostics after every diag_every steps; 0: only after the last step */
-    int32_t variant;     /* DECBPM_VARIANT_FUSED | DECBPM_VARIANT_PLAIN (C128 only) */
+    int32_t variant;     /* DECBPM_VARIANT_FUSED | DECBPM_VARIANT_ROWS | DECBPM_VARIANT_PLAIN (C128, one
+                            mesh, one field); decbpm_vjp and decbpm_propagate_noalloc take FUSED */
     double  cheb_tol;    /* Chebyshev truncation: tail bound; 0 = 1e-16 (C128) / 1e-9 (C64) */
 } decbpm_params;
 
@@ -224,6 +227,10 @@ typedef struct {
     int32_t graphs;        /* 1 if step blocks are replayed from captured CUDA graphs */
     int32_t stages;        /* grid-wide stages per step for the last configured dz (max degree) */
     int32_t n_meshes;
+    int32_t tile_slots;    /* > 0: the FUSED variant runs the tile-staged kernel with this many shared-memory
+                              slots (complex64, 9..16 fields); 0: the row kernel */
+    int32_t tile_slot_bytes;
+    int32_t tile_grid;     /* CTAs (of 512 threads) of the tile-staged launch */
 } decbpm_plan_config;
 int decbpm_plan_get_config(decbpm_plan_t plan, decbpm_plan_config *cfg);
 

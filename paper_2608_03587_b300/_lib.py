@@ -27,6 +27,7 @@ KERR_LUMPED = 0
 KERR_ELEMENT = 1
 VARIANT_FUSED = 0
 VARIANT_PLAIN = 1
+VARIANT_ROWS = 2
 ORDER_DEFAULT = 0
 ORDER_RCM = 1
 ORDER_HILBERT = 2
@@ -62,7 +63,8 @@ class Params(ctypes.Structure):
 
 class PlanConfig(ctypes.Structure):
     _fields_ = [("grid", ctypes.c_int32), ("block", ctypes.c_int32), ("fields_padded", ctypes.c_int32),
-                ("graphs", ctypes.c_int32), ("stages", ctypes.c_int32), ("n_meshes", ctypes.c_int32)]
+                ("graphs", ctypes.c_int32), ("stages", ctypes.c_int32), ("n_meshes", ctypes.c_int32),
+                ("tile_slots", ctypes.c_int32), ("tile_slot_bytes", ctypes.c_int32), ("tile_grid", ctypes.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -51,7 +51,8 @@ def _desc(coords, cells, V_cell=None, chi_cell=None, sigma=None, p=(1.0,), order
 def _params(dz, n_steps, precision, kerr="lumped", diag_every=0, variant="fused", cheb_tol=0.0):
     return L.Params(dz=float(dz), n_steps=int(n_steps), precision=precision,
                     kerr_mode=L.KERR_LUMPED if kerr == "lumped" else L.KERR_ELEMENT,
-                    diag_every=int(diag_every), variant=L.VARIANT_FUSED if variant == "fused" else L.VARIANT_PLAIN,
+                    diag_every=int(diag_every), variant={"fused": L.VARIANT_FUSED, "plain": L.VARIANT_PLAIN,
+                                                            "rows": L.VARIANT_ROWS}[variant],
                     cheb_tol=float(cheb_tol))
 
 
@@ -236,9 +237,9 @@ class Plan:
     def degree(self, i, dz, cheb_tol=0.0):
         return int(_lib().decbpm_plan_degree(self._h, i, float(dz), self.precision, float(cheb_tol)))
 
-    def propagate(self, psis, dz, n_steps, diag_every=0, kerr="lumped", cheb_tol=0.0, stream=None):
+    def propagate(self, psis, dz, n_steps, diag_every=0, kerr="lumped", cheb_tol=0.0, stream=None, variant="fused"):
         lib = _lib()
-        prm = _params(dz, n_steps, self.precision, kerr, diag_every, "fused", cheb_tol)
+        prm = _params(dz, n_steps, self.precision, kerr, diag_every, variant, cheb_tol)
         npts = _n_diag(n_steps, diag_every)
         nrec = npts * sum(self.fields)
         buf = (L.Diag * nrec)()
@@ -246,9 +247,10 @@ class Plan:
         L.check(lib.decbpm_plan_propagate(self._h, ctypes.byref(prm), ptrs, _stream_handle(stream), buf))
         return _diag_array(buf, npts, sum(self.fields))
 
-    def propagate_host(self, psis_host, dz, n_steps, diag_every=0, kerr="lumped", cheb_tol=0.0, stream=None):
+    def propagate_host(self, psis_host, dz, n_steps, diag_every=0, kerr="lumped", cheb_tol=0.0, stream=None,
+                       variant="fused"):
         lib = _lib()
-        prm = _params(dz, n_steps, self.precision, kerr, diag_every, "fused", cheb_tol)
+        prm = _params(dz, n_steps, self.precision, kerr, diag_every, variant, cheb_tol)
         npts = _n_diag(n_steps, diag_every)
         buf = (L.Diag * (npts * sum(self.fields)))()
         ptrs = (ctypes.c_void_p * len(psis_host))(*[p.data_ptr() for p in psis_host])

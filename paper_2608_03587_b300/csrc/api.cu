@@ -84,8 +84,75 @@ struct decbpm_mesh_s {
     int32_t *csr_ptr = nullptr, *csr_col = nullptr;
     double *csr_val = nullptr;
     std::map<std::pair<int, int>, decbpm_plan_t> plans;   // (fields, precision) -> cached single-mesh plan
+    // tile maps of the tile-staged march (built on first use)
+    bool tiles_ready = false;
+    uint16_t *lcol = nullptr;
+    int32_t *tdesc = nullptr, *halo_rows = nullptr;
+    int n_tiles = 0, max_halo = 0, max_entries = 0;
     double r() const { return 0.5 * A.rho; }
 };
+
+// Per 128-row tile: the sorted rows outside the tile that its SELL entries
+// reference (halo), for every entry its row in the tile's window (tile rows
+// 0..127, then halo rows), and a descriptor of 8 int32:
+//   {e0, ne, h0, nh, es0 | es1 << 16, es2 | es3 << 16, w0 | w1 << 8 | w2 << 16 | w3 << 24, 0}
+// (first entry and entry count, halo list offset and length, per-slice entry
+// offsets relative to e0 and widths).  Padding entries point inside the
+// tile, so every window row a kernel reads was copied in.
+static int build_tiles(decbpm_mesh_t M) {
+    if (M->tiles_ready) return DECBPM_OK;
+    const Sell &S = M->S;
+    const int64_t n0 = M->A.n0;
+    const int nt = int((n0 + kTileRows - 1) / kTileRows);
+    constexpr int spt = kTileRows / kSlice;
+    static_assert(spt == 4, "descriptor packs four slices");
+    std::vector<uint16_t> lcol(S.col.size(), 0);
+    std::vector<int32_t> desc(size_t(nt) * 8, 0), hrows;
+    std::vector<int32_t> uniq;
+    int max_halo = 0, max_entries = 0;
+    for (int t = 0; t < nt; ++t) {
+        const int64_t r0 = int64_t(t) * kTileRows, r1 = std::min<int64_t>(r0 + kTileRows, n0);
+        const int64_t s0 = int64_t(t) * spt, s1 = std::min<int64_t>(s0 + spt, S.n_slices);
+        const int64_t e0 = S.slice_ptr[s0], e1 = S.slice_ptr[s1];
+        if (e1 - e0 > 65535) return fail(DECBPM_ERR_UNSUPPORTED, "tile %d has %lld SELL entries", t, (long long)(e1 - e0));
+        uniq.clear();
+        for (int64_t e = e0; e < e1; ++e)
+            if (S.col[e] < r0 || S.col[e] >= r1) uniq.push_back(S.col[e]);
+        std::sort(uniq.begin(), uniq.end());
+        uniq.erase(std::unique(uniq.begin(), uniq.end()), uniq.end());
+        if (kTileRows + uniq.size() > 65535) return fail(DECBPM_ERR_UNSUPPORTED, "tile %d has %zu halo rows", t, uniq.size());
+        for (int64_t e = e0; e < e1; ++e) {
+            const int32_t q = S.col[e];
+            if (q >= r0 && q < r1) lcol[e] = uint16_t(q - r0);
+            else lcol[e] = uint16_t(kTileRows + (std::lower_bound(uniq.begin(), uniq.end(), q) - uniq.begin()));
+        }
+        int32_t *d = &desc[size_t(t) * 8];
+        d[0] = int32_t(e0);
+        d[1] = int32_t(e1 - e0);
+        d[2] = int32_t(hrows.size());
+        d[3] = int32_t(uniq.size());
+        uint32_t es[4] = {0, 0, 0, 0}, w[4] = {0, 0, 0, 0};
+        for (int64_t sl = s0; sl < s1; ++sl) {
+            if (S.slice_w[sl] > 255) return fail(DECBPM_ERR_UNSUPPORTED, "slice %lld is wider than 255", (long long)sl);
+            es[sl - s0] = uint32_t(S.slice_ptr[sl] - e0);
+            w[sl - s0] = uint32_t(S.slice_w[sl]);
+        }
+        d[4] = int32_t(es[0] | es[1] << 16);
+        d[5] = int32_t(es[2] | es[3] << 16);
+        d[6] = int32_t(w[0] | w[1] << 8 | w[2] << 16 | w[3] << 24);
+        hrows.insert(hrows.end(), uniq.begin(), uniq.end());
+        max_halo = std::max(max_halo, int(uniq.size()));
+        max_entries = std::max(max_entries, int(e1 - e0));
+    }
+    TRY(M->mem.upload(&M->lcol, lcol));
+    TRY(M->mem.upload(&M->tdesc, desc));
+    TRY(M->mem.upload(&M->halo_rows, hrows));
+    M->n_tiles = nt;
+    M->max_halo = max_halo;
+    M->max_entries = max_entries;
+    M->tiles_ready = true;
+    return DECBPM_OK;
+}
 
 static int mesh_upload(decbpm_mesh_t M) {
     const Assembly &A = M->A;
@@ -184,8 +251,14 @@ struct decbpm_plan_s {
     std::vector<int> order, M, item_begin, items;
     std::vector<double> theta0;                   // per mesh: phase left out of the step coefficients
     int S = 0, total_items = 0;
+    // tile-staged march (complex64 with 9..16 fields)
+    bool tile_mode = false;
+    int tile_grid = 0, n_slots = 0, slot_bytes = 0, off_psi = 0, off_h = 0, off_lcol = 0, off_x = 0, off_hdr = 0;
+    std::vector<int> tile_begin;
+    int32_t *active_tiles = nullptr;
+    int active_tiles_cap = 0, total_tiles = 0;
     // graphs: key -> exec
-    std::map<std::tuple<double, int64_t, int32_t, int32_t, double>, cudaGraphExec_t> graphs;
+    std::map<std::tuple<double, int64_t, int32_t, int32_t, double, int32_t>, cudaGraphExec_t> graphs;
     bool graphs_ok = true;
     ~decbpm_plan_s() {
         for (auto &g : graphs) cudaGraphExecDestroy(g.second);
@@ -230,6 +303,44 @@ template <typename R> static const void *march_ptr_for(int bpad) {
 
 static const void *march_kernel_ptr(int precision, int bpad) {
     return precision == DECBPM_C64 ? march_ptr_for<float>(bpad) : march_ptr_for<double>(bpad);
+}
+
+// Shared-memory ring of the tile-staged march: as many slots (3, else 2) of
+// the largest tile window of the plan's meshes as fit next to the kernel's
+// static shared memory.  Plans it does not fit keep the row kernel.
+static int setup_tiles(decbpm_plan_t P) {
+    P->tile_mode = false;
+    if (P->precision != DECBPM_C64 || P->bpad != 16) return DECBPM_OK;
+    int max_halo = 0, max_entries = 0;
+    for (decbpm_mesh_t m : P->meshes) {
+        TRY(build_tiles(m));
+        max_halo = std::max(max_halo, m->max_halo);
+        max_entries = std::max(max_entries, m->max_entries);
+    }
+    auto up = [](int x) { return (x + 127) / 128 * 128; };
+    const int row = 16 * 8;
+    P->off_psi = up((kTileRows + max_halo) * row);
+    P->off_h = P->off_psi + kTileRows * row;
+    P->off_lcol = P->off_h + kTileRows * row;
+    P->off_x = P->off_lcol + up(max_entries * 2);
+    P->off_hdr = P->off_x + up(max_entries * 4);
+    P->slot_bytes = P->off_hdr + 128;
+    cudaFuncAttributes fa{};
+    CK(cudaFuncGetAttributes(&fa, (const void *)march_tile_kernel));
+    int optin = 0;
+    CK(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, P->device));
+    const int avail = optin - int(fa.sharedSizeBytes);
+    P->n_slots = avail >= 3 * P->slot_bytes ? 3 : avail >= 2 * P->slot_bytes ? 2 : 0;
+    if (P->n_slots == 0) return DECBPM_OK;
+    const int dyn = P->n_slots * P->slot_bytes;
+    // the attribute is per function, not per plan: allow the largest ring any plan may use
+    CK(cudaFuncSetAttribute((const void *)march_tile_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, avail));
+    int per_sm = 0;
+    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void *)march_tile_kernel, kTileThreads, dyn));
+    if (per_sm < 1) return DECBPM_OK;
+    P->tile_grid = P->num_sms * per_sm;
+    P->tile_mode = true;
+    return DECBPM_OK;
 }
 
 static int plan_create_impl(const decbpm_mesh_t *meshes, int32_t n, const int32_t *fields, int32_t precision,
@@ -288,6 +399,7 @@ static int plan_create_impl(const decbpm_mesh_t *meshes, int32_t n, const int32_
     CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, march_kernel_ptr(precision, P->bpad), P->block, 0));
     if (per_sm < 1) return fail(DECBPM_ERR_CUDA, "march kernel cannot be resident with %d threads", P->block);
     P->grid = P->num_sms * std::min(per_sm, 4);
+    TRY(setup_tiles(P.get()));
     *out = P.release();
     return DECBPM_OK;
 }
@@ -319,6 +431,24 @@ static int plan_configure(decbpm_plan_t P, double dz, double tol) {
         acc += P->items[i];
     }
     P->total_items = acc;
+    std::vector<int32_t> active_t(P->S, 0);
+    if (P->tile_mode) {
+        P->tile_begin.assign(n, 0);
+        int tacc = 0;
+        for (int j = 0; j < n; ++j) {
+            const int i = P->order[j];
+            P->tile_begin[i] = tacc;
+            tacc += P->meshes[i]->n_tiles;
+        }
+        P->total_tiles = tacc;
+        for (int s = 0; s < P->S; ++s)
+            for (int j = 0; j < n; ++j)
+                if (ch[P->order[j]].M > P->S - 1 - s) active_t[s] += P->meshes[P->order[j]]->n_tiles;
+        if (P->S > P->active_tiles_cap) {
+            TRY(P->mem.alloc(&P->active_tiles, P->S));
+            P->active_tiles_cap = P->S;
+        }
+    }
     std::vector<int32_t> active(P->S);
     for (int s = 0; s < P->S; ++s) {
         const int k = P->S - 1 - s;
@@ -400,8 +530,15 @@ static int plan_configure(decbpm_plan_t P, double dz, double tol) {
         v.psi = (C *)P->psi[i];
         v.b[0] = (C *)P->b0[i]; v.b[1] = (C *)P->b1[i]; v.b[2] = (C *)P->b2[i];
         v.coef = (const StageCoef<R> *)P->coef + off;
+        if (P->tile_mode) {
+            v.lcol = m->lcol;
+            v.tdesc = m->tdesc;
+            v.halo_rows = m->halo_rows;
+            v.tile_begin = P->tile_begin[i];
+        }
         off += Mi;
     }
+    if (P->tile_mode) CK(cudaMemcpy(P->active_tiles, active_t.data(), sizeof(int32_t) * P->S, cudaMemcpyHostToDevice));
     CK(cudaMemcpy(P->coef, coef.data(), sizeof(StageCoef<R>) * total_coef, cudaMemcpyHostToDevice));
     CK(cudaMemcpy(P->active, active.data(), sizeof(int32_t) * P->S, cudaMemcpyHostToDevice));
     CK(cudaMemcpy(P->views, views.data(), sizeof(MeshView<R>) * n, cudaMemcpyHostToDevice));
@@ -413,7 +550,7 @@ static int plan_configure(decbpm_plan_t P, double dz, double tol) {
 }
 
 template <typename R>
-static int launch_march(decbpm_plan_t P, cudaStream_t s, int n_steps, int kerr_mode, double dz) {
+static int launch_march(decbpm_plan_t P, cudaStream_t s, int n_steps, int kerr_mode, double dz, int variant) {
     MarchParams<R> mp{};
     mp.meshes = (const MeshView<R> *)P->views;
     mp.active_items = P->active;
@@ -441,7 +578,24 @@ static int launch_march(decbpm_plan_t P, cudaStream_t s, int n_steps, int kerr_m
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     void *args[] = {&mp};
-    CK(cudaLaunchKernelExC(&cfg, march_ptr_for<R>(P->bpad), args));
+    const void *fn = march_ptr_for<R>(P->bpad);
+    if constexpr (sizeof(R) == 4) {
+        if (P->tile_mode && variant == DECBPM_VARIANT_FUSED) {
+            mp.active_tiles = P->active_tiles;
+            mp.n_slots = P->n_slots;
+            mp.slot_bytes = P->slot_bytes;
+            mp.off_psi = P->off_psi;
+            mp.off_h = P->off_h;
+            mp.off_lcol = P->off_lcol;
+            mp.off_x = P->off_x;
+            mp.off_hdr = P->off_hdr;
+            cfg.gridDim = dim3(P->tile_grid);
+            cfg.blockDim = dim3(kTileThreads);
+            cfg.dynamicSmemBytes = size_t(P->n_slots) * P->slot_bytes;
+            fn = (const void *)march_tile_kernel;
+        }
+    }
+    CK(cudaLaunchKernelExC(&cfg, fn, args));
     return DECBPM_OK;
 }
 
@@ -474,7 +628,7 @@ static int enqueue_march(decbpm_plan_t P, cudaStream_t s, const decbpm_params *p
         const int64_t nb = std::min<int64_t>(every, prm->n_steps - done);
         if (nb > 0x7fffffff) return fail(DECBPM_ERR_INVALID_ARG, "step block too long");
         if (first) CK(cudaEventRecordWithFlags(P->ev0, s, cudaEventRecordExternal));
-        TRY(launch_march<R>(P, s, int(nb), prm->kerr_mode, prm->dz));
+        TRY(launch_march<R>(P, s, int(nb), prm->kerr_mode, prm->dz, prm->variant));
         if (done + nb >= prm->n_steps) CK(cudaEventRecordWithFlags(P->ev1, s, cudaEventRecordExternal));
         first = false;
         done += nb;
@@ -502,7 +656,8 @@ static int check_params(const decbpm_params *p) {
     if (p->precision != DECBPM_C64 && p->precision != DECBPM_C128) return fail(DECBPM_ERR_INVALID_ARG, "bad precision");
     if (p->kerr_mode != DECBPM_KERR_LUMPED && p->kerr_mode != DECBPM_KERR_ELEMENT) return fail(DECBPM_ERR_INVALID_ARG, "bad kerr_mode");
     if (p->diag_every < 0) return fail(DECBPM_ERR_INVALID_ARG, "diag_every < 0");
-    if (p->variant != DECBPM_VARIANT_FUSED && p->variant != DECBPM_VARIANT_PLAIN) return fail(DECBPM_ERR_INVALID_ARG, "bad variant");
+    if (p->variant != DECBPM_VARIANT_FUSED && p->variant != DECBPM_VARIANT_PLAIN && p->variant != DECBPM_VARIANT_ROWS)
+        return fail(DECBPM_ERR_INVALID_ARG, "bad variant");
     if (!(p->cheb_tol >= 0)) return fail(DECBPM_ERR_INVALID_ARG, "cheb_tol < 0");
     return DECBPM_OK;
 }
@@ -558,7 +713,7 @@ static int plan_propagate_impl(decbpm_plan_t P, const decbpm_params *prm, void *
     }
     CK(cudaGetLastError());
     // capture the march + diagnostics once per parameter set, replay afterwards
-    auto key = std::make_tuple(prm->dz, prm->n_steps, prm->diag_every, prm->kerr_mode, default_tol(prm));
+    auto key = std::make_tuple(prm->dz, prm->n_steps, prm->diag_every, prm->kerr_mode, default_tol(prm), prm->variant);
     bool launched = false;
     if (P->graphs_ok) {
         auto it = P->graphs.find(key);
@@ -608,7 +763,7 @@ static int plan_propagate_dispatch(decbpm_plan_t P, const decbpm_params *prm, vo
     for (size_t i = 0; i < P->meshes.size(); ++i)
         if (!psi_dev[i]) return fail(DECBPM_ERR_INVALID_ARG, "psi_dev[%zu] is NULL", i);
     if (prm->precision != P->precision) return fail(DECBPM_ERR_INVALID_ARG, "params precision differs from the plan's");
-    if (prm->variant != DECBPM_VARIANT_FUSED) return fail(DECBPM_ERR_UNSUPPORTED, "plans run the fused variant only");
+    if (prm->variant == DECBPM_VARIANT_PLAIN) return fail(DECBPM_ERR_UNSUPPORTED, "plans run the fused variants only");
     if (P->precision == DECBPM_C64) return plan_propagate_impl<float>(P, prm, psi_dev, (cudaStream_t)stream, diag_out);
     return plan_propagate_impl<double>(P, prm, psi_dev, (cudaStream_t)stream, diag_out);
 }
@@ -1282,6 +1437,9 @@ int decbpm_plan_get_config(decbpm_plan_t P, decbpm_plan_config *cfg) {
     cfg->graphs = (P->graphs_ok && !P->graphs.empty()) ? 1 : 0;
     cfg->stages = P->S;
     cfg->n_meshes = int32_t(P->meshes.size());
+    cfg->tile_slots = P->tile_mode ? P->n_slots : 0;
+    cfg->tile_slot_bytes = P->tile_mode ? P->slot_bytes : 0;
+    cfg->tile_grid = P->tile_mode ? P->tile_grid : 0;
     return DECBPM_OK;
 }
 

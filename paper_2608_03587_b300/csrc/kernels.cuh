@@ -152,6 +152,14 @@ template <typename R> struct MeshView {
     const R *coff, *cdiag;   // element-averaged Kerr operator (SELL) and diagonal
     typename CT<R>::c2 *psi, *b[3];
     const StageCoef<R> *coef;   // [M]: index k
+    // tile-staged march (complex64, 16 fields): per 128-row tile the
+    // neighbour rows outside the tile ("halo", sorted) and each SELL entry's
+    // row in the tile's shared-memory window (tile rows, then halo rows)
+    const uint16_t *lcol;
+    const int32_t *tdesc;    // per tile 8 int32 (TileDesc)
+    const int32_t *halo_rows;
+    int32_t tile_begin;      // first plan-global tile of this mesh
+    int32_t pad_;
 };
 
 template <typename R> struct MarchParams {
@@ -166,6 +174,10 @@ template <typename R> struct MarchParams {
     unsigned long long *barrier; // zeroed before every launch
     int *status;                 // 0, or a DECBPM_ERR_* code written by the device
     long long timeout_ns;        // limit of one barrier wait
+    // tile-staged march only
+    const int32_t *active_tiles; // [S]: tiles of meshes with M > S-1-s
+    int32_t n_slots, slot_bytes; // shared-memory ring of tile windows
+    int32_t off_psi, off_h, off_lcol, off_x, off_hdr;   // areas of a slot (the neighbour window starts at 0)
 };
 
 // ------------------------------------------------------------ grid barrier
@@ -566,6 +578,418 @@ __global__ void __launch_bounds__(256, MarchMinBlocks<R>::value) march_kernel(Ma
             for_my_items(P, s_begin, P.total_items, [&](const MeshView<R> &m, int li) {
                 element_kerr_item<R, FPT>(m, li, h_post, bl, m.b[0], m.psi);
             });
+            if (!grid_barrier(P.barrier, target, P.status, P.timeout_ns)) return;
+        }
+    }
+}
+
+// ------------------------------------------------------------ tile-staged march
+// The same Clenshaw march for complex64 with 16 fields per vertex (128-byte
+// rows), with every operand of a stage staged in shared memory by the bulk
+// copy engine.  A tile is 128 consecutive rows (4 SELL slices) of one mesh.
+// Per tile one slot of a ring holds
+//   [0, (128 + H) rows)   g = b_{k+1} (or psi): the tile's rows, then its halo
+//                         rows (neighbours outside the tile, sorted)
+//   off_psi, off_h        psi and b_{k+2} rows of the tile
+//   off_lcol, off_x       the tile's SELL entries: window row (uint16), x_pq
+//   off_hdr               the tile descriptor's slice offsets and widths
+// Warp specialisation: warps 0..15 compute (8 rows each), warp 16 copies.
+// The copy warp fills slot (seq mod D) once the compute warps released it
+// (`empty` mbarrier, one arrival per compute warp) and signals `full` with
+// the transaction byte count; compute warps wait on `full`.  The copy warp
+// reads the static tile descriptors and halo row lists one to two tiles
+// ahead (and the next stage's first tiles before the grid barrier), so no
+// dependent global load sits in front of a copy or a compute.
+// Lanes: 4 per row.  A lane holds the 16-byte chunks c1 = l + 4 (slot & 1)
+// and c2 = c1 ^ 4 of its row (l = lane & 3, slot = lane >> 2), so a
+// quarter-warp's 128-bit shared loads touch all 32 banks once whatever rows
+// it gathers.
+constexpr int kTileRows = 128;
+constexpr int kTileComputeWarps = 16;
+constexpr int kTileThreads = 32 * (kTileComputeWarps + 1);
+constexpr int kMaxSlots = 4;
+constexpr int kHaloRegs = 3;          // halo rows per copy-warp lane held ahead (96 per tile)
+
+// Static per-tile descriptor (two int4): {e0, ne, h0, nh} and
+// {es0 | es1 << 16, es2 | es3 << 16, w0 | w1 << 8 | w2 << 16 | w3 << 24, 0}
+// with es = first SELL entry of each slice relative to e0, w = slice widths.
+struct TileDesc { int4 a, b; };
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return uint32_t(__cvta_generic_to_shared(p)); }
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint32_t bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, unsigned parity) {
+    unsigned ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Bounded wait for the completion of the phase of parity `parity`: gives up
+// after timeout_ns (or once another CTA reported an error) and records
+// DECBPM_ERR_TIMEOUT.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, unsigned parity, int *status, long long timeout_ns) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const long long t0 = global_ns();
+    for (unsigned spins = 1;; ++spins) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if ((spins & 255u) == 0) {
+            if (*(volatile int *)status != 0) return false;
+            if (global_ns() - t0 > timeout_ns) {
+                atomicCAS(status, 0, -4);
+                return false;
+            }
+        }
+    }
+}
+// global -> shared bulk copy (16-byte aligned addresses, size a multiple of 16)
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, unsigned bytes, uint32_t bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 ::"r"(dst), "l"(src), "r"(bytes), "r"(bar) : "memory");
+}
+// order this thread's generic-proxy global accesses with its async-proxy ones
+__device__ __forceinline__ void fence_proxy_async_global() { asm volatile("fence.proxy.async.global;" ::: "memory"); }
+
+__device__ __forceinline__ int mesh_of_tile(const int32_t *s_tbeg, int n_meshes, int t) {
+    int mi = 0;
+    while (mi + 1 < n_meshes && t >= s_tbeg[mi + 1]) ++mi;
+    return mi;
+}
+
+// The tiles of stage s that this CTA walks: [lo, hi), backwards on odd k.
+struct TileRange {
+    int lo, n;
+    bool rev;
+    __device__ int at(int i) const { return rev ? lo + n - 1 - i : lo + i; }
+};
+__device__ __forceinline__ TileRange tile_range(const MarchParams<float> &P, int s) {
+    const int n_act = __ldg(P.active_tiles + s);
+    const int lo = int((long long)n_act * blockIdx.x / gridDim.x);
+    const int hi = int((long long)n_act * (blockIdx.x + 1) / gridDim.x);
+    const int k = P.S - 1 - s;
+    return TileRange{lo, hi - lo, DECBPM_REVERSE_ODD && (k & 1)};
+}
+
+// Copy-warp state: descriptors of the next two tiles to fill and the halo
+// rows of the next one.
+struct TileAhead {
+    int4 da, db;        // .a parts (e0, ne, h0, nh); db valid if hb
+    int ta, tb;         // their plan-global tiles
+    bool hb;
+    int halo[kHaloRegs];
+};
+
+__device__ __forceinline__ int4 load_tile_a(const MeshView<float> *sv, const int32_t *s_tbeg, int n_meshes, int t) {
+    const int mi = mesh_of_tile(s_tbeg, n_meshes, t);
+    return __ldg(reinterpret_cast<const int4 *>(sv[mi].tdesc) + 2 * (t - s_tbeg[mi]));
+}
+__device__ __forceinline__ void load_halo(const MeshView<float> *sv, const int32_t *s_tbeg, int n_meshes, int t,
+                                          int4 d, int (&h)[kHaloRegs]) {
+    const int lane = threadIdx.x & 31;
+    const int mi = mesh_of_tile(s_tbeg, n_meshes, t);
+#pragma unroll
+    for (int u = 0; u < kHaloRegs; ++u) {
+        const int j = lane + 32 * u;
+        h[u] = j < d.w ? __ldg(sv[mi].halo_rows + d.z + j) : 0;
+    }
+}
+// Prime the look-ahead with the first two tiles of stage s.
+__device__ __forceinline__ void ahead_start(TileAhead &A, const MarchParams<float> &P, const MeshView<float> *sv,
+                                            const int32_t *s_tbeg, int s) {
+    const TileRange R = tile_range(P, s);
+    A.hb = false;
+    A.ta = -1;
+    if (R.n == 0) return;
+    A.ta = R.at(0);
+    A.da = load_tile_a(sv, s_tbeg, P.n_meshes, A.ta);
+    if (R.n > 1) {
+        A.tb = R.at(1);
+        A.db = load_tile_a(sv, s_tbeg, P.n_meshes, A.tb);
+        A.hb = true;
+    }
+    load_halo(sv, s_tbeg, P.n_meshes, A.ta, A.da, A.halo);
+}
+
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void *src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
+}
+// arrive on `bar` once this thread's earlier cp.async copies have landed
+// (the pending count is raised now and lowered on completion: no net change)
+__device__ __forceinline__ void cp_async_arrive(uint32_t bar) {
+    asm volatile("cp.async.mbarrier.arrive.shared::cta.b64 [%0];" ::"r"(bar) : "memory");
+}
+
+// Copy warp: fill `slot` with everything tile A.ta needs in stage k.  The
+// contiguous blocks (tile rows, SELL entries, descriptor) are bulk copies;
+// the scattered halo rows are 16-byte cp.async copies, eight lanes per row.
+__device__ __forceinline__ void tile_fill(const TileAhead &A, const MeshView<float> *sv, const StageCoef<float> *scoef,
+                                          const int32_t *s_tbeg, int n_meshes, int k, char *slot, uint32_t bar,
+                                          const MarchParams<float> &P) {
+    const int lane = threadIdx.x & 31;
+    const int t = A.ta;
+    const int mi = mesh_of_tile(s_tbeg, n_meshes, t);
+    const MeshView<float> &m = sv[mi];
+    const int flags = scoef[mi].flags;
+    const int tl = t - s_tbeg[mi];
+    const int r0 = tl * kTileRows, nrows = min(kTileRows, m.n0 - r0);
+    const int e0 = A.da.x, ne = A.da.y, h0 = A.da.z, nh = A.da.w;
+    const float2 *g = (flags & kGisPsi) ? m.psi : m.b[(k + 1) % 3];
+    const uint32_t base = smem_u32(slot);
+    // halo rows held ahead: row r = (lane >> 3) + 4u, chunk lane & 7
+#pragma unroll
+    for (int u = 0; u < 8 * kHaloRegs; ++u) {
+        const int r = (lane >> 3) + 4 * u;
+        const int q = __shfl_sync(0xffffffffu, A.halo[u >> 3], r & 31);
+        if (r < nh) cp_async16(base + unsigned(kTileRows + r) * 128u + 16u * (lane & 7), g + (size_t)q * 16 + 2 * (lane & 7));
+    }
+    cp_async_arrive(bar);
+    const int n_bulk_halo = max(nh - 32 * kHaloRegs, 0);
+    const unsigned row_bytes = unsigned(nrows) * 128u;
+    const unsigned total = row_bytes * (1u + ((flags & kGisPsi) ? 0u : 1u) + ((flags & kHasH) ? 1u : 0u)) +
+                           unsigned(ne) * 6u + unsigned(n_bulk_halo) * 128u + 16u;
+    __syncwarp();
+    if (lane == 0) mbar_arrive_expect_tx(bar, total);
+    __syncwarp();
+    fence_proxy_async_global();
+    if (lane == 0) bulk_g2s(base, g + (size_t)r0 * 16, row_bytes, bar);
+    if (lane == 1 && !(flags & kGisPsi)) bulk_g2s(base + P.off_psi, m.psi + (size_t)r0 * 16, row_bytes, bar);
+    if (lane == 2 && (flags & kHasH)) bulk_g2s(base + P.off_h, m.b[(k + 2) % 3] + (size_t)r0 * 16, row_bytes, bar);
+    if (lane == 3 && ne > 0) bulk_g2s(base + P.off_lcol, m.lcol + e0, unsigned(ne) * 2u, bar);
+    if (lane == 4 && ne > 0) bulk_g2s(base + P.off_x, m.xval + e0, unsigned(ne) * 4u, bar);
+    if (lane == 5) bulk_g2s(base + P.off_hdr, reinterpret_cast<const int4 *>(m.tdesc) + 2 * tl + 1, 16u, bar);
+    for (int j = lane + 32 * kHaloRegs; j < nh; j += 32) {      // rare: more halo rows than held ahead
+        const int q = __ldg(m.halo_rows + h0 + j);
+        bulk_g2s(base + unsigned(kTileRows + j) * 128u, g + (size_t)q * 16, 128u, bar);
+    }
+}
+
+// Advance the look-ahead after tile i of range R was filled.
+__device__ __forceinline__ void ahead_next(TileAhead &A, const TileRange &R, int i, const MeshView<float> *sv,
+                                           const int32_t *s_tbeg, int n_meshes) {
+    if (A.hb) {
+        A.ta = A.tb;
+        A.da = A.db;
+        A.hb = false;
+        if (i + 2 < R.n) {
+            A.tb = R.at(i + 2);
+            A.db = load_tile_a(sv, s_tbeg, n_meshes, A.tb);
+            A.hb = true;
+        }
+        load_halo(sv, s_tbeg, n_meshes, A.ta, A.da, A.halo);
+    } else {
+        A.ta = -1;
+    }
+}
+
+__device__ __forceinline__ uint32_t lds_u16(uint32_t addr) {
+    unsigned short v;
+    asm volatile("ld.shared.u16 %0, [%1];" : "=h"(v) : "r"(addr));
+    return v;
+}
+__device__ __forceinline__ float lds_f32(uint32_t addr) {
+    float v;
+    asm volatile("ld.shared.f32 %0, [%1];" : "=f"(v) : "r"(addr));
+    return v;
+}
+__device__ __forceinline__ int4 lds_i4(uint32_t addr) {
+    int4 v;
+    asm volatile("ld.shared.v4.s32 {%0, %1, %2, %3}, [%4];" : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "r"(addr));
+    return v;
+}
+__device__ __forceinline__ void lds_chunk(uint32_t addr, float2 &a, float2 &b) {
+    asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];" : "=f"(a.x), "=f"(a.y), "=f"(b.x), "=f"(b.y) : "r"(addr));
+}
+__device__ __forceinline__ void stg_chunk(float2 *p, float2 a, float2 b) {
+    *reinterpret_cast<float4 *>(p) = make_float4(a.x, a.y, b.x, b.y);
+}
+
+// One compute warp's 8 rows of tile t (resident in `slot`).
+__device__ __forceinline__ void tile_compute(const MeshView<float> *sv, const StageCoef<float> *scoef,
+                                             const int32_t *s_tbeg, int n_meshes, int t, int k, const char *slot,
+                                             float h_post, int kerr_mode, const MarchParams<float> &P) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int mi = mesh_of_tile(s_tbeg, n_meshes, t);
+    const MeshView<float> &m = sv[mi];
+    const StageCoef<float> sc = scoef[mi];
+    const int tl = t - s_tbeg[mi];
+    const int lr = warp * 8 + (lane >> 2);                 // row in the tile
+    const int row = tl * kTileRows + lr;
+    if (row >= m.n0) return;
+    const int c1 = (lane & 3) + 4 * ((lane >> 2) & 1), c2 = c1 ^ 4;
+    const int sl = lr >> 5;
+    const uint32_t base = smem_u32(slot);
+    const int4 hdr = lds_i4(base + P.off_hdr);
+    const int es = ((sl < 2 ? hdr.x : hdr.y) >> (16 * (sl & 1)) & 0xffff) + (lr & 31);
+    const int width = (hdr.z >> (8 * sl)) & 0xff;
+    const uint32_t gw = base;                              // neighbour window
+    const uint32_t pw = (sc.flags & kGisPsi) ? base : base + P.off_psi;
+    const uint32_t lc = base + P.off_lcol + 2 * es;      // entry (row, j) at lc + 64 j
+    const uint32_t xs = base + P.off_x + 4 * es;         // and xs + 128 j
+    float2 gp[4], ps[4], hh[4], acc[4];
+    lds_chunk(gw + lr * 128 + 16 * c1, gp[0], gp[1]);
+    lds_chunk(gw + lr * 128 + 16 * c2, gp[2], gp[3]);
+    lds_chunk(pw + lr * 128 + 16 * c1, ps[0], ps[1]);
+    lds_chunk(pw + lr * 128 + 16 * c2, ps[2], ps[3]);
+    if (sc.flags & kHasH) {
+        lds_chunk(base + P.off_h + lr * 128 + 16 * c1, hh[0], hh[1]);
+        lds_chunk(base + P.off_h + lr * 128 + 16 * c2, hh[2], hh[3]);
+    }
+#pragma unroll
+    for (int f = 0; f < 4; ++f) acc[f] = make_float2(0.f, 0.f);
+    int j = 0;
+    for (; j + 4 <= width; j += 4) {
+        float2 gq[4][4];
+        float xv[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const uint32_t q = lds_u16(lc + 64 * (j + u));
+            xv[u] = lds_f32(xs + 128 * (j + u));
+            lds_chunk(gw + q * 128 + 16 * c1, gq[u][0], gq[u][1]);
+            lds_chunk(gw + q * 128 + 16 * c2, gq[u][2], gq[u][3]);
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int f = 0; f < 4; ++f) acc[f] = cfma(xv[u], csub(gp[f], gq[u][f]), acc[f]);
+    }
+    for (; j < width; ++j) {
+        float2 gq[4];
+        const uint32_t q = lds_u16(lc + 64 * j);
+        const float xv = lds_f32(xs + 128 * j);
+        lds_chunk(gw + q * 128 + 16 * c1, gq[0], gq[1]);
+        lds_chunk(gw + q * 128 + 16 * c2, gq[2], gq[3]);
+#pragma unroll
+        for (int f = 0; f < 4; ++f) acc[f] = cfma(xv, csub(gp[f], gq[f]), acc[f]);
+    }
+    float2 out[4];
+#pragma unroll
+    for (int f = 0; f < 4; ++f) {
+        float2 tt = cmul(sc.alpha, ps[f]);
+        if (sc.flags & kFinal) tt = cadd(tt, cmul(sc.alpha_lo, ps[f]));
+        out[f] = cadd(tt, cmul(sc.beta, csub(acc[f], gp[f])));
+        if (sc.flags & kHasH) out[f] = csub(out[f], hh[f]);
+    }
+    float2 *dst;
+    if (sc.flags & kFinal) {
+        if (kerr_mode == 0) {
+            float em, phi;
+            diag_factors(__ldg(m.sigma + row), h_post, em, phi);
+            const float vv = __ldg(m.v + row), cb = __ldg(m.chib + row);
+#pragma unroll
+            for (int f = 0; f < 4; ++f) out[f] = diag_apply(out[f], vv, cb, h_post, em, phi);
+            dst = m.psi;
+        } else {
+            dst = m.b[0];        // element-averaged Kerr needs the neighbours' |S|^2: park S in b[0]
+        }
+    } else {
+        dst = m.b[k % 3];
+    }
+    stg_chunk(dst + (size_t)row * 16 + 2 * c1, out[0], out[1]);
+    stg_chunk(dst + (size_t)row * 16 + 2 * c2, out[2], out[3]);
+}
+
+__global__ void __launch_bounds__(kTileThreads, 1) march_tile_kernel(MarchParams<float> P) {
+    constexpr int FPT = Geo<float, 16>::FPT;
+    extern __shared__ __align__(128) char s_ring[];
+    __shared__ int32_t s_begin[kMaxMeshes + 1];
+    __shared__ int32_t s_tbeg[kMaxMeshes + 1];
+    __shared__ MeshView<float> s_view[kMaxMeshes];
+    __shared__ StageCoef<float> s_coef[kMaxMeshes];
+    __shared__ __align__(8) unsigned long long s_full[kMaxSlots], s_empty[kMaxSlots];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const bool copier = warp == kTileComputeWarps;
+    for (int i = threadIdx.x; i < P.n_meshes; i += blockDim.x) {
+        s_begin[i] = P.meshes[i].item_begin;
+        s_tbeg[i] = P.meshes[i].tile_begin;
+        s_view[i] = P.meshes[i];
+    }
+    if (threadIdx.x < P.n_slots) {
+        mbar_init(smem_u32(&s_full[threadIdx.x]), 1);
+        mbar_init(smem_u32(&s_empty[threadIdx.x]), kTileComputeWarps);
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    __syncthreads();
+    unsigned long long target = 0;
+    const float h = P.h, hh = P.h * 0.5f;
+    const int bl = Geo<float, 16>::TPR_LOG2 + Geo<float, 16>::FPT_LOG2;
+    const unsigned D = unsigned(P.n_slots);
+    unsigned seq = 0;                                      // tiles filled / consumed so far by this CTA
+    TileAhead A;
+    if (copier) ahead_start(A, P, s_view, s_tbeg, 0);
+    for (int step = 0; step < P.n_steps; ++step) {
+        if (step == 0 && P.pre_half) {
+            if (P.kerr_mode == 0) {
+                for_my_items(P, s_begin, P.total_items, [&](const MeshView<float> &m, int li) {
+                    lumped_diag_item<float, FPT>(m, li, hh, bl);
+                });
+                fence_proxy_async_global();
+                if (!grid_barrier(P.barrier, target, P.status, P.timeout_ns)) return;
+            } else {
+                for_my_items(P, s_begin, P.total_items, [&](const MeshView<float> &m, int li) {
+                    element_kerr_item<float, FPT>(m, li, hh, bl, m.psi, m.b[0]);
+                });
+                if (!grid_barrier(P.barrier, target, P.status, P.timeout_ns)) return;
+                for_my_items(P, s_begin, P.total_items, [&](const MeshView<float> &m, int li) {
+                    copy_item<float, FPT>(m, li, bl, m.b[0], m.psi);
+                });
+                fence_proxy_async_global();
+                if (!grid_barrier(P.barrier, target, P.status, P.timeout_ns)) return;
+            }
+        }
+        const float h_post = (step == P.n_steps - 1 && P.post_half) ? hh : h;
+        for (int s = 0; s < P.S; ++s) {
+            const int k = P.S - 1 - s;
+            for (int i = threadIdx.x; i < P.n_meshes; i += blockDim.x)
+                if (s_view[i].M > k) s_coef[i] = s_view[i].coef[k];
+            __syncthreads();
+            const TileRange R = tile_range(P, s);
+            bool ok = true;
+            if (copier) {
+                for (int i = 0; i < R.n && ok; ++i) {
+                    const unsigned q = seq + unsigned(i), sl = q % D;
+                    if (q >= D) ok = mbar_wait(smem_u32(&s_empty[sl]), ((q / D) - 1u) & 1u, P.status, P.timeout_ns);
+                    if (ok) {
+                        tile_fill(A, s_view, s_coef, s_tbeg, P.n_meshes, k, s_ring + (size_t)sl * P.slot_bytes,
+                                  smem_u32(&s_full[sl]), P);
+                        ahead_next(A, R, i, s_view, s_tbeg, P.n_meshes);
+                    }
+                }
+                // the next stage's first tiles: their descriptors do not depend on this stage
+                if (ok) ahead_start(A, P, s_view, s_tbeg, s + 1 < P.S ? s + 1 : 0);
+            } else {
+                for (int i = 0; i < R.n && ok; ++i) {
+                    const unsigned q = seq + unsigned(i), sl = q % D;
+                    ok = mbar_wait(smem_u32(&s_full[sl]), (q / D) & 1u, P.status, P.timeout_ns);
+                    if (ok) {
+                        tile_compute(s_view, s_coef, s_tbeg, P.n_meshes, R.at(i), k,
+                                     s_ring + (size_t)sl * P.slot_bytes, h_post, P.kerr_mode, P);
+                        __syncwarp();
+                        if (lane == 0) mbar_arrive(smem_u32(&s_empty[sl]));
+                    }
+                }
+            }
+            seq += unsigned(R.n);
+            if (!ok) return;
+            fence_proxy_async_global();
+            if (!grid_barrier(P.barrier, target, P.status, P.timeout_ns)) return;
+        }
+        if (P.kerr_mode != 0) {
+            for_my_items(P, s_begin, P.total_items, [&](const MeshView<float> &m, int li) {
+                element_kerr_item<float, FPT>(m, li, h_post, bl, m.b[0], m.psi);
+            });
+            fence_proxy_async_global();
             if (!grid_barrier(P.barrier, target, P.status, P.timeout_ns)) return;
         }
     }
