@@ -55,6 +55,7 @@ extern "C" {
 #define DECBPM_ERR_CUDA          -5   /* a CUDA runtime call failed */
 #define DECBPM_ERR_OOM           -6   /* device or host allocation failed */
 #define DECBPM_ERR_UNSUPPORTED   -7   /* valid request that this build does not implement */
+#define DECBPM_ERR_DEVICE_CHECK  -8   /* a device-side consistency check failed; the kernel skipped the work */
 
 /* ---- enumerations -------------------------------------------------------- */
 #define DECBPM_C64   1   /* complex64 field, FP32 arithmetic, FP64 diagnostics */

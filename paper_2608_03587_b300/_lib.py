@@ -21,6 +21,7 @@ ERR_TIMEOUT = -4
 ERR_CUDA = -5
 ERR_OOM = -6
 ERR_UNSUPPORTED = -7
+ERR_DEVICE_CHECK = -8
 C64 = 1
 C128 = 2
 KERR_LUMPED = 0

@@ -85,29 +85,34 @@ struct decbpm_mesh_s {
     double *csr_val = nullptr;
     std::map<std::pair<int, int>, decbpm_plan_t> plans;   // (fields, precision) -> cached single-mesh plan
     // tile maps of the tile-staged march (built on first use)
-    bool tiles_ready = false;
+    bool tiles_ready = false, tiles_ok = false;
     uint16_t *lcol = nullptr;
-    int32_t *tdesc = nullptr, *halo_rows = nullptr;
+    int32_t *tdesc = nullptr, *halo_rows = nullptr, *halo_ovf = nullptr;
     int n_tiles = 0, max_halo = 0, max_entries = 0;
     double r() const { return 0.5 * A.rho; }
 };
 
 // Per 128-row tile: the sorted rows outside the tile that its SELL entries
-// reference (halo), for every entry its row in the tile's window (tile rows
-// 0..127, then halo rows), and a descriptor of 8 int32:
-//   {e0, ne, h0, nh, es0 | es1 << 16, es2 | es3 << 16, w0 | w1 << 8 | w2 << 16 | w3 << 24, 0}
-// (first entry and entry count, halo list offset and length, per-slice entry
-// offsets relative to e0 and widths).  Padding entries point inside the
-// tile, so every window row a kernel reads was copied in.
+// reference (halo; the first 96 at rows [96 t, 96 t + 96) of a padded list,
+// the rest in an overflow list), for every entry its row in the tile's
+// window (tile rows 0..127, then halo rows), and a descriptor of 8 int32:
+//   {e0, ne, ovf, nh, es0 | es1 << 16, es2 | es3 << 16, w0 | w1 << 8 | w2 << 16 | w3 << 24, 0}
+// (first entry and entry count, overflow offset and halo length, per-slice
+// entry offsets relative to e0 and widths).  An entry's window row is stored as
+// its byte offset (row * 128, 16 fields of complex64), so windows are
+// limited to 511 rows; meshes with larger halos keep the row kernel.
+// Padding entries point inside the tile, so every window row a kernel reads
+// was copied in.
 static int build_tiles(decbpm_mesh_t M) {
     if (M->tiles_ready) return DECBPM_OK;
     const Sell &S = M->S;
     const int64_t n0 = M->A.n0;
     const int nt = int((n0 + kTileRows - 1) / kTileRows);
     constexpr int spt = kTileRows / kSlice;
+    constexpr int held = 32 * kHaloRegs;                 // halo rows per tile at a fixed place
     static_assert(spt == 4, "descriptor packs four slices");
     std::vector<uint16_t> lcol(S.col.size(), 0);
-    std::vector<int32_t> desc(size_t(nt) * 8, 0), hrows;
+    std::vector<int32_t> desc(size_t(nt) * 8, 0), hfixed(size_t(nt) * held, 0), hovf;
     std::vector<int32_t> uniq;
     int max_halo = 0, max_entries = 0;
     for (int t = 0; t < nt; ++t) {
@@ -120,16 +125,21 @@ static int build_tiles(decbpm_mesh_t M) {
             if (S.col[e] < r0 || S.col[e] >= r1) uniq.push_back(S.col[e]);
         std::sort(uniq.begin(), uniq.end());
         uniq.erase(std::unique(uniq.begin(), uniq.end()), uniq.end());
-        if (kTileRows + uniq.size() > 65535) return fail(DECBPM_ERR_UNSUPPORTED, "tile %d has %zu halo rows", t, uniq.size());
+        if ((kTileRows + uniq.size()) * 128 > 65535) {   // window offsets must fit 16 bits: keep the row kernel
+            M->tiles_ready = true;
+            M->tiles_ok = false;
+            return DECBPM_OK;
+        }
         for (int64_t e = e0; e < e1; ++e) {
             const int32_t q = S.col[e];
-            if (q >= r0 && q < r1) lcol[e] = uint16_t(q - r0);
-            else lcol[e] = uint16_t(kTileRows + (std::lower_bound(uniq.begin(), uniq.end(), q) - uniq.begin()));
+            const int64_t w = (q >= r0 && q < r1) ? q - r0
+                                                  : kTileRows + (std::lower_bound(uniq.begin(), uniq.end(), q) - uniq.begin());
+            lcol[e] = uint16_t(w * 128);                    // byte offset of the row in the window
         }
         int32_t *d = &desc[size_t(t) * 8];
         d[0] = int32_t(e0);
         d[1] = int32_t(e1 - e0);
-        d[2] = int32_t(hrows.size());
+        d[2] = int32_t(hovf.size());
         d[3] = int32_t(uniq.size());
         uint32_t es[4] = {0, 0, 0, 0}, w[4] = {0, 0, 0, 0};
         for (int64_t sl = s0; sl < s1; ++sl) {
@@ -140,17 +150,22 @@ static int build_tiles(decbpm_mesh_t M) {
         d[4] = int32_t(es[0] | es[1] << 16);
         d[5] = int32_t(es[2] | es[3] << 16);
         d[6] = int32_t(w[0] | w[1] << 8 | w[2] << 16 | w[3] << 24);
-        hrows.insert(hrows.end(), uniq.begin(), uniq.end());
+        for (size_t j = 0; j < uniq.size(); ++j) {
+            if (j < size_t(held)) hfixed[size_t(t) * held + j] = uniq[j];
+            else hovf.push_back(uniq[j]);
+        }
         max_halo = std::max(max_halo, int(uniq.size()));
         max_entries = std::max(max_entries, int(e1 - e0));
     }
     TRY(M->mem.upload(&M->lcol, lcol));
     TRY(M->mem.upload(&M->tdesc, desc));
-    TRY(M->mem.upload(&M->halo_rows, hrows));
+    TRY(M->mem.upload(&M->halo_rows, hfixed));
+    TRY(M->mem.upload(&M->halo_ovf, hovf));
     M->n_tiles = nt;
     M->max_halo = max_halo;
     M->max_entries = max_entries;
     M->tiles_ready = true;
+    M->tiles_ok = true;
     return DECBPM_OK;
 }
 
@@ -254,6 +269,7 @@ struct decbpm_plan_s {
     // tile-staged march (complex64 with 9..16 fields)
     bool tile_mode = false;
     int tile_grid = 0, n_slots = 0, slot_bytes = 0, off_psi = 0, off_h = 0, off_lcol = 0, off_x = 0, off_hdr = 0;
+    int slot_entries = 0;
     std::vector<int> tile_begin;
     int32_t *active_tiles = nullptr;
     int active_tiles_cap = 0, total_tiles = 0;
@@ -314,6 +330,7 @@ static int setup_tiles(decbpm_plan_t P) {
     int max_halo = 0, max_entries = 0;
     for (decbpm_mesh_t m : P->meshes) {
         TRY(build_tiles(m));
+        if (!m->tiles_ok) return DECBPM_OK;
         max_halo = std::max(max_halo, m->max_halo);
         max_entries = std::max(max_entries, m->max_entries);
     }
@@ -324,6 +341,7 @@ static int setup_tiles(decbpm_plan_t P) {
     P->off_lcol = P->off_h + kTileRows * row;
     P->off_x = P->off_lcol + up(max_entries * 2);
     P->off_hdr = P->off_x + up(max_entries * 4);
+    P->slot_entries = max_entries;
     P->slot_bytes = P->off_hdr + 128;
     cudaFuncAttributes fa{};
     CK(cudaFuncGetAttributes(&fa, (const void *)march_tile_kernel));
@@ -534,6 +552,7 @@ static int plan_configure(decbpm_plan_t P, double dz, double tol) {
             v.lcol = m->lcol;
             v.tdesc = m->tdesc;
             v.halo_rows = m->halo_rows;
+            v.halo_ovf = m->halo_ovf;
             v.tile_begin = P->tile_begin[i];
         }
         off += Mi;
@@ -589,6 +608,7 @@ static int launch_march(decbpm_plan_t P, cudaStream_t s, int n_steps, int kerr_m
             mp.off_lcol = P->off_lcol;
             mp.off_x = P->off_x;
             mp.off_hdr = P->off_hdr;
+            mp.slot_entries = P->slot_entries;
             cfg.gridDim = dim3(P->tile_grid);
             cfg.blockDim = dim3(kTileThreads);
             cfg.dynamicSmemBytes = size_t(P->n_slots) * P->slot_bytes;

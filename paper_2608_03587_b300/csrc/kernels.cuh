@@ -82,6 +82,11 @@ __device__ __forceinline__ float2 cscale(float2 a, float s) {
 }
 #endif
 
+// complex64 product with a fixed evaluation order (the tile-staged kernel
+// forms the same roundings with packed instructions)
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+    return make_float2(__fmaf_rn(-a.y, b.y, __fmul_rn(a.x, b.x)), __fmaf_rn(a.y, b.x, __fmul_rn(a.x, b.y)));
+}
 __device__ __forceinline__ void sincos_r(float x, float *s, float *c) { sincosf(x, s, c); }
 __device__ __forceinline__ void sincos_r(double x, double *s, double *c) { sincos(x, s, c); }
 __device__ __forceinline__ float exp_r(float x) { return expf(x); }
@@ -157,7 +162,8 @@ template <typename R> struct MeshView {
     // row in the tile's shared-memory window (tile rows, then halo rows)
     const uint16_t *lcol;
     const int32_t *tdesc;    // per tile 8 int32 (TileDesc)
-    const int32_t *halo_rows;
+    const int32_t *halo_rows; // per tile 96 rows (first 96 halo rows, padded)
+    const int32_t *halo_ovf;  // halo rows beyond the first 96
     int32_t tile_begin;      // first plan-global tile of this mesh
     int32_t pad_;
 };
@@ -178,6 +184,7 @@ template <typename R> struct MarchParams {
     const int32_t *active_tiles; // [S]: tiles of meshes with M > S-1-s
     int32_t n_slots, slot_bytes; // shared-memory ring of tile windows
     int32_t off_psi, off_h, off_lcol, off_x, off_hdr;   // areas of a slot (the neighbour window starts at 0)
+    int32_t slot_entries;        // SELL entries a slot holds
 };
 
 // ------------------------------------------------------------ grid barrier
@@ -593,8 +600,12 @@ __global__ void __launch_bounds__(256, MarchMinBlocks<R>::value) march_kernel(Ma
 //   off_psi, off_h        psi and b_{k+2} rows of the tile
 //   off_lcol, off_x       the tile's SELL entries: window row (uint16), x_pq
 //   off_hdr               the tile descriptor's slice offsets and widths
-// Warp specialisation: warps 0..15 compute (8 rows each), warp 16 copies.
-// The copy warp fills slot (seq mod D) once the compute warps released it
+// Warp specialisation: warps 0..15 compute (8 rows each), warps 16..18 copy.
+// Copy warp c owns ring slot c and fills the tiles with sequence number
+// = c mod D, so copy instructions are spread over three schedulers and each
+// slot's mbarriers are driven by a single producer (a parity wait can only
+// tell the current phase from the previous one).  A copy warp fills
+// slot (seq mod D) once the compute warps released it
 // (`empty` mbarrier, one arrival per compute warp) and signals `full` with
 // the transaction byte count; compute warps wait on `full`.  The copy warp
 // reads the static tile descriptors and halo row lists one to two tiles
@@ -606,11 +617,13 @@ __global__ void __launch_bounds__(256, MarchMinBlocks<R>::value) march_kernel(Ma
 // it gathers.
 constexpr int kTileRows = 128;
 constexpr int kTileComputeWarps = 16;
-constexpr int kTileThreads = 32 * (kTileComputeWarps + 1);
-constexpr int kMaxSlots = 4;
+constexpr int kTileCopyWarps = 3;     // copy warp c owns ring slot c (at most 3 slots)
+constexpr int kTileThreads = 32 * (kTileComputeWarps + kTileCopyWarps);
+constexpr int kMaxSlots = kTileCopyWarps;
 constexpr int kHaloRegs = 3;          // halo rows per copy-warp lane held ahead (96 per tile)
 
-// Static per-tile descriptor (two int4): {e0, ne, h0, nh} and
+// Static per-tile descriptor (two int4): {e0, ne, ovf, nh} (ovf: offset of
+// the halo rows beyond the first 96 in the overflow list) and
 // {es0 | es1 << 16, es2 | es3 << 16, w0 | w1 << 8 | w2 << 16 | w3 << 24, 0}
 // with es = first SELL entry of each slice relative to e0, w = slice widths.
 struct TileDesc { int4 a, b; };
@@ -626,14 +639,17 @@ __device__ __forceinline__ void mbar_arrive_expect_tx(uint32_t bar, unsigned byt
 __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
 }
+// A waiting thread is suspended until the phase completes or about
+// kWaitHintNs passed, so waiting warps do not spin on the issue slots.
+constexpr unsigned kWaitHintNs = 20000;
 __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, unsigned parity) {
     unsigned ok;
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
         "selp.u32 %0, 1, 0, p;\n\t}"
         : "=r"(ok)
-        : "r"(bar), "r"(parity)
+        : "r"(bar), "r"(parity), "n"(kWaitHintNs)
         : "memory");
     return ok != 0;
 }
@@ -654,7 +670,11 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, unsigned parity, int *st
         }
     }
 }
-// global -> shared bulk copy (16-byte aligned addresses, size a multiple of 16)
+// global -> shared bulk copy (16-byte aligned addresses, size a multiple of 16).
+// Field data written with ordinary stores by other CTAs is read by bulk
+// copies (async proxy): writers fence before the grid barrier, the copy warp
+// fences once after it (a fence per copy would wait for its own cp.async
+// copies in flight).
 __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, unsigned bytes, uint32_t bar) {
     asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
                  ::"r"(dst), "l"(src), "r"(bytes), "r"(bar) : "memory");
@@ -682,44 +702,35 @@ __device__ __forceinline__ TileRange tile_range(const MarchParams<float> &P, int
     return TileRange{lo, hi - lo, DECBPM_REVERSE_ODD && (k & 1)};
 }
 
-// Copy-warp state: descriptors of the next two tiles to fill and the halo
-// rows of the next one.
-struct TileAhead {
-    int4 da, db;        // .a parts (e0, ne, h0, nh); db valid if hb
-    int ta, tb;         // their plan-global tiles
-    bool hb;
-    int halo[kHaloRegs];
+// Copy-warp look-ahead: the descriptor and the first 96 halo rows of each
+// of the next kLookAhead tiles to fill are copied (cp.async) into a small
+// shared ring kLookAhead fills before they are used, so no register waits
+// on a load (the halo list of tile t sits at a fixed place, 96 t, so the two
+// loads are independent).  The cursor runs through the same (stage, tile)
+// sequence as the fills, across stage and step boundaries: descriptors are
+// static, only the field copies wait for the grid barrier.
+constexpr int kLookAhead = 4;           // per copy warp, i.e. 4 D tiles ahead
+constexpr int kLookInts = 104;        // 96 halo rows, descriptor (4), tile, pad
+struct LookCursor {
+    int s, i;           // stage and index in the stage's range of the next tile to load
+    TileRange R;
 };
 
-__device__ __forceinline__ int4 load_tile_a(const MeshView<float> *sv, const int32_t *s_tbeg, int n_meshes, int t) {
-    const int mi = mesh_of_tile(s_tbeg, n_meshes, t);
-    return __ldg(reinterpret_cast<const int4 *>(sv[mi].tdesc) + 2 * (t - s_tbeg[mi]));
-}
-__device__ __forceinline__ void load_halo(const MeshView<float> *sv, const int32_t *s_tbeg, int n_meshes, int t,
-                                          int4 d, int (&h)[kHaloRegs]) {
-    const int lane = threadIdx.x & 31;
-    const int mi = mesh_of_tile(s_tbeg, n_meshes, t);
-#pragma unroll
-    for (int u = 0; u < kHaloRegs; ++u) {
-        const int j = lane + 32 * u;
-        h[u] = j < d.w ? __ldg(sv[mi].halo_rows + d.z + j) : 0;
+// Next tile of the fill sequence after the cursor (or -1 if this CTA has
+// none in any stage); advances the cursor.  look_next_n skips n - 1 tiles.
+__device__ __forceinline__ int look_next(LookCursor &c, const MarchParams<float> &P) {
+    for (int guard = 0; guard <= P.S; ++guard) {
+        if (c.i < c.R.n) return c.R.at(c.i++);
+        c.s = c.s + 1 < P.S ? c.s + 1 : 0;
+        c.R = tile_range(P, c.s);
+        c.i = 0;
     }
+    return -1;
 }
-// Prime the look-ahead with the first two tiles of stage s.
-__device__ __forceinline__ void ahead_start(TileAhead &A, const MarchParams<float> &P, const MeshView<float> *sv,
-                                            const int32_t *s_tbeg, int s) {
-    const TileRange R = tile_range(P, s);
-    A.hb = false;
-    A.ta = -1;
-    if (R.n == 0) return;
-    A.ta = R.at(0);
-    A.da = load_tile_a(sv, s_tbeg, P.n_meshes, A.ta);
-    if (R.n > 1) {
-        A.tb = R.at(1);
-        A.db = load_tile_a(sv, s_tbeg, P.n_meshes, A.tb);
-        A.hb = true;
-    }
-    load_halo(sv, s_tbeg, P.n_meshes, A.ta, A.da, A.halo);
+__device__ __forceinline__ int look_next_n(LookCursor &c, const MarchParams<float> &P, int n) {
+    int t = -1;
+    for (int i = 0; i < n; ++i) t = look_next(c, P);
+    return t;
 }
 
 __device__ __forceinline__ void cp_async16(uint32_t dst, const void *src) {
@@ -731,28 +742,47 @@ __device__ __forceinline__ void cp_async_arrive(uint32_t bar) {
     asm volatile("cp.async.mbarrier.arrive.shared::cta.b64 [%0];" ::"r"(bar) : "memory");
 }
 
-// Copy warp: fill `slot` with everything tile A.ta needs in stage k.  The
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N> __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+// Copy warp: request the look-ahead entry of tile t (one commit group).
+__device__ __forceinline__ void look_issue(int *entry, int t, const MeshView<float> *sv, const int32_t *s_tbeg,
+                                           int n_meshes) {
+    const int lane = threadIdx.x & 31;
+    if (t >= 0) {
+        const int mi = mesh_of_tile(s_tbeg, n_meshes, t);
+        const int tl = t - s_tbeg[mi];
+        if (lane < 24) cp_async16(smem_u32(entry + 4 * lane), sv[mi].halo_rows + (size_t)tl * (32 * kHaloRegs) + 4 * lane);
+        if (lane == 24) cp_async16(smem_u32(entry + 96), sv[mi].tdesc + 8 * (size_t)tl);
+    }
+    if (lane == 25) entry[100] = t;
+    cp_async_commit();
+}
+
+// Copy warp: fill `slot` with everything the tile of look-ahead `entry` needs in stage k.  The
 // contiguous blocks (tile rows, SELL entries, descriptor) are bulk copies;
 // the scattered halo rows are 16-byte cp.async copies, eight lanes per row.
-__device__ __forceinline__ void tile_fill(const TileAhead &A, const MeshView<float> *sv, const StageCoef<float> *scoef,
+__device__ __forceinline__ void tile_fill(const int *entry, const MeshView<float> *sv, const StageCoef<float> *scoef,
                                           const int32_t *s_tbeg, int n_meshes, int k, char *slot, uint32_t bar,
                                           const MarchParams<float> &P) {
     const int lane = threadIdx.x & 31;
-    const int t = A.ta;
+    const int t = entry[100];
+    const int4 dsc = *reinterpret_cast<const int4 *>(entry + 96);
     const int mi = mesh_of_tile(s_tbeg, n_meshes, t);
     const MeshView<float> &m = sv[mi];
     const int flags = scoef[mi].flags;
     const int tl = t - s_tbeg[mi];
     const int r0 = tl * kTileRows, nrows = min(kTileRows, m.n0 - r0);
-    const int e0 = A.da.x, ne = A.da.y, h0 = A.da.z, nh = A.da.w;
+    const int e0 = dsc.x, ne = dsc.y, ovf = dsc.z, nh = dsc.w;
     const float2 *g = (flags & kGisPsi) ? m.psi : m.b[(k + 1) % 3];
     const uint32_t base = smem_u32(slot);
     // halo rows held ahead: row r = (lane >> 3) + 4u, chunk lane & 7
 #pragma unroll
     for (int u = 0; u < 8 * kHaloRegs; ++u) {
         const int r = (lane >> 3) + 4 * u;
-        const int q = __shfl_sync(0xffffffffu, A.halo[u >> 3], r & 31);
-        if (r < nh) cp_async16(base + unsigned(kTileRows + r) * 128u + 16u * (lane & 7), g + (size_t)q * 16 + 2 * (lane & 7));
+        if (r >= nh) break;
+        const int q = entry[r];
+        cp_async16(base + unsigned(kTileRows + r) * 128u + 16u * (lane & 7), g + (size_t)q * 16 + 2 * (lane & 7));
     }
     cp_async_arrive(bar);
     const int n_bulk_halo = max(nh - 32 * kHaloRegs, 0);
@@ -762,7 +792,6 @@ __device__ __forceinline__ void tile_fill(const TileAhead &A, const MeshView<flo
     __syncwarp();
     if (lane == 0) mbar_arrive_expect_tx(bar, total);
     __syncwarp();
-    fence_proxy_async_global();
     if (lane == 0) bulk_g2s(base, g + (size_t)r0 * 16, row_bytes, bar);
     if (lane == 1 && !(flags & kGisPsi)) bulk_g2s(base + P.off_psi, m.psi + (size_t)r0 * 16, row_bytes, bar);
     if (lane == 2 && (flags & kHasH)) bulk_g2s(base + P.off_h, m.b[(k + 2) % 3] + (size_t)r0 * 16, row_bytes, bar);
@@ -770,26 +799,8 @@ __device__ __forceinline__ void tile_fill(const TileAhead &A, const MeshView<flo
     if (lane == 4 && ne > 0) bulk_g2s(base + P.off_x, m.xval + e0, unsigned(ne) * 4u, bar);
     if (lane == 5) bulk_g2s(base + P.off_hdr, reinterpret_cast<const int4 *>(m.tdesc) + 2 * tl + 1, 16u, bar);
     for (int j = lane + 32 * kHaloRegs; j < nh; j += 32) {      // rare: more halo rows than held ahead
-        const int q = __ldg(m.halo_rows + h0 + j);
+        const int q = __ldg(m.halo_ovf + ovf + j - 32 * kHaloRegs);
         bulk_g2s(base + unsigned(kTileRows + j) * 128u, g + (size_t)q * 16, 128u, bar);
-    }
-}
-
-// Advance the look-ahead after tile i of range R was filled.
-__device__ __forceinline__ void ahead_next(TileAhead &A, const TileRange &R, int i, const MeshView<float> *sv,
-                                           const int32_t *s_tbeg, int n_meshes) {
-    if (A.hb) {
-        A.ta = A.tb;
-        A.da = A.db;
-        A.hb = false;
-        if (i + 2 < R.n) {
-            A.tb = R.at(i + 2);
-            A.db = load_tile_a(sv, s_tbeg, n_meshes, A.tb);
-            A.hb = true;
-        }
-        load_halo(sv, s_tbeg, n_meshes, A.ta, A.da, A.halo);
-    } else {
-        A.ta = -1;
     }
 }
 
@@ -808,14 +819,47 @@ __device__ __forceinline__ int4 lds_i4(uint32_t addr) {
     asm volatile("ld.shared.v4.s32 {%0, %1, %2, %3}, [%4];" : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "r"(addr));
     return v;
 }
-__device__ __forceinline__ void lds_chunk(uint32_t addr, float2 &a, float2 &b) {
-    asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];" : "=f"(a.x), "=f"(a.y), "=f"(b.x), "=f"(b.y) : "r"(addr));
+// Complex64 values kept as 64-bit register pairs (re in the low half) for
+// the packed FP32x2 instructions: loads, arithmetic and stores use them
+// without unpacking (same rounding as the scalar FADD / FFMA / FMUL).
+using cf2 = unsigned long long;
+__device__ __forceinline__ cf2 f2_pack(float re, float im) {
+    cf2 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(re), "f"(im));
+    return r;
 }
-__device__ __forceinline__ void stg_chunk(float2 *p, float2 a, float2 b) {
-    *reinterpret_cast<float4 *>(p) = make_float4(a.x, a.y, b.x, b.y);
+__device__ __forceinline__ cf2 f2_swap(cf2 a) {                  // (re, im) -> (im, re)
+    float re, im;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(re), "=f"(im) : "l"(a));
+    return f2_pack(im, re);
+}
+__device__ __forceinline__ cf2 f2_add(cf2 a, cf2 b) { cf2 r; asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b)); return r; }
+__device__ __forceinline__ cf2 f2_sub(cf2 a, cf2 b) { cf2 r; asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b)); return r; }
+__device__ __forceinline__ cf2 f2_mul(cf2 a, cf2 b) { cf2 r; asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b)); return r; }
+__device__ __forceinline__ cf2 f2_fma(cf2 a, cf2 b, cf2 c) {
+    cf2 r;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+    return r;
+}
+// complex product z w with z given as (zr, zr) and (-zi, zi): zr w + (-zi, zi) swap(w)
+__device__ __forceinline__ cf2 f2_cmul(cf2 zrr, cf2 zni, cf2 w) { return f2_fma(zni, f2_swap(w), f2_mul(zrr, w)); }
+__device__ __forceinline__ void lds_c2(uint32_t addr, cf2 &a, cf2 &b) {
+    asm volatile("ld.shared.v2.b64 {%0, %1}, [%2];" : "=l"(a), "=l"(b) : "r"(addr));
+}
+__device__ __forceinline__ void stg_c2(float2 *p, cf2 a, cf2 b) {
+    asm volatile("st.global.v2.b64 [%0], {%1, %2};" ::"l"(p), "l"(a), "l"(b) : "memory");
+}
+__device__ __forceinline__ float2 f2_unpack(cf2 a) {
+    float2 r;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(r.x), "=f"(r.y) : "l"(a));
+    return r;
 }
 
-// One compute warp's 8 rows of tile t (resident in `slot`).
+// One compute warp's 8 rows of tile t (resident in `slot`).  The entry
+// arrays hold the neighbour's byte offset in the window (row * 128, uint16)
+// and x_pq.  Arithmetic order is that of the row kernel: for each
+// neighbour in SELL order acc += x (g_p - g_q), then
+// out = alpha psi (+ alpha_lo psi) + beta (acc - g_p) - h.
 __device__ __forceinline__ void tile_compute(const MeshView<float> *sv, const StageCoef<float> *scoef,
                                              const int32_t *s_tbeg, int n_meshes, int t, int k, const char *slot,
                                              float h_post, int kerr_mode, const MarchParams<float> &P) {
@@ -833,53 +877,61 @@ __device__ __forceinline__ void tile_compute(const MeshView<float> *sv, const St
     const int4 hdr = lds_i4(base + P.off_hdr);
     const int es = ((sl < 2 ? hdr.x : hdr.y) >> (16 * (sl & 1)) & 0xffff) + (lr & 31);
     const int width = (hdr.z >> (8 * sl)) & 0xff;
-    const uint32_t gw = base;                              // neighbour window
+    if (width > 0 && es + 32 * (width - 1) >= P.slot_entries) {   // cannot happen with a consistent ring
+        atomicCAS(P.status, 0, -8);                               // DECBPM_ERR_DEVICE_CHECK
+        return;
+    }
+    const uint32_t g1 = base + 16 * c1, g2 = base + 16 * c2;           // this lane's chunks of window row 0
     const uint32_t pw = (sc.flags & kGisPsi) ? base : base + P.off_psi;
     const uint32_t lc = base + P.off_lcol + 2 * es;      // entry (row, j) at lc + 64 j
     const uint32_t xs = base + P.off_x + 4 * es;         // and xs + 128 j
-    float2 gp[4], ps[4], hh[4], acc[4];
-    lds_chunk(gw + lr * 128 + 16 * c1, gp[0], gp[1]);
-    lds_chunk(gw + lr * 128 + 16 * c2, gp[2], gp[3]);
-    lds_chunk(pw + lr * 128 + 16 * c1, ps[0], ps[1]);
-    lds_chunk(pw + lr * 128 + 16 * c2, ps[2], ps[3]);
+    cf2 gp[4], ps[4], hh[4], acc[4];
+    lds_c2(g1 + lr * 128, gp[0], gp[1]);
+    lds_c2(g2 + lr * 128, gp[2], gp[3]);
+    lds_c2(pw + lr * 128 + 16 * c1, ps[0], ps[1]);
+    lds_c2(pw + lr * 128 + 16 * c2, ps[2], ps[3]);
     if (sc.flags & kHasH) {
-        lds_chunk(base + P.off_h + lr * 128 + 16 * c1, hh[0], hh[1]);
-        lds_chunk(base + P.off_h + lr * 128 + 16 * c2, hh[2], hh[3]);
+        lds_c2(base + P.off_h + lr * 128 + 16 * c1, hh[0], hh[1]);
+        lds_c2(base + P.off_h + lr * 128 + 16 * c2, hh[2], hh[3]);
     }
 #pragma unroll
-    for (int f = 0; f < 4; ++f) acc[f] = make_float2(0.f, 0.f);
+    for (int f = 0; f < 4; ++f) acc[f] = 0ull;
     int j = 0;
     for (; j + 4 <= width; j += 4) {
-        float2 gq[4][4];
-        float xv[4];
+        cf2 gq[4][4], xv[4];
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
-            const uint32_t q = lds_u16(lc + 64 * (j + u));
-            xv[u] = lds_f32(xs + 128 * (j + u));
-            lds_chunk(gw + q * 128 + 16 * c1, gq[u][0], gq[u][1]);
-            lds_chunk(gw + q * 128 + 16 * c2, gq[u][2], gq[u][3]);
+            const uint32_t off = lds_u16(lc + 64 * (j + u));
+            const float x = lds_f32(xs + 128 * (j + u));
+            xv[u] = f2_pack(x, x);
+            lds_c2(g1 + off, gq[u][0], gq[u][1]);
+            lds_c2(g2 + off, gq[u][2], gq[u][3]);
         }
 #pragma unroll
         for (int u = 0; u < 4; ++u)
 #pragma unroll
-            for (int f = 0; f < 4; ++f) acc[f] = cfma(xv[u], csub(gp[f], gq[u][f]), acc[f]);
+            for (int f = 0; f < 4; ++f) acc[f] = f2_fma(xv[u], f2_sub(gp[f], gq[u][f]), acc[f]);
     }
     for (; j < width; ++j) {
-        float2 gq[4];
-        const uint32_t q = lds_u16(lc + 64 * j);
-        const float xv = lds_f32(xs + 128 * j);
-        lds_chunk(gw + q * 128 + 16 * c1, gq[0], gq[1]);
-        lds_chunk(gw + q * 128 + 16 * c2, gq[2], gq[3]);
+        cf2 gq[4];
+        const uint32_t off = lds_u16(lc + 64 * j);
+        const float x = lds_f32(xs + 128 * j);
+        const cf2 xv = f2_pack(x, x);
+        lds_c2(g1 + off, gq[0], gq[1]);
+        lds_c2(g2 + off, gq[2], gq[3]);
 #pragma unroll
-        for (int f = 0; f < 4; ++f) acc[f] = cfma(xv, csub(gp[f], gq[f]), acc[f]);
+        for (int f = 0; f < 4; ++f) acc[f] = f2_fma(xv, f2_sub(gp[f], gq[f]), acc[f]);
     }
-    float2 out[4];
+    const cf2 arr = f2_pack(sc.alpha.x, sc.alpha.x), ani = f2_pack(-sc.alpha.y, sc.alpha.y);
+    const cf2 brr = f2_pack(sc.beta.x, sc.beta.x), bni = f2_pack(-sc.beta.y, sc.beta.y);
+    cf2 out[4];
 #pragma unroll
     for (int f = 0; f < 4; ++f) {
-        float2 tt = cmul(sc.alpha, ps[f]);
-        if (sc.flags & kFinal) tt = cadd(tt, cmul(sc.alpha_lo, ps[f]));
-        out[f] = cadd(tt, cmul(sc.beta, csub(acc[f], gp[f])));
-        if (sc.flags & kHasH) out[f] = csub(out[f], hh[f]);
+        cf2 tt = f2_cmul(arr, ani, ps[f]);
+        if (sc.flags & kFinal)
+            tt = f2_add(tt, f2_cmul(f2_pack(sc.alpha_lo.x, sc.alpha_lo.x), f2_pack(-sc.alpha_lo.y, sc.alpha_lo.y), ps[f]));
+        out[f] = f2_add(tt, f2_cmul(brr, bni, f2_sub(acc[f], gp[f])));
+        if (sc.flags & kHasH) out[f] = f2_sub(out[f], hh[f]);
     }
     float2 *dst;
     if (sc.flags & kFinal) {
@@ -888,7 +940,10 @@ __device__ __forceinline__ void tile_compute(const MeshView<float> *sv, const St
             diag_factors(__ldg(m.sigma + row), h_post, em, phi);
             const float vv = __ldg(m.v + row), cb = __ldg(m.chib + row);
 #pragma unroll
-            for (int f = 0; f < 4; ++f) out[f] = diag_apply(out[f], vv, cb, h_post, em, phi);
+            for (int f = 0; f < 4; ++f) {
+                const float2 o = diag_apply(f2_unpack(out[f]), vv, cb, h_post, em, phi);
+                out[f] = f2_pack(o.x, o.y);
+            }
             dst = m.psi;
         } else {
             dst = m.b[0];        // element-averaged Kerr needs the neighbours' |S|^2: park S in b[0]
@@ -896,20 +951,114 @@ __device__ __forceinline__ void tile_compute(const MeshView<float> *sv, const St
     } else {
         dst = m.b[k % 3];
     }
-    stg_chunk(dst + (size_t)row * 16 + 2 * c1, out[0], out[1]);
-    stg_chunk(dst + (size_t)row * 16 + 2 * c2, out[2], out[3]);
+    stg_c2(dst + (size_t)row * 16 + 2 * c1, out[0], out[1]);
+    stg_c2(dst + (size_t)row * 16 + 2 * c2, out[2], out[3]);
+}
+
+// The whole launch as seen by one role: the copy warp (COPIER) or a compute
+// warp.  Both take the same grid barriers; each role's registers are live
+// only in its own instantiation.
+template <bool COPIER>
+__device__ __forceinline__ void tile_march_role(int copier,const MarchParams<float> &P, char *s_ring, const int32_t *s_begin,
+                                                const int32_t *s_tbeg, const MeshView<float> *s_view,
+                                                StageCoef<float> *s_coef, unsigned long long *s_full,
+                                                unsigned long long *s_empty, int *s_look) {
+    constexpr int FPT = Geo<float, 16>::FPT;
+    const int lane = threadIdx.x & 31;
+    unsigned long long target = 0;
+    const float h = P.h, hh = P.h * 0.5f;
+    const int bl = Geo<float, 16>::TPR_LOG2 + Geo<float, 16>::FPT_LOG2;
+    const unsigned D = unsigned(P.n_slots);
+    unsigned seq = 0;                                      // tiles filled / consumed so far by this CTA
+    LookCursor cur{0, 0, tile_range(P, 0)};
+    int *ring = s_look + copier * (kLookAhead * kLookInts);
+    if constexpr (COPIER) {
+        fence_proxy_async_global();
+        if (copier < int(D))
+            for (int e = 0; e < kLookAhead; ++e)
+                look_issue(ring + e * kLookInts, look_next_n(cur, P, e == 0 ? copier + 1 : int(D)), s_view, s_tbeg,
+                           P.n_meshes);
+    }
+    for (int step = 0; step < P.n_steps; ++step) {
+        if (step == 0 && P.pre_half) {
+            if (P.kerr_mode == 0) {
+                for_my_items(P, s_begin, P.total_items, [&](const MeshView<float> &m, int li) {
+                    lumped_diag_item<float, FPT>(m, li, hh, bl);
+                });
+                fence_proxy_async_global();
+                if (!grid_barrier(P.barrier, target, P.status, P.timeout_ns)) return;
+                if constexpr (COPIER) fence_proxy_async_global();   // other CTAs' writes, then bulk reads
+            } else {
+                for_my_items(P, s_begin, P.total_items, [&](const MeshView<float> &m, int li) {
+                    element_kerr_item<float, FPT>(m, li, hh, bl, m.psi, m.b[0]);
+                });
+                if (!grid_barrier(P.barrier, target, P.status, P.timeout_ns)) return;
+                if constexpr (COPIER) fence_proxy_async_global();   // other CTAs' writes, then bulk reads
+                for_my_items(P, s_begin, P.total_items, [&](const MeshView<float> &m, int li) {
+                    copy_item<float, FPT>(m, li, bl, m.b[0], m.psi);
+                });
+                fence_proxy_async_global();
+                if (!grid_barrier(P.barrier, target, P.status, P.timeout_ns)) return;
+                if constexpr (COPIER) fence_proxy_async_global();   // other CTAs' writes, then bulk reads
+            }
+        }
+        const float h_post = (step == P.n_steps - 1 && P.post_half) ? hh : h;
+        for (int s = 0; s < P.S; ++s) {
+            const int k = P.S - 1 - s;
+            for (int i = threadIdx.x; i < P.n_meshes; i += blockDim.x)
+                if (s_view[i].M > k) s_coef[i] = s_view[i].coef[k];
+            __syncthreads();
+            const TileRange R = tile_range(P, s);
+            bool ok = true;
+            for (int i = 0; i < R.n && ok; ++i) {
+                const unsigned q = seq + unsigned(i), sl = q % D;
+                if constexpr (COPIER) {
+                    if (int(sl) != copier) continue;              // slot sl belongs to copy warp sl
+                    if (q >= D) ok = mbar_wait(smem_u32(&s_empty[sl]), ((q / D) - 1u) & 1u, P.status, P.timeout_ns);
+                    if (ok) {
+                        int *entry = ring + ((q / D) % kLookAhead) * kLookInts;
+                        cp_async_wait<kLookAhead - 1>();       // this entry's group has landed
+                        __syncwarp();
+                        tile_fill(entry, s_view, s_coef, s_tbeg, P.n_meshes, k, s_ring + (size_t)sl * P.slot_bytes,
+                                  smem_u32(&s_full[sl]), P);
+                        __syncwarp();
+                        look_issue(entry, look_next_n(cur, P, int(D)), s_view, s_tbeg, P.n_meshes);
+                    }
+                } else {
+                    ok = mbar_wait(smem_u32(&s_full[sl]), (q / D) & 1u, P.status, P.timeout_ns);
+                    if (ok) {
+                        tile_compute(s_view, s_coef, s_tbeg, P.n_meshes, R.at(i), k, s_ring + (size_t)sl * P.slot_bytes,
+                                     h_post, P.kerr_mode, P);
+                        __syncwarp();
+                        if (lane == 0) mbar_arrive(smem_u32(&s_empty[sl]));
+                    }
+                }
+            }
+            seq += unsigned(R.n);
+            if (!ok) return;
+            fence_proxy_async_global();
+            if (!grid_barrier(P.barrier, target, P.status, P.timeout_ns)) return;
+                if constexpr (COPIER) fence_proxy_async_global();   // other CTAs' writes, then bulk reads
+        }
+        if (P.kerr_mode != 0) {
+            for_my_items(P, s_begin, P.total_items, [&](const MeshView<float> &m, int li) {
+                element_kerr_item<float, FPT>(m, li, h_post, bl, m.b[0], m.psi);
+            });
+            fence_proxy_async_global();
+            if (!grid_barrier(P.barrier, target, P.status, P.timeout_ns)) return;
+                if constexpr (COPIER) fence_proxy_async_global();   // other CTAs' writes, then bulk reads
+        }
+    }
 }
 
 __global__ void __launch_bounds__(kTileThreads, 1) march_tile_kernel(MarchParams<float> P) {
-    constexpr int FPT = Geo<float, 16>::FPT;
     extern __shared__ __align__(128) char s_ring[];
     __shared__ int32_t s_begin[kMaxMeshes + 1];
     __shared__ int32_t s_tbeg[kMaxMeshes + 1];
     __shared__ MeshView<float> s_view[kMaxMeshes];
     __shared__ StageCoef<float> s_coef[kMaxMeshes];
     __shared__ __align__(8) unsigned long long s_full[kMaxSlots], s_empty[kMaxSlots];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const bool copier = warp == kTileComputeWarps;
+    __shared__ __align__(16) int s_look[kTileCopyWarps * kLookAhead * kLookInts];
     for (int i = threadIdx.x; i < P.n_meshes; i += blockDim.x) {
         s_begin[i] = P.meshes[i].item_begin;
         s_tbeg[i] = P.meshes[i].tile_begin;
@@ -921,77 +1070,13 @@ __global__ void __launch_bounds__(kTileThreads, 1) march_tile_kernel(MarchParams
     }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     __syncthreads();
-    unsigned long long target = 0;
-    const float h = P.h, hh = P.h * 0.5f;
-    const int bl = Geo<float, 16>::TPR_LOG2 + Geo<float, 16>::FPT_LOG2;
-    const unsigned D = unsigned(P.n_slots);
-    unsigned seq = 0;                                      // tiles filled / consumed so far by this CTA
-    TileAhead A;
-    if (copier) ahead_start(A, P, s_view, s_tbeg, 0);
-    for (int step = 0; step < P.n_steps; ++step) {
-        if (step == 0 && P.pre_half) {
-            if (P.kerr_mode == 0) {
-                for_my_items(P, s_begin, P.total_items, [&](const MeshView<float> &m, int li) {
-                    lumped_diag_item<float, FPT>(m, li, hh, bl);
-                });
-                fence_proxy_async_global();
-                if (!grid_barrier(P.barrier, target, P.status, P.timeout_ns)) return;
-            } else {
-                for_my_items(P, s_begin, P.total_items, [&](const MeshView<float> &m, int li) {
-                    element_kerr_item<float, FPT>(m, li, hh, bl, m.psi, m.b[0]);
-                });
-                if (!grid_barrier(P.barrier, target, P.status, P.timeout_ns)) return;
-                for_my_items(P, s_begin, P.total_items, [&](const MeshView<float> &m, int li) {
-                    copy_item<float, FPT>(m, li, bl, m.b[0], m.psi);
-                });
-                fence_proxy_async_global();
-                if (!grid_barrier(P.barrier, target, P.status, P.timeout_ns)) return;
-            }
-        }
-        const float h_post = (step == P.n_steps - 1 && P.post_half) ? hh : h;
-        for (int s = 0; s < P.S; ++s) {
-            const int k = P.S - 1 - s;
-            for (int i = threadIdx.x; i < P.n_meshes; i += blockDim.x)
-                if (s_view[i].M > k) s_coef[i] = s_view[i].coef[k];
-            __syncthreads();
-            const TileRange R = tile_range(P, s);
-            bool ok = true;
-            if (copier) {
-                for (int i = 0; i < R.n && ok; ++i) {
-                    const unsigned q = seq + unsigned(i), sl = q % D;
-                    if (q >= D) ok = mbar_wait(smem_u32(&s_empty[sl]), ((q / D) - 1u) & 1u, P.status, P.timeout_ns);
-                    if (ok) {
-                        tile_fill(A, s_view, s_coef, s_tbeg, P.n_meshes, k, s_ring + (size_t)sl * P.slot_bytes,
-                                  smem_u32(&s_full[sl]), P);
-                        ahead_next(A, R, i, s_view, s_tbeg, P.n_meshes);
-                    }
-                }
-                // the next stage's first tiles: their descriptors do not depend on this stage
-                if (ok) ahead_start(A, P, s_view, s_tbeg, s + 1 < P.S ? s + 1 : 0);
-            } else {
-                for (int i = 0; i < R.n && ok; ++i) {
-                    const unsigned q = seq + unsigned(i), sl = q % D;
-                    ok = mbar_wait(smem_u32(&s_full[sl]), (q / D) & 1u, P.status, P.timeout_ns);
-                    if (ok) {
-                        tile_compute(s_view, s_coef, s_tbeg, P.n_meshes, R.at(i), k,
-                                     s_ring + (size_t)sl * P.slot_bytes, h_post, P.kerr_mode, P);
-                        __syncwarp();
-                        if (lane == 0) mbar_arrive(smem_u32(&s_empty[sl]));
-                    }
-                }
-            }
-            seq += unsigned(R.n);
-            if (!ok) return;
-            fence_proxy_async_global();
-            if (!grid_barrier(P.barrier, target, P.status, P.timeout_ns)) return;
-        }
-        if (P.kerr_mode != 0) {
-            for_my_items(P, s_begin, P.total_items, [&](const MeshView<float> &m, int li) {
-                element_kerr_item<float, FPT>(m, li, h_post, bl, m.b[0], m.psi);
-            });
-            fence_proxy_async_global();
-            if (!grid_barrier(P.barrier, target, P.status, P.timeout_ns)) return;
-        }
+    const int warp = threadIdx.x >> 5;
+    if (warp >= kTileComputeWarps) {
+        tile_march_role<true>(warp - kTileComputeWarps, P, s_ring, s_begin, s_tbeg, s_view, s_coef, s_full, s_empty,
+                              s_look);
+        cp_async_wait<0>();           // no look-ahead copy may land after the CTA exits
+    } else {
+        tile_march_role<false>(0, P, s_ring, s_begin, s_tbeg, s_view, s_coef, s_full, s_empty, s_look);
     }
 }
 

@@ -255,6 +255,39 @@ def test_tile_staged_kernel_equals_row_kernel(kerr):
     assert all(torch.isfinite(torch.view_as_real(x)).all() for x in a)
 
 
+@pytest.mark.parametrize("kerr", ["lumped", "element"])
+def test_tile_staged_ring_wraps_many_times(kerr):
+    """A 100k-vertex fiber (782 tiles): every CTA fills and drains its
+    shared-memory ring several times per stage and the copy warps' look-ahead
+    crosses stage and step boundaries; still bit for bit the row kernel."""
+    coords, tris = W.mesh_disk_graded(4.0, 100_000, 3.0, interfaces=(1.0,), seed=61, grade_from=1.0)
+    V, chi = W.step_index_materials(coords, tris)
+    sigma = W.absorber_profile(coords, 4.0, 20.0)
+    mesh = api.Mesh(coords, tris, V, chi, sigma)
+    psi0 = W.hg_superpositions(coords, 16, np.random.default_rng(61))
+    plan = api.Plan([mesh], [16], "c64")
+    assert plan.config()["tile_slots"] >= 2
+    a, b = to_dev(psi0, torch.complex64), to_dev(psi0, torch.complex64)
+    plan.propagate([a], 5e-4, 3, kerr=kerr)
+    plan.propagate([b], 5e-4, 3, kerr=kerr, variant="rows")
+    assert torch.equal(a, b)
+
+
+def test_tile_staged_full_bench_batch_one_step():
+    """The bench workload at full size (16 fibers, 20k..500k vertices, 16
+    fields): one step of the tile-staged kernel equals the row kernel."""
+    wl = W.batched_fibers(n_meshes=16, fields_per_mesh=16, n_min=20_000, ratio=25.0, seed=4)
+    meshes = [api.Mesh.from_workload(m, p=wl.p) for m in wl.meshes]
+    plan = api.Plan(meshes, [16] * len(meshes), "c64")
+    assert plan.config()["tile_slots"] >= 2
+    a = [to_dev(p, torch.complex64) for p in wl.psi0]
+    b = [x.clone() for x in a]
+    plan.propagate(a, wl.dz, 1)
+    plan.propagate(b, wl.dz, 1, variant="rows")
+    for x, y in zip(a, b):
+        assert torch.equal(x, y)
+
+
 # ------------------------------------------------------------------ edge cases
 def test_single_triangle_and_tiny_meshes():
     coords = np.array([[0.0, 0.0], [1.0, 0.0], [0.2, 0.9]])
