@@ -40,8 +40,8 @@ UNIT = "vertex-steps/s"
 # workload, from the one-pass ncu capture of this bench's own launches
 # (profiles/launches_bench_batched_fibers.md), valid for the kernel source
 # whose hash is recorded with it; traffic is reported as null otherwise.
-TRAFFIC_RATIO = 0.967
-TRAFFIC_SRC_HASH = "d74759874ca68737"
+TRAFFIC_RATIO = 0.9395
+TRAFFIC_SRC_HASH = "8a6cdbe5db760b32"
 
 
 def kernel_source_hash() -> str:
@@ -240,7 +240,7 @@ def run_ours(args, rank, world, local_rank):
             "vertices_total": int(sum(i["n_vertices"] for i in infos)), "fields_per_mesh": fields[0],
             "cheb_degree_min": int(min(degrees)), "cheb_degree_max": int(max(degrees)),
             "ordering": "hilbert", "parallelism": "replicas" if world > 1 else "single",
-            "grid": cfg["tile_grid"] if tiled else cfg["grid"], "block": 512 if tiled else cfg["block"],
+            "grid": cfg["tile_grid"] if tiled else cfg["grid"], "block": cfg["tile_block"] if tiled else cfg["block"],
             "march_kernel": kernel_name, "tile_slots": cfg["tile_slots"] if tiled else 0,
             "cuda_graph": bool(cfg["graphs"]),
             "l2": "working set %.2f GB > 126 MB L2; no flush" % (units_per_step * 8 * 4 / 1e9),

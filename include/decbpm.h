@@ -231,7 +231,8 @@ typedef struct {
     int32_t tile_slots;    /* > 0: the FUSED variant runs the tile-staged kernel with this many shared-memory
                               slots (complex64, 9..16 fields); 0: the row kernel */
     int32_t tile_slot_bytes;
-    int32_t tile_grid;     /* CTAs (of 512 threads) of the tile-staged launch */
+    int32_t tile_grid;     /* CTAs of the tile-staged launch */
+    int32_t tile_block;    /* threads per CTA of the tile-staged launch (16 compute + 3 copy warps) */
 } decbpm_plan_config;
 int decbpm_plan_get_config(decbpm_plan_t plan, decbpm_plan_config *cfg);
 

@@ -65,7 +65,8 @@ class Params(ctypes.Structure):
 class PlanConfig(ctypes.Structure):
     _fields_ = [("grid", ctypes.c_int32), ("block", ctypes.c_int32), ("fields_padded", ctypes.c_int32),
                 ("graphs", ctypes.c_int32), ("stages", ctypes.c_int32), ("n_meshes", ctypes.c_int32),
-                ("tile_slots", ctypes.c_int32), ("tile_slot_bytes", ctypes.c_int32), ("tile_grid", ctypes.c_int32)]
+                ("tile_slots", ctypes.c_int32), ("tile_slot_bytes", ctypes.c_int32), ("tile_grid", ctypes.c_int32),
+                ("tile_block", ctypes.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

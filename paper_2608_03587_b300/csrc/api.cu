@@ -1460,6 +1460,7 @@ int decbpm_plan_get_config(decbpm_plan_t P, decbpm_plan_config *cfg) {
     cfg->tile_slots = P->tile_mode ? P->n_slots : 0;
     cfg->tile_slot_bytes = P->tile_mode ? P->slot_bytes : 0;
     cfg->tile_grid = P->tile_mode ? P->tile_grid : 0;
+    cfg->tile_block = P->tile_mode ? kTileThreads : 0;
     return DECBPM_OK;
 }
 
