@@ -354,3 +354,83 @@ def dopri5(ops: Operators, p, psi0: np.ndarray, z_end: float, rtol=1e-9, atol=1e
             rejected = True
             h = h * max(0.2, 0.9 * E ** (-0.2))
     return y, {"n_accepted": n_acc, "n_rejected": n_rej, "n_rhs": n_rhs, "h_last": h_last}
+
+
+# --------------------------------------------------------------------------
+# discrete soliton: self-consistent nonlinear eigenmode
+# --------------------------------------------------------------------------
+def soliton_operator(ops: Operators, p, phi: np.ndarray, kerr="lumped") -> sp.csr_matrix:
+    """*0 H(phi) with H(phi) = p1 A - diag(v + N(|phi|^2)): the generator of
+    Eq. 10 with the nonlinearity frozen at phi, so that a stationary field
+    psi(z) = phi e^{-i mu z} solves  H(phi) phi = mu phi.  Multiplied by *0 it
+    is a symmetric matrix (K symmetric, *0 diagonal): the generalized
+    eigenproblem  (*0 H) phi = mu *0 phi  is symmetric-definite."""
+    if len(p) != 1:
+        raise ValueError("the soliton solver takes p_1 only")
+    I = np.abs(phi) ** 2
+    if kerr == "lumped":
+        Nr = ops.chib * I
+    else:
+        Nr = (sp.diags(1.0 / ops.H0) @ ops.QtDQ) @ I
+    return (p[0] * ops.K - sp.diags(ops.H0 * (ops.v + Nr))).tocsr()
+
+
+def soliton(ops: Operators, p, power: float, phi0=None, kerr="lumped", tol=1e-12, max_iter=500, mix=0.5):
+    """Fundamental discrete soliton of power P = sum_p m_p |phi_p|^2 (the
+    paper's self-consistent nonlinear eigenmode, Supp. Note 4, whose text is
+    not available): repeat
+        mu, u <- lowest eigenpair of (*0 H(phi)) u = mu *0 u   (scipy eigsh)
+        u     <- u scaled to power P, sign fixed by sum m u > 0
+        phi   <- u  (with the intensity entering H mixed:  I <- mix |u|^2 + (1 - mix) I)
+    until the intensity changes by less than tol (relative, *0-weighted).
+    The start is phi0 if given, else the linear fundamental mode (which is
+    localized only where the potential traps it: a homogeneous medium needs
+    a localized phi0).  Returns (phi (real), mu, iterations)."""
+    from scipy.sparse.linalg import eigsh
+
+    M = sp.diags(ops.H0).tocsc()
+    n = ops.n0
+
+    def lowest(Hm, guess):
+        vals, vecs = eigsh(Hm.tocsc(), k=1, M=M, sigma=guess, which="LM", tol=1e-14, v0=None)
+        return float(vals[0]), vecs[:, 0]
+
+    def scaled(u):
+        u = np.asarray(u, dtype=np.float64)
+        u = u * math.sqrt(power / float(np.sum(ops.H0 * u * u)))
+        return u if float(np.sum(ops.H0 * u)) >= 0 else -u
+
+    # start: the linear fundamental mode (or the given guess)
+    if phi0 is None:
+        H_lin = (p[0] * ops.K - sp.diags(ops.H0 * ops.v)).tocsr()
+        lo = float(np.min(-ops.v)) - 1.0
+        _, u = lowest(H_lin, lo)
+        phi = scaled(u)
+    else:
+        phi = scaled(np.real(phi0))
+    I = phi * phi
+    mu = None
+    for it in range(1, max_iter + 1):
+        Hm = soliton_operator(ops, p, np.sqrt(I), kerr)
+        shift = float(np.min(-(ops.v + (ops.chib * I if kerr == "lumped" else
+                                         (sp.diags(1.0 / ops.H0) @ ops.QtDQ) @ I)))) - 1.0
+        mu, u = lowest(Hm, shift)
+        phi_new = scaled(u)
+        I_new = mix * phi_new ** 2 + (1.0 - mix) * I
+        change = math.sqrt(float(np.sum(ops.H0 * (I_new - I) ** 2)) / float(np.sum(ops.H0 * I ** 2)))
+        I, phi = I_new, phi_new
+        if change < tol:
+            break
+    # final eigenpair at the converged intensity
+    Hm = soliton_operator(ops, p, phi, kerr)
+    shift = float(np.min(-(ops.v + (ops.chib * phi ** 2 if kerr == "lumped" else
+                                     (sp.diags(1.0 / ops.H0) @ ops.QtDQ) @ (phi ** 2))))) - 1.0
+    mu, u = lowest(Hm, shift)
+    return scaled(u), mu, it
+
+
+def soliton_residual(ops: Operators, p, phi: np.ndarray, mu: float, kerr="lumped") -> float:
+    """|| H(phi) phi - mu phi ||_*0 / ||phi||_*0."""
+    Hm = soliton_operator(ops, p, phi, kerr)
+    r = Hm @ phi / ops.H0 - mu * phi
+    return math.sqrt(float(np.sum(ops.H0 * np.abs(r) ** 2)) / float(np.sum(ops.H0 * np.abs(phi) ** 2)))

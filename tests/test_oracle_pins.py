@@ -474,3 +474,80 @@ def test_dec_rhs_is_the_ode_of_the_split_step(tiny):
         errs.append(np.linalg.norm((step - psi) / h - f) / np.linalg.norm(f))
     # first-order difference quotient: the error halves with h
     assert errs[1] < 2e-3 and 0.4 < errs[1] / errs[0] < 0.6
+
+
+# ------------------------------------------------------------------ discrete soliton
+def test_soliton_1d_converges_to_sech():
+    """i psi_z + psi_xx/2 + |psi|^2 psi = 0: the fundamental soliton of power
+    P is a sech(a x) with a = P/2 and mu = -P^2/8 (psi = phi e^{-i mu z}).
+    The discrete self-consistent eigenmode reaches it at O(h^2): the
+    eigenvalue error falls ~4x when h halves, for two powers (this pins the
+    sign and the scale of the Kerr term against diffraction)."""
+    for P in (2.0, 3.0):
+        errs = []
+        for n in (513, 1025):
+            # a uniform, symmetric mesh: a homogeneous medium has a neutral
+            # translation mode, which a jittered mesh would let drift
+            coords, cells = W.mesh_1d_jittered(n, jitter=0.0)
+            ne = len(cells)
+            ops = dec.Operators(coords, cells, np.zeros(ne), np.ones(ne))
+            # a localized start: from the constant (the linear ground state of
+            # a homogeneous medium) the iteration stays uniform
+            phi, mu, _ = bpm.soliton(ops, (0.5,), P, phi0=np.exp(-coords[:, 0] ** 2))
+            assert bpm.power(ops, phi) == pytest.approx(P, rel=1e-12)
+            assert bpm.soliton_residual(ops, (0.5,), phi, mu) < 1e-9
+            a = P / 2.0
+            exact = a / np.cosh(a * coords[:, 0])
+            assert bpm.relative_error(ops, phi.astype(complex), exact.astype(complex)) < 2e-3
+            errs.append(abs(mu + P * P / 8.0))
+        assert errs[1] < 1e-3 * P * P / 8.0
+        assert 3.0 < errs[0] / errs[1] < 5.0, (P, errs)
+
+
+def _lp01_eigenvalue(V0):
+    """Lowest eigenvalue u^2 of -lap + V0 1_{r > 1} in the plane (the LP01
+    mode of a step-index fiber of core radius 1): u solves
+    u J1(u) / J0(u) = w K1(w) / K0(w), u^2 + w^2 = V0."""
+    from scipy.optimize import brentq
+    from scipy.special import j0, j1, k0, k1
+
+    def f(u):
+        w = math.sqrt(V0 - u * u)
+        return u * j1(u) / j0(u) - w * k1(w) / k0(w)
+
+    u = brentq(f, 1e-6, min(2.404825557695773, math.sqrt(V0)) - 1e-9)
+    return u * u
+
+
+def test_soliton_linear_limit_is_the_lp01_mode():
+    """Without the Kerr term the self-consistent mode is the fundamental
+    guided mode; its eigenvalue converges at O(h^2) to the Bessel-function
+    LP01 eigenvalue of the step-index fiber (Table II V-number)."""
+    V0 = -W.FIBER_V_CLAD
+    lam = _lp01_eigenvalue(V0)
+    errs = []
+    for n in (3000, 12000):
+        coords, tris = W.mesh_disk_graded(4.0, n, 3.0, interfaces=(1.0,), seed=5, grade_from=1.0)
+        V, chi = W.step_index_materials(coords, tris)
+        ops = dec.Operators(coords, tris, V, 0.0 * chi)
+        phi, mu, _ = bpm.soliton(ops, (1.0,), 1.0)
+        errs.append(abs(mu - lam) / lam)
+    assert errs[1] < 3e-3
+    assert errs[0] / errs[1] > 2.5, errs
+
+
+def test_soliton_is_stationary_under_the_paper_integrator():
+    """A computed nonlinear mode keeps its intensity under the paper's RK45
+    integration of Eq. 10 (the eigen-equation and the ODE use one sign
+    convention), for lumped and element-averaged Kerr."""
+    coords, tris = W.mesh_disk_graded(4.0, 800, 3.0, interfaces=(1.0,), seed=7, grade_from=1.0)
+    V, chi = W.step_index_materials(coords, tris)
+    ops = dec.Operators(coords, tris, V, chi)
+    for kerr in ("lumped", "element"):
+        phi, mu, _ = bpm.soliton(ops, (1.0,), 6.0, kerr=kerr)
+        assert bpm.soliton_residual(ops, (1.0,), phi, mu, kerr) < 1e-9
+        out, _ = bpm.dopri5(ops, (1.0,), phi.astype(complex), 0.3, rtol=1e-11, atol=1e-13, kerr=kerr)
+        assert bpm.intensity_error(ops, out, phi.astype(complex)) < 1e-8
+        # and the phase advances as e^{-i mu z}
+        ph = np.angle(np.sum(ops.H0 * out * phi) / np.sum(ops.H0 * phi * phi))
+        assert ph == pytest.approx(np.angle(np.exp(-1j * mu * 0.3)), abs=1e-8)
