@@ -276,6 +276,35 @@ typedef struct { int64_t n_accepted, n_rejected, n_rhs; double h_last, z; } decb
 int decbpm_rk45(decbpm_mesh_t mesh, double z_end, int32_t kerr_mode, const decbpm_rk45_opts *opts, void *psi_dev,
                 void *stream, decbpm_rk45_stats *stats);
 
+/* ---- discrete soliton --------------------------------------------------------
+ * The fundamental nonlinear mode used as the launch field of the paper's
+ * soliton case (computed there by a self-consistent eigenmode solver on the
+ * same mesh, Supp. Note 4): a field phi with  H(phi) phi = mu phi,
+ * H(phi) = p1 A - diag(v + N(|phi|^2))  (the generator of Eq. 10, sign per
+ * Eq. 1), and power sum_p m_p |phi_p|^2 = power; then psi(z) = phi e^{-i mu z}
+ * solves Eq. 10.  Method: imaginary-z iteration with the nonlinearity frozen
+ * per iteration, phi <- e^{-tau H(phi)} phi renormalised (FP64 Chebyshev
+ * series of the exponential; its fixed points are exactly the self-consistent
+ * eigenmodes), until || H phi - mu phi ||_*0 / || phi ||_*0 < tol.  psi_dev is
+ * one complex128 field [N0] in caller order: the start on input (e.g. a
+ * Gaussian on the core), the mode on output.  p_1 > 0 only.               */
+typedef struct {
+    double power;        /* sum_p m_p |phi_p|^2 > 0 */
+    double tau;          /* imaginary-z step of one iteration > 0 (e.g. 0.5) */
+    double tol;          /* stop when the relative residual is below tol */
+    double mix;          /* (0, 1]: the frozen potential uses I <- mix |phi|^2 + (1 - mix) I */
+    int64_t max_iter;    /* >= 1 */
+    int32_t kerr_mode;   /* DECBPM_KERR_LUMPED | DECBPM_KERR_ELEMENT */
+} decbpm_soliton_opts;
+typedef struct { double mu, residual; int64_t iterations, cheb_terms; } decbpm_soliton_stats;
+int decbpm_soliton(decbpm_mesh_t mesh, const decbpm_soliton_opts *opts, void *psi_dev, void *stream,
+                   decbpm_soliton_stats *stats);
+
+/* Host only: e^{-a} I_k(a), k = 0..n-1, with every later term < tol e^{-a} I_0(a)
+ * (the coefficients of the Chebyshev series of e^{-a x}); *n_out = n; out may
+ * be NULL to query n; at most n_max values are written. */
+int decbpm_bessel_i_scaled(double a, double tol, int32_t n_max, double *out, int32_t *n_out);
+
 /* One-shot convenience: plan_create + plan_propagate + plan_destroy. */
 int decbpm_propagate_batch(const decbpm_mesh_t *meshes, int32_t n_meshes, const int32_t *fields_per_mesh,
                            const decbpm_params *params, void *const *psi_dev, void *stream,

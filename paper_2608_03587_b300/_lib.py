@@ -85,6 +85,19 @@ class Rk45Stats(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class SolitonOpts(ctypes.Structure):
+    _fields_ = [("power", ctypes.c_double), ("tau", ctypes.c_double), ("tol", ctypes.c_double),
+                ("mix", ctypes.c_double), ("max_iter", ctypes.c_int64), ("kerr_mode", ctypes.c_int32)]
+
+
+class SolitonStats(ctypes.Structure):
+    _fields_ = [("mu", ctypes.c_double), ("residual", ctypes.c_double), ("iterations", ctypes.c_int64),
+                ("cheb_terms", ctypes.c_int64)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 class Diag(ctypes.Structure):
     _fields_ = [("z", ctypes.c_double), ("power", ctypes.c_double), ("hamiltonian", ctypes.c_double),
                 ("max_intensity", ctypes.c_double)]
@@ -119,6 +132,8 @@ SIGNATURES = {
     "decbpm_selftest_barrier": (_i32, [_i32, _i64, _vp]),
     "decbpm_mesh_set_potential": (_i32, [_vp, _c_double_p]),
     "decbpm_vjp": (_i32, [_vp, ctypes.POINTER(Params), _vp, _vp, _vp, _vp, _vp, _i64, _i32, _vp]),
+    "decbpm_soliton": (_i32, [_vp, ctypes.POINTER(SolitonOpts), _vp, _vp, ctypes.POINTER(SolitonStats)]),
+    "decbpm_bessel_i_scaled": (_i32, [_dbl, _dbl, _i32, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_i32)]),
     "decbpm_rk45": (_i32, [_vp, _dbl, _i32, ctypes.POINTER(Rk45Opts), _vp, _vp, ctypes.POINTER(Rk45Stats)]),
     "decbpm_propagate_noalloc": (_i32, [_vp, ctypes.POINTER(Params), _vp, _i64, _vp]),
     "decbpm_propagate_batch": (_i32, [ctypes.POINTER(_vp), _i32, _c_int32_p, ctypes.POINTER(Params),

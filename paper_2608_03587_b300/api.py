@@ -368,3 +368,30 @@ def rk45(mesh: Mesh, psi, z_end, rtol=1e-9, atol=1e-11, h0=0.0, kerr="lumped", m
     L.check(lib.decbpm_rk45(mesh.handle, float(z_end), L.KERR_LUMPED if kerr == "lumped" else L.KERR_ELEMENT,
                             ctypes.byref(o), ctypes.c_void_p(psi.data_ptr()), _stream_handle(stream), ctypes.byref(st)))
     return st.as_dict()
+
+
+# ---------------------------------------------------------------- discrete soliton
+def soliton(mesh: Mesh, psi, power, tau=0.05, tol=1e-11, max_iter=5000, kerr="lumped", mix=1.0, stream=None):
+    """decbpm_soliton: the fundamental nonlinear mode of the given power, in
+    place on a complex128 CUDA field [N0] (input: the start); returns
+    {mu, residual, iterations, cheb_terms}."""
+    lib = _lib()
+    if psi.dtype.__str__() != "torch.complex128" or psi.dim() != 1:
+        raise TypeError("soliton works on one complex128 field [N0]")
+    o = L.SolitonOpts(power=float(power), tau=float(tau), tol=float(tol), mix=float(mix), max_iter=int(max_iter),
+                      kerr_mode=L.KERR_LUMPED if kerr == "lumped" else L.KERR_ELEMENT)
+    st = L.SolitonStats()
+    L.check(lib.decbpm_soliton(mesh.handle, ctypes.byref(o), ctypes.c_void_p(psi.data_ptr()), _stream_handle(stream),
+                               ctypes.byref(st)))
+    return st.as_dict()
+
+
+def bessel_i_scaled(a, tol=1e-17):
+    """decbpm_bessel_i_scaled: e^{-a} I_k(a) for k = 0.. until below tol e^{-a} I_0(a)."""
+    lib = _lib()
+    n = ctypes.c_int32(0)
+    L.check(lib.decbpm_bessel_i_scaled(float(a), float(tol), 0, None, ctypes.byref(n)))
+    out = np.zeros(n.value)
+    L.check(lib.decbpm_bessel_i_scaled(float(a), float(tol), n.value, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                       ctypes.byref(n)))
+    return out

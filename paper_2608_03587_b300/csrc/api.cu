@@ -251,6 +251,8 @@ struct decbpm_plan_s {
     size_t adj_ws_bytes = 0;
     char *rk_ws = nullptr;                       // Dormand-Prince workspace (stages, states, norms)
     size_t rk_ws_bytes = 0;
+    char *sol_ws = nullptr;                      // soliton iteration workspace
+    size_t sol_ws_bytes = 0;
     void *views = nullptr, *coef = nullptr;
     int32_t *active = nullptr;
     int coef_cap = 0, active_cap = 0;
@@ -284,6 +286,7 @@ struct decbpm_plan_s {
         if (ev1) cudaEventDestroy(ev1);
         if (adj_ws) cudaFree(adj_ws);
         if (rk_ws) cudaFree(rk_ws);
+        if (sol_ws) cudaFree(sol_ws);
         mem.release();
     }
 };
@@ -1159,6 +1162,118 @@ static int rk45_impl(decbpm_mesh_t mesh, decbpm_plan_t P, double z_end, int kerr
     return DECBPM_OK;
 }
 
+
+// ============================================================== discrete soliton
+// Fundamental nonlinear mode of power P: y <- e^{-tau (H(y) - lo)} y, renormalised,
+// with H(y) = p1 A + diag(d(y)) frozen per iteration.  A fixed point satisfies
+// e^{-tau H(y)} y = c y, i.e. H(y) y = mu y: the self-consistent eigenmode,
+// without splitting bias.  Spectrum of H within [min d, max d + p1 rho].
+static int soliton_impl(decbpm_mesh_t mesh, decbpm_plan_t P, const decbpm_soliton_opts *o, void *psi_dev,
+                        cudaStream_t s, decbpm_soliton_stats *st) {
+    const int n0 = int(mesh->A.n0);
+    if (mesh->A.p.size() != 1 || !(mesh->A.p[0] > 0)) return fail(DECBPM_ERR_UNSUPPORTED, "the soliton solver takes p_1 > 0 only");
+    const double p1 = mesh->A.p[0], rA = 0.5 * mesh->A.rho, p1rA = p1 * rA;
+    const int T = kRkThreads, G = (n0 + T - 1) / T;
+    const int NB = std::min(2 * P->num_sms, G);
+    const size_t vec = size_t(n0) * sizeof(double2);
+    const size_t need = 5 * vec + 2 * size_t(n0) * sizeof(double) + sizeof(double) * (2 * NB + 2);
+    if (need > P->sol_ws_bytes) {
+        if (P->sol_ws) cudaFree(P->sol_ws);
+        P->sol_ws = nullptr;
+        P->sol_ws_bytes = 0;
+        cudaError_t e = cudaMalloc(&P->sol_ws, need);
+        if (e != cudaSuccess) return fail(DECBPM_ERR_OOM, "soliton workspace of %zu bytes: %s", need, cudaGetErrorString(e));
+        P->sol_ws_bytes = need;
+    }
+    double2 *y = reinterpret_cast<double2 *>(P->sol_ws);
+    double2 *B[3] = {y + n0, y + 2 * size_t(n0), y + 3 * size_t(n0)};
+    double2 *hy = y + 4 * size_t(n0);
+    double *d = reinterpret_cast<double *>(P->sol_ws + 5 * vec);
+    double *Imix = d + n0;
+    double *part = Imix + n0;
+    double *hy_I = reinterpret_cast<double *>(hy);          // |y|^2 for the residual, in hy's space before H y is formed
+    double *res = part + 2 * NB;
+    MeshView<double> mv{};
+    CK(cudaMemcpy(&mv, P->views, sizeof(mv), cudaMemcpyDeviceToHost));
+    auto reduce = [&](int mode, const double2 *a, const double2 *b, const double *r, double mu, double out[2]) -> int {
+        sol_reduce_partial_kernel<<<NB, T, 0, s>>>(mode, a, b, r, mesh->m64, mu, n0, part);
+        sol_reduce_final_kernel<<<1, T, 0, s>>>(mode, part, NB, res);
+        CK(cudaMemcpyAsync(out, res, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        return DECBPM_OK;
+    };
+    auto normalise = [&]() -> int {
+        double q[2];
+        TRY(reduce(0, y, nullptr, nullptr, 0.0, q));
+        if (!(q[0] > 0) || !std::isfinite(q[0])) return fail(DECBPM_ERR_NONFINITE, "soliton iteration: field power is %g", q[0]);
+        sol_scale_kernel<<<G, T, 0, s>>>(y, std::sqrt(o->power / q[0]), n0);
+        return DECBPM_OK;
+    };
+    permute_in_kernel<double2><<<std::min(G, 4 * P->num_sms), T, 0, s>>>((const double2 *)psi_dev, y, mesh->perm, n0, 1, 1);
+    CK(cudaGetLastError());
+    TRY(normalise());
+    double mu = 0, resid = 1e300;
+    int64_t it = 0, terms = 0;
+    std::vector<double> sk;
+    for (it = 1; it <= o->max_iter; ++it) {
+        sol_mix_kernel<<<G, T, 0, s>>>(y, Imix, o->mix, it == 1, n0);
+        sol_potential_kernel<<<G, T, 0, s>>>(mv, Imix, o->kerr_mode, d);
+        double mm[2];
+        TRY(reduce(3, nullptr, nullptr, d, 0.0, mm));
+        const double lo = mm[0], hi = mm[1] + p1 * mesh->A.rho;
+        const double c = 0.5 * (lo + hi), r = 0.5 * (hi - lo), a = o->tau * r;
+        // e^{-tau (lambda - lo)} = e^{-a (x + 1)} = s_0 + 2 sum_k (-1)^k s_k T_k(x),  s_k = e^{-a} I_k(a)
+        bessel_i_scaled(a, 1e-17, sk);
+        const int M = int(sk.size()) - 1;
+        terms += M + 1;
+        auto coef = [&](int k) { return k == 0 ? sk[0] : 2.0 * ((k & 1) ? -sk[k] : sk[k]); };
+        double2 *out = nullptr;
+        if (M == 0) {
+            sol_stage_kernel<<<G, T, 0, s>>>(mv, y, nullptr, nullptr, B[0], d, p1rA, c, 1.0 / r, coef(0), 0.0);
+            out = B[0];
+        } else {
+            // b_M = c_M y;  b_k = c_k y + 2 X b_{k+1} - b_{k+2};  S = c_0 y + X b_1 - b_2
+            int i1 = 0, i2 = 1, i0 = 2;                      // b_{k+1}, b_{k+2}, b_k
+            sol_stage_kernel<<<G, T, 0, s>>>(mv, y, nullptr, nullptr, B[i1], d, p1rA, c, 1.0 / r, coef(M), 0.0);
+            bool have2 = false;
+            for (int k = M - 1; k >= 0; --k) {
+                const double beta = k == 0 ? 1.0 : 2.0;
+                sol_stage_kernel<<<G, T, 0, s>>>(mv, y, B[i1], have2 ? B[i2] : nullptr, B[i0], d, p1rA, c, 1.0 / r,
+                                                 coef(k), beta);
+                const int t = i2; i2 = i1; i1 = i0; i0 = t;
+                have2 = true;
+            }
+            out = B[i1];
+        }
+        CK(cudaGetLastError());
+        CK(cudaMemcpyAsync(y, out, vec, cudaMemcpyDeviceToDevice, s));
+        TRY(normalise());
+        // convergence: Rayleigh quotient and residual at the new field (unmixed intensity)
+        sol_mix_kernel<<<G, T, 0, s>>>(y, hy_I, 1.0, 1, n0);
+        sol_potential_kernel<<<G, T, 0, s>>>(mv, hy_I, o->kerr_mode, d);
+        sol_apply_h_kernel<<<G, T, 0, s>>>(mv, y, d, p1rA, hy);
+        double q0[2], q1[2], q2[2];
+        TRY(reduce(0, y, nullptr, nullptr, 0.0, q0));
+        TRY(reduce(1, y, hy, nullptr, 0.0, q1));
+        mu = q1[0] / q0[0];
+        TRY(reduce(2, y, hy, nullptr, mu, q2));
+        resid = std::sqrt(q2[0] / q0[0]);
+        if (!std::isfinite(resid)) return fail(DECBPM_ERR_NONFINITE, "soliton iteration diverged");
+        if (resid < o->tol) break;
+    }
+    permute_out_kernel<double2><<<std::min(G, 4 * P->num_sms), T, 0, s>>>(y, (double2 *)psi_dev, mesh->perm, n0, 1, 1,
+                                                                         1.0, 0.0);
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(s));
+    if (st) {
+        st->mu = mu;
+        st->residual = resid;
+        st->iterations = std::min<int64_t>(it, o->max_iter);
+        st->cheb_terms = terms;
+    }
+    return DECBPM_OK;
+}
+
 // ============================================================== C ABI
 extern "C" {
 
@@ -1447,6 +1562,33 @@ int decbpm_rk45(decbpm_mesh_t mesh, double z_end, int32_t kerr_mode, const decbp
     TRY(single_plan(mesh, 1, DECBPM_C128, &P));
     if (P->order.empty()) TRY(plan_configure<double>(P, 1e-3, 1e-16));   // only for the device view of the mesh
     return rk45_impl(mesh, P, z_end, kerr_mode, opts, psi_dev, (cudaStream_t)stream, stats);
+}
+
+int decbpm_soliton(decbpm_mesh_t mesh, const decbpm_soliton_opts *opts, void *psi_dev, void *stream,
+                   decbpm_soliton_stats *stats) {
+    clear_error();
+    if (!mesh || !opts || !psi_dev) return fail(DECBPM_ERR_INVALID_ARG, "NULL argument");
+    if (!(opts->power > 0) || !std::isfinite(opts->power)) return fail(DECBPM_ERR_INVALID_ARG, "power must be > 0");
+    if (!(opts->tau > 0) || !std::isfinite(opts->tau)) return fail(DECBPM_ERR_INVALID_ARG, "tau must be > 0");
+    if (!(opts->tol > 0)) return fail(DECBPM_ERR_INVALID_ARG, "tol must be > 0");
+    if (opts->max_iter < 1) return fail(DECBPM_ERR_INVALID_ARG, "max_iter must be >= 1");
+    if (!(opts->mix > 0) || opts->mix > 1) return fail(DECBPM_ERR_INVALID_ARG, "mix must be in (0, 1]");
+    if (opts->kerr_mode != DECBPM_KERR_LUMPED && opts->kerr_mode != DECBPM_KERR_ELEMENT)
+        return fail(DECBPM_ERR_INVALID_ARG, "bad kerr_mode");
+    decbpm_plan_t P;
+    TRY(single_plan(mesh, 1, DECBPM_C128, &P));
+    if (P->order.empty()) TRY(plan_configure<double>(P, 1e-3, 1e-16));   // only for the device view of the mesh
+    return soliton_impl(mesh, P, opts, psi_dev, (cudaStream_t)stream, stats);
+}
+
+int decbpm_bessel_i_scaled(double a, double tol, int32_t n_max, double *out, int32_t *n_out) {
+    clear_error();
+    if (!(a >= 0) || !std::isfinite(a) || !(tol > 0) || !n_out) return fail(DECBPM_ERR_INVALID_ARG, "bad argument");
+    std::vector<double> sk;
+    bessel_i_scaled(a, tol, sk);
+    *n_out = int32_t(sk.size());
+    if (out) for (int32_t k = 0; k < std::min<int32_t>(n_max, int32_t(sk.size())); ++k) out[k] = sk[k];
+    return DECBPM_OK;
 }
 
 int decbpm_plan_get_config(decbpm_plan_t P, decbpm_plan_config *cfg) {

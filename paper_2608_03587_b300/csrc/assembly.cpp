@@ -488,6 +488,32 @@ void bessel_sequence(double a, int kmax, double *J) {
     for (int k = 0; k <= kmax; ++k) J[k] = Jall[k] / norm;
 }
 
+void bessel_i_scaled(double a, double tol, std::vector<double> &s) {
+    s.assign(1, 1.0);
+    if (a <= 0.0) return;
+    const int start = int(a + 40.0 + 12.0 * std::sqrt(a + 1.0));
+    std::vector<double> v(start + 2, 0.0);
+    double ip1 = 0.0, i = 1e-300;
+    v[start] = i;
+    for (int k = start; k >= 1; --k) {
+        const double im1 = (2.0 * k / a) * i + ip1;
+        ip1 = i;
+        i = im1;
+        v[k - 1] = i;
+        if (i > 1e200) {                                   // rescale to avoid overflow
+            for (int q = k - 1; q <= start; ++q) v[q] *= 1e-200;
+            i *= 1e-200; ip1 *= 1e-200;
+        }
+    }
+    double norm = v[0];
+    for (int k = 1; k <= start; ++k) norm += 2.0 * v[k];
+    int M = 0;
+    for (int k = 0; k <= start; ++k)
+        if (v[k] / norm >= tol * (v[0] / norm)) M = k;
+    s.resize(M + 1);
+    for (int k = 0; k <= M; ++k) s[k] = v[k] / norm;
+}
+
 int cheb_coefficients(const std::vector<double> &p, double rho, double h, double tol, Cheb &out) {
     using cd = std::complex<double>;
     const double c = 0.5 * rho, r = 0.5 * rho;

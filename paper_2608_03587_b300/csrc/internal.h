@@ -65,6 +65,12 @@ void build_sell(const Assembly &a, Sell &s);
 // Bessel J_0..J_kmax(a) (a >= 0) by Miller's backward recurrence.
 void bessel_sequence(double a, int kmax, double *J);
 
+// Scaled modified Bessel functions s_k = e^{-a} I_k(a), k = 0..M, a >= 0, by
+// Miller's backward recurrence normalised with I_0 + 2 sum_k I_k = e^a; M is
+// the first index from which every s_k < tol s_0.  They give the Chebyshev
+// series e^{-a x} = e^{a} [s_0 + 2 sum_k (-1)^k s_k T_k(x)] on [-1, 1].
+void bessel_i_scaled(double a, double tol, std::vector<double> &s);
+
 // Chebyshev expansion of f(lambda) = exp(i h g(lambda)), g = sum_n p_n (-lambda)^n,
 // on [0, rho] in x = (lambda - c) / r, c = r = rho / 2:
 //     f = exp(i theta0) sum_k a_k T_k(x),   theta0 = h g(c).

@@ -1408,6 +1408,145 @@ __global__ void __launch_bounds__(kRkThreads) rk_norm_final_kernel(const double 
     if (threadIdx.x == 0) *out = red[0];
 }
 
+// ------------------------------------------------------------ discrete soliton
+// Imaginary-z iteration for the fundamental nonlinear mode (FP64, one field,
+// internal order): with the potential frozen at the current field,
+//   H = p1 A + diag(d),  d_p = -v_p - N_p(|y|^2),
+// y <- e^{-tau (H - lo)} y is applied by Clenshaw's recurrence on
+// X = (H - c)/r, then renormalised to the requested power.
+
+// I <- |y|^2 (first) or beta |y|^2 + (1 - beta) I: the intensity that enters
+// the frozen potential (mixing damps the self-consistency iteration; at a
+// fixed point I = |y|^2)
+__global__ void sol_mix_kernel(const double2 *__restrict__ y, double *__restrict__ I, double beta, int32_t first,
+                               int32_t n) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n) return;
+    const double a = y[p].x * y[p].x + y[p].y * y[p].y;
+    I[p] = first ? a : beta * a + (1.0 - beta) * I[p];
+}
+
+// d_p = -v_p - N_p(I): lumped chib I_p or element-averaged cdiag I_p + sum_q c_pq I_q (Eq. 14)
+__global__ void sol_potential_kernel(MeshView<double> m, const double *__restrict__ I, int32_t kerr_mode,
+                                     double *__restrict__ d) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= m.n0) return;
+    double nr;
+    if (kerr_mode == 0) {
+        nr = m.chib[p] * I[p];
+    } else {
+        const int s = p >> 5, base = m.slice_ptr[s] + (p & 31), w = m.slice_w[s];
+        nr = m.cdiag[p] * I[p];
+        for (int j = 0; j < w; ++j) nr += m.coff[base + 32 * j] * I[m.col[base + 32 * j]];
+    }
+    d[p] = -m.v[p] - nr;
+}
+
+// (H g)_p = p1 (A g)_p + d_p g_p, (A g)_p = rA sum_q x_pq (g_p - g_q)
+__device__ __forceinline__ double2 sol_h_row(const MeshView<double> &m, const double2 *__restrict__ g,
+                                             const double *__restrict__ d, int p, double p1rA) {
+    const double2 a = a_row(m, g, p, 1.0);
+    const double2 gp = g[p];
+    return make_double2(p1rA * a.x + d[p] * gp.x, p1rA * a.y + d[p] * gp.y);
+}
+
+// out = alpha y + beta X g - (h ? h : 0),  X g = (H g - c g) / r
+__global__ void sol_stage_kernel(MeshView<double> m, const double2 *__restrict__ y, const double2 *__restrict__ g,
+                                 const double2 *__restrict__ h, double2 *__restrict__ out,
+                                 const double *__restrict__ d, double p1rA, double c, double rinv, double alpha,
+                                 double beta) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= m.n0) return;
+    double2 o = make_double2(alpha * y[p].x, alpha * y[p].y);
+    if (g) {
+        const double2 hg = sol_h_row(m, g, d, p, p1rA);
+        const double2 gp = g[p];
+        o.x += beta * (hg.x - c * gp.x) * rinv;
+        o.y += beta * (hg.y - c * gp.y) * rinv;
+    }
+    if (h) { o.x -= h[p].x; o.y -= h[p].y; }
+    out[p] = o;
+}
+
+__global__ void sol_apply_h_kernel(MeshView<double> m, const double2 *__restrict__ y, const double *__restrict__ d,
+                                   double p1rA, double2 *__restrict__ hy) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= m.n0) return;
+    hy[p] = sol_h_row(m, y, d, p, p1rA);
+}
+
+// Per-block partial reductions (fixed grid, fixed tree):
+//   mode 0: sum m |a|^2      mode 1: sum m Re(conj(a) b)      mode 2: sum m |b - mu a|^2
+//   mode 3: min and max of the real array r (two outputs per block)
+__global__ void __launch_bounds__(kRkThreads) sol_reduce_partial_kernel(int32_t mode, const double2 *__restrict__ a,
+                                                                         const double2 *__restrict__ b,
+                                                                         const double *__restrict__ r,
+                                                                         const double *__restrict__ m64, double mu,
+                                                                         int32_t n, double *__restrict__ part) {
+    __shared__ double red[2][kRkThreads];
+    const int lo = int((long long)n * blockIdx.x / gridDim.x), hi = int((long long)n * (blockIdx.x + 1) / gridDim.x);
+    double s0 = mode == 3 ? 1e300 : 0.0, s1 = -1e300;
+    for (int p = lo + threadIdx.x; p < hi; p += blockDim.x) {
+        if (mode == 0) s0 += m64[p] * (a[p].x * a[p].x + a[p].y * a[p].y);
+        else if (mode == 1) s0 += m64[p] * (a[p].x * b[p].x + a[p].y * b[p].y);
+        else if (mode == 2) {
+            const double ex = b[p].x - mu * a[p].x, ey = b[p].y - mu * a[p].y;
+            s0 += m64[p] * (ex * ex + ey * ey);
+        } else {
+            s0 = fmin(s0, r[p]);
+            s1 = fmax(s1, r[p]);
+        }
+    }
+    red[0][threadIdx.x] = s0;
+    red[1][threadIdx.x] = s1;
+    __syncthreads();
+    for (int half = kRkThreads / 2; half > 0; half >>= 1) {
+        if (threadIdx.x < half) {
+            if (mode == 3) {
+                red[0][threadIdx.x] = fmin(red[0][threadIdx.x], red[0][threadIdx.x + half]);
+                red[1][threadIdx.x] = fmax(red[1][threadIdx.x], red[1][threadIdx.x + half]);
+            } else {
+                red[0][threadIdx.x] += red[0][threadIdx.x + half];
+            }
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        part[2 * blockIdx.x] = red[0][0];
+        part[2 * blockIdx.x + 1] = red[1][0];
+    }
+}
+
+__global__ void __launch_bounds__(kRkThreads) sol_reduce_final_kernel(int32_t mode, const double *__restrict__ part,
+                                                                       int32_t nb, double *__restrict__ out) {
+    __shared__ double red[2][kRkThreads];
+    double s0 = mode == 3 ? 1e300 : 0.0, s1 = -1e300;
+    for (int b = threadIdx.x; b < nb; b += blockDim.x) {
+        if (mode == 3) { s0 = fmin(s0, part[2 * b]); s1 = fmax(s1, part[2 * b + 1]); }
+        else s0 += part[2 * b];
+    }
+    red[0][threadIdx.x] = s0;
+    red[1][threadIdx.x] = s1;
+    __syncthreads();
+    for (int half = kRkThreads / 2; half > 0; half >>= 1) {
+        if (threadIdx.x < half) {
+            if (mode == 3) {
+                red[0][threadIdx.x] = fmin(red[0][threadIdx.x], red[0][threadIdx.x + half]);
+                red[1][threadIdx.x] = fmax(red[1][threadIdx.x], red[1][threadIdx.x + half]);
+            } else {
+                red[0][threadIdx.x] += red[0][threadIdx.x + half];
+            }
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) { out[0] = red[0][0]; out[1] = red[1][0]; }
+}
+
+__global__ void sol_scale_kernel(double2 *__restrict__ y, double s, int32_t n) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p < n) { y[p].x *= s; y[p].y *= s; }
+}
+
 // ------------------------------------------------------------ plain path
 // Unfused single-field FP64 reference path: a CSR SpMV launch and an update
 // launch per Clenshaw term, a separate launch for each diagonal flow.

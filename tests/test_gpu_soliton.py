@@ -1,0 +1,122 @@
+"""GPU discrete soliton (imaginary-z iteration with frozen nonlinearity)
+against the oracle's self-consistent eigenmode solver (scipy eigsh), and the
+paper's soliton case: the mode is stationary under the fused march."""
+import math
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import bpm, dec  # noqa: E402
+from paper_2608_03587_b300 import _lib as L  # noqa: E402
+from paper_2608_03587_b300 import api  # noqa: E402
+from paper_2608_03587_b300 import workloads as W  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+DEV = torch.device("cuda:0")
+
+
+def fiber(n, seed):
+    coords, tris = W.mesh_disk_graded(4.0, n, 3.0, interfaces=(1.0,), seed=seed, grade_from=1.0)
+    V, chi = W.step_index_materials(coords, tris)
+    return coords, tris, V, chi
+
+
+def start_field(coords):
+    return np.exp(-(coords[:, 0] ** 2 + coords[:, 1] ** 2)).astype(np.complex128)
+
+
+def aligned(phi, ref, w):
+    """phi times the unit phase that best matches ref (the mode's global phase is free)."""
+    c = np.sum(w * np.conj(phi) * ref)
+    return phi * (c / abs(c))
+
+
+@pytest.mark.parametrize("kerr", ["lumped", "element"])
+def test_soliton_matches_oracle(kerr):
+    coords, tris, V, chi = fiber(1500, 71)
+    ops = dec.Operators(coords, tris, V, chi)
+    mesh = api.Mesh(coords, tris, V, chi)
+    P = 6.0
+    ref, mu_ref, _ = bpm.soliton(ops, (1.0,), P, kerr=kerr)
+    t = torch.from_numpy(start_field(coords)).to(DEV)
+    st = api.soliton(mesh, t, P, tau=0.5, tol=1e-11, kerr=kerr)
+    assert st["residual"] < 1e-11
+    assert st["mu"] == pytest.approx(mu_ref, rel=1e-9, abs=1e-9)
+    phi = aligned(t.cpu().numpy(), ref.astype(complex), ops.H0)
+    assert bpm.power(ops, phi) == pytest.approx(P, rel=1e-12)
+    assert bpm.relative_error(ops, phi, ref.astype(complex)) < 1e-8
+
+
+def test_soliton_bad_arguments():
+    coords, tris, V, chi = fiber(300, 72)
+    mesh = api.Mesh(coords, tris, V, chi)
+    t = torch.from_numpy(start_field(coords)).to(DEV)
+    for kw in ({"power": 0.0}, {"power": 1.0, "tau": -1.0}, {"power": 1.0, "tol": 0.0}, {"power": 1.0, "max_iter": 0},
+               {"power": 1.0, "mix": 0.0}, {"power": 1.0, "mix": 1.5}):
+        args = dict(power=1.0, tau=0.5, tol=1e-10, max_iter=10)
+        args.update(kw)
+        with pytest.raises(L.DecbpmError):
+            api.soliton(mesh, t, args.pop("power"), **args)
+    with pytest.raises(TypeError):
+        api.soliton(mesh, t.to(torch.complex64), 1.0)
+
+
+MU_REF = -3.5537      # the paper's reference soliton eigenvalue (Sec. "Fundamental soliton", SIP 1024 x 1024)
+
+
+def test_paper_soliton_case_long_run():
+    """The paper's soliton case: the fundamental mode of the step-index fiber
+    (Table II) with eigenvalue mu_ref = -3.5537, on a 25k-vertex mesh (the
+    paper quotes mu_DEC = -3.5540 at N = 25,217), propagated by the fused
+    FP64 march to z = 25.  The mode's power is not printed (Supp. Note 4 is
+    missing): it is found here by a secant search on mu(P).  With dz below
+    pi / lambda_max (no split-step resonance) the intensity error of Eq. 15
+    stays at the O(dz^2) splitting level: <= 3e-6 at dz = 1e-4 (the paper's
+    DEC curve sits near 1e-6), and falls ~9x from dz = 3e-4."""
+    coords, tris, V, chi = fiber(25000, 5)
+    mesh = api.Mesh(coords, tris, V, chi)
+    m = api.assemble_host(coords, tris, V, chi)["m"]
+    start = start_field(coords)
+
+    def mode(P):
+        t = torch.from_numpy(start).to(DEV)
+        st = api.soliton(mesh, t, P, tau=0.05, tol=1e-11, max_iter=5000)
+        assert st["residual"] < 1e-10
+        return t, st["mu"]
+
+    Ps, mus = [9.0, 10.0], []
+    for P in Ps:
+        mus.append(mode(P)[1])
+    for _ in range(8):
+        P = Ps[-1] + (MU_REF - mus[-1]) * (Ps[-1] - Ps[-2]) / (mus[-1] - mus[-2])
+        t, mu = mode(P)
+        Ps.append(P)
+        mus.append(mu)
+        if abs(mu - MU_REF) < 1e-8:
+            break
+    assert abs(mus[-1] - MU_REF) < 1e-8
+    assert 9.5 < Ps[-1] < 11.0                           # below the collapse power (11.70 for chi = 1)
+    phi = t.cpu().numpy()
+    I0 = np.abs(phi) ** 2
+
+    def erel(x):
+        I = np.abs(x.cpu().numpy()) ** 2
+        return math.sqrt(np.sum(m * (I - I0) ** 2) / np.sum(m * I0 ** 2))
+
+    worst = {}
+    for dz in (3e-4, 1e-4):
+        x = torch.from_numpy(phi).to(DEV)
+        n = int(round(1.0 / dz))
+        errs = []
+        for _ in range(25):
+            api.propagate(mesh, x, dz, n)
+            errs.append(erel(x))
+        worst[dz] = max(errs)
+    assert worst[1e-4] < 3e-6, worst
+    assert 5.0 < worst[3e-4] / worst[1e-4] < 12.0, worst

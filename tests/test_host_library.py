@@ -181,3 +181,18 @@ def test_null_arguments_are_rejected(lib):
     h = ctypes.c_void_p()
     assert lib.decbpm_plan_create(None, 0, None, L.C64, ctypes.byref(h)) == L.ERR_INVALID_ARG
     assert lib.decbpm_mesh_destroy(None) == L.OK
+
+
+def test_bessel_i_scaled_matches_scipy():
+    """Coefficients of the Chebyshev series of e^{-a x} used by the soliton
+    iteration: e^{-a} I_k(a) by Miller's recurrence, against scipy.special.ive."""
+    from scipy.special import ive
+
+    from paper_2608_03587_b300 import api
+    assert list(api.bessel_i_scaled(0.0)) == [1.0]
+    for a in (1e-3, 0.5, 3.0, 40.0, 700.0, 5000.0):
+        s = api.bessel_i_scaled(a, 1e-17)
+        k = np.arange(len(s))
+        assert np.max(np.abs(s - ive(k, a))) < 1e-15 * max(1.0, ive(0, a))
+        assert ive(len(s), a) < 1e-17 * ive(0, a) * 1.01          # truncated where the tail is negligible
+        assert s[0] + 2 * s[1:].sum() == pytest.approx(1.0, abs=1e-13)
