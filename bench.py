@@ -173,6 +173,9 @@ def run_ours(args, rank, world, local_rank):
     fields = [int(p.shape[1]) for p in wl.psi0]
     plan = api.Plan(meshes, fields, "c64")
     setup_s = time.time() - t0
+    t_tune = time.time()
+    tune = plan.autotune(wl.dz, trial_steps=3) if args.variant == "fused" else None
+    tune_s = time.time() - t_tune
     psis = [torch.from_numpy(p).to(dev, torch.complex64).contiguous() for p in wl.psi0]
     infos = [m.info() for m in meshes]
     degrees = [plan.degree(i, wl.dz) for i in range(len(meshes))]
@@ -227,7 +230,7 @@ def run_ours(args, rank, world, local_rank):
     # kernels of ours per timed call: permute in / out per mesh, the march
     # kernel, two diagnostic kernels per mesh
     launches = 1 + 4 * len(meshes)
-    tiled = cfg.get("tile_slots", 0) > 0 and args.variant == "fused"
+    tiled = bool(cfg.get("fused_kernel", 0)) and args.variant == "fused"
     kernel_name = "march_tile_kernel" if tiled else "march_kernel<float,%d>" % cfg["fields_padded"]
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -241,7 +244,11 @@ def run_ours(args, rank, world, local_rank):
             "cheb_degree_min": int(min(degrees)), "cheb_degree_max": int(max(degrees)),
             "ordering": "hilbert", "parallelism": "replicas" if world > 1 else "single",
             "grid": cfg["tile_grid"] if tiled else cfg["grid"], "block": cfg["tile_block"] if tiled else cfg["block"],
-            "march_kernel": kernel_name, "tile_slots": cfg["tile_slots"] if tiled else 0,
+            "march_kernel": kernel_name, "tile_slots": cfg["tile_slots_used"] if tiled else 0,
+            "forward_walk": cfg["forward_walk"],
+            "autotune": None if tune is None else {k: tune[k] for k in ("kernel", "ctas_per_sm", "tile_slots",
+                                                                        "forward_walk", "ms_per_step", "candidates")},
+            "autotune_s": round(tune_s, 2),
             "cuda_graph": bool(cfg["graphs"]),
             "l2": "working set %.2f GB > 126 MB L2; no flush" % (units_per_step * 8 * 4 / 1e9),
             "setup_s": round(setup_s, 2),

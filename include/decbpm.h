@@ -233,8 +233,35 @@ typedef struct {
     int32_t tile_slot_bytes;
     int32_t tile_grid;     /* CTAs of the tile-staged launch */
     int32_t tile_block;    /* threads per CTA of the tile-staged launch (16 compute + 3 copy warps) */
+    int32_t tuned;         /* 1 once decbpm_plan_autotune chose the launch shapes below */
+    int32_t fused_kernel;  /* FUSED runs: 1 the tile-staged kernel, 0 the row kernel (grid above) */
+    int32_t tile_slots_used; /* ring slots the tile-staged kernel uses */
+    int32_t forward_walk;  /* 1: odd stages do not walk backwards */
 } decbpm_plan_config;
 int decbpm_plan_get_config(decbpm_plan_t plan, decbpm_plan_config *cfg);
+
+/* Autotuner of the FUSED variant's launch shapes (no counterpart in the paper:
+ * the kernels' own tuning).  Times short trial marches of `trial_steps` steps
+ * (1..1000) at step dz on the plan's internal buffers, for every candidate:
+ * the tile-staged kernel with 3 or 2 ring slots (complex64 plans with 9..16
+ * fields), the row kernel with 1..max co-resident CTAs per SM, each with and
+ * without the reverse walk of odd stages; keeps the fastest for this plan and
+ * caches it for the process (key: the meshes' content, field counts,
+ * precision, dz, kerr_mode), so another plan of the same problem takes it
+ * without timing (out->from_cache = 1).  Results do not depend on the choice:
+ * every candidate does the same arithmetic per row.  Synchronous; the plan's
+ * internal buffers are overwritten (they hold nothing between calls). */
+typedef struct {
+    int32_t variant;       /* DECBPM_VARIANT_FUSED: the tile-staged kernel; DECBPM_VARIANT_ROWS: the row kernel */
+    int32_t ctas_per_sm;   /* row kernel: co-resident CTAs per SM (tile kernel: 1) */
+    int32_t tile_slots;    /* tile kernel: ring slots (0 for the row kernel) */
+    int32_t forward_walk;  /* 1: odd stages walk forwards */
+    double  ms_per_step;   /* best trial time per step */
+    int32_t candidates;    /* configurations timed (0 when taken from the cache) */
+    int32_t from_cache;
+} decbpm_tune_result;
+int decbpm_plan_autotune(decbpm_plan_t plan, double dz, int32_t kerr_mode, int32_t trial_steps, void *stream,
+                         decbpm_tune_result *out);
 
 /* Device time in ms, from CUDA events recorded on the launch stream, from the
  * start of the first march-kernel launch to the end of the last one in the

@@ -66,10 +66,22 @@ class PlanConfig(ctypes.Structure):
     _fields_ = [("grid", ctypes.c_int32), ("block", ctypes.c_int32), ("fields_padded", ctypes.c_int32),
                 ("graphs", ctypes.c_int32), ("stages", ctypes.c_int32), ("n_meshes", ctypes.c_int32),
                 ("tile_slots", ctypes.c_int32), ("tile_slot_bytes", ctypes.c_int32), ("tile_grid", ctypes.c_int32),
-                ("tile_block", ctypes.c_int32)]
+                ("tile_block", ctypes.c_int32), ("tuned", ctypes.c_int32), ("fused_kernel", ctypes.c_int32),
+                ("tile_slots_used", ctypes.c_int32), ("forward_walk", ctypes.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class TuneResult(ctypes.Structure):
+    _fields_ = [("variant", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32), ("tile_slots", ctypes.c_int32),
+                ("forward_walk", ctypes.c_int32), ("ms_per_step", ctypes.c_double), ("candidates", ctypes.c_int32),
+                ("from_cache", ctypes.c_int32)]
+
+    def as_dict(self):
+        d = {k: getattr(self, k) for k, _ in self._fields_}
+        d["kernel"] = "tile" if self.variant == VARIANT_FUSED else "rows"
+        return d
 
 
 class Rk45Opts(ctypes.Structure):
@@ -128,6 +140,7 @@ SIGNATURES = {
                                           ctypes.POINTER(Diag)]),
     "decbpm_plan_degree": (_i32, [_vp, _i32, _dbl, _i32, _dbl]),
     "decbpm_plan_get_config": (_i32, [_vp, ctypes.POINTER(PlanConfig)]),
+    "decbpm_plan_autotune": (_i32, [_vp, _dbl, _i32, _i32, _vp, ctypes.POINTER(TuneResult)]),
     "decbpm_plan_last_march_ms": (_i32, [_vp, ctypes.POINTER(ctypes.c_double)]),
     "decbpm_selftest_barrier": (_i32, [_i32, _i64, _vp]),
     "decbpm_mesh_set_potential": (_i32, [_vp, _c_double_p]),

@@ -257,6 +257,14 @@ class Plan:
         L.check(lib.decbpm_plan_propagate_host(self._h, ctypes.byref(prm), ptrs, _stream_handle(stream), buf))
         return _diag_array(buf, npts, sum(self.fields))
 
+    def autotune(self, dz, trial_steps=3, kerr="lumped", stream=None) -> dict:
+        """decbpm_plan_autotune: time the FUSED variant's launch shapes on
+        trial marches and keep the fastest (cached per problem for the process)."""
+        r = L.TuneResult()
+        L.check(_lib().decbpm_plan_autotune(self._h, float(dz), L.KERR_LUMPED if kerr == "lumped" else L.KERR_ELEMENT,
+                                            int(trial_steps), _stream_handle(stream), ctypes.byref(r)))
+        return r.as_dict()
+
     def config(self) -> dict:
         c = L.PlanConfig()
         L.check(_lib().decbpm_plan_get_config(self._h, ctypes.byref(c)))

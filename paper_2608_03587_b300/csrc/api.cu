@@ -8,6 +8,7 @@
 #include <mutex>
 #include <memory>
 #include <numeric>
+#include <string>
 #include <tuple>
 #include <vector>
 
@@ -272,6 +273,12 @@ struct decbpm_plan_s {
     bool tile_mode = false;
     int tile_grid = 0, n_slots = 0, slot_bytes = 0, off_psi = 0, off_h = 0, off_lcol = 0, off_x = 0, off_hdr = 0;
     int slot_entries = 0;
+    // launch configuration of the FUSED variant (defaults until decbpm_plan_autotune picks one)
+    int max_per_sm = 1;                          // co-resident row-kernel CTAs per SM
+    int tune_rows = 0;                           // 1: FUSED runs the row kernel even where tiles are possible
+    int tune_slots = 0;                          // tile ring slots (0: all that fit)
+    int forward_walk = 0;                        // 1: no reverse walk on odd stages
+    bool tuned = false;
     std::vector<int> tile_begin;
     int32_t *active_tiles = nullptr;
     int active_tiles_cap = 0, total_tiles = 0;
@@ -419,7 +426,8 @@ static int plan_create_impl(const decbpm_mesh_t *meshes, int32_t n, const int32_
     int per_sm = 0;
     CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, march_kernel_ptr(precision, P->bpad), P->block, 0));
     if (per_sm < 1) return fail(DECBPM_ERR_CUDA, "march kernel cannot be resident with %d threads", P->block);
-    P->grid = P->num_sms * std::min(per_sm, 4);
+    P->max_per_sm = std::min(per_sm, 4);
+    P->grid = P->num_sms * P->max_per_sm;
     TRY(setup_tiles(P.get()));
     *out = P.release();
     return DECBPM_OK;
@@ -588,6 +596,7 @@ static int launch_march(decbpm_plan_t P, cudaStream_t s, int n_steps, int kerr_m
     mp.barrier = P->barrier;
     mp.status = P->status;
     mp.timeout_ns = kBarrierTimeoutNs;
+    mp.forward_walk = P->forward_walk;
     CK(cudaMemsetAsync(P->barrier, 0, sizeof(unsigned long long), s));
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(P->grid);
@@ -602,9 +611,10 @@ static int launch_march(decbpm_plan_t P, cudaStream_t s, int n_steps, int kerr_m
     void *args[] = {&mp};
     const void *fn = march_ptr_for<R>(P->bpad);
     if constexpr (sizeof(R) == 4) {
-        if (P->tile_mode && variant == DECBPM_VARIANT_FUSED) {
+        if (P->tile_mode && variant == DECBPM_VARIANT_FUSED && !P->tune_rows) {
+            const int slots = P->tune_slots > 0 ? std::min(P->tune_slots, P->n_slots) : P->n_slots;
             mp.active_tiles = P->active_tiles;
-            mp.n_slots = P->n_slots;
+            mp.n_slots = slots;
             mp.slot_bytes = P->slot_bytes;
             mp.off_psi = P->off_psi;
             mp.off_h = P->off_h;
@@ -614,7 +624,7 @@ static int launch_march(decbpm_plan_t P, cudaStream_t s, int n_steps, int kerr_m
             mp.slot_entries = P->slot_entries;
             cfg.gridDim = dim3(P->tile_grid);
             cfg.blockDim = dim3(kTileThreads);
-            cfg.dynamicSmemBytes = size_t(P->n_slots) * P->slot_bytes;
+            cfg.dynamicSmemBytes = size_t(slots) * P->slot_bytes;
             fn = (const void *)march_tile_kernel;
         }
     }
@@ -1274,6 +1284,137 @@ static int soliton_impl(decbpm_mesh_t mesh, decbpm_plan_t P, const decbpm_solito
     return DECBPM_OK;
 }
 
+
+// ============================================================== autotuner
+// Launch shapes of the FUSED march picked by timing: for complex64 plans that
+// can run the tile-staged kernel, {tile kernel with 3 or 2 ring slots, row
+// kernel with 1..max CTAs per SM} x {reverse walk on odd stages, forward
+// only}; otherwise the row kernel's CTAs per SM x walk order.  Every
+// candidate performs the same arithmetic per row (results are bitwise
+// identical), so only time decides.  Each candidate runs one untimed launch
+// and then the best of two timed launches of `trial_steps` steps on the
+// plan's internal buffers (zeroed first: their contents are scratch between
+// calls).  The winner is cached for the process, keyed by the meshes'
+// content fingerprints, the field counts, the precision, dz and kerr_mode.
+struct TuneChoice { int rows, per_sm, slots, forward; double ms; };
+static std::mutex g_tune_mutex;
+static std::map<std::string, TuneChoice> g_tune_cache;
+
+static uint64_t fnv(uint64_t h, const void *p, size_t n) {
+    const unsigned char *c = static_cast<const unsigned char *>(p);
+    for (size_t i = 0; i < n; ++i) h = (h ^ c[i]) * 1099511628211ull;
+    return h;
+}
+static std::string tune_key(decbpm_plan_t P, double dz, int kerr_mode) {
+    std::string k;
+    char buf[96];
+    for (size_t i = 0; i < P->meshes.size(); ++i) {
+        const decbpm_mesh_t m = P->meshes[i];
+        uint64_t h = 1469598103934665603ull;
+        h = fnv(h, &m->A.n0, sizeof(m->A.n0));
+        h = fnv(h, &m->A.rho, sizeof(m->A.rho));
+        h = fnv(h, m->S.slice_w.data(), m->S.slice_w.size() * sizeof(int32_t));
+        h = fnv(h, m->S.col.data(), m->S.col.size() * sizeof(int32_t));
+        h = fnv(h, m->A.p.data(), m->A.p.size() * sizeof(double));
+        std::snprintf(buf, sizeof(buf), "%016llx:%d;", (unsigned long long)h, P->B[i]);
+        k += buf;
+    }
+    std::snprintf(buf, sizeof(buf), "p%d|dz%.17g|k%d", P->precision, dz, kerr_mode);
+    return k + buf;
+}
+
+static void apply_choice(decbpm_plan_t P, const TuneChoice &c) {
+    P->tune_rows = c.rows;
+    P->tune_slots = c.slots;
+    P->forward_walk = c.forward;
+    P->grid = P->num_sms * c.per_sm;
+    P->tuned = true;
+    for (auto &g : P->graphs) cudaGraphExecDestroy(g.second);   // captured launches carry the old shape
+    P->graphs.clear();
+}
+
+static decbpm_tune_result tune_result(const TuneChoice &c, int trial_steps, int n_cand, int from_cache) {
+    decbpm_tune_result r{};
+    r.variant = c.rows ? DECBPM_VARIANT_ROWS : DECBPM_VARIANT_FUSED;
+    r.ctas_per_sm = c.rows ? c.per_sm : 1;
+    r.tile_slots = c.slots;
+    r.forward_walk = c.forward;
+    r.ms_per_step = c.ms / trial_steps;
+    r.candidates = n_cand;
+    r.from_cache = from_cache;
+    return r;
+}
+
+template <typename R>
+static int autotune_impl(decbpm_plan_t P, double dz, int kerr_mode, int trial_steps, cudaStream_t s,
+                         decbpm_tune_result *out) {
+    TRY(plan_configure<R>(P, dz, P->precision == DECBPM_C64 ? 1e-9 : 1e-16));
+    const std::string key = tune_key(P, dz, kerr_mode);
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mutex);
+        auto it = g_tune_cache.find(key);
+        if (it != g_tune_cache.end()) {
+            apply_choice(P, it->second);
+            if (out) *out = tune_result(it->second, trial_steps, 0, 1);
+            return DECBPM_OK;
+        }
+    }
+    const size_t cs = csize(P->precision);
+    for (size_t i = 0; i < P->meshes.size(); ++i) {
+        const size_t bytes = size_t(P->meshes[i]->A.n0) * P->bpad * cs;
+        CK(cudaMemsetAsync(P->psi[i], 0, bytes, s));
+        CK(cudaMemsetAsync(P->b0[i], 0, bytes, s));
+        CK(cudaMemsetAsync(P->b1[i], 0, bytes, s));
+        CK(cudaMemsetAsync(P->b2[i], 0, bytes, s));
+    }
+    std::vector<TuneChoice> cand;
+    for (int fw = 0; fw <= 1; ++fw) {
+        if (P->tile_mode)
+            for (int sl = P->n_slots; sl >= 2; --sl) cand.push_back({0, P->max_per_sm, sl, fw, 0.0});
+        for (int ps = 1; ps <= P->max_per_sm; ++ps) cand.push_back({1, ps, 0, fw, 0.0});
+    }
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    TuneChoice best{};
+    best.ms = 1e300;
+    int rc = DECBPM_OK;
+    for (TuneChoice &c : cand) {
+        apply_choice(P, c);
+        if (cudaMemsetAsync(P->status, 0, sizeof(int), s) != cudaSuccess) { rc = fail(DECBPM_ERR_CUDA, "memset failed"); break; }
+        double t_best = 1e300;
+        for (int rep = 0; rep < 3 && rc == DECBPM_OK; ++rep) {
+            if (cudaEventRecord(e0, s) != cudaSuccess) { rc = fail(DECBPM_ERR_CUDA, "event record failed"); break; }
+            rc = launch_march<R>(P, s, trial_steps, kerr_mode, dz, DECBPM_VARIANT_FUSED);
+            if (rc != DECBPM_OK) break;
+            cudaEventRecord(e1, s);
+            if (cudaEventSynchronize(e1) != cudaSuccess) { rc = fail(DECBPM_ERR_CUDA, "autotune trial failed"); break; }
+            float ms = 0;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (rep > 0) t_best = std::min(t_best, double(ms));   // the first launch is untimed
+        }
+        if (rc != DECBPM_OK) break;
+        int status = 0;
+        if (cudaMemcpy(&status, P->status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) {
+            rc = fail(DECBPM_ERR_CUDA, "status read failed");
+            break;
+        }
+        if (status != 0) { rc = fail(status, "device reported status %d during autotuning", status); break; }
+        c.ms = t_best;
+        if (t_best < best.ms) best = c;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc != DECBPM_OK) return rc;
+    apply_choice(P, best);
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mutex);
+        g_tune_cache[key] = best;
+    }
+    if (out) *out = tune_result(best, trial_steps, int(cand.size()), 0);
+    return DECBPM_OK;
+}
+
 // ============================================================== C ABI
 extern "C" {
 
@@ -1591,6 +1732,17 @@ int decbpm_bessel_i_scaled(double a, double tol, int32_t n_max, double *out, int
     return DECBPM_OK;
 }
 
+int decbpm_plan_autotune(decbpm_plan_t P, double dz, int32_t kerr_mode, int32_t trial_steps, void *stream,
+                         decbpm_tune_result *out) {
+    clear_error();
+    if (!P) return fail(DECBPM_ERR_INVALID_ARG, "plan is NULL");
+    if (!(dz > 0) || !std::isfinite(dz)) return fail(DECBPM_ERR_INVALID_ARG, "dz must be finite and > 0");
+    if (trial_steps < 1 || trial_steps > 1000) return fail(DECBPM_ERR_INVALID_ARG, "trial_steps must be in 1..1000");
+    if (kerr_mode != DECBPM_KERR_LUMPED && kerr_mode != DECBPM_KERR_ELEMENT) return fail(DECBPM_ERR_INVALID_ARG, "bad kerr_mode");
+    if (P->precision == DECBPM_C64) return autotune_impl<float>(P, dz, kerr_mode, trial_steps, (cudaStream_t)stream, out);
+    return autotune_impl<double>(P, dz, kerr_mode, trial_steps, (cudaStream_t)stream, out);
+}
+
 int decbpm_plan_get_config(decbpm_plan_t P, decbpm_plan_config *cfg) {
     if (!P || !cfg) return fail(DECBPM_ERR_INVALID_ARG, "NULL argument");
     cfg->grid = P->grid;
@@ -1603,6 +1755,11 @@ int decbpm_plan_get_config(decbpm_plan_t P, decbpm_plan_config *cfg) {
     cfg->tile_slot_bytes = P->tile_mode ? P->slot_bytes : 0;
     cfg->tile_grid = P->tile_mode ? P->tile_grid : 0;
     cfg->tile_block = P->tile_mode ? kTileThreads : 0;
+    cfg->tuned = P->tuned ? 1 : 0;
+    cfg->fused_kernel = (P->tile_mode && !P->tune_rows) ? 1 : 0;
+    cfg->tile_slots_used =
+        (P->tile_mode && !P->tune_rows) ? (P->tune_slots > 0 ? std::min(P->tune_slots, P->n_slots) : P->n_slots) : 0;
+    cfg->forward_walk = P->forward_walk;
     return DECBPM_OK;
 }
 

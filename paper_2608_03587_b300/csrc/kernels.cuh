@@ -24,9 +24,6 @@ namespace decbpm {
 #ifndef DECBPM_FPT4
 #define DECBPM_FPT4 4           // most complex64 values per thread (2, 4 or 8)
 #endif
-#ifndef DECBPM_REVERSE_ODD
-#define DECBPM_REVERSE_ODD 1    // odd stages walk the CTA's items backwards (L2 reuse between stages)
-#endif
 
 constexpr int kMaxMeshes = 64;
 constexpr int kMaxFields = 64;
@@ -180,6 +177,8 @@ template <typename R> struct MarchParams {
     unsigned long long *barrier; // zeroed before every launch
     int *status;                 // 0, or a DECBPM_ERR_* code written by the device
     long long timeout_ns;        // limit of one barrier wait
+    int32_t forward_walk;        // 0: odd stages walk each CTA's share backwards (a stage starts on the
+                                 // rows the previous one wrote last: L2 reuse); 1: always forwards
     // tile-staged march only
     const int32_t *active_tiles; // [S]: tiles of meshes with M > S-1-s
     int32_t n_slots, slot_bytes; // shared-memory ring of tile windows
@@ -336,7 +335,8 @@ __device__ __forceinline__ void load_meta(const MeshView<R> *sv, const int32_t *
 // are in flight, so one memory latency (not three) is exposed per item.
 template <typename R, int BPAD>
 __device__ __forceinline__ void clenshaw_stage(const MeshView<R> *sv, const StageCoef<R> *scoef, const int32_t *s_begin,
-                                               int n_meshes, int n_active, int k, R h_post, int kerr_mode) {
+                                               int n_meshes, int n_active, int k, R h_post, int kerr_mode,
+                                               bool rev_odd) {
     using G = Geo<R, BPAD>;
     using C = typename CT<R>::c2;
     constexpr int FPT = G::FPT;
@@ -348,7 +348,7 @@ __device__ __forceinline__ void clenshaw_stage(const MeshView<R> *sv, const Stag
     const int row_lane0 = lane & ~(G::TPR - 1);
     // items of this CTA in walk order: forward on even stages, backward on odd
     // ones, so a stage starts on the rows the previous stage wrote last
-    const bool rev = DECBPM_REVERSE_ODD && (k & 1);
+    const bool rev = rev_odd && (k & 1);
     const int n_mine = hi - lo;
     auto item_at = [&](int i) { return rev ? hi - 1 - i : lo + i; };
     int idx = warp;
@@ -578,7 +578,8 @@ __global__ void __launch_bounds__(256, MarchMinBlocks<R>::value) march_kernel(Ma
             for (int i = threadIdx.x; i < P.n_meshes; i += blockDim.x)
                 if (s_view[i].M > k) s_coef[i] = s_view[i].coef[k];
             __syncthreads();
-            clenshaw_stage<R, BPAD>(s_view, s_coef, s_begin, P.n_meshes, P.active_items[s], k, h_post, P.kerr_mode);
+            clenshaw_stage<R, BPAD>(s_view, s_coef, s_begin, P.n_meshes, P.active_items[s], k, h_post, P.kerr_mode,
+                                    P.forward_walk == 0);
             if (!grid_barrier(P.barrier, target, P.status, P.timeout_ns)) return;
         }
         if (P.kerr_mode != 0) {
@@ -699,7 +700,7 @@ __device__ __forceinline__ TileRange tile_range(const MarchParams<float> &P, int
     const int lo = int((long long)n_act * blockIdx.x / gridDim.x);
     const int hi = int((long long)n_act * (blockIdx.x + 1) / gridDim.x);
     const int k = P.S - 1 - s;
-    return TileRange{lo, hi - lo, DECBPM_REVERSE_ODD && (k & 1)};
+    return TileRange{lo, hi - lo, P.forward_walk == 0 && (k & 1)};
 }
 
 // Copy-warp look-ahead: the descriptor and the first 96 halo rows of each

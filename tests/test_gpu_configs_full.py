@@ -1,0 +1,109 @@
+"""The workloads at their full sizes and run lengths (FP32 path as the bench
+launches it), checked where the FP64 oracle cannot follow: the GPU FP64 march,
+itself checked against the oracle (test_gpu_parity.py, including one full-size
+step of the 200k-vertex disk), stands in for the oracle over long runs, and
+properties that hold at any size cover the rest:
+  * FP32 vs FP64 on the same launch: <= 1e-4 relative (*0-weighted L2) over
+    the run length compared;
+  * without the absorber, the FP64 march conserves the power to round-off;
+  * with the absorber, the power never increases, and fields stay finite."""
+import math
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import dec  # noqa: E402
+from paper_2608_03587_b300 import api  # noqa: E402
+from paper_2608_03587_b300 import workloads as W  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+DEV = torch.device("cuda:0")
+
+
+def rel(w, a, b):
+    """*0-weighted relative L2 difference (fields [N0] or [N0, B])."""
+    a = np.asarray(a, dtype=np.complex128)
+    b = np.asarray(b, dtype=np.complex128)
+    ww = w if a.ndim == 1 else w[:, None]
+    return math.sqrt(float(np.sum(ww * np.abs(a - b) ** 2)) / float(np.sum(ww * np.abs(b) ** 2)))
+
+
+def test_gaussian_disk_full_run_fp32_vs_fp64():
+    """200k-vertex graded disk, elliptic Gaussian at half the collapse power,
+    absorber, dz = 5e-4, the full 10,000 steps."""
+    wl = W.gaussian_disk()
+    m = wl.meshes[0]
+    w = dec.star0(m.coords, m.cells)
+    mesh = api.Mesh.from_workload(m)
+    a = torch.from_numpy(wl.psi0[0][:, 0]).to(DEV, torch.complex128)
+    b = torch.from_numpy(wl.psi0[0][:, 0]).to(DEV, torch.complex64)
+    da = api.propagate(mesh, a, wl.dz, wl.n_steps, diag_every=1000)
+    db = api.propagate(mesh, b, wl.dz, wl.n_steps, diag_every=1000)
+    assert rel(w, b.cpu().numpy(), a.cpu().numpy()) <= 1e-4
+    p = da["power"][:, 0]
+    assert np.all(np.diff(p) <= 1e-12 * p[0])
+    assert np.allclose(db["power"][:, 0], p, rtol=1e-4)
+
+
+def test_vortex_multimode_full_size():
+    """1M-vertex large-core step-index guide, charge-1 vortex: FP32 vs FP64
+    over the first 500 steps, FP64 power conservation without the absorber,
+    and the full 20,000-step FP32 run (power non-increasing, finite)."""
+    wl = W.vortex_multimode()
+    m = wl.meshes[0]
+    w = dec.star0(m.coords, m.cells)
+    mesh = api.Mesh.from_workload(m)
+    assert mesh.n_vertices >= 950_000
+    psi0 = wl.psi0[0][:, 0]
+    a = torch.from_numpy(psi0).to(DEV, torch.complex128)
+    b = torch.from_numpy(psi0).to(DEV, torch.complex64)
+    api.propagate(mesh, a, wl.dz, 500)
+    api.propagate(mesh, b, wl.dz, 500)
+    assert rel(w, b.cpu().numpy(), a.cpu().numpy()) <= 1e-4
+    # no absorber: power conserved by the FP64 march (unitary propagator, exact phase flow)
+    free = api.Mesh(m.coords, m.cells, m.V_cell, m.chi_cell)
+    c = torch.from_numpy(psi0).to(DEV, torch.complex128)
+    d = api.propagate(free, c, wl.dz, 200, diag_every=50)["power"][:, 0]
+    P0 = float(np.sum(w * np.abs(psi0) ** 2))
+    assert np.max(np.abs(d - P0)) <= 1e-11 * P0
+    # the full run in FP32
+    b = torch.from_numpy(psi0).to(DEV, torch.complex64)
+    dd = api.propagate(mesh, b, wl.dz, wl.n_steps, diag_every=2000)["power"][:, 0]
+    assert np.all(np.isfinite(dd)) and torch.isfinite(torch.view_as_real(b)).all()
+    assert np.all(np.diff(dd) <= 1e-6 * P0) and dd[0] <= P0 * (1 + 1e-6)
+
+
+def test_batched_fibers_full_run():
+    """The bench workload (16 fibers, 20k..500k vertices, 16 fields each):
+    FP32 vs FP64 on the whole batch over 20 steps; the full 5,000-step FP32
+    run (tile-staged kernel), whose four smallest meshes are compared with an
+    FP64 plan of those meshes over the same 5,000 steps."""
+    wl = W.batched_fibers()
+    meshes = [api.Mesh.from_workload(mm, p=wl.p) for mm in wl.meshes]
+    ws = [dec.star0(mm.coords, mm.cells) for mm in wl.meshes]
+    plan32 = api.Plan(meshes, [16] * len(meshes), "c64")
+    assert plan32.config()["tile_slots"] >= 2
+    plan64 = api.Plan(meshes, [16] * len(meshes), "c128")
+    a = [torch.from_numpy(p).to(DEV, torch.complex128) for p in wl.psi0]
+    b = [torch.from_numpy(p).to(DEV, torch.complex64) for p in wl.psi0]
+    plan64.propagate(a, wl.dz, 20)
+    plan32.propagate(b, wl.dz, 20)
+    for w, x, y in zip(ws, b, a):
+        assert rel(w, x.cpu().numpy(), y.cpu().numpy()) <= 1e-5 * 20
+    # full FP32 run from the launch fields
+    b = [torch.from_numpy(p).to(DEV, torch.complex64) for p in wl.psi0]
+    diag = plan32.propagate(b, wl.dz, wl.n_steps, diag_every=1000)
+    P = diag["power"]
+    assert np.all(np.isfinite(P)) and np.all(np.diff(P, axis=0) <= 1e-6)
+    small = list(np.argsort([mm.n_vertices for mm in wl.meshes])[:4])
+    plan_s = api.Plan([meshes[i] for i in small], [16] * 4, "c128")
+    c = [torch.from_numpy(wl.psi0[i]).to(DEV, torch.complex128) for i in small]
+    plan_s.propagate(c, wl.dz, wl.n_steps)
+    for j, i in enumerate(small):
+        assert rel(ws[i], b[i].cpu().numpy(), c[j].cpu().numpy()) <= 1e-4

@@ -288,6 +288,47 @@ def test_tile_staged_full_bench_batch_one_step():
         assert torch.equal(x, y)
 
 
+@pytest.mark.parametrize("precision", ["c64", "c128"])
+def test_autotuner_picks_a_shape_without_changing_results(precision):
+    """decbpm_plan_autotune times the FUSED launch shapes (tile-staged kernel
+    with 3/2 ring slots, row kernel with 1..max CTAs per SM, walk order) and
+    keeps the fastest: the fields it produces are bit for bit those of the
+    default shape; a second plan of the same problem takes the cached choice."""
+    specs = [(4000, 16, 81), (12000, 16, 82), (600, 9, 83)]
+    meshes, psis = [], []
+    for n, B, seed in specs:
+        coords, tris = W.mesh_disk_graded(4.0, n, 3.0, interfaces=(1.0,), seed=seed, grade_from=1.0)
+        V, chi = W.step_index_materials(coords, tris)
+        sigma = W.absorber_profile(coords, 4.0, 20.0)
+        meshes.append(api.Mesh(coords, tris, V, chi, sigma))
+        psis.append(W.hg_superpositions(coords, B, np.random.default_rng(seed)))
+    dt = torch.complex64 if precision == "c64" else torch.complex128
+    dz = 5e-4
+    ref_plan = api.Plan(meshes, [p.shape[1] for p in psis], precision)
+    a = [to_dev(p, dt) for p in psis]
+    ref_plan.propagate(a, dz, 7)
+    plan = api.Plan(meshes, [p.shape[1] for p in psis], precision)
+    tune = plan.autotune(dz, trial_steps=2)
+    assert tune["from_cache"] == 0 and tune["candidates"] >= 2 and tune["ms_per_step"] > 0
+    cfg = plan.config()
+    assert cfg["tuned"] == 1
+    assert cfg["fused_kernel"] == (1 if tune["kernel"] == "tile" else 0)
+    if precision == "c128":
+        assert tune["kernel"] == "rows"
+    b = [to_dev(p, dt) for p in psis]
+    plan.propagate(b, dz, 7)
+    for x, y in zip(a, b):
+        assert torch.equal(x, y)
+    again = api.Plan(meshes, [p.shape[1] for p in psis], precision).autotune(dz, trial_steps=2)
+    assert again["from_cache"] == 1
+    keys = ("kernel", "ctas_per_sm", "tile_slots", "forward_walk")
+    assert {k: again[k] for k in keys} == {k: tune[k] for k in keys}
+    with pytest.raises(L.DecbpmError):
+        plan.autotune(dz, trial_steps=0)
+    with pytest.raises(L.DecbpmError):
+        plan.autotune(-1.0)
+
+
 # ------------------------------------------------------------------ edge cases
 def test_single_triangle_and_tiny_meshes():
     coords = np.array([[0.0, 0.0], [1.0, 0.0], [0.2, 0.9]])
