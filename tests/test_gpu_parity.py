@@ -16,6 +16,7 @@ import pytest
 torch = pytest.importorskip("torch")
 
 from oracle import bpm, dec  # noqa: E402
+from paper_2608_03587_b300 import _lib as L  # noqa: E402
 from paper_2608_03587_b300 import api  # noqa: E402
 from paper_2608_03587_b300 import workloads as W  # noqa: E402
 
