@@ -268,6 +268,7 @@ def run_ours(args, rank, world, local_rank):
         line["rk45"] = rk45_comparison(wl, meshes, api, torch, dev, args.steps)
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args, wl)
+        line["cpu_baseline_all_cores"] = cpu_baseline_all_cores(wl, args.cpu_meshes, 16)
     return line
 
 
@@ -340,6 +341,46 @@ def cpu_baseline(args, wl):
     return {"value": units / secs, "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": "first field of the %d smallest fibers, 1 step each (%d vertex-steps, %.1f s); "
                       "numpy/scipy single thread" % (args.cpu_meshes, units, secs)}
+
+
+def _oracle_task(task):
+    """One (mesh, field) oracle march in a worker process; returns
+    (vertex-steps, seconds of the march alone, worker pid)."""
+    coords, cells, V, chi, sigma, p, psi, dz, n_steps = task
+    from oracle import bpm, dec
+    ops = dec.Operators(coords, cells, V, chi)
+    t = time.perf_counter()
+    bpm.propagate(ops, p, psi, dz, n_steps, sigma)
+    return coords.shape[0] * n_steps, time.perf_counter() - t, os.getpid()
+
+
+def cpu_baseline_all_cores(wl, n_meshes, n_fields, cores=None):
+    """The oracle on every host core: independent (mesh, field) marches of the
+    n_meshes smallest fibers (n_fields fields each, one step), one process per
+    core (spawn start: the parent already holds a CUDA context), one thread
+    per process.  Throughput = all vertex-steps / the largest per-process march
+    time (process start-up and assembly excluded, as the GPU's setup is)."""
+    import multiprocessing as mp
+    cores = cores or os.cpu_count() or 1
+    order = np.argsort([m.n_vertices for m in wl.meshes])[:n_meshes]
+    tasks = []
+    for i in order:
+        m = wl.meshes[i]
+        for b in range(min(n_fields, wl.psi0[i].shape[1])):
+            tasks.append((m.coords, m.cells, m.V_cell, m.chi_cell, m.sigma, wl.p, wl.psi0[i][:, b], wl.dz, 1))
+    workers = max(1, min(cores, len(tasks)))
+    for var in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[var] = "1"
+    busy = {}
+    units = 0
+    with mp.get_context("spawn").Pool(workers) as pool:
+        for u, sec, pid in pool.imap_unordered(_oracle_task, tasks, chunksize=1):
+            units += u
+            busy[pid] = busy.get(pid, 0.0) + sec
+    wall = max(busy.values())
+    return {"value": units / wall, "unit": UNIT, "cores": workers, "kind": "oracle",
+            "sample": "%d fields x 1 step on the %d smallest fibers (%d vertex-steps), one process per core, "
+                      "slowest process %.1f s" % (len(tasks), n_meshes, units, wall)}
 
 
 def run_reference(args, rank, world):

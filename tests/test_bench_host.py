@@ -53,3 +53,13 @@ def test_max_over_ranks_gloo_two_ranks():
     assert out[0] == [2.0, 5.0, 3.0]
     assert out[1] == [2.0, 5.0, 3.0]
     assert bench.max_over_ranks([7.0], 1) == [7.0]
+
+
+def test_cpu_baseline_on_all_cores_counts_every_march():
+    """The all-cores oracle baseline runs every (mesh, field) march once, in
+    spawned processes (one thread each), and reports the cores it used."""
+    from paper_2608_03587_b300 import workloads as W
+    wl = W.batched_fibers(n_meshes=2, fields_per_mesh=2, n_min=800, ratio=1.5, seed=4)
+    r = bench.cpu_baseline_all_cores(wl, 2, 2, cores=2)
+    assert r["cores"] == 2 and r["kind"] == "oracle" and r["value"] > 0
+    assert "%d vertex-steps" % sum(m.n_vertices * 2 for m in wl.meshes) in r["sample"]
