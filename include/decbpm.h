@@ -332,6 +332,24 @@ int decbpm_soliton(decbpm_mesh_t mesh, const decbpm_soliton_opts *opts, void *ps
  * be NULL to query n; at most n_max values are written. */
 int decbpm_bessel_i_scaled(double a, double tol, int32_t n_max, double *out, int32_t *n_out);
 
+/* ---- perfectly matched layer ---------------------------------------------------
+ * Absorbing layer by complex stretching of the discrete Hodge stars, the
+ * extension the paper proposes in its Conclusion (exterior complex scaling):
+ * about (x0, y0), beyond r_inner the radius continues into the complex plane,
+ * r~ = r + i int sigma dr, sigma = sigma_max ((r - r_inner)/(r_outer - r_inner))^order
+ * (order 0: constant sigma_max beyond r_inner).  Per triangle the Whitney
+ * inner product of *1 (Eq. 9) takes the tensor (r~/(s r)) e_r e_r^T +
+ * (s r/r~) e_t e_t^T, s = 1 + i sigma, and *0 the factor s r~ / r; v and chib
+ * keep their lumped definitions with the stretched *0.  FP64, assembled on the
+ * host.  Once set, the mesh runs with decbpm_rk45 (lumped Kerr) only: every
+ * split-step entry point returns DECBPM_ERR_UNSUPPORTED, because the
+ * stretched operator's spectrum leaves the real axis by up to ~2 sigma rho
+ * and the Chebyshev series of exp(-i h A) evaluated by Clenshaw then
+ * amplifies rounding by about e^{2 h sigma rho}.  pml = NULL or sigma_max = 0
+ * removes the layer.  2D meshes only. */
+typedef struct { double x0, y0, r_inner, r_outer, sigma_max; int32_t order; } decbpm_pml;
+int decbpm_mesh_set_pml(decbpm_mesh_t mesh, const decbpm_pml *pml);
+
 /* One-shot convenience: plan_create + plan_propagate + plan_destroy. */
 int decbpm_propagate_batch(const decbpm_mesh_t *meshes, int32_t n_meshes, const int32_t *fields_per_mesh,
                            const decbpm_params *params, void *const *psi_dev, void *stream,

@@ -8,7 +8,7 @@ imported without the library.
 """
 _API = ("Mesh", "Plan", "mesh_create", "plan_create", "propagate", "propagate_host", "diagnostics",
         "assemble_host", "bessel_coefficients", "vjp", "march", "set_potential", "propagate_noalloc", "rk45",
-        "soliton", "bessel_i_scaled")
+        "soliton", "bessel_i_scaled", "set_pml")
 
 
 def __getattr__(name):

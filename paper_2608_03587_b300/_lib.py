@@ -84,6 +84,11 @@ class TuneResult(ctypes.Structure):
         return d
 
 
+class Pml(ctypes.Structure):
+    _fields_ = [("x0", ctypes.c_double), ("y0", ctypes.c_double), ("r_inner", ctypes.c_double),
+                ("r_outer", ctypes.c_double), ("sigma_max", ctypes.c_double), ("order", ctypes.c_int32)]
+
+
 class Rk45Opts(ctypes.Structure):
     _fields_ = [("rtol", ctypes.c_double), ("atol", ctypes.c_double), ("h0", ctypes.c_double),
                 ("max_steps", ctypes.c_int64)]
@@ -147,6 +152,7 @@ SIGNATURES = {
     "decbpm_vjp": (_i32, [_vp, ctypes.POINTER(Params), _vp, _vp, _vp, _vp, _vp, _i64, _i32, _vp]),
     "decbpm_soliton": (_i32, [_vp, ctypes.POINTER(SolitonOpts), _vp, _vp, ctypes.POINTER(SolitonStats)]),
     "decbpm_bessel_i_scaled": (_i32, [_dbl, _dbl, _i32, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_i32)]),
+    "decbpm_mesh_set_pml": (_i32, [_vp, ctypes.POINTER(Pml)]),
     "decbpm_rk45": (_i32, [_vp, _dbl, _i32, ctypes.POINTER(Rk45Opts), _vp, _vp, ctypes.POINTER(Rk45Stats)]),
     "decbpm_propagate_noalloc": (_i32, [_vp, ctypes.POINTER(Params), _vp, _i64, _vp]),
     "decbpm_propagate_batch": (_i32, [ctypes.POINTER(_vp), _i32, _c_int32_p, ctypes.POINTER(Params),

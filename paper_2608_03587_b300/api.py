@@ -403,3 +403,17 @@ def bessel_i_scaled(a, tol=1e-17):
     L.check(lib.decbpm_bessel_i_scaled(float(a), float(tol), n.value, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
                                        ctypes.byref(n)))
     return out
+
+
+# ---------------------------------------------------------------- perfectly matched layer
+def set_pml(mesh: Mesh, r_inner=None, r_outer=None, sigma_max=0.0, order=2, center=(0.0, 0.0)):
+    """decbpm_mesh_set_pml: radial complex-stretching layer beyond r_inner
+    (sigma_max = 0 or r_inner = None removes it).  A mesh with a layer runs
+    with rk45 only."""
+    lib = _lib()
+    if r_inner is None or sigma_max == 0.0:
+        L.check(lib.decbpm_mesh_set_pml(mesh.handle, None))
+        return
+    o = L.Pml(x0=float(center[0]), y0=float(center[1]), r_inner=float(r_inner), r_outer=float(r_outer),
+              sigma_max=float(sigma_max), order=int(order))
+    L.check(lib.decbpm_mesh_set_pml(mesh.handle, ctypes.byref(o)))

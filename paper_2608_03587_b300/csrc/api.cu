@@ -2,6 +2,7 @@
 // See include/decbpm.h for the contract of every entry point.
 #include <algorithm>
 #include <cmath>
+#include <complex>
 #include <cstdio>
 #include <cstring>
 #include <map>
@@ -10,6 +11,7 @@
 #include <numeric>
 #include <string>
 #include <tuple>
+#include <unordered_map>
 #include <vector>
 
 #include <cuda_runtime.h>
@@ -85,6 +87,12 @@ struct decbpm_mesh_s {
     int32_t *csr_ptr = nullptr, *csr_col = nullptr;
     double *csr_val = nullptr;
     std::map<std::pair<int, int>, decbpm_plan_t> plans;   // (fields, precision) -> cached single-mesh plan
+    // geometry and materials in caller order, kept for operators assembled later (PML)
+    std::vector<double> g_coords, g_V, g_chi;
+    std::vector<int32_t> g_cells;
+    // PML (complex-stretched metric): SELL weights a_pq = -K~_pq / m~_p and lumped v, chib
+    bool pml_on = false;
+    double2 *pml_a = nullptr, *pml_v = nullptr, *pml_chib = nullptr;
     // tile maps of the tile-staged march (built on first use)
     bool tiles_ready = false, tiles_ok = false;
     uint16_t *lcol = nullptr;
@@ -297,6 +305,9 @@ struct decbpm_plan_s {
         mem.release();
     }
 };
+
+static int reject_pml(decbpm_mesh_t m);        // meshes with a PML run the RK45 integrator only
+static int reject_pml_plan(decbpm_plan_t P);
 
 // Pinned host buffer for diagnostics of n_points points; graphs hold its
 // address, so they are dropped when it moves.
@@ -792,6 +803,7 @@ static int plan_propagate_dispatch(decbpm_plan_t P, const decbpm_params *prm, vo
                                    decbpm_diag *diag_out) {
     TRY(check_params(prm));
     if (!P) return fail(DECBPM_ERR_INVALID_ARG, "plan is NULL");
+    TRY(reject_pml_plan(P));
     if (!psi_dev) return fail(DECBPM_ERR_INVALID_ARG, "psi_dev is NULL");
     for (size_t i = 0; i < P->meshes.size(); ++i)
         if (!psi_dev[i]) return fail(DECBPM_ERR_INVALID_ARG, "psi_dev[%zu] is NULL", i);
@@ -1080,7 +1092,15 @@ static int rk45_impl(decbpm_mesh_t mesh, decbpm_plan_t P, double z_end, int kerr
     permute_in_kernel<double2><<<std::min(G, 4 * P->num_sms), T, 0, s>>>((const double2 *)psi_dev, y, mesh->perm, n0, 1, 1);
     int64_t n_rhs = 0;
     auto rhs = [&](const double2 *in, double2 *out) -> int {
-        if (pp.size() == 1) {
+        if (mesh->pml_on) {
+            const PmlOps po{mv.slice_ptr, mv.slice_w, mv.col, mesh->pml_a, mesh->pml_v, mesh->pml_chib, mv.sigma, n0};
+            if (pp.size() == 1) {
+                rk_rhs_pml_kernel<<<G, T, 0, s>>>(po, in, out, nullptr, 0, p1, p2);
+            } else {
+                rk_rhs_pml_kernel<<<G, T, 0, s>>>(po, in, out, tA, 1, p1, p2);
+                rk_rhs_pml_kernel<<<G, T, 0, s>>>(po, in, out, tA, 2, p1, p2);
+            }
+        } else if (pp.size() == 1) {
             rk_rhs_kernel<<<G, T, 0, s>>>(mv, in, out, nullptr, 0, r, p1, p2, kerr_mode);
         } else {
             rk_rhs_kernel<<<G, T, 0, s>>>(mv, in, out, tA, 1, r, p1, p2, kerr_mode);
@@ -1415,6 +1435,118 @@ static int autotune_impl(decbpm_plan_t P, double dz, int kerr_mode, int trial_st
     return DECBPM_OK;
 }
 
+
+// ============================================================== PML
+// Radial exterior complex scaling of the Hodge stars about (x0, y0): beyond
+// r_inner the radius continues into the complex plane, r~ = r + i int sigma,
+// s = 1 + i sigma(r), sigma = sigma_max ((r - r_inner)/(r_outer - r_inner))^order.
+// Per triangle (at its centroid) the Whitney inner product of *1 gets the
+// tensor Lambda = (r~/(s r)) e_r e_r^T + (s r/r~) e_t e_t^T and *0 the factor
+// J = s r~ / r; K~ = d0^T *1~ d0 is the P1 stiffness with Lambda (complex
+// symmetric, zero row sums); v and chib keep their lumped definitions with
+// the stretched *0.  The RK45 integrator uses A~ = *0~^{-1} K~ in difference
+// form: (A~ g)_p = sum_q a_pq (g_p - g_q), a_pq = -K~_pq / m~_p.
+static int reject_pml(decbpm_mesh_t m) {
+    if (m && m->pml_on)
+        return fail(DECBPM_ERR_UNSUPPORTED,
+                    "this mesh has a PML: it runs with decbpm_rk45 only (the split-step's Chebyshev series of "
+                    "exp(-i h A) is not stable on the complex spectrum of the stretched operator)");
+    return DECBPM_OK;
+}
+static int reject_pml_plan(decbpm_plan_t P) {
+    if (P)
+        for (decbpm_mesh_t m : P->meshes) TRY(reject_pml(m));
+    return DECBPM_OK;
+}
+
+static int set_pml_impl(decbpm_mesh_t M, const decbpm_pml *o) {
+    using cd = std::complex<double>;
+    const Assembly &A = M->A;
+    const Sell &S = M->S;
+    if (A.dim != 2) return fail(DECBPM_ERR_UNSUPPORTED, "the PML is radial: 2D meshes only");
+    if (!(o->r_outer > o->r_inner) || !(o->r_inner >= 0) || !(o->sigma_max >= 0) || o->order < 0 || o->order > 8 ||
+        !std::isfinite(o->x0 + o->y0 + o->r_inner + o->r_outer + o->sigma_max))
+        return fail(DECBPM_ERR_INVALID_ARG, "PML needs 0 <= r_inner < r_outer, sigma_max >= 0, order in 0..8");
+    const int64_t n0 = A.n0, nc = int64_t(M->g_cells.size()) / 3;
+    const double *X = M->g_coords.data();
+    const int32_t *C = M->g_cells.data();
+    std::vector<cd> mt(n0, 0.0), nv(n0, 0.0), nchi(n0, 0.0);
+    std::unordered_map<uint64_t, cd> K;
+    K.reserve(size_t(nc) * 3);
+    auto key = [&](int32_t a, int32_t b) { return uint64_t(std::min(a, b)) * uint64_t(n0) + uint64_t(std::max(a, b)); };
+    for (int64_t t = 0; t < nc; ++t) {
+        const int32_t v[3] = {C[3 * t], C[3 * t + 1], C[3 * t + 2]};
+        const double px[3] = {X[2 * v[0]], X[2 * v[1]], X[2 * v[2]]}, py[3] = {X[2 * v[0] + 1], X[2 * v[1] + 1], X[2 * v[2] + 1]};
+        const double a2 = (px[1] - px[0]) * (py[2] - py[0]) - (py[1] - py[0]) * (px[2] - px[0]);
+        const double area = 0.5 * std::fabs(a2);
+        double g[3][2];
+        for (int i = 0; i < 3; ++i) {             // grad lambda_i = perp(opposite edge) / (2 |t|), signed
+            const int j = (i + 1) % 3, k = (i + 2) % 3;
+            g[i][0] = (py[j] - py[k]) / a2;
+            g[i][1] = (px[k] - px[j]) / a2;
+        }
+        const double cx = (px[0] + px[1] + px[2]) / 3.0 - o->x0, cy = (py[0] + py[1] + py[2]) / 3.0 - o->y0;
+        const double r = std::hypot(cx, cy);
+        const double u = std::max(0.0, (r - o->r_inner) / (o->r_outer - o->r_inner));
+        const double sig = o->order > 0 ? o->sigma_max * std::pow(u, o->order) : (r > o->r_inner ? o->sigma_max : 0.0);
+        const cd sc(1.0, sig);
+        const cd rt(r, o->sigma_max * (o->r_outer - o->r_inner) * std::pow(u, o->order + 1) / (o->order + 1));
+        cd L[2][2], J;
+        if (r > 0) {
+            const double er[2] = {cx / r, cy / r}, et[2] = {-cy / r, cx / r};
+            const cd ar = rt / (sc * r), at = sc * r / rt;
+            for (int a = 0; a < 2; ++a)
+                for (int b = 0; b < 2; ++b) L[a][b] = ar * er[a] * er[b] + at * et[a] * et[b];
+            J = sc * rt / r;
+        } else {
+            L[0][0] = L[1][1] = 1.0;
+            L[0][1] = L[1][0] = 0.0;
+            J = 1.0;
+        }
+        for (int i = 0; i < 3; ++i) {
+            mt[v[i]] += J * area / 3.0;
+            nv[v[i]] += J * area / 3.0 * M->g_V[t];
+            nchi[v[i]] += J * area / 3.0 * M->g_chi[t];
+            for (int j = i + 1; j < 3; ++j) {
+                cd kij = 0.0;
+                for (int a = 0; a < 2; ++a)
+                    for (int b = 0; b < 2; ++b) kij += g[i][a] * L[a][b] * g[j][b];
+                K[key(v[i], v[j])] += area * kij;
+            }
+        }
+    }
+    std::vector<double2> a_sell(S.col.size()), vv(n0), cc(n0);
+    for (int64_t sl = 0; sl < S.n_slices; ++sl)
+        for (int j = 0; j < S.slice_w[sl]; ++j)
+            for (int lane = 0; lane < kSlice; ++lane) {
+                const int64_t idx = S.slice_ptr[sl] + int64_t(j) * kSlice + lane, row = sl * kSlice + lane;
+                cd a = 0.0;
+                if (row < n0 && j < S.degree[row]) {
+                    const int32_t o1 = A.perm[row], o2 = A.perm[S.col[idx]];
+                    auto it = K.find(key(o1, o2));
+                    if (it == K.end()) return fail(DECBPM_ERR_BAD_MESH, "PML assembly: edge %d-%d not found", o1, o2);
+                    a = -it->second / mt[o1];
+                }
+                a_sell[idx] = make_double2(a.real(), a.imag());
+            }
+    for (int64_t i = 0; i < n0; ++i) {
+        const int32_t oi = A.perm[i];
+        const cd v = nv[oi] / mt[oi], c = nchi[oi] / mt[oi];
+        vv[i] = make_double2(v.real(), v.imag());
+        cc[i] = make_double2(c.real(), c.imag());
+    }
+    if (!M->pml_a) {
+        TRY(M->mem.alloc(&M->pml_a, a_sell.size()));
+        TRY(M->mem.alloc(&M->pml_v, size_t(n0)));
+        TRY(M->mem.alloc(&M->pml_chib, size_t(n0)));
+    }
+    CK(cudaMemcpy(M->pml_a, a_sell.data(), sizeof(double2) * a_sell.size(), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(M->pml_v, vv.data(), sizeof(double2) * n0, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(M->pml_chib, cc.data(), sizeof(double2) * n0, cudaMemcpyHostToDevice));
+    M->pml_on = true;
+    return DECBPM_OK;
+}
+
 // ============================================================== C ABI
 extern "C" {
 
@@ -1491,6 +1623,15 @@ int decbpm_mesh_create(const decbpm_mesh_desc *desc, decbpm_mesh_t *out) {
     *out = nullptr;
     auto M = std::make_unique<decbpm_mesh_s>();
     TRY(assemble(desc, M->A));
+    {
+        const int64_t nv = desc->n_vertices, nc = desc->n_cells;
+        M->g_coords.assign(desc->coords, desc->coords + nv * desc->dim);
+        M->g_cells.assign(desc->cells, desc->cells + nc * (desc->dim + 1));
+        M->g_V.assign(nc, 0.0);
+        M->g_chi.assign(nc, 1.0);
+        if (desc->V_cell) M->g_V.assign(desc->V_cell, desc->V_cell + nc);
+        if (desc->chi_cell) M->g_chi.assign(desc->chi_cell, desc->chi_cell + nc);
+    }
     build_sell(M->A, M->S);
     CK(cudaGetDevice(&M->device));
     int rc = mesh_upload(M.get());
@@ -1544,6 +1685,7 @@ int decbpm_propagate(decbpm_mesh_t mesh, const decbpm_params *params, void *psi_
     clear_error();
     if (!mesh || !psi_dev) return fail(DECBPM_ERR_INVALID_ARG, "mesh and psi_dev are required");
     TRY(check_params(params));
+    TRY(reject_pml(mesh));
     if (params->variant == DECBPM_VARIANT_PLAIN) {
         if (n_fields != 1) return fail(DECBPM_ERR_UNSUPPORTED, "the plain variant runs one field");
         if (params->kerr_mode != DECBPM_KERR_LUMPED) return fail(DECBPM_ERR_UNSUPPORTED, "the plain variant runs lumped Kerr");
@@ -1559,6 +1701,7 @@ int decbpm_propagate_host(decbpm_mesh_t mesh, const decbpm_params *params, void 
                           decbpm_diag *diag_out) {
     clear_error();
     if (!mesh || !psi_host) return fail(DECBPM_ERR_INVALID_ARG, "mesh and psi_host are required");
+    TRY(reject_pml(mesh));
     TRY(check_params(params));
     decbpm_plan_t P;
     TRY(single_plan(mesh, n_fields, params->precision, &P));
@@ -1628,6 +1771,7 @@ int decbpm_plan_propagate_host(decbpm_plan_t P, const decbpm_params *params, voi
     clear_error();
     TRY(check_params(params));
     if (!P || !psi_host) return fail(DECBPM_ERR_INVALID_ARG, "NULL argument");
+    TRY(reject_pml_plan(P));
     cudaStream_t s = (cudaStream_t)stream;
     const size_t cs = csize(P->precision);
     for (size_t i = 0; i < P->meshes.size(); ++i) {
@@ -1678,6 +1822,7 @@ int decbpm_vjp(decbpm_mesh_t mesh, const decbpm_params *params, const void *psi0
                void *stream) {
     clear_error();
     if (!mesh || !psi0_dev || !gN_dev || !grad_psi0_dev) return fail(DECBPM_ERR_INVALID_ARG, "NULL argument");
+    TRY(reject_pml(mesh));
     TRY(check_params(params));
     if (params->kerr_mode != DECBPM_KERR_LUMPED) return fail(DECBPM_ERR_UNSUPPORTED, "the adjoint supports lumped Kerr");
     if (params->variant != DECBPM_VARIANT_FUSED) return fail(DECBPM_ERR_UNSUPPORTED, "the adjoint runs the fused variant");
@@ -1699,6 +1844,8 @@ int decbpm_rk45(decbpm_mesh_t mesh, double z_end, int32_t kerr_mode, const decbp
     if (!(z_end >= 0) || !std::isfinite(z_end)) return fail(DECBPM_ERR_INVALID_ARG, "z_end must be finite and >= 0");
     if (!(opts->rtol > 0) || !(opts->atol > 0)) return fail(DECBPM_ERR_INVALID_ARG, "rtol and atol must be > 0");
     if (kerr_mode != DECBPM_KERR_LUMPED && kerr_mode != DECBPM_KERR_ELEMENT) return fail(DECBPM_ERR_INVALID_ARG, "bad kerr_mode");
+    if (mesh->pml_on && kerr_mode != DECBPM_KERR_LUMPED)
+        return fail(DECBPM_ERR_UNSUPPORTED, "with a PML the RK45 path takes lumped Kerr");
     decbpm_plan_t P;
     TRY(single_plan(mesh, 1, DECBPM_C128, &P));
     if (P->order.empty()) TRY(plan_configure<double>(P, 1e-3, 1e-16));   // only for the device view of the mesh
@@ -1709,6 +1856,7 @@ int decbpm_soliton(decbpm_mesh_t mesh, const decbpm_soliton_opts *opts, void *ps
                    decbpm_soliton_stats *stats) {
     clear_error();
     if (!mesh || !opts || !psi_dev) return fail(DECBPM_ERR_INVALID_ARG, "NULL argument");
+    TRY(reject_pml(mesh));
     if (!(opts->power > 0) || !std::isfinite(opts->power)) return fail(DECBPM_ERR_INVALID_ARG, "power must be > 0");
     if (!(opts->tau > 0) || !std::isfinite(opts->tau)) return fail(DECBPM_ERR_INVALID_ARG, "tau must be > 0");
     if (!(opts->tol > 0)) return fail(DECBPM_ERR_INVALID_ARG, "tol must be > 0");
@@ -1736,11 +1884,22 @@ int decbpm_plan_autotune(decbpm_plan_t P, double dz, int32_t kerr_mode, int32_t 
                          decbpm_tune_result *out) {
     clear_error();
     if (!P) return fail(DECBPM_ERR_INVALID_ARG, "plan is NULL");
+    TRY(reject_pml_plan(P));
     if (!(dz > 0) || !std::isfinite(dz)) return fail(DECBPM_ERR_INVALID_ARG, "dz must be finite and > 0");
     if (trial_steps < 1 || trial_steps > 1000) return fail(DECBPM_ERR_INVALID_ARG, "trial_steps must be in 1..1000");
     if (kerr_mode != DECBPM_KERR_LUMPED && kerr_mode != DECBPM_KERR_ELEMENT) return fail(DECBPM_ERR_INVALID_ARG, "bad kerr_mode");
     if (P->precision == DECBPM_C64) return autotune_impl<float>(P, dz, kerr_mode, trial_steps, (cudaStream_t)stream, out);
     return autotune_impl<double>(P, dz, kerr_mode, trial_steps, (cudaStream_t)stream, out);
+}
+
+int decbpm_mesh_set_pml(decbpm_mesh_t mesh, const decbpm_pml *pml) {
+    clear_error();
+    if (!mesh) return fail(DECBPM_ERR_INVALID_ARG, "mesh is NULL");
+    if (!pml || pml->sigma_max == 0.0) {
+        mesh->pml_on = false;
+        return DECBPM_OK;
+    }
+    return set_pml_impl(mesh, pml);
 }
 
 int decbpm_plan_get_config(decbpm_plan_t P, decbpm_plan_config *cfg) {
@@ -1813,6 +1972,7 @@ int decbpm_propagate_batch(const decbpm_mesh_t *meshes, int32_t n_meshes, const 
     TRY(check_params(params));
     decbpm_plan_t P = nullptr;
     TRY(plan_create_impl(meshes, n_meshes, fields_per_mesh, params->precision, &P));
+    if (P->meshes.size() && reject_pml_plan(P) != DECBPM_OK) { delete P; return DECBPM_ERR_UNSUPPORTED; }
     int rc = plan_propagate_dispatch(P, params, psi_dev, stream, diag_out);
     delete P;
     return rc;
@@ -2005,6 +2165,7 @@ extern "C" int decbpm_propagate_noalloc(decbpm_mesh_t mesh, const decbpm_params 
     TRY(check_params(params));
     if (params->variant != DECBPM_VARIANT_FUSED)
         return fail(DECBPM_ERR_UNSUPPORTED, "decbpm_propagate_noalloc runs the fused variant only");
+    TRY(reject_pml(mesh));
     if (n_fields < 1 || n_fields > kMaxFields) return fail(DECBPM_ERR_UNSUPPORTED, "n_fields must be in 1..%d", kMaxFields);
     cudaStream_t s = (cudaStream_t)stream;
     if (params->precision == DECBPM_C64) return propagate_noalloc_impl<float>(mesh, params, psi_dev, n_fields, s);

@@ -1348,6 +1348,52 @@ __global__ void rk_rhs_kernel(MeshView<double> m, const double2 *__restrict__ y,
     k[p] = make_double2(gi - sg * yp.x, -gr - sg * yp.y);  // -i (g) - sigma y
 }
 
+// The same right-hand side on a mesh with a PML (complex-stretched Hodge
+// stars): (A~ g)_p = sum_q a_pq (g_p - g_q) with complex a_pq = -K~_pq / m~_p,
+// complex lumped v and chib; lumped Kerr.
+struct PmlOps {
+    const int32_t *slice_ptr, *slice_w, *col;
+    const double2 *a, *v, *chib;
+    const double *sigma;
+    int32_t n0;
+};
+__device__ __forceinline__ double2 pml_a_row(const PmlOps &o, const double2 *__restrict__ y, int p) {
+    const int s = p >> 5, base = o.slice_ptr[s] + (p & 31), w = o.slice_w[s];
+    const double2 yp = y[p];
+    double ar = 0, ai = 0;
+    for (int j = 0; j < w; ++j) {
+        const double2 a = o.a[base + 32 * j];
+        const double2 yq = y[o.col[base + 32 * j]];
+        const double dr = yp.x - yq.x, di = yp.y - yq.y;
+        ar += a.x * dr - a.y * di;
+        ai += a.x * di + a.y * dr;
+    }
+    return make_double2(ar, ai);
+}
+__global__ void rk_rhs_pml_kernel(PmlOps o, const double2 *__restrict__ y, double2 *__restrict__ k,
+                                  double2 *__restrict__ t, int32_t pass, double p1, double p2) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= o.n0) return;
+    if (pass == 1) {
+        t[p] = pml_a_row(o, y, p);
+        return;
+    }
+    const double2 yp = y[p];
+    double2 lin;
+    if (pass == 0) {
+        const double2 ay = pml_a_row(o, y, p);
+        lin = make_double2(p1 * ay.x, p1 * ay.y);
+    } else {
+        const double2 ay = t[p], aay = pml_a_row(o, t, p);
+        lin = make_double2(p1 * ay.x - p2 * aay.x, p1 * ay.y - p2 * aay.y);
+    }
+    const double I = yp.x * yp.x + yp.y * yp.y;
+    const double qr = o.v[p].x + o.chib[p].x * I, qi = o.v[p].y + o.chib[p].y * I;    // v + N (complex)
+    const double gr = lin.x - (qr * yp.x - qi * yp.y), gi = lin.y - (qr * yp.y + qi * yp.x);
+    const double sg = o.sigma[p];
+    k[p] = make_double2(gi - sg * yp.x, -gr - sg * yp.y);  // -i (g) - sigma y
+}
+
 struct RkCombine {
     const double2 *k[7];
     double a[7];
