@@ -54,7 +54,7 @@ extern "C" {
 #define DECBPM_ERR_TIMEOUT       -4   /* a device-side grid barrier gave up waiting (bounded spin) */
 #define DECBPM_ERR_CUDA          -5   /* a CUDA runtime call failed */
 #define DECBPM_ERR_OOM           -6   /* device or host allocation failed */
-#define DECBPM_ERR_UNSUPPORTED   -7   /* valid request that this build does not implement */
+#define DECBPM_ERR_UNSUPPORTED   -7   /* valid request that this library does not implement */
 #define DECBPM_ERR_DEVICE_CHECK  -8   /* a device-side consistency check failed; the kernel skipped the work */
 
 /* ---- enumerations -------------------------------------------------------- */
