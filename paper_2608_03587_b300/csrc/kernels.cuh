@@ -84,16 +84,6 @@ __device__ __forceinline__ float2 cscale(float2 a, float s) {
 __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
     return make_float2(__fmaf_rn(-a.y, b.y, __fmul_rn(a.x, b.x)), __fmaf_rn(a.y, b.x, __fmul_rn(a.x, b.y)));
 }
-// c + a b for complex a, b, c with the product folded into the sum by two
-// fused multiply-adds per component (no separately rounded a b): on a
-// stationary field the rounding of an intermediate a b repeats step after
-// step and acts as a small systematic gain; folding it removes most of that
-__device__ __forceinline__ float2 cmla(float2 a, float2 b, float2 c) {
-    return make_float2(__fmaf_rn(a.x, b.x, __fmaf_rn(-a.y, b.y, c.x)), __fmaf_rn(a.x, b.y, __fmaf_rn(a.y, b.x, c.y)));
-}
-__device__ __forceinline__ double2 cmla(double2 a, double2 b, double2 c) {
-    return make_double2(fma(a.x, b.x, fma(-a.y, b.y, c.x)), fma(a.x, b.y, fma(a.y, b.x, c.y)));
-}
 __device__ __forceinline__ void sincos_r(float x, float *s, float *c) { sincosf(x, s, c); }
 __device__ __forceinline__ void sincos_r(double x, double *s, double *c) { sincos(x, s, c); }
 __device__ __forceinline__ float exp_r(float x) { return expf(x); }
@@ -422,13 +412,15 @@ __device__ __forceinline__ void clenshaw_stage(const MeshView<R> *sv, const Stag
             Pack<R, FPT> out;
 #pragma unroll
             for (int f = 0; f < FPT; ++f) {
-                // out = alpha psi (+ alpha_lo psi) + beta (X g) - h, the psi
-                // products folded into the sum (cmla); the lambda = 0 residual
-                // enters before alpha psi, where it is not rounded away
-                C v = cmul(sc.beta, csub(acc.v[f], gp.v[f]));
-                if (sc.flags & kHasH) v = csub(v, hh.v[f]);
-                if (sc.flags & kFinal) v = cmla(sc.alpha_lo, ps.v[f], v);
-                out.v[f] = cmla(sc.alpha, ps.v[f], v);
+                // the lambda = 0 residual joins alpha*psi, where it is about one
+                // ulp; added to the full sum it would round away
+                C t = cmul(sc.alpha, ps.v[f]);
+                if (sc.flags & kFinal) t = cadd(t, cmul(sc.alpha_lo, ps.v[f]));
+                out.v[f] = cadd(t, cmul(sc.beta, csub(acc.v[f], gp.v[f])));
+            }
+            if (sc.flags & kHasH) {
+#pragma unroll
+                for (int f = 0; f < FPT; ++f) out.v[f] = csub(out.v[f], hh.v[f]);
             }
             if (sc.flags & kFinal) {
                 if (kerr_mode == 0) {
@@ -852,8 +844,6 @@ __device__ __forceinline__ cf2 f2_fma(cf2 a, cf2 b, cf2 c) {
 }
 // complex product z w with z given as (zr, zr) and (-zi, zi): zr w + (-zi, zi) swap(w)
 __device__ __forceinline__ cf2 f2_cmul(cf2 zrr, cf2 zni, cf2 w) { return f2_fma(zni, f2_swap(w), f2_mul(zrr, w)); }
-// c + z w with z given as (zr, zr) and (-zi, zi): inner (-zi wi + c.re, zi wr + c.im), then zr w + inner
-__device__ __forceinline__ cf2 f2_cmla(cf2 zrr, cf2 zni, cf2 w, cf2 c) { return f2_fma(zrr, w, f2_fma(zni, f2_swap(w), c)); }
 __device__ __forceinline__ void lds_c2(uint32_t addr, cf2 &a, cf2 &b) {
     asm volatile("ld.shared.v2.b64 {%0, %1}, [%2];" : "=l"(a), "=l"(b) : "r"(addr));
 }
@@ -938,13 +928,11 @@ __device__ __forceinline__ void tile_compute(const MeshView<float> *sv, const St
     cf2 out[4];
 #pragma unroll
     for (int f = 0; f < 4; ++f) {
-        // the row kernel's order: v = beta (X g) - h, then the psi products
-        // folded in by fused multiply-adds (same roundings as cmla)
-        cf2 v = f2_cmul(brr, bni, f2_sub(acc[f], gp[f]));
-        if (sc.flags & kHasH) v = f2_sub(v, hh[f]);
+        cf2 tt = f2_cmul(arr, ani, ps[f]);
         if (sc.flags & kFinal)
-            v = f2_cmla(f2_pack(sc.alpha_lo.x, sc.alpha_lo.x), f2_pack(-sc.alpha_lo.y, sc.alpha_lo.y), ps[f], v);
-        out[f] = f2_cmla(arr, ani, ps[f], v);
+            tt = f2_add(tt, f2_cmul(f2_pack(sc.alpha_lo.x, sc.alpha_lo.x), f2_pack(-sc.alpha_lo.y, sc.alpha_lo.y), ps[f]));
+        out[f] = f2_add(tt, f2_cmul(brr, bni, f2_sub(acc[f], gp[f])));
+        if (sc.flags & kHasH) out[f] = f2_sub(out[f], hh[f]);
     }
     float2 *dst;
     if (sc.flags & kFinal) {
