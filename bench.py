@@ -40,8 +40,8 @@ UNIT = "vertex-steps/s"
 # workload, from the one-pass ncu capture of this bench's own launches
 # (profiles/launches_bench_batched_fibers.md), valid for the kernel source
 # whose hash is recorded with it; traffic is reported as null otherwise.
-TRAFFIC_RATIO = 0.9390
-TRAFFIC_SRC_HASH = "c8eb4e96274dd311"
+TRAFFIC_RATIO = 0.9392
+TRAFFIC_SRC_HASH = "b9b27c6b528c0473"
 
 
 def kernel_source_hash() -> str:

@@ -84,6 +84,41 @@ __device__ __forceinline__ float2 cscale(float2 a, float s) {
 __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
     return make_float2(__fmaf_rn(-a.y, b.y, __fmul_rn(a.x, b.x)), __fmaf_rn(a.y, b.x, __fmul_rn(a.x, b.y)));
 }
+// The last Clenshaw stage of a complex64 step, S = alpha psi + alpha_lo psi +
+// beta (acc - g) - h, in double-float FP32 arithmetic (error-free products by
+// FMA, error-free sums; Knuth's TwoSum) and rounded once.  Rounded term by
+// term, this combination repeats its roundings step after step on a
+// stationary field and acts as a gain of ~2e-8 per step; the stage runs
+// once per step.  Explicit intrinsics: every kernel that calls it produces
+// the same bits.
+struct DF { float hi, lo; };
+__device__ __forceinline__ void df_add(DF &acc, float th, float tl) {
+    const float s = __fadd_rn(acc.hi, th), bb = __fsub_rn(s, acc.hi);
+    const float e = __fadd_rn(__fsub_rn(acc.hi, __fsub_rn(s, bb)), __fsub_rn(th, bb));
+    acc.hi = s;
+    acc.lo = __fadd_rn(acc.lo, __fadd_rn(e, tl));
+}
+__device__ __forceinline__ void df_prod(DF &acc, float a, float b) {
+    const float p = __fmul_rn(a, b);
+    df_add(acc, p, __fmaf_rn(a, b, -p));
+}
+__device__ __forceinline__ float2 final_combine(float2 alpha, float2 alpha_lo, float2 beta, float2 ps, float2 acc,
+                                                float2 gp, float2 hh, bool has_h) {
+    DF dr{0.f, 0.f}, di{0.f, 0.f};
+    df_add(dr, acc.x, 0.f); df_add(dr, -gp.x, 0.f);               // d = acc - g, exactly as hi + lo
+    df_add(di, acc.y, 0.f); df_add(di, -gp.y, 0.f);
+    DF re{0.f, 0.f}, im{0.f, 0.f};
+    df_prod(re, alpha.x, ps.x);    df_prod(re, -alpha.y, ps.y);
+    df_prod(im, alpha.x, ps.y);    df_prod(im, alpha.y, ps.x);
+    df_prod(re, alpha_lo.x, ps.x); df_prod(re, -alpha_lo.y, ps.y);
+    df_prod(im, alpha_lo.x, ps.y); df_prod(im, alpha_lo.y, ps.x);
+    df_prod(re, beta.x, dr.hi);    df_prod(re, -beta.y, di.hi);
+    df_prod(im, beta.x, di.hi);    df_prod(im, beta.y, dr.hi);
+    df_prod(re, beta.x, dr.lo);    df_prod(re, -beta.y, di.lo);
+    df_prod(im, beta.x, di.lo);    df_prod(im, beta.y, dr.lo);
+    if (has_h) { df_add(re, -hh.x, 0.f); df_add(im, -hh.y, 0.f); }
+    return make_float2(__fadd_rn(re.hi, re.lo), __fadd_rn(im.hi, im.lo));
+}
 __device__ __forceinline__ void sincos_r(float x, float *s, float *c) { sincosf(x, s, c); }
 __device__ __forceinline__ void sincos_r(double x, double *s, double *c) { sincos(x, s, c); }
 __device__ __forceinline__ float exp_r(float x) { return expf(x); }
@@ -410,17 +445,30 @@ __device__ __forceinline__ void clenshaw_stage(const MeshView<R> *sv, const Stag
         }
         if (live) {
             Pack<R, FPT> out;
+            bool done = false;
+            if constexpr (sizeof(R) == 4) {
+                if (sc.flags & kFinal) {           // double-float final stage (complex64)
 #pragma unroll
-            for (int f = 0; f < FPT; ++f) {
-                // the lambda = 0 residual joins alpha*psi, where it is about one
-                // ulp; added to the full sum it would round away
-                C t = cmul(sc.alpha, ps.v[f]);
-                if (sc.flags & kFinal) t = cadd(t, cmul(sc.alpha_lo, ps.v[f]));
-                out.v[f] = cadd(t, cmul(sc.beta, csub(acc.v[f], gp.v[f])));
+                    for (int f = 0; f < FPT; ++f)
+                        out.v[f] = final_combine(sc.alpha, sc.alpha_lo, sc.beta, ps.v[f], acc.v[f], gp.v[f],
+                                                 (sc.flags & kHasH) ? hh.v[f] : make_float2(0.f, 0.f),
+                                                 (sc.flags & kHasH) != 0);
+                    done = true;
+                }
             }
-            if (sc.flags & kHasH) {
+            if (!done) {
 #pragma unroll
-                for (int f = 0; f < FPT; ++f) out.v[f] = csub(out.v[f], hh.v[f]);
+                for (int f = 0; f < FPT; ++f) {
+                    // the lambda = 0 residual joins alpha*psi, where it is about one
+                    // ulp; added to the full sum it would round away
+                    C t = cmul(sc.alpha, ps.v[f]);
+                    if (sc.flags & kFinal) t = cadd(t, cmul(sc.alpha_lo, ps.v[f]));
+                    out.v[f] = cadd(t, cmul(sc.beta, csub(acc.v[f], gp.v[f])));
+                }
+                if (sc.flags & kHasH) {
+#pragma unroll
+                    for (int f = 0; f < FPT; ++f) out.v[f] = csub(out.v[f], hh.v[f]);
+                }
             }
             if (sc.flags & kFinal) {
                 if (kerr_mode == 0) {
@@ -926,13 +974,21 @@ __device__ __forceinline__ void tile_compute(const MeshView<float> *sv, const St
     const cf2 arr = f2_pack(sc.alpha.x, sc.alpha.x), ani = f2_pack(-sc.alpha.y, sc.alpha.y);
     const cf2 brr = f2_pack(sc.beta.x, sc.beta.x), bni = f2_pack(-sc.beta.y, sc.beta.y);
     cf2 out[4];
+    if (sc.flags & kFinal) {                       // double-float final stage (same bits as the row kernel)
 #pragma unroll
-    for (int f = 0; f < 4; ++f) {
-        cf2 tt = f2_cmul(arr, ani, ps[f]);
-        if (sc.flags & kFinal)
-            tt = f2_add(tt, f2_cmul(f2_pack(sc.alpha_lo.x, sc.alpha_lo.x), f2_pack(-sc.alpha_lo.y, sc.alpha_lo.y), ps[f]));
-        out[f] = f2_add(tt, f2_cmul(brr, bni, f2_sub(acc[f], gp[f])));
-        if (sc.flags & kHasH) out[f] = f2_sub(out[f], hh[f]);
+        for (int f = 0; f < 4; ++f) {
+            const float2 o = final_combine(sc.alpha, sc.alpha_lo, sc.beta, f2_unpack(ps[f]), f2_unpack(acc[f]),
+                                           f2_unpack(gp[f]), (sc.flags & kHasH) ? f2_unpack(hh[f]) : make_float2(0.f, 0.f),
+                                           (sc.flags & kHasH) != 0);
+            out[f] = f2_pack(o.x, o.y);
+        }
+    } else {
+#pragma unroll
+        for (int f = 0; f < 4; ++f) {
+            cf2 tt = f2_cmul(arr, ani, ps[f]);
+            out[f] = f2_add(tt, f2_cmul(brr, bni, f2_sub(acc[f], gp[f])));
+            if (sc.flags & kHasH) out[f] = f2_sub(out[f], hh[f]);
+        }
     }
     float2 *dst;
     if (sc.flags & kFinal) {
