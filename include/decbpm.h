@@ -17,7 +17,8 @@
  *
  * One z-step of length h is the Strang split D_{h/2} E_h D_{h/2}:
  *   E_h  = exp(i h sum_n p_n (-A)^n), A = *0^{-1} d0^T *1 d0, applied by a
- *          Chebyshev expansion on the Gershgorin interval of A;
+ *          Chebyshev expansion on an interval [0, rho] that contains the
+ *          spectrum of A (rho: see DECBPM_BOUND_*);
  *   D_h  = exact flow of dpsi/dz = i (v + chib |psi|^2) psi - sigma psi per
  *          vertex (potential, Kerr phase and absorber damping).
  *
@@ -73,18 +74,32 @@ extern "C" {
 #define DECBPM_ORDER_RCM      1  /* reverse Cuthill-McKee (small bandwidth, thin level sets) */
 #define DECBPM_ORDER_HILBERT  2  /* Hilbert space-filling curve of the vertex positions (compact blocks) */
 
-/* The Chebyshev interval [0, rho] must contain the spectrum of A.
+/* The Chebyshev interval [0, rho] must contain the spectrum of A (outside it
+ * the truncated series of exp(-i h A) grows like cosh(k acosh x)).
  * GERSHGORIN: rho = min(Gershgorin bound, element bound max_t lambda_max(K_t, M_t)), both
- *   deterministic upper bounds, times 1 + 1e-6.
- * LANCZOS (default): the smaller of that and 1.01 x the largest Ritz value of 200 Lanczos
- *   steps on *0^{-1/2} K *0^{-1/2} from a fixed pseudo-random start.  By the
- *   Kuczynski-Wozniakowski bound the probability (over start vectors) that lambda_max
- *   exceeds it is below 1.648 sqrt(n) exp(-0.0995 * 399) < 1e-12 for n < 2^30.  It is
- *   typically 1.6x tighter than Gershgorin on graded meshes, and the Chebyshev degree
- *   (hence the work per step) shrinks nearly in proportion. */
+ *   deterministic upper bounds, times 1 + 1e-6 (DECBPM_RHO_RIGOROUS).
+ * LANCZOS (default): theta = the largest Ritz value of lanczos_steps (default 200) Lanczos
+ *   steps on *0^{-1/2} K *0^{-1/2} from a fixed pseudo-random start; theta <= lambda_max
+ *   and is typically within a fraction of a percent of it on these meshes, 1.6x tighter
+ *   than Gershgorin on graded meshes (the Chebyshev degree, hence the work per step,
+ *   shrinks nearly in proportion).  The candidate 1.01 theta is then checked for each
+ *   mesh: a degree-128 Chebyshev polynomial of the operator on [0, 1.01 theta / 1.002],
+ *   applied in FP64 to a seeded probe vector (pseudo-random plus spikes at the vertices
+ *   with the largest Gershgorin rows), must not raise the probe's norm; an eigenvalue
+ *   above the candidate would raise it by cosh(128 acosh x).  If it passes, rho =
+ *   1.01 theta (DECBPM_RHO_LANCZOS_CHECKED); otherwise rho falls back to the rigorous
+ *   bound (DECBPM_RHO_LANCZOS_REJECTED).  The check shows the bound for every
+ *   eigenvector whose component in the probe is at least 1e-3 of its norm; it is no
+ *   proof for an eigenvector orthogonal to the probe, and no probability is claimed. */
 #define DECBPM_BOUND_DEFAULT     0
 #define DECBPM_BOUND_LANCZOS     1
 #define DECBPM_BOUND_GERSHGORIN  2
+
+/* which bound rho is (decbpm_mesh_info_t.rho_kind) */
+#define DECBPM_RHO_RIGOROUS          0   /* min(Gershgorin, element bound) (DECBPM_BOUND_GERSHGORIN, or
+                                            Lanczos not tighter) */
+#define DECBPM_RHO_LANCZOS_CHECKED   1   /* 1.01 x the Lanczos Ritz value, passed the per-mesh check */
+#define DECBPM_RHO_LANCZOS_REJECTED  2   /* the Lanczos candidate failed the check: the rigorous bound */
 
 typedef struct decbpm_mesh_s *decbpm_mesh_t;
 typedef struct decbpm_plan_s *decbpm_plan_t;
@@ -109,6 +124,8 @@ typedef struct {
     int32_t        n_p;
     int32_t        ordering;      /* internal vertex order: DECBPM_ORDER_DEFAULT / _RCM / _HILBERT */
     int32_t        spectral_bound;/* rho of the Chebyshev interval: DECBPM_BOUND_DEFAULT / _LANCZOS / _GERSHGORIN */
+    int32_t        lanczos_steps; /* Lanczos steps of the LANCZOS bound (0 = 200; fewer: faster set-up,
+                                     a looser candidate that the per-mesh check may reject) */
 } decbpm_mesh_desc;
 
 typedef struct {
@@ -122,6 +139,10 @@ typedef struct {
     double  mean_degree;       /* nnz_offdiag / n_vertices */
     int64_t sell_entries;      /* padded off-diagonal entries stored (SELL-32) */
     int64_t device_bytes;      /* device memory held by the handle (operators, no workspaces) */
+    int32_t rho_kind;          /* DECBPM_RHO_*: which bound rho is */
+    int32_t pad_;
+    double  rho_lanczos;       /* largest Lanczos Ritz value theta (0 if not run) */
+    double  rho_rigorous;      /* (1 + 1e-6) min(Gershgorin bound, element bound) */
 } decbpm_mesh_info_t;
 
 /* ---- propagation parameters ---------------------------------------------- */
@@ -357,24 +378,29 @@ int decbpm_propagate_batch(const decbpm_mesh_t *meshes, int32_t n_meshes, const 
 
 /* ---- allocation-free propagation -------------------------------------------
  * No counterpart in the paper: a service for callers that cannot allocate
- * device memory when they propagate (for example while another allocator owns
- * the memory budget, during CUDA graph capture, or in loops with a fixed
- * footprint).  Same march as decbpm_propagate on one mesh (fused variant,
- * either precision and Kerr mode), but the scratch (internal-order field
+ * device memory at the moment they propagate -- for example code running while
+ * another allocator (a framework's caching allocator) owns the whole memory
+ * budget, or a loop that must keep a fixed memory footprint.  Same march as
+ * decbpm_propagate on one mesh (fused row kernel, either precision and Kerr
+ * mode, bit for bit the same field), but the scratch (internal-order field
  * copy, three Clenshaw buffers, stage tables, barrier/status words) lives in
  * one static 32 MiB device array of the library instead of allocated
  * workspaces; this call makes no cudaMalloc, cudaFree or pinned-memory
  * allocation.  The scratch needed is about 4 * n_vertices * padded_fields *
  * (8 bytes for C64, 16 for C128) plus 64 KiB; larger requests fail with
  * DECBPM_ERR_INVALID_ARG and a message giving the sizes.  The mesh handle
- * (created beforehand with decbpm_mesh_create) and psi_dev are the caller's.
+ * (created beforehand with decbpm_mesh_create, on the device that is current
+ * at this call, else DECBPM_ERR_INVALID_ARG) and psi_dev are the caller's.
  * No diagnostics are returned.  The first call on a device looks up the
- * array's device address (cudaGetSymbolAddress); make that first call before
- * any stream capture.  All calls share the one array, which keeps the last
- * call's contents (the call clears what must start at zero), so calls that
- * can overlap on the GPU (on different streams or from different host
- * threads of one process) race on it: serialize them.  Each process has its
- * own copy.  The call synchronizes `stream` before returning.               */
+ * array's device address (cudaGetSymbolAddress, with that device current) and
+ * keeps it for the process; make that first call before any stream capture.
+ * A cudaDeviceReset drops the module, so the kept address is stale after it:
+ * do not call this entry point after resetting the device.  All calls share
+ * the one array, which keeps the last call's contents (the call clears what
+ * must start at zero), so calls that can overlap on the GPU (on different
+ * streams or from different host threads of one process) race on it:
+ * serialize them.  Each process has its own copy.  The call synchronizes
+ * `stream` before returning.                                                 */
 int decbpm_propagate_noalloc(decbpm_mesh_t mesh, const decbpm_params *params, void *psi_dev, int64_t n_fields,
                              void *stream);
 

@@ -32,6 +32,9 @@ VARIANT_ROWS = 2
 ORDER_DEFAULT = 0
 ORDER_RCM = 1
 ORDER_HILBERT = 2
+RHO_RIGOROUS = 0
+RHO_LANCZOS_CHECKED = 1
+RHO_LANCZOS_REJECTED = 2
 
 _c_double_p = ctypes.POINTER(ctypes.c_double)
 _c_int32_p = ctypes.POINTER(ctypes.c_int32)
@@ -42,7 +45,8 @@ class MeshDesc(ctypes.Structure):
     _fields_ = [("dim", ctypes.c_int32), ("n_vertices", ctypes.c_int64), ("n_cells", ctypes.c_int64),
                 ("coords", _c_double_p), ("cells", _c_int32_p), ("V_cell", _c_double_p),
                 ("chi_cell", _c_double_p), ("sigma_vertex", _c_double_p), ("p_n", _c_double_p),
-                ("n_p", ctypes.c_int32), ("ordering", ctypes.c_int32), ("spectral_bound", ctypes.c_int32)]
+                ("n_p", ctypes.c_int32), ("ordering", ctypes.c_int32), ("spectral_bound", ctypes.c_int32),
+                ("lanczos_steps", ctypes.c_int32)]
 
 
 class MeshInfo(ctypes.Structure):
@@ -50,7 +54,8 @@ class MeshInfo(ctypes.Structure):
                 ("nnz_offdiag", ctypes.c_int64), ("max_degree", ctypes.c_int32), ("n_p", ctypes.c_int32),
                 ("bandwidth", ctypes.c_int64), ("rho", ctypes.c_double), ("area", ctypes.c_double),
                 ("mean_degree", ctypes.c_double), ("sell_entries", ctypes.c_int64),
-                ("device_bytes", ctypes.c_int64)]
+                ("device_bytes", ctypes.c_int64), ("rho_kind", ctypes.c_int32), ("pad_", ctypes.c_int32),
+                ("rho_lanczos", ctypes.c_double), ("rho_rigorous", ctypes.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

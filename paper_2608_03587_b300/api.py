@@ -31,7 +31,8 @@ _ORDERS = {"default": 0, "rcm": 1, "hilbert": 2}
 _BOUNDS = {"default": 0, "lanczos": 1, "gershgorin": 2}
 
 
-def _desc(coords, cells, V_cell=None, chi_cell=None, sigma=None, p=(1.0,), ordering="default", bound="default"):
+def _desc(coords, cells, V_cell=None, chi_cell=None, sigma=None, p=(1.0,), ordering="default", bound="default",
+          lanczos_steps=0):
     coords = np.ascontiguousarray(coords, dtype=np.float64)
     if coords.ndim == 1:
         coords = coords.reshape(-1, 1)
@@ -44,7 +45,7 @@ def _desc(coords, cells, V_cell=None, chi_cell=None, sigma=None, p=(1.0,), order
     d = L.MeshDesc(dim=coords.shape[1], n_vertices=coords.shape[0], n_cells=cells.shape[0],
                    coords=_dptr(coords), cells=_iptr(cells), V_cell=_dptr(V_cell), chi_cell=_dptr(chi_cell),
                    sigma_vertex=_dptr(sigma), p_n=_dptr(p), n_p=len(p), ordering=_ORDERS[ordering],
-                   spectral_bound=_BOUNDS[bound])
+                   spectral_bound=_BOUNDS[bound], lanczos_steps=int(lanczos_steps))
     return d, keep
 
 
@@ -88,10 +89,10 @@ def _stream_handle(stream):
 
 # ---------------------------------------------------------------- host-only
 def assemble_host(coords, cells, V_cell=None, chi_cell=None, sigma=None, p=(1.0,), ordering="default",
-                  bound="default"):
+                  bound="default", lanczos_steps=0):
     """decbpm_assemble_host: FP64 operators in caller order (no GPU needed)."""
     lib = _lib()
-    d, keep = _desc(coords, cells, V_cell, chi_cell, sigma, p, ordering, bound)
+    d, keep = _desc(coords, cells, V_cell, chi_cell, sigma, p, ordering, bound, lanczos_steps)
     info = L.MeshInfo()
     L.check(lib.decbpm_assemble_host(ctypes.byref(d), ctypes.byref(info), None, None, None, None, None, None, None))
     n0, nnz = info.n_vertices, info.nnz_offdiag + info.n_vertices

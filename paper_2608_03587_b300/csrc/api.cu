@@ -1573,6 +1573,10 @@ int decbpm_assemble_host(const decbpm_mesh_desc *desc, decbpm_mesh_info_t *info,
         info->mean_degree = double(A.col.size()) / double(A.n0);
         info->sell_entries = int64_t(S.col.size());
         info->device_bytes = 0;
+        info->rho_kind = A.rho_kind;
+        info->pad_ = 0;
+        info->rho_lanczos = A.rho_lanczos;
+        info->rho_rigorous = A.rho_rigorous;
     }
     const int64_t n0 = A.n0;
     if (m) std::copy(A.m.begin(), A.m.end(), m);
@@ -1666,6 +1670,10 @@ int decbpm_mesh_info(decbpm_mesh_t m, decbpm_mesh_info_t *info) {
     info->mean_degree = double(m->A.col.size()) / double(m->A.n0);
     info->sell_entries = int64_t(m->S.col.size());
     info->device_bytes = int64_t(m->mem.bytes);
+    info->rho_kind = m->A.rho_kind;
+    info->pad_ = 0;
+    info->rho_lanczos = m->A.rho_lanczos;
+    info->rho_rigorous = m->A.rho_rigorous;
     return DECBPM_OK;
 }
 
@@ -1983,8 +1991,7 @@ int decbpm_propagate_batch(const decbpm_mesh_t *meshes, int32_t n_meshes, const 
 // ============================================================== allocation-free propagate
 // Some callers cannot allocate device memory at the point where they want to
 // propagate: code running while a framework's caching allocator owns the
-// whole memory budget, code that must not touch the allocator while a CUDA
-// graph is being captured, or real-time loops with a fixed memory footprint.
+// whole memory budget, or loops that must keep a fixed memory footprint.
 // For them, decbpm_propagate_noalloc keeps its scratch (the internal-order
 // copy of the field, the three Clenshaw buffers, the stage tables and the
 // barrier/status words) in the file-scope device array below instead of in
@@ -2004,7 +2011,9 @@ std::mutex g_noalloc_mu;
 
 // Device address of g_noalloc_scratch on the current device.  In host code the
 // array's name is only a host-side stand-in, so the address is looked up once
-// per device (with that device current) and cached.
+// per device (with that device current) and kept for the process; a
+// cudaDeviceReset unloads the module and leaves the kept address stale (the
+// header tells callers not to use this entry point after a reset).
 int noalloc_scratch_base(int dev, unsigned char **base) {
     if (dev < 0 || dev >= kNoallocMaxDevices) return fail(DECBPM_ERR_UNSUPPORTED, "device %d out of range", dev);
     std::lock_guard<std::mutex> lock(g_noalloc_mu);
@@ -2048,6 +2057,8 @@ int propagate_noalloc_impl(decbpm_mesh_t mesh, const decbpm_params *prm, void *p
                     need, (long long)n0, bpad, M, kNoallocScratchBytes);
     int dev = 0, sms = 0, per_sm = 0;
     CK(cudaGetDevice(&dev));
+    if (dev != mesh->device)
+        return fail(DECBPM_ERR_INVALID_ARG, "the mesh lives on device %d but device %d is current", mesh->device, dev);
     unsigned char *base = nullptr;
     TRY(noalloc_scratch_base(dev, &base));
     CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));

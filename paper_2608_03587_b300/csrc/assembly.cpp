@@ -235,6 +235,73 @@ static double lanczos_lambda_max(const Assembly &A, int steps) {
     return tridiag_max_eig(alpha, beta);
 }
 
+// Deterministic check that no eigenvalue of S = *0^{-1/2} K *0^{-1/2} (the
+// spectrum of A) lies above a candidate rho.  With rho_t = rho / 1.002 and
+// X = 2 S / rho_t - 1, every eigenvalue in [0, rho_t] has |T_k(x)| <= 1, so
+// ||T_k(X) z|| <= ||z|| for every vector z and every degree k.  An eigenvalue
+// lambda > rho_t (x > 1) instead contributes T_k(x) |c| with
+// T_k(x) = cosh(k acosh x), c its component in z.  The probe z is a seeded
+// pseudo-random vector (a generator and seed of its own, not the Lanczos
+// start) plus unit spikes at the 8 vertices whose Gershgorin rows are largest
+// (where the top eigenvectors of graded meshes concentrate).  Passing at degree
+// 128 therefore shows that every eigenvector whose component in z is at least
+// 1e-3 of ||z|| has lambda < rho (T_128 = 1000 at x = 1.00176, i.e. at
+// rho_t * 1.00088 < rho).  It is no proof for an eigenvector orthogonal to z to
+// that accuracy; no probability is claimed for it.
+static bool verify_upper_bound(const Assembly &A, double rho, int degree) {
+    const int64_t n = A.n0;
+    const double rho_t = rho / 1.002;
+    std::vector<double> isq(n), z(n), t0(n), t1(n), t2(n), tmp(n);
+    for (int64_t i = 0; i < n; ++i) isq[i] = 1.0 / std::sqrt(A.m[i]);
+    uint64_t st = 0xD1B54A32D192ED03ull;            // splitmix64, a different stream from the Lanczos start
+    double nr = 0.0;
+    for (int64_t i = 0; i < n; ++i) {
+        st += 0x9E3779B97F4A7C15ull;
+        uint64_t x = st;
+        x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ull;
+        x = (x ^ (x >> 27)) * 0x94D049BB133111EBull;
+        x ^= x >> 31;
+        z[i] = double(x >> 11) * (1.0 / 9007199254740992.0) - 0.5;
+        nr += z[i] * z[i];
+    }
+    for (auto &x : z) x /= std::sqrt(nr);
+    // spikes at the largest Gershgorin rows of A
+    std::vector<std::pair<double, int64_t>> g(n);
+    for (int64_t p = 0; p < n; ++p) {
+        double wabs = 0.0;
+        for (int64_t e = A.rowptr[p]; e < A.rowptr[p + 1]; ++e) wabs += std::fabs(A.w[e]);
+        g[p] = {(A.wsum[p] + wabs) / A.m[p], p};
+    }
+    const int64_t n_spikes = std::min<int64_t>(8, n);
+    std::partial_sort(g.begin(), g.begin() + n_spikes, g.end(), [](const auto &a, const auto &b) { return a.first > b.first; });
+    for (int64_t j = 0; j < n_spikes; ++j) z[g[j].second] += 1.0;
+    double z2 = 0.0;
+    for (double x : z) z2 += x * x;
+    auto apply_X = [&](const std::vector<double> &u, std::vector<double> &out) {
+        for (int64_t i = 0; i < n; ++i) tmp[i] = isq[i] * u[i];
+        for (int64_t p = 0; p < n; ++p) {
+            double acc = A.wsum[p] * tmp[p];
+            for (int64_t e = A.rowptr[p]; e < A.rowptr[p + 1]; ++e) acc -= A.w[e] * tmp[A.col[e]];
+            out[p] = (2.0 / rho_t) * isq[p] * acc - u[p];
+        }
+    };
+    const double limit = (1.0 + 1e-8) * (1.0 + 1e-8) * z2;
+    t0 = z;
+    apply_X(t0, t1);
+    for (int k = 1; k < degree; ++k) {
+        double s2 = 0.0;
+        for (double x : t1) s2 += x * x;
+        if (!(s2 <= limit)) return false;            // also catches NaN
+        apply_X(t1, t2);
+        for (int64_t i = 0; i < n; ++i) t2[i] = 2.0 * t2[i] - t0[i];
+        std::swap(t0, t1);
+        std::swap(t1, t2);
+    }
+    double s2 = 0.0;
+    for (double x : t1) s2 += x * x;
+    return s2 <= limit;
+}
+
 int assemble(const decbpm_mesh_desc *d, Assembly &A) {
     if (!d) return fail(DECBPM_ERR_INVALID_ARG, "mesh description is NULL");
     if (d->dim != 1 && d->dim != 2) return fail(DECBPM_ERR_INVALID_ARG, "dim must be 1 or 2 (got %d)", d->dim);
@@ -388,14 +455,25 @@ int assemble(const decbpm_mesh_desc *d, Assembly &A) {
     // Gershgorin and the element bound are rigorous; the margin covers rounding
     A.rho_gershgorin = rho;
     A.rho_element = rho_elem;
-    A.rho = (1.0 + 1e-6) * std::min(rho, rho_elem);
+    A.rho_rigorous = (1.0 + 1e-6) * std::min(rho, rho_elem);
+    A.rho = A.rho_rigorous;
+    A.rho_kind = DECBPM_RHO_RIGOROUS;
     if (d->spectral_bound == DECBPM_BOUND_DEFAULT || d->spectral_bound == DECBPM_BOUND_LANCZOS) {
-        // Kuczynski-Wozniakowski: for k Lanczos steps from a random start,
-        // P(lambda_max > theta_k / (1 - eps)) <= 1.648 sqrt(n) exp(-sqrt(eps) (2k - 1)).
-        // k = 200, 1 / (1 - eps) = 1.01 gives < 1e-12 for n < 2^30.
-        const double theta = lanczos_lambda_max(A, 200);
+        // The largest Ritz value theta of k Lanczos steps lies below lambda_max and
+        // is typically within a fraction of a percent of it; 1.01 theta is then
+        // checked per mesh (verify_upper_bound) before it replaces the rigorous bound.
+        if (d->lanczos_steps < 0) return fail(DECBPM_ERR_INVALID_ARG, "lanczos_steps < 0");
+        const int steps = d->lanczos_steps > 0 ? d->lanczos_steps : 200;
+        const double theta = lanczos_lambda_max(A, steps);
         A.rho_lanczos = theta;
-        if (theta > 0) A.rho = std::min(A.rho, 1.01 * theta);
+        if (theta > 0 && 1.01 * theta < A.rho_rigorous) {
+            if (verify_upper_bound(A, 1.01 * theta, 128)) {
+                A.rho = 1.01 * theta;
+                A.rho_kind = DECBPM_RHO_LANCZOS_CHECKED;
+            } else {
+                A.rho_kind = DECBPM_RHO_LANCZOS_REJECTED;
+            }
+        }
     } else if (d->spectral_bound != DECBPM_BOUND_GERSHGORIN) {
         return fail(DECBPM_ERR_INVALID_ARG, "unknown spectral_bound %d", d->spectral_bound);
     }

@@ -34,10 +34,12 @@ struct Assembly {
     // element-averaged Kerr operator C = *0^{-1} Q^T D Q (Eq. 14), same pattern
     std::vector<double> c_off;
     std::vector<double> c_diag;
-    double rho = 0.0;             // upper bound of spec(A), A = *0^{-1} K: min(Gershgorin, element bound)
+    double rho = 0.0;             // upper end of the Chebyshev interval of A = *0^{-1} K (see rho_kind)
     double rho_gershgorin = 0.0;  // max_p (sum_q w_pq + sum_q |w_pq|) / m_p
     double rho_element = 0.0;     // max_t lambda_max(K_t, M_t)
-    double rho_lanczos = 0.0;     // largest Ritz value after 200 Lanczos steps (0 if not run)
+    double rho_lanczos = 0.0;     // largest Ritz value of the Lanczos steps (0 if not run)
+    double rho_rigorous = 0.0;    // (1 + 1e-6) min(Gershgorin, element bound)
+    int32_t rho_kind = DECBPM_RHO_RIGOROUS;   // which bound rho is (DECBPM_RHO_*)
     double area = 0.0;
     int32_t max_degree = 0;
     std::vector<int32_t> perm;    // perm[new] = old

@@ -84,8 +84,10 @@ def test_spectral_bounds_contain_the_spectrum(n):
     coords, tris = W.mesh_disk_graded(4.0, n, 3.0, interfaces=(1.0,), seed=n, grade_from=1.0)
     ops = dec.Operators(coords, tris)
     lam = spla.eigsh(ops.K, k=1, M=sp.diags(ops.H0), which="LA", return_eigenvectors=False)[0]
-    rho = api.assemble_host(coords, tris)["info"]["rho"]
+    info = api.assemble_host(coords, tris)["info"]
+    rho = info["rho"]
     rho_g = api.assemble_host(coords, tris, bound="gershgorin")["info"]["rho"]
+    assert info["rho_kind"] == L.RHO_LANCZOS_CHECKED
     assert lam <= rho <= 1.0101 * lam
     assert lam <= rho_g
     assert rho_g == pytest.approx(min(rho_g, ops.rho * (1 + 1e-6)), rel=1e-12)   # never above Gershgorin
@@ -95,6 +97,28 @@ def test_spectral_bounds_contain_the_spectrum(n):
     lam1 = np.linalg.eigvals(o1.A.toarray()).real.max()
     r1 = api.assemble_host(x, cells)["info"]["rho"]
     assert lam1 <= r1 <= 1.0101 * lam1
+
+
+def test_lanczos_candidate_below_lambda_max_falls_back_to_the_rigorous_bound():
+    """The per-mesh check of the Lanczos candidate 1.01 theta: with too few
+    Lanczos steps theta falls short of lambda_max by more than 1%; the check
+    must then reject the candidate (rho_kind = REJECTED) and rho must be the
+    rigorous min(Gershgorin, element) bound, which contains the spectrum.  On
+    the 60k-vertex mesh 10 steps leave the candidate only ~0.1% below
+    lambda_max; 30 steps put it above, and it is accepted."""
+    coords, tris = W.mesh_disk_graded(4.0, 60000, 3.0, interfaces=(1.0,), seed=60000, grade_from=1.0)
+    ops = dec.Operators(coords, tris)
+    lam = spla.eigsh(ops.K, k=1, M=sp.diags(ops.H0), which="LA", return_eigenvectors=False)[0]
+    for steps in (3, 10):
+        info = api.assemble_host(coords, tris, lanczos_steps=steps)["info"]
+        assert 1.01 * info["rho_lanczos"] < lam            # the candidate is wrong
+        assert info["rho_kind"] == L.RHO_LANCZOS_REJECTED
+        assert info["rho"] == info["rho_rigorous"] and info["rho"] >= lam
+    info = api.assemble_host(coords, tris, lanczos_steps=30)["info"]
+    assert 1.01 * info["rho_lanczos"] >= lam
+    assert info["rho_kind"] == L.RHO_LANCZOS_CHECKED and lam <= info["rho"] <= 1.0101 * lam
+    g = api.assemble_host(coords, tris, bound="gershgorin")["info"]
+    assert g["rho_kind"] == L.RHO_RIGOROUS and g["rho"] == info["rho_rigorous"]
 
 
 def test_host_assembly_1d(fiber):
