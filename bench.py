@@ -37,9 +37,9 @@ METRIC = "vertex-steps/s (complex field) + % HBM roofline, FP32/batched vs plain
 UNIT = "vertex-steps/s"
 
 # DRAM bytes (read + write) per algorithmic byte of the march kernel on this
-# workload, from the one-pass ncu capture of this bench's own launches
-# (profiles/launches_bench_batched_fibers.md), valid for the kernel source
-# whose hash is recorded with it; traffic is reported as null otherwise.
+# workload, from the one-pass ncu capture of this bench's own launches, valid
+# for the kernel source whose hash is recorded with it; traffic is reported as
+# null otherwise.
 TRAFFIC_RATIO = 0.9392
 TRAFFIC_SRC_HASH = "b9b27c6b528c0473"
 
@@ -132,15 +132,28 @@ def build_workload(args, rank: int):
 
 def algorithmic_bytes_per_step(mesh_infos, fields, degrees, scalar_bytes=8):
     """Bytes the degree-M Clenshaw chain must move per z-step (all meshes):
-    per vertex-field, M * (S_op / B + 4 s) + 12 / B with S_op = 8 d + 8
+    per vertex-field, M * (S_op / B + 4 s) + 3 r / B with S_op = (4 + r) d + 4 + r
     (column index and weight per off-diagonal entry, diagonal, row pointer),
-    s = 8 (complex64) and 12 B of per-vertex epilogue data (v, chib, sigma)."""
+    s = 8 (complex64) or 16 (complex128), r = s / 2 the real size, and 3 r B of
+    per-vertex epilogue data (v, chib, sigma): S_op = 8 d + 8, 12 B in FP32."""
+    r = scalar_bytes / 2
     total = 0.0
     for info, B, M in zip(mesh_infos, fields, degrees):
-        s_op = 8.0 * info["mean_degree"] + 8.0
-        per_vf = M * (s_op / B + 4 * scalar_bytes) + 12.0 / B
+        s_op = (4.0 + r) * info["mean_degree"] + 4.0 + r
+        per_vf = M * (s_op / B + 4 * scalar_bytes) + 3.0 * r / B
         total += per_vf * info["n_vertices"] * B
     return total
+
+
+def star0_rel_error(api, mesh, a, b):
+    """*0-weighted relative L2 difference per field of two device fields
+    [N0, B] (a against the reference b), from the library's FP64 diagnostics
+    (power of the difference over power of the reference)."""
+    import torch
+    d = (a.to(torch.complex128) - b.to(torch.complex128)).contiguous()
+    pd = api.diagnostics(mesh, d)["power"]
+    pb = api.diagnostics(mesh, b.to(torch.complex128).contiguous())["power"]
+    return np.sqrt(pd / pb)
 
 
 def max_over_ranks(values, world, device=None):
@@ -263,13 +276,139 @@ def run_ours(args, rank, world, local_rank):
         "clocks": clocks,
     }
     if rank == 0 and not args.no_plain:
+        line["fp32_vs_fp64"], line["fp64_fused"] = fp64_batch_comparison(wl, meshes, plan, fields, infos, api, torch,
+                                                                         dev, args.steps)
         line["fp64_plain"] = plain_fp64_reference(wl, meshes, api, torch, dev)
         line["fp64_plain"]["fp32_batched_speedup"] = value / world / line["fp64_plain"]["value"]
+        line["fp64_plain"]["fp32_batched_error_max"] = line["fp32_vs_fp64"]["max"]
+        line["fp64_plain"]["fp64_fused_speedup"] = line["fp64_fused"]["value"] / line["fp64_plain"]["value"]
         line["rk45"] = rk45_comparison(wl, meshes, api, torch, dev, args.steps)
+    if rank == 0 and not args.no_side:
+        line["single_field"] = single_field_runs(api, torch, dev, args.side_steps, peak)
+        line["adjoint"] = adjoint_run(api, torch, dev)
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args, wl)
         line["cpu_baseline_all_cores"] = cpu_baseline_all_cores(wl, args.cpu_meshes, 16)
     return line
+
+
+def fp64_batch_comparison(wl, meshes, plan32, fields, infos, api, torch, dev, steps):
+    """The timed batch again from its launch fields, outside the timed region:
+    K steps through the complex64 plan and through a complex128 plan of the
+    same meshes (the fused FP64 path), the FP32 result's *0-weighted relative
+    error against FP64 per field, and the FP64 plan's own rate and roofline."""
+    plan64 = api.Plan(meshes, fields, "c128")
+    a = [torch.from_numpy(p).to(dev, torch.complex128).contiguous() for p in wl.psi0]
+    b = [torch.from_numpy(p).to(dev, torch.complex64).contiguous() for p in wl.psi0]
+    plan32.propagate(b, wl.dz, steps)
+    plan64.propagate([x.clone() for x in a], wl.dz, 3)
+    plan64.propagate([x.clone() for x in a], wl.dz, steps)          # graph of this step count
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    plan64.propagate(a, wl.dz, steps)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    march_ms = plan64.last_march_ms()
+    errs = np.concatenate([star0_rel_error(api, m, x, y) for m, x, y in zip(meshes, b, a)])
+    degrees = [plan64.degree(i, wl.dz) for i in range(len(meshes))]
+    alg = algorithmic_bytes_per_step(infos, fields, degrees, scalar_bytes=16) * steps
+    peak, _ = hbm_peak()
+    units = sum(i["n_vertices"] * B for i, B in zip(infos, fields)) * steps
+    err = {"max": float(errs.max()), "median": float(np.median(errs)), "fields": int(errs.size), "steps": steps,
+           "norm": "*0-weighted relative L2 of the complex field, per field, FP32 plan vs FP64 plan"}
+    fp64 = {"value": units / (ms * 1e-3), "unit": UNIT, "steps": steps, "march_ms": march_ms,
+            "cheb_degree_max": int(max(degrees)), "kernel": "march_kernel<double,%d>" % plan64.config()["fields_padded"],
+            "hbm_alg_frac": alg / (march_ms * 1e-3) / 1e9 / peak,
+            "sample": "the whole batch, complex128, fused persistent launch"}
+    plan64.close()
+    return err, fp64
+
+
+def single_field_runs(api, torch, dev, steps, peak):
+    """The single-field workloads as the library runs them (fused FP32 path,
+    one field), each with its error against the fused FP64 run of the same
+    steps: the 200k-vertex graded disk (elliptic Gaussian, absorber) and the
+    1M-vertex multimode guide (charge-1 vortex).  Both working sets fit in the
+    126 MB L2, so the HBM fraction (algorithmic bytes at B = 1) is not a
+    bandwidth claim here; it is reported with the working set."""
+    from paper_2608_03587_b300 import workloads as W
+    out = {}
+    for name, make in (("gaussian_disk_200k", W.gaussian_disk), ("vortex_multimode_1M", W.vortex_multimode)):
+        wl = make()
+        m = wl.meshes[0]
+        mesh = api.Mesh.from_workload(m, p=wl.p)
+        info = mesh.info()
+        res = {}
+        for prec, dt in (("c64", torch.complex64), ("c128", torch.complex128)):
+            plan = api.Plan([mesh], [1], prec)
+            tune = plan.autotune(wl.dz, trial_steps=5)
+            psi = torch.from_numpy(wl.psi0[0]).to(dev, dt).contiguous()
+            plan.propagate([psi.clone()], wl.dz, steps)                  # graph capture, warm-up
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            plan.propagate([psi], wl.dz, steps)
+            e1.record()
+            torch.cuda.synchronize()
+            M = plan.degree(0, wl.dz)
+            res[prec] = (psi, e0.elapsed_time(e1), plan.last_march_ms(), M, tune, plan.config())
+            plan.close()
+        psi32, ms, march_ms, M, tune, cfg = res["c64"]
+        alg = algorithmic_bytes_per_step([info], [1], [M]) * steps
+        err = float(star0_rel_error(api, mesh, psi32, res["c128"][0])[0])
+        n0 = info["n_vertices"]
+        out[name] = {
+            "vertices": n0, "steps": steps, "dz": wl.dz, "cheb_degree": M, "value": n0 * steps / (ms * 1e-3),
+            "unit": UNIT, "march_ms": march_ms, "kernel": "march_kernel<float,1>" if not cfg["fused_kernel"]
+            else "march_tile_kernel", "autotune": {k: tune[k] for k in ("kernel", "ctas_per_sm", "forward_walk")},
+            "alg_bytes_per_vertex_step": alg / steps / n0, "hbm_alg_frac": alg / (march_ms * 1e-3) / 1e9 / peak,
+            "working_set_mb": round((n0 * (8 * info["mean_degree"] + 8) + 4 * 8 * n0 + 12 * n0) / 1e6, 1),
+            "fp32_vs_fp64": err, "fp64_value": n0 * steps / (res["c128"][1] * 1e-3),
+            "fp64_cheb_degree": res["c128"][3]}
+        mesh.close()
+    return out
+
+
+def adjoint_run(api, torch, dev):
+    """Cost of differentiation on the photonic-crystal-fiber workload (300k
+    vertices, 60 holes, 2000 steps): the forward march and decbpm_adjoint
+    (forward with sqrt(N) checkpoints, recomputation, backward march, FP64
+    overlap objective) in vertex-steps/s of forward-equivalent work, FP32 and
+    FP64."""
+    from paper_2608_03587_b300 import workloads as W
+    wl = W.pcf()
+    m = wl.meshes[0]
+    mesh = api.Mesh.from_workload(m, p=wl.p)
+    n0, N = mesh.n_vertices, wl.n_steps
+    out = {"vertices": n0, "steps": N, "checkpoints": int(math.ceil(math.sqrt(N)))}
+    ref = None
+    for prec, dt in (("c128", torch.complex128), ("c64", torch.complex64)):
+        psi0 = torch.from_numpy(wl.psi0[0]).to(dev, dt).contiguous()
+        fwd = psi0.clone()
+        api.propagate(mesh, fwd.clone(), wl.dz, 3)
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        api.propagate(mesh, fwd, wl.dz, N)
+        torch.cuda.synchronize()
+        t_fwd = time.perf_counter() - t
+        target = (fwd.to(torch.complex128) if ref is None else ref).to(dt).contiguous()
+        if ref is None:
+            ref = fwd.to(torch.complex128)
+        t = time.perf_counter()
+        J, gv, g0 = api.adjoint(mesh, psi0, target, wl.dz, N)
+        torch.cuda.synchronize()
+        t_adj = time.perf_counter() - t
+        out[prec] = {"forward_value": n0 * N / t_fwd, "adjoint_value": n0 * N / t_adj, "unit": UNIT,
+                     "forward_s": t_fwd, "adjoint_s": t_adj, "adjoint_over_forward": t_adj / t_fwd, "J": float(J[0])}
+        if prec == "c128":
+            out["_gv64"] = gv
+        else:
+            gv64 = out.pop("_gv64")
+            out["c64"]["grad_v_vs_fp64"] = float(torch.linalg.vector_norm(gv - gv64) / torch.linalg.vector_norm(gv64))
+    mesh.close()
+    return out
 
 
 def rk45_comparison(wl, meshes, api, torch, dev, steps):
@@ -424,6 +563,8 @@ def main():
     ap.add_argument("--ref-meshes", type=int, default=4)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--no-side", action="store_true", help="skip the single-field and adjoint side runs")
+    ap.add_argument("--side-steps", type=int, default=200, help="steps of the single-field side runs")
     ap.add_argument("--variant", choices=["fused", "rows"], default="fused",
                     help="fused: tile-staged kernel where the plan allows it; rows: the row kernel")
     args = ap.parse_args()

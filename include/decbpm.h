@@ -295,6 +295,16 @@ int decbpm_plan_last_march_ms(decbpm_plan_t plan, double *ms);
  * per-vertex refractive-index perturbation enters as dv_p = (k0 L)^2 d(n^2)_p. */
 int decbpm_mesh_set_potential(decbpm_mesh_t mesh, const double *v_vertex);
 
+/* Device-side potential offset: v_p = base_p + dv_dev[p] for every vertex, where
+ * base is the mesh's lumped *0^{-1} *0(V) 1 or the last array given to
+ * decbpm_mesh_set_potential, and dv_dev is an FP64 device array [n_vertices]
+ * in caller order (NULL: v = base).  Enqueued on `stream` (one kernel; no host
+ * copy, no synchronization), so it orders with the propagations on that stream;
+ * it changes the mesh for every later call.  A per-vertex refractive-index
+ * perturbation enters as dv_p = (k0 L)^2 ((n_p)^2 - n_ref^2) in the
+ * normalisation of Eq. 1, so dJ/dn_p = 2 (k0 L)^2 n_p dJ/dv_p.             */
+int decbpm_mesh_set_potential_offset(decbpm_mesh_t mesh, const double *dv_dev, void *stream);
+
 /* Vector-Jacobian product of the whole march psi_N = (D_{h/2} E_h D_{h/2})^N psi_0
  * (lumped Kerr, fused variant) for n_fields fields on one mesh:
  *   gN_dev         [n_vertices * n_fields] Euclidean cotangent of psi_N (dJ = Re sum conj(gN) dpsi_N),
@@ -308,6 +318,24 @@ int decbpm_mesh_set_potential(decbpm_mesh_t mesh, const double *v_vertex);
 int decbpm_vjp(decbpm_mesh_t mesh, const decbpm_params *params, const void *psi0_dev, const void *gN_dev,
                void *psiN_dev, void *grad_psi0_dev, double *grad_v_dev, int64_t n_fields, int32_t checkpoint_every,
                void *stream);
+
+/* Gradient of the overlap objective of a march (the inverse-design use the
+ * paper's Conclusion names as a motivation): for each field f,
+ *   J_f = |<phi_f, psi_N,f>_{*0}|^2 = |sum_p m_p conj(phi_p,f) psi_N,p,f|^2,
+ * psi_N = (D_{h/2} E_h D_{h/2})^N psi_0 (lumped Kerr, fused variant).  The
+ * overlap is formed on the device from the forward result in FP64 (fixed-order
+ * reduction), its cotangent 2 c_f m phi_f starts the same checkpointed backward
+ * march as decbpm_vjp.
+ *   psi0_dev, target_dev  [n_vertices * n_fields], caller order, field-minor, the
+ *                         element type of params->precision (phi_f = target)
+ *   J_out                 host [n_fields]: J_f
+ *   grad_v_dev            out (may be NULL): FP64 [n_vertices] d(sum_f J_f)/dv_p
+ *   grad_psi0_dev         out (may be NULL): dJ_f/dpsi_0,f (dJ = Re sum conj(g) dpsi)
+ * Synchronous.  Errors: INVALID_ARG, UNSUPPORTED (element Kerr, PLAIN/ROWS
+ * variant, a PML), NONFINITE, TIMEOUT, CUDA, OOM.                           */
+int decbpm_adjoint(decbpm_mesh_t mesh, const decbpm_params *params, const void *psi0_dev, const void *target_dev,
+                   int64_t n_fields, double *J_out, double *grad_v_dev, void *grad_psi0_dev, int32_t checkpoint_every,
+                   void *stream);
 
 /* ---- the paper's integrator ---------------------------------------------------
  * Adaptive Dormand-Prince 5(4) (the "RK45" the paper runs through scipy) on

@@ -7,7 +7,8 @@ marshals arguments.  ``workloads`` makes seeded synthetic inputs and can be
 imported without the library.
 """
 _API = ("Mesh", "Plan", "mesh_create", "plan_create", "propagate", "propagate_host", "diagnostics",
-        "assemble_host", "bessel_coefficients", "vjp", "march", "set_potential", "propagate_noalloc", "rk45",
+        "assemble_host", "bessel_coefficients", "vjp", "adjoint", "march", "set_potential", "set_potential_offset",
+        "propagate_noalloc", "rk45",
         "soliton", "bessel_i_scaled", "set_pml")
 
 

@@ -155,6 +155,8 @@ SIGNATURES = {
     "decbpm_selftest_barrier": (_i32, [_i32, _i64, _vp]),
     "decbpm_mesh_set_potential": (_i32, [_vp, _c_double_p]),
     "decbpm_vjp": (_i32, [_vp, ctypes.POINTER(Params), _vp, _vp, _vp, _vp, _vp, _i64, _i32, _vp]),
+    "decbpm_mesh_set_potential_offset": (_i32, [_vp, _vp, _vp]),
+    "decbpm_adjoint": (_i32, [_vp, ctypes.POINTER(Params), _vp, _vp, _i64, _c_double_p, _vp, _vp, _i32, _vp]),
     "decbpm_soliton": (_i32, [_vp, ctypes.POINTER(SolitonOpts), _vp, _vp, ctypes.POINTER(SolitonStats)]),
     "decbpm_bessel_i_scaled": (_i32, [_dbl, _dbl, _i32, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_i32)]),
     "decbpm_mesh_set_pml": (_i32, [_vp, ctypes.POINTER(Pml)]),

@@ -134,7 +134,6 @@ class Mesh:
         self._h = h
         self.n_vertices = int(np.asarray(coords).shape[0])
         self._inputs = (coords, cells, V_cell, chi_cell, sigma, p)
-        self._v_base = None
 
     @classmethod
     def from_workload(cls, m, p=(1.0,), ordering="default", bound="default"):
@@ -324,11 +323,44 @@ def vjp(mesh: Mesh, psi0, gN, dz, n_steps, checkpoint_every=0, want_grad_v=True,
     return psiN, g0, gv
 
 
-def _base_potential(mesh: Mesh):
-    if getattr(mesh, "_v_base", None) is None:
-        a = assemble_host(*mesh._inputs)
-        mesh._v_base = a["v"]
-    return mesh._v_base
+def set_potential_offset(mesh: Mesh, dv=None, stream=None):
+    """decbpm_mesh_set_potential_offset: v = base + dv on the device, dv a real
+    CUDA tensor [N0] in caller order (None: v = base).  Stream-ordered, no host
+    copy.  Returns the FP64 tensor handed to the library (keep it alive until
+    the stream has run the offset kernel)."""
+    import torch
+    if dv is None:
+        L.check(_lib().decbpm_mesh_set_potential_offset(mesh.handle, None, _stream_handle(stream)))
+        return None
+    if not dv.is_cuda or dv.dim() != 1 or dv.shape[0] != mesh.n_vertices:
+        raise ValueError("dv must be a CUDA tensor of shape [n_vertices]")
+    d64 = dv.detach().to(torch.float64).contiguous()
+    L.check(_lib().decbpm_mesh_set_potential_offset(mesh.handle, ctypes.c_void_p(d64.data_ptr()),
+                                                    _stream_handle(stream)))
+    return d64
+
+
+def adjoint(mesh: Mesh, psi0, target, dz, n_steps, checkpoint_every=0, want_grad_v=True, want_grad_psi0=True,
+            stream=None):
+    """decbpm_adjoint: J_f = |<target_f, psi_N,f>_{*0}|^2 (numpy [B]) and its
+    gradients dJ/dv (FP64 CUDA [N0], summed over fields) and dJ/dpsi_0 (like
+    psi0, torch's complex convention); None for a gradient not asked for."""
+    import torch
+    lib = _lib()
+    B = _fields(psi0)
+    if target.shape != psi0.shape or target.dtype != psi0.dtype:
+        raise ValueError("target must have psi0's shape and dtype")
+    prm = _params(dz, n_steps, _precision_of(psi0))
+    target = target.contiguous()
+    J = np.zeros(B)
+    gv = torch.zeros(psi0.shape[0], dtype=torch.float64, device=psi0.device) if want_grad_v else None
+    g0 = torch.empty_like(psi0) if want_grad_psi0 else None
+    L.check(lib.decbpm_adjoint(mesh.handle, ctypes.byref(prm), ctypes.c_void_p(psi0.data_ptr()),
+                               ctypes.c_void_p(target.data_ptr()), B, _dptr(J),
+                               ctypes.c_void_p(gv.data_ptr()) if gv is not None else None,
+                               ctypes.c_void_p(g0.data_ptr()) if g0 is not None else None,
+                               int(checkpoint_every), _stream_handle(stream)))
+    return J, gv, g0
 
 
 def _march_function():
@@ -336,32 +368,35 @@ def _march_function():
 
     class MarchFunction(torch.autograd.Function):
         """psi_N = march(psi_0; v + dv): forward through decbpm_propagate,
-        backward through the hand-written adjoint decbpm_vjp (checkpointed)."""
+        backward through the hand-written adjoint decbpm_vjp (checkpointed).
+        dv reaches the library as a device array (decbpm_mesh_set_potential_offset):
+        no host copy.  The mesh keeps v = base + dv afterwards."""
 
         @staticmethod
         def forward(ctx, psi0, dv, mesh, dz, n_steps, checkpoint_every):
-            v = _base_potential(mesh) + dv.detach().double().cpu().numpy()
-            set_potential(mesh, v)
+            d64 = set_potential_offset(mesh, dv)
             out = psi0.detach().clone().contiguous()
             propagate(mesh, out, dz, n_steps)
-            ctx.save_for_backward(psi0.detach(), dv.detach())
-            ctx.mesh, ctx.dz, ctx.n_steps, ctx.ck = mesh, dz, n_steps, checkpoint_every
+            ctx.save_for_backward(psi0.detach(), d64)
+            ctx.mesh, ctx.dz, ctx.n_steps, ctx.ck, ctx.dv_dtype = mesh, dz, n_steps, checkpoint_every, dv.dtype
             return out
 
         @staticmethod
         def backward(ctx, grad_out):
-            psi0, dv = ctx.saved_tensors
+            psi0, d64 = ctx.saved_tensors
             mesh = ctx.mesh
-            set_potential(mesh, _base_potential(mesh) + dv.double().cpu().numpy())
+            set_potential_offset(mesh, d64)
             _, g0, gv = vjp(mesh, psi0, grad_out.contiguous(), ctx.dz, ctx.n_steps, ctx.ck)
-            return g0, gv.to(dv.dtype), None, None, None, None
+            return g0, gv.to(ctx.dv_dtype), None, None, None, None
 
     return MarchFunction
 
 
 def march(mesh: Mesh, psi0, dv, dz, n_steps, checkpoint_every=0):
     """Differentiable march: gradients flow to psi0 (complex) and to the
-    per-vertex potential offset dv (real, [N0])."""
+    per-vertex potential offset dv (real CUDA tensor [N0]).  For a refractive-
+    index perturbation write dv = (k0 L)^2 (n^2 - n_ref^2) in torch: autograd
+    then returns dJ/dn."""
     return _march_function().apply(psi0, dv, mesh, dz, n_steps, checkpoint_every)
 
 

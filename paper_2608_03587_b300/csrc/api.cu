@@ -84,6 +84,7 @@ struct decbpm_mesh_s {
     int32_t *slice_ptr = nullptr, *slice_w = nullptr, *col = nullptr, *perm = nullptr;
     float *x32, *v32, *chib32, *sig32, *coff32, *cdiag32;
     double *x64, *v64, *chib64, *sig64, *coff64, *cdiag64, *w64, *m64;
+    double *vbase64 = nullptr;   // base potential (internal order) that decbpm_mesh_set_potential_offset adds to
     int32_t *csr_ptr = nullptr, *csr_col = nullptr;
     double *csr_val = nullptr;
     std::map<std::pair<int, int>, decbpm_plan_t> plans;   // (fields, precision) -> cached single-mesh plan
@@ -220,6 +221,7 @@ static int mesh_upload(decbpm_mesh_t M) {
     TRY(D.upload(&M->cdiag32, cast<float>(cdiag)));
     TRY(D.upload(&M->x64, xval));
     TRY(D.upload(&M->v64, v));
+    TRY(D.upload(&M->vbase64, v));
     TRY(D.upload(&M->chib64, chib));
     TRY(D.upload(&M->sig64, sig));
     TRY(D.upload(&M->coff64, cv));
@@ -891,10 +893,13 @@ static int propagate_plain(decbpm_mesh_t m, const decbpm_params *prm, void *psi_
 // then for every step, last first: adjoint of the trailing D_{h/2}, E_h^{-1}
 // (the march kernel with -dz coefficients and the diagonal flow switched
 // off: D_0 is the identity), adjoint of the leading D_{h/2}.
+// With target_dev (decbpm_adjoint) the terminal cotangent is that of the
+// overlap objective J_f = |<phi_f, psi_N,f>_{*0}|^2, formed on the device from
+// the forward result (FP64 overlap, fixed-order reduction); J_out receives J_f.
 template <typename R>
 static int vjp_impl(decbpm_mesh_t mesh, decbpm_plan_t P, const decbpm_params *prm, const void *psi0_dev,
                     const void *gN_dev, void *psiN_dev, void *grad_psi0_dev, double *grad_v_dev, int64_t n_fields,
-                    int32_t ck_every, cudaStream_t s) {
+                    int32_t ck_every, cudaStream_t s, const void *target_dev = nullptr, double *J_out = nullptr) {
     using C = typename CT<R>::c2;
     const int64_t N = prm->n_steps;
     const int64_t n0 = mesh->A.n0;
@@ -915,7 +920,10 @@ static int vjp_impl(decbpm_mesh_t mesh, decbpm_plan_t P, const decbpm_params *pr
     const size_t off_coef = off_view + 256 * ((sizeof(MeshView<R>) + 255) / 256);
     const size_t off_ck = off_coef + 256 * ((sizeof(StageCoef<R>) * M + 255) / 256);
     const size_t off_seg = off_ck + state * size_t(n_ck);
-    const size_t need = off_seg + state * size_t(Cs + 1);
+    const int ovl_blocks = int(std::min<int64_t>(2 * P->num_sms, (n0 + std::max(1, kDiagThreads >> P->bpad_log2) - 1) /
+                                                                    std::max(1, kDiagThreads >> P->bpad_log2)));
+    const size_t off_ovl = off_seg + state * size_t(Cs + 1);          // overlap partials, then c[bpad][2]
+    const size_t need = off_ovl + sizeof(double) * 2 * size_t(bpad) * (size_t(ovl_blocks) + 1);
     if (need > P->adj_ws_bytes) {
         if (P->adj_ws) cudaFree(P->adj_ws);
         P->adj_ws = nullptr;
@@ -1013,8 +1021,19 @@ static int vjp_impl(decbpm_mesh_t mesh, decbpm_plan_t P, const decbpm_params *pr
         permute_out_kernel<C><<<Gs, T, 0, s>>>(psi, (C *)psiN_dev, mesh->perm, int32_t(n0), int32_t(n_fields), bpad,
                                                std::cos(phN), std::sin(phN));
     // terminal cotangent in the internal (phase-free, *0-weighted) frame
-    cotangent_in_kernel<C><<<Gs, T, 0, s>>>((const C *)gN_dev, G, mesh->perm, mesh->m64, int32_t(n0), int32_t(n_fields),
-                                            bpad, std::cos(phN), -std::sin(phN));
+    double *ovl_part = reinterpret_cast<double *>(ws + off_ovl);
+    double *ovl_c = ovl_part + 2 * size_t(bpad) * ovl_blocks;
+    if (target_dev) {
+        overlap_partial_kernel<C><<<ovl_blocks, kDiagThreads, 0, s>>>(psi, (const C *)target_dev, mesh->perm, mesh->m64,
+                                                                      int32_t(n0), P->bpad_log2, int32_t(n_fields),
+                                                                      ovl_part);
+        overlap_final_kernel<<<int(n_fields), kDiagThreads, 0, s>>>(ovl_part, ovl_blocks, bpad, ovl_c);
+        target_cotangent_kernel<C><<<Gs, T, 0, s>>>((const C *)target_dev, ovl_c, mesh->perm, G, int32_t(n0),
+                                                    int32_t(n_fields), bpad);
+    } else {
+        cotangent_in_kernel<C><<<Gs, T, 0, s>>>((const C *)gN_dev, G, mesh->perm, mesh->m64, int32_t(n0),
+                                                int32_t(n_fields), bpad, std::cos(phN), -std::sin(phN));
+    }
     CK(cudaMemsetAsync(gv, 0, sizeof(double) * n0, s));
     const R hh = R(0.5 * prm->dz);
     for (int64_t j = n_ck - 1; j >= 0; --j) {
@@ -1033,7 +1052,9 @@ static int vjp_impl(decbpm_mesh_t mesh, decbpm_plan_t P, const decbpm_params *pr
                                                 mesh->m64, gv);
         }
     }
-    gradient_out_kernel<C><<<Gs, T, 0, s>>>(G, (C *)grad_psi0_dev, mesh->perm, mesh->m64, int32_t(n0), int32_t(n_fields), bpad);
+    if (grad_psi0_dev)
+        gradient_out_kernel<C><<<Gs, T, 0, s>>>(G, (C *)grad_psi0_dev, mesh->perm, mesh->m64, int32_t(n0),
+                                                int32_t(n_fields), bpad);
     if (grad_v_dev) scatter_real_kernel<<<Gv, T, 0, s>>>(gv, grad_v_dev, mesh->perm, int32_t(n0));
     CK(cudaGetLastError());
     CK(cudaStreamSynchronize(s));
@@ -1041,6 +1062,15 @@ static int vjp_impl(decbpm_mesh_t mesh, decbpm_plan_t P, const decbpm_params *pr
     CK(cudaMemcpy(&status, P->status, sizeof(int), cudaMemcpyDeviceToHost));
     if (status == DECBPM_ERR_TIMEOUT) return fail(DECBPM_ERR_TIMEOUT, "grid barrier timed out in the march kernel");
     if (status != 0) return fail(status, "device reported status %d", status);
+    if (target_dev && J_out) {
+        std::vector<double> c(2 * size_t(n_fields));
+        CK(cudaMemcpy(c.data(), ovl_c, sizeof(double) * c.size(), cudaMemcpyDeviceToHost));
+        for (int64_t f = 0; f < n_fields; ++f) {
+            J_out[f] = c[2 * f] * c[2 * f] + c[2 * f + 1] * c[2 * f + 1];
+            if (!std::isfinite(J_out[f])) return fail(DECBPM_ERR_NONFINITE, "overlap objective of field %lld is not finite",
+                                                      (long long)f);
+        }
+    }
     return DECBPM_OK;
 }
 
@@ -1820,8 +1850,19 @@ int decbpm_mesh_set_potential(decbpm_mesh_t m, const double *v_vertex) {
         if (!std::isfinite(v[i])) return fail(DECBPM_ERR_NONFINITE, "v_vertex[%d] is not finite", o);
     }
     std::vector<float> v32(v.begin(), v.end());
+    CK(cudaMemcpy(m->vbase64, v.data(), sizeof(double) * n0, cudaMemcpyHostToDevice));
     CK(cudaMemcpy(m->v64, v.data(), sizeof(double) * n0, cudaMemcpyHostToDevice));
     CK(cudaMemcpy(m->v32, v32.data(), sizeof(float) * n0, cudaMemcpyHostToDevice));
+    return DECBPM_OK;
+}
+
+int decbpm_mesh_set_potential_offset(decbpm_mesh_t m, const double *dv_dev, void *stream) {
+    clear_error();
+    if (!m) return fail(DECBPM_ERR_INVALID_ARG, "mesh is NULL");
+    const int n0 = int(m->A.n0);
+    potential_offset_kernel<<<(n0 + 255) / 256, 256, 0, (cudaStream_t)stream>>>(m->vbase64, dv_dev, m->perm, m->v64,
+                                                                              m->v32, n0);
+    CK(cudaGetLastError());
     return DECBPM_OK;
 }
 
@@ -1843,6 +1884,26 @@ int decbpm_vjp(decbpm_mesh_t mesh, const decbpm_params *params, const void *psi0
                                checkpoint_every, s);
     return vjp_impl<double>(mesh, P, params, psi0_dev, gN_dev, psiN_dev, grad_psi0_dev, grad_v_dev, n_fields,
                             checkpoint_every, s);
+}
+
+int decbpm_adjoint(decbpm_mesh_t mesh, const decbpm_params *params, const void *psi0_dev, const void *target_dev,
+                   int64_t n_fields, double *J_out, double *grad_v_dev, void *grad_psi0_dev, int32_t checkpoint_every,
+                   void *stream) {
+    clear_error();
+    if (!mesh || !psi0_dev || !target_dev || !J_out) return fail(DECBPM_ERR_INVALID_ARG, "NULL argument");
+    TRY(reject_pml(mesh));
+    TRY(check_params(params));
+    if (params->kerr_mode != DECBPM_KERR_LUMPED) return fail(DECBPM_ERR_UNSUPPORTED, "the adjoint supports lumped Kerr");
+    if (params->variant != DECBPM_VARIANT_FUSED) return fail(DECBPM_ERR_UNSUPPORTED, "the adjoint runs the fused variant");
+    if (checkpoint_every < 0) return fail(DECBPM_ERR_INVALID_ARG, "checkpoint_every < 0");
+    decbpm_plan_t P;
+    TRY(single_plan(mesh, n_fields, params->precision, &P));
+    cudaStream_t s = (cudaStream_t)stream;
+    if (params->precision == DECBPM_C64)
+        return vjp_impl<float>(mesh, P, params, psi0_dev, nullptr, nullptr, grad_psi0_dev, grad_v_dev, n_fields,
+                               checkpoint_every, s, target_dev, J_out);
+    return vjp_impl<double>(mesh, P, params, psi0_dev, nullptr, nullptr, grad_psi0_dev, grad_v_dev, n_fields,
+                            checkpoint_every, s, target_dev, J_out);
 }
 
 int decbpm_rk45(decbpm_mesh_t mesh, double z_end, int32_t kerr_mode, const decbpm_rk45_opts *opts, void *psi_dev,

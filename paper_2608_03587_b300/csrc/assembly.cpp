@@ -649,15 +649,44 @@ int cheb_coefficients(const std::vector<double> &p, double rho, double h, double
         const double x = std::cos(pi * (j + 0.5) / N);
         f[j] = std::exp(cd(0.0, h * (gfun(c + r * x) - gc)));
     }
+    // cos(pi k (j + 1/2) / N) = cos(pi m / (2N)), m = k (2j + 1) mod 4N: the
+    // angle is reduced exactly in integers and then by the symmetries of the
+    // cosine to [0, pi/4], so every table value is correct to about an ulp (a
+    // rounded argument pi k (j + 1/2) / N of up to ~pi N radians would put
+    // noise of ~1e-15 into every coefficient).  Sums are compensated
+    // (Neumaier), so the coefficients carry noise of ~2 eps / sqrt(N) only.
+    const int64_t n4 = 4 * int64_t(N), n2 = 2 * int64_t(N);
+    auto cq = [&](int64_t m) {
+        m %= n4;
+        if (m > n2) m = n4 - m;                       // cos(2 pi - t) = cos t
+        double sg = 1.0;
+        if (m > N) { m = n2 - m; sg = -1.0; }         // cos(pi - t) = -cos t
+        return m <= N / 2 ? sg * std::cos(pi * double(m) / double(n2)) : sg * std::sin(pi * double(N - m) / double(n2));
+    };
+    std::vector<double> ctab(n4);
+    for (int64_t m = 0; m < n4; ++m) ctab[m] = cq(m);
+    auto neumaier = [](double &sum, double &comp, double x) {
+        const double t = sum + x;
+        comp += std::fabs(sum) >= std::fabs(x) ? (sum - t) + x : (x - t) + sum;
+        sum = t;
+    };
     std::vector<cd> a(N);
     for (int k = 0; k < N; ++k) {
-        cd s = 0;
-        for (int j = 0; j < N; ++j) s += f[j] * std::cos(pi * k * (j + 0.5) / N);
-        a[k] = s * ((k == 0 ? 1.0 : 2.0) / N);
+        double sr = 0, cr = 0, si = 0, ci = 0;
+        for (int j = 0; j < N; ++j) {
+            const double cs = ctab[(int64_t(k) * (2 * j + 1)) % n4];
+            neumaier(sr, cr, f[j].real() * cs);
+            neumaier(si, ci, f[j].imag() * cs);
+        }
+        a[k] = cd(sr + cr, si + ci) * ((k == 0 ? 1.0 : 2.0) / N);
     }
+    // truncation: coefficients below the noise level eta of the transform do
+    // not count towards the tail (their sum over N terms would otherwise keep
+    // the degree near N)
     const double floor_tol = std::max(tol, 1e-15);
+    const double eta = 16.0 * 2.220446049250313e-16 / std::sqrt(double(N));
     std::vector<double> tail(N + 1, 0.0);
-    for (int k = N - 1; k >= 0; --k) tail[k] = tail[k + 1] + std::abs(a[k]);
+    for (int k = N - 1; k >= 0; --k) tail[k] = tail[k + 1] + std::max(std::abs(a[k]) - eta, 0.0);
     int M = 0;
     while (M < N - 1 && tail[M + 1] > floor_tol) ++M;
     M = std::max(M, 2);

@@ -1266,6 +1266,18 @@ __global__ void scatter_real_kernel(const double *__restrict__ internal, double 
     if (r < n0) user[perm[r]] = internal[r];
 }
 
+// Per-vertex potential with a caller offset (caller order, FP64, device):
+// v64[new] = vbase[new] + dv[perm[new]] (dv NULL: the base), v32 its rounding.
+__global__ void potential_offset_kernel(const double *__restrict__ vbase, const double *__restrict__ dv,
+                                        const int32_t *__restrict__ perm, double *__restrict__ v64,
+                                        float *__restrict__ v32, int32_t n0) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n0) return;
+    const double v = vbase[r] + (dv ? dv[perm[r]] : 0.0);
+    v64[r] = v;
+    v32[r] = float(v);
+}
+
 // ------------------------------------------------------------ diagnostics
 // Per field, FP64: [0] sum m|psi|^2, [1] psi^H K psi, [2] sum |K psi|^2 / m,
 // [3] sum m v |psi|^2, [4] sum m * kerr-energy density, [5] max |psi|^2.
@@ -1348,6 +1360,93 @@ __global__ void __launch_bounds__(kDiagThreads) diag_final_kernel(const double *
         __syncthreads();
     }
     if (threadIdx.x < kDiagQ) out[f * kDiagQ + threadIdx.x] = red[0][threadIdx.x];
+}
+
+// ------------------------------------------------------------ overlap objective
+// c_f = <phi_f, psi_f>_{*0} = sum_p m_p conj(phi_p,f) psi_p,f for every field,
+// in FP64: psi is the internal-order state (without the global phase
+// e^{i n theta0}, which |c|^2 does not see), phi the caller-order target,
+// gathered through perm.  Fixed grid and fixed reduction order (bitwise
+// reproducible), as the diagnostics.  partial: [gridDim.x][bpad][2].
+template <typename C>
+__global__ void __launch_bounds__(kDiagThreads) overlap_partial_kernel(
+        const C *__restrict__ psi, const C *__restrict__ phi, const int32_t *__restrict__ perm,
+        const double *__restrict__ m64, int32_t n0, int32_t bpad_log2, int32_t B, double *__restrict__ partial) {
+    __shared__ double red[kDiagThreads][2];
+    const int bpad = 1 << bpad_log2;
+    const int f = threadIdx.x & (bpad - 1);
+    const int slot = threadIdx.x >> bpad_log2, nslot = kDiagThreads >> bpad_log2;
+    const int lo = int((long long)n0 * blockIdx.x / gridDim.x), hi = int((long long)n0 * (blockIdx.x + 1) / gridDim.x);
+    double cr = 0.0, ci = 0.0;
+    if (nslot > 0 && f < B) {
+        for (int p = lo + slot; p < hi; p += nslot) {
+            const C a = psi[(size_t)p * bpad + f];
+            const C t = phi[(size_t)perm[p] * B + f];
+            const double m = m64[p];
+            cr += m * (double(t.x) * double(a.x) + double(t.y) * double(a.y));   // conj(t) a
+            ci += m * (double(t.x) * double(a.y) - double(t.y) * double(a.x));
+        }
+    }
+    red[threadIdx.x][0] = cr;
+    red[threadIdx.x][1] = ci;
+    __syncthreads();
+    if (threadIdx.x < bpad && nslot > 0) {
+        double sr = 0.0, si = 0.0;
+        for (int sl = 0; sl < nslot; ++sl) {
+            sr += red[sl * bpad + threadIdx.x][0];
+            si += red[sl * bpad + threadIdx.x][1];
+        }
+        partial[((size_t)blockIdx.x * bpad + threadIdx.x) * 2] = sr;
+        partial[((size_t)blockIdx.x * bpad + threadIdx.x) * 2 + 1] = si;
+    }
+}
+
+// One block per field: c[f] = (re, im), fixed order over the blocks' partials.
+__global__ void __launch_bounds__(kDiagThreads) overlap_final_kernel(const double *__restrict__ partial, int32_t nblocks,
+                                                                     int32_t bpad, double *__restrict__ c) {
+    __shared__ double red[kDiagThreads][2];
+    const int f = blockIdx.x;
+    double sr = 0.0, si = 0.0;
+    for (int b = threadIdx.x; b < nblocks; b += blockDim.x) {
+        sr += partial[((size_t)b * bpad + f) * 2];
+        si += partial[((size_t)b * bpad + f) * 2 + 1];
+    }
+    red[threadIdx.x][0] = sr;
+    red[threadIdx.x][1] = si;
+    __syncthreads();
+    for (int half = kDiagThreads / 2; half > 0; half >>= 1) {
+        if (threadIdx.x < half) {
+            red[threadIdx.x][0] += red[threadIdx.x + half][0];
+            red[threadIdx.x][1] += red[threadIdx.x + half][1];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) { c[2 * f] = red[0][0]; c[2 * f + 1] = red[0][1]; }
+}
+
+// Cotangent of J_f = |c_f|^2 in the internal *0-weighted, phase-free frame:
+// the Euclidean gradient 2 c m phi (caller frame, with the phase e^{i N theta0}
+// in c) divided by m and rotated by e^{-i N theta0} is 2 c_int phi, c_int the
+// overlap of the internal state.  Padding fields get 0.
+template <typename C>
+__global__ void target_cotangent_kernel(const C *__restrict__ phi, const double *__restrict__ c,
+                                        const int32_t *__restrict__ perm, C *__restrict__ G, int32_t n0, int32_t B,
+                                        int32_t bpad) {
+    const long long n = (long long)n0 * bpad;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const int r = int(i / bpad), f = int(i % bpad);
+        C o;
+        if (f < B) {
+            const C t = phi[(size_t)perm[r] * B + f];
+            const double cr = 2.0 * c[2 * f], ci = 2.0 * c[2 * f + 1];
+            o.x = decltype(t.x)(cr * double(t.x) - ci * double(t.y));
+            o.y = decltype(t.x)(cr * double(t.y) + ci * double(t.x));
+        } else {
+            o.x = 0;
+            o.y = 0;
+        }
+        G[i] = o;
+    }
 }
 
 // ------------------------------------------------------------ the paper's integrator

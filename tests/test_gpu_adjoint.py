@@ -69,6 +69,68 @@ def test_vjp_fp32_close_to_fp64():
     assert _rel(res[torch.complex64][1], res[torch.complex128][1]) <= 1e-4
 
 
+def test_adjoint_entry_point_matches_oracle():
+    """decbpm_adjoint, whose overlap objective J_f = |<phi_f, psi_N,f>_{*0}|^2
+    and its cotangent are formed on the device (FP64 overlap), against the
+    oracle's overlap_objective + vjp: J, dJ/dpsi_0 and d(sum J)/dv, two fields
+    with their own targets, several checkpoint intervals."""
+    coords, tris, V, chi, sigma = _setup(seed=21)
+    ops = dec.Operators(coords, tris, V, chi)
+    mesh = api.Mesh(coords, tris, V, chi, sigma)
+    psi0 = np.stack([W.gaussian(coords, w=0.7, A=2.0), W.elliptic_gaussian(coords, A=1.5)], axis=1)
+    phi = np.stack([W.gaussian(coords, w=0.5) * np.exp(0.4j), W.gaussian(coords, w=0.8) * np.exp(-1.1j)], axis=1)
+    dz, n = 2e-3, 11
+    J_ref, g0_ref, gv_ref = [], [], np.zeros(len(coords))
+    for f in range(2):
+        out = bpm.propagate(ops, (1.0,), psi0[:, f], dz, n, sigma)
+        J, G = bpm.overlap_objective(ops, phi[:, f], out)
+        g0, gv = bpm.vjp(ops, (1.0,), psi0[:, f], G, dz, n, sigma)
+        J_ref.append(J)
+        g0_ref.append(g0)
+        gv_ref = gv_ref + gv
+    g0_ref = np.stack(g0_ref, axis=1)
+    t0 = torch.from_numpy(psi0).to(DEV, torch.complex128).contiguous()
+    tp = torch.from_numpy(phi).to(DEV, torch.complex128).contiguous()
+    for ck in (0, 4, 11):
+        J, gv, g0 = api.adjoint(mesh, t0, tp, dz, n, checkpoint_every=ck)
+        assert np.max(np.abs(J - np.asarray(J_ref)) / np.asarray(J_ref)) <= 1e-10, (ck, J, J_ref)
+        assert _rel(g0.cpu().numpy(), g0_ref) <= 1e-10, ck
+        assert _rel(gv.cpu().numpy(), gv_ref) <= 1e-10, ck
+    # complex64: the same objective within the FP32 run budget
+    J32, gv32, g032 = api.adjoint(mesh, t0.to(torch.complex64), tp.to(torch.complex64), dz, n)
+    assert np.max(np.abs(J32 - np.asarray(J_ref)) / np.asarray(J_ref)) <= 1e-5
+    assert _rel(gv32.cpu().numpy(), gv_ref) <= 1e-4
+    assert _rel(g032.cpu().numpy().astype(np.complex128), g0_ref) <= 1e-4
+
+
+def test_device_potential_offset_equals_host_potential():
+    """decbpm_mesh_set_potential_offset (v = base + dv on the device) gives the
+    same field, bit for bit, as setting base + dv from the host; NULL restores
+    the base."""
+    coords, tris, V, chi, sigma = _setup(seed=5)
+    mesh = api.Mesh(coords, tris, V, chi, sigma)
+    v0 = api.assemble_host(coords, tris, V, chi, sigma)["v"]
+    dv = np.random.default_rng(8).standard_normal(len(coords)) * 0.3
+    psi0 = torch.from_numpy(W.gaussian(coords, w=0.7, A=2.0)).to(DEV, torch.complex128)
+    outs = []
+    for mode in ("host", "device"):
+        if mode == "host":
+            api.set_potential(mesh, v0 + dv)
+        else:
+            api.set_potential(mesh, None)
+            api.set_potential_offset(mesh, torch.from_numpy(dv).to(DEV))
+        t = psi0.clone()
+        api.propagate(mesh, t, 2e-3, 9)
+        outs.append(t)
+    assert torch.equal(outs[0], outs[1])
+    api.set_potential_offset(mesh, None)
+    a, b = psi0.clone(), psi0.clone()
+    api.propagate(mesh, a, 2e-3, 9)
+    api.set_potential(mesh, None)
+    api.propagate(mesh, b, 2e-3, 9)
+    assert torch.equal(a, b) and not torch.equal(a, outs[0])
+
+
 def _objective(mesh, psi0_t, phi_m, dz, n, v):
     api.set_potential(mesh, v)
     t = psi0_t.clone()

@@ -4,7 +4,11 @@ Tolerances (relative *0-weighted L2 error of the complex field):
   FP64 (C128) fused and plain paths ........ 1e-12 over whole runs
   FP32 (C64) fused path .................... 1e-5 for one step from the oracle
                                              state, 1e-4 over a whole run
-Diagnostics (power, Hamiltonian) are FP64 on both sides: 1e-11 relative.
+Diagnostics are FP64 on both sides: power 1e-11 relative; Hamiltonian 1e-10,
+because its kinetic term psi^H K psi weights the field difference by A: a
+1e-12 difference in the stiffest modes (lambda ~ rho = 1.1e3, where the two
+propagators' truncation errors sit) against a field whose mean lambda is ~1.5
+appears in H amplified by up to 2 sqrt(rho / lambda) ~ 50.
 Sizes span many SELL slices and a ragged last slice; edge cases cover a
 single triangle, fewer than 32 vertices, the maximum field count, zero steps.
 """
@@ -114,17 +118,40 @@ def test_fp64_diagnostics_and_blocks(fiber):
     del nt
 
 
-def test_fp64_higher_order_diffraction(fiber):
-    """p = (p1, p2): exp(i h (p2 A^2 - p1 A)) by the DCT Chebyshev path."""
+@pytest.mark.parametrize("p2", [2e-5, -3e-5])
+def test_fp64_higher_order_diffraction(fiber, p2):
+    """p = (p1, p2): exp(i h (p2 A^2 - p1 A)) (Table I's higher-order row) by
+    the Chebyshev path whose coefficients come from a cosine transform."""
     coords, tris, V, chi, sigma, ops, mesh = fiber
-    p = (1.0, 2e-5)
+    p = (1.0, p2)
     m2 = api.Mesh(coords, tris, V, chi, sigma, p=p)
-    psi0 = launch(coords, 1, seed=5)[:, 0]
+    psi0 = launch(coords, 2, seed=5)
     dz, n = 1e-3, 6
     ref = bpm.propagate(ops, p, psi0, dz, n, sigma)
     t = to_dev(psi0)
     api.propagate(m2, t, dz, n)
-    assert rel(ops, from_dev(t), ref) <= 1e-11
+    assert rel(ops, from_dev(t), ref) <= 1e-12
+
+
+def test_fp32_higher_order_diffraction(fiber):
+    """The p2 path in FP32: one step from the oracle's state (<= 1e-5) and a
+    whole run (<= 1e-4)."""
+    coords, tris, V, chi, sigma, ops, mesh = fiber
+    p = (1.0, 2e-5)
+    m2 = api.Mesh(coords, tris, V, chi, sigma, p=p)
+    psi0 = launch(coords, 2, seed=15)
+    dz = 1e-3
+    state = bpm.propagate(ops, p, psi0, dz, 4, sigma)
+    state32 = state.astype(np.complex64).astype(np.complex128)
+    ref = bpm.propagate(ops, p, state32, dz, 1, sigma)
+    t = to_dev(state32, torch.complex64)
+    api.propagate(m2, t, dz, 1)
+    assert rel(ops, from_dev(t), ref) <= 1e-5
+    n = 300
+    ref = bpm.propagate(ops, p, psi0, dz, n, sigma)
+    t = to_dev(psi0, torch.complex64)
+    api.propagate(m2, t, dz, n)
+    assert rel(ops, from_dev(t), ref) <= 1e-4
 
 
 def test_fp64_element_kerr(fiber):
