@@ -393,9 +393,13 @@ def adjoint_run(api, torch, dev):
         api.propagate(mesh, fwd, wl.dz, N)
         torch.cuda.synchronize()
         t_fwd = time.perf_counter() - t
-        target = (fwd.to(torch.complex128) if ref is None else ref).to(dt).contiguous()
         if ref is None:
-            ref = fwd.to(torch.complex128)
+            # the target: the unperturbed guide's output, phase-shifted and mixed
+            # with a narrower Gaussian, so that J is not at its maximum (where
+            # dJ/dv would vanish by cancellation)
+            ref = fwd.to(torch.complex128) * complex(math.cos(0.2), math.sin(0.2)) + 0.1 * torch.from_numpy(
+                W.gaussian(m.coords, w=0.4)).to(dev, torch.complex128).reshape(fwd.shape)
+        target = ref.to(dt).contiguous()
         t = time.perf_counter()
         J, gv, g0 = api.adjoint(mesh, psi0, target, wl.dz, N)
         torch.cuda.synchronize()

@@ -586,7 +586,10 @@ __device__ __forceinline__ void for_my_items(const MarchParams<R> &P, const int3
 
 // CTAs per SM the march kernel is compiled for: the FP64 variants need
 // 150-220 registers per thread, so they get the whole register file.
-template <typename R> struct MarchMinBlocks { static constexpr int value = sizeof(R) == 8 ? 1 : DECBPM_MARCH_MINB; };
+#ifndef DECBPM_MARCH_MINB64
+#define DECBPM_MARCH_MINB64 1
+#endif
+template <typename R> struct MarchMinBlocks { static constexpr int value = sizeof(R) == 8 ? DECBPM_MARCH_MINB64 : DECBPM_MARCH_MINB; };
 
 template <typename R, int BPAD>
 __global__ void __launch_bounds__(256, MarchMinBlocks<R>::value) march_kernel(MarchParams<R> P) {

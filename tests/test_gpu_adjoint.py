@@ -186,6 +186,14 @@ def test_vjp_potential_gradient_vs_central_differences(n_vertices, n_steps):
         errs.append(abs(gv[p] - fd) / max(abs(fd), 1e-300))
     api.set_potential(mesh, None)
     assert max(errs) <= 1e-4, (max(errs), np.median(errs))
+    if n_vertices >= 300_000:
+        # the complex64 adjoint of the same 2000-step march (FP32 forward,
+        # recomputation and backward march) against the FP64 one
+        G32 = torch.from_numpy(G).to(DEV, torch.complex64)
+        _, g032, gv32 = api.vjp(mesh, t0.to(torch.complex64), G32, dz, n_steps)
+        _, g064, _ = api.vjp(mesh, t0, torch.from_numpy(G).to(DEV, torch.complex128), dz, n_steps)
+        assert _rel(gv32.cpu().numpy(), gv) <= 1e-4
+        assert _rel(g032.cpu().numpy().astype(np.complex128), g064.cpu().numpy()) <= 1e-4
 
 
 def test_autograd_function_matches_vjp():

@@ -80,30 +80,49 @@ def test_vortex_multimode_full_size():
 
 
 def test_batched_fibers_full_run():
-    """The bench workload (16 fibers, 20k..500k vertices, 16 fields each):
-    FP32 vs FP64 on the whole batch over 20 steps; the full 5,000-step FP32
-    run (tile-staged kernel), whose four smallest meshes are compared with an
-    FP64 plan of those meshes over the same 5,000 steps."""
+    """The bench workload (16 fibers, 20k..500k vertices, 16 fields each)
+    through the complex64 plan the bench times (tile-staged kernel), against
+    the fused FP64 march, <= 1e-4 per field (*0-weighted relative L2):
+      * the whole 5,000-step run on every one of the 16 meshes: field f = i mod
+        16 of mesh i against a one-field FP64 plan of the same meshes;
+      * all 256 fields over the first 100 steps against an FP64 plan of the
+        whole batch.
+    The FP64 arithmetic of B300 (its FP64 pipe, not HBM, bounds the FP64
+    march: ~340 ms per step for the 256 fields) puts a 5,000-step FP64 replay
+    of all 256 fields (~29 min) beyond a test run; the fields of a mesh are
+    seeded superpositions of the same eight modes, and the FP32 drift that the
+    long comparison guards against depends on the mesh (its degree, its
+    spectrum), which every mesh's own field covers.  With the absorber the
+    FP32 power never increases."""
     wl = W.batched_fibers()
     meshes = [api.Mesh.from_workload(mm, p=wl.p) for mm in wl.meshes]
     ws = [dec.star0(mm.coords, mm.cells) for mm in wl.meshes]
-    plan32 = api.Plan(meshes, [16] * len(meshes), "c64")
+    n_m = len(meshes)
+    plan32 = api.Plan(meshes, [16] * n_m, "c64")
     assert plan32.config()["tile_slots"] >= 2
-    plan64 = api.Plan(meshes, [16] * len(meshes), "c128")
-    a = [torch.from_numpy(p).to(DEV, torch.complex128) for p in wl.psi0]
     b = [torch.from_numpy(p).to(DEV, torch.complex64) for p in wl.psi0]
-    plan64.propagate(a, wl.dz, 20)
-    plan32.propagate(b, wl.dz, 20)
+    # all 256 fields, first 100 steps
+    plan64 = api.Plan(meshes, [16] * n_m, "c128")
+    a = [torch.from_numpy(p).to(DEV, torch.complex128) for p in wl.psi0]
+    plan64.propagate(a, wl.dz, 100)
+    plan32.propagate(b, wl.dz, 100)
+    worst = 0.0
     for w, x, y in zip(ws, b, a):
-        assert rel(w, x.cpu().numpy(), y.cpu().numpy()) <= 1e-5 * 20
-    # full FP32 run from the launch fields
+        xx, yy = x.cpu().numpy().astype(np.complex128), y.cpu().numpy()
+        for f in range(16):
+            worst = max(worst, rel(w, xx[:, f], yy[:, f]))
+    assert worst <= 1e-4, worst
+    plan64.close()
+    del a
+    # the full run: FP32 batch from the launch fields, one field per mesh in FP64
     b = [torch.from_numpy(p).to(DEV, torch.complex64) for p in wl.psi0]
     diag = plan32.propagate(b, wl.dz, wl.n_steps, diag_every=1000)
     P = diag["power"]
     assert np.all(np.isfinite(P)) and np.all(np.diff(P, axis=0) <= 1e-6)
-    small = list(np.argsort([mm.n_vertices for mm in wl.meshes])[:4])
-    plan_s = api.Plan([meshes[i] for i in small], [16] * 4, "c128")
-    c = [torch.from_numpy(wl.psi0[i]).to(DEV, torch.complex128) for i in small]
-    plan_s.propagate(c, wl.dz, wl.n_steps)
-    for j, i in enumerate(small):
-        assert rel(ws[i], b[i].cpu().numpy(), c[j].cpu().numpy()) <= 1e-4
+    cols = [i % 16 for i in range(n_m)]
+    plan1 = api.Plan(meshes, [1] * n_m, "c128")
+    c = [torch.from_numpy(np.ascontiguousarray(wl.psi0[i][:, f])).to(DEV, torch.complex128).reshape(-1, 1)
+         for i, f in enumerate(cols)]
+    plan1.propagate(c, wl.dz, wl.n_steps)
+    errs = [rel(ws[i], b[i][:, f].cpu().numpy(), c[i][:, 0].cpu().numpy()) for i, f in enumerate(cols)]
+    assert max(errs) <= 1e-4, errs
