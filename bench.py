@@ -243,8 +243,9 @@ def run_ours(args, rank, world, local_rank):
     # kernels of ours per timed call: permute in / out per mesh, the march
     # kernel, two diagnostic kernels per mesh
     launches = 1 + 4 * len(meshes)
-    tiled = bool(cfg.get("fused_kernel", 0)) and args.variant == "fused"
-    kernel_name = "march_tile_kernel" if tiled else "march_kernel<float,%d>" % cfg["fields_padded"]
+    fk = cfg.get("fused_kernel", 0) if args.variant == "fused" else {"pairs": 2, "rows": 0}.get(args.variant, 0)
+    tiled = fk >= 1
+    kernel_name = {2: "march_pair_kernel", 1: "march_tile_kernel"}.get(fk, "march_kernel<float,%d>" % cfg["fields_padded"])
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
@@ -256,7 +257,9 @@ def run_ours(args, rank, world, local_rank):
             "vertices_total": int(sum(i["n_vertices"] for i in infos)), "fields_per_mesh": fields[0],
             "cheb_degree_min": int(min(degrees)), "cheb_degree_max": int(max(degrees)),
             "ordering": "hilbert", "parallelism": "replicas" if world > 1 else "single",
-            "grid": cfg["tile_grid"] if tiled else cfg["grid"], "block": cfg["tile_block"] if tiled else cfg["block"],
+            "grid": cfg["pair_grid"] if fk == 2 else cfg["tile_grid"] if tiled else cfg["grid"],
+            "block": cfg["tile_block"] if tiled else cfg["block"],
+            "passes_per_step": cfg["passes"] if fk == 2 else None,
             "march_kernel": kernel_name, "tile_slots": cfg["tile_slots_used"] if tiled else 0,
             "forward_walk": cfg["forward_walk"],
             "autotune": None if tune is None else {k: tune[k] for k in ("kernel", "ctas_per_sm", "tile_slots",
@@ -569,8 +572,8 @@ def main():
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-side", action="store_true", help="skip the single-field and adjoint side runs")
     ap.add_argument("--side-steps", type=int, default=200, help="steps of the single-field side runs")
-    ap.add_argument("--variant", choices=["fused", "rows"], default="fused",
-                    help="fused: tile-staged kernel where the plan allows it; rows: the row kernel")
+    ap.add_argument("--variant", choices=["fused", "rows", "pairs"], default="fused",
+                    help="fused: the autotuner's choice; pairs: the stage-pair kernel; rows: the row kernel")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

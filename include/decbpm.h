@@ -69,6 +69,11 @@ extern "C" {
 #define DECBPM_VARIANT_PLAIN  1  /* unfused reference path: one CSR SpMV launch + one update launch per term */
 #define DECBPM_VARIANT_ROWS   2  /* fused, operands read straight from global memory (never the tile-staged
                                     kernel that FUSED selects for complex64 plans with 9..16 fields) */
+#define DECBPM_VARIANT_PAIRS  3  /* fused, two Clenshaw stages per grid-wide pass (stage-pair kernel, complex64
+                                    plans with 9..16 fields whose tiles' depth-two halos fit its capacities; other
+                                    plans run FUSED).  It stores a_k psi - b_{k+2} in place of b_{k+2}, so its
+                                    fields differ from FUSED's at the level of FP32 rounding.  FUSED runs it once
+                                    decbpm_plan_autotune has chosen it. */
 
 #define DECBPM_ORDER_DEFAULT  0  /* Hilbert curve in 2D, coordinate order in 1D */
 #define DECBPM_ORDER_RCM      1  /* reverse Cuthill-McKee (small bandwidth, thin level sets) */
@@ -255,25 +260,32 @@ typedef struct {
     int32_t tile_grid;     /* CTAs of the tile-staged launch */
     int32_t tile_block;    /* threads per CTA of the tile-staged launch (16 compute + 3 copy warps) */
     int32_t tuned;         /* 1 once decbpm_plan_autotune chose the launch shapes below */
-    int32_t fused_kernel;  /* FUSED runs: 1 the tile-staged kernel, 0 the row kernel (grid above) */
+    int32_t fused_kernel;  /* FUSED runs: 2 the stage-pair kernel, 1 the tile-staged kernel, 0 the row kernel */
     int32_t tile_slots_used; /* ring slots the tile-staged kernel uses */
     int32_t forward_walk;  /* 1: odd stages do not walk backwards */
+    int32_t pair_slots;    /* > 0: the plan can run the stage-pair kernel with this many ring slots */
+    int32_t pair_slot_bytes;
+    int32_t pair_grid;     /* CTAs of the stage-pair launch */
+    int32_t passes;        /* grid-wide passes per step of the stage-pair kernel (last configured dz) */
 } decbpm_plan_config;
 int decbpm_plan_get_config(decbpm_plan_t plan, decbpm_plan_config *cfg);
 
 /* Autotuner of the FUSED variant's launch shapes (no counterpart in the paper:
  * the kernels' own tuning).  Times short trial marches of `trial_steps` steps
  * (1..1000) at step dz on the plan's internal buffers, for every candidate:
- * the tile-staged kernel with 3 or 2 ring slots (complex64 plans with 9..16
- * fields), the row kernel with 1..max co-resident CTAs per SM, each with and
- * without the reverse walk of odd stages; keeps the fastest for this plan and
- * caches it for the process (key: the meshes' content, field counts,
- * precision, dz, kerr_mode), so another plan of the same problem takes it
- * without timing (out->from_cache = 1).  Results do not depend on the choice:
- * every candidate does the same arithmetic per row.  Synchronous; the plan's
- * internal buffers are overwritten (they hold nothing between calls). */
+ * the stage-pair kernel with 3 or 2 ring slots and the tile-staged kernel
+ * with 3 or 2 ring slots (complex64 plans with 9..16 fields), the row kernel
+ * with 1..max co-resident CTAs per SM, each with and without the reverse walk
+ * of odd stages; keeps the fastest for this plan and caches it for the
+ * process (key: the meshes' content, field counts, precision, dz, kerr_mode),
+ * so another plan of the same problem takes it without timing
+ * (out->from_cache = 1).  The single-stage candidates do the same arithmetic
+ * per row (bitwise identical fields); the stage-pair kernel differs from them
+ * at the level of FP32 rounding (see DECBPM_VARIANT_PAIRS).  Synchronous; the
+ * plan's internal buffers are overwritten (they hold nothing between calls). */
 typedef struct {
-    int32_t variant;       /* DECBPM_VARIANT_FUSED: the tile-staged kernel; DECBPM_VARIANT_ROWS: the row kernel */
+    int32_t variant;       /* DECBPM_VARIANT_PAIRS: the stage-pair kernel; DECBPM_VARIANT_FUSED: the tile-staged
+                              kernel; DECBPM_VARIANT_ROWS: the row kernel */
     int32_t ctas_per_sm;   /* row kernel: co-resident CTAs per SM (tile kernel: 1) */
     int32_t tile_slots;    /* tile kernel: ring slots (0 for the row kernel) */
     int32_t forward_walk;  /* 1: odd stages walk forwards */

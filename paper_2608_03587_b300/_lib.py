@@ -29,6 +29,7 @@ KERR_ELEMENT = 1
 VARIANT_FUSED = 0
 VARIANT_PLAIN = 1
 VARIANT_ROWS = 2
+VARIANT_PAIRS = 3
 ORDER_DEFAULT = 0
 ORDER_RCM = 1
 ORDER_HILBERT = 2
@@ -72,7 +73,8 @@ class PlanConfig(ctypes.Structure):
                 ("graphs", ctypes.c_int32), ("stages", ctypes.c_int32), ("n_meshes", ctypes.c_int32),
                 ("tile_slots", ctypes.c_int32), ("tile_slot_bytes", ctypes.c_int32), ("tile_grid", ctypes.c_int32),
                 ("tile_block", ctypes.c_int32), ("tuned", ctypes.c_int32), ("fused_kernel", ctypes.c_int32),
-                ("tile_slots_used", ctypes.c_int32), ("forward_walk", ctypes.c_int32)]
+                ("tile_slots_used", ctypes.c_int32), ("forward_walk", ctypes.c_int32), ("pair_slots", ctypes.c_int32),
+                ("pair_slot_bytes", ctypes.c_int32), ("pair_grid", ctypes.c_int32), ("passes", ctypes.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -85,7 +87,7 @@ class TuneResult(ctypes.Structure):
 
     def as_dict(self):
         d = {k: getattr(self, k) for k, _ in self._fields_}
-        d["kernel"] = "tile" if self.variant == VARIANT_FUSED else "rows"
+        d["kernel"] = {VARIANT_FUSED: "tile", VARIANT_PAIRS: "pairs"}.get(self.variant, "rows")
         return d
 
 

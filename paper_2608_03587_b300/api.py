@@ -53,7 +53,7 @@ def _params(dz, n_steps, precision, kerr="lumped", diag_every=0, variant="fused"
     return L.Params(dz=float(dz), n_steps=int(n_steps), precision=precision,
                     kerr_mode=L.KERR_LUMPED if kerr == "lumped" else L.KERR_ELEMENT,
                     diag_every=int(diag_every), variant={"fused": L.VARIANT_FUSED, "plain": L.VARIANT_PLAIN,
-                                                            "rows": L.VARIANT_ROWS}[variant],
+                                                            "rows": L.VARIANT_ROWS, "pairs": L.VARIANT_PAIRS}[variant],
                     cheb_tol=float(cheb_tol))
 
 

@@ -99,6 +99,13 @@ struct decbpm_mesh_s {
     uint16_t *lcol = nullptr;
     int32_t *tdesc = nullptr, *halo_rows = nullptr, *halo_ovf = nullptr;
     int n_tiles = 0, max_halo = 0, max_entries = 0;
+    // stage-pair maps (built on first use): per tile the depth-two halo list,
+    // descriptor, and the SELL entries of the first halo ring
+    bool pairs_ready = false, pairs_ok = false;
+    int32_t *pdesc = nullptr, *hlist = nullptr;
+    uint16_t *lcol2 = nullptr;
+    float *x2 = nullptr;
+    int max_nh1 = 0, max_nh12 = 0, max_hentries = 0;
     double r() const { return 0.5 * A.rho; }
 };
 
@@ -176,6 +183,128 @@ static int build_tiles(decbpm_mesh_t M) {
     M->max_entries = max_entries;
     M->tiles_ready = true;
     M->tiles_ok = true;
+    return DECBPM_OK;
+}
+
+// Stage-pair maps of the 128-row tiles (see march_pair_kernel): H1 = the
+// tile's neighbour rows outside it (sorted; the same order as the tile maps'
+// halo, so the tile's own window offsets stay valid), H2 = the neighbour rows
+// of H1 outside tile + H1 (sorted).  Per tile: the list [H1, H2] at a fixed
+// place kPairHL t, a descriptor of kPairDesc int32 (see the kernel), and the
+// SELL entries of the H1 rows in slices of 32 (each row's entries in the
+// mesh's SELL order, window offsets into [tile, H1, H2] as row * 128 and the
+// same FP32 x_pq, so a halo row's b_k is the one its owner computes).
+// Meshes whose tiles exceed the capacities keep the single-stage kernels.
+static int build_pair_maps(decbpm_mesh_t M) {
+    if (M->pairs_ready) return DECBPM_OK;
+    TRY(build_tiles(M));
+    M->pairs_ready = true;
+    M->pairs_ok = false;
+    if (!M->tiles_ok) return DECBPM_OK;
+    const Sell &S = M->S;
+    const Assembly &A = M->A;
+    const int64_t n0 = A.n0;
+    const int nt = int((n0 + kTileRows - 1) / kTileRows);
+    constexpr int spt = kTileRows / kSlice;
+    const double r = M->r();
+    std::vector<int32_t> pdesc(size_t(nt) * kPairDesc, 0), hlist(size_t(nt) * kPairHL, 0);
+    std::vector<uint16_t> lcol2;
+    std::vector<float> x2;
+    std::vector<int32_t> h1, h2;
+    std::unordered_map<int32_t, int32_t> widx;
+    int max_nh1 = 0, max_nh12 = 0, max_he = 0;
+    for (int t = 0; t < nt; ++t) {
+        const int64_t r0 = int64_t(t) * kTileRows, r1 = std::min<int64_t>(r0 + kTileRows, n0);
+        const int64_t s0 = int64_t(t) * spt, s1 = std::min<int64_t>(s0 + spt, S.n_slices);
+        const int64_t e0 = S.slice_ptr[s0], e1 = S.slice_ptr[s1];
+        h1.clear();
+        for (int64_t e = e0; e < e1; ++e)
+            if (S.col[e] < r0 || S.col[e] >= r1) h1.push_back(S.col[e]);
+        std::sort(h1.begin(), h1.end());
+        h1.erase(std::unique(h1.begin(), h1.end()), h1.end());
+        auto in_w1 = [&](int32_t q) { return (q >= r0 && q < r1) || std::binary_search(h1.begin(), h1.end(), q); };
+        h2.clear();
+        for (int32_t q : h1) {
+            const int64_t sq = q >> 5, lq = q & 31;
+            for (int j = 0; j < S.slice_w[sq]; ++j) {
+                const int32_t c = S.col[S.slice_ptr[sq] + int64_t(j) * kSlice + lq];
+                if (!in_w1(c)) h2.push_back(c);
+            }
+        }
+        std::sort(h2.begin(), h2.end());
+        h2.erase(std::unique(h2.begin(), h2.end()), h2.end());
+        const int nh1 = int(h1.size()), nh2 = int(h2.size());
+        if (nh1 > kPairH1 || nh1 + nh2 > kPairHL) return DECBPM_OK;     // capacity: keep single-stage kernels
+        widx.clear();
+        for (int i = 0; i < nh1; ++i) widx[h1[i]] = kTileRows + i;
+        for (int i = 0; i < nh2; ++i) widx[h2[i]] = kTileRows + nh1 + i;
+        auto wpos = [&](int32_t c) -> int32_t {
+            if (c >= r0 && c < r1) return int32_t(c - r0);
+            auto it = widx.find(c);
+            return it == widx.end() ? -1 : it->second;
+        };
+        // H1 rows' SELL entries, slices of 32 halo rows
+        const int he0 = int(lcol2.size());
+        uint32_t hw[4] = {0, 0, 0, 0};
+        const int nhs = (nh1 + kSlice - 1) / kSlice;
+        for (int sl = 0; sl < nhs; ++sl) {
+            int w = 0;
+            for (int i = sl * kSlice; i < std::min(nh1, (sl + 1) * kSlice); ++i) w = std::max(w, int(S.slice_w[h1[i] >> 5]));
+            if (w > 255) return DECBPM_OK;
+            hw[sl] = uint32_t(w);
+            const size_t base = lcol2.size();
+            lcol2.resize(base + size_t(kSlice) * w, 0);
+            x2.resize(base + size_t(kSlice) * w, 0.0f);
+            for (int lane = 0; lane < kSlice; ++lane) {
+                const int i = sl * kSlice + lane;
+                const int32_t self = kTileRows + std::min(i, std::max(nh1 - 1, 0));
+                for (int j = 0; j < w; ++j) {
+                    const size_t o = base + size_t(j) * kSlice + lane;
+                    lcol2[o] = uint16_t(self * 128);
+                    x2[o] = 0.0f;
+                    if (i >= nh1) continue;
+                    const int32_t q = h1[i];
+                    const int64_t sq = q >> 5, lq = q & 31;
+                    if (j >= S.slice_w[sq]) continue;
+                    const int64_t idx = S.slice_ptr[sq] + int64_t(j) * kSlice + lq;
+                    const int32_t pos = wpos(S.col[idx]);
+                    if (pos < 0) return fail(DECBPM_ERR_CUDA, "internal: halo neighbour outside the pair window");
+                    lcol2[o] = uint16_t(pos * 128);
+                    x2[o] = float(S.w[idx] / (r * A.m[A.perm[q]]));
+                }
+            }
+        }
+        const int hne = int(lcol2.size()) - he0;
+        int32_t *d = &pdesc[size_t(t) * kPairDesc];
+        d[0] = int32_t(e0);
+        d[1] = int32_t(e1 - e0);
+        d[2] = int32_t(nh1 | (nh2 << 16));
+        d[3] = he0;
+        uint32_t es[4] = {0, 0, 0, 0}, w[4] = {0, 0, 0, 0};
+        for (int64_t sl = s0; sl < s1; ++sl) {
+            es[sl - s0] = uint32_t(S.slice_ptr[sl] - e0);
+            w[sl - s0] = uint32_t(S.slice_w[sl]);
+        }
+        d[4] = int32_t(es[0] | es[1] << 16);
+        d[5] = int32_t(es[2] | es[3] << 16);
+        d[6] = int32_t(w[0] | w[1] << 8 | w[2] << 16 | w[3] << 24);
+        d[7] = int32_t(hw[0] | hw[1] << 8 | hw[2] << 16 | hw[3] << 24);
+        d[8] = hne;
+        for (int i = 0; i < nh1; ++i) hlist[size_t(t) * kPairHL + i] = h1[i];
+        for (int i = 0; i < nh2; ++i) hlist[size_t(t) * kPairHL + nh1 + i] = h2[i];
+        max_nh1 = std::max(max_nh1, nh1);
+        max_nh12 = std::max(max_nh12, nh1 + nh2);
+        max_he = std::max(max_he, hne);
+    }
+    if (lcol2.empty()) { lcol2.push_back(0); x2.push_back(0.0f); }
+    TRY(M->mem.upload(&M->pdesc, pdesc));
+    TRY(M->mem.upload(&M->hlist, hlist));
+    TRY(M->mem.upload(&M->lcol2, lcol2));
+    TRY(M->mem.upload(&M->x2, x2));
+    M->max_nh1 = max_nh1;
+    M->max_nh12 = max_nh12;
+    M->max_hentries = max_he;
+    M->pairs_ok = true;
     return DECBPM_OK;
 }
 
@@ -292,6 +421,18 @@ struct decbpm_plan_s {
     std::vector<int> tile_begin;
     int32_t *active_tiles = nullptr;
     int active_tiles_cap = 0, total_tiles = 0;
+    // stage-pair march (complex64, 16 fields): a fourth field buffer per mesh,
+    // the slot layout, per-pass active tiles and per-stage coefficients
+    bool pair_mode = false;
+    int pair_slots = 0, pair_slot_bytes = 0, pair_grid = 0, n_passes = 0;
+    int p_off_h = 0, p_off_psi = 0, p_off_lcol = 0, p_off_x = 0, p_off_lcol2 = 0, p_off_x2 = 0, p_off_hdr = 0;
+    int p_slot_entries = 0, p_slot_hentries = 0, p_w2 = 0, p_w1 = 0;
+    std::vector<void *> b3;
+    int32_t *active_passes = nullptr;
+    int active_passes_cap = 0;
+    void *pcoef = nullptr;
+    int pcoef_cap = 0;
+    int tune_pair = -1;                          // 1: FUSED runs the stage-pair kernel; 0: not; -1: default
     // graphs: key -> exec
     std::map<std::tuple<double, int64_t, int32_t, int32_t, double, int32_t>, cudaGraphExec_t> graphs;
     bool graphs_ok = true;
@@ -384,6 +525,58 @@ static int setup_tiles(decbpm_plan_t P) {
     return DECBPM_OK;
 }
 
+// Shared-memory ring of the stage-pair march: two slots of the largest pair
+// window of the plan's meshes (see march_pair_kernel).  Plans whose slots do
+// not fit twice keep the single-stage kernels.
+static int setup_pairs(decbpm_plan_t P) {
+    P->pair_mode = false;
+    if (!P->tile_mode) return DECBPM_OK;
+    int max_nh1 = 0, max_nh12 = 0, max_entries = 0, max_he = 0;
+    for (decbpm_mesh_t m : P->meshes) {
+        TRY(build_pair_maps(m));
+        if (!m->pairs_ok) return DECBPM_OK;
+        max_nh1 = std::max(max_nh1, m->max_nh1);
+        max_nh12 = std::max(max_nh12, m->max_nh12);
+        max_entries = std::max(max_entries, m->max_entries);
+        max_he = std::max(max_he, m->max_hentries);
+    }
+    auto up = [](int x) { return (x + 127) / 128 * 128; };
+    const int row = 128;
+    P->p_w2 = kTileRows + max_nh12;
+    P->p_w1 = kTileRows + max_nh1;
+    P->p_off_h = up(P->p_w2 * row);
+    P->p_off_psi = P->p_off_h + up(P->p_w1 * row);
+    P->p_off_lcol = P->p_off_psi + kTileRows * row;
+    P->p_off_x = P->p_off_lcol + up(max_entries * 2);
+    P->p_off_lcol2 = P->p_off_x + up(max_entries * 4);
+    P->p_off_x2 = P->p_off_lcol2 + up(std::max(max_he, 1) * 2);
+    P->p_off_hdr = P->p_off_x2 + up(std::max(max_he, 1) * 4);
+    P->p_slot_entries = max_entries;
+    P->p_slot_hentries = max_he;
+    P->pair_slot_bytes = P->p_off_hdr + 128;
+    cudaFuncAttributes fa{};
+    CK(cudaFuncGetAttributes(&fa, (const void *)march_pair_kernel));
+    int optin = 0;
+    CK(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, P->device));
+    const int avail = optin - int(fa.sharedSizeBytes);
+    P->pair_slots = avail >= 3 * P->pair_slot_bytes ? 3 : avail >= 2 * P->pair_slot_bytes ? 2 : 0;
+    if (P->pair_slots == 0) return DECBPM_OK;
+    CK(cudaFuncSetAttribute((const void *)march_pair_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, avail));
+    int per_sm = 0;
+    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void *)march_pair_kernel, kTileThreads,
+                                                     P->pair_slots * P->pair_slot_bytes));
+    if (per_sm < 1) return DECBPM_OK;
+    P->pair_grid = P->num_sms * per_sm;
+    const size_t cs = csize(P->precision);
+    for (size_t i = 0; i < P->meshes.size(); ++i) {
+        char *t;
+        TRY(P->mem.alloc(&t, size_t(P->meshes[i]->A.n0) * P->bpad * cs));
+        P->b3.push_back(t);
+    }
+    P->pair_mode = true;
+    return DECBPM_OK;
+}
+
 static int plan_create_impl(const decbpm_mesh_t *meshes, int32_t n, const int32_t *fields, int32_t precision,
                             decbpm_plan_t *out) {
     if (!out) return fail(DECBPM_ERR_INVALID_ARG, "out is NULL");
@@ -442,6 +635,7 @@ static int plan_create_impl(const decbpm_mesh_t *meshes, int32_t n, const int32_
     P->max_per_sm = std::min(per_sm, 4);
     P->grid = P->num_sms * P->max_per_sm;
     TRY(setup_tiles(P.get()));
+    TRY(setup_pairs(P.get()));
     *out = P.release();
     return DECBPM_OK;
 }
@@ -581,6 +775,64 @@ static int plan_configure(decbpm_plan_t P, double dz, double tol) {
         }
         off += Mi;
     }
+    if (P->pair_mode) {
+        // passes of a step: pairs (S-1, S-2), (S-3, S-4), ... down to stage 1, a
+        // single pass for stage 1 when S - 1 is odd, the final stage 0; a mesh
+        // takes part in a pass from its top stage M - 1 on (tiles: a prefix, the
+        // meshes being sorted by degree)
+        const int n_pairs = (P->S - 1) / 2;
+        P->n_passes = n_pairs + ((P->S - 1) & 1) + 1;
+        std::vector<int32_t> ap(P->n_passes, 0);
+        for (int ps = 0; ps < P->n_passes; ++ps) {
+            const int lowest = ps < n_pairs ? P->S - 2 - 2 * ps : (ps == n_pairs && ((P->S - 1) & 1)) ? 1 : 0;
+            for (int j = 0; j < n; ++j)
+                if (ch[P->order[j]].M > lowest) ap[ps] += P->meshes[P->order[j]]->n_tiles;
+        }
+        if (P->n_passes > P->active_passes_cap) {
+            TRY(P->mem.alloc(&P->active_passes, P->n_passes));
+            P->active_passes_cap = P->n_passes;
+        }
+        CK(cudaMemcpy(P->active_passes, ap.data(), sizeof(int32_t) * P->n_passes, cudaMemcpyHostToDevice));
+        if (sizeof(R) == 4) {
+            if (total_coef > P->pcoef_cap) {
+                char *t;
+                TRY(P->mem.alloc(&t, sizeof(PairCoef) * total_coef));
+                P->pcoef = t;
+                P->pcoef_cap = total_coef;
+            }
+            std::vector<PairCoef> pc(total_coef);
+            int o = 0;
+            for (int j = 0; j < n; ++j) {
+                const int Mi = ch[P->order[j]].M;
+                for (int k = 0; k < Mi; ++k) {
+                    const StageCoef<R> &sc = coef[o + k];
+                    PairCoef c{};
+                    c.alpha = make_float2(float(sc.alpha.x), float(sc.alpha.y));
+                    c.beta = make_float2(float(sc.beta.x), float(sc.beta.y));
+                    c.alpha_lo = make_float2(float(sc.alpha_lo.x), float(sc.alpha_lo.y));
+                    c.flags = sc.flags;
+                    if (k > 0) {
+                        const StageCoef<R> &nx = coef[o + k - 1];
+                        c.alpha_next = make_float2(float(nx.alpha.x), float(nx.alpha.y));
+                        if (nx.flags & kHasH) c.flags |= kNextHasH;
+                        if (nx.flags & kFinal) c.flags |= kNextFinal;
+                    }
+                    pc[o + k] = c;
+                }
+                views[j].pcoef = reinterpret_cast<const PairCoef *>(P->pcoef) + o;
+                o += Mi;
+            }
+            CK(cudaMemcpy(P->pcoef, pc.data(), sizeof(PairCoef) * total_coef, cudaMemcpyHostToDevice));
+        }
+        for (int j = 0; j < n; ++j) {
+            const int i = P->order[j];
+            views[j].b3 = (C *)P->b3[i];
+            views[j].pdesc = P->meshes[i]->pdesc;
+            views[j].hlist = P->meshes[i]->hlist;
+            views[j].lcol2 = P->meshes[i]->lcol2;
+            views[j].x2 = P->meshes[i]->x2;
+        }
+    }
     if (P->tile_mode) CK(cudaMemcpy(P->active_tiles, active_t.data(), sizeof(int32_t) * P->S, cudaMemcpyHostToDevice));
     CK(cudaMemcpy(P->coef, coef.data(), sizeof(StageCoef<R>) * total_coef, cudaMemcpyHostToDevice));
     CK(cudaMemcpy(P->active, active.data(), sizeof(int32_t) * P->S, cudaMemcpyHostToDevice));
@@ -624,8 +876,35 @@ static int launch_march(decbpm_plan_t P, cudaStream_t s, int n_steps, int kerr_m
     void *args[] = {&mp};
     const void *fn = march_ptr_for<R>(P->bpad);
     if constexpr (sizeof(R) == 4) {
-        if (P->tile_mode && variant == DECBPM_VARIANT_FUSED && !P->tune_rows) {
-            const int slots = P->tune_slots > 0 ? std::min(P->tune_slots, P->n_slots) : P->n_slots;
+        const bool pairs = P->pair_mode && (variant == DECBPM_VARIANT_PAIRS ||
+                                            (variant == DECBPM_VARIANT_FUSED && !P->tune_rows && P->tune_pair == 1));
+        if (pairs) {
+            const int slots = (P->tune_pair == 1 && P->tune_slots > 0) ? std::min(P->tune_slots, P->pair_slots)
+                                                                       : P->pair_slots;
+            mp.active_tiles = P->active_passes;
+            mp.n_passes = P->n_passes;
+            mp.n_slots = slots;
+            mp.slot_bytes = P->pair_slot_bytes;
+            mp.off_psi = P->p_off_psi;
+            mp.off_h = P->p_off_h;
+            mp.off_lcol = P->p_off_lcol;
+            mp.off_x = P->p_off_x;
+            mp.off_lcol2 = P->p_off_lcol2;
+            mp.off_x2 = P->p_off_x2;
+            mp.off_hdr = P->p_off_hdr;
+            mp.slot_entries = P->p_slot_entries;
+            mp.slot_hentries = P->p_slot_hentries;
+            mp.w2_rows = P->p_w2;
+            mp.w1_rows = P->p_w1;
+            cfg.gridDim = dim3(P->pair_grid);
+            cfg.blockDim = dim3(kTileThreads);
+            cfg.dynamicSmemBytes = size_t(slots) * P->pair_slot_bytes;
+            void *pargs[] = {&mp};
+            CK(cudaLaunchKernelExC(&cfg, (const void *)march_pair_kernel, pargs));
+            return DECBPM_OK;
+        }
+        if (P->tile_mode && (variant == DECBPM_VARIANT_FUSED || variant == DECBPM_VARIANT_PAIRS) && !P->tune_rows) {
+            const int slots = (P->tune_pair != 1 && P->tune_slots > 0) ? std::min(P->tune_slots, P->n_slots) : P->n_slots;
             mp.active_tiles = P->active_tiles;
             mp.n_slots = slots;
             mp.slot_bytes = P->slot_bytes;
@@ -702,7 +981,8 @@ static int check_params(const decbpm_params *p) {
     if (p->precision != DECBPM_C64 && p->precision != DECBPM_C128) return fail(DECBPM_ERR_INVALID_ARG, "bad precision");
     if (p->kerr_mode != DECBPM_KERR_LUMPED && p->kerr_mode != DECBPM_KERR_ELEMENT) return fail(DECBPM_ERR_INVALID_ARG, "bad kerr_mode");
     if (p->diag_every < 0) return fail(DECBPM_ERR_INVALID_ARG, "diag_every < 0");
-    if (p->variant != DECBPM_VARIANT_FUSED && p->variant != DECBPM_VARIANT_PLAIN && p->variant != DECBPM_VARIANT_ROWS)
+    if (p->variant != DECBPM_VARIANT_FUSED && p->variant != DECBPM_VARIANT_PLAIN && p->variant != DECBPM_VARIANT_ROWS &&
+        p->variant != DECBPM_VARIANT_PAIRS)
         return fail(DECBPM_ERR_INVALID_ARG, "bad variant");
     if (!(p->cheb_tol >= 0)) return fail(DECBPM_ERR_INVALID_ARG, "cheb_tol < 0");
     return DECBPM_OK;
@@ -1339,14 +1619,17 @@ static int soliton_impl(decbpm_mesh_t mesh, decbpm_plan_t P, const decbpm_solito
 // Launch shapes of the FUSED march picked by timing: for complex64 plans that
 // can run the tile-staged kernel, {tile kernel with 3 or 2 ring slots, row
 // kernel with 1..max CTAs per SM} x {reverse walk on odd stages, forward
-// only}; otherwise the row kernel's CTAs per SM x walk order.  Every
-// candidate performs the same arithmetic per row (results are bitwise
-// identical), so only time decides.  Each candidate runs one untimed launch
+// only}; otherwise the row kernel's CTAs per SM x walk order; plans the
+// stage-pair kernel can run also time it with 3 or 2 slots.  The single-stage
+// candidates perform the same arithmetic per row (bitwise identical
+// results); the stage-pair kernel stores a_k psi - b_{k+2} in place of b_{k+2}
+// and so rounds differently (same FP32 accuracy against the oracle), so a plan
+// that picks it differs from the others at the level of FP32 rounding.  Each candidate runs one untimed launch
 // and then the best of two timed launches of `trial_steps` steps on the
 // plan's internal buffers (zeroed first: their contents are scratch between
 // calls).  The winner is cached for the process, keyed by the meshes'
 // content fingerprints, the field counts, the precision, dz and kerr_mode.
-struct TuneChoice { int rows, per_sm, slots, forward; double ms; };
+struct TuneChoice { int rows, per_sm, slots, forward, pair; double ms; };
 static std::mutex g_tune_mutex;
 static std::map<std::string, TuneChoice> g_tune_cache;
 
@@ -1375,6 +1658,7 @@ static std::string tune_key(decbpm_plan_t P, double dz, int kerr_mode) {
 
 static void apply_choice(decbpm_plan_t P, const TuneChoice &c) {
     P->tune_rows = c.rows;
+    P->tune_pair = c.pair;
     P->tune_slots = c.slots;
     P->forward_walk = c.forward;
     P->grid = P->num_sms * c.per_sm;
@@ -1385,7 +1669,7 @@ static void apply_choice(decbpm_plan_t P, const TuneChoice &c) {
 
 static decbpm_tune_result tune_result(const TuneChoice &c, int trial_steps, int n_cand, int from_cache) {
     decbpm_tune_result r{};
-    r.variant = c.rows ? DECBPM_VARIANT_ROWS : DECBPM_VARIANT_FUSED;
+    r.variant = c.rows ? DECBPM_VARIANT_ROWS : c.pair ? DECBPM_VARIANT_PAIRS : DECBPM_VARIANT_FUSED;
     r.ctas_per_sm = c.rows ? c.per_sm : 1;
     r.tile_slots = c.slots;
     r.forward_walk = c.forward;
@@ -1416,12 +1700,15 @@ static int autotune_impl(decbpm_plan_t P, double dz, int kerr_mode, int trial_st
         CK(cudaMemsetAsync(P->b0[i], 0, bytes, s));
         CK(cudaMemsetAsync(P->b1[i], 0, bytes, s));
         CK(cudaMemsetAsync(P->b2[i], 0, bytes, s));
+        if (P->pair_mode) CK(cudaMemsetAsync(P->b3[i], 0, bytes, s));
     }
     std::vector<TuneChoice> cand;
     for (int fw = 0; fw <= 1; ++fw) {
+        if (P->pair_mode)
+            for (int sl = P->pair_slots; sl >= 2; --sl) cand.push_back({0, 1, sl, fw, 1, 0.0});
         if (P->tile_mode)
-            for (int sl = P->n_slots; sl >= 2; --sl) cand.push_back({0, P->max_per_sm, sl, fw, 0.0});
-        for (int ps = 1; ps <= P->max_per_sm; ++ps) cand.push_back({1, ps, 0, fw, 0.0});
+            for (int sl = P->n_slots; sl >= 2; --sl) cand.push_back({0, P->max_per_sm, sl, fw, 0, 0.0});
+        for (int ps = 1; ps <= P->max_per_sm; ++ps) cand.push_back({1, ps, 0, fw, 0, 0.0});
     }
     cudaEvent_t e0, e1;
     CK(cudaEventCreate(&e0));
@@ -1988,6 +2275,14 @@ int decbpm_plan_get_config(decbpm_plan_t P, decbpm_plan_config *cfg) {
     cfg->tile_slots_used =
         (P->tile_mode && !P->tune_rows) ? (P->tune_slots > 0 ? std::min(P->tune_slots, P->n_slots) : P->n_slots) : 0;
     cfg->forward_walk = P->forward_walk;
+    if (cfg->fused_kernel == 1 && P->pair_mode && P->tune_pair == 1) {
+        cfg->fused_kernel = 2;
+        cfg->tile_slots_used = P->tune_slots > 0 ? std::min(P->tune_slots, P->pair_slots) : P->pair_slots;
+    }
+    cfg->pair_slots = P->pair_mode ? P->pair_slots : 0;
+    cfg->pair_slot_bytes = P->pair_mode ? P->pair_slot_bytes : 0;
+    cfg->pair_grid = P->pair_mode ? P->pair_grid : 0;
+    cfg->passes = P->pair_mode ? P->n_passes : 0;
     return DECBPM_OK;
 }
 

@@ -198,6 +198,15 @@ template <typename R> struct MeshView {
     const int32_t *halo_ovf;  // halo rows beyond the first 96
     int32_t tile_begin;      // first plan-global tile of this mesh
     int32_t pad_;
+    // stage-pair march (complex64, 16 fields): a fourth field buffer, per tile
+    // the depth-two halo list and descriptor, the halo rows' SELL entries, and
+    // the per-stage coefficients of the pair passes
+    typename CT<R>::c2 *b3;
+    const int32_t *pdesc;     // per tile kPairDesc int32 (see PairDesc)
+    const int32_t *hlist;     // per tile kPairHL rows: H1 (neighbours of the tile), then H2 (of H1)
+    const uint16_t *lcol2;    // halo rows' SELL entries: window offset (row * 128) in [tile, H1, H2]
+    const float *x2;          //   and x_pq
+    const void *pcoef;        // PairCoef[M]
 };
 
 template <typename R> struct MarchParams {
@@ -219,6 +228,11 @@ template <typename R> struct MarchParams {
     int32_t n_slots, slot_bytes; // shared-memory ring of tile windows
     int32_t off_psi, off_h, off_lcol, off_x, off_hdr;   // areas of a slot (the neighbour window starts at 0)
     int32_t slot_entries;        // SELL entries a slot holds
+    // stage-pair march only (off_h: the r / b_k window; off_hdr: descriptor and slot meta)
+    int32_t off_lcol2, off_x2;   // the halo rows' SELL entries
+    int32_t slot_hentries;       // halo SELL entries a slot holds
+    int32_t n_passes;            // passes per step
+    int32_t w2_rows, w1_rows;    // window capacities (rows) of g (tile + H1 + H2) and r (tile + H1)
 };
 
 // ------------------------------------------------------------ grid barrier
@@ -1137,6 +1151,505 @@ __global__ void __launch_bounds__(kTileThreads, 1) march_tile_kernel(MarchParams
         cp_async_wait<0>();           // no look-ahead copy may land after the CTA exits
     } else {
         tile_march_role<false>(0, P, s_ring, s_begin, s_tbeg, s_view, s_coef, s_full, s_empty, s_look);
+    }
+}
+
+// ------------------------------------------------------------ stage-pair march
+// Two Clenshaw stages per grid-wide pass (complex64, 16 fields).  For a tile
+// R0 of 128 rows let H1 be its neighbour rows outside it and H2 the neighbour
+// rows of H1 outside R0 + H1.  Pass (k, k-1) fills one slot with
+//   g window  [R0, H1, H2] rows of b_{k+1} (or psi at a mesh's top stage),
+//   r window  [R0, H1] rows of r_k = a_k psi - b_{k+2} (the previous pass
+//             stored this combination instead of b_{k+2}),
+//   psi       R0 rows,
+// the tile's SELL entries and H1's SELL entries (window offsets, x_pq), then
+//   phase 1: b_k = r_k + beta_k (X g) on R0 and H1 (into the r window, in place),
+//   phase 2: b_{k-1} = a_{k-1} psi - b_{k+1} + beta_{k-1} (X b_k) on R0,
+// and stores b_{k-1} and r_{k-2} = a_{k-2} psi - b_k for the next pass.  The
+// halo rows' b_k are computed again by every tile that needs them (about half
+// a tile of extra rows), in exchange for half the grid barriers and, per two
+// stages, 3 row reads and 2 row writes of HBM instead of 6 and 2.  Stages
+// S-1 .. 1 run in pairs from the top (a single pass for stage 1 when S - 1 is
+// odd), stage 0 always alone, because its double-float combination needs psi
+// and b_2 separately.  A mesh of a plan with degree M < S joins at the pass
+// holding its top stage M - 1 (in phase 2 when that is the pass's second
+// stage).  Two sets {G = b, R = r} of field buffers alternate between passes.
+constexpr int kPairHL = 256;            // H1 + H2 rows per tile at most
+constexpr int kPairH1 = 128;            // H1 rows per tile at most (four SELL slices)
+constexpr int kPairDesc = 12;           // int32 per tile descriptor
+constexpr int kPairLook = 2;            // look-ahead entries per copy warp
+constexpr int kPairLookInts = kPairHL + 16;   // list, descriptor, tile index, pad
+enum : int { kNextHasH = 8, kNextFinal = 16 };
+// per stage j: out = r + beta (X g) with r as above; alpha_next = a_{j-1} for the
+// r of the next stage, whose flags kNextHasH / kNextFinal also live here
+struct PairCoef {
+    float2 alpha, beta, alpha_lo, alpha_next;
+    int flags, pad;
+};
+// Tile descriptor (kPairDesc int32): e0, ne, nh1 | nh2 << 16, he0,
+// es0 | es1 << 16, es2 | es3 << 16, w0..w3 (8 bit each), hw0..hw3 (halo slice
+// widths), hne, 0, 0, 0.  Slot header: the descriptor, then mesh index and
+// local tile index written by the copy warp.
+constexpr int kPairHdrBytes = 64;
+
+__device__ __forceinline__ void sts_c2(uint32_t addr, cf2 a, cf2 b) {
+    asm volatile("st.shared.v2.b64 [%0], {%1, %2};" ::"r"(addr), "l"(a), "l"(b) : "memory");
+}
+__device__ __forceinline__ void sts_i32(uint32_t addr, int v) {
+    asm volatile("st.shared.s32 [%0], %1;" ::"r"(addr), "r"(v) : "memory");
+}
+__device__ __forceinline__ int lds_i32(uint32_t addr) {
+    int v;
+    asm volatile("ld.shared.s32 %0, [%1];" : "=r"(v) : "r"(addr));
+    return v;
+}
+// barriers of the 16 compute warps only (the copy warps never take them)
+__device__ __forceinline__ void compute_warps_sync() { asm volatile("bar.sync 1, 512;" ::: "memory"); }
+// AND of v over the 16 compute warps (a barrier as well)
+__device__ __forceinline__ bool compute_warps_and(bool v) {
+    unsigned r;
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\t"
+        "setp.ne.u32 p, %1, 0;\n\t"
+        "bar.red.and.pred q, 2, 512, p;\n\t"
+        "selp.u32 %0, 1, 0, q;\n\t}"
+        : "=r"(r)
+        : "r"(unsigned(v))
+        : "memory");
+    return r != 0;
+}
+
+// Pass p of a step: a pair (k, k-1), the single stage 1, or the final stage 0.
+struct PassInfo { int k, type; };            // type 0: pair, 1: single, 2: final
+__device__ __forceinline__ PassInfo pass_info(int S, int p) {
+    const int n_pairs = (S - 1) / 2;
+    if (p < n_pairs) return PassInfo{S - 1 - 2 * p, 0};
+    if (((S - 1) & 1) && p == n_pairs) return PassInfo{1, 1};
+    return PassInfo{0, 2};
+}
+__device__ __forceinline__ TileRange pair_tile_range(const MarchParams<float> &P, int p) {
+    const int n_act = __ldg(P.active_tiles + p);
+    const int lo = int((long long)n_act * blockIdx.x / gridDim.x);
+    const int hi = int((long long)n_act * (blockIdx.x + 1) / gridDim.x);
+    return TileRange{lo, hi - lo, P.forward_walk == 0 && (p & 1)};
+}
+__device__ __forceinline__ int pair_look_next(LookCursor &c, const MarchParams<float> &P) {
+    for (int guard = 0; guard <= P.n_passes; ++guard) {
+        if (c.i < c.R.n) return c.R.at(c.i++);
+        c.s = c.s + 1 < P.n_passes ? c.s + 1 : 0;
+        c.R = pair_tile_range(P, c.s);
+        c.i = 0;
+    }
+    return -1;
+}
+__device__ __forceinline__ int pair_look_next_n(LookCursor &c, const MarchParams<float> &P, int n) {
+    int t = -1;
+    for (int i = 0; i < n; ++i) t = pair_look_next(c, P);
+    return t;
+}
+// Copy warp: request the look-ahead entry of tile t (halo list and descriptor; one commit group).
+__device__ __forceinline__ void pair_look_issue(int *entry, int t, const MeshView<float> *sv, const int32_t *s_tbeg,
+                                                int n_meshes) {
+    const int lane = threadIdx.x & 31;
+    if (t >= 0) {
+        const int mi = mesh_of_tile(s_tbeg, n_meshes, t);
+        const int tl = t - s_tbeg[mi];
+        const int32_t *hl = sv[mi].hlist + (size_t)tl * kPairHL;
+        cp_async16(smem_u32(entry + 4 * lane), hl + 4 * lane);                 // rows 0..127
+        cp_async16(smem_u32(entry + 128 + 4 * lane), hl + 128 + 4 * lane);     // rows 128..255
+        if (lane < 3) cp_async16(smem_u32(entry + kPairHL + 4 * lane), sv[mi].pdesc + (size_t)tl * kPairDesc + 4 * lane);
+    }
+    if (lane == 31) entry[kPairHL + kPairDesc] = t;
+    cp_async_commit();
+}
+
+// The role of mesh m in pass (k, type): the first stage it runs (fk) and
+// whether it runs phase 1 on the halo as well.
+struct PairRole { int fk; bool two; };
+__device__ __forceinline__ PairRole pair_role(int M, int k, int type) {
+    if (type == 0) return k < M ? PairRole{k, true} : PairRole{k - 1, false};
+    return PairRole{k, false};
+}
+
+// Copy warp: fill `slot` for the tile of look-ahead `entry` in pass p.
+__device__ __forceinline__ void pair_fill(const int *entry, const MeshView<float> *sv, const int32_t *s_tbeg,
+                                          int n_meshes, int p, PassInfo pi, char *slot, uint32_t bar,
+                                          const MarchParams<float> &P) {
+    const int lane = threadIdx.x & 31;
+    const int t = entry[kPairHL + kPairDesc];
+    const int *dsc = entry + kPairHL;
+    const int mi = mesh_of_tile(s_tbeg, n_meshes, t);
+    const MeshView<float> &m = sv[mi];
+    const int tl = t - s_tbeg[mi];
+    const int r0 = tl * kTileRows, nrows = min(kTileRows, m.n0 - r0);
+    const int e0 = dsc[0], ne = dsc[1], nh1 = dsc[2] & 0xffff, nh2 = dsc[2] >> 16, he0 = dsc[3], hne = dsc[8];
+    const PairRole role = pair_role(m.M, pi.k, pi.type);
+    const PairCoef pc = reinterpret_cast<const PairCoef *>(m.pcoef)[role.fk];
+    const bool gis = (pc.flags & kGisPsi) != 0;
+    const float2 *Gin = (p & 1) ? m.b[1] : m.b[0];
+    const float2 *Rin = (p & 1) ? m.b3 : m.b[2];
+    const float2 *g = gis ? m.psi : Gin;
+    // r rows: [R0, H1] in phase 1 of a pair; R0 for a single pass; R0 for the
+    // final pass when it has an h term (b_2, stored plain); none at a top stage
+    const bool need_r = !gis && (pi.type != 2 || (pc.flags & kHasH));
+    const bool r_halo = need_r && role.two;
+    const int ng_halo = role.two ? nh1 + nh2 : nh1;       // g rows beyond the tile
+    const uint32_t base = smem_u32(slot);
+    // scattered halo rows, 16-byte cp.async, 8 lanes per 128-byte row
+    for (int u = lane >> 3; u < ng_halo; u += 4) {
+        const int q = entry[u];
+        cp_async16(base + unsigned(kTileRows + u) * 128u + 16u * (lane & 7), g + (size_t)q * 16 + 2 * (lane & 7));
+    }
+    if (r_halo)
+        for (int u = lane >> 3; u < nh1; u += 4) {
+            const int q = entry[u];
+            cp_async16(base + unsigned(P.off_h) + unsigned(kTileRows + u) * 128u + 16u * (lane & 7),
+                       Rin + (size_t)q * 16 + 2 * (lane & 7));
+        }
+    cp_async_arrive(bar);
+    const unsigned row_bytes = unsigned(nrows) * 128u;
+    const unsigned total = row_bytes * (1u + (need_r ? 1u : 0u) + (gis ? 0u : 1u)) + unsigned(ne) * 6u +
+                           (role.two ? unsigned(hne) * 6u : 0u);
+    __syncwarp();
+    if (lane == 0) {
+        const uint32_t hdr = base + P.off_hdr;
+        for (int i = 0; i < kPairDesc; ++i) sts_i32(hdr + 4 * i, dsc[i]);
+        sts_i32(hdr + 4 * kPairDesc, mi);
+        sts_i32(hdr + 4 * kPairDesc + 4, tl);
+        mbar_arrive_expect_tx(bar, total);
+    }
+    __syncwarp();
+    if (lane == 0) bulk_g2s(base, g + (size_t)r0 * 16, row_bytes, bar);
+    if (lane == 1 && need_r) bulk_g2s(base + P.off_h, Rin + (size_t)r0 * 16, row_bytes, bar);
+    if (lane == 2 && !gis) bulk_g2s(base + P.off_psi, m.psi + (size_t)r0 * 16, row_bytes, bar);
+    if (lane == 3 && ne > 0) bulk_g2s(base + P.off_lcol, m.lcol + e0, unsigned(ne) * 2u, bar);
+    if (lane == 4 && ne > 0) bulk_g2s(base + P.off_x, m.xval + e0, unsigned(ne) * 4u, bar);
+    if (lane == 5 && role.two && hne > 0) bulk_g2s(base + P.off_lcol2, m.lcol2 + he0, unsigned(hne) * 2u, bar);
+    if (lane == 6 && role.two && hne > 0) bulk_g2s(base + P.off_x2, m.x2 + he0, unsigned(hne) * 4u, bar);
+}
+
+// acc = sum_j x_j (g_p - g_q) over `width` SELL entries at lc (offsets) / xs (x_pq),
+// entry j at lc + 64 j and xs + 128 j; g rows in the window at g1 / g2 (this lane's chunks)
+__device__ __forceinline__ void pair_gather(uint32_t g1, uint32_t g2, uint32_t lc, uint32_t xs, int width,
+                                            const cf2 gp[4], cf2 acc[4]) {
+#pragma unroll
+    for (int f = 0; f < 4; ++f) acc[f] = 0ull;
+    int j = 0;
+    for (; j + 4 <= width; j += 4) {
+        cf2 gq[4][4], xv[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const uint32_t off = lds_u16(lc + 64 * (j + u));
+            const float x = lds_f32(xs + 128 * (j + u));
+            xv[u] = f2_pack(x, x);
+            lds_c2(g1 + off, gq[u][0], gq[u][1]);
+            lds_c2(g2 + off, gq[u][2], gq[u][3]);
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int f = 0; f < 4; ++f) acc[f] = f2_fma(xv[u], f2_sub(gp[f], gq[u][f]), acc[f]);
+    }
+    for (; j < width; ++j) {
+        cf2 gq[4];
+        const uint32_t off = lds_u16(lc + 64 * j);
+        const float x = lds_f32(xs + 128 * j);
+        const cf2 xv = f2_pack(x, x);
+        lds_c2(g1 + off, gq[0], gq[1]);
+        lds_c2(g2 + off, gq[2], gq[3]);
+#pragma unroll
+        for (int f = 0; f < 4; ++f) acc[f] = f2_fma(xv, f2_sub(gp[f], gq[f]), acc[f]);
+    }
+}
+// entry offsets of row lr (0..127) of a four-slice block: first entry and width
+__device__ __forceinline__ void slice_entry(int lr, int es01, int es23, int widths, int &es, int &width) {
+    const int sl = lr >> 5;
+    es = ((sl < 2 ? es01 : es23) >> (16 * (sl & 1)) & 0xffff) + (lr & 31);
+    width = (widths >> (8 * sl)) & 0xff;
+}
+
+// Compute warps: the stages of pass p on the tile in `slot`.
+__device__ __forceinline__ void pair_compute(const MeshView<float> *sv, int p, PassInfo pi, const char *slot,
+                                             float h_post, int kerr_mode, const MarchParams<float> &P) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint32_t base = smem_u32(slot);
+    const uint32_t hdr = base + P.off_hdr;
+    const int4 d0 = lds_i4(hdr), d1 = lds_i4(hdr + 16), d2 = lds_i4(hdr + 32);
+    const int mi = lds_i32(hdr + 4 * kPairDesc), tl = lds_i32(hdr + 4 * kPairDesc + 4);
+    const int nh1 = d0.z & 0xffff, hne = d2.x;
+    const MeshView<float> &m = sv[mi];
+    const PairRole role = pair_role(m.M, pi.k, pi.type);
+    const PairCoef *pcs = reinterpret_cast<const PairCoef *>(m.pcoef);
+    const int c1 = (lane & 3) + 4 * ((lane >> 2) & 1), c2 = c1 ^ 4;
+    const uint32_t gw = base, rw = base + P.off_h, pw = base + P.off_psi;
+    const uint32_t g1 = gw + 16 * c1, g2 = gw + 16 * c2;
+    float2 *Gout = (p & 1) ? m.b[0] : m.b[1];
+    float2 *Rout = (p & 1) ? m.b[2] : m.b3;
+    const int lr = warp * 8 + (lane >> 2);
+    const int row = tl * kTileRows + lr;
+    const bool valid = row < m.n0;
+    int es, width;
+    slice_entry(lr, d1.x, d1.y, d1.z, es, width);
+    bool valid_row = valid;
+    if (valid && width > 0 && es + 32 * (width - 1) >= P.slot_entries) {   // cannot happen with consistent maps
+        atomicCAS(P.status, 0, -8);                 // DECBPM_ERR_DEVICE_CHECK; the row is skipped (no early
+        valid_row = false;                          // return: every compute warp must reach the phase barrier)
+    }
+    const uint32_t lc = base + P.off_lcol + 2 * es, xs = base + P.off_x + 4 * es;
+    const PairCoef c_first = pcs[role.fk];
+    const bool gis1 = (c_first.flags & kGisPsi) != 0;
+    if (role.two) {
+        // ---- phase 1: b_k on R0 (round A) and on H1 (round B), into the r window
+        const cf2 arr = f2_pack(c_first.alpha.x, c_first.alpha.x), ani = f2_pack(-c_first.alpha.y, c_first.alpha.y);
+        const cf2 brr = f2_pack(c_first.beta.x, c_first.beta.x), bni = f2_pack(-c_first.beta.y, c_first.beta.y);
+        for (int round = 0; round < 2; ++round) {
+            int wr, e1, wd;
+            uint32_t l1, x1;
+            bool ok;
+            if (round == 0) {
+                wr = lr; ok = valid_row; l1 = lc; x1 = xs; wd = width;
+            } else {
+                wr = kTileRows + lr; ok = lr < nh1;
+                slice_entry(lr, 0, 0, d1.w, e1, wd);
+                // halo slices are contiguous: slice s starts at 32 * sum_{s' < s} w_s'
+                int pre = 0;
+                for (int s2 = 0; s2 < (lr >> 5); ++s2) pre += (d1.w >> (8 * s2)) & 0xff;
+                e1 = 32 * pre + (lr & 31);
+                if (ok && wd > 0 && e1 + 32 * (wd - 1) >= P.slot_hentries) { atomicCAS(P.status, 0, -8); ok = false; }
+                (void)hne;
+                l1 = base + P.off_lcol2 + 2 * e1; x1 = base + P.off_x2 + 4 * e1;
+            }
+            if (ok) {
+                cf2 gp[4], acc[4], rr[4];
+                lds_c2(g1 + wr * 128, gp[0], gp[1]);
+                lds_c2(g2 + wr * 128, gp[2], gp[3]);
+                if (gis1) {
+#pragma unroll
+                    for (int f = 0; f < 4; ++f) rr[f] = f2_cmul(arr, ani, gp[f]);
+                } else {
+                    lds_c2(rw + wr * 128 + 16 * c1, rr[0], rr[1]);
+                    lds_c2(rw + wr * 128 + 16 * c2, rr[2], rr[3]);
+                }
+                pair_gather(g1, g2, l1, x1, wd, gp, acc);
+                cf2 out[4];
+#pragma unroll
+                for (int f = 0; f < 4; ++f) out[f] = f2_add(rr[f], f2_cmul(brr, bni, f2_sub(acc[f], gp[f])));
+                sts_c2(rw + wr * 128 + 16 * c1, out[0], out[1]);
+                sts_c2(rw + wr * 128 + 16 * c2, out[2], out[3]);
+            }
+        }
+        compute_warps_sync();
+    }
+    if (!valid_row) return;
+    // ---- the pass's last stage j on R0: g = b_k (r window) after phase 1, else the g window
+    const int j = role.two ? role.fk - 1 : role.fk;
+    const PairCoef c = role.two ? pcs[j] : c_first;
+    const bool gisj = (c.flags & kGisPsi) != 0;
+    const uint32_t gb = role.two ? rw : gw;
+    const uint32_t h1 = gb + 16 * c1, h2 = gb + 16 * c2;
+    cf2 gp[4], acc[4], ps[4], hv[4];
+    lds_c2(h1 + lr * 128, gp[0], gp[1]);
+    lds_c2(h2 + lr * 128, gp[2], gp[3]);
+    // psi of the row: the psi area, or the g window when it holds psi
+    const uint32_t pb = (gis1) ? gw : pw;
+    lds_c2(pb + lr * 128 + 16 * c1, ps[0], ps[1]);
+    lds_c2(pb + lr * 128 + 16 * c2, ps[2], ps[3]);
+    // the h term of stage j: b_{j+2} = the g window's own row after phase 1
+    // (b_{k+1}); for a single or final pass the r window holds r_j or b_2
+    const bool hasH = (c.flags & kHasH) != 0;
+    if (role.two) {
+        if (hasH) { lds_c2(g1 + lr * 128, hv[0], hv[1]); lds_c2(g2 + lr * 128, hv[2], hv[3]); }
+    } else if (!gisj && (pi.type != 2 || hasH)) {
+        lds_c2(rw + lr * 128 + 16 * c1, hv[0], hv[1]);
+        lds_c2(rw + lr * 128 + 16 * c2, hv[2], hv[3]);
+    }
+    pair_gather(h1, h2, lc, xs, width, gp, acc);
+    const cf2 arr = f2_pack(c.alpha.x, c.alpha.x), ani = f2_pack(-c.alpha.y, c.alpha.y);
+    const cf2 brr = f2_pack(c.beta.x, c.beta.x), bni = f2_pack(-c.beta.y, c.beta.y);
+    cf2 out[4];
+    if (pi.type == 2) {
+        // final stage: S = a_0 psi + a_lo psi + (X b_1) - b_2 in double-float arithmetic
+        // (X b_1 = acc - b_1 in difference form), then the diagonal flow
+#pragma unroll
+        for (int f = 0; f < 4; ++f) {
+            const float2 o = final_combine(c.alpha, c.alpha_lo, c.beta, f2_unpack(ps[f]), f2_unpack(acc[f]),
+                                           f2_unpack(gp[f]), hasH ? f2_unpack(hv[f]) : make_float2(0.f, 0.f), hasH);
+            out[f] = f2_pack(o.x, o.y);
+        }
+        float2 *dst;
+        if (kerr_mode == 0) {
+            float em, phi;
+            diag_factors(__ldg(m.sigma + row), h_post, em, phi);
+            const float vv = __ldg(m.v + row), cb = __ldg(m.chib + row);
+#pragma unroll
+            for (int f = 0; f < 4; ++f) {
+                const float2 o = diag_apply(f2_unpack(out[f]), vv, cb, h_post, em, phi);
+                out[f] = f2_pack(o.x, o.y);
+            }
+            dst = m.psi;
+        } else {
+            dst = Gout;          // element-averaged Kerr needs the neighbours' |S|^2: park S
+        }
+        stg_c2(dst + (size_t)row * 16 + 2 * c1, out[0], out[1]);
+        stg_c2(dst + (size_t)row * 16 + 2 * c2, out[2], out[3]);
+        return;
+    }
+    // r term of stage j
+    cf2 rr[4];
+    if (role.two) {
+#pragma unroll
+        for (int f = 0; f < 4; ++f) {
+            rr[f] = f2_cmul(arr, ani, ps[f]);
+            if (hasH) rr[f] = f2_sub(rr[f], hv[f]);
+        }
+    } else if (gisj) {
+#pragma unroll
+        for (int f = 0; f < 4; ++f) rr[f] = f2_cmul(arr, ani, gp[f]);
+    } else {
+#pragma unroll
+        for (int f = 0; f < 4; ++f) rr[f] = hv[f];
+    }
+#pragma unroll
+    for (int f = 0; f < 4; ++f) out[f] = f2_add(rr[f], f2_cmul(brr, bni, f2_sub(acc[f], gp[f])));
+    stg_c2(Gout + (size_t)row * 16 + 2 * c1, out[0], out[1]);
+    stg_c2(Gout + (size_t)row * 16 + 2 * c2, out[2], out[3]);
+    // what the next stage j - 1 needs besides b_j: b_{j+1} itself if it is the
+    // final stage (kept apart for its double-float combination), else
+    // r_{j-1} = a_{j-1} psi - b_{j+1} (without b_{j+1} when it has no h term)
+    // (b_{j+1} is this stage's own g: phase 1's b_k, or the single pass's input)
+    if ((c.flags & kNextFinal) && !(c.flags & kNextHasH)) return;
+    cf2 nx[4];
+    if (c.flags & kNextFinal) {
+#pragma unroll
+        for (int f = 0; f < 4; ++f) nx[f] = gp[f];
+    } else {
+        const cf2 nrr = f2_pack(c.alpha_next.x, c.alpha_next.x), nni = f2_pack(-c.alpha_next.y, c.alpha_next.y);
+#pragma unroll
+        for (int f = 0; f < 4; ++f) {
+            nx[f] = f2_cmul(nrr, nni, ps[f]);
+            if (c.flags & kNextHasH) nx[f] = f2_sub(nx[f], gp[f]);
+        }
+    }
+    stg_c2(Rout + (size_t)row * 16 + 2 * c1, nx[0], nx[1]);
+    stg_c2(Rout + (size_t)row * 16 + 2 * c2, nx[2], nx[3]);
+}
+
+template <bool COPIER>
+__device__ __forceinline__ void pair_march_role(int copier, const MarchParams<float> &P, char *s_ring,
+                                                const int32_t *s_begin, const int32_t *s_tbeg,
+                                                const MeshView<float> *s_view, unsigned long long *s_full,
+                                                unsigned long long *s_empty, int *s_look) {
+    constexpr int FPT = Geo<float, 16>::FPT;
+    const int lane = threadIdx.x & 31;
+    unsigned long long target = 0;
+    const float h = P.h, hh = P.h * 0.5f;
+    const int bl = Geo<float, 16>::TPR_LOG2 + Geo<float, 16>::FPT_LOG2;
+    const unsigned D = unsigned(P.n_slots);
+    unsigned seq = 0;
+    LookCursor cur{0, 0, pair_tile_range(P, 0)};
+    int *ring = s_look + copier * (kPairLook * kPairLookInts);
+    if constexpr (COPIER) {
+        fence_proxy_async_global();
+        if (copier < int(D))
+            for (int e = 0; e < kPairLook; ++e)
+                pair_look_issue(ring + e * kPairLookInts, pair_look_next_n(cur, P, e == 0 ? copier + 1 : int(D)),
+                                s_view, s_tbeg, P.n_meshes);
+    }
+    for (int step = 0; step < P.n_steps; ++step) {
+        if (step == 0 && P.pre_half) {
+            if (P.kerr_mode == 0) {
+                for_my_items(P, s_begin, P.total_items, [&](const MeshView<float> &m, int li) {
+                    lumped_diag_item<float, FPT>(m, li, hh, bl);
+                });
+                fence_proxy_async_global();
+                if (!grid_barrier(P.barrier, target, P.status, P.timeout_ns)) return;
+                if constexpr (COPIER) fence_proxy_async_global();
+            } else {
+                for_my_items(P, s_begin, P.total_items, [&](const MeshView<float> &m, int li) {
+                    element_kerr_item<float, FPT>(m, li, hh, bl, m.psi, m.b[0]);
+                });
+                if (!grid_barrier(P.barrier, target, P.status, P.timeout_ns)) return;
+                for_my_items(P, s_begin, P.total_items, [&](const MeshView<float> &m, int li) {
+                    copy_item<float, FPT>(m, li, bl, m.b[0], m.psi);
+                });
+                fence_proxy_async_global();
+                if (!grid_barrier(P.barrier, target, P.status, P.timeout_ns)) return;
+                if constexpr (COPIER) fence_proxy_async_global();
+            }
+        }
+        const float h_post = (step == P.n_steps - 1 && P.post_half) ? hh : h;
+        for (int p = 0; p < P.n_passes; ++p) {
+            const PassInfo pi = pass_info(P.S, p);
+            const TileRange R = pair_tile_range(P, p);
+            bool ok = true;
+            for (int i = 0; i < R.n && ok; ++i) {
+                const unsigned q = seq + unsigned(i), sl = q % D;
+                if constexpr (COPIER) {
+                    if (int(sl) != copier) continue;
+                    if (q >= D) ok = mbar_wait(smem_u32(&s_empty[sl]), ((q / D) - 1u) & 1u, P.status, P.timeout_ns);
+                    if (ok) {
+                        int *entry = ring + ((q / D) % kPairLook) * kPairLookInts;
+                        cp_async_wait<kPairLook - 1>();
+                        __syncwarp();
+                        pair_fill(entry, s_view, s_tbeg, P.n_meshes, p, pi, s_ring + (size_t)sl * P.slot_bytes,
+                                  smem_u32(&s_full[sl]), P);
+                        __syncwarp();
+                        pair_look_issue(entry, pair_look_next_n(cur, P, int(D)), s_view, s_tbeg, P.n_meshes);
+                    }
+                } else {
+                    ok = mbar_wait(smem_u32(&s_full[sl]), (q / D) & 1u, P.status, P.timeout_ns);
+                    // every compute warp reaches the same phase-1 barrier of a tile, so
+                    // a failed wait is made uniform first (one warp cannot leave alone)
+                    ok = compute_warps_and(ok);
+                    if (ok) {
+                        pair_compute(s_view, p, pi, s_ring + (size_t)sl * P.slot_bytes, h_post, P.kerr_mode, P);
+                        __syncwarp();
+                        if (lane == 0) mbar_arrive(smem_u32(&s_empty[sl]));
+                    }
+                }
+            }
+            seq += unsigned(R.n);
+            if (!ok) return;
+            fence_proxy_async_global();
+            if (!grid_barrier(P.barrier, target, P.status, P.timeout_ns)) return;
+            if constexpr (COPIER) fence_proxy_async_global();
+        }
+        if (P.kerr_mode != 0) {
+            const int pf = P.n_passes - 1;        // the final pass parked S in its G output
+            for_my_items(P, s_begin, P.total_items, [&](const MeshView<float> &m, int li) {
+                element_kerr_item<float, FPT>(m, li, h_post, bl, (pf & 1) ? m.b[0] : m.b[1], m.psi);
+            });
+            fence_proxy_async_global();
+            if (!grid_barrier(P.barrier, target, P.status, P.timeout_ns)) return;
+            if constexpr (COPIER) fence_proxy_async_global();
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kTileThreads, 1) march_pair_kernel(MarchParams<float> P) {
+    extern __shared__ __align__(128) char s_ring[];
+    __shared__ int32_t s_begin[kMaxMeshes + 1];
+    __shared__ int32_t s_tbeg[kMaxMeshes + 1];
+    __shared__ MeshView<float> s_view[kMaxMeshes];
+    __shared__ __align__(8) unsigned long long s_full[kMaxSlots], s_empty[kMaxSlots];
+    __shared__ __align__(16) int s_look[kTileCopyWarps * kPairLook * kPairLookInts];
+    for (int i = threadIdx.x; i < P.n_meshes; i += blockDim.x) {
+        s_begin[i] = P.meshes[i].item_begin;
+        s_tbeg[i] = P.meshes[i].tile_begin;
+        s_view[i] = P.meshes[i];
+    }
+    if (threadIdx.x < P.n_slots) {
+        mbar_init(smem_u32(&s_full[threadIdx.x]), 1);
+        mbar_init(smem_u32(&s_empty[threadIdx.x]), kTileComputeWarps);
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    __syncthreads();
+    const int warp = threadIdx.x >> 5;
+    if (warp >= kTileComputeWarps) {
+        pair_march_role<true>(warp - kTileComputeWarps, P, s_ring, s_begin, s_tbeg, s_view, s_full, s_empty, s_look);
+        cp_async_wait<0>();
+    } else {
+        pair_march_role<false>(0, P, s_ring, s_begin, s_tbeg, s_view, s_full, s_empty, s_look);
     }
 }
 

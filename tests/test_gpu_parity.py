@@ -316,6 +316,72 @@ def test_tile_staged_full_bench_batch_one_step():
         assert torch.equal(x, y)
 
 
+@pytest.mark.parametrize("kerr", ["lumped", "element"])
+def test_stage_pair_kernel(kerr):
+    """The stage-pair kernel (two Clenshaw stages per grid-wide pass, depth-two
+    halos recomputed per tile) on meshes of uneven size and degree (so that a
+    mesh's top stage falls in either phase of a pass, and single and final
+    passes occur), with 9..16 fields, a single triangle and meshes below one
+    tile: against the row kernel (FP32 rounding only: <= 2e-6 relative after
+    7 steps in three blocks) and against the FP64 oracle within the FP32
+    bars (one step <= 1e-5, the run <= 1e-4)."""
+    specs = [(600, 16, 51), (2500, 9, 52), (5000, 12, 53), (90, 16, 54), (40, 16, 55), (3, 16, 56)]
+    meshes, opss, sigs, psis = [], [], [], []
+    for n, B, seed in specs:
+        if n == 3:
+            coords = np.array([[0.0, 0.0], [1.0, 0.0], [0.2, 0.9]])
+            tris = np.array([[0, 1, 2]], dtype=np.int32)
+        else:
+            coords, tris = W.mesh_disk_graded(4.0, n, 3.0, interfaces=(1.0,), seed=seed, grade_from=1.0)
+        V, chi = W.step_index_materials(coords, tris)
+        sigma = W.absorber_profile(coords, 4.0, 20.0)
+        meshes.append(api.Mesh(coords, tris, V, chi, sigma))
+        opss.append(dec.Operators(coords, tris, V, chi))
+        sigs.append(sigma)
+        psis.append(W.hg_superpositions(coords, B, np.random.default_rng(seed)) * 2.0)
+    plan = api.Plan(meshes, [p.shape[1] for p in psis], "c64")
+    cfg = plan.config()
+    assert cfg["pair_slots"] >= 2 and cfg["tile_slots"] >= 2
+    dz = 2e-3
+    degs = [plan.degree(i, dz) for i in range(len(specs))]
+    assert len({d % 2 for d in degs}) == 2          # both parities: top stages in both phases
+    a = [to_dev(p, torch.complex64) for p in psis]
+    b = [x.clone() for x in a]
+    plan.propagate(a, dz, 7, diag_every=3, kerr=kerr, variant="pairs")
+    plan.propagate(b, dz, 7, diag_every=3, kerr=kerr, variant="rows")
+    for x, y in zip(a, b):
+        assert torch.isfinite(torch.view_as_real(x)).all()
+        d = float(torch.linalg.vector_norm((x - y).to(torch.complex128)) / torch.linalg.vector_norm(y.to(torch.complex128)))
+        assert d <= 2e-6, d
+    for ops, sigma, p0, t in zip(opss, sigs, psis, a):
+        ref = bpm.propagate(ops, (1.0,), p0, dz, 7, sigma, kerr=kerr)
+        assert rel(ops, from_dev(t), ref) <= 1e-4
+    # one step from the oracle's state rounded to FP32
+    states = [bpm.propagate(ops, (1.0,), p0, dz, 3, sigma, kerr=kerr).astype(np.complex64) for ops, sigma, p0 in
+              zip(opss, sigs, psis)]
+    c = [to_dev(st, torch.complex64) for st in states]
+    plan.propagate(c, dz, 1, kerr=kerr, variant="pairs")
+    for ops, sigma, st, t in zip(opss, sigs, states, c):
+        ref = bpm.propagate(ops, (1.0,), st.astype(np.complex128), dz, 1, sigma, kerr=kerr)
+        assert rel(ops, from_dev(t), ref) <= 1e-5
+
+
+def test_stage_pair_kernel_full_bench_batch():
+    """The bench workload at full size: a 3-step launch of the stage-pair
+    kernel against the row kernel (FP32 rounding only)."""
+    wl = W.batched_fibers(n_meshes=16, fields_per_mesh=16, n_min=20_000, ratio=25.0, seed=4)
+    meshes = [api.Mesh.from_workload(m, p=wl.p) for m in wl.meshes]
+    plan = api.Plan(meshes, [16] * len(meshes), "c64")
+    assert plan.config()["pair_slots"] >= 2
+    a = [to_dev(p, torch.complex64) for p in wl.psi0]
+    b = [x.clone() for x in a]
+    plan.propagate(a, wl.dz, 3, variant="pairs")
+    plan.propagate(b, wl.dz, 3, variant="rows")
+    for x, y in zip(a, b):
+        d = float(torch.linalg.vector_norm((x - y).to(torch.complex128)) / torch.linalg.vector_norm(y.to(torch.complex128)))
+        assert d <= 2e-6, d
+
+
 @pytest.mark.parametrize("precision", ["c64", "c128"])
 def test_autotuner_picks_a_shape_without_changing_results(precision):
     """decbpm_plan_autotune times the FUSED launch shapes (tile-staged kernel
@@ -340,13 +406,17 @@ def test_autotuner_picks_a_shape_without_changing_results(precision):
     assert tune["from_cache"] == 0 and tune["candidates"] >= 2 and tune["ms_per_step"] > 0
     cfg = plan.config()
     assert cfg["tuned"] == 1
-    assert cfg["fused_kernel"] == (1 if tune["kernel"] == "tile" else 0)
+    assert cfg["fused_kernel"] == {"pairs": 2, "tile": 1, "rows": 0}[tune["kernel"]]
     if precision == "c128":
         assert tune["kernel"] == "rows"
     b = [to_dev(p, dt) for p in psis]
     plan.propagate(b, dz, 7)
     for x, y in zip(a, b):
-        assert torch.equal(x, y)
+        if tune["kernel"] == "pairs":       # the stage-pair kernel rounds differently (FP32 level)
+            d = float(torch.linalg.vector_norm((x - y).to(torch.complex128)) / torch.linalg.vector_norm(y))
+            assert d <= 2e-6, d
+        else:
+            assert torch.equal(x, y)
     again = api.Plan(meshes, [p.shape[1] for p in psis], precision).autotune(dz, trial_steps=2)
     assert again["from_cache"] == 1
     keys = ("kernel", "ctas_per_sm", "tile_slots", "forward_walk")
