@@ -815,14 +815,15 @@ template <int N> __device__ __forceinline__ void cp_async_wait() { asm volatile(
 __device__ __forceinline__ void look_issue(int *entry, int t, const MeshView<float> *sv, const int32_t *s_tbeg,
                                            int n_meshes) {
     const int lane = threadIdx.x & 31;
+    int mi = 0, tl = 0;
     if (t >= 0) {
-        const int mi = mesh_of_tile(s_tbeg, n_meshes, t);
-        const int tl = t - s_tbeg[mi];
+        mi = mesh_of_tile(s_tbeg, n_meshes, t);
+        tl = t - s_tbeg[mi];
         if (lane < 24) cp_async16(smem_u32(entry + 4 * lane), sv[mi].halo_rows + (size_t)tl * (32 * kHaloRegs) + 4 * lane);
         if (lane == 24) cp_async16(smem_u32(entry + 96), sv[mi].tdesc + 8 * (size_t)tl);
     }
-    if (lane == 25) entry[100] = t;
-    cp_async_commit();
+    if (lane == 25) { entry[100] = t; entry[101] = mi; entry[102] = tl; }   // (the fill and the compute warps
+    cp_async_commit();                                                    //  need no mesh search)
 }
 
 // Copy warp: fill `slot` with everything the tile of look-ahead `entry` needs in stage k.  The
@@ -832,12 +833,12 @@ __device__ __forceinline__ void tile_fill(const int *entry, const MeshView<float
                                           const int32_t *s_tbeg, int n_meshes, int k, char *slot, uint32_t bar,
                                           const MarchParams<float> &P) {
     const int lane = threadIdx.x & 31;
-    const int t = entry[100];
     const int4 dsc = *reinterpret_cast<const int4 *>(entry + 96);
-    const int mi = mesh_of_tile(s_tbeg, n_meshes, t);
+    const int mi = entry[101], tl = entry[102];
+    (void)s_tbeg;
+    (void)n_meshes;
     const MeshView<float> &m = sv[mi];
     const int flags = scoef[mi].flags;
-    const int tl = t - s_tbeg[mi];
     const int r0 = tl * kTileRows, nrows = min(kTileRows, m.n0 - r0);
     const int e0 = dsc.x, ne = dsc.y, ovf = dsc.z, nh = dsc.w;
     const float2 *g = (flags & kGisPsi) ? m.psi : m.b[(k + 1) % 3];
@@ -856,7 +857,12 @@ __device__ __forceinline__ void tile_fill(const int *entry, const MeshView<float
     const unsigned total = row_bytes * (1u + ((flags & kGisPsi) ? 0u : 1u) + ((flags & kHasH) ? 1u : 0u)) +
                            unsigned(ne) * 6u + unsigned(n_bulk_halo) * 128u + 16u;
     __syncwarp();
-    if (lane == 0) mbar_arrive_expect_tx(bar, total);
+    if (lane == 0) {
+        // mesh and local tile index for the compute warps, next to the descriptor
+        // (written before the arrive, whose release orders it before their wait)
+        asm volatile("st.shared.v2.s32 [%0], {%1, %2};" ::"r"(base + P.off_hdr + 16), "r"(mi), "r"(tl) : "memory");
+        mbar_arrive_expect_tx(bar, total);
+    }
     __syncwarp();
     if (lane == 0) bulk_g2s(base, g + (size_t)r0 * 16, row_bytes, bar);
     if (lane == 1 && !(flags & kGisPsi)) bulk_g2s(base + P.off_psi, m.psi + (size_t)r0 * 16, row_bytes, bar);
@@ -930,16 +936,19 @@ __device__ __forceinline__ void tile_compute(const MeshView<float> *sv, const St
                                              const int32_t *s_tbeg, int n_meshes, int t, int k, const char *slot,
                                              float h_post, int kerr_mode, const MarchParams<float> &P) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int mi = mesh_of_tile(s_tbeg, n_meshes, t);
+    const uint32_t base = smem_u32(slot);
+    int mi, tl;                                            // written by the copy warp next to the descriptor
+    asm volatile("ld.shared.v2.s32 {%0, %1}, [%2];" : "=r"(mi), "=r"(tl) : "r"(base + P.off_hdr + 16));
+    (void)s_tbeg;
+    (void)n_meshes;
+    (void)t;
     const MeshView<float> &m = sv[mi];
     const StageCoef<float> sc = scoef[mi];
-    const int tl = t - s_tbeg[mi];
     const int lr = warp * 8 + (lane >> 2);                 // row in the tile
     const int row = tl * kTileRows + lr;
     if (row >= m.n0) return;
     const int c1 = (lane & 3) + 4 * ((lane >> 2) & 1), c2 = c1 ^ 4;
     const int sl = lr >> 5;
-    const uint32_t base = smem_u32(slot);
     const int4 hdr = lds_i4(base + P.off_hdr);
     const int es = ((sl < 2 ? hdr.x : hdr.y) >> (16 * (sl & 1)) & 0xffff) + (lr & 31);
     const int width = (hdr.z >> (8 * sl)) & 0xff;
@@ -1203,18 +1212,25 @@ __device__ __forceinline__ int lds_i32(uint32_t addr) {
     asm volatile("ld.shared.s32 %0, [%1];" : "=r"(v) : "r"(addr));
     return v;
 }
-// barriers of the 16 compute warps only (the copy warps never take them)
-__device__ __forceinline__ void compute_warps_sync() { asm volatile("bar.sync 1, 512;" ::: "memory"); }
-// AND of v over the 16 compute warps (a barrier as well)
-__device__ __forceinline__ bool compute_warps_and(bool v) {
+// The compute warps form two groups of 8 that take alternate tiles, so one
+// group's phase barrier overlaps the other group's work.  Barriers of one
+// group only (hardware barriers 1 + g and 3 + g, 256 threads; the copy warps
+// and the other group never take them).
+constexpr int kPairGroups = 2;
+constexpr int kPairGroupWarps = kTileComputeWarps / kPairGroups;
+__device__ __forceinline__ void group_sync(int g) {
+    asm volatile("bar.sync %0, 256;" ::"r"(1 + g) : "memory");
+}
+// AND of v over the group's warps (a barrier as well)
+__device__ __forceinline__ bool group_and(int g, bool v) {
     unsigned r;
     asm volatile(
         "{\n\t.reg .pred p, q;\n\t"
-        "setp.ne.u32 p, %1, 0;\n\t"
-        "bar.red.and.pred q, 2, 512, p;\n\t"
+        "setp.ne.u32 p, %2, 0;\n\t"
+        "bar.red.and.pred q, %1, 256, p;\n\t"
         "selp.u32 %0, 1, 0, q;\n\t}"
         : "=r"(r)
-        : "r"(unsigned(v))
+        : "r"(3 + g), "r"(unsigned(v))
         : "memory");
     return r != 0;
 }
@@ -1251,15 +1267,20 @@ __device__ __forceinline__ int pair_look_next_n(LookCursor &c, const MarchParams
 __device__ __forceinline__ void pair_look_issue(int *entry, int t, const MeshView<float> *sv, const int32_t *s_tbeg,
                                                 int n_meshes) {
     const int lane = threadIdx.x & 31;
+    int mi = 0, tl = 0;
     if (t >= 0) {
-        const int mi = mesh_of_tile(s_tbeg, n_meshes, t);
-        const int tl = t - s_tbeg[mi];
+        mi = mesh_of_tile(s_tbeg, n_meshes, t);
+        tl = t - s_tbeg[mi];
         const int32_t *hl = sv[mi].hlist + (size_t)tl * kPairHL;
         cp_async16(smem_u32(entry + 4 * lane), hl + 4 * lane);                 // rows 0..127
         cp_async16(smem_u32(entry + 128 + 4 * lane), hl + 128 + 4 * lane);     // rows 128..255
         if (lane < 3) cp_async16(smem_u32(entry + kPairHL + 4 * lane), sv[mi].pdesc + (size_t)tl * kPairDesc + 4 * lane);
     }
-    if (lane == 31) entry[kPairHL + kPairDesc] = t;
+    if (lane == 31) {
+        entry[kPairHL + kPairDesc] = t;
+        entry[kPairHL + kPairDesc + 1] = mi;
+        entry[kPairHL + kPairDesc + 2] = tl;
+    }
     cp_async_commit();
 }
 
@@ -1272,26 +1293,26 @@ __device__ __forceinline__ PairRole pair_role(int M, int k, int type) {
 }
 
 // Copy warp: fill `slot` for the tile of look-ahead `entry` in pass p.
-__device__ __forceinline__ void pair_fill(const int *entry, const MeshView<float> *sv, const int32_t *s_tbeg,
-                                          int n_meshes, int p, PassInfo pi, char *slot, uint32_t bar,
-                                          const MarchParams<float> &P) {
+__device__ __forceinline__ void pair_fill(const int *entry, const MeshView<float> *sv, const PairCoef *s_pc,
+                                          const int32_t *s_tbeg, int n_meshes, int p, PassInfo pi, char *slot,
+                                          uint32_t bar, const MarchParams<float> &P) {
     const int lane = threadIdx.x & 31;
-    const int t = entry[kPairHL + kPairDesc];
     const int *dsc = entry + kPairHL;
-    const int mi = mesh_of_tile(s_tbeg, n_meshes, t);
+    const int mi = entry[kPairHL + kPairDesc + 1], tl = entry[kPairHL + kPairDesc + 2];
+    (void)s_tbeg;
+    (void)n_meshes;
     const MeshView<float> &m = sv[mi];
-    const int tl = t - s_tbeg[mi];
     const int r0 = tl * kTileRows, nrows = min(kTileRows, m.n0 - r0);
     const int e0 = dsc[0], ne = dsc[1], nh1 = dsc[2] & 0xffff, nh2 = dsc[2] >> 16, he0 = dsc[3], hne = dsc[8];
     const PairRole role = pair_role(m.M, pi.k, pi.type);
-    const PairCoef pc = reinterpret_cast<const PairCoef *>(m.pcoef)[role.fk];
-    const bool gis = (pc.flags & kGisPsi) != 0;
+    const int pflags = s_pc[2 * mi].flags;                 // the pass's first stage for this mesh
+    const bool gis = (pflags & kGisPsi) != 0;
     const float2 *Gin = (p & 1) ? m.b[1] : m.b[0];
     const float2 *Rin = (p & 1) ? m.b3 : m.b[2];
     const float2 *g = gis ? m.psi : Gin;
     // r rows: [R0, H1] in phase 1 of a pair; R0 for a single pass; R0 for the
     // final pass when it has an h term (b_2, stored plain); none at a top stage
-    const bool need_r = !gis && (pi.type != 2 || (pc.flags & kHasH));
+    const bool need_r = !gis && (pi.type != 2 || (pflags & kHasH));
     const bool r_halo = need_r && role.two;
     const int ng_halo = role.two ? nh1 + nh2 : nh1;       // g rows beyond the tile
     const uint32_t base = smem_u32(slot);
@@ -1368,82 +1389,48 @@ __device__ __forceinline__ void slice_entry(int lr, int es01, int es23, int widt
     width = (widths >> (8 * sl)) & 0xff;
 }
 
-// Compute warps: the stages of pass p on the tile in `slot`.
-__device__ __forceinline__ void pair_compute(const MeshView<float> *sv, int p, PassInfo pi, const char *slot,
-                                             float h_post, int kerr_mode, const MarchParams<float> &P) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const uint32_t base = smem_u32(slot);
-    const uint32_t hdr = base + P.off_hdr;
-    const int4 d0 = lds_i4(hdr), d1 = lds_i4(hdr + 16), d2 = lds_i4(hdr + 32);
-    const int mi = lds_i32(hdr + 4 * kPairDesc), tl = lds_i32(hdr + 4 * kPairDesc + 4);
-    const int nh1 = d0.z & 0xffff, hne = d2.x;
-    const MeshView<float> &m = sv[mi];
-    const PairRole role = pair_role(m.M, pi.k, pi.type);
-    const PairCoef *pcs = reinterpret_cast<const PairCoef *>(m.pcoef);
+// Compute warps of group g: the stages of pass p on the tile in `slot`.  The
+// group's 8 warps take 64 rows per round (8 rows of 4 lanes per warp): two
+// rounds of tile rows and up to two of halo rows in phase 1, two rounds of
+// tile rows in phase 2.
+__device__ __forceinline__ void pair_row_stage1(const char *slot, int wr, int lwin, bool ok, bool gis1, cf2 arr,
+                                                cf2 ani, cf2 brr, cf2 bni, uint32_t lcb, uint32_t xsb, int width,
+                                                const MarchParams<float> &P) {
+    (void)lwin;
+    if (!ok) return;
+    const int lane = threadIdx.x & 31;
     const int c1 = (lane & 3) + 4 * ((lane >> 2) & 1), c2 = c1 ^ 4;
+    const uint32_t base = smem_u32(slot);
+    const uint32_t g1 = base + 16 * c1, g2 = base + 16 * c2, rw = base + P.off_h;
+    cf2 gp[4], acc[4], rr[4];
+    lds_c2(g1 + wr * 128, gp[0], gp[1]);
+    lds_c2(g2 + wr * 128, gp[2], gp[3]);
+    if (gis1) {
+#pragma unroll
+        for (int f = 0; f < 4; ++f) rr[f] = f2_cmul(arr, ani, gp[f]);
+    } else {
+        lds_c2(rw + wr * 128 + 16 * c1, rr[0], rr[1]);
+        lds_c2(rw + wr * 128 + 16 * c2, rr[2], rr[3]);
+    }
+    pair_gather(g1, g2, lcb, xsb, width, gp, acc);
+    cf2 out[4];
+#pragma unroll
+    for (int f = 0; f < 4; ++f) out[f] = f2_add(rr[f], f2_cmul(brr, bni, f2_sub(acc[f], gp[f])));
+    sts_c2(rw + wr * 128 + 16 * c1, out[0], out[1]);
+    sts_c2(rw + wr * 128 + 16 * c2, out[2], out[3]);
+}
+
+__device__ __forceinline__ void pair_row_last(const MeshView<float> &m, int p, PassInfo pi, const PairRole role,
+                                              const PairCoef &c, bool gis1, const char *slot, int lr, int row,
+                                              uint32_t lc, uint32_t xs, int width, float h_post, int kerr_mode,
+                                              const MarchParams<float> &P) {
+    const int lane = threadIdx.x & 31;
+    const int c1 = (lane & 3) + 4 * ((lane >> 2) & 1), c2 = c1 ^ 4;
+    const uint32_t base = smem_u32(slot);
     const uint32_t gw = base, rw = base + P.off_h, pw = base + P.off_psi;
     const uint32_t g1 = gw + 16 * c1, g2 = gw + 16 * c2;
     float2 *Gout = (p & 1) ? m.b[0] : m.b[1];
     float2 *Rout = (p & 1) ? m.b[2] : m.b3;
-    const int lr = warp * 8 + (lane >> 2);
-    const int row = tl * kTileRows + lr;
-    const bool valid = row < m.n0;
-    int es, width;
-    slice_entry(lr, d1.x, d1.y, d1.z, es, width);
-    bool valid_row = valid;
-    if (valid && width > 0 && es + 32 * (width - 1) >= P.slot_entries) {   // cannot happen with consistent maps
-        atomicCAS(P.status, 0, -8);                 // DECBPM_ERR_DEVICE_CHECK; the row is skipped (no early
-        valid_row = false;                          // return: every compute warp must reach the phase barrier)
-    }
-    const uint32_t lc = base + P.off_lcol + 2 * es, xs = base + P.off_x + 4 * es;
-    const PairCoef c_first = pcs[role.fk];
-    const bool gis1 = (c_first.flags & kGisPsi) != 0;
-    if (role.two) {
-        // ---- phase 1: b_k on R0 (round A) and on H1 (round B), into the r window
-        const cf2 arr = f2_pack(c_first.alpha.x, c_first.alpha.x), ani = f2_pack(-c_first.alpha.y, c_first.alpha.y);
-        const cf2 brr = f2_pack(c_first.beta.x, c_first.beta.x), bni = f2_pack(-c_first.beta.y, c_first.beta.y);
-        for (int round = 0; round < 2; ++round) {
-            int wr, e1, wd;
-            uint32_t l1, x1;
-            bool ok;
-            if (round == 0) {
-                wr = lr; ok = valid_row; l1 = lc; x1 = xs; wd = width;
-            } else {
-                wr = kTileRows + lr; ok = lr < nh1;
-                slice_entry(lr, 0, 0, d1.w, e1, wd);
-                // halo slices are contiguous: slice s starts at 32 * sum_{s' < s} w_s'
-                int pre = 0;
-                for (int s2 = 0; s2 < (lr >> 5); ++s2) pre += (d1.w >> (8 * s2)) & 0xff;
-                e1 = 32 * pre + (lr & 31);
-                if (ok && wd > 0 && e1 + 32 * (wd - 1) >= P.slot_hentries) { atomicCAS(P.status, 0, -8); ok = false; }
-                (void)hne;
-                l1 = base + P.off_lcol2 + 2 * e1; x1 = base + P.off_x2 + 4 * e1;
-            }
-            if (ok) {
-                cf2 gp[4], acc[4], rr[4];
-                lds_c2(g1 + wr * 128, gp[0], gp[1]);
-                lds_c2(g2 + wr * 128, gp[2], gp[3]);
-                if (gis1) {
-#pragma unroll
-                    for (int f = 0; f < 4; ++f) rr[f] = f2_cmul(arr, ani, gp[f]);
-                } else {
-                    lds_c2(rw + wr * 128 + 16 * c1, rr[0], rr[1]);
-                    lds_c2(rw + wr * 128 + 16 * c2, rr[2], rr[3]);
-                }
-                pair_gather(g1, g2, l1, x1, wd, gp, acc);
-                cf2 out[4];
-#pragma unroll
-                for (int f = 0; f < 4; ++f) out[f] = f2_add(rr[f], f2_cmul(brr, bni, f2_sub(acc[f], gp[f])));
-                sts_c2(rw + wr * 128 + 16 * c1, out[0], out[1]);
-                sts_c2(rw + wr * 128 + 16 * c2, out[2], out[3]);
-            }
-        }
-        compute_warps_sync();
-    }
-    if (!valid_row) return;
-    // ---- the pass's last stage j on R0: g = b_k (r window) after phase 1, else the g window
-    const int j = role.two ? role.fk - 1 : role.fk;
-    const PairCoef c = role.two ? pcs[j] : c_first;
     const bool gisj = (c.flags & kGisPsi) != 0;
     const uint32_t gb = role.two ? rw : gw;
     const uint32_t h1 = gb + 16 * c1, h2 = gb + 16 * c2;
@@ -1451,7 +1438,7 @@ __device__ __forceinline__ void pair_compute(const MeshView<float> *sv, int p, P
     lds_c2(h1 + lr * 128, gp[0], gp[1]);
     lds_c2(h2 + lr * 128, gp[2], gp[3]);
     // psi of the row: the psi area, or the g window when it holds psi
-    const uint32_t pb = (gis1) ? gw : pw;
+    const uint32_t pb = gis1 ? gw : pw;
     lds_c2(pb + lr * 128 + 16 * c1, ps[0], ps[1]);
     lds_c2(pb + lr * 128 + 16 * c2, ps[2], ps[3]);
     // the h term of stage j: b_{j+2} = the g window's own row after phase 1
@@ -1515,8 +1502,8 @@ __device__ __forceinline__ void pair_compute(const MeshView<float> *sv, int p, P
     stg_c2(Gout + (size_t)row * 16 + 2 * c2, out[2], out[3]);
     // what the next stage j - 1 needs besides b_j: b_{j+1} itself if it is the
     // final stage (kept apart for its double-float combination), else
-    // r_{j-1} = a_{j-1} psi - b_{j+1} (without b_{j+1} when it has no h term)
-    // (b_{j+1} is this stage's own g: phase 1's b_k, or the single pass's input)
+    // r_{j-1} = a_{j-1} psi - b_{j+1} (without b_{j+1} when it has no h term);
+    // b_{j+1} is this stage's own g (phase 1's b_k, or the single pass's input)
     if ((c.flags & kNextFinal) && !(c.flags & kNextHasH)) return;
     cf2 nx[4];
     if (c.flags & kNextFinal) {
@@ -1534,11 +1521,73 @@ __device__ __forceinline__ void pair_compute(const MeshView<float> *sv, int p, P
     stg_c2(Rout + (size_t)row * 16 + 2 * c2, nx[2], nx[3]);
 }
 
+__device__ __forceinline__ void pair_compute(const MeshView<float> *sv, const PairCoef *s_pc, int p, PassInfo pi,
+                                             const char *slot, float h_post, int kerr_mode, int grp,
+                                             const MarchParams<float> &P) {
+    const int lane = threadIdx.x & 31, lw = (threadIdx.x >> 5) & (kPairGroupWarps - 1);
+    const uint32_t base = smem_u32(slot);
+    const uint32_t hdr = base + P.off_hdr;
+    const int4 d0 = lds_i4(hdr), d1 = lds_i4(hdr + 16);
+    const int mi = lds_i32(hdr + 4 * kPairDesc), tl = lds_i32(hdr + 4 * kPairDesc + 4);
+    const int nh1 = d0.z & 0xffff;
+    const MeshView<float> &m = sv[mi];
+    const PairRole role = pair_role(m.M, pi.k, pi.type);
+    const PairCoef c_first = s_pc[2 * mi];
+    const bool gis1 = (c_first.flags & kGisPsi) != 0;
+    constexpr int kRound = 8 * kPairGroupWarps;             // rows per round of the group
+    // this lane's tile rows (one per round) and their SELL entries
+    int es[kTileRows / kRound], width[kTileRows / kRound];
+    bool okr[kTileRows / kRound];
+#pragma unroll
+    for (int u = 0; u < kTileRows / kRound; ++u) {
+        const int lr = u * kRound + lw * 8 + (lane >> 2);
+        slice_entry(lr, d1.x, d1.y, d1.z, es[u], width[u]);
+        okr[u] = tl * kTileRows + lr < m.n0;
+        if (okr[u] && width[u] > 0 && es[u] + 32 * (width[u] - 1) >= P.slot_entries) {   // inconsistent maps
+            atomicCAS(P.status, 0, -8);           // DECBPM_ERR_DEVICE_CHECK; the row is skipped (no early
+            okr[u] = false;                       // return: the whole group must reach the phase barrier)
+        }
+    }
+    if (role.two) {
+        // ---- phase 1: b_k on the tile rows and on H1, into the r window
+        const cf2 arr = f2_pack(c_first.alpha.x, c_first.alpha.x), ani = f2_pack(-c_first.alpha.y, c_first.alpha.y);
+        const cf2 brr = f2_pack(c_first.beta.x, c_first.beta.x), bni = f2_pack(-c_first.beta.y, c_first.beta.y);
+#pragma unroll
+        for (int u = 0; u < kTileRows / kRound; ++u) {
+            const int lr = u * kRound + lw * 8 + (lane >> 2);
+            pair_row_stage1(slot, lr, lr, okr[u], gis1, arr, ani, brr, bni, base + P.off_lcol + 2 * es[u],
+                            base + P.off_x + 4 * es[u], width[u], P);
+        }
+        for (int i0 = 0; i0 < nh1; i0 += kRound) {
+            const int i = i0 + lw * 8 + (lane >> 2);
+            bool ok = i < nh1;
+            int e1, wd;
+            slice_entry(i, 0, 0, d1.w, e1, wd);
+            int pre = 0;                        // halo slices are contiguous: slice s starts at 32 sum_{s'<s} w_s'
+            for (int s2 = 0; s2 < (i >> 5); ++s2) pre += (d1.w >> (8 * s2)) & 0xff;
+            e1 = 32 * pre + (i & 31);
+            if (ok && wd > 0 && e1 + 32 * (wd - 1) >= P.slot_hentries) { atomicCAS(P.status, 0, -8); ok = false; }
+            pair_row_stage1(slot, kTileRows + i, i, ok, gis1, arr, ani, brr, bni, base + P.off_lcol2 + 2 * e1,
+                            base + P.off_x2 + 4 * e1, wd, P);
+        }
+        group_sync(grp);
+    }
+    // ---- the pass's last stage j on the tile rows
+    const PairCoef c = s_pc[2 * mi + 1];                    // the pass's last stage (= the first one unless a pair)
+#pragma unroll
+    for (int u = 0; u < kTileRows / kRound; ++u) {
+        if (!okr[u]) continue;
+        const int lr = u * kRound + lw * 8 + (lane >> 2);
+        pair_row_last(m, p, pi, role, c, gis1, slot, lr, tl * kTileRows + lr, base + P.off_lcol + 2 * es[u],
+                      base + P.off_x + 4 * es[u], width[u], h_post, kerr_mode, P);
+    }
+}
+
 template <bool COPIER>
 __device__ __forceinline__ void pair_march_role(int copier, const MarchParams<float> &P, char *s_ring,
                                                 const int32_t *s_begin, const int32_t *s_tbeg,
-                                                const MeshView<float> *s_view, unsigned long long *s_full,
-                                                unsigned long long *s_empty, int *s_look) {
+                                                const MeshView<float> *s_view, PairCoef *s_pc,
+                                                unsigned long long *s_full, unsigned long long *s_empty, int *s_look) {
     constexpr int FPT = Geo<float, 16>::FPT;
     const int lane = threadIdx.x & 31;
     unsigned long long target = 0;
@@ -1546,6 +1595,7 @@ __device__ __forceinline__ void pair_march_role(int copier, const MarchParams<fl
     const int bl = Geo<float, 16>::TPR_LOG2 + Geo<float, 16>::FPT_LOG2;
     const unsigned D = unsigned(P.n_slots);
     unsigned seq = 0;
+    const int grp = COPIER ? 0 : (int(threadIdx.x >> 5) / kPairGroupWarps);
     LookCursor cur{0, 0, pair_tile_range(P, 0)};
     int *ring = s_look + copier * (kPairLook * kPairLookInts);
     if constexpr (COPIER) {
@@ -1580,6 +1630,17 @@ __device__ __forceinline__ void pair_march_role(int copier, const MarchParams<fl
         const float h_post = (step == P.n_steps - 1 && P.post_half) ? hh : h;
         for (int p = 0; p < P.n_passes; ++p) {
             const PassInfo pi = pass_info(P.S, p);
+            // the coefficients of this pass's first and last stage per mesh (meshes
+            // not yet active load a placeholder they never use)
+            for (int i = threadIdx.x; i < P.n_meshes; i += blockDim.x) {
+                const int M = s_view[i].M;
+                const PairRole role = pair_role(M, pi.k, pi.type);
+                const PairCoef *pcs = reinterpret_cast<const PairCoef *>(s_view[i].pcoef);
+                const int f0 = min(max(role.fk, 0), M - 1);
+                s_pc[2 * i] = pcs[f0];
+                s_pc[2 * i + 1] = pcs[role.two ? max(f0 - 1, 0) : f0];
+            }
+            __syncthreads();
             const TileRange R = pair_tile_range(P, p);
             bool ok = true;
             for (int i = 0; i < R.n && ok; ++i) {
@@ -1591,18 +1652,20 @@ __device__ __forceinline__ void pair_march_role(int copier, const MarchParams<fl
                         int *entry = ring + ((q / D) % kPairLook) * kPairLookInts;
                         cp_async_wait<kPairLook - 1>();
                         __syncwarp();
-                        pair_fill(entry, s_view, s_tbeg, P.n_meshes, p, pi, s_ring + (size_t)sl * P.slot_bytes,
+                        pair_fill(entry, s_view, s_pc, s_tbeg, P.n_meshes, p, pi, s_ring + (size_t)sl * P.slot_bytes,
                                   smem_u32(&s_full[sl]), P);
                         __syncwarp();
                         pair_look_issue(entry, pair_look_next_n(cur, P, int(D)), s_view, s_tbeg, P.n_meshes);
                     }
                 } else {
+                    if (int(q & 1u) != grp) continue;          // the other group's tile
                     ok = mbar_wait(smem_u32(&s_full[sl]), (q / D) & 1u, P.status, P.timeout_ns);
-                    // every compute warp reaches the same phase-1 barrier of a tile, so
-                    // a failed wait is made uniform first (one warp cannot leave alone)
-                    ok = compute_warps_and(ok);
+                    // every warp of the group reaches the same phase barrier of a tile,
+                    // so a failed wait is made uniform first (one warp cannot leave alone)
+                    ok = group_and(grp, ok);
                     if (ok) {
-                        pair_compute(s_view, p, pi, s_ring + (size_t)sl * P.slot_bytes, h_post, P.kerr_mode, P);
+                        pair_compute(s_view, s_pc, p, pi, s_ring + (size_t)sl * P.slot_bytes, h_post, P.kerr_mode, grp,
+                                     P);
                         __syncwarp();
                         if (lane == 0) mbar_arrive(smem_u32(&s_empty[sl]));
                     }
@@ -1633,6 +1696,7 @@ __global__ void __launch_bounds__(kTileThreads, 1) march_pair_kernel(MarchParams
     __shared__ MeshView<float> s_view[kMaxMeshes];
     __shared__ __align__(8) unsigned long long s_full[kMaxSlots], s_empty[kMaxSlots];
     __shared__ __align__(16) int s_look[kTileCopyWarps * kPairLook * kPairLookInts];
+    __shared__ __align__(16) PairCoef s_pc[2 * kMaxMeshes];
     for (int i = threadIdx.x; i < P.n_meshes; i += blockDim.x) {
         s_begin[i] = P.meshes[i].item_begin;
         s_tbeg[i] = P.meshes[i].tile_begin;
@@ -1640,16 +1704,17 @@ __global__ void __launch_bounds__(kTileThreads, 1) march_pair_kernel(MarchParams
     }
     if (threadIdx.x < P.n_slots) {
         mbar_init(smem_u32(&s_full[threadIdx.x]), 1);
-        mbar_init(smem_u32(&s_empty[threadIdx.x]), kTileComputeWarps);
+        mbar_init(smem_u32(&s_empty[threadIdx.x]), kPairGroupWarps);    // one group empties a slot
     }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     __syncthreads();
     const int warp = threadIdx.x >> 5;
     if (warp >= kTileComputeWarps) {
-        pair_march_role<true>(warp - kTileComputeWarps, P, s_ring, s_begin, s_tbeg, s_view, s_full, s_empty, s_look);
+        pair_march_role<true>(warp - kTileComputeWarps, P, s_ring, s_begin, s_tbeg, s_view, s_pc, s_full, s_empty,
+                              s_look);
         cp_async_wait<0>();
     } else {
-        pair_march_role<false>(0, P, s_ring, s_begin, s_tbeg, s_view, s_full, s_empty, s_look);
+        pair_march_role<false>(0, P, s_ring, s_begin, s_tbeg, s_view, s_pc, s_full, s_empty, s_look);
     }
 }
 
