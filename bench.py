@@ -263,7 +263,8 @@ def run_ours(args, rank, world, local_rank):
             "march_kernel": kernel_name, "tile_slots": cfg["tile_slots_used"] if tiled else 0,
             "forward_walk": cfg["forward_walk"],
             "autotune": None if tune is None else {k: tune[k] for k in ("kernel", "ctas_per_sm", "tile_slots",
-                                                                        "forward_walk", "ms_per_step", "candidates")},
+                                                                        "forward_walk", "values_per_thread",
+                                                                        "ms_per_step", "candidates")},
             "autotune_s": round(tune_s, 2),
             "cuda_graph": bool(cfg["graphs"]),
             "l2": "working set %.2f GB > 126 MB L2; no flush" % (units_per_step * 8 * 4 / 1e9),
@@ -287,8 +288,10 @@ def run_ours(args, rank, world, local_rank):
         line["fp64_plain"]["fp64_fused_speedup"] = line["fp64_fused"]["value"] / line["fp64_plain"]["value"]
         line["rk45"] = rk45_comparison(wl, meshes, api, torch, dev, args.steps)
     if rank == 0 and not args.no_side:
-        line["single_field"] = single_field_runs(api, torch, dev, args.side_steps, peak)
-        line["adjoint"] = adjoint_run(api, torch, dev)
+        side = set(args.side_workloads.split(","))
+        line["single_field"] = single_field_runs(api, torch, dev, args.side_steps, peak, side)
+        if "adjoint" in side:
+            line["adjoint"] = adjoint_run(api, torch, dev)
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args, wl)
         line["cpu_baseline_all_cores"] = cpu_baseline_all_cores(wl, args.cpu_meshes, 16)
@@ -329,7 +332,7 @@ def fp64_batch_comparison(wl, meshes, plan32, fields, infos, api, torch, dev, st
     return err, fp64
 
 
-def single_field_runs(api, torch, dev, steps, peak):
+def single_field_runs(api, torch, dev, steps, peak, which=("disk", "vortex")):
     """The single-field workloads as the library runs them (fused FP32 path,
     one field), each with its error against the fused FP64 run of the same
     steps: the 200k-vertex graded disk (elliptic Gaussian, absorber) and the
@@ -338,7 +341,10 @@ def single_field_runs(api, torch, dev, steps, peak):
     bandwidth claim here; it is reported with the working set."""
     from paper_2608_03587_b300 import workloads as W
     out = {}
-    for name, make in (("gaussian_disk_200k", W.gaussian_disk), ("vortex_multimode_1M", W.vortex_multimode)):
+    for key, name, make in (("disk", "gaussian_disk_200k", W.gaussian_disk),
+                            ("vortex", "vortex_multimode_1M", W.vortex_multimode)):
+        if key not in which:
+            continue
         wl = make()
         m = wl.meshes[0]
         mesh = api.Mesh.from_workload(m, p=wl.p)
@@ -365,7 +371,8 @@ def single_field_runs(api, torch, dev, steps, peak):
         out[name] = {
             "vertices": n0, "steps": steps, "dz": wl.dz, "cheb_degree": M, "value": n0 * steps / (ms * 1e-3),
             "unit": UNIT, "march_ms": march_ms, "kernel": "march_kernel<float,1>" if not cfg["fused_kernel"]
-            else "march_tile_kernel", "autotune": {k: tune[k] for k in ("kernel", "ctas_per_sm", "forward_walk")},
+            else "march_tile_kernel", "autotune": {k: tune[k] for k in ("kernel", "ctas_per_sm", "forward_walk",
+                                                                        "values_per_thread", "candidates")},
             "alg_bytes_per_vertex_step": alg / steps / n0, "hbm_alg_frac": alg / (march_ms * 1e-3) / 1e9 / peak,
             "working_set_mb": round((n0 * (8 * info["mean_degree"] + 8) + 4 * 8 * n0 + 12 * n0) / 1e6, 1),
             "fp32_vs_fp64": err, "fp64_value": n0 * steps / (res["c128"][1] * 1e-3),
@@ -572,6 +579,8 @@ def main():
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-side", action="store_true", help="skip the single-field and adjoint side runs")
     ap.add_argument("--side-steps", type=int, default=200, help="steps of the single-field side runs")
+    ap.add_argument("--side-workloads", default="disk,vortex,adjoint",
+                    help="side runs to make: any of disk (200k single field), vortex (1M), adjoint (300k PCF)")
     ap.add_argument("--variant", choices=["fused", "rows", "pairs"], default="fused",
                     help="fused: the autotuner's choice; pairs: the stage-pair kernel; rows: the row kernel")
     args = ap.parse_args()

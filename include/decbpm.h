@@ -267,6 +267,8 @@ typedef struct {
     int32_t pair_slot_bytes;
     int32_t pair_grid;     /* CTAs of the stage-pair launch */
     int32_t passes;        /* grid-wide passes per step of the stage-pair kernel (last configured dz) */
+    int32_t values_per_thread; /* row kernel: complex values per thread (a row is fields_padded / this lanes) */
+    int32_t rows_per_item; /* row kernel: vertex rows per warp work item */
 } decbpm_plan_config;
 int decbpm_plan_get_config(decbpm_plan_t plan, decbpm_plan_config *cfg);
 
@@ -275,7 +277,8 @@ int decbpm_plan_get_config(decbpm_plan_t plan, decbpm_plan_config *cfg);
  * (1..1000) at step dz on the plan's internal buffers, for every candidate:
  * the stage-pair kernel with 3 or 2 ring slots and the tile-staged kernel
  * with 3 or 2 ring slots (complex64 plans with 9..16 fields), the row kernel
- * with 1..max co-resident CTAs per SM, each with and without the reverse walk
+ * with 1..max co-resident CTAs per SM and (complex64 plans with 4+ fields) 4 or
+ * 2 complex values per thread, each with and without the reverse walk
  * of odd stages; keeps the fastest for this plan and caches it for the
  * process (key: the meshes' content, field counts, precision, dz, kerr_mode),
  * so another plan of the same problem takes it without timing
@@ -292,9 +295,17 @@ typedef struct {
     double  ms_per_step;   /* best trial time per step */
     int32_t candidates;    /* configurations timed (0 when taken from the cache) */
     int32_t from_cache;
+    int32_t values_per_thread; /* row kernel: complex values per thread (complex64 plans of 4+ fields: 4 or 2;
+                                  so rows per warp item = 32 x this / padded fields); others: the default */
 } decbpm_tune_result;
 int decbpm_plan_autotune(decbpm_plan_t plan, double dz, int32_t kerr_mode, int32_t trial_steps, void *stream,
                          decbpm_tune_result *out);
+/* Apply a launch shape without timing (for example one that decbpm_plan_autotune
+ * returned in an earlier process): variant (PAIRS, FUSED = tile-staged, ROWS),
+ * ctas_per_sm and values_per_thread (ROWS), tile_slots (PAIRS, FUSED),
+ * forward_walk; ms_per_step, candidates and from_cache are ignored.  Shapes the
+ * plan cannot run return DECBPM_ERR_UNSUPPORTED or DECBPM_ERR_INVALID_ARG. */
+int decbpm_plan_set_shape(decbpm_plan_t plan, const decbpm_tune_result *shape);
 
 /* Device time in ms, from CUDA events recorded on the launch stream, from the
  * start of the first march-kernel launch to the end of the last one in the

@@ -74,7 +74,8 @@ class PlanConfig(ctypes.Structure):
                 ("tile_slots", ctypes.c_int32), ("tile_slot_bytes", ctypes.c_int32), ("tile_grid", ctypes.c_int32),
                 ("tile_block", ctypes.c_int32), ("tuned", ctypes.c_int32), ("fused_kernel", ctypes.c_int32),
                 ("tile_slots_used", ctypes.c_int32), ("forward_walk", ctypes.c_int32), ("pair_slots", ctypes.c_int32),
-                ("pair_slot_bytes", ctypes.c_int32), ("pair_grid", ctypes.c_int32), ("passes", ctypes.c_int32)]
+                ("pair_slot_bytes", ctypes.c_int32), ("pair_grid", ctypes.c_int32), ("passes", ctypes.c_int32),
+                ("values_per_thread", ctypes.c_int32), ("rows_per_item", ctypes.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -83,7 +84,7 @@ class PlanConfig(ctypes.Structure):
 class TuneResult(ctypes.Structure):
     _fields_ = [("variant", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32), ("tile_slots", ctypes.c_int32),
                 ("forward_walk", ctypes.c_int32), ("ms_per_step", ctypes.c_double), ("candidates", ctypes.c_int32),
-                ("from_cache", ctypes.c_int32)]
+                ("from_cache", ctypes.c_int32), ("values_per_thread", ctypes.c_int32)]
 
     def as_dict(self):
         d = {k: getattr(self, k) for k, _ in self._fields_}
@@ -153,6 +154,7 @@ SIGNATURES = {
     "decbpm_plan_degree": (_i32, [_vp, _i32, _dbl, _i32, _dbl]),
     "decbpm_plan_get_config": (_i32, [_vp, ctypes.POINTER(PlanConfig)]),
     "decbpm_plan_autotune": (_i32, [_vp, _dbl, _i32, _i32, _vp, ctypes.POINTER(TuneResult)]),
+    "decbpm_plan_set_shape": (_i32, [_vp, ctypes.POINTER(TuneResult)]),
     "decbpm_plan_last_march_ms": (_i32, [_vp, ctypes.POINTER(ctypes.c_double)]),
     "decbpm_selftest_barrier": (_i32, [_i32, _i64, _vp]),
     "decbpm_mesh_set_potential": (_i32, [_vp, _c_double_p]),

@@ -265,6 +265,14 @@ class Plan:
                                             int(trial_steps), _stream_handle(stream), ctypes.byref(r)))
         return r.as_dict()
 
+    def set_shape(self, kernel="rows", ctas_per_sm=1, tile_slots=0, forward_walk=0, values_per_thread=0):
+        """decbpm_plan_set_shape: apply a launch shape without timing (kernel
+        "pairs", "tile" or "rows"; e.g. the dict autotune() returned)."""
+        var = {"pairs": L.VARIANT_PAIRS, "tile": L.VARIANT_FUSED, "rows": L.VARIANT_ROWS}[kernel]
+        r = L.TuneResult(variant=var, ctas_per_sm=int(ctas_per_sm), tile_slots=int(tile_slots),
+                         forward_walk=int(forward_walk), values_per_thread=int(values_per_thread))
+        L.check(_lib().decbpm_plan_set_shape(self._h, ctypes.byref(r)))
+
     def config(self) -> dict:
         c = L.PlanConfig()
         L.check(_lib().decbpm_plan_get_config(self._h, ctypes.byref(c)))

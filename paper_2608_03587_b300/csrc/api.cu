@@ -468,8 +468,28 @@ static int ensure_diag_host(decbpm_plan_t P, int n_points) {
 
 static size_t csize(int precision) { return precision == DECBPM_C64 ? 8 : 16; }
 
-// The march kernel is instantiated per padded field count (1..64).
-template <typename R> static const void *march_ptr_for(int bpad) {
+// The march kernel is instantiated per padded field count (1..64) and, for
+// complex64 rows of four or more fields, per complex values per thread (4 or
+// 2; the default is 4): fpt = 0 or the default picks the default instance.
+static int default_fpt(int precision, int bpad) {
+    return precision == DECBPM_C64 ? std::min(bpad, DECBPM_FPT4) : (bpad > 32 ? 2 : 1);
+}
+static bool fpt_allowed(int precision, int bpad, int fpt) {
+    if (fpt == default_fpt(precision, bpad)) return true;
+    return precision == DECBPM_C64 && bpad >= 4 && fpt == 2;
+}
+template <typename R> static const void *march_ptr_for(int bpad, int fpt = 0) {
+    if constexpr (sizeof(R) == 4) {
+        if (fpt == 2 && bpad >= 4) {
+            switch (bpad) {
+                case 4: return (const void *)march_kernel<float, 4, 2>;
+                case 8: return (const void *)march_kernel<float, 8, 2>;
+                case 16: return (const void *)march_kernel<float, 16, 2>;
+                case 32: return (const void *)march_kernel<float, 32, 2>;
+                default: return (const void *)march_kernel<float, 64, 2>;
+            }
+        }
+    }
     switch (bpad) {
         case 1: return (const void *)march_kernel<R, 1>;
         case 2: return (const void *)march_kernel<R, 2>;
@@ -481,8 +501,8 @@ template <typename R> static const void *march_ptr_for(int bpad) {
     }
 }
 
-static const void *march_kernel_ptr(int precision, int bpad) {
-    return precision == DECBPM_C64 ? march_ptr_for<float>(bpad) : march_ptr_for<double>(bpad);
+static const void *march_kernel_ptr(int precision, int bpad, int fpt = 0) {
+    return precision == DECBPM_C64 ? march_ptr_for<float>(bpad, fpt) : march_ptr_for<double>(bpad, fpt);
 }
 
 // Shared-memory ring of the tile-staged march: as many slots (3, else 2) of
@@ -597,8 +617,8 @@ static int plan_create_impl(const decbpm_mesh_t *meshes, int32_t n, const int32_
     P->precision = precision;
     P->bpad_log2 = ilog2(maxB);
     P->bpad = 1 << P->bpad_log2;
-    // complex values per thread; must match Geo<R, BPAD>::FPT of the kernel
-    P->fpt = precision == DECBPM_C64 ? std::min(P->bpad, DECBPM_FPT4) : (P->bpad > 32 ? 2 : 1);
+    // complex values per thread; must match Geo<R, BPAD, FPT>::FPT of the kernel launched
+    P->fpt = default_fpt(precision, P->bpad);
     CK(cudaGetDevice(&P->device));
     CK(cudaDeviceGetAttribute(&P->num_sms, cudaDevAttrMultiProcessorCount, P->device));
     const size_t cs = csize(precision);
@@ -874,7 +894,7 @@ static int launch_march(decbpm_plan_t P, cudaStream_t s, int n_steps, int kerr_m
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     void *args[] = {&mp};
-    const void *fn = march_ptr_for<R>(P->bpad);
+    const void *fn = march_ptr_for<R>(P->bpad, P->fpt);
     if constexpr (sizeof(R) == 4) {
         const bool pairs = P->pair_mode && (variant == DECBPM_VARIANT_PAIRS ||
                                             (variant == DECBPM_VARIANT_FUSED && !P->tune_rows && P->tune_pair == 1));
@@ -1278,7 +1298,7 @@ static int vjp_impl(decbpm_mesh_t mesh, decbpm_plan_t P, const decbpm_params *pr
         cfg.attrs = attr;
         cfg.numAttrs = 1;
         void *args[] = {&mp};
-        CK(cudaLaunchKernelExC(&cfg, march_ptr_for<R>(bpad), args));
+        CK(cudaLaunchKernelExC(&cfg, march_ptr_for<R>(bpad, P->fpt), args));
         return DECBPM_OK;
     };
     const MeshView<R> *fwd_view = reinterpret_cast<const MeshView<R> *>(P->views);
@@ -1629,7 +1649,7 @@ static int soliton_impl(decbpm_mesh_t mesh, decbpm_plan_t P, const decbpm_solito
 // plan's internal buffers (zeroed first: their contents are scratch between
 // calls).  The winner is cached for the process, keyed by the meshes'
 // content fingerprints, the field counts, the precision, dz and kerr_mode.
-struct TuneChoice { int rows, per_sm, slots, forward, pair; double ms; };
+struct TuneChoice { int rows, per_sm, slots, forward, pair, fpt; double ms; };
 static std::mutex g_tune_mutex;
 static std::map<std::string, TuneChoice> g_tune_cache;
 
@@ -1657,6 +1677,12 @@ static std::string tune_key(decbpm_plan_t P, double dz, int kerr_mode) {
 }
 
 static void apply_choice(decbpm_plan_t P, const TuneChoice &c) {
+    const int fpt = c.fpt > 0 ? c.fpt : default_fpt(P->precision, P->bpad);
+    if (fpt != P->fpt) {
+        P->fpt = fpt;
+        P->cfg_dz = 0;           // rows per warp item changed: the stage tables are rebuilt on the next call
+        P->cfg_tol = -1;
+    }
     P->tune_rows = c.rows;
     P->tune_pair = c.pair;
     P->tune_slots = c.slots;
@@ -1676,6 +1702,7 @@ static decbpm_tune_result tune_result(const TuneChoice &c, int trial_steps, int 
     r.ms_per_step = c.ms / trial_steps;
     r.candidates = n_cand;
     r.from_cache = from_cache;
+    r.values_per_thread = c.fpt;
     return r;
 }
 
@@ -1703,12 +1730,19 @@ static int autotune_impl(decbpm_plan_t P, double dz, int kerr_mode, int trial_st
         if (P->pair_mode) CK(cudaMemsetAsync(P->b3[i], 0, bytes, s));
     }
     std::vector<TuneChoice> cand;
+    const int fpt0 = default_fpt(P->precision, P->bpad);
     for (int fw = 0; fw <= 1; ++fw) {
         if (P->pair_mode)
-            for (int sl = P->pair_slots; sl >= 2; --sl) cand.push_back({0, 1, sl, fw, 1, 0.0});
+            for (int sl = P->pair_slots; sl >= 2; --sl) cand.push_back({0, 1, sl, fw, 1, fpt0, 0.0});
         if (P->tile_mode)
-            for (int sl = P->n_slots; sl >= 2; --sl) cand.push_back({0, P->max_per_sm, sl, fw, 0, 0.0});
-        for (int ps = 1; ps <= P->max_per_sm; ++ps) cand.push_back({1, ps, 0, fw, 0, 0.0});
+            for (int sl = P->n_slots; sl >= 2; --sl) cand.push_back({0, P->max_per_sm, sl, fw, 0, fpt0, 0.0});
+        std::vector<int> fpts = {fpt0};
+        if (fpt0 == 4 && fpt_allowed(P->precision, P->bpad, 2)) fpts.push_back(2);
+        for (int fpt : fpts) {
+            int occ = 0;
+            CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, march_kernel_ptr(P->precision, P->bpad, fpt), P->block, 0));
+            for (int ps = 1; ps <= std::min(occ, 4); ++ps) cand.push_back({1, ps, 0, fw, 0, fpt, 0.0});
+        }
     }
     cudaEvent_t e0, e1;
     CK(cudaEventCreate(&e0));
@@ -1718,6 +1752,8 @@ static int autotune_impl(decbpm_plan_t P, double dz, int kerr_mode, int trial_st
     int rc = DECBPM_OK;
     for (TuneChoice &c : cand) {
         apply_choice(P, c);
+        rc = plan_configure<R>(P, dz, P->precision == DECBPM_C64 ? 1e-9 : 1e-16);
+        if (rc != DECBPM_OK) break;
         if (cudaMemsetAsync(P->status, 0, sizeof(int), s) != cudaSuccess) { rc = fail(DECBPM_ERR_CUDA, "memset failed"); break; }
         double t_best = 1e300;
         for (int rep = 0; rep < 3 && rc == DECBPM_OK; ++rep) {
@@ -2248,6 +2284,39 @@ int decbpm_plan_autotune(decbpm_plan_t P, double dz, int32_t kerr_mode, int32_t 
     return autotune_impl<double>(P, dz, kerr_mode, trial_steps, (cudaStream_t)stream, out);
 }
 
+int decbpm_plan_set_shape(decbpm_plan_t P, const decbpm_tune_result *shape) {
+    clear_error();
+    if (!P || !shape) return fail(DECBPM_ERR_INVALID_ARG, "NULL argument");
+    TuneChoice c{};
+    c.forward = shape->forward_walk ? 1 : 0;
+    c.fpt = shape->values_per_thread > 0 ? shape->values_per_thread : default_fpt(P->precision, P->bpad);
+    if (shape->variant == DECBPM_VARIANT_PAIRS) {
+        if (!P->pair_mode) return fail(DECBPM_ERR_UNSUPPORTED, "this plan cannot run the stage-pair kernel");
+        if (shape->tile_slots < 2 || shape->tile_slots > P->pair_slots)
+            return fail(DECBPM_ERR_INVALID_ARG, "tile_slots must be in 2..%d", P->pair_slots);
+        c.pair = 1; c.per_sm = 1; c.slots = shape->tile_slots;
+        c.fpt = default_fpt(P->precision, P->bpad);
+    } else if (shape->variant == DECBPM_VARIANT_FUSED) {
+        if (!P->tile_mode) return fail(DECBPM_ERR_UNSUPPORTED, "this plan cannot run the tile-staged kernel");
+        if (shape->tile_slots < 2 || shape->tile_slots > P->n_slots)
+            return fail(DECBPM_ERR_INVALID_ARG, "tile_slots must be in 2..%d", P->n_slots);
+        c.slots = shape->tile_slots; c.per_sm = P->max_per_sm;
+        c.fpt = default_fpt(P->precision, P->bpad);
+    } else if (shape->variant == DECBPM_VARIANT_ROWS) {
+        if (!fpt_allowed(P->precision, P->bpad, c.fpt))
+            return fail(DECBPM_ERR_UNSUPPORTED, "values_per_thread %d is not built for this plan", c.fpt);
+        int occ = 0;
+        CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, march_kernel_ptr(P->precision, P->bpad, c.fpt), P->block, 0));
+        if (shape->ctas_per_sm < 1 || shape->ctas_per_sm > std::min(occ, 4))
+            return fail(DECBPM_ERR_INVALID_ARG, "ctas_per_sm must be in 1..%d", std::min(occ, 4));
+        c.rows = 1; c.per_sm = shape->ctas_per_sm;
+    } else {
+        return fail(DECBPM_ERR_INVALID_ARG, "bad variant %d", shape->variant);
+    }
+    apply_choice(P, c);
+    return DECBPM_OK;
+}
+
 int decbpm_mesh_set_pml(decbpm_mesh_t mesh, const decbpm_pml *pml) {
     clear_error();
     if (!mesh) return fail(DECBPM_ERR_INVALID_ARG, "mesh is NULL");
@@ -2283,6 +2352,8 @@ int decbpm_plan_get_config(decbpm_plan_t P, decbpm_plan_config *cfg) {
     cfg->pair_slot_bytes = P->pair_mode ? P->pair_slot_bytes : 0;
     cfg->pair_grid = P->pair_mode ? P->pair_grid : 0;
     cfg->passes = P->pair_mode ? P->n_passes : 0;
+    cfg->values_per_thread = P->fpt;
+    cfg->rows_per_item = 32 * P->fpt / P->bpad;
     return DECBPM_OK;
 }
 

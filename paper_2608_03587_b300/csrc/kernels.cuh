@@ -323,11 +323,15 @@ __device__ __forceinline__ int mesh_of_item(const int32_t *s_begin, int n_meshes
 // FPT complex values per thread, TPR threads per row, RPW rows per warp item.
 // A row's operator entries j < 8 live in registers of the row's lanes: entry j
 // in lane (j % TPR) of the row group, slot j / TPR (E slots per lane).
-template <typename R, int BPAD> struct Geo {
-    // complex64: four per thread (32-byte accesses) from four fields on, two
-    // (16-byte) for two or three; complex128: one (already 16 bytes) unless a
-    // row needs more than a warp
-    static constexpr int FPT = sizeof(R) == 4 ? (BPAD < DECBPM_FPT4 ? BPAD : DECBPM_FPT4) : (BPAD > 32 ? 2 : 1);
+// Default complex values per thread: complex64 four (32-byte accesses) from
+// four fields on, two (16-byte) for two or three; complex128 one (already 16
+// bytes) unless a row needs more than a warp.  FPT_ > 0 overrides it (the
+// autotuner's "values per thread" dimension; rows per warp item follow).
+template <typename R, int BPAD> constexpr int default_fpt() {
+    return sizeof(R) == 4 ? (BPAD < DECBPM_FPT4 ? BPAD : DECBPM_FPT4) : (BPAD > 32 ? 2 : 1);
+}
+template <typename R, int BPAD, int FPT_ = 0> struct Geo {
+    static constexpr int FPT = FPT_ > 0 ? FPT_ : default_fpt<R, BPAD>();
     static constexpr int FPT_LOG2 = FPT == 8 ? 3 : FPT == 4 ? 2 : FPT == 2 ? 1 : 0;
     static constexpr int NB = FPT >= 8 ? 2 : FPT >= 4 ? 4 : 8;     // neighbour gathers in flight per batch
     static constexpr int TPR = BPAD / FPT;
@@ -347,10 +351,10 @@ template <typename R, int E> struct ItemMeta {
 
 // Metadata of plan-global item `it`: row, slice offsets and this lane's
 // share of the row's (column, weight) entries.
-template <typename R, int BPAD>
+template <typename R, int BPAD, int FPT_ = 0>
 __device__ __forceinline__ void load_meta(const MeshView<R> *sv, const int32_t *s_begin, int n_meshes, int it,
-                                          ItemMeta<R, Geo<R, BPAD>::E> &mt) {
-    using G = Geo<R, BPAD>;
+                                          ItemMeta<R, Geo<R, BPAD, FPT_>::E> &mt) {
+    using G = Geo<R, BPAD, FPT_>;
     const int lane = threadIdx.x & 31;
     int mi = 0;
     while (mi + 1 < n_meshes && it >= s_begin[mi + 1]) ++mi;
@@ -382,11 +386,11 @@ __device__ __forceinline__ void load_meta(const MeshView<R> *sv, const int32_t *
 // Each warp walks its items as a two-deep software pipeline: the next item's
 // operator metadata is requested while the current item's neighbour gathers
 // are in flight, so one memory latency (not three) is exposed per item.
-template <typename R, int BPAD>
+template <typename R, int BPAD, int FPT_ = 0>
 __device__ __forceinline__ void clenshaw_stage(const MeshView<R> *sv, const StageCoef<R> *scoef, const int32_t *s_begin,
                                                int n_meshes, int n_active, int k, R h_post, int kerr_mode,
                                                bool rev_odd) {
-    using G = Geo<R, BPAD>;
+    using G = Geo<R, BPAD, FPT_>;
     using C = typename CT<R>::c2;
     constexpr int FPT = G::FPT;
     const int lane = threadIdx.x & 31;
@@ -402,7 +406,7 @@ __device__ __forceinline__ void clenshaw_stage(const MeshView<R> *sv, const Stag
     auto item_at = [&](int i) { return rev ? hi - 1 - i : lo + i; };
     int idx = warp;
     ItemMeta<R, G::E> cur;
-    if (idx < n_mine) load_meta<R, BPAD>(sv, s_begin, n_meshes, item_at(idx), cur);
+    if (idx < n_mine) load_meta<R, BPAD, FPT_>(sv, s_begin, n_meshes, item_at(idx), cur);
     while (idx < n_mine) {
         const int nidx = idx + nwarps;
         const MeshView<R> &m = sv[cur.mi];
@@ -442,7 +446,7 @@ __device__ __forceinline__ void clenshaw_stage(const MeshView<R> *sv, const Stag
                     gq[jj] = ld_pack<R, FPT>(g + (size_t)qj * BPAD + fo);
                 }
             }
-            if (j0 == 0 && nidx < n_mine) load_meta<R, BPAD>(sv, s_begin, n_meshes, item_at(nidx), nm);
+            if (j0 == 0 && nidx < n_mine) load_meta<R, BPAD, FPT_>(sv, s_begin, n_meshes, item_at(nidx), nm);
 #pragma unroll
             for (int jj = 0; jj < G::NB; ++jj)
                 if (j0 + jj < cur.width) {
@@ -605,9 +609,9 @@ __device__ __forceinline__ void for_my_items(const MarchParams<R> &P, const int3
 #endif
 template <typename R> struct MarchMinBlocks { static constexpr int value = sizeof(R) == 8 ? DECBPM_MARCH_MINB64 : DECBPM_MARCH_MINB; };
 
-template <typename R, int BPAD>
+template <typename R, int BPAD, int FPT_ = 0>
 __global__ void __launch_bounds__(256, MarchMinBlocks<R>::value) march_kernel(MarchParams<R> P) {
-    constexpr int FPT = Geo<R, BPAD>::FPT;
+    constexpr int FPT = Geo<R, BPAD, FPT_>::FPT;
     __shared__ int32_t s_begin[kMaxMeshes + 1];
     __shared__ MeshView<R> s_view[kMaxMeshes];
     __shared__ StageCoef<R> s_coef[kMaxMeshes];
@@ -618,7 +622,7 @@ __global__ void __launch_bounds__(256, MarchMinBlocks<R>::value) march_kernel(Ma
     __syncthreads();
     unsigned long long target = 0;
     const R h = P.h, hh = P.h * R(0.5);
-    const int bl = Geo<R, BPAD>::TPR_LOG2 + Geo<R, BPAD>::FPT_LOG2;
+    const int bl = Geo<R, BPAD, FPT_>::TPR_LOG2 + Geo<R, BPAD, FPT_>::FPT_LOG2;
     for (int step = 0; step < P.n_steps; ++step) {
         if (step == 0 && P.pre_half) {
             if (P.kerr_mode == 0) {
@@ -643,8 +647,8 @@ __global__ void __launch_bounds__(256, MarchMinBlocks<R>::value) march_kernel(Ma
             for (int i = threadIdx.x; i < P.n_meshes; i += blockDim.x)
                 if (s_view[i].M > k) s_coef[i] = s_view[i].coef[k];
             __syncthreads();
-            clenshaw_stage<R, BPAD>(s_view, s_coef, s_begin, P.n_meshes, P.active_items[s], k, h_post, P.kerr_mode,
-                                    P.forward_walk == 0);
+            clenshaw_stage<R, BPAD, FPT_>(s_view, s_coef, s_begin, P.n_meshes, P.active_items[s], k, h_post,
+                                          P.kerr_mode, P.forward_walk == 0);
             if (!grid_barrier(P.barrier, target, P.status, P.timeout_ns)) return;
         }
         if (P.kerr_mode != 0) {

@@ -427,6 +427,45 @@ def test_autotuner_picks_a_shape_without_changing_results(precision):
         plan.autotune(-1.0)
 
 
+@pytest.mark.parametrize("B", [4, 8, 16])
+def test_every_launch_shape_gives_the_same_fields(B):
+    """decbpm_plan_set_shape forces each single-stage launch shape the
+    autotuner searches (row kernel with 4 or 2 complex values per thread, i.e.
+    8B/4B.. rows per warp item, 1..max CTAs per SM, either walk; the
+    tile-staged kernel with 3 or 2 slots): every one gives the default shape's
+    fields bit for bit; shapes a plan cannot run are refused."""
+    specs = [(3000, 61), (700, 62)]
+    meshes, psis = [], []
+    for n, seed in specs:
+        coords, tris = W.mesh_disk_graded(4.0, n, 3.0, interfaces=(1.0,), seed=seed, grade_from=1.0)
+        V, chi = W.step_index_materials(coords, tris)
+        sigma = W.absorber_profile(coords, 4.0, 20.0)
+        meshes.append(api.Mesh(coords, tris, V, chi, sigma))
+        psis.append(W.hg_superpositions(coords, B, np.random.default_rng(seed)))
+    plan = api.Plan(meshes, [B] * len(specs), "c64")
+    ref = [to_dev(p, torch.complex64) for p in psis]
+    plan.propagate(ref, 1e-3, 5, variant="rows")
+    shapes = [dict(kernel="rows", ctas_per_sm=c, values_per_thread=v, forward_walk=f)
+              for v in (4, 2) for c in (1, 2) for f in (0, 1)]
+    if B == 16:
+        shapes += [dict(kernel="tile", tile_slots=t) for t in (2, 3)]
+    for sh in shapes:
+        plan.set_shape(**sh)
+        cfg = plan.config()
+        if sh["kernel"] == "rows":
+            assert cfg["values_per_thread"] == sh["values_per_thread"]
+            assert cfg["rows_per_item"] == 32 * sh["values_per_thread"] // B
+        out = [to_dev(p, torch.complex64) for p in psis]
+        plan.propagate(out, 1e-3, 5)
+        for x, y in zip(out, ref):
+            assert torch.equal(x, y), sh
+    with pytest.raises(L.DecbpmError):
+        plan.set_shape(kernel="rows", values_per_thread=8)
+    if B != 16:
+        with pytest.raises(L.DecbpmError):
+            plan.set_shape(kernel="tile", tile_slots=2)
+
+
 # ------------------------------------------------------------------ edge cases
 def test_single_triangle_and_tiny_meshes():
     coords = np.array([[0.0, 0.0], [1.0, 0.0], [0.2, 0.9]])
