@@ -123,3 +123,53 @@ class StretchedOperators:
         for j in range(3):
             np.add.at(self.H0, cells[:, j], meas / 3.0)
         self.rho = float(np.max(np.asarray(abs(self.A).sum(axis=1)).ravel()))
+
+
+# --------------------------------------------------------------------------
+# split-step march with the layer
+# --------------------------------------------------------------------------
+def diagonal_flow_stretched(ops, psi, h, sigma=None):
+    """Exact flow over h of dpsi_p/dz = i (v_p + chib_p |psi_p|^2) psi_p - sigma_p psi_p
+    with the complex lumped v and chib of the stretched metric (lumped Kerr).
+
+    The intensity I = |psi|^2 obeys dI/dz = -alpha I - beta I^2 with
+    alpha = 2 (Im v + sigma), beta = 2 Im chib (a Bernoulli equation):
+        I(h) = I0 e^{-alpha h} / D,   D = 1 + beta I0 q,   q = (1 - e^{-alpha h}) / alpha,
+    and the phase is the integral of Re v + Re chib I(z):
+        theta = Re v h + Re chib ln(D) / beta   (-> Re chib I0 q as beta -> 0),
+    so psi(h) = psi0 sqrt(e^{-alpha h} / D) e^{i theta}.  With real v and chib
+    this is the flow of bpm.diagonal_flow."""
+    n0 = ops.n0
+    sigma = np.zeros(n0) if sigma is None else np.asarray(sigma, dtype=np.float64)
+    psi = np.asarray(psi, dtype=np.complex128)
+    v = np.asarray(ops.v, dtype=np.complex128)
+    c = np.asarray(ops.chib, dtype=np.complex128)
+    if psi.ndim == 2:
+        v, c, sigma = v[:, None], c[:, None], sigma[:, None]
+    I0 = np.abs(psi) ** 2
+    alpha = 2.0 * (v.imag + sigma)
+    beta = 2.0 * c.imag
+    ah = alpha * h
+    with np.errstate(divide="ignore", invalid="ignore"):
+        q = np.where(np.abs(ah) > 1e-300, -np.expm1(-ah) / np.where(alpha == 0, 1.0, alpha), h)
+        x = beta * I0 * q
+        # ln(1 + x) / beta = I0 q log1p(x) / x, the ratio -> 1 as x -> 0
+        ratio = np.where(np.abs(x) > 1e-300, np.log1p(x) / np.where(x == 0, 1.0, x), 1.0)
+    integral = I0 * q * ratio
+    theta = v.real * h + c.real * integral
+    amp = np.sqrt(np.exp(-ah) / (1.0 + x))
+    return psi * amp * np.exp(1j * theta)
+
+
+def propagate_stretched(ops, p, psi0, h, n_steps, sigma=None):
+    """n_steps Strang steps D_{h/2} E_h D_{h/2} on the stretched operators:
+    E_h = exp(-i h L_diff) with the complex A~ (bpm.linear_step, Taylor with
+    substeps: the series holds for any matrix), D the flow above.  Half steps
+    are applied as written (no merging)."""
+    from . import bpm
+    psi = np.array(psi0, dtype=np.complex128, copy=True)
+    for _ in range(n_steps):
+        psi = diagonal_flow_stretched(ops, psi, 0.5 * h, sigma)
+        psi = bpm.linear_step(ops, p, psi, h)
+        psi = diagonal_flow_stretched(ops, psi, 0.5 * h, sigma)
+    return psi

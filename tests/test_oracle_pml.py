@@ -106,3 +106,61 @@ def test_layer_absorbs_an_outgoing_beam():
         errs[name] = np.sqrt(np.sum(w * np.abs(small[inner] - ref[inner]) ** 2) / np.sum(ops.H0 * np.abs(psi0) ** 2))
     assert errs["neumann"] > 0.3, errs
     assert errs["pml"] < 0.03 and errs["pml"] < 0.05 * errs["neumann"], errs
+
+
+def test_stretched_diagonal_flow_matches_ode_integration(fiber):
+    """The exact flow with complex lumped v and chib (Bernoulli equation for
+    the intensity, closed-form phase integral) against DOP853 on the vertex
+    ODE dpsi/dz = i (v + chib |psi|^2) psi - sigma psi, with damping and
+    gaining imaginary parts and an absorber; and equal to bpm.diagonal_flow
+    when the coefficients are real."""
+    from scipy.integrate import solve_ivp
+    coords, tris, V, chi = fiber
+    ops = pml.StretchedOperators(coords, tris, V, chi, r_in=3.0, R=4.0, sigma_max=2.0, order=2)
+    rng = np.random.default_rng(5)
+    n = 12
+    idx = rng.choice(ops.n0, n, replace=False)
+    class Fake:
+        pass
+    f = Fake()
+    f.n0 = n
+    f.v = rng.uniform(-8, 3, n) + 1j * rng.uniform(-0.5, 2.0, n)
+    f.chib = rng.uniform(0.2, 1.5, n) + 1j * rng.uniform(-0.05, 0.4, n)
+    sigma = np.where(rng.random(n) < 0.5, rng.uniform(0.0, 5.0, n), 0.0)
+    psi = (rng.standard_normal(n) + 1j * rng.standard_normal(n)) * 1.2
+    h = 0.09
+    out = pml.diagonal_flow_stretched(f, psi, h, sigma)
+    for p in range(n):
+        def rhs(_z, y, p=p):
+            c = y[0] + 1j * y[1]
+            d = 1j * (f.v[p] + f.chib[p] * abs(c) ** 2) * c - sigma[p] * c
+            return [d.real, d.imag]
+        sol = solve_ivp(rhs, (0, h), [psi[p].real, psi[p].imag], method="DOP853", rtol=1e-13, atol=1e-15)
+        ref = sol.y[0, -1] + 1j * sol.y[1, -1]
+        assert abs(out[p] - ref) <= 1e-10 * abs(psi[p]), p
+    plain = dec.Operators(coords, tris, V, chi)
+    psi2 = (rng.standard_normal(plain.n0) + 1j * rng.standard_normal(plain.n0)) * 1.5
+    sig2 = W.absorber_profile(coords, 4.0, 6.0)
+    a = pml.diagonal_flow_stretched(plain, psi2, 0.05, sig2)
+    b = bpm.diagonal_flow(plain, psi2, 0.05, sig2)
+    assert np.max(np.abs(a - b)) <= 1e-14 * np.max(np.abs(psi2))
+    _ = idx
+
+
+def test_split_step_with_layer_converges_to_the_rk45_integration(fiber):
+    """The Strang march on the stretched operators converges at second order
+    in dz to the oracle's Dormand-Prince integration of the same equation
+    with the layer (linear and Kerr launches)."""
+    coords, tris, V, chi = fiber
+    ops = pml.StretchedOperators(coords, tris, V, chi, r_in=3.0, R=4.0, sigma_max=4.0, order=2)
+    x, y = coords[:, 0], coords[:, 1]
+    psi0 = 2.0 * np.exp(-((x - 0.3) ** 2 + y ** 2) / 0.5 + 3.0j * x)
+    z = 0.02
+    ref, _ = bpm.dopri5(ops, (1.0,), psi0, z, rtol=1e-12, atol=1e-14)
+    errs = []
+    for n in (10, 20, 40):
+        out = pml.propagate_stretched(ops, (1.0,), psi0, z / n, n)
+        errs.append(bpm.relative_error(ops, out, ref))
+    assert errs[-1] < 1e-4
+    for e1, e2 in zip(errs, errs[1:]):
+        assert 3.3 < e1 / e2 < 4.8, errs
