@@ -413,12 +413,16 @@ int decbpm_bessel_i_scaled(double a, double tol, int32_t n_max, double *out, int
  * inner product of *1 (Eq. 9) takes the tensor (r~/(s r)) e_r e_r^T +
  * (s r/r~) e_t e_t^T, s = 1 + i sigma, and *0 the factor s r~ / r; v and chib
  * keep their lumped definitions with the stretched *0.  FP64, assembled on the
- * host.  Once set, the mesh runs with decbpm_rk45 (lumped Kerr) only: every
- * split-step entry point returns DECBPM_ERR_UNSUPPORTED, because the
- * stretched operator's spectrum leaves the real axis by up to ~2 sigma rho
- * and the Chebyshev series of exp(-i h A) evaluated by Clenshaw then
- * amplifies rounding by about e^{2 h sigma rho}.  pml = NULL or sigma_max = 0
- * removes the layer.  2D meshes only. */
+ * host.  Once set, the mesh runs with decbpm_rk45 (lumped Kerr) and with
+ * decbpm_propagate for one complex128 field, lumped Kerr and p_1 only: the
+ * Strang split-step on the stretched operators, E_h by the Chebyshev series
+ * of exp(-i a x) evaluated on the complex spectrum (degree from the Bernstein
+ * ellipse of the Gershgorin box of A~), D_h the exact flow with the complex
+ * v and chib (their imaginary parts damp the intensity by a Bernoulli
+ * equation); unfused FP64 launches.  Every other split-step entry point
+ * (plans, batches, complex64, the adjoint, the soliton solver, the
+ * allocation-free call) returns DECBPM_ERR_UNSUPPORTED.  pml = NULL or
+ * sigma_max = 0 removes the layer.  2D meshes only. */
 typedef struct { double x0, y0, r_inner, r_outer, sigma_max; int32_t order; } decbpm_pml;
 int decbpm_mesh_set_pml(decbpm_mesh_t mesh, const decbpm_pml *pml);
 

@@ -94,6 +94,8 @@ struct decbpm_mesh_s {
     // PML (complex-stretched metric): SELL weights a_pq = -K~_pq / m~_p and lumped v, chib
     bool pml_on = false;
     double2 *pml_a = nullptr, *pml_v = nullptr, *pml_chib = nullptr;
+    // Gershgorin region of A~ (the union of the discs |z - sum_q a_pq| <= sum_q |a_pq|) as a box
+    double pml_re_lo = 0, pml_re_hi = 0, pml_im_lo = 0, pml_im_hi = 0;
     // tile maps of the tile-staged march (built on first use)
     bool tiles_ready = false, tiles_ok = false;
     uint16_t *lcol = nullptr;
@@ -449,7 +451,10 @@ struct decbpm_plan_s {
     }
 };
 
-static int reject_pml(decbpm_mesh_t m);        // meshes with a PML run the RK45 integrator only
+static int reject_pml(decbpm_mesh_t m);        // meshes with a PML run decbpm_propagate (one C128 field) and RK45 only
+extern "C" {
+static int single_plan(decbpm_mesh_t mesh, int64_t n_fields, int32_t precision, decbpm_plan_t *P);
+}
 static int reject_pml_plan(decbpm_plan_t P);
 
 // Pinned host buffer for diagnostics of n_points points; graphs hold its
@@ -1802,8 +1807,8 @@ static int autotune_impl(decbpm_plan_t P, double dz, int kerr_mode, int trial_st
 static int reject_pml(decbpm_mesh_t m) {
     if (m && m->pml_on)
         return fail(DECBPM_ERR_UNSUPPORTED,
-                    "this mesh has a PML: it runs with decbpm_rk45 only (the split-step's Chebyshev series of "
-                    "exp(-i h A) is not stable on the complex spectrum of the stretched operator)");
+                    "this mesh has a PML: it runs with decbpm_propagate (one complex128 field, lumped Kerr, p_1) "
+                    "and decbpm_rk45 only");
     return DECBPM_OK;
 }
 static int reject_pml_plan(decbpm_plan_t P) {
@@ -1888,6 +1893,23 @@ static int set_pml_impl(decbpm_mesh_t M, const decbpm_pml *o) {
         vv[i] = make_double2(v.real(), v.imag());
         cc[i] = make_double2(c.real(), c.imag());
     }
+    // Gershgorin discs of A~ in internal order: centre sum_q a_pq, radius sum_q |a_pq|
+    double re_lo = 1e300, re_hi = -1e300, im_lo = 1e300, im_hi = -1e300;
+    for (int64_t row = 0; row < n0; ++row) {
+        const int64_t sl = row / kSlice, lane = row % kSlice;
+        cd z = 0.0;
+        double rad = 0.0;
+        for (int j = 0; j < S.slice_w[sl]; ++j) {
+            const double2 a = a_sell[S.slice_ptr[sl] + int64_t(j) * kSlice + lane];
+            z += cd(a.x, a.y);
+            rad += std::hypot(a.x, a.y);
+        }
+        re_lo = std::min(re_lo, z.real() - rad);
+        re_hi = std::max(re_hi, z.real() + rad);
+        im_lo = std::min(im_lo, z.imag() - rad);
+        im_hi = std::max(im_hi, z.imag() + rad);
+    }
+    M->pml_re_lo = re_lo; M->pml_re_hi = re_hi; M->pml_im_lo = im_lo; M->pml_im_hi = im_hi;
     if (!M->pml_a) {
         TRY(M->mem.alloc(&M->pml_a, a_sell.size()));
         TRY(M->mem.alloc(&M->pml_v, size_t(n0)));
@@ -1898,6 +1920,107 @@ static int set_pml_impl(decbpm_mesh_t M, const decbpm_pml *o) {
     CK(cudaMemcpy(M->pml_chib, cc.data(), sizeof(double2) * n0, cudaMemcpyHostToDevice));
     M->pml_on = true;
     return DECBPM_OK;
+}
+
+// ============================================================== split-step with a PML
+// The Strang march on the complex-stretched operators (one complex128 field,
+// lumped Kerr, p_1 only), unfused: one stage launch per Chebyshev term and a
+// launch per diagonal flow.  E_h = exp(-i h p1 A~) is the Chebyshev series of
+// exp(-i a x), a = h p1 r, in x = (lambda - c) / r over the real extent
+// [c - r, c + r] of the Gershgorin region of A~; the series of this entire
+// function converges on the complex spectrum too, and its degree is the
+// smallest M whose tail sum_{k>M} 2 |J_k(a)| rho_e^k is below tol, rho_e the
+// largest Bernstein-ellipse parameter of the region's box (so the truncation
+// holds on every eigenvalue the box contains).
+static int propagate_plain_pml(decbpm_mesh_t m, const decbpm_params *prm, void *psi_dev, cudaStream_t s,
+                               decbpm_diag *diag_out) {
+    using cd = std::complex<double>;
+    if (prm->precision != DECBPM_C128) return fail(DECBPM_ERR_UNSUPPORTED, "with a PML the split-step runs complex128");
+    if (prm->kerr_mode != DECBPM_KERR_LUMPED) return fail(DECBPM_ERR_UNSUPPORTED, "with a PML the split-step takes lumped Kerr");
+    if (m->A.p.size() != 1) return fail(DECBPM_ERR_UNSUPPORTED, "with a PML the split-step takes p_1 only");
+    const int n0 = int(m->A.n0);
+    const double p1 = m->A.p[0];
+    const double lo = m->pml_re_lo, hi = m->pml_re_hi;
+    const double c = 0.5 * (lo + hi), r = 0.5 * (hi - lo);
+    if (!(r > 0)) return fail(DECBPM_ERR_BAD_MESH, "PML operator has an empty spectral box");
+    // largest Bernstein-ellipse parameter over the boundary of the box
+    double rho_e = 1.0;
+    const double ylo = m->pml_im_lo / r, yhi = m->pml_im_hi / r;
+    auto bern = [](cd x) {
+        const cd w = x + std::sqrt(x * x - 1.0);
+        return std::max(std::abs(w), 1.0 / std::abs(w));
+    };
+    for (int i = 0; i <= 400; ++i) {
+        const double t = -1.0 + 2.0 * i / 400.0, u = ylo + (yhi - ylo) * i / 400.0;
+        rho_e = std::max({rho_e, bern(cd(t, ylo)), bern(cd(t, yhi)), bern(cd(-1.0, u)), bern(cd(1.0, u))});
+    }
+    rho_e *= 1.01;
+    const double a = prm->dz * p1 * r;
+    const double tol = default_tol(prm);
+    int kmax = int(std::fabs(a) * rho_e + 60 + 12 * std::cbrt(std::fabs(a) + 1.0));
+    int M = 0;
+    std::vector<double> J;
+    for (;; kmax *= 2) {
+        if (kmax > 200000) return fail(DECBPM_ERR_UNSUPPORTED, "Chebyshev degree on the PML spectrum too large (reduce dz)");
+        J.assign(kmax + 1, 0.0);
+        bessel_sequence(std::fabs(a), kmax, J.data());
+        std::vector<double> tail(kmax + 2, 0.0);
+        for (int k = kmax; k >= 0; --k) tail[k] = tail[k + 1] + 2.0 * std::fabs(J[k]) * std::pow(rho_e, k);
+        M = 0;
+        while (M < kmax && tail[M + 1] > tol) ++M;
+        if (M < kmax - 20) break;
+    }
+    M = std::max(M, 2);
+    std::vector<cd> coef(M + 1);
+    for (int k = 0; k <= M; ++k) {
+        const double jk = J[k] * ((a < 0 && (k & 1)) ? -1.0 : 1.0) * (k == 0 ? 1.0 : 2.0);
+        coef[k] = std::pow(cd(0.0, -1.0), k) * jk;
+    }
+    const double theta0 = -prm->dz * p1 * c;        // exp(-i h p1 lambda) = e^{i theta0} sum_k coef_k T_k(x)
+    decbpm_plan_t P = nullptr;
+    TRY(single_plan(m, 1, DECBPM_C128, &P));
+    if (P->order.empty()) TRY(plan_configure<double>(P, prm->dz, default_tol(prm)));   // buffers and the device view
+    MeshView<double> mv{};
+    CK(cudaMemcpy(&mv, P->views, sizeof(mv), cudaMemcpyDeviceToHost));
+    const PmlOps po{mv.slice_ptr, mv.slice_w, mv.col, m->pml_a, m->pml_v, m->pml_chib, m->sig64, n0};
+    double2 *psi = (double2 *)P->psi[0];
+    double2 *b[3] = {(double2 *)P->b0[0], (double2 *)P->b1[0], (double2 *)P->b2[0]};
+    const int n_points = n_diag_points(prm);
+    TRY(ensure_diag_host(P, n_points));
+    const int T = 256, G = (n0 + T - 1) / T;
+    permute_in_kernel<double2><<<std::min(G, 4 * P->num_sms), T, 0, s>>>((const double2 *)psi_dev, psi, m->perm, n0, 1, 1);
+    const int64_t every = prm->diag_every > 0 ? prm->diag_every : std::max<int64_t>(prm->n_steps, 1);
+    int point = 0;
+    auto d2 = [](cd z) { return make_double2(z.real(), z.imag()); };
+    CK(cudaEventRecord(P->ev0, s));
+    for (int64_t step = 0; step < prm->n_steps; ++step) {
+        const bool block_start = (step % every) == 0;
+        const bool block_end = ((step + 1) % every) == 0 || step + 1 == prm->n_steps;
+        if (block_start) pml_diag_kernel<<<G, T, 0, s>>>(psi, m->pml_v, m->pml_chib, m->sig64, 0.5 * prm->dz, n0);
+        for (int k = M - 1; k >= 0; --k) {
+            cd alpha = coef[k], beta = (k == 0) ? 1.0 : 2.0;
+            const double2 *g = b[(k + 1) % 3], *hh = b[(k + 2) % 3];
+            if (k == M - 1) { g = psi; beta = 2.0 * coef[M]; hh = nullptr; }
+            else if (k == M - 2) { alpha = coef[k] - coef[M]; hh = nullptr; }
+            double2 *outp = (k == 0) ? psi : b[k % 3];
+            pml_stage_kernel<<<G, T, 0, s>>>(po, psi, g, hh, outp, c, 1.0 / r, d2(alpha), d2(beta));
+        }
+        pml_diag_kernel<<<G, T, 0, s>>>(psi, m->pml_v, m->pml_chib, m->sig64, block_end ? 0.5 * prm->dz : prm->dz, n0);
+        if (block_end) {
+            if (step + 1 == prm->n_steps) CK(cudaEventRecord(P->ev1, s));
+            TRY(launch_diag<double>(P, s, DECBPM_KERR_LUMPED, point++));
+        }
+    }
+    if (prm->n_steps == 0) {
+        CK(cudaEventRecord(P->ev1, s));
+        TRY(launch_diag<double>(P, s, DECBPM_KERR_LUMPED, point++));
+    }
+    const double ph = std::fmod(double(prm->n_steps) * theta0, 2.0 * M_PI);
+    permute_out_kernel<double2><<<std::min(G, 4 * P->num_sms), T, 0, s>>>(psi, (double2 *)psi_dev, m->perm, n0, 1, 1,
+                                                                         std::cos(ph), std::sin(ph));
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(s));
+    return finish_diag(P, prm, n_points, diag_out);
 }
 
 // ============================================================== C ABI
@@ -2046,7 +2169,10 @@ int decbpm_propagate(decbpm_mesh_t mesh, const decbpm_params *params, void *psi_
     clear_error();
     if (!mesh || !psi_dev) return fail(DECBPM_ERR_INVALID_ARG, "mesh and psi_dev are required");
     TRY(check_params(params));
-    TRY(reject_pml(mesh));
+    if (mesh->pml_on) {
+        if (n_fields != 1) return fail(DECBPM_ERR_UNSUPPORTED, "with a PML the split-step runs one field");
+        return propagate_plain_pml(mesh, params, psi_dev, (cudaStream_t)stream, diag_out);
+    }
     if (params->variant == DECBPM_VARIANT_PLAIN) {
         if (n_fields != 1) return fail(DECBPM_ERR_UNSUPPORTED, "the plain variant runs one field");
         if (params->kerr_mode != DECBPM_KERR_LUMPED) return fail(DECBPM_ERR_UNSUPPORTED, "the plain variant runs lumped Kerr");

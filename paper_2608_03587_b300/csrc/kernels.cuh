@@ -2134,6 +2134,50 @@ __global__ void rk_rhs_pml_kernel(PmlOps o, const double2 *__restrict__ y, doubl
     k[p] = make_double2(gi - sg * yp.x, -gr - sg * yp.y);  // -i (g) - sigma y
 }
 
+// Split-step march with the layer (FP64, one field, internal order): one
+// Clenshaw stage on the stretched operator X~ = (A~ - c) / r,
+//   out = alpha y + beta (X~ g) - (h ? h : 0),   (A~ g)_p = sum_q a_pq (g_p - g_q),
+// with complex a_pq; g = NULL stands for a zero b.
+__global__ void pml_stage_kernel(PmlOps o, const double2 *__restrict__ y, const double2 *__restrict__ g,
+                                 const double2 *__restrict__ hh, double2 *__restrict__ out, double c, double rinv,
+                                 double2 alpha, double2 beta) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= o.n0) return;
+    const double2 yp = y[p];
+    double2 acc = cmul(alpha, yp);
+    if (g) {
+        const double2 ag = pml_a_row(o, g, p), gp = g[p];
+        const double2 xg = make_double2((ag.x - c * gp.x) * rinv, (ag.y - c * gp.y) * rinv);
+        acc = cadd(acc, cmul(beta, xg));
+    }
+    if (hh) acc = csub(acc, hh[p]);
+    out[p] = acc;
+}
+
+// Exact flow over h of dpsi/dz = i (v + chib |psi|^2) psi - sigma psi with the
+// complex lumped v and chib of the stretched metric: the intensity solves
+// dI/dz = -alpha I - beta I^2, alpha = 2 (Im v + sigma), beta = 2 Im chib:
+//   I(h) = I0 e^{-alpha h} / D,  D = 1 + beta I0 q,  q = (1 - e^{-alpha h}) / alpha,
+// and the phase is Re v h + Re chib ln(D) / beta (-> Re chib I0 q as beta I0 q -> 0).
+__global__ void pml_diag_kernel(double2 *__restrict__ psi, const double2 *__restrict__ v,
+                                const double2 *__restrict__ chib, const double *__restrict__ sigma, double h,
+                                int32_t n0) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n0) return;
+    const double2 y = psi[p];
+    const double I0 = y.x * y.x + y.y * y.y;
+    const double alpha = 2.0 * (v[p].y + sigma[p]), beta = 2.0 * chib[p].y;
+    const double ah = alpha * h;
+    const double q = ah != 0.0 ? -expm1(-ah) / alpha : h;
+    const double x = beta * I0 * q;
+    const double ratio = x != 0.0 ? log1p(x) / x : 1.0;
+    const double theta = v[p].x * h + chib[p].x * I0 * q * ratio;
+    const double amp = sqrt(exp(-ah) / (1.0 + x));
+    double sn, cs;
+    sincos(theta, &sn, &cs);
+    psi[p] = make_double2(amp * (y.x * cs - y.y * sn), amp * (y.x * sn + y.y * cs));
+}
+
 struct RkCombine {
     const double2 *k[7];
     double a[7];

@@ -39,19 +39,76 @@ def test_rk45_with_pml_matches_oracle(amp, p):
     assert bpm.relative_error(ops, t.cpu().numpy(), ref) <= 1e-11
 
 
-def test_pml_mesh_rejects_the_split_step_and_can_be_removed():
+@pytest.mark.parametrize("amp,dz,n,every", [(1.0, 1e-3, 30, 0), (2.5, 5e-4, 40, 15)])
+def test_split_step_with_pml_matches_oracle(amp, dz, n, every):
+    """The Strang march on the complex-stretched operators (the layer the
+    paper's Conclusion proposes) through decbpm_propagate: the Chebyshev
+    series of exp(-i a x) evaluated on the stretched operator's complex
+    spectrum, degree set by the Bernstein ellipse of its Gershgorin box, and
+    the exact diagonal flow with complex lumped v and chib, against the
+    oracle's Strang march on the same operators (Taylor action, no merging
+    of half steps) <= 1e-12; an outgoing beam loses power to the layer."""
+    coords, tris = W.mesh_disk_graded(4.0, 1500, 2.0, interfaces=(1.0,), seed=91, grade_from=1.0)
+    V, chi = W.step_index_materials(coords, tris)
+    ops = pml.StretchedOperators(coords, tris, V, chi, **LAYER)
+    mesh = api.Mesh(coords, tris, V, chi)
+    api.set_pml(mesh, r_inner=3.0, r_outer=4.0, sigma_max=4.0, order=2)
+    x, y = coords[:, 0], coords[:, 1]
+    psi0 = (amp * np.exp(-((x - 0.3) ** 2 + y ** 2) / 0.5 + 3.0j * x)).astype(np.complex128)
+    ref = pml.propagate_stretched(ops, (1.0,), psi0, dz, n)
+    t = torch.from_numpy(psi0).to(DEV)
+    d = api.propagate(mesh, t, dz, n, diag_every=every)
+    assert bpm.relative_error(ops, t.cpu().numpy(), ref) <= 1e-12
+    P = d["power"][:, 0]
+    assert np.all(np.isfinite(P)) and np.all(P <= bpm.power(ops, psi0) * (1 + 1e-12))
+
+
+def test_split_step_with_pml_absorbs_an_outgoing_beam():
+    """A k = 4 beam on a homogeneous disk leaves through the layer: by z = 0.7
+    the split-step with the layer keeps 8% of the power (Neumann walls keep
+    all of it), follows the oracle's Strang march over the 700 steps
+    (<= 1e-11) and the GPU's own RK45 integration with the layer (the
+    splitting error, <= 1e-5)."""
+    coords, tris = W.mesh_disk_graded(4.0, 1500, 2.0, seed=91)
+    nc = len(tris)
+    V, chi = np.zeros(nc), np.ones(nc)
+    ops = pml.StretchedOperators(coords, tris, V, chi, **LAYER)
+    mesh = api.Mesh(coords, tris, V, chi)
+    api.set_pml(mesh, r_inner=3.0, r_outer=4.0, sigma_max=4.0, order=2)
+    x, y = coords[:, 0], coords[:, 1]
+    psi0 = np.exp(-((x - 0.3) ** 2 + y ** 2) / 0.5 + 4.0j * x).astype(np.complex128)
+    t = torch.from_numpy(psi0).to(DEV)
+    d = api.propagate(mesh, t, 1e-3, 700, diag_every=100)
+    P, P0 = d["power"][:, 0], bpm.power(ops, psi0)
+    assert P[-1] < 0.1 * P0 and np.all(np.diff(P) <= 1e-12 * P0)
+    ref = pml.propagate_stretched(ops, (1.0,), psi0, 1e-3, 700)
+    assert bpm.relative_error(ops, t.cpu().numpy(), ref) <= 1e-11
+    r = torch.from_numpy(psi0).to(DEV)
+    api.rk45(mesh, r, 0.7, rtol=1e-10, atol=1e-12)
+    assert bpm.relative_error(ops, t.cpu().numpy(), r.cpu().numpy()) <= 1e-5
+
+
+def test_pml_mesh_limits_and_removal():
+    """With a layer the split-step runs one complex128 field with lumped Kerr
+    (decbpm_propagate) besides decbpm_rk45; plans, complex64, several fields
+    and element Kerr are refused; removing the layer restores everything."""
     coords, tris = W.mesh_disk_graded(4.0, 600, 2.0, interfaces=(1.0,), seed=92, grade_from=1.0)
     V, chi = W.step_index_materials(coords, tris)
     mesh = api.Mesh(coords, tris, V, chi)
     x = torch.from_numpy(np.exp(-(coords[:, 0] ** 2 + coords[:, 1] ** 2)).astype(np.complex128)).to(DEV)
     api.set_pml(mesh, r_inner=3.0, r_outer=4.0, sigma_max=4.0)
-    with pytest.raises(L.DecbpmError) as e:
-        api.propagate(mesh, x.clone(), 1e-3, 2)
-    assert "PML" in str(e.value)
-    with pytest.raises(L.DecbpmError):
-        api.Plan([mesh], [1], "c128").propagate([x.clone()], 1e-3, 2)
+    y = x.clone()
+    api.propagate(mesh, y, 1e-3, 2)
+    assert torch.isfinite(torch.view_as_real(y)).all()
+    for bad in (lambda: api.propagate(mesh, x.clone().to(torch.complex64), 1e-3, 2),
+                lambda: api.propagate(mesh, torch.stack([x, x], dim=1).contiguous(), 1e-3, 2),
+                lambda: api.propagate(mesh, x.clone(), 1e-3, 2, kerr="element"),
+                lambda: api.Plan([mesh], [1], "c128").propagate([x.clone()], 1e-3, 2)):
+        with pytest.raises(L.DecbpmError) as e:
+            bad()
     with pytest.raises(L.DecbpmError):
         api.set_pml(mesh, r_inner=4.0, r_outer=3.0, sigma_max=1.0)        # bad geometry
     api.set_pml(mesh, None)
-    api.propagate(mesh, x, 1e-3, 2)                                     # the split-step runs again
-    assert torch.isfinite(torch.view_as_real(x)).all()
+    z = x.to(torch.complex64)
+    api.propagate(mesh, z, 1e-3, 2)                                     # every split-step path runs again
+    assert torch.isfinite(torch.view_as_real(z)).all()
