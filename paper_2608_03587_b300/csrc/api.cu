@@ -15,6 +15,7 @@
 #include <vector>
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include "decbpm.h"
 #include "internal.h"
@@ -41,6 +42,15 @@ using namespace decbpm;
     } while (0)
 
 namespace {
+
+// NVTX range around a public entry point (named in profiler timelines; a
+// no-op without a tool attached).
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
 
 struct DevAllocs {
     std::vector<void *> ptrs;
@@ -2099,6 +2109,7 @@ int decbpm_bessel_coefficients(double a, double tol, int32_t max_terms, double *
 }
 
 int decbpm_mesh_create(const decbpm_mesh_desc *desc, decbpm_mesh_t *out) {
+    NvtxRange nvtx_("decbpm_mesh_create");
     if (!out) return fail(DECBPM_ERR_INVALID_ARG, "out is NULL");
     *out = nullptr;
     auto M = std::make_unique<decbpm_mesh_s>();
@@ -2166,6 +2177,7 @@ static int single_plan(decbpm_mesh_t mesh, int64_t n_fields, int32_t precision, 
 
 int decbpm_propagate(decbpm_mesh_t mesh, const decbpm_params *params, void *psi_dev, int64_t n_fields, void *stream,
                      decbpm_diag *diag_out) {
+    NvtxRange nvtx_("decbpm_propagate");
     clear_error();
     if (!mesh || !psi_dev) return fail(DECBPM_ERR_INVALID_ARG, "mesh and psi_dev are required");
     TRY(check_params(params));
@@ -2186,6 +2198,7 @@ int decbpm_propagate(decbpm_mesh_t mesh, const decbpm_params *params, void *psi_
 
 int decbpm_propagate_host(decbpm_mesh_t mesh, const decbpm_params *params, void *psi_host, int64_t n_fields, void *stream,
                           decbpm_diag *diag_out) {
+    NvtxRange nvtx_("decbpm_propagate_host");
     clear_error();
     if (!mesh || !psi_host) return fail(DECBPM_ERR_INVALID_ARG, "mesh and psi_host are required");
     TRY(reject_pml(mesh));
@@ -2249,12 +2262,14 @@ int decbpm_plan_destroy(decbpm_plan_t plan) {
 
 int decbpm_plan_propagate(decbpm_plan_t plan, const decbpm_params *params, void *const *psi_dev, void *stream,
                           decbpm_diag *diag_out) {
+    NvtxRange nvtx_("decbpm_plan_propagate");
     clear_error();
     return plan_propagate_dispatch(plan, params, psi_dev, stream, diag_out);
 }
 
 int decbpm_plan_propagate_host(decbpm_plan_t P, const decbpm_params *params, void *const *psi_host, void *stream,
                                decbpm_diag *diag_out) {
+    NvtxRange nvtx_("decbpm_plan_propagate_host");
     clear_error();
     TRY(check_params(params));
     if (!P || !psi_host) return fail(DECBPM_ERR_INVALID_ARG, "NULL argument");
@@ -2318,6 +2333,7 @@ int decbpm_mesh_set_potential_offset(decbpm_mesh_t m, const double *dv_dev, void
 int decbpm_vjp(decbpm_mesh_t mesh, const decbpm_params *params, const void *psi0_dev, const void *gN_dev,
                void *psiN_dev, void *grad_psi0_dev, double *grad_v_dev, int64_t n_fields, int32_t checkpoint_every,
                void *stream) {
+    NvtxRange nvtx_("decbpm_vjp");
     clear_error();
     if (!mesh || !psi0_dev || !gN_dev || !grad_psi0_dev) return fail(DECBPM_ERR_INVALID_ARG, "NULL argument");
     TRY(reject_pml(mesh));
@@ -2338,6 +2354,7 @@ int decbpm_vjp(decbpm_mesh_t mesh, const decbpm_params *params, const void *psi0
 int decbpm_adjoint(decbpm_mesh_t mesh, const decbpm_params *params, const void *psi0_dev, const void *target_dev,
                    int64_t n_fields, double *J_out, double *grad_v_dev, void *grad_psi0_dev, int32_t checkpoint_every,
                    void *stream) {
+    NvtxRange nvtx_("decbpm_adjoint");
     clear_error();
     if (!mesh || !psi0_dev || !target_dev || !J_out) return fail(DECBPM_ERR_INVALID_ARG, "NULL argument");
     TRY(reject_pml(mesh));
@@ -2357,6 +2374,7 @@ int decbpm_adjoint(decbpm_mesh_t mesh, const decbpm_params *params, const void *
 
 int decbpm_rk45(decbpm_mesh_t mesh, double z_end, int32_t kerr_mode, const decbpm_rk45_opts *opts, void *psi_dev,
                 void *stream, decbpm_rk45_stats *stats) {
+    NvtxRange nvtx_("decbpm_rk45");
     clear_error();
     if (!mesh || !opts || !psi_dev) return fail(DECBPM_ERR_INVALID_ARG, "NULL argument");
     if (!(z_end >= 0) || !std::isfinite(z_end)) return fail(DECBPM_ERR_INVALID_ARG, "z_end must be finite and >= 0");
@@ -2372,6 +2390,7 @@ int decbpm_rk45(decbpm_mesh_t mesh, double z_end, int32_t kerr_mode, const decbp
 
 int decbpm_soliton(decbpm_mesh_t mesh, const decbpm_soliton_opts *opts, void *psi_dev, void *stream,
                    decbpm_soliton_stats *stats) {
+    NvtxRange nvtx_("decbpm_soliton");
     clear_error();
     if (!mesh || !opts || !psi_dev) return fail(DECBPM_ERR_INVALID_ARG, "NULL argument");
     TRY(reject_pml(mesh));
@@ -2400,6 +2419,7 @@ int decbpm_bessel_i_scaled(double a, double tol, int32_t n_max, double *out, int
 
 int decbpm_plan_autotune(decbpm_plan_t P, double dz, int32_t kerr_mode, int32_t trial_steps, void *stream,
                          decbpm_tune_result *out) {
+    NvtxRange nvtx_("decbpm_plan_autotune");
     clear_error();
     if (!P) return fail(DECBPM_ERR_INVALID_ARG, "plan is NULL");
     TRY(reject_pml_plan(P));
@@ -2444,6 +2464,7 @@ int decbpm_plan_set_shape(decbpm_plan_t P, const decbpm_tune_result *shape) {
 }
 
 int decbpm_mesh_set_pml(decbpm_mesh_t mesh, const decbpm_pml *pml) {
+    NvtxRange nvtx_("decbpm_mesh_set_pml");
     clear_error();
     if (!mesh) return fail(DECBPM_ERR_INVALID_ARG, "mesh is NULL");
     if (!pml || pml->sigma_max == 0.0) {
@@ -2529,6 +2550,7 @@ int decbpm_selftest_barrier(int32_t missing_arrivals, int64_t timeout_ns, void *
 
 int decbpm_propagate_batch(const decbpm_mesh_t *meshes, int32_t n_meshes, const int32_t *fields_per_mesh,
                            const decbpm_params *params, void *const *psi_dev, void *stream, decbpm_diag *diag_out) {
+    NvtxRange nvtx_("decbpm_propagate_batch");
     clear_error();
     TRY(check_params(params));
     decbpm_plan_t P = nullptr;
@@ -2724,6 +2746,7 @@ int propagate_noalloc_impl(decbpm_mesh_t mesh, const decbpm_params *prm, void *p
 
 extern "C" int decbpm_propagate_noalloc(decbpm_mesh_t mesh, const decbpm_params *params, void *psi_dev,
                                         int64_t n_fields, void *stream) {
+    NvtxRange nvtx_("decbpm_propagate_noalloc");
     clear_error();
     if (!mesh || !psi_dev) return fail(DECBPM_ERR_INVALID_ARG, "mesh and psi_dev are required");
     TRY(check_params(params));

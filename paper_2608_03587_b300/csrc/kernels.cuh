@@ -834,13 +834,10 @@ __device__ __forceinline__ void look_issue(int *entry, int t, const MeshView<flo
 // contiguous blocks (tile rows, SELL entries, descriptor) are bulk copies;
 // the scattered halo rows are 16-byte cp.async copies, eight lanes per row.
 __device__ __forceinline__ void tile_fill(const int *entry, const MeshView<float> *sv, const StageCoef<float> *scoef,
-                                          const int32_t *s_tbeg, int n_meshes, int k, char *slot, uint32_t bar,
-                                          const MarchParams<float> &P) {
+                                          int k, char *slot, uint32_t bar, const MarchParams<float> &P) {
     const int lane = threadIdx.x & 31;
     const int4 dsc = *reinterpret_cast<const int4 *>(entry + 96);
     const int mi = entry[101], tl = entry[102];
-    (void)s_tbeg;
-    (void)n_meshes;
     const MeshView<float> &m = sv[mi];
     const int flags = scoef[mi].flags;
     const int r0 = tl * kTileRows, nrows = min(kTileRows, m.n0 - r0);
@@ -936,16 +933,13 @@ __device__ __forceinline__ float2 f2_unpack(cf2 a) {
 // and x_pq.  Arithmetic order is that of the row kernel: for each
 // neighbour in SELL order acc += x (g_p - g_q), then
 // out = alpha psi (+ alpha_lo psi) + beta (acc - g_p) - h.
-__device__ __forceinline__ void tile_compute(const MeshView<float> *sv, const StageCoef<float> *scoef,
-                                             const int32_t *s_tbeg, int n_meshes, int t, int k, const char *slot,
+__device__ __forceinline__ void tile_compute(const MeshView<float> *sv, const StageCoef<float> *scoef, int k,
+                                             const char *slot,
                                              float h_post, int kerr_mode, const MarchParams<float> &P) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const uint32_t base = smem_u32(slot);
     int mi, tl;                                            // written by the copy warp next to the descriptor
     asm volatile("ld.shared.v2.s32 {%0, %1}, [%2];" : "=r"(mi), "=r"(tl) : "r"(base + P.off_hdr + 16));
-    (void)s_tbeg;
-    (void)n_meshes;
-    (void)t;
     const MeshView<float> &m = sv[mi];
     const StageCoef<float> sc = scoef[mi];
     const int lr = warp * 8 + (lane >> 2);                 // row in the tile
@@ -1106,7 +1100,7 @@ __device__ __forceinline__ void tile_march_role(int copier,const MarchParams<flo
                         int *entry = ring + ((q / D) % kLookAhead) * kLookInts;
                         cp_async_wait<kLookAhead - 1>();       // this entry's group has landed
                         __syncwarp();
-                        tile_fill(entry, s_view, s_coef, s_tbeg, P.n_meshes, k, s_ring + (size_t)sl * P.slot_bytes,
+                        tile_fill(entry, s_view, s_coef, k, s_ring + (size_t)sl * P.slot_bytes,
                                   smem_u32(&s_full[sl]), P);
                         __syncwarp();
                         look_issue(entry, look_next_n(cur, P, int(D)), s_view, s_tbeg, P.n_meshes);
@@ -1114,7 +1108,7 @@ __device__ __forceinline__ void tile_march_role(int copier,const MarchParams<flo
                 } else {
                     ok = mbar_wait(smem_u32(&s_full[sl]), (q / D) & 1u, P.status, P.timeout_ns);
                     if (ok) {
-                        tile_compute(s_view, s_coef, s_tbeg, P.n_meshes, R.at(i), k, s_ring + (size_t)sl * P.slot_bytes,
+                        tile_compute(s_view, s_coef, k, s_ring + (size_t)sl * P.slot_bytes,
                                      h_post, P.kerr_mode, P);
                         __syncwarp();
                         if (lane == 0) mbar_arrive(smem_u32(&s_empty[sl]));
@@ -1297,14 +1291,11 @@ __device__ __forceinline__ PairRole pair_role(int M, int k, int type) {
 }
 
 // Copy warp: fill `slot` for the tile of look-ahead `entry` in pass p.
-__device__ __forceinline__ void pair_fill(const int *entry, const MeshView<float> *sv, const PairCoef *s_pc,
-                                          const int32_t *s_tbeg, int n_meshes, int p, PassInfo pi, char *slot,
-                                          uint32_t bar, const MarchParams<float> &P) {
+__device__ __forceinline__ void pair_fill(const int *entry, const MeshView<float> *sv, const PairCoef *s_pc, int p,
+                                          PassInfo pi, char *slot, uint32_t bar, const MarchParams<float> &P) {
     const int lane = threadIdx.x & 31;
     const int *dsc = entry + kPairHL;
     const int mi = entry[kPairHL + kPairDesc + 1], tl = entry[kPairHL + kPairDesc + 2];
-    (void)s_tbeg;
-    (void)n_meshes;
     const MeshView<float> &m = sv[mi];
     const int r0 = tl * kTileRows, nrows = min(kTileRows, m.n0 - r0);
     const int e0 = dsc[0], ne = dsc[1], nh1 = dsc[2] & 0xffff, nh2 = dsc[2] >> 16, he0 = dsc[3], hne = dsc[8];
@@ -1397,10 +1388,9 @@ __device__ __forceinline__ void slice_entry(int lr, int es01, int es23, int widt
 // group's 8 warps take 64 rows per round (8 rows of 4 lanes per warp): two
 // rounds of tile rows and up to two of halo rows in phase 1, two rounds of
 // tile rows in phase 2.
-__device__ __forceinline__ void pair_row_stage1(const char *slot, int wr, int lwin, bool ok, bool gis1, cf2 arr,
+__device__ __forceinline__ void pair_row_stage1(const char *slot, int wr, bool ok, bool gis1, cf2 arr,
                                                 cf2 ani, cf2 brr, cf2 bni, uint32_t lcb, uint32_t xsb, int width,
                                                 const MarchParams<float> &P) {
-    (void)lwin;
     if (!ok) return;
     const int lane = threadIdx.x & 31;
     const int c1 = (lane & 3) + 4 * ((lane >> 2) & 1), c2 = c1 ^ 4;
@@ -1559,7 +1549,7 @@ __device__ __forceinline__ void pair_compute(const MeshView<float> *sv, const Pa
 #pragma unroll
         for (int u = 0; u < kTileRows / kRound; ++u) {
             const int lr = u * kRound + lw * 8 + (lane >> 2);
-            pair_row_stage1(slot, lr, lr, okr[u], gis1, arr, ani, brr, bni, base + P.off_lcol + 2 * es[u],
+            pair_row_stage1(slot, lr, okr[u], gis1, arr, ani, brr, bni, base + P.off_lcol + 2 * es[u],
                             base + P.off_x + 4 * es[u], width[u], P);
         }
         for (int i0 = 0; i0 < nh1; i0 += kRound) {
@@ -1571,7 +1561,7 @@ __device__ __forceinline__ void pair_compute(const MeshView<float> *sv, const Pa
             for (int s2 = 0; s2 < (i >> 5); ++s2) pre += (d1.w >> (8 * s2)) & 0xff;
             e1 = 32 * pre + (i & 31);
             if (ok && wd > 0 && e1 + 32 * (wd - 1) >= P.slot_hentries) { atomicCAS(P.status, 0, -8); ok = false; }
-            pair_row_stage1(slot, kTileRows + i, i, ok, gis1, arr, ani, brr, bni, base + P.off_lcol2 + 2 * e1,
+            pair_row_stage1(slot, kTileRows + i, ok, gis1, arr, ani, brr, bni, base + P.off_lcol2 + 2 * e1,
                             base + P.off_x2 + 4 * e1, wd, P);
         }
         group_sync(grp);
@@ -1656,7 +1646,7 @@ __device__ __forceinline__ void pair_march_role(int copier, const MarchParams<fl
                         int *entry = ring + ((q / D) % kPairLook) * kPairLookInts;
                         cp_async_wait<kPairLook - 1>();
                         __syncwarp();
-                        pair_fill(entry, s_view, s_pc, s_tbeg, P.n_meshes, p, pi, s_ring + (size_t)sl * P.slot_bytes,
+                        pair_fill(entry, s_view, s_pc, p, pi, s_ring + (size_t)sl * P.slot_bytes,
                                   smem_u32(&s_full[sl]), P);
                         __syncwarp();
                         pair_look_issue(entry, pair_look_next_n(cur, P, int(D)), s_view, s_tbeg, P.n_meshes);
