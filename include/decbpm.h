@@ -74,6 +74,13 @@ extern "C" {
                                     plans run FUSED).  It stores a_k psi - b_{k+2} in place of b_{k+2}, so its
                                     fields differ from FUSED's at the level of FP32 rounding.  FUSED runs it once
                                     decbpm_plan_autotune has chosen it. */
+#define DECBPM_VARIANT_FLOW   4  /* fused, the tile-staged kernel without grid barriers between Clenshaw stages
+                                    (dataflow kernel): a tile waits only for the tiles adjacent to it in the
+                                    operator graph to finish the previous stage (per-tile completion counters),
+                                    so CTAs are not held in lockstep.  Same arithmetic per row as FUSED's
+                                    tile-staged kernel (bitwise identical fields); complex64 plans with 9..16
+                                    fields whose tiles have at most 31 such neighbours, other plans run FUSED.
+                                    FUSED runs it once decbpm_plan_autotune has chosen it. */
 
 #define DECBPM_ORDER_DEFAULT  0  /* Hilbert curve in 2D, coordinate order in 1D */
 #define DECBPM_ORDER_RCM      1  /* reverse Cuthill-McKee (small bandwidth, thin level sets) */
@@ -157,8 +164,8 @@ typedef struct {
     int32_t precision;   /* DECBPM_C64 | DECBPM_C128: element type of the field buffers */
     int32_t kerr_mode;   /* DECBPM_KERR_LUMPED | DECBPM_KERR_ELEMENT */
     int32_t diag_every;  /* > 0: diagnostics after every diag_every steps; 0: only after the last step */
-    int32_t variant;     /* DECBPM_VARIANT_FUSED | DECBPM_VARIANT_ROWS | DECBPM_VARIANT_PLAIN (C128, one
-                            mesh, one field); decbpm_vjp and decbpm_propagate_noalloc take FUSED */
+    int32_t variant;     /* DECBPM_VARIANT_FUSED | _ROWS | _PAIRS | _FLOW | _PLAIN (C128, one mesh, one
+                            field); decbpm_vjp and decbpm_propagate_noalloc take FUSED */
     double  cheb_tol;    /* Chebyshev truncation: tail bound; 0 = 1e-16 (C128) / 1e-9 (C64) */
 } decbpm_params;
 
@@ -170,6 +177,9 @@ typedef struct {
 typedef struct { double z, power, hamiltonian, max_intensity; } decbpm_diag;
 
 /* ---- library ------------------------------------------------------------- */
+/* Library name and target; the bounds-check build (-DDECBPM_BOUNDS_CHECK,
+   libdecbpm_checked.so) says "bounds-checked": its march kernels test every
+   gather index against its buffer and report DECBPM_ERR_DEVICE_CHECK. */
 const char *decbpm_version(void);
 /* Message of the last failed call on this thread ("" if none).  Owned by the library. */
 const char *decbpm_last_error(void);
@@ -260,7 +270,8 @@ typedef struct {
     int32_t tile_grid;     /* CTAs of the tile-staged launch */
     int32_t tile_block;    /* threads per CTA of the tile-staged launch (16 compute + 3 copy warps) */
     int32_t tuned;         /* 1 once decbpm_plan_autotune chose the launch shapes below */
-    int32_t fused_kernel;  /* FUSED runs: 2 the stage-pair kernel, 1 the tile-staged kernel, 0 the row kernel */
+    int32_t fused_kernel;  /* FUSED runs: 3 the dataflow kernel, 2 the stage-pair kernel, 1 the tile-staged
+                              kernel, 0 the row kernel */
     int32_t tile_slots_used; /* ring slots the tile-staged kernel uses */
     int32_t forward_walk;  /* 1: odd stages do not walk backwards */
     int32_t pair_slots;    /* > 0: the plan can run the stage-pair kernel with this many ring slots */
@@ -269,14 +280,19 @@ typedef struct {
     int32_t passes;        /* grid-wide passes per step of the stage-pair kernel (last configured dz) */
     int32_t values_per_thread; /* row kernel: complex values per thread (a row is fields_padded / this lanes) */
     int32_t rows_per_item; /* row kernel: vertex rows per warp work item */
+    int32_t flow_grid;     /* > 0: the plan can run the dataflow kernel with this many CTAs (one more warp
+                              than the tile-staged kernel's: a publisher of tile completions) */
+    int32_t flow_skip;     /* dataflow kernel: a reversed walk starts this many tiles before the previous
+                              walk's end */
 } decbpm_plan_config;
 int decbpm_plan_get_config(decbpm_plan_t plan, decbpm_plan_config *cfg);
 
 /* Autotuner of the FUSED variant's launch shapes (no counterpart in the paper:
  * the kernels' own tuning).  Times short trial marches of `trial_steps` steps
  * (1..1000) at step dz on the plan's internal buffers, for every candidate:
- * the stage-pair kernel with 3 or 2 ring slots and the tile-staged kernel
- * with 3 or 2 ring slots (complex64 plans with 9..16 fields), the row kernel
+ * the stage-pair kernel with 3 or 2 ring slots, the tile-staged kernel
+ * with 3 or 2 ring slots and the dataflow kernel with walk skips 4, 8 and 16
+ * (complex64 plans with 9..16 fields), the row kernel
  * with 1..max co-resident CTAs per SM and (complex64 plans with 4+ fields) 4 or
  * 2 complex values per thread, each with and without the reverse walk
  * of odd stages; keeps the fastest for this plan and caches it for the
@@ -288,7 +304,8 @@ int decbpm_plan_get_config(decbpm_plan_t plan, decbpm_plan_config *cfg);
  * plan's internal buffers are overwritten (they hold nothing between calls). */
 typedef struct {
     int32_t variant;       /* DECBPM_VARIANT_PAIRS: the stage-pair kernel; DECBPM_VARIANT_FUSED: the tile-staged
-                              kernel; DECBPM_VARIANT_ROWS: the row kernel */
+                              kernel; DECBPM_VARIANT_FLOW: the dataflow kernel; DECBPM_VARIANT_ROWS: the row
+                              kernel */
     int32_t ctas_per_sm;   /* row kernel: co-resident CTAs per SM (tile kernel: 1) */
     int32_t tile_slots;    /* tile kernel: ring slots (0 for the row kernel) */
     int32_t forward_walk;  /* 1: odd stages walk forwards */
@@ -297,13 +314,15 @@ typedef struct {
     int32_t from_cache;
     int32_t values_per_thread; /* row kernel: complex values per thread (complex64 plans of 4+ fields: 4 or 2;
                                   so rows per warp item = 32 x this / padded fields); others: the default */
+    int32_t walk_skip;     /* dataflow kernel: see decbpm_plan_config.flow_skip (0: the default, 8) */
 } decbpm_tune_result;
 int decbpm_plan_autotune(decbpm_plan_t plan, double dz, int32_t kerr_mode, int32_t trial_steps, void *stream,
                          decbpm_tune_result *out);
 /* Apply a launch shape without timing (for example one that decbpm_plan_autotune
- * returned in an earlier process): variant (PAIRS, FUSED = tile-staged, ROWS),
- * ctas_per_sm and values_per_thread (ROWS), tile_slots (PAIRS, FUSED),
- * forward_walk; ms_per_step, candidates and from_cache are ignored.  Shapes the
+ * returned in an earlier process): variant (PAIRS, FUSED = tile-staged, FLOW,
+ * ROWS), ctas_per_sm and values_per_thread (ROWS), tile_slots (PAIRS, FUSED,
+ * FLOW), walk_skip (FLOW), forward_walk; ms_per_step, candidates and
+ * from_cache are ignored.  Shapes the
  * plan cannot run return DECBPM_ERR_UNSUPPORTED or DECBPM_ERR_INVALID_ARG. */
 int decbpm_plan_set_shape(decbpm_plan_t plan, const decbpm_tune_result *shape);
 

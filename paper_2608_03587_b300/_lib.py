@@ -1,7 +1,9 @@
 """ctypes loader of libdecbpm.so: argument types of every C-ABI entry point.
 
 The library is built in-tree (``paper_2608_03587_b300/libdecbpm.so``).  There
-is no fallback: if it is missing and cannot be built, loading raises.
+is no fallback: if it is missing and cannot be built, loading raises.  With
+DECBPM_BOUNDS_CHECK=1 in the environment the bounds-check build
+(``libdecbpm_checked.so``, same entry points) is loaded instead.
 """
 from __future__ import annotations
 
@@ -10,7 +12,8 @@ import os
 import threading
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "libdecbpm.so")
+CHECKED = os.environ.get("DECBPM_BOUNDS_CHECK", "0") not in ("", "0")
+LIB_PATH = os.path.join(HERE, "libdecbpm_checked.so" if CHECKED else "libdecbpm.so")
 
 # status codes (include/decbpm.h)
 OK = 0
@@ -30,6 +33,7 @@ VARIANT_FUSED = 0
 VARIANT_PLAIN = 1
 VARIANT_ROWS = 2
 VARIANT_PAIRS = 3
+VARIANT_FLOW = 4
 ORDER_DEFAULT = 0
 ORDER_RCM = 1
 ORDER_HILBERT = 2
@@ -75,7 +79,8 @@ class PlanConfig(ctypes.Structure):
                 ("tile_block", ctypes.c_int32), ("tuned", ctypes.c_int32), ("fused_kernel", ctypes.c_int32),
                 ("tile_slots_used", ctypes.c_int32), ("forward_walk", ctypes.c_int32), ("pair_slots", ctypes.c_int32),
                 ("pair_slot_bytes", ctypes.c_int32), ("pair_grid", ctypes.c_int32), ("passes", ctypes.c_int32),
-                ("values_per_thread", ctypes.c_int32), ("rows_per_item", ctypes.c_int32)]
+                ("values_per_thread", ctypes.c_int32), ("rows_per_item", ctypes.c_int32),
+                ("flow_grid", ctypes.c_int32), ("flow_skip", ctypes.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -84,11 +89,11 @@ class PlanConfig(ctypes.Structure):
 class TuneResult(ctypes.Structure):
     _fields_ = [("variant", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32), ("tile_slots", ctypes.c_int32),
                 ("forward_walk", ctypes.c_int32), ("ms_per_step", ctypes.c_double), ("candidates", ctypes.c_int32),
-                ("from_cache", ctypes.c_int32), ("values_per_thread", ctypes.c_int32)]
+                ("from_cache", ctypes.c_int32), ("values_per_thread", ctypes.c_int32), ("walk_skip", ctypes.c_int32)]
 
     def as_dict(self):
         d = {k: getattr(self, k) for k, _ in self._fields_}
-        d["kernel"] = {VARIANT_FUSED: "tile", VARIANT_PAIRS: "pairs"}.get(self.variant, "rows")
+        d["kernel"] = {VARIANT_FUSED: "tile", VARIANT_PAIRS: "pairs", VARIANT_FLOW: "flow"}.get(self.variant, "rows")
         return d
 
 
@@ -189,14 +194,15 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
             return _lib
         if build_if_missing:
             from . import build as _build
-            if not os.path.exists(LIB_PATH) or not _build.up_to_date():
+            if not os.path.exists(LIB_PATH) or not _build.up_to_date(CHECKED):
                 try:
-                    _build.build()
+                    _build.build(checked=CHECKED)
                 except Exception as exc:  # noqa: BLE001
                     if not os.path.exists(LIB_PATH):
-                        raise RuntimeError("libdecbpm.so is missing and could not be built: %s" % exc) from exc
+                        raise RuntimeError("%s is missing and could not be built: %s"
+                                           % (os.path.basename(LIB_PATH), exc)) from exc
         if not os.path.exists(LIB_PATH):
-            raise RuntimeError("libdecbpm.so not found at %s (run python -m paper_2608_03587_b300.build)" % LIB_PATH)
+            raise RuntimeError("%s not found (run python -m paper_2608_03587_b300.build --all)" % LIB_PATH)
         lib = ctypes.CDLL(LIB_PATH)
         for name, (res, args) in SIGNATURES.items():
             fn = getattr(lib, name)

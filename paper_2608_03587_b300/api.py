@@ -53,7 +53,8 @@ def _params(dz, n_steps, precision, kerr="lumped", diag_every=0, variant="fused"
     return L.Params(dz=float(dz), n_steps=int(n_steps), precision=precision,
                     kerr_mode=L.KERR_LUMPED if kerr == "lumped" else L.KERR_ELEMENT,
                     diag_every=int(diag_every), variant={"fused": L.VARIANT_FUSED, "plain": L.VARIANT_PLAIN,
-                                                            "rows": L.VARIANT_ROWS, "pairs": L.VARIANT_PAIRS}[variant],
+                                                            "rows": L.VARIANT_ROWS, "pairs": L.VARIANT_PAIRS,
+                                                            "flow": L.VARIANT_FLOW}[variant],
                     cheb_tol=float(cheb_tol))
 
 
@@ -265,12 +266,14 @@ class Plan:
                                             int(trial_steps), _stream_handle(stream), ctypes.byref(r)))
         return r.as_dict()
 
-    def set_shape(self, kernel="rows", ctas_per_sm=1, tile_slots=0, forward_walk=0, values_per_thread=0):
+    def set_shape(self, kernel="rows", ctas_per_sm=1, tile_slots=0, forward_walk=0, values_per_thread=0,
+                  walk_skip=0):
         """decbpm_plan_set_shape: apply a launch shape without timing (kernel
-        "pairs", "tile" or "rows"; e.g. the dict autotune() returned)."""
-        var = {"pairs": L.VARIANT_PAIRS, "tile": L.VARIANT_FUSED, "rows": L.VARIANT_ROWS}[kernel]
+        "pairs", "tile", "flow" or "rows"; e.g. the dict autotune() returned)."""
+        var = {"pairs": L.VARIANT_PAIRS, "tile": L.VARIANT_FUSED, "flow": L.VARIANT_FLOW, "rows": L.VARIANT_ROWS}[kernel]
         r = L.TuneResult(variant=var, ctas_per_sm=int(ctas_per_sm), tile_slots=int(tile_slots),
-                         forward_walk=int(forward_walk), values_per_thread=int(values_per_thread))
+                         forward_walk=int(forward_walk), values_per_thread=int(values_per_thread),
+                         walk_skip=int(walk_skip))
         L.check(_lib().decbpm_plan_set_shape(self._h, ctypes.byref(r)))
 
     def config(self) -> dict:

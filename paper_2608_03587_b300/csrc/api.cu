@@ -111,6 +111,10 @@ struct decbpm_mesh_s {
     uint16_t *lcol = nullptr;
     int32_t *tdesc = nullptr, *halo_rows = nullptr, *halo_ovf = nullptr;
     int n_tiles = 0, max_halo = 0, max_entries = 0;
+    // dataflow march: per tile kDepInts int32 (count, then the tiles adjacent
+    // to it in the operator graph and itself); flow_ok if every list fits
+    int32_t *tdeps = nullptr;
+    bool flow_ok = false;
     // stage-pair maps (built on first use): per tile the depth-two halo list,
     // descriptor, and the SELL entries of the first halo ring
     bool pairs_ready = false, pairs_ok = false;
@@ -143,6 +147,7 @@ static int build_tiles(decbpm_mesh_t M) {
     std::vector<uint16_t> lcol(S.col.size(), 0);
     std::vector<int32_t> desc(size_t(nt) * 8, 0), hfixed(size_t(nt) * held, 0), hovf;
     std::vector<int32_t> uniq;
+    std::vector<std::vector<int32_t>> adj(nt);          // tiles holding a tile's halo rows
     int max_halo = 0, max_entries = 0;
     for (int t = 0; t < nt; ++t) {
         const int64_t r0 = int64_t(t) * kTileRows, r1 = std::min<int64_t>(r0 + kTileRows, n0);
@@ -182,10 +187,35 @@ static int build_tiles(decbpm_mesh_t M) {
         for (size_t j = 0; j < uniq.size(); ++j) {
             if (j < size_t(held)) hfixed[size_t(t) * held + j] = uniq[j];
             else hovf.push_back(uniq[j]);
+            const int32_t tq = uniq[j] / kTileRows;
+            if (adj[t].empty() || adj[t].back() != tq) adj[t].push_back(tq);    // uniq is sorted
         }
         max_halo = std::max(max_halo, int(uniq.size()));
         max_entries = std::max(max_entries, int(e1 - e0));
     }
+    // dependency lists of the dataflow march: the tile itself and every tile
+    // adjacent to it, made symmetric (a tile whose rows another tile reads as
+    // halo depends on that tile too), at most kDepInts - 1 entries
+    std::vector<std::vector<int32_t>> dep(nt);
+    for (int t = 0; t < nt; ++t) {
+        dep[t].push_back(t);
+        for (int32_t u : adj[t]) {
+            dep[t].push_back(u);
+            dep[u].push_back(t);
+        }
+    }
+    std::vector<int32_t> tdeps(size_t(nt) * kDepInts, 0);
+    bool flow_ok = true;
+    for (int t = 0; t < nt && flow_ok; ++t) {
+        std::vector<int32_t> &d = dep[t];
+        std::sort(d.begin(), d.end());
+        d.erase(std::unique(d.begin(), d.end()), d.end());
+        if (int(d.size()) > kDepInts - 1) { flow_ok = false; break; }
+        tdeps[size_t(t) * kDepInts] = int32_t(d.size());
+        for (size_t j = 0; j < d.size(); ++j) tdeps[size_t(t) * kDepInts + 1 + j] = d[j];
+    }
+    if (flow_ok) TRY(M->mem.upload(&M->tdeps, tdeps));
+    M->flow_ok = flow_ok;
     TRY(M->mem.upload(&M->lcol, lcol));
     TRY(M->mem.upload(&M->tdesc, desc));
     TRY(M->mem.upload(&M->halo_rows, hfixed));
@@ -445,6 +475,15 @@ struct decbpm_plan_s {
     void *pcoef = nullptr;
     int pcoef_cap = 0;
     int tune_pair = -1;                          // 1: FUSED runs the stage-pair kernel; 0: not; -1: default
+    // dataflow march (the tile-staged kernel without stage barriers): per-tile
+    // counters, per-CTA tile lists of the current stage tables, the walk skip
+    bool flow_mode = false;
+    int flow_grid = 0;
+    unsigned *tile_done = nullptr;
+    int32_t *cta_tiles = nullptr, *cta_ptr = nullptr, *cta_cnt = nullptr, *active_meshes = nullptr;
+    int cta_cnt_cap = 0, active_meshes_cap = 0;
+    int tune_flow = 0;                           // 1: FUSED runs the dataflow kernel
+    int flow_skip = kDefaultFlowSkip;
     // graphs: key -> exec
     std::map<std::tuple<double, int64_t, int32_t, int32_t, double, int32_t>, cudaGraphExec_t> graphs;
     bool graphs_ok = true;
@@ -557,6 +596,80 @@ static int setup_tiles(decbpm_plan_t P) {
     if (per_sm < 1) return DECBPM_OK;
     P->tile_grid = P->num_sms * per_sm;
     P->tile_mode = true;
+    // the dataflow kernel: same ring and static shared memory, one more warp
+    P->flow_mode = false;
+    bool deps_ok = true;
+    int total = 0;
+    for (decbpm_mesh_t m : P->meshes) {
+        deps_ok = deps_ok && m->flow_ok;
+        total += m->n_tiles;
+    }
+    if (!deps_ok) return DECBPM_OK;
+    CK(cudaFuncGetAttributes(&fa, (const void *)march_flow_kernel));
+    const int favail = optin - int(fa.sharedSizeBytes);
+    if (favail < dyn) return DECBPM_OK;
+    CK(cudaFuncSetAttribute((const void *)march_flow_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, favail));
+    int fper_sm = 0;
+    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fper_sm, (const void *)march_flow_kernel, kFlowThreads, dyn));
+    if (fper_sm < 1) return DECBPM_OK;
+    P->flow_grid = P->num_sms * fper_sm;
+    TRY(P->mem.alloc(&P->tile_done, size_t(total)));
+    TRY(P->mem.alloc(&P->cta_ptr, size_t(P->flow_grid) + 1));
+    TRY(P->mem.alloc(&P->cta_tiles, size_t(total)));
+    P->flow_mode = true;
+    return DECBPM_OK;
+}
+
+// Per-CTA tile lists of the dataflow march for the current plan order:
+// every mesh's tiles are cut into grid contiguous chunks, in CTA order, whose
+// sizes differ by at most one; the extra tiles of successive meshes go to
+// successive CTAs (round robin), so every CTA's share of any prefix of the
+// meshes differs from the others' by at most one tile.  A CTA's list holds
+// its chunks of the meshes in plan order (meshes sorted by degree, so the
+// meshes active in a stage are a prefix and a CTA's tiles of that stage a
+// prefix of its list).
+static int build_flow_lists(decbpm_plan_t P, const std::vector<int> &Ms) {
+    const int n = int(P->meshes.size()), G = P->flow_grid;
+    std::vector<std::vector<int32_t>> lists(G);
+    std::vector<int32_t> cnt(size_t(G) * n, 0);
+    int phi = 0;
+    for (int j = 0; j < n; ++j) {
+        const int i = P->order[j];
+        const int T = P->meshes[i]->n_tiles, q = T / G, r = T % G;
+        int start = 0;
+        for (int c = 0; c < G; ++c) {
+            const bool extra = ((c - phi + G) % G) < r;
+            const int sz = q + (extra ? 1 : 0);
+            for (int u = 0; u < sz; ++u) lists[c].push_back(P->tile_begin[i] + start + u);
+            start += sz;
+            cnt[size_t(c) * n + j] = int32_t(lists[c].size());
+        }
+        phi = (phi + r) % G;
+    }
+    std::vector<int32_t> ptr(G + 1, 0), flat;
+    flat.reserve(P->total_tiles);
+    for (int c = 0; c < G; ++c) {
+        ptr[c] = int32_t(flat.size());
+        flat.insert(flat.end(), lists[c].begin(), lists[c].end());
+    }
+    ptr[G] = int32_t(flat.size());
+    if (int(flat.size()) != P->total_tiles) return fail(DECBPM_ERR_CUDA, "dataflow tile lists are inconsistent");
+    if (G * n > P->cta_cnt_cap) {
+        TRY(P->mem.alloc(&P->cta_cnt, size_t(G) * n));
+        P->cta_cnt_cap = G * n;
+    }
+    if (P->S > P->active_meshes_cap) {
+        TRY(P->mem.alloc(&P->active_meshes, size_t(P->S)));
+        P->active_meshes_cap = P->S;
+    }
+    std::vector<int32_t> am(P->S, 0);
+    for (int s = 0; s < P->S; ++s)
+        for (int j = 0; j < n; ++j)
+            if (Ms[P->order[j]] > P->S - 1 - s) am[s] = j + 1;
+    CK(cudaMemcpy(P->cta_tiles, flat.data(), sizeof(int32_t) * flat.size(), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(P->cta_ptr, ptr.data(), sizeof(int32_t) * ptr.size(), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(P->cta_cnt, cnt.data(), sizeof(int32_t) * cnt.size(), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(P->active_meshes, am.data(), sizeof(int32_t) * am.size(), cudaMemcpyHostToDevice));
     return DECBPM_OK;
 }
 
@@ -806,9 +919,15 @@ static int plan_configure(decbpm_plan_t P, double dz, double tol) {
             v.tdesc = m->tdesc;
             v.halo_rows = m->halo_rows;
             v.halo_ovf = m->halo_ovf;
+            v.tdeps = m->tdeps;
             v.tile_begin = P->tile_begin[i];
         }
         off += Mi;
+    }
+    if (P->flow_mode) {
+        std::vector<int> Ms(n);
+        for (int i = 0; i < n; ++i) Ms[i] = ch[i].M;
+        TRY(build_flow_lists(P, Ms));
     }
     if (P->pair_mode) {
         // passes of a step: pairs (S-1, S-2), (S-3, S-4), ... down to stage 1, a
@@ -938,7 +1057,11 @@ static int launch_march(decbpm_plan_t P, cudaStream_t s, int n_steps, int kerr_m
             CK(cudaLaunchKernelExC(&cfg, (const void *)march_pair_kernel, pargs));
             return DECBPM_OK;
         }
-        if (P->tile_mode && (variant == DECBPM_VARIANT_FUSED || variant == DECBPM_VARIANT_PAIRS) && !P->tune_rows) {
+        const bool flow = P->flow_mode && (variant == DECBPM_VARIANT_FLOW ||
+                                           (variant == DECBPM_VARIANT_FUSED && !P->tune_rows && P->tune_pair != 1 &&
+                                            P->tune_flow == 1));
+        if (P->tile_mode && (variant == DECBPM_VARIANT_FUSED || variant == DECBPM_VARIANT_PAIRS || flow) &&
+            !P->tune_rows) {
             const int slots = (P->tune_pair != 1 && P->tune_slots > 0) ? std::min(P->tune_slots, P->n_slots) : P->n_slots;
             mp.active_tiles = P->active_tiles;
             mp.n_slots = slots;
@@ -953,6 +1076,18 @@ static int launch_march(decbpm_plan_t P, cudaStream_t s, int n_steps, int kerr_m
             cfg.blockDim = dim3(kTileThreads);
             cfg.dynamicSmemBytes = size_t(slots) * P->slot_bytes;
             fn = (const void *)march_tile_kernel;
+            if (flow) {
+                mp.tile_done = P->tile_done;
+                mp.cta_tiles = P->cta_tiles;
+                mp.cta_ptr = P->cta_ptr;
+                mp.cta_cnt = P->cta_cnt;
+                mp.active_meshes = P->active_meshes;
+                mp.flow_skip = P->flow_skip;
+                CK(cudaMemsetAsync(P->tile_done, 0, sizeof(unsigned) * size_t(P->total_tiles), s));
+                cfg.gridDim = dim3(P->flow_grid);
+                cfg.blockDim = dim3(kFlowThreads);
+                fn = (const void *)march_flow_kernel;
+            }
         }
     }
     CK(cudaLaunchKernelExC(&cfg, fn, args));
@@ -1017,7 +1152,7 @@ static int check_params(const decbpm_params *p) {
     if (p->kerr_mode != DECBPM_KERR_LUMPED && p->kerr_mode != DECBPM_KERR_ELEMENT) return fail(DECBPM_ERR_INVALID_ARG, "bad kerr_mode");
     if (p->diag_every < 0) return fail(DECBPM_ERR_INVALID_ARG, "diag_every < 0");
     if (p->variant != DECBPM_VARIANT_FUSED && p->variant != DECBPM_VARIANT_PLAIN && p->variant != DECBPM_VARIANT_ROWS &&
-        p->variant != DECBPM_VARIANT_PAIRS)
+        p->variant != DECBPM_VARIANT_PAIRS && p->variant != DECBPM_VARIANT_FLOW)
         return fail(DECBPM_ERR_INVALID_ARG, "bad variant");
     if (!(p->cheb_tol >= 0)) return fail(DECBPM_ERR_INVALID_ARG, "cheb_tol < 0");
     return DECBPM_OK;
@@ -1664,7 +1799,7 @@ static int soliton_impl(decbpm_mesh_t mesh, decbpm_plan_t P, const decbpm_solito
 // plan's internal buffers (zeroed first: their contents are scratch between
 // calls).  The winner is cached for the process, keyed by the meshes'
 // content fingerprints, the field counts, the precision, dz and kerr_mode.
-struct TuneChoice { int rows, per_sm, slots, forward, pair, fpt; double ms; };
+struct TuneChoice { int rows, per_sm, slots, forward, pair, fpt; double ms; int flow, skip; };
 static std::mutex g_tune_mutex;
 static std::map<std::string, TuneChoice> g_tune_cache;
 
@@ -1700,6 +1835,8 @@ static void apply_choice(decbpm_plan_t P, const TuneChoice &c) {
     }
     P->tune_rows = c.rows;
     P->tune_pair = c.pair;
+    P->tune_flow = c.flow;
+    P->flow_skip = c.skip > 0 ? c.skip : kDefaultFlowSkip;
     P->tune_slots = c.slots;
     P->forward_walk = c.forward;
     P->grid = P->num_sms * c.per_sm;
@@ -1710,7 +1847,9 @@ static void apply_choice(decbpm_plan_t P, const TuneChoice &c) {
 
 static decbpm_tune_result tune_result(const TuneChoice &c, int trial_steps, int n_cand, int from_cache) {
     decbpm_tune_result r{};
-    r.variant = c.rows ? DECBPM_VARIANT_ROWS : c.pair ? DECBPM_VARIANT_PAIRS : DECBPM_VARIANT_FUSED;
+    r.variant = c.rows ? DECBPM_VARIANT_ROWS : c.pair ? DECBPM_VARIANT_PAIRS : c.flow ? DECBPM_VARIANT_FLOW
+                                                                                     : DECBPM_VARIANT_FUSED;
+    r.walk_skip = c.flow ? c.skip : 0;
     r.ctas_per_sm = c.rows ? c.per_sm : 1;
     r.tile_slots = c.slots;
     r.forward_walk = c.forward;
@@ -1748,15 +1887,18 @@ static int autotune_impl(decbpm_plan_t P, double dz, int kerr_mode, int trial_st
     const int fpt0 = default_fpt(P->precision, P->bpad);
     for (int fw = 0; fw <= 1; ++fw) {
         if (P->pair_mode)
-            for (int sl = P->pair_slots; sl >= 2; --sl) cand.push_back({0, 1, sl, fw, 1, fpt0, 0.0});
+            for (int sl = P->pair_slots; sl >= 2; --sl) cand.push_back({0, 1, sl, fw, 1, fpt0, 0.0, 0, 0});
         if (P->tile_mode)
-            for (int sl = P->n_slots; sl >= 2; --sl) cand.push_back({0, P->max_per_sm, sl, fw, 0, fpt0, 0.0});
+            for (int sl = P->n_slots; sl >= 2; --sl) cand.push_back({0, P->max_per_sm, sl, fw, 0, fpt0, 0.0, 0, 0});
+        if (P->flow_mode)         // the skip only shapes reversed walks
+            for (int skip : (fw == 0 ? std::vector<int>{4, 8, 16} : std::vector<int>{kDefaultFlowSkip}))
+                cand.push_back({0, P->max_per_sm, P->n_slots, fw, 0, fpt0, 0.0, 1, skip});
         std::vector<int> fpts = {fpt0};
         if (fpt0 == 4 && fpt_allowed(P->precision, P->bpad, 2)) fpts.push_back(2);
         for (int fpt : fpts) {
             int occ = 0;
             CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, march_kernel_ptr(P->precision, P->bpad, fpt), P->block, 0));
-            for (int ps = 1; ps <= std::min(occ, 4); ++ps) cand.push_back({1, ps, 0, fw, 0, fpt, 0.0});
+            for (int ps = 1; ps <= std::min(occ, 4); ++ps) cand.push_back({1, ps, 0, fw, 0, fpt, 0.0, 0, 0});
         }
     }
     cudaEvent_t e0, e1;
@@ -2036,7 +2178,11 @@ static int propagate_plain_pml(decbpm_mesh_t m, const decbpm_params *prm, void *
 // ============================================================== C ABI
 extern "C" {
 
+#ifdef DECBPM_BOUNDS_CHECK
+const char *decbpm_version(void) { return "decbpm 0.1 (sm_103a, bounds-checked)"; }
+#else
 const char *decbpm_version(void) { return "decbpm 0.1 (sm_103a)"; }
+#endif
 
 const char *decbpm_last_error(void) { return last_error_cstr(); }
 
@@ -2442,12 +2588,18 @@ int decbpm_plan_set_shape(decbpm_plan_t P, const decbpm_tune_result *shape) {
             return fail(DECBPM_ERR_INVALID_ARG, "tile_slots must be in 2..%d", P->pair_slots);
         c.pair = 1; c.per_sm = 1; c.slots = shape->tile_slots;
         c.fpt = default_fpt(P->precision, P->bpad);
-    } else if (shape->variant == DECBPM_VARIANT_FUSED) {
+    } else if (shape->variant == DECBPM_VARIANT_FUSED || shape->variant == DECBPM_VARIANT_FLOW) {
         if (!P->tile_mode) return fail(DECBPM_ERR_UNSUPPORTED, "this plan cannot run the tile-staged kernel");
+        if (shape->variant == DECBPM_VARIANT_FLOW && !P->flow_mode)
+            return fail(DECBPM_ERR_UNSUPPORTED, "this plan cannot run the dataflow kernel");
         if (shape->tile_slots < 2 || shape->tile_slots > P->n_slots)
             return fail(DECBPM_ERR_INVALID_ARG, "tile_slots must be in 2..%d", P->n_slots);
+        if (shape->variant == DECBPM_VARIANT_FLOW && (shape->walk_skip < 0 || shape->walk_skip > 4096))
+            return fail(DECBPM_ERR_INVALID_ARG, "walk_skip must be in 0..4096");
         c.slots = shape->tile_slots; c.per_sm = P->max_per_sm;
         c.fpt = default_fpt(P->precision, P->bpad);
+        c.flow = shape->variant == DECBPM_VARIANT_FLOW ? 1 : 0;
+        c.skip = c.flow ? (shape->walk_skip > 0 ? shape->walk_skip : kDefaultFlowSkip) : 0;
     } else if (shape->variant == DECBPM_VARIANT_ROWS) {
         if (!fpt_allowed(P->precision, P->bpad, c.fpt))
             return fail(DECBPM_ERR_UNSUPPORTED, "values_per_thread %d is not built for this plan", c.fpt);
@@ -2494,7 +2646,11 @@ int decbpm_plan_get_config(decbpm_plan_t P, decbpm_plan_config *cfg) {
     if (cfg->fused_kernel == 1 && P->pair_mode && P->tune_pair == 1) {
         cfg->fused_kernel = 2;
         cfg->tile_slots_used = P->tune_slots > 0 ? std::min(P->tune_slots, P->pair_slots) : P->pair_slots;
+    } else if (cfg->fused_kernel == 1 && P->flow_mode && P->tune_flow == 1) {
+        cfg->fused_kernel = 3;
     }
+    cfg->flow_grid = P->flow_mode ? P->flow_grid : 0;
+    cfg->flow_skip = P->flow_skip;
     cfg->pair_slots = P->pair_mode ? P->pair_slots : 0;
     cfg->pair_slot_bytes = P->pair_mode ? P->pair_slot_bytes : 0;
     cfg->pair_grid = P->pair_mode ? P->pair_grid : 0;

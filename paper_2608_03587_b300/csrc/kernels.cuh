@@ -29,6 +29,27 @@ constexpr int kMaxMeshes = 64;
 constexpr int kMaxFields = 64;
 constexpr long long kBarrierTimeoutNs = 4000000000LL;   // default limit of one barrier wait: 4 s
 
+// Bounds-check build (-DDECBPM_BOUNDS_CHECK; libdecbpm_checked.so): every
+// gather index of the march kernels (a neighbour row in a field buffer, a
+// window offset in shared memory) is tested against its buffer.  An index
+// outside [0, n) records DECBPM_ERR_DEVICE_CHECK (-8) in *status and is
+// replaced by 0, so the access stays inside the buffer and the control flow
+// (every barrier and mbarrier phase) is that of the unchecked kernel; the
+// host then reports the status like a barrier time-out.  The default build
+// compiles the checks away.
+#ifdef DECBPM_BOUNDS_CHECK
+template <typename I> __device__ __forceinline__ I checked_index(I i, I n, int *status) {
+    if ((unsigned long long)(long long)i >= (unsigned long long)(long long)n) {
+        atomicCAS(status, 0, -8);
+        return I(0);
+    }
+    return i;
+}
+#define DECBPM_IDX(i, n, status) ::decbpm::checked_index((i), (n), (status))
+#else
+#define DECBPM_IDX(i, n, status) (i)
+#endif
+
 // ------------------------------------------------------------ complex types
 template <typename R> struct CT;
 template <> struct CT<float>  { using c2 = float2; };
@@ -196,6 +217,7 @@ template <typename R> struct MeshView {
     const int32_t *tdesc;    // per tile 8 int32 (TileDesc)
     const int32_t *halo_rows; // per tile 96 rows (first 96 halo rows, padded)
     const int32_t *halo_ovf;  // halo rows beyond the first 96
+    const int32_t *tdeps;     // per tile kDepInts int32: count, then the tiles holding its rows and halo rows
     int32_t tile_begin;      // first plan-global tile of this mesh
     int32_t pad_;
     // stage-pair march (complex64, 16 fields): a fourth field buffer, per tile
@@ -233,6 +255,15 @@ template <typename R> struct MarchParams {
     int32_t slot_hentries;       // halo SELL entries a slot holds
     int32_t n_passes;            // passes per step
     int32_t w2_rows, w1_rows;    // window capacities (rows) of g (tile + H1 + H2) and r (tile + H1)
+    // dataflow march only: per-tile completion counters (zeroed before every
+    // launch), this launch's per-CTA tile lists and the walk's skip
+    unsigned *tile_done;         // [total tiles]: last completed stage epoch of the tile
+    const int32_t *cta_tiles;    // per CTA: its chunk of every mesh, meshes in plan order
+    const int32_t *cta_ptr;      // [grid + 1]: start of each CTA's list
+    const int32_t *cta_cnt;      // [grid * n_meshes]: tiles of the CTA in meshes 0..j
+    const int32_t *active_meshes;// [S]: meshes with M > S-1-s (a prefix)
+    int32_t flow_skip;           // reversed walks start this many tiles before the previous stage's end
+    int32_t pad_flow;
 };
 
 // ------------------------------------------------------------ grid barrier
@@ -353,7 +384,7 @@ template <typename R, int E> struct ItemMeta {
 // share of the row's (column, weight) entries.
 template <typename R, int BPAD, int FPT_ = 0>
 __device__ __forceinline__ void load_meta(const MeshView<R> *sv, const int32_t *s_begin, int n_meshes, int it,
-                                          ItemMeta<R, Geo<R, BPAD, FPT_>::E> &mt) {
+                                          ItemMeta<R, Geo<R, BPAD, FPT_>::E> &mt, int *status) {
     using G = Geo<R, BPAD, FPT_>;
     const int lane = threadIdx.x & 31;
     int mi = 0;
@@ -369,7 +400,7 @@ __device__ __forceinline__ void load_meta(const MeshView<R> *sv, const int32_t *
     for (int e = 0; e < G::E; ++e) {
         const int j = e * G::TPR + lr;
         if (j < mt.width) {
-            mt.q[e] = __ldg(m.col + mt.base + 32 * j);
+            mt.q[e] = DECBPM_IDX(__ldg(m.col + mt.base + 32 * j), m.n0, status);
             mt.x[e] = __ldg(m.xval + mt.base + 32 * j);
         } else {
             mt.q[e] = 0;
@@ -389,7 +420,7 @@ __device__ __forceinline__ void load_meta(const MeshView<R> *sv, const int32_t *
 template <typename R, int BPAD, int FPT_ = 0>
 __device__ __forceinline__ void clenshaw_stage(const MeshView<R> *sv, const StageCoef<R> *scoef, const int32_t *s_begin,
                                                int n_meshes, int n_active, int k, R h_post, int kerr_mode,
-                                               bool rev_odd) {
+                                               bool rev_odd, int *status) {
     using G = Geo<R, BPAD, FPT_>;
     using C = typename CT<R>::c2;
     constexpr int FPT = G::FPT;
@@ -406,7 +437,7 @@ __device__ __forceinline__ void clenshaw_stage(const MeshView<R> *sv, const Stag
     auto item_at = [&](int i) { return rev ? hi - 1 - i : lo + i; };
     int idx = warp;
     ItemMeta<R, G::E> cur;
-    if (idx < n_mine) load_meta<R, BPAD, FPT_>(sv, s_begin, n_meshes, item_at(idx), cur);
+    if (idx < n_mine) load_meta<R, BPAD, FPT_>(sv, s_begin, n_meshes, item_at(idx), cur, status);
     while (idx < n_mine) {
         const int nidx = idx + nwarps;
         const MeshView<R> &m = sv[cur.mi];
@@ -446,7 +477,7 @@ __device__ __forceinline__ void clenshaw_stage(const MeshView<R> *sv, const Stag
                     gq[jj] = ld_pack<R, FPT>(g + (size_t)qj * BPAD + fo);
                 }
             }
-            if (j0 == 0 && nidx < n_mine) load_meta<R, BPAD, FPT_>(sv, s_begin, n_meshes, item_at(nidx), nm);
+            if (j0 == 0 && nidx < n_mine) load_meta<R, BPAD, FPT_>(sv, s_begin, n_meshes, item_at(nidx), nm, status);
 #pragma unroll
             for (int jj = 0; jj < G::NB; ++jj)
                 if (j0 + jj < cur.width) {
@@ -455,7 +486,7 @@ __device__ __forceinline__ void clenshaw_stage(const MeshView<R> *sv, const Stag
                 }
         }
         for (int j = 8; j < cur.width; ++j) {               // rare: slices wider than 8
-            const int qq = __ldg(m.col + cur.base + 32 * j);
+            const int qq = DECBPM_IDX(__ldg(m.col + cur.base + 32 * j), m.n0, status);
             const R xx = __ldg(m.xval + cur.base + 32 * j);
             const Pack<R, FPT> gg = ld_pack<R, FPT>(g + (size_t)qq * BPAD + fo);
 #pragma unroll
@@ -513,7 +544,8 @@ __device__ __forceinline__ void clenshaw_stage(const MeshView<R> *sv, const Stag
 //   theta_p = v_p h + sum_q c_pq |src_q|^2 phi(sigma_q, h),  dst_p = src_p e^{-sigma_p h} e^{i theta_p}
 template <typename R, int FPT>
 __device__ __forceinline__ void element_kerr_item(const MeshView<R> &m, int local_item, R hh, int bpad_log2,
-                                                  const typename CT<R>::c2 *src, typename CT<R>::c2 *dst) {
+                                                  const typename CT<R>::c2 *src, typename CT<R>::c2 *dst,
+                                                  int *status) {
     using C = typename CT<R>::c2;
     const int lane = threadIdx.x & 31;
     const int tpr_log2 = bpad_log2 - (FPT == 8 ? 3 : FPT == 4 ? 2 : FPT == 2 ? 1 : 0);
@@ -533,7 +565,7 @@ __device__ __forceinline__ void element_kerr_item(const MeshView<R> &m, int loca
 #pragma unroll
     for (int f = 0; f < FPT; ++f) rate[f] = cd * (s.v[f].x * s.v[f].x + s.v[f].y * s.v[f].y);
     for (int j = 0; j < width; ++j) {
-        const int q = __ldg(m.col + base + 32 * j);
+        const int q = DECBPM_IDX(__ldg(m.col + base + 32 * j), m.n0, status);
         const R cq = __ldg(m.coff + base + 32 * j);
         R dq, pq;
         diag_factors(__ldg(m.sigma + q), hh, dq, pq);
@@ -632,7 +664,7 @@ __global__ void __launch_bounds__(256, MarchMinBlocks<R>::value) march_kernel(Ma
                 if (!grid_barrier(P.barrier, target, P.status, P.timeout_ns)) return;
             } else {
                 for_my_items(P, s_begin, P.total_items, [&](const MeshView<R> &m, int li) {
-                    element_kerr_item<R, FPT>(m, li, hh, bl, m.psi, m.b[0]);
+                    element_kerr_item<R, FPT>(m, li, hh, bl, m.psi, m.b[0], P.status);
                 });
                 if (!grid_barrier(P.barrier, target, P.status, P.timeout_ns)) return;
                 for_my_items(P, s_begin, P.total_items, [&](const MeshView<R> &m, int li) {
@@ -648,12 +680,12 @@ __global__ void __launch_bounds__(256, MarchMinBlocks<R>::value) march_kernel(Ma
                 if (s_view[i].M > k) s_coef[i] = s_view[i].coef[k];
             __syncthreads();
             clenshaw_stage<R, BPAD, FPT_>(s_view, s_coef, s_begin, P.n_meshes, P.active_items[s], k, h_post,
-                                          P.kerr_mode, P.forward_walk == 0);
+                                          P.kerr_mode, P.forward_walk == 0, P.status);
             if (!grid_barrier(P.barrier, target, P.status, P.timeout_ns)) return;
         }
         if (P.kerr_mode != 0) {
             for_my_items(P, s_begin, P.total_items, [&](const MeshView<R> &m, int li) {
-                element_kerr_item<R, FPT>(m, li, h_post, bl, m.b[0], m.psi);
+                element_kerr_item<R, FPT>(m, li, h_post, bl, m.b[0], m.psi, P.status);
             });
             if (!grid_barrier(P.barrier, target, P.status, P.timeout_ns)) return;
         }
@@ -780,11 +812,124 @@ __device__ __forceinline__ TileRange tile_range(const MarchParams<float> &P, int
 // sequence as the fills, across stage and step boundaries: descriptors are
 // static, only the field copies wait for the grid barrier.
 constexpr int kLookAhead = 4;           // per copy warp, i.e. 4 D tiles ahead
-constexpr int kLookInts = 104;        // 96 halo rows, descriptor (4), tile, pad
+constexpr int kDepInts = 32;            // dependency list of a tile: count, then up to 31 tiles
+constexpr int kLookDeps = 104;          // entry offset of the dependency list (dataflow march)
+constexpr int kLookCoef = kLookDeps + kDepInts;   // and of the tile's stage coefficients (8 int32)
+constexpr int kLookInts = kLookCoef + 8;  // 96 halo rows, descriptor (4), tile, mesh, pad, deps, coefficients
+constexpr int kHdrCoef = 32;            // slot header: descriptor (16 B), mesh and tile (8 B), pad, StageCoef
 struct LookCursor {
     int s, i;           // stage and index in the stage's range of the next tile to load
     TileRange R;
 };
+
+// ------------------------------------------------------------ dataflow march
+// The dataflow variant of the tile-staged march has no grid barrier between
+// Clenshaw stages.  Every tile keeps a completion counter (the epoch
+// step * S + s + 1 of the last stage it finished); before a copy warp loads
+// tile t for stage s it waits until every tile in t's dependency list (t
+// itself and the tiles holding t's halo rows, i.e. the tiles adjacent to t
+// in the operator graph, a symmetric relation) has finished the mesh's
+// previous stage.  That covers both hazards of the three rotating buffers:
+// b_{k+1} of the neighbours is complete (read after write), and b_{k+3},
+// which b_k overwrites, was last read by the neighbours in stages k+2 and
+// k+1 (write after read).  Each mesh's tiles are split into fixed per-CTA
+// chunks, so a tile always lives on the same CTA; a CTA walks its chunks
+// (meshes in plan order) forwards on even epochs and backwards on odd ones,
+// a backward walk starting flow_skip tiles before the previous walk's end
+// and taking those last tiles at its own end.  The first tiles of a stage
+// then depend on tiles finished several tiles earlier, and most reads of a
+// stage's first tiles hit L2.  A publisher warp turns the compute warps'
+// tile completions into counter stores.  Progress: the earliest unfinished
+// (epoch, position) item of any CTA depends only on finished items of the
+// previous epoch, all CTAs being co-resident (cooperative launch); every wait
+// is bounded.
+struct FlowRange {
+    int base, n, skip;
+    bool rev;
+    const int32_t *tiles;
+    __device__ int at(int i) const {
+        const int p = rev ? n - 1 - (i + skip) % n : i;
+        return __ldg(tiles + base + p);
+    }
+};
+__device__ __forceinline__ FlowRange flow_range(const MarchParams<float> &P, int step, int s) {
+    const int a = __ldg(P.active_meshes + s);
+    FlowRange R;
+    R.base = __ldg(P.cta_ptr + blockIdx.x);
+    R.n = __ldg(P.cta_cnt + blockIdx.x * P.n_meshes + a - 1);
+    R.skip = P.flow_skip;
+    R.rev = P.forward_walk == 0 && (((step & P.S) ^ s) & 1);     // parity of the epoch step * S + s
+    R.tiles = P.cta_tiles;
+    return R;
+}
+struct FlowCursor {
+    int step, s, i;
+    FlowRange R;
+};
+__device__ __forceinline__ int flow_next(FlowCursor &c, const MarchParams<float> &P) {
+    for (int guard = 0; guard <= P.S; ++guard) {
+        if (c.i < c.R.n) return c.R.at(c.i++);
+        if (c.s + 1 < P.S) {
+            ++c.s;
+        } else {
+            c.s = 0;
+            ++c.step;
+        }
+        c.R = flow_range(P, c.step, c.s);
+        c.i = 0;
+    }
+    return -1;
+}
+__device__ __forceinline__ int flow_next_n(FlowCursor &c, const MarchParams<float> &P, int n) {
+    int t = -1;
+    for (int i = 0; i < n; ++i) t = flow_next(c, P);
+    return t;
+}
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned *p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_relaxed_u32(unsigned *p, unsigned v) {
+    asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ void fence_acq_rel_gpu() { asm volatile("fence.acq_rel.gpu;" ::: "memory"); }
+__device__ __forceinline__ void red_release_cta_shared(unsigned *p, unsigned v) {
+    asm volatile("red.release.cta.shared::cta.add.u32 [%0], %1;" ::"r"(smem_u32(p)), "r"(v) : "memory");
+}
+__device__ __forceinline__ unsigned ld_acquire_cta_shared(const unsigned *p) {
+    unsigned v;
+    asm volatile("ld.acquire.cta.shared::cta.u32 %0, [%1];" : "=r"(v) : "r"(smem_u32(p)) : "memory");
+    return v;
+}
+// Copy warp: wait (bounded) until every tile in the dependency list of the
+// look-ahead entry has reached epoch `need` (counters compared modulo 2^32).
+__device__ __forceinline__ bool flow_wait_deps(const int *entry, const MeshView<float> &m, unsigned need,
+                                               const MarchParams<float> &P) {
+    const int lane = threadIdx.x & 31;
+    const int cnt = min(entry[kLookDeps], kDepInts - 1);
+    bool ok = true;
+    if (lane < cnt) {
+        const int dep = DECBPM_IDX(entry[kLookDeps + 1 + lane], (m.n0 + kTileRows - 1) / kTileRows, P.status);
+        const unsigned *f = P.tile_done + m.tile_begin + dep;
+        if (int(ld_acquire_u32(f) - need) < 0) {
+            const long long t0 = global_ns();
+            for (unsigned spins = 1;; ++spins) {
+                __nanosleep(64);
+                if (int(ld_acquire_u32(f) - need) >= 0) break;
+                if ((spins & 63u) == 0) {
+                    if (*(volatile int *)P.status != 0) { ok = false; break; }
+                    if (global_ns() - t0 > P.timeout_ns) {
+                        atomicCAS(P.status, 0, -4);
+                        ok = false;
+                        break;
+                    }
+                }
+            }
+        }
+    }
+    return __all_sync(0xffffffffu, ok);
+}
 
 // Next tile of the fill sequence after the cursor (or -1 if this CTA has
 // none in any stage); advances the cursor.  look_next_n skips n - 1 tiles.
@@ -815,9 +960,12 @@ __device__ __forceinline__ void cp_async_arrive(uint32_t bar) {
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 template <int N> __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
-// Copy warp: request the look-ahead entry of tile t (one commit group).
+// Copy warp: request the look-ahead entry of tile t (one commit group); the
+// dataflow march also fetches the tile's dependency list and its stage-k
+// coefficients.
+template <bool FLOW = false>
 __device__ __forceinline__ void look_issue(int *entry, int t, const MeshView<float> *sv, const int32_t *s_tbeg,
-                                           int n_meshes) {
+                                           int n_meshes, int k = 0) {
     const int lane = threadIdx.x & 31;
     int mi = 0, tl = 0;
     if (t >= 0) {
@@ -825,6 +973,10 @@ __device__ __forceinline__ void look_issue(int *entry, int t, const MeshView<flo
         tl = t - s_tbeg[mi];
         if (lane < 24) cp_async16(smem_u32(entry + 4 * lane), sv[mi].halo_rows + (size_t)tl * (32 * kHaloRegs) + 4 * lane);
         if (lane == 24) cp_async16(smem_u32(entry + 96), sv[mi].tdesc + 8 * (size_t)tl);
+        if (FLOW && lane < kDepInts / 4)
+            cp_async16(smem_u32(entry + kLookDeps + 4 * lane), sv[mi].tdeps + (size_t)tl * kDepInts + 4 * lane);
+        if (FLOW && lane >= 26 && lane < 28)
+            cp_async16(smem_u32(entry + kLookCoef + 4 * (lane - 26)), reinterpret_cast<const int4 *>(sv[mi].coef + k) + (lane - 26));
     }
     if (lane == 25) { entry[100] = t; entry[101] = mi; entry[102] = tl; }   // (the fill and the compute warps
     cp_async_commit();                                                    //  need no mesh search)
@@ -833,13 +985,18 @@ __device__ __forceinline__ void look_issue(int *entry, int t, const MeshView<flo
 // Copy warp: fill `slot` with everything the tile of look-ahead `entry` needs in stage k.  The
 // contiguous blocks (tile rows, SELL entries, descriptor) are bulk copies;
 // the scattered halo rows are 16-byte cp.async copies, eight lanes per row.
+// The dataflow march (FLOW) takes the tile's stage coefficients from the
+// look-ahead entry (the CTA's roles may be in different stages) and passes
+// them to the compute warps in the slot header; its copy warp has fenced the
+// async proxy after the dependency wait, before the bulk copies.
+template <bool FLOW = false>
 __device__ __forceinline__ void tile_fill(const int *entry, const MeshView<float> *sv, const StageCoef<float> *scoef,
                                           int k, char *slot, uint32_t bar, const MarchParams<float> &P) {
     const int lane = threadIdx.x & 31;
     const int4 dsc = *reinterpret_cast<const int4 *>(entry + 96);
     const int mi = entry[101], tl = entry[102];
     const MeshView<float> &m = sv[mi];
-    const int flags = scoef[mi].flags;
+    const int flags = FLOW ? entry[kLookCoef + 6] : scoef[mi].flags;
     const int r0 = tl * kTileRows, nrows = min(kTileRows, m.n0 - r0);
     const int e0 = dsc.x, ne = dsc.y, ovf = dsc.z, nh = dsc.w;
     const float2 *g = (flags & kGisPsi) ? m.psi : m.b[(k + 1) % 3];
@@ -849,7 +1006,7 @@ __device__ __forceinline__ void tile_fill(const int *entry, const MeshView<float
     for (int u = 0; u < 8 * kHaloRegs; ++u) {
         const int r = (lane >> 3) + 4 * u;
         if (r >= nh) break;
-        const int q = entry[r];
+        const int q = DECBPM_IDX(entry[r], m.n0, P.status);
         cp_async16(base + unsigned(kTileRows + r) * 128u + 16u * (lane & 7), g + (size_t)q * 16 + 2 * (lane & 7));
     }
     cp_async_arrive(bar);
@@ -862,6 +1019,14 @@ __device__ __forceinline__ void tile_fill(const int *entry, const MeshView<float
         // mesh and local tile index for the compute warps, next to the descriptor
         // (written before the arrive, whose release orders it before their wait)
         asm volatile("st.shared.v2.s32 [%0], {%1, %2};" ::"r"(base + P.off_hdr + 16), "r"(mi), "r"(tl) : "memory");
+        if constexpr (FLOW) {
+            const int4 c0 = *reinterpret_cast<const int4 *>(entry + kLookCoef);
+            const int4 c1 = *reinterpret_cast<const int4 *>(entry + kLookCoef + 4);
+            asm volatile("st.shared.v4.s32 [%0], {%1, %2, %3, %4};" ::"r"(base + P.off_hdr + kHdrCoef), "r"(c0.x),
+                         "r"(c0.y), "r"(c0.z), "r"(c0.w) : "memory");
+            asm volatile("st.shared.v4.s32 [%0], {%1, %2, %3, %4};" ::"r"(base + P.off_hdr + kHdrCoef + 16), "r"(c1.x),
+                         "r"(c1.y), "r"(c1.z), "r"(c1.w) : "memory");
+        }
         mbar_arrive_expect_tx(bar, total);
     }
     __syncwarp();
@@ -872,9 +1037,22 @@ __device__ __forceinline__ void tile_fill(const int *entry, const MeshView<float
     if (lane == 4 && ne > 0) bulk_g2s(base + P.off_x, m.xval + e0, unsigned(ne) * 4u, bar);
     if (lane == 5) bulk_g2s(base + P.off_hdr, reinterpret_cast<const int4 *>(m.tdesc) + 2 * tl + 1, 16u, bar);
     for (int j = lane + 32 * kHaloRegs; j < nh; j += 32) {      // rare: more halo rows than held ahead
-        const int q = __ldg(m.halo_ovf + ovf + j - 32 * kHaloRegs);
+        const int q = DECBPM_IDX(__ldg(m.halo_ovf + ovf + j - 32 * kHaloRegs), m.n0, P.status);
         bulk_g2s(base + unsigned(kTileRows + j) * 128u, g + (size_t)q * 16, 128u, bar);
     }
+}
+
+__device__ __forceinline__ StageCoef<float> lds_stage_coef(uint32_t addr) {
+    float4 a, b;
+    asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];" : "=f"(a.x), "=f"(a.y), "=f"(a.z), "=f"(a.w) : "r"(addr));
+    asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];" : "=f"(b.x), "=f"(b.y), "=f"(b.z), "=f"(b.w) : "r"(addr + 16));
+    StageCoef<float> c;
+    c.alpha = make_float2(a.x, a.y);
+    c.beta = make_float2(a.z, a.w);
+    c.alpha_lo = make_float2(b.x, b.y);
+    c.flags = __float_as_int(b.z);
+    c.pad = __float_as_int(b.w);
+    return c;
 }
 
 __device__ __forceinline__ uint32_t lds_u16(uint32_t addr) {
@@ -933,6 +1111,7 @@ __device__ __forceinline__ float2 f2_unpack(cf2 a) {
 // and x_pq.  Arithmetic order is that of the row kernel: for each
 // neighbour in SELL order acc += x (g_p - g_q), then
 // out = alpha psi (+ alpha_lo psi) + beta (acc - g_p) - h.
+template <bool FLOW = false>
 __device__ __forceinline__ void tile_compute(const MeshView<float> *sv, const StageCoef<float> *scoef, int k,
                                              const char *slot,
                                              float h_post, int kerr_mode, const MarchParams<float> &P) {
@@ -941,7 +1120,7 @@ __device__ __forceinline__ void tile_compute(const MeshView<float> *sv, const St
     int mi, tl;                                            // written by the copy warp next to the descriptor
     asm volatile("ld.shared.v2.s32 {%0, %1}, [%2];" : "=r"(mi), "=r"(tl) : "r"(base + P.off_hdr + 16));
     const MeshView<float> &m = sv[mi];
-    const StageCoef<float> sc = scoef[mi];
+    const StageCoef<float> sc = FLOW ? lds_stage_coef(base + P.off_hdr + kHdrCoef) : scoef[mi];
     const int lr = warp * 8 + (lane >> 2);                 // row in the tile
     const int row = tl * kTileRows + lr;
     if (row >= m.n0) return;
@@ -974,7 +1153,7 @@ __device__ __forceinline__ void tile_compute(const MeshView<float> *sv, const St
         cf2 gq[4][4], xv[4];
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
-            const uint32_t off = lds_u16(lc + 64 * (j + u));
+            const uint32_t off = DECBPM_IDX(lds_u16(lc + 64 * (j + u)), uint32_t(P.off_psi), P.status);
             const float x = lds_f32(xs + 128 * (j + u));
             xv[u] = f2_pack(x, x);
             lds_c2(g1 + off, gq[u][0], gq[u][1]);
@@ -987,7 +1166,7 @@ __device__ __forceinline__ void tile_compute(const MeshView<float> *sv, const St
     }
     for (; j < width; ++j) {
         cf2 gq[4];
-        const uint32_t off = lds_u16(lc + 64 * j);
+        const uint32_t off = DECBPM_IDX(lds_u16(lc + 64 * j), uint32_t(P.off_psi), P.status);
         const float x = lds_f32(xs + 128 * j);
         const cf2 xv = f2_pack(x, x);
         lds_c2(g1 + off, gq[0], gq[1]);
@@ -1036,14 +1215,20 @@ __device__ __forceinline__ void tile_compute(const MeshView<float> *sv, const St
     stg_c2(dst + (size_t)row * 16 + 2 * c2, out[2], out[3]);
 }
 
-// The whole launch as seen by one role: the copy warp (COPIER) or a compute
-// warp.  Both take the same grid barriers; each role's registers are live
-// only in its own instantiation.
-template <bool COPIER>
-__device__ __forceinline__ void tile_march_role(int copier,const MarchParams<float> &P, char *s_ring, const int32_t *s_begin,
-                                                const int32_t *s_tbeg, const MeshView<float> *s_view,
-                                                StageCoef<float> *s_coef, unsigned long long *s_full,
-                                                unsigned long long *s_empty, int *s_look) {
+// The whole launch as seen by one role: a copy warp (COPIER), a compute
+// warp, or (dataflow march only) the publisher warp (PUBLISHER).  All roles
+// take the same grid barriers; each role's registers are live only in its own
+// instantiation.  The barrier march (FLOW = false) ends every stage with a
+// grid barrier; the dataflow march replaces those by the per-tile dependency
+// waits (see FlowRange) and keeps grid barriers only around the passes over
+// all rows (the first half step's diagonal flow, the element-averaged Kerr
+// flow).
+template <bool COPIER, bool FLOW, bool PUBLISHER = false>
+__device__ __forceinline__ void tile_march_role(int copier, const MarchParams<float> &P, char *s_ring,
+                                                const int32_t *s_begin, const int32_t *s_tbeg,
+                                                const MeshView<float> *s_view, StageCoef<float> *s_coef,
+                                                unsigned long long *s_full, unsigned long long *s_empty, int *s_look,
+                                                unsigned *s_done) {
     constexpr int FPT = Geo<float, 16>::FPT;
     const int lane = threadIdx.x & 31;
     unsigned long long target = 0;
@@ -1051,14 +1236,24 @@ __device__ __forceinline__ void tile_march_role(int copier,const MarchParams<flo
     const int bl = Geo<float, 16>::TPR_LOG2 + Geo<float, 16>::FPT_LOG2;
     const unsigned D = unsigned(P.n_slots);
     unsigned seq = 0;                                      // tiles filled / consumed so far by this CTA
-    LookCursor cur{0, 0, tile_range(P, 0)};
+    LookCursor cur{0, 0, TileRange{}};
+    FlowCursor fcur{0, 0, 0, FlowRange{}};
+    if constexpr (FLOW) fcur.R = flow_range(P, 0, 0);
+    else cur.R = tile_range(P, 0);
+    unsigned seen = 0;           // publisher: compute-warp tile completions seen (and fenced) so far
     int *ring = s_look + copier * (kLookAhead * kLookInts);
     if constexpr (COPIER) {
         fence_proxy_async_global();
         if (copier < int(D))
-            for (int e = 0; e < kLookAhead; ++e)
-                look_issue(ring + e * kLookInts, look_next_n(cur, P, e == 0 ? copier + 1 : int(D)), s_view, s_tbeg,
-                           P.n_meshes);
+            for (int e = 0; e < kLookAhead; ++e) {
+                const int nskip = e == 0 ? copier + 1 : int(D);
+                if constexpr (FLOW) {
+                    const int t = flow_next_n(fcur, P, nskip);
+                    look_issue<true>(ring + e * kLookInts, t, s_view, s_tbeg, P.n_meshes, P.S - 1 - fcur.s);
+                }
+                else
+                    look_issue(ring + e * kLookInts, look_next_n(cur, P, nskip), s_view, s_tbeg, P.n_meshes);
+            }
     }
     for (int step = 0; step < P.n_steps; ++step) {
         if (step == 0 && P.pre_half) {
@@ -1071,7 +1266,7 @@ __device__ __forceinline__ void tile_march_role(int copier,const MarchParams<flo
                 if constexpr (COPIER) fence_proxy_async_global();   // other CTAs' writes, then bulk reads
             } else {
                 for_my_items(P, s_begin, P.total_items, [&](const MeshView<float> &m, int li) {
-                    element_kerr_item<float, FPT>(m, li, hh, bl, m.psi, m.b[0]);
+                    element_kerr_item<float, FPT>(m, li, hh, bl, m.psi, m.b[0], P.status);
                 });
                 if (!grid_barrier(P.barrier, target, P.status, P.timeout_ns)) return;
                 if constexpr (COPIER) fence_proxy_async_global();   // other CTAs' writes, then bulk reads
@@ -1086,53 +1281,111 @@ __device__ __forceinline__ void tile_march_role(int copier,const MarchParams<flo
         const float h_post = (step == P.n_steps - 1 && P.post_half) ? hh : h;
         for (int s = 0; s < P.S; ++s) {
             const int k = P.S - 1 - s;
-            for (int i = threadIdx.x; i < P.n_meshes; i += blockDim.x)
-                if (s_view[i].M > k) s_coef[i] = s_view[i].coef[k];
-            __syncthreads();
-            const TileRange R = tile_range(P, s);
+            if constexpr (!FLOW) {
+                for (int i = threadIdx.x; i < P.n_meshes; i += blockDim.x)
+                    if (s_view[i].M > k) s_coef[i] = s_view[i].coef[k];
+                __syncthreads();
+            }
+            int n_tiles;
+            FlowRange FR{};
+            if constexpr (FLOW) {
+                FR = flow_range(P, step, s);
+                n_tiles = FR.n;
+            } else {
+                n_tiles = tile_range(P, s).n;
+            }
+            const unsigned epoch = unsigned(step) * unsigned(P.S) + unsigned(s);   // epochs before this stage
             bool ok = true;
-            for (int i = 0; i < R.n && ok; ++i) {
+            for (int i = 0; i < n_tiles && ok; ++i) {
                 const unsigned q = seq + unsigned(i), sl = q % D;
-                if constexpr (COPIER) {
+                if constexpr (PUBLISHER) {
+                    // tile q is finished once all compute warps counted it; one fence
+                    // covers every tile seen finished so far (counts compared modulo 2^32)
+                    const unsigned need = (q + 1u) * unsigned(kTileComputeWarps);
+                    if (int(seen - need) < 0) {
+                        unsigned c = ld_acquire_cta_shared(s_done);
+                        if (int(c - need) < 0) {
+                            const long long t0 = global_ns();
+                            for (unsigned spins = 1;; ++spins) {
+                                __nanosleep(64);
+                                c = ld_acquire_cta_shared(s_done);
+                                if (int(c - need) >= 0) break;
+                                if ((spins & 63u) == 0) {
+                                    if (*(volatile int *)P.status != 0) { ok = false; break; }
+                                    if (global_ns() - t0 > P.timeout_ns) {
+                                        atomicCAS(P.status, 0, -4);
+                                        ok = false;
+                                        break;
+                                    }
+                                }
+                            }
+                        }
+                        seen = c;
+                        fence_acq_rel_gpu();
+                    }
+                    if (ok && lane == 0) st_relaxed_u32(P.tile_done + FR.at(i), epoch + 1u);
+                } else if constexpr (COPIER) {
                     if (int(sl) != copier) continue;              // slot sl belongs to copy warp sl
-                    if (q >= D) ok = mbar_wait(smem_u32(&s_empty[sl]), ((q / D) - 1u) & 1u, P.status, P.timeout_ns);
+                    int *entry = ring + ((q / D) % kLookAhead) * kLookInts;
+                    cp_async_wait<kLookAhead - 1>();           // this entry's group has landed
+                    __syncwarp();
+                    if constexpr (FLOW) {
+                        // the tile's neighbours finished the mesh's previous stage: the
+                        // previous step's last stage at the mesh's top stage, else stage s - 1
+                        const int M = s_view[entry[101]].M;
+                        const unsigned need = (k == M - 1) ? unsigned(step) * unsigned(P.S) : epoch;
+                        ok = flow_wait_deps(entry, s_view[entry[101]], need, P);
+                        if (ok) fence_proxy_async_global();     // the acquired stores, then bulk reads
+                    }
+                    if (ok && q >= D) ok = mbar_wait(smem_u32(&s_empty[sl]), ((q / D) - 1u) & 1u, P.status, P.timeout_ns);
                     if (ok) {
-                        int *entry = ring + ((q / D) % kLookAhead) * kLookInts;
-                        cp_async_wait<kLookAhead - 1>();       // this entry's group has landed
+                        tile_fill<FLOW>(entry, s_view, s_coef, k, s_ring + (size_t)sl * P.slot_bytes,
+                                        smem_u32(&s_full[sl]), P);
                         __syncwarp();
-                        tile_fill(entry, s_view, s_coef, k, s_ring + (size_t)sl * P.slot_bytes,
-                                  smem_u32(&s_full[sl]), P);
-                        __syncwarp();
-                        look_issue(entry, look_next_n(cur, P, int(D)), s_view, s_tbeg, P.n_meshes);
+                        if constexpr (FLOW) {
+                            const int t = flow_next_n(fcur, P, int(D));
+                            look_issue<true>(entry, t, s_view, s_tbeg, P.n_meshes, P.S - 1 - fcur.s);
+                        }
+                        else
+                            look_issue(entry, look_next_n(cur, P, int(D)), s_view, s_tbeg, P.n_meshes);
                     }
                 } else {
                     ok = mbar_wait(smem_u32(&s_full[sl]), (q / D) & 1u, P.status, P.timeout_ns);
                     if (ok) {
-                        tile_compute(s_view, s_coef, k, s_ring + (size_t)sl * P.slot_bytes,
-                                     h_post, P.kerr_mode, P);
+                        tile_compute<FLOW>(s_view, s_coef, k, s_ring + (size_t)sl * P.slot_bytes,
+                                           h_post, P.kerr_mode, P);
                         __syncwarp();
-                        if (lane == 0) mbar_arrive(smem_u32(&s_empty[sl]));
+                        if (lane == 0) {
+                            mbar_arrive(smem_u32(&s_empty[sl]));
+                            if constexpr (FLOW) red_release_cta_shared(s_done, 1u);
+                        }
                     }
                 }
             }
-            seq += unsigned(R.n);
+            seq += unsigned(n_tiles);
             if (!ok) return;
-            fence_proxy_async_global();
-            if (!grid_barrier(P.barrier, target, P.status, P.timeout_ns)) return;
+            if constexpr (!FLOW) {
+                fence_proxy_async_global();
+                if (!grid_barrier(P.barrier, target, P.status, P.timeout_ns)) return;
                 if constexpr (COPIER) fence_proxy_async_global();   // other CTAs' writes, then bulk reads
+            }
         }
         if (P.kerr_mode != 0) {
+            if constexpr (FLOW) {          // every tile's final stage is done before the pass reads S
+                if (!grid_barrier(P.barrier, target, P.status, P.timeout_ns)) return;
+            }
             for_my_items(P, s_begin, P.total_items, [&](const MeshView<float> &m, int li) {
-                element_kerr_item<float, FPT>(m, li, h_post, bl, m.b[0], m.psi);
+                element_kerr_item<float, FPT>(m, li, h_post, bl, m.b[0], m.psi, P.status);
             });
             fence_proxy_async_global();
             if (!grid_barrier(P.barrier, target, P.status, P.timeout_ns)) return;
-                if constexpr (COPIER) fence_proxy_async_global();   // other CTAs' writes, then bulk reads
+            if constexpr (COPIER) fence_proxy_async_global();   // other CTAs' writes, then bulk reads
         }
     }
 }
 
-__global__ void __launch_bounds__(kTileThreads, 1) march_tile_kernel(MarchParams<float> P) {
+template <bool FLOW>
+__device__ __forceinline__ void tile_march_body(const MarchParams<float> &P) {
     extern __shared__ __align__(128) char s_ring[];
     __shared__ int32_t s_begin[kMaxMeshes + 1];
     __shared__ int32_t s_tbeg[kMaxMeshes + 1];
@@ -1140,6 +1393,7 @@ __global__ void __launch_bounds__(kTileThreads, 1) march_tile_kernel(MarchParams
     __shared__ StageCoef<float> s_coef[kMaxMeshes];
     __shared__ __align__(8) unsigned long long s_full[kMaxSlots], s_empty[kMaxSlots];
     __shared__ __align__(16) int s_look[kTileCopyWarps * kLookAhead * kLookInts];
+    __shared__ unsigned s_done;                       // dataflow march: tiles x compute warps finished
     for (int i = threadIdx.x; i < P.n_meshes; i += blockDim.x) {
         s_begin[i] = P.meshes[i].item_begin;
         s_tbeg[i] = P.meshes[i].tile_begin;
@@ -1149,17 +1403,30 @@ __global__ void __launch_bounds__(kTileThreads, 1) march_tile_kernel(MarchParams
         mbar_init(smem_u32(&s_full[threadIdx.x]), 1);
         mbar_init(smem_u32(&s_empty[threadIdx.x]), kTileComputeWarps);
     }
+    if (threadIdx.x == 0) s_done = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     __syncthreads();
     const int warp = threadIdx.x >> 5;
-    if (warp >= kTileComputeWarps) {
-        tile_march_role<true>(warp - kTileComputeWarps, P, s_ring, s_begin, s_tbeg, s_view, s_coef, s_full, s_empty,
-                              s_look);
+    if (warp >= kTileComputeWarps + kTileCopyWarps) {
+        if constexpr (FLOW)
+            tile_march_role<false, true, true>(0, P, s_ring, s_begin, s_tbeg, s_view, s_coef, s_full, s_empty, s_look,
+                                               &s_done);
+    } else if (warp >= kTileComputeWarps) {
+        tile_march_role<true, FLOW>(warp - kTileComputeWarps, P, s_ring, s_begin, s_tbeg, s_view, s_coef, s_full,
+                                    s_empty, s_look, &s_done);
         cp_async_wait<0>();           // no look-ahead copy may land after the CTA exits
     } else {
-        tile_march_role<false>(0, P, s_ring, s_begin, s_tbeg, s_view, s_coef, s_full, s_empty, s_look);
+        tile_march_role<false, FLOW>(0, P, s_ring, s_begin, s_tbeg, s_view, s_coef, s_full, s_empty, s_look, &s_done);
     }
 }
+
+__global__ void __launch_bounds__(kTileThreads, 1) march_tile_kernel(MarchParams<float> P) { tile_march_body<false>(P); }
+
+// The dataflow march: the tile-staged kernel without grid barriers between
+// stages, plus a publisher warp.
+constexpr int kFlowThreads = kTileThreads + 32;
+constexpr int kDefaultFlowSkip = 8;
+__global__ void __launch_bounds__(kFlowThreads, 1) march_flow_kernel(MarchParams<float> P) { tile_march_body<true>(P); }
 
 // ------------------------------------------------------------ stage-pair march
 // Two Clenshaw stages per grid-wide pass (complex64, 16 fields).  For a tile
@@ -1313,12 +1580,12 @@ __device__ __forceinline__ void pair_fill(const int *entry, const MeshView<float
     const uint32_t base = smem_u32(slot);
     // scattered halo rows, 16-byte cp.async, 8 lanes per 128-byte row
     for (int u = lane >> 3; u < ng_halo; u += 4) {
-        const int q = entry[u];
+        const int q = DECBPM_IDX(entry[u], m.n0, P.status);
         cp_async16(base + unsigned(kTileRows + u) * 128u + 16u * (lane & 7), g + (size_t)q * 16 + 2 * (lane & 7));
     }
     if (r_halo)
         for (int u = lane >> 3; u < nh1; u += 4) {
-            const int q = entry[u];
+            const int q = DECBPM_IDX(entry[u], m.n0, P.status);
             cp_async16(base + unsigned(P.off_h) + unsigned(kTileRows + u) * 128u + 16u * (lane & 7),
                        Rin + (size_t)q * 16 + 2 * (lane & 7));
         }
@@ -1347,7 +1614,7 @@ __device__ __forceinline__ void pair_fill(const int *entry, const MeshView<float
 // acc = sum_j x_j (g_p - g_q) over `width` SELL entries at lc (offsets) / xs (x_pq),
 // entry j at lc + 64 j and xs + 128 j; g rows in the window at g1 / g2 (this lane's chunks)
 __device__ __forceinline__ void pair_gather(uint32_t g1, uint32_t g2, uint32_t lc, uint32_t xs, int width,
-                                            const cf2 gp[4], cf2 acc[4]) {
+                                            const cf2 gp[4], cf2 acc[4], uint32_t lim, int *status) {
 #pragma unroll
     for (int f = 0; f < 4; ++f) acc[f] = 0ull;
     int j = 0;
@@ -1355,7 +1622,7 @@ __device__ __forceinline__ void pair_gather(uint32_t g1, uint32_t g2, uint32_t l
         cf2 gq[4][4], xv[4];
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
-            const uint32_t off = lds_u16(lc + 64 * (j + u));
+            const uint32_t off = DECBPM_IDX(lds_u16(lc + 64 * (j + u)), lim, status);
             const float x = lds_f32(xs + 128 * (j + u));
             xv[u] = f2_pack(x, x);
             lds_c2(g1 + off, gq[u][0], gq[u][1]);
@@ -1368,7 +1635,7 @@ __device__ __forceinline__ void pair_gather(uint32_t g1, uint32_t g2, uint32_t l
     }
     for (; j < width; ++j) {
         cf2 gq[4];
-        const uint32_t off = lds_u16(lc + 64 * j);
+        const uint32_t off = DECBPM_IDX(lds_u16(lc + 64 * j), lim, status);
         const float x = lds_f32(xs + 128 * j);
         const cf2 xv = f2_pack(x, x);
         lds_c2(g1 + off, gq[0], gq[1]);
@@ -1406,7 +1673,7 @@ __device__ __forceinline__ void pair_row_stage1(const char *slot, int wr, bool o
         lds_c2(rw + wr * 128 + 16 * c1, rr[0], rr[1]);
         lds_c2(rw + wr * 128 + 16 * c2, rr[2], rr[3]);
     }
-    pair_gather(g1, g2, lcb, xsb, width, gp, acc);
+    pair_gather(g1, g2, lcb, xsb, width, gp, acc, uint32_t(P.w2_rows) * 128u, P.status);
     cf2 out[4];
 #pragma unroll
     for (int f = 0; f < 4; ++f) out[f] = f2_add(rr[f], f2_cmul(brr, bni, f2_sub(acc[f], gp[f])));
@@ -1444,7 +1711,7 @@ __device__ __forceinline__ void pair_row_last(const MeshView<float> &m, int p, P
         lds_c2(rw + lr * 128 + 16 * c1, hv[0], hv[1]);
         lds_c2(rw + lr * 128 + 16 * c2, hv[2], hv[3]);
     }
-    pair_gather(h1, h2, lc, xs, width, gp, acc);
+    pair_gather(h1, h2, lc, xs, width, gp, acc, uint32_t(role.two ? P.w1_rows : P.w2_rows) * 128u, P.status);
     const cf2 arr = f2_pack(c.alpha.x, c.alpha.x), ani = f2_pack(-c.alpha.y, c.alpha.y);
     const cf2 brr = f2_pack(c.beta.x, c.beta.x), bni = f2_pack(-c.beta.y, c.beta.y);
     cf2 out[4];
@@ -1610,7 +1877,7 @@ __device__ __forceinline__ void pair_march_role(int copier, const MarchParams<fl
                 if constexpr (COPIER) fence_proxy_async_global();
             } else {
                 for_my_items(P, s_begin, P.total_items, [&](const MeshView<float> &m, int li) {
-                    element_kerr_item<float, FPT>(m, li, hh, bl, m.psi, m.b[0]);
+                    element_kerr_item<float, FPT>(m, li, hh, bl, m.psi, m.b[0], P.status);
                 });
                 if (!grid_barrier(P.barrier, target, P.status, P.timeout_ns)) return;
                 for_my_items(P, s_begin, P.total_items, [&](const MeshView<float> &m, int li) {
@@ -1674,7 +1941,7 @@ __device__ __forceinline__ void pair_march_role(int copier, const MarchParams<fl
         if (P.kerr_mode != 0) {
             const int pf = P.n_passes - 1;        // the final pass parked S in its G output
             for_my_items(P, s_begin, P.total_items, [&](const MeshView<float> &m, int li) {
-                element_kerr_item<float, FPT>(m, li, h_post, bl, (pf & 1) ? m.b[0] : m.b[1], m.psi);
+                element_kerr_item<float, FPT>(m, li, h_post, bl, (pf & 1) ? m.b[0] : m.b[1], m.psi, P.status);
             });
             fence_proxy_async_global();
             if (!grid_barrier(P.barrier, target, P.status, P.timeout_ns)) return;

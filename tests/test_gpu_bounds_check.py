@@ -1,0 +1,112 @@
+"""The bounds-check build (libdecbpm_checked.so, -DDECBPM_BOUNDS_CHECK): its
+march kernels test every gather index (neighbour rows in the field buffers,
+window offsets in the tile and stage-pair kernels' shared-memory ring)
+against its buffer and report DECBPM_ERR_DEVICE_CHECK instead of reading out
+of bounds.  On consistent meshes no check fires, and the fields it produces
+are bit for bit those of the default build, in every march kernel: the row
+kernel (complex64 at 2 and 4 values per thread, complex128, one field), the
+tile-staged kernel, the dataflow kernel (its dependency lists are checked
+too) and the stage-pair kernel, with lumped and element-averaged Kerr.
+
+The checked library is loaded in a child process (DECBPM_BOUNDS_CHECK=1 in
+its environment); the parent runs the same cases on the default library."""
+import os
+import subprocess
+import sys
+import tempfile
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from paper_2608_03587_b300 import _lib as L  # noqa: E402
+from paper_2608_03587_b300 import api  # noqa: E402
+from paper_2608_03587_b300 import workloads as W  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+DEV = torch.device("cuda:0")
+
+# (vertices, fields, seed): uneven sizes and degrees, a mesh below one tile
+# and a single triangle
+SPECS = [(600, 16, 51), (2500, 9, 52), (5000, 12, 53), (90, 16, 54), (3, 16, 56)]
+
+
+def _meshes():
+    meshes, psis = [], []
+    for n, B, seed in SPECS:
+        if n == 3:
+            coords = np.array([[0.0, 0.0], [1.0, 0.0], [0.2, 0.9]])
+            tris = np.array([[0, 1, 2]], dtype=np.int32)
+        else:
+            coords, tris = W.mesh_disk_graded(4.0, n, 3.0, interfaces=(1.0,), seed=seed, grade_from=1.0)
+        V, chi = W.step_index_materials(coords, tris)
+        sigma = W.absorber_profile(coords, 4.0, 20.0)
+        meshes.append(api.Mesh(coords, tris, V, chi, sigma))
+        psis.append(W.hg_superpositions(coords, B, np.random.default_rng(seed)) * 2.0)
+    return meshes, psis
+
+
+def run_cases() -> dict:
+    """Every case on the library this process loaded: name -> final fields."""
+    meshes, psis = _meshes()
+    dz, n = 2e-3, 7
+    out = {}
+    # (precision, variant, fields per mesh (None: 9..16), row-kernel values per thread)
+    cases = [("c64", "pairs", None, 0), ("c64", "fused", None, 0), ("c64", "flow", None, 0), ("c64", "rows", None, 0),
+             ("c64", "fused", None, 2), ("c64", "rows", 4, 0), ("c128", "fused", 3, 0)]
+    for prec, variant, fields, fpt in cases:
+        dt = torch.complex64 if prec == "c64" else torch.complex128
+        ps = [p if fields is None else p[:, :fields] for p in psis]
+        plan = api.Plan(meshes, [p.shape[1] for p in ps], prec)
+        if fpt:
+            plan.set_shape("rows", values_per_thread=fpt)
+            assert plan.config()["values_per_thread"] == fpt
+        elif (prec, variant, fields) == ("c64", "fused", None):
+            out["tile_kernel_used"] = np.array(plan.config()["fused_kernel"] == 1)
+        for kerr in ("lumped", "element"):
+            t = [torch.from_numpy(np.ascontiguousarray(p)).to(DEV, dt) for p in ps]
+            plan.propagate(t, dz, n, diag_every=3, kerr=kerr, variant=variant)
+            torch.cuda.synchronize()
+            for i, x in enumerate(t):
+                out["%s_%s_%s_%d_%s_%d" % (prec, variant, fields, fpt, kerr, i)] = x.cpu().numpy()
+    # the single-field entry point (row kernel, one field)
+    x = torch.from_numpy(np.ascontiguousarray(psis[2][:, 0])).to(DEV, torch.complex128)
+    api.propagate(meshes[2], x, dz, n, kerr="element")
+    out["single_c128"] = x.cpu().numpy()
+    return out
+
+
+@pytest.mark.skipif(not torch.cuda.is_available(), reason="no CUDA device")
+def test_bounds_checked_build_gives_the_same_fields():
+    if L.CHECKED:
+        pytest.skip("this process already loaded the bounds-check build")
+    lib = L.load()
+    assert b"bounds-checked" not in lib.decbpm_version()
+    with tempfile.TemporaryDirectory() as tmp:
+        path = os.path.join(tmp, "checked.npz")
+        env = dict(os.environ, DECBPM_BOUNDS_CHECK="1")
+        res = subprocess.run([sys.executable, os.path.abspath(__file__), path], env=env, cwd=ROOT,
+                             capture_output=True, text=True, timeout=900)
+        assert res.returncode == 0, res.stdout[-3000:] + res.stderr[-3000:]
+        assert "bounds-checked" in res.stdout
+        checked = dict(np.load(path))
+    plain = run_cases()
+    assert bool(plain["tile_kernel_used"]) and bool(checked["tile_kernel_used"])
+    assert sorted(plain) == sorted(checked)
+    for k in plain:
+        assert np.array_equal(plain[k], checked[k]), k
+
+
+if __name__ == "__main__":
+    # child: DECBPM_BOUNDS_CHECK=1 selects libdecbpm_checked.so at load time;
+    # a check that fires makes the propagation raise DecbpmError (status -8)
+    ver = L.load().decbpm_version().decode()
+    assert "bounds-checked" in ver, ver
+    print(ver, flush=True)
+    np.savez(sys.argv[1], **run_cases())

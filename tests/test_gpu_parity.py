@@ -382,6 +382,67 @@ def test_stage_pair_kernel_full_bench_batch():
         assert d <= 2e-6, d
 
 
+@pytest.mark.parametrize("kerr", ["lumped", "element"])
+def test_dataflow_kernel_matches_tile_kernel(kerr):
+    """The dataflow kernel (no grid barrier between Clenshaw stages; a tile
+    waits for its neighbour tiles' previous stage) gives the tile-staged
+    kernel's fields bit for bit: meshes of uneven size and degree (meshes
+    join the march at different stages), 9..16 fields, a mesh below one tile
+    and a single triangle, three launches (diagnostics every 3 of 7 steps),
+    walk skips from 1 to beyond a CTA's share and either walk.  Repeated runs
+    of one shape are bitwise equal too (the waits order every read after the
+    write it needs, whatever the timing)."""
+    specs = [(600, 16, 51), (2500, 9, 52), (5000, 12, 53), (90, 16, 54), (40, 16, 55), (3, 16, 56),
+             (20000, 16, 57)]
+    meshes, psis = [], []
+    for n, B, seed in specs:
+        if n == 3:
+            coords = np.array([[0.0, 0.0], [1.0, 0.0], [0.2, 0.9]])
+            tris = np.array([[0, 1, 2]], dtype=np.int32)
+        else:
+            coords, tris = W.mesh_disk_graded(4.0, n, 3.0, interfaces=(1.0,), seed=seed, grade_from=1.0)
+        V, chi = W.step_index_materials(coords, tris)
+        sigma = W.absorber_profile(coords, 4.0, 20.0)
+        meshes.append(api.Mesh(coords, tris, V, chi, sigma))
+        psis.append(W.hg_superpositions(coords, B, np.random.default_rng(seed)) * 2.0)
+    plan = api.Plan(meshes, [p.shape[1] for p in psis], "c64")
+    assert plan.config()["flow_grid"] > 0
+    dz = 2e-3
+    assert len({plan.degree(i, dz) for i in range(len(specs))}) >= 3
+    ref = [to_dev(p, torch.complex64) for p in psis]
+    plan.set_shape("tile", tile_slots=3)
+    plan.propagate(ref, dz, 7, diag_every=3, kerr=kerr)
+    for slots, skip, fw, reps in ((3, 8, 0, 3), (2, 8, 0, 1), (3, 1, 0, 1), (3, 4000, 0, 1), (3, 8, 1, 1)):
+        plan.set_shape("flow", tile_slots=slots, walk_skip=skip, forward_walk=fw)
+        for _ in range(reps):
+            out = [to_dev(p, torch.complex64) for p in psis]
+            plan.propagate(out, dz, 7, diag_every=3, kerr=kerr)
+            for x, y in zip(out, ref):
+                assert torch.equal(x, y), (slots, skip, fw)
+    # the explicit variant runs it whatever shape the plan holds
+    plan.set_shape("tile", tile_slots=3)
+    out = [to_dev(p, torch.complex64) for p in psis]
+    plan.propagate(out, dz, 7, diag_every=3, kerr=kerr, variant="flow")
+    for x, y in zip(out, ref):
+        assert torch.equal(x, y)
+
+
+def test_dataflow_kernel_full_bench_batch():
+    """The bench workload at full size: a 3-step launch of the dataflow kernel
+    against the tile-staged kernel, bit for bit."""
+    wl = W.batched_fibers(n_meshes=16, fields_per_mesh=16, n_min=20_000, ratio=25.0, seed=4)
+    meshes = [api.Mesh.from_workload(m, p=wl.p) for m in wl.meshes]
+    plan = api.Plan(meshes, [16] * len(meshes), "c64")
+    assert plan.config()["flow_grid"] > 0
+    a = [to_dev(p, torch.complex64) for p in wl.psi0]
+    b = [x.clone() for x in a]
+    plan.propagate(a, wl.dz, 3, variant="flow")
+    plan.set_shape("tile", tile_slots=3)
+    plan.propagate(b, wl.dz, 3)
+    for x, y in zip(a, b):
+        assert torch.equal(x, y)
+
+
 @pytest.mark.parametrize("precision", ["c64", "c128"])
 def test_autotuner_picks_a_shape_without_changing_results(precision):
     """decbpm_plan_autotune times the FUSED launch shapes (tile-staged kernel
@@ -406,7 +467,7 @@ def test_autotuner_picks_a_shape_without_changing_results(precision):
     assert tune["from_cache"] == 0 and tune["candidates"] >= 2 and tune["ms_per_step"] > 0
     cfg = plan.config()
     assert cfg["tuned"] == 1
-    assert cfg["fused_kernel"] == {"pairs": 2, "tile": 1, "rows": 0}[tune["kernel"]]
+    assert cfg["fused_kernel"] == {"flow": 3, "pairs": 2, "tile": 1, "rows": 0}[tune["kernel"]]
     if precision == "c128":
         assert tune["kernel"] == "rows"
     b = [to_dev(p, dt) for p in psis]
@@ -419,7 +480,7 @@ def test_autotuner_picks_a_shape_without_changing_results(precision):
             assert torch.equal(x, y)
     again = api.Plan(meshes, [p.shape[1] for p in psis], precision).autotune(dz, trial_steps=2)
     assert again["from_cache"] == 1
-    keys = ("kernel", "ctas_per_sm", "tile_slots", "forward_walk")
+    keys = ("kernel", "ctas_per_sm", "tile_slots", "forward_walk", "walk_skip")
     assert {k: again[k] for k in keys} == {k: tune[k] for k in keys}
     with pytest.raises(L.DecbpmError):
         plan.autotune(dz, trial_steps=0)
@@ -432,7 +493,8 @@ def test_every_launch_shape_gives_the_same_fields(B):
     """decbpm_plan_set_shape forces each single-stage launch shape the
     autotuner searches (row kernel with 4 or 2 complex values per thread, i.e.
     8B/4B.. rows per warp item, 1..max CTAs per SM, either walk; the
-    tile-staged kernel with 3 or 2 slots): every one gives the default shape's
+    tile-staged kernel with 3 or 2 slots; the dataflow kernel with 3 or 2 slots,
+    several walk skips and either walk): every one gives the default shape's
     fields bit for bit; shapes a plan cannot run are refused."""
     specs = [(3000, 61), (700, 62)]
     meshes, psis = [], []
@@ -449,12 +511,16 @@ def test_every_launch_shape_gives_the_same_fields(B):
               for v in (4, 2) for c in (1, 2) for f in (0, 1)]
     if B == 16:
         shapes += [dict(kernel="tile", tile_slots=t) for t in (2, 3)]
+        shapes += [dict(kernel="flow", tile_slots=t, walk_skip=k, forward_walk=f)
+                   for t in (2, 3) for k in (1, 8, 1000) for f in (0, 1)]
     for sh in shapes:
         plan.set_shape(**sh)
         cfg = plan.config()
         if sh["kernel"] == "rows":
             assert cfg["values_per_thread"] == sh["values_per_thread"]
             assert cfg["rows_per_item"] == 32 * sh["values_per_thread"] // B
+        if sh["kernel"] == "flow":
+            assert cfg["fused_kernel"] == 3 and cfg["flow_skip"] == sh["walk_skip"] and cfg["flow_grid"] > 0
         out = [to_dev(p, torch.complex64) for p in psis]
         plan.propagate(out, 1e-3, 5)
         for x, y in zip(out, ref):
@@ -464,6 +530,11 @@ def test_every_launch_shape_gives_the_same_fields(B):
     if B != 16:
         with pytest.raises(L.DecbpmError):
             plan.set_shape(kernel="tile", tile_slots=2)
+        with pytest.raises(L.DecbpmError):
+            plan.set_shape(kernel="flow", tile_slots=2)
+    else:
+        with pytest.raises(L.DecbpmError):
+            plan.set_shape(kernel="flow", tile_slots=3, walk_skip=-1)
 
 
 # ------------------------------------------------------------------ edge cases

@@ -36,6 +36,19 @@ def test_library_exports_every_declared_symbol(lib):
     assert lib.decbpm_version().decode().startswith("decbpm")
 
 
+def test_bounds_checked_build_exports_the_same_entry_points():
+    """libdecbpm_checked.so (-DDECBPM_BOUNDS_CHECK) is the same library with
+    the march kernels' index checks compiled in: every declared entry point,
+    and a version string that says so."""
+    from paper_2608_03587_b300 import build as B
+    B.build(checked=True)
+    chk = ctypes.CDLL(B.CHECKED_LIB)
+    for n in declared_functions():
+        assert hasattr(chk, n), n
+    chk.decbpm_version.restype = ctypes.c_char_p
+    assert b"bounds-checked" in chk.decbpm_version()
+
+
 @pytest.fixture(scope="module")
 def fiber():
     coords, tris = W.mesh_disk_graded(4.0, 2500, 3.0, interfaces=(1.0,), seed=17, grade_from=1.0)
