@@ -581,7 +581,7 @@ def main():
     ap.add_argument("--side-steps", type=int, default=200, help="steps of the single-field side runs")
     ap.add_argument("--side-workloads", default="disk,vortex,adjoint",
                     help="side runs to make: any of disk (200k single field), vortex (1M), adjoint (300k PCF)")
-    ap.add_argument("--variant", choices=["fused", "rows", "pairs"], default="fused",
+    ap.add_argument("--variant", choices=["fused", "rows", "pairs", "flow"], default="fused",
                     help="fused: the autotuner's choice; pairs: the stage-pair kernel; rows: the row kernel")
     args = ap.parse_args()
     if args.warmup < 3:

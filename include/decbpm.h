@@ -284,6 +284,10 @@ typedef struct {
                               than the tile-staged kernel's: a publisher of tile completions) */
     int32_t flow_skip;     /* dataflow kernel: a reversed walk starts this many tiles before the previous
                               walk's end */
+    int32_t meta_items;    /* row kernel, single-mesh plans: warp items per CTA whose operator metadata
+                              (columns, weights, slice widths) a launch caches in shared memory once, so
+                              that no stage reads it from L2 again; 0: not cached (several meshes, the
+                              cache switched off, or it does not fit with the launch's CTAs per SM) */
 } decbpm_plan_config;
 int decbpm_plan_get_config(decbpm_plan_t plan, decbpm_plan_config *cfg);
 
@@ -315,14 +319,16 @@ typedef struct {
     int32_t values_per_thread; /* row kernel: complex values per thread (complex64 plans of 4+ fields: 4 or 2;
                                   so rows per warp item = 32 x this / padded fields); others: the default */
     int32_t walk_skip;     /* dataflow kernel: see decbpm_plan_config.flow_skip (0: the default, 8) */
+    int32_t no_meta_cache; /* row kernel: 1 reads the operator metadata every stage (see
+                              decbpm_plan_config.meta_items); 0: cached where it fits */
 } decbpm_tune_result;
 int decbpm_plan_autotune(decbpm_plan_t plan, double dz, int32_t kerr_mode, int32_t trial_steps, void *stream,
                          decbpm_tune_result *out);
 /* Apply a launch shape without timing (for example one that decbpm_plan_autotune
  * returned in an earlier process): variant (PAIRS, FUSED = tile-staged, FLOW,
- * ROWS), ctas_per_sm and values_per_thread (ROWS), tile_slots (PAIRS, FUSED,
- * FLOW), walk_skip (FLOW), forward_walk; ms_per_step, candidates and
- * from_cache are ignored.  Shapes the
+ * ROWS), ctas_per_sm, values_per_thread and no_meta_cache (ROWS), tile_slots
+ * (PAIRS, FUSED, FLOW), walk_skip (FLOW), forward_walk; ms_per_step,
+ * candidates and from_cache are ignored.  Shapes the
  * plan cannot run return DECBPM_ERR_UNSUPPORTED or DECBPM_ERR_INVALID_ARG. */
 int decbpm_plan_set_shape(decbpm_plan_t plan, const decbpm_tune_result *shape);
 

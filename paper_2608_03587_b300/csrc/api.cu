@@ -483,6 +483,12 @@ struct decbpm_plan_s {
     int32_t *cta_tiles = nullptr, *cta_ptr = nullptr, *cta_cnt = nullptr, *active_meshes = nullptr;
     int cta_cnt_cap = 0, active_meshes_cap = 0;
     int tune_flow = 0;                           // 1: FUSED runs the dataflow kernel
+    int tune_meta = 1;                           // row kernel, single-mesh plans: cache the item metadata
+    // the last metadata-cache decision (row_meta_cache), so launches recorded
+    // into a graph make no attribute or occupancy call
+    const void *meta_fn = nullptr;
+    int meta_grid = 0, meta_fpt = 0, meta_on = -1, meta_items = 0;
+    size_t meta_dyn = 0;
     int flow_skip = kDefaultFlowSkip;
     // graphs: key -> exec
     std::map<std::tuple<double, int64_t, int32_t, int32_t, double, int32_t>, cudaGraphExec_t> graphs;
@@ -557,6 +563,40 @@ template <typename R> static const void *march_ptr_for(int bpad, int fpt = 0) {
 
 static const void *march_kernel_ptr(int precision, int bpad, int fpt = 0) {
     return precision == DECBPM_C64 ? march_ptr_for<float>(bpad, fpt) : march_ptr_for<double>(bpad, fpt);
+}
+
+// Shared-memory metadata cache of the row kernel (see MetaCache): warp items
+// per CTA and dynamic shared-memory bytes for a launch of `grid` CTAs, or
+// {0, 0} for plans of several meshes (their stages' items differ), with the
+// cache switched off, or when the CTAs would no longer all be co-resident.
+constexpr size_t kMetaCacheMaxBytes = 96 * 1024;
+static std::pair<int, size_t> row_meta_cache_eval(decbpm_plan_t P, const void *fn, int grid, int fpt) {
+    if (P->meshes.size() != 1 || !P->tune_meta || grid < 1) return {0, 0};
+    const size_t rs = P->precision == DECBPM_C64 ? sizeof(float) : sizeof(double);
+    const int tpr = std::max(1, P->bpad / std::max(1, fpt));
+    const int E = tpr >= 8 ? 1 : 8 / tpr;
+    const int items = (P->total_items + grid - 1) / grid;
+    size_t dyn = size_t(items) * E * 32 * (4 + rs) + size_t(items) * 4;
+    dyn = (dyn + 15) / 16 * 16;
+    if (items < 1 || dyn > kMetaCacheMaxBytes) return {0, 0};
+    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kMetaCacheMaxBytes)) != cudaSuccess)
+        return {0, 0};
+    int occ = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, P->block, dyn) != cudaSuccess) return {0, 0};
+    if (occ * P->num_sms < grid) return {0, 0};
+    return {items, dyn};
+}
+static std::pair<int, size_t> row_meta_cache(decbpm_plan_t P, const void *fn, int grid, int fpt) {
+    if (P->meta_fn != fn || P->meta_grid != grid || P->meta_fpt != fpt || P->meta_on != P->tune_meta) {
+        const std::pair<int, size_t> r = row_meta_cache_eval(P, fn, grid, fpt);
+        P->meta_fn = fn;
+        P->meta_grid = grid;
+        P->meta_fpt = fpt;
+        P->meta_on = P->tune_meta;
+        P->meta_items = r.first;
+        P->meta_dyn = r.second;
+    }
+    return {P->meta_items, P->meta_dyn};
 }
 
 // Shared-memory ring of the tile-staged march: as many slots (3, else 2) of
@@ -1090,6 +1130,11 @@ static int launch_march(decbpm_plan_t P, cudaStream_t s, int n_steps, int kerr_m
             }
         }
     }
+    if (fn == march_ptr_for<R>(P->bpad, P->fpt)) {
+        const std::pair<int, size_t> mc = row_meta_cache(P, fn, int(cfg.gridDim.x), P->fpt);
+        mp.meta_items = mc.first;
+        cfg.dynamicSmemBytes = mc.second;
+    }
     CK(cudaLaunchKernelExC(&cfg, fn, args));
     return DECBPM_OK;
 }
@@ -1209,6 +1254,8 @@ static int plan_propagate_impl(decbpm_plan_t P, const decbpm_params *prm, void *
     }
     CK(cudaGetLastError());
     // capture the march + diagnostics once per parameter set, replay afterwards
+    // (the row kernel's metadata-cache decision is made here, not during capture)
+    row_meta_cache(P, march_kernel_ptr(P->precision, P->bpad, P->fpt), P->grid, P->fpt);
     auto key = std::make_tuple(prm->dz, prm->n_steps, prm->diag_every, prm->kerr_mode, default_tol(prm), prm->variant);
     bool launched = false;
     if (P->graphs_ok) {
@@ -1448,7 +1495,11 @@ static int vjp_impl(decbpm_mesh_t mesh, decbpm_plan_t P, const decbpm_params *pr
         cfg.attrs = attr;
         cfg.numAttrs = 1;
         void *args[] = {&mp};
-        CK(cudaLaunchKernelExC(&cfg, march_ptr_for<R>(bpad, P->fpt), args));
+        const void *fn = march_ptr_for<R>(bpad, P->fpt);
+        const std::pair<int, size_t> mc = row_meta_cache(P, fn, P->grid, P->fpt);
+        mp.meta_items = mc.first;
+        cfg.dynamicSmemBytes = mc.second;
+        CK(cudaLaunchKernelExC(&cfg, fn, args));
         return DECBPM_OK;
     };
     const MeshView<R> *fwd_view = reinterpret_cast<const MeshView<R> *>(P->views);
@@ -1799,7 +1850,7 @@ static int soliton_impl(decbpm_mesh_t mesh, decbpm_plan_t P, const decbpm_solito
 // plan's internal buffers (zeroed first: their contents are scratch between
 // calls).  The winner is cached for the process, keyed by the meshes'
 // content fingerprints, the field counts, the precision, dz and kerr_mode.
-struct TuneChoice { int rows, per_sm, slots, forward, pair, fpt; double ms; int flow, skip; };
+struct TuneChoice { int rows, per_sm, slots, forward, pair, fpt; double ms; int flow, skip, nometa; };
 static std::mutex g_tune_mutex;
 static std::map<std::string, TuneChoice> g_tune_cache;
 
@@ -1836,6 +1887,7 @@ static void apply_choice(decbpm_plan_t P, const TuneChoice &c) {
     P->tune_rows = c.rows;
     P->tune_pair = c.pair;
     P->tune_flow = c.flow;
+    P->tune_meta = c.nometa ? 0 : 1;
     P->flow_skip = c.skip > 0 ? c.skip : kDefaultFlowSkip;
     P->tune_slots = c.slots;
     P->forward_walk = c.forward;
@@ -1850,6 +1902,7 @@ static decbpm_tune_result tune_result(const TuneChoice &c, int trial_steps, int 
     r.variant = c.rows ? DECBPM_VARIANT_ROWS : c.pair ? DECBPM_VARIANT_PAIRS : c.flow ? DECBPM_VARIANT_FLOW
                                                                                      : DECBPM_VARIANT_FUSED;
     r.walk_skip = c.flow ? c.skip : 0;
+    r.no_meta_cache = c.nometa;
     r.ctas_per_sm = c.rows ? c.per_sm : 1;
     r.tile_slots = c.slots;
     r.forward_walk = c.forward;
@@ -2608,6 +2661,7 @@ int decbpm_plan_set_shape(decbpm_plan_t P, const decbpm_tune_result *shape) {
         if (shape->ctas_per_sm < 1 || shape->ctas_per_sm > std::min(occ, 4))
             return fail(DECBPM_ERR_INVALID_ARG, "ctas_per_sm must be in 1..%d", std::min(occ, 4));
         c.rows = 1; c.per_sm = shape->ctas_per_sm;
+        c.nometa = shape->no_meta_cache ? 1 : 0;
     } else {
         return fail(DECBPM_ERR_INVALID_ARG, "bad variant %d", shape->variant);
     }
@@ -2651,6 +2705,11 @@ int decbpm_plan_get_config(decbpm_plan_t P, decbpm_plan_config *cfg) {
     }
     cfg->flow_grid = P->flow_mode ? P->flow_grid : 0;
     cfg->flow_skip = P->flow_skip;
+    cfg->meta_items = 0;
+    if (cfg->fused_kernel == 0) {
+        const void *fn = march_kernel_ptr(P->precision, P->bpad, P->fpt);
+        cfg->meta_items = row_meta_cache(P, fn, P->grid, P->fpt).first;
+    }
     cfg->pair_slots = P->pair_mode ? P->pair_slots : 0;
     cfg->pair_slot_bytes = P->pair_mode ? P->pair_slot_bytes : 0;
     cfg->pair_grid = P->pair_mode ? P->pair_grid : 0;

@@ -245,6 +245,8 @@ template <typename R> struct MarchParams {
     long long timeout_ns;        // limit of one barrier wait
     int32_t forward_walk;        // 0: odd stages walk each CTA's share backwards (a stage starts on the
                                  // rows the previous one wrote last: L2 reuse); 1: always forwards
+    int32_t meta_items;          // row kernel, single-mesh plans: > 0 caches the operator metadata of
+                                 // this many warp items per CTA in shared memory (0: read every stage)
     // tile-staged march only
     const int32_t *active_tiles; // [S]: tiles of meshes with M > S-1-s
     int32_t n_slots, slot_bytes; // shared-memory ring of tile windows
@@ -409,6 +411,50 @@ __device__ __forceinline__ void load_meta(const MeshView<R> *sv, const int32_t *
     }
 }
 
+// Shared-memory cache of a CTA's warp items (row kernel, single-mesh plans,
+// whose active items are the same in every stage): per local item li and
+// entry slot e, lane l's column at int [(li E + e) 32 + l] and weight at the
+// same index of the value area, then the items' slice widths.  Filled once
+// per launch, so a stage reads no operator metadata from L2: its only global
+// round trip per item is the field gathers.
+template <typename R, int E> struct MetaCache {
+    int32_t *q;
+    R *x;
+    int32_t *w;
+    __device__ MetaCache(unsigned char *base, int items)
+        : q(reinterpret_cast<int32_t *>(base)),
+          x(reinterpret_cast<R *>(base + size_t(items) * E * 32 * 4)),
+          w(reinterpret_cast<int32_t *>(base + size_t(items) * E * 32 * (4 + sizeof(R)))) {}
+};
+template <typename R, int BPAD, int FPT_ = 0>
+__device__ __forceinline__ void meta_store(const MetaCache<R, Geo<R, BPAD, FPT_>::E> &mc, int li,
+                                           const ItemMeta<R, Geo<R, BPAD, FPT_>::E> &mt) {
+    constexpr int E = Geo<R, BPAD, FPT_>::E;
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+        mc.q[(li * E + e) * 32 + lane] = mt.q[e];
+        mc.x[(li * E + e) * 32 + lane] = mt.x[e];
+    }
+    if (lane == 0) mc.w[li] = mt.width;
+}
+template <typename R, int BPAD, int FPT_ = 0>
+__device__ __forceinline__ void meta_load(const MetaCache<R, Geo<R, BPAD, FPT_>::E> &mc, const MeshView<R> &m, int li,
+                                          int it, ItemMeta<R, Geo<R, BPAD, FPT_>::E> &mt) {
+    using G = Geo<R, BPAD, FPT_>;
+    const int lane = threadIdx.x & 31;
+    mt.mi = 0;
+    mt.row = it * G::RPW + (lane >> G::TPR_LOG2);
+    mt.width = mc.w[li];
+    // the SELL offset is needed only by slices wider than the register-held entries
+    mt.base = mt.width > 8 ? __ldg(m.slice_ptr + (mt.row >> 5)) + (mt.row & 31) : 0;
+#pragma unroll
+    for (int e = 0; e < G::E; ++e) {
+        mt.q[e] = mc.q[(li * G::E + e) * 32 + lane];
+        mt.x[e] = mc.x[(li * G::E + e) * 32 + lane];
+    }
+}
+
 // One Clenshaw stage over this CTA's share of the active items.  X g is
 // evaluated in difference form, (X g)_p = sum_q x_pq (g_p - g_q) - g_p with
 // x_pq = w_pq / (r m_p) > 0 (X = A/r - I since c = r): constants are
@@ -420,7 +466,7 @@ __device__ __forceinline__ void load_meta(const MeshView<R> *sv, const int32_t *
 template <typename R, int BPAD, int FPT_ = 0>
 __device__ __forceinline__ void clenshaw_stage(const MeshView<R> *sv, const StageCoef<R> *scoef, const int32_t *s_begin,
                                                int n_meshes, int n_active, int k, R h_post, int kerr_mode,
-                                               bool rev_odd, int *status) {
+                                               bool rev_odd, int *status, unsigned char *meta, int meta_items) {
     using G = Geo<R, BPAD, FPT_>;
     using C = typename CT<R>::c2;
     constexpr int FPT = G::FPT;
@@ -437,7 +483,12 @@ __device__ __forceinline__ void clenshaw_stage(const MeshView<R> *sv, const Stag
     auto item_at = [&](int i) { return rev ? hi - 1 - i : lo + i; };
     int idx = warp;
     ItemMeta<R, G::E> cur;
-    if (idx < n_mine) load_meta<R, BPAD, FPT_>(sv, s_begin, n_meshes, item_at(idx), cur, status);
+    const MetaCache<R, G::E> mc(meta, meta_items);
+    auto fetch = [&](int i, ItemMeta<R, G::E> &mt) {
+        if (meta_items > 0) meta_load<R, BPAD, FPT_>(mc, sv[0], item_at(i) - lo, item_at(i), mt);
+        else load_meta<R, BPAD, FPT_>(sv, s_begin, n_meshes, item_at(i), mt, status);
+    };
+    if (idx < n_mine) fetch(idx, cur);
     while (idx < n_mine) {
         const int nidx = idx + nwarps;
         const MeshView<R> &m = sv[cur.mi];
@@ -477,7 +528,7 @@ __device__ __forceinline__ void clenshaw_stage(const MeshView<R> *sv, const Stag
                     gq[jj] = ld_pack<R, FPT>(g + (size_t)qj * BPAD + fo);
                 }
             }
-            if (j0 == 0 && nidx < n_mine) load_meta<R, BPAD, FPT_>(sv, s_begin, n_meshes, item_at(nidx), nm, status);
+            if (j0 == 0 && nidx < n_mine) fetch(nidx, nm);
 #pragma unroll
             for (int jj = 0; jj < G::NB; ++jj)
                 if (j0 + jj < cur.width) {
@@ -647,11 +698,23 @@ __global__ void __launch_bounds__(256, MarchMinBlocks<R>::value) march_kernel(Ma
     __shared__ int32_t s_begin[kMaxMeshes + 1];
     __shared__ MeshView<R> s_view[kMaxMeshes];
     __shared__ StageCoef<R> s_coef[kMaxMeshes];
+    extern __shared__ __align__(16) unsigned char s_meta[];
     for (int i = threadIdx.x; i < P.n_meshes; i += blockDim.x) {
         s_begin[i] = P.meshes[i].item_begin;
         s_view[i] = P.meshes[i];
     }
     __syncthreads();
+    if (P.meta_items > 0) {       // single-mesh plan: every stage's items are this CTA's [lo, hi)
+        const int lo = int((long long)P.total_items * blockIdx.x / gridDim.x);
+        const int hi = int((long long)P.total_items * (blockIdx.x + 1) / gridDim.x);
+        const MetaCache<R, Geo<R, BPAD, FPT_>::E> mc(s_meta, P.meta_items);
+        for (int it = lo + int(threadIdx.x >> 5); it < hi && it - lo < P.meta_items; it += int(blockDim.x >> 5)) {
+            ItemMeta<R, Geo<R, BPAD, FPT_>::E> mt;
+            load_meta<R, BPAD, FPT_>(s_view, s_begin, P.n_meshes, it, mt, P.status);
+            meta_store<R, BPAD, FPT_>(mc, it - lo, mt);
+        }
+        __syncthreads();
+    }
     unsigned long long target = 0;
     const R h = P.h, hh = P.h * R(0.5);
     const int bl = Geo<R, BPAD, FPT_>::TPR_LOG2 + Geo<R, BPAD, FPT_>::FPT_LOG2;
@@ -680,7 +743,7 @@ __global__ void __launch_bounds__(256, MarchMinBlocks<R>::value) march_kernel(Ma
                 if (s_view[i].M > k) s_coef[i] = s_view[i].coef[k];
             __syncthreads();
             clenshaw_stage<R, BPAD, FPT_>(s_view, s_coef, s_begin, P.n_meshes, P.active_items[s], k, h_post,
-                                          P.kerr_mode, P.forward_walk == 0, P.status);
+                                          P.kerr_mode, P.forward_walk == 0, P.status, s_meta, P.meta_items);
             if (!grid_barrier(P.barrier, target, P.status, P.timeout_ns)) return;
         }
         if (P.kerr_mode != 0) {

@@ -537,6 +537,38 @@ def test_every_launch_shape_gives_the_same_fields(B):
             plan.set_shape(kernel="flow", tile_slots=3, walk_skip=-1)
 
 
+@pytest.mark.parametrize("precision,B", [("c64", 1), ("c128", 1), ("c64", 4)])
+def test_row_kernel_metadata_cache(precision, B):
+    """Single-mesh plans cache each CTA's warp-item metadata (columns,
+    weights, slice widths) in shared memory once per launch: the fields are
+    bit for bit those of the uncached row kernel, at 1..4 CTAs per SM (the
+    cache is dropped where it would cost co-residency), both Kerr modes and
+    several launches (diagnostics every 4 of 9 steps)."""
+    coords, tris = W.mesh_disk_graded(4.0, 6000, 3.0, interfaces=(1.0,), seed=91, grade_from=1.0)
+    V, chi = W.step_index_materials(coords, tris)
+    sigma = W.absorber_profile(coords, 4.0, 20.0)
+    mesh = api.Mesh(coords, tris, V, chi, sigma)
+    psi0 = W.hg_superpositions(coords, B, np.random.default_rng(92)) * 2.0
+    dt = torch.complex64 if precision == "c64" else torch.complex128
+    plan = api.Plan([mesh], [B], precision)
+    n_cached = 0
+    for kerr in ("lumped", "element"):
+        plan.set_shape("rows", ctas_per_sm=1, no_meta_cache=1)
+        assert plan.config()["meta_items"] == 0
+        ref = to_dev(psi0, dt)
+        plan.propagate([ref], 1e-3, 9, diag_every=4, kerr=kerr)
+        for per_sm in (1, 2, 4):
+            try:
+                plan.set_shape("rows", ctas_per_sm=per_sm)
+            except L.DecbpmError:
+                continue            # more CTAs per SM than this build can hold
+            n_cached += plan.config()["meta_items"] > 0
+            out = to_dev(psi0, dt)
+            plan.propagate([out], 1e-3, 9, diag_every=4, kerr=kerr)
+            assert torch.equal(out, ref), (kerr, per_sm)
+    assert n_cached >= 2
+
+
 # ------------------------------------------------------------------ edge cases
 def test_single_triangle_and_tiny_meshes():
     coords = np.array([[0.0, 0.0], [1.0, 0.0], [0.2, 0.9]])
