@@ -264,8 +264,8 @@ typedef struct {
     int32_t graphs;        /* 1 if step blocks are replayed from captured CUDA graphs */
     int32_t stages;        /* grid-wide stages per step for the last configured dz (max degree) */
     int32_t n_meshes;
-    int32_t tile_slots;    /* > 0: the FUSED variant runs the tile-staged kernel with this many shared-memory
-                              slots (complex64, 9..16 fields); 0: the row kernel */
+    int32_t tile_slots;    /* > 0: the FUSED variant runs a tile-staged kernel with this many shared-memory
+                              slots (complex64 with 9..16 fields, or one field per mesh); 0: the row kernel */
     int32_t tile_slot_bytes;
     int32_t tile_grid;     /* CTAs of the tile-staged launch */
     int32_t tile_block;    /* threads per CTA of the tile-staged launch (16 compute + 3 copy warps) */
@@ -284,6 +284,8 @@ typedef struct {
                               than the tile-staged kernel's: a publisher of tile completions) */
     int32_t flow_skip;     /* dataflow kernel: a reversed walk starts this many tiles before the previous
                               walk's end */
+    int32_t tile_rows;     /* rows per tile of the tile-staged kernel: 128 (16 fields, march_tile_kernel),
+                              512 (one field, march_tile1_kernel), 0: none */
     int32_t meta_items;    /* row kernel, single-mesh plans: warp items per CTA whose operator metadata
                               (columns, weights, slice widths) a launch caches in shared memory once, so
                               that no stage reads it from L2 again; 0: not cached (several meshes, the

@@ -52,6 +52,18 @@ struct NvtxRange {
     NvtxRange &operator=(const NvtxRange &) = delete;
 };
 
+// Tile maps of a mesh for one tile geometry (see build_tiles).
+struct TileMaps {
+    bool ready = false, ok = false;
+    uint16_t *lcol = nullptr;
+    int32_t *tdesc = nullptr, *halo_rows = nullptr, *halo_ovf = nullptr;
+    int n_tiles = 0, max_halo = 0, max_entries = 0;
+    // dataflow march: per tile kDepInts int32 (count, then the tiles adjacent
+    // to it in the operator graph and itself); flow_ok if every list fits
+    int32_t *tdeps = nullptr;
+    bool flow_ok = false;
+};
+
 struct DevAllocs {
     std::vector<void *> ptrs;
     size_t bytes = 0;
@@ -106,15 +118,9 @@ struct decbpm_mesh_s {
     double2 *pml_a = nullptr, *pml_v = nullptr, *pml_chib = nullptr;
     // Gershgorin region of A~ (the union of the discs |z - sum_q a_pq| <= sum_q |a_pq|) as a box
     double pml_re_lo = 0, pml_re_hi = 0, pml_im_lo = 0, pml_im_hi = 0;
-    // tile maps of the tile-staged march (built on first use)
-    bool tiles_ready = false, tiles_ok = false;
-    uint16_t *lcol = nullptr;
-    int32_t *tdesc = nullptr, *halo_rows = nullptr, *halo_ovf = nullptr;
-    int n_tiles = 0, max_halo = 0, max_entries = 0;
-    // dataflow march: per tile kDepInts int32 (count, then the tiles adjacent
-    // to it in the operator graph and itself); flow_ok if every list fits
-    int32_t *tdeps = nullptr;
-    bool flow_ok = false;
+    // tile maps of the tile-staged march (built on first use): 128-row tiles
+    // of 16 fields (t16) and 512-row tiles of one field (t1)
+    TileMaps t16, t1;
     // stage-pair maps (built on first use): per tile the depth-two halo list,
     // descriptor, and the SELL entries of the first halo ring
     bool pairs_ready = false, pairs_ok = false;
@@ -125,50 +131,53 @@ struct decbpm_mesh_s {
     double r() const { return 0.5 * A.rho; }
 };
 
-// Per 128-row tile: the sorted rows outside the tile that its SELL entries
-// reference (halo; the first 96 at rows [96 t, 96 t + 96) of a padded list,
-// the rest in an overflow list), for every entry its row in the tile's
-// window (tile rows 0..127, then halo rows), and a descriptor of 8 int32:
+// Per tile (128 rows of 16 fields, or with one = true 512 rows of one
+// field): the sorted rows outside the tile that its SELL entries reference
+// (halo; the first 96 at rows [96 t, 96 t + 96) of a padded list, the rest in
+// an overflow list), for every entry its row in the tile's window (tile rows,
+// then halo rows), and a descriptor of 8 int32:
 //   {e0, ne, ovf, nh, es0 | es1 << 16, es2 | es3 << 16, w0 | w1 << 8 | w2 << 16 | w3 << 24, 0}
 // (first entry and entry count, overflow offset and halo length, per-slice
-// entry offsets relative to e0 and widths).  An entry's window row is stored as
-// its byte offset (row * 128, 16 fields of complex64), so windows are
-// limited to 511 rows; meshes with larger halos keep the row kernel.
-// Padding entries point inside the tile, so every window row a kernel reads
-// was copied in.
-static int build_tiles(decbpm_mesh_t M) {
-    if (M->tiles_ready) return DECBPM_OK;
+// entry offsets relative to e0 and widths; the 512-row tiles leave the slice
+// fields 0: their kernel copies the 16 slices' offsets and widths).  An
+// entry's window row is stored as its byte offset (row * 128 for 16
+// complex64 fields, row * 8 for one), so windows are limited to 511 or 8191
+// rows; meshes with larger halos keep the row kernel.  Padding entries point
+// inside the tile, so every window row a kernel reads was copied in.
+static int build_tiles(decbpm_mesh_t M, bool one = false) {
+    TileMaps &T = one ? M->t1 : M->t16;
+    if (T.ready) return DECBPM_OK;
     const Sell &S = M->S;
     const int64_t n0 = M->A.n0;
-    const int nt = int((n0 + kTileRows - 1) / kTileRows);
-    constexpr int spt = kTileRows / kSlice;
+    const int tile_rows = one ? kTile1Rows : kTileRows, row_bytes = one ? 8 : 128;
+    const int nt = int((n0 + tile_rows - 1) / tile_rows);
+    const int spt = tile_rows / kSlice;
     constexpr int held = 32 * kHaloRegs;                 // halo rows per tile at a fixed place
-    static_assert(spt == 4, "descriptor packs four slices");
     std::vector<uint16_t> lcol(S.col.size(), 0);
     std::vector<int32_t> desc(size_t(nt) * 8, 0), hfixed(size_t(nt) * held, 0), hovf;
     std::vector<int32_t> uniq;
     std::vector<std::vector<int32_t>> adj(nt);          // tiles holding a tile's halo rows
     int max_halo = 0, max_entries = 0;
     for (int t = 0; t < nt; ++t) {
-        const int64_t r0 = int64_t(t) * kTileRows, r1 = std::min<int64_t>(r0 + kTileRows, n0);
+        const int64_t r0 = int64_t(t) * tile_rows, r1 = std::min<int64_t>(r0 + tile_rows, n0);
         const int64_t s0 = int64_t(t) * spt, s1 = std::min<int64_t>(s0 + spt, S.n_slices);
         const int64_t e0 = S.slice_ptr[s0], e1 = S.slice_ptr[s1];
-        if (e1 - e0 > 65535) return fail(DECBPM_ERR_UNSUPPORTED, "tile %d has %lld SELL entries", t, (long long)(e1 - e0));
+        if (!one && e1 - e0 > 65535) return fail(DECBPM_ERR_UNSUPPORTED, "tile %d has %lld SELL entries", t, (long long)(e1 - e0));
         uniq.clear();
         for (int64_t e = e0; e < e1; ++e)
             if (S.col[e] < r0 || S.col[e] >= r1) uniq.push_back(S.col[e]);
         std::sort(uniq.begin(), uniq.end());
         uniq.erase(std::unique(uniq.begin(), uniq.end()), uniq.end());
-        if ((kTileRows + uniq.size()) * 128 > 65535) {   // window offsets must fit 16 bits: keep the row kernel
-            M->tiles_ready = true;
-            M->tiles_ok = false;
+        if ((tile_rows + uniq.size()) * row_bytes > 65535) {   // window offsets must fit 16 bits: keep the row kernel
+            T.ready = true;
+            T.ok = false;
             return DECBPM_OK;
         }
         for (int64_t e = e0; e < e1; ++e) {
             const int32_t q = S.col[e];
             const int64_t w = (q >= r0 && q < r1) ? q - r0
-                                                  : kTileRows + (std::lower_bound(uniq.begin(), uniq.end(), q) - uniq.begin());
-            lcol[e] = uint16_t(w * 128);                    // byte offset of the row in the window
+                                                  : tile_rows + (std::lower_bound(uniq.begin(), uniq.end(), q) - uniq.begin());
+            lcol[e] = uint16_t(w * row_bytes);              // byte offset of the row in the window
         }
         int32_t *d = &desc[size_t(t) * 8];
         d[0] = int32_t(e0);
@@ -176,7 +185,7 @@ static int build_tiles(decbpm_mesh_t M) {
         d[2] = int32_t(hovf.size());
         d[3] = int32_t(uniq.size());
         uint32_t es[4] = {0, 0, 0, 0}, w[4] = {0, 0, 0, 0};
-        for (int64_t sl = s0; sl < s1; ++sl) {
+        for (int64_t sl = s0; sl < s1 && !one; ++sl) {
             if (S.slice_w[sl] > 255) return fail(DECBPM_ERR_UNSUPPORTED, "slice %lld is wider than 255", (long long)sl);
             es[sl - s0] = uint32_t(S.slice_ptr[sl] - e0);
             w[sl - s0] = uint32_t(S.slice_w[sl]);
@@ -187,7 +196,7 @@ static int build_tiles(decbpm_mesh_t M) {
         for (size_t j = 0; j < uniq.size(); ++j) {
             if (j < size_t(held)) hfixed[size_t(t) * held + j] = uniq[j];
             else hovf.push_back(uniq[j]);
-            const int32_t tq = uniq[j] / kTileRows;
+            const int32_t tq = uniq[j] / tile_rows;
             if (adj[t].empty() || adj[t].back() != tq) adj[t].push_back(tq);    // uniq is sorted
         }
         max_halo = std::max(max_halo, int(uniq.size()));
@@ -214,17 +223,17 @@ static int build_tiles(decbpm_mesh_t M) {
         tdeps[size_t(t) * kDepInts] = int32_t(d.size());
         for (size_t j = 0; j < d.size(); ++j) tdeps[size_t(t) * kDepInts + 1 + j] = d[j];
     }
-    if (flow_ok) TRY(M->mem.upload(&M->tdeps, tdeps));
-    M->flow_ok = flow_ok;
-    TRY(M->mem.upload(&M->lcol, lcol));
-    TRY(M->mem.upload(&M->tdesc, desc));
-    TRY(M->mem.upload(&M->halo_rows, hfixed));
-    TRY(M->mem.upload(&M->halo_ovf, hovf));
-    M->n_tiles = nt;
-    M->max_halo = max_halo;
-    M->max_entries = max_entries;
-    M->tiles_ready = true;
-    M->tiles_ok = true;
+    if (flow_ok) TRY(M->mem.upload(&T.tdeps, tdeps));
+    T.flow_ok = flow_ok;
+    TRY(M->mem.upload(&T.lcol, lcol));
+    TRY(M->mem.upload(&T.tdesc, desc));
+    TRY(M->mem.upload(&T.halo_rows, hfixed));
+    TRY(M->mem.upload(&T.halo_ovf, hovf));
+    T.n_tiles = nt;
+    T.max_halo = max_halo;
+    T.max_entries = max_entries;
+    T.ready = true;
+    T.ok = true;
     return DECBPM_OK;
 }
 
@@ -242,7 +251,7 @@ static int build_pair_maps(decbpm_mesh_t M) {
     TRY(build_tiles(M));
     M->pairs_ready = true;
     M->pairs_ok = false;
-    if (!M->tiles_ok) return DECBPM_OK;
+    if (!M->t16.ok) return DECBPM_OK;
     const Sell &S = M->S;
     const Assembly &A = M->A;
     const int64_t n0 = A.n0;
@@ -380,8 +389,14 @@ static int mesh_upload(decbpm_mesh_t M) {
         cdiag[i] = A.c_diag[o];
     }
     DevAllocs &D = M->mem;
-    TRY(D.upload(&M->slice_ptr, S.slice_ptr));
-    TRY(D.upload(&M->slice_w, S.slice_w));
+    // slice tables padded to a multiple of 16 entries (the single-field tiles
+    // bulk-copy 16 slices' offsets and widths; padding: no entries)
+    const size_t nsp = (S.slice_ptr.size() + 15) / 16 * 16;
+    std::vector<int32_t> sp(S.slice_ptr), sw(S.slice_w);
+    sp.resize(nsp, S.slice_ptr.back());
+    sw.resize(nsp, 0);
+    TRY(D.upload(&M->slice_ptr, sp));
+    TRY(D.upload(&M->slice_w, sw));
     TRY(D.upload(&M->col, S.col));
     TRY(D.upload(&M->perm, A.perm));
     TRY(D.upload(&M->x32, cast<float>(xval)));
@@ -452,6 +467,7 @@ struct decbpm_plan_s {
     int S = 0, total_items = 0;
     // tile-staged march (complex64 with 9..16 fields)
     bool tile_mode = false;
+    bool tile_one = false;                       // the single-field tiles (512 rows of one field)
     int tile_grid = 0, n_slots = 0, slot_bytes = 0, off_psi = 0, off_h = 0, off_lcol = 0, off_x = 0, off_hdr = 0;
     int slot_entries = 0;
     // launch configuration of the FUSED variant (defaults until decbpm_plan_autotune picks one)
@@ -505,6 +521,9 @@ struct decbpm_plan_s {
         mem.release();
     }
 };
+
+// the tile maps a plan's tile-staged march uses
+static const TileMaps &tile_maps(decbpm_plan_t P, decbpm_mesh_t m) { return P->tile_one ? m->t1 : m->t16; }
 
 static int reject_pml(decbpm_mesh_t m);        // meshes with a PML run decbpm_propagate (one C128 field) and RK45 only
 extern "C" {
@@ -601,28 +620,34 @@ static std::pair<int, size_t> row_meta_cache(decbpm_plan_t P, const void *fn, in
 
 // Shared-memory ring of the tile-staged march: as many slots (3, else 2) of
 // the largest tile window of the plan's meshes as fit next to the kernel's
-// static shared memory.  Plans it does not fit keep the row kernel.
+// static shared memory.  Complex64 plans of 9..16 fields use 128-row tiles
+// (march_tile_kernel), plans of one field per mesh 512-row tiles
+// (march_tile1_kernel).  Plans it does not fit keep the row kernel.
 static int setup_tiles(decbpm_plan_t P) {
     P->tile_mode = false;
-    if (P->precision != DECBPM_C64 || P->bpad != 16) return DECBPM_OK;
+    P->tile_one = false;
+    if (P->precision != DECBPM_C64 || (P->bpad != 16 && P->bpad != 1)) return DECBPM_OK;
+    const bool one = P->bpad == 1;
     int max_halo = 0, max_entries = 0;
     for (decbpm_mesh_t m : P->meshes) {
-        TRY(build_tiles(m));
-        if (!m->tiles_ok) return DECBPM_OK;
-        max_halo = std::max(max_halo, m->max_halo);
-        max_entries = std::max(max_entries, m->max_entries);
+        TRY(build_tiles(m, one));
+        const TileMaps &T = one ? m->t1 : m->t16;
+        if (!T.ok) return DECBPM_OK;
+        max_halo = std::max(max_halo, T.max_halo);
+        max_entries = std::max(max_entries, T.max_entries);
     }
     auto up = [](int x) { return (x + 127) / 128 * 128; };
-    const int row = 16 * 8;
-    P->off_psi = up((kTileRows + max_halo) * row);
-    P->off_h = P->off_psi + kTileRows * row;
-    P->off_lcol = P->off_h + kTileRows * row;
+    const int row = one ? 8 : 16 * 8, rows = one ? kTile1Rows : kTileRows;
+    P->off_psi = up((rows + max_halo) * row);
+    P->off_h = P->off_psi + rows * row;
+    P->off_lcol = P->off_h + rows * row;
     P->off_x = P->off_lcol + up(max_entries * 2);
     P->off_hdr = P->off_x + up(max_entries * 4);
     P->slot_entries = max_entries;
-    P->slot_bytes = P->off_hdr + 128;
+    P->slot_bytes = P->off_hdr + (one ? kTile1HdrBytes : 128);
+    const void *fn = one ? (const void *)march_tile1_kernel : (const void *)march_tile_kernel;
     cudaFuncAttributes fa{};
-    CK(cudaFuncGetAttributes(&fa, (const void *)march_tile_kernel));
+    CK(cudaFuncGetAttributes(&fa, fn));
     int optin = 0;
     CK(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, P->device));
     const int avail = optin - int(fa.sharedSizeBytes);
@@ -630,19 +655,27 @@ static int setup_tiles(decbpm_plan_t P) {
     if (P->n_slots == 0) return DECBPM_OK;
     const int dyn = P->n_slots * P->slot_bytes;
     // the attribute is per function, not per plan: allow the largest ring any plan may use
-    CK(cudaFuncSetAttribute((const void *)march_tile_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, avail));
+    CK(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, avail));
     int per_sm = 0;
-    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void *)march_tile_kernel, kTileThreads, dyn));
+    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kTileThreads, dyn));
     if (per_sm < 1) return DECBPM_OK;
     P->tile_grid = P->num_sms * per_sm;
     P->tile_mode = true;
+    P->tile_one = one;
+    // single-field plans run the row kernel until the autotuner picks the
+    // tiles (faster on the 1M-vertex guide, slower on the L2-resident meshes
+    // where the row kernel caches its metadata); no dataflow variant
+    if (one) {
+        P->tune_rows = 1;
+        return DECBPM_OK;
+    }
     // the dataflow kernel: same ring and static shared memory, one more warp
     P->flow_mode = false;
     bool deps_ok = true;
     int total = 0;
     for (decbpm_mesh_t m : P->meshes) {
-        deps_ok = deps_ok && m->flow_ok;
-        total += m->n_tiles;
+        deps_ok = deps_ok && m->t16.flow_ok;
+        total += m->t16.n_tiles;
     }
     if (!deps_ok) return DECBPM_OK;
     CK(cudaFuncGetAttributes(&fa, (const void *)march_flow_kernel));
@@ -675,7 +708,7 @@ static int build_flow_lists(decbpm_plan_t P, const std::vector<int> &Ms) {
     int phi = 0;
     for (int j = 0; j < n; ++j) {
         const int i = P->order[j];
-        const int T = P->meshes[i]->n_tiles, q = T / G, r = T % G;
+        const int T = P->meshes[i]->t16.n_tiles, q = T / G, r = T % G;
         int start = 0;
         for (int c = 0; c < G; ++c) {
             const bool extra = ((c - phi + G) % G) < r;
@@ -718,14 +751,14 @@ static int build_flow_lists(decbpm_plan_t P, const std::vector<int> &Ms) {
 // not fit twice keep the single-stage kernels.
 static int setup_pairs(decbpm_plan_t P) {
     P->pair_mode = false;
-    if (!P->tile_mode) return DECBPM_OK;
+    if (!P->tile_mode || P->tile_one) return DECBPM_OK;
     int max_nh1 = 0, max_nh12 = 0, max_entries = 0, max_he = 0;
     for (decbpm_mesh_t m : P->meshes) {
         TRY(build_pair_maps(m));
         if (!m->pairs_ok) return DECBPM_OK;
         max_nh1 = std::max(max_nh1, m->max_nh1);
         max_nh12 = std::max(max_nh12, m->max_nh12);
-        max_entries = std::max(max_entries, m->max_entries);
+        max_entries = std::max(max_entries, m->t16.max_entries);
         max_he = std::max(max_he, m->max_hentries);
     }
     auto up = [](int x) { return (x + 127) / 128 * 128; };
@@ -791,7 +824,8 @@ static int plan_create_impl(const decbpm_mesh_t *meshes, int32_t n, const int32_
     CK(cudaDeviceGetAttribute(&P->num_sms, cudaDevAttrMultiProcessorCount, P->device));
     const size_t cs = csize(precision);
     for (int i = 0; i < n; ++i) {
-        const size_t elems = size_t(meshes[i]->A.n0) * P->bpad;
+        // rows rounded up to a SELL slice: the single-field tiles bulk-copy an even row count
+        const size_t elems = size_t((meshes[i]->A.n0 + kSlice - 1) / kSlice * kSlice) * P->bpad;
         void *a, *b, *c, *d;
         char *t;
         TRY(P->mem.alloc(&t, elems * cs)); a = t;
@@ -862,12 +896,12 @@ static int plan_configure(decbpm_plan_t P, double dz, double tol) {
         for (int j = 0; j < n; ++j) {
             const int i = P->order[j];
             P->tile_begin[i] = tacc;
-            tacc += P->meshes[i]->n_tiles;
+            tacc += tile_maps(P, P->meshes[i]).n_tiles;
         }
         P->total_tiles = tacc;
         for (int s = 0; s < P->S; ++s)
             for (int j = 0; j < n; ++j)
-                if (ch[P->order[j]].M > P->S - 1 - s) active_t[s] += P->meshes[P->order[j]]->n_tiles;
+                if (ch[P->order[j]].M > P->S - 1 - s) active_t[s] += tile_maps(P, P->meshes[P->order[j]]).n_tiles;
         if (P->S > P->active_tiles_cap) {
             TRY(P->mem.alloc(&P->active_tiles, P->S));
             P->active_tiles_cap = P->S;
@@ -955,11 +989,12 @@ static int plan_configure(decbpm_plan_t P, double dz, double tol) {
         v.b[0] = (C *)P->b0[i]; v.b[1] = (C *)P->b1[i]; v.b[2] = (C *)P->b2[i];
         v.coef = (const StageCoef<R> *)P->coef + off;
         if (P->tile_mode) {
-            v.lcol = m->lcol;
-            v.tdesc = m->tdesc;
-            v.halo_rows = m->halo_rows;
-            v.halo_ovf = m->halo_ovf;
-            v.tdeps = m->tdeps;
+            const TileMaps &T = tile_maps(P, m);
+            v.lcol = T.lcol;
+            v.tdesc = T.tdesc;
+            v.halo_rows = T.halo_rows;
+            v.halo_ovf = T.halo_ovf;
+            v.tdeps = T.tdeps;
             v.tile_begin = P->tile_begin[i];
         }
         off += Mi;
@@ -980,7 +1015,7 @@ static int plan_configure(decbpm_plan_t P, double dz, double tol) {
         for (int ps = 0; ps < P->n_passes; ++ps) {
             const int lowest = ps < n_pairs ? P->S - 2 - 2 * ps : (ps == n_pairs && ((P->S - 1) & 1)) ? 1 : 0;
             for (int j = 0; j < n; ++j)
-                if (ch[P->order[j]].M > lowest) ap[ps] += P->meshes[P->order[j]]->n_tiles;
+                if (ch[P->order[j]].M > lowest) ap[ps] += P->meshes[P->order[j]]->t16.n_tiles;
         }
         if (P->n_passes > P->active_passes_cap) {
             TRY(P->mem.alloc(&P->active_passes, P->n_passes));
@@ -1115,7 +1150,7 @@ static int launch_march(decbpm_plan_t P, cudaStream_t s, int n_steps, int kerr_m
             cfg.gridDim = dim3(P->tile_grid);
             cfg.blockDim = dim3(kTileThreads);
             cfg.dynamicSmemBytes = size_t(slots) * P->slot_bytes;
-            fn = (const void *)march_tile_kernel;
+            fn = P->tile_one ? (const void *)march_tile1_kernel : (const void *)march_tile_kernel;
             if (flow) {
                 mp.tile_done = P->tile_done;
                 mp.cta_tiles = P->cta_tiles;
@@ -2703,6 +2738,7 @@ int decbpm_plan_get_config(decbpm_plan_t P, decbpm_plan_config *cfg) {
     } else if (cfg->fused_kernel == 1 && P->flow_mode && P->tune_flow == 1) {
         cfg->fused_kernel = 3;
     }
+    cfg->tile_rows = P->tile_mode ? (P->tile_one ? kTile1Rows : kTileRows) : 0;
     cfg->flow_grid = P->flow_mode ? P->flow_grid : 0;
     cfg->flow_skip = P->flow_skip;
     cfg->meta_items = 0;

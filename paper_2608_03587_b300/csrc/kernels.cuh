@@ -334,10 +334,22 @@ __device__ __forceinline__ void diag_factors(R sigma, R h, R &em, R &phi) {
     }
 }
 
+// Real multiply, add and FMA rounded to nearest with no contraction left to
+// the compiler: the diagonal flows are inlined into several kernels (row,
+// tile-staged, single-field tiles, all-row passes), and each must produce the
+// same bits.
+__device__ __forceinline__ float rmul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double rmul(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float radd(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ double radd(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ float rfma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double rfma(double a, double b, double c) { return __fma_rn(a, b, c); }
+template <typename C> __device__ __forceinline__ auto cnorm2(C s) { return rfma(s.x, s.x, rmul(s.y, s.y)); }
+
 template <typename C, typename R>
 __device__ __forceinline__ C diag_apply(C s, R v, R chib, R h, R em, R phi) {
-    const R I = s.x * s.x + s.y * s.y;
-    const R theta = v * h + chib * I * phi;
+    const R I = cnorm2(s);
+    const R theta = rfma(v, h, rmul(rmul(chib, I), phi));
     R sh, ch;
     sincos_r(R(0.5) * theta, &sh, &ch);
     const C e = cmk<C>(R(-2) * sh * sh, R(2) * sh * ch);             // e^{i theta} - 1
@@ -614,7 +626,7 @@ __device__ __forceinline__ void element_kerr_item(const MeshView<R> &m, int loca
     R rate[FPT];
     const R cd = __ldg(m.cdiag + row) * phi;
 #pragma unroll
-    for (int f = 0; f < FPT; ++f) rate[f] = cd * (s.v[f].x * s.v[f].x + s.v[f].y * s.v[f].y);
+    for (int f = 0; f < FPT; ++f) rate[f] = rmul(cd, cnorm2(s.v[f]));
     for (int j = 0; j < width; ++j) {
         const int q = DECBPM_IDX(__ldg(m.col + base + 32 * j), m.n0, status);
         const R cq = __ldg(m.coff + base + 32 * j);
@@ -622,14 +634,14 @@ __device__ __forceinline__ void element_kerr_item(const MeshView<R> &m, int loca
         diag_factors(__ldg(m.sigma + q), hh, dq, pq);
         const Pack<R, FPT> sq = ld_pack<R, FPT>(src + (size_t)q * bpad + fo);
 #pragma unroll
-        for (int f = 0; f < FPT; ++f) rate[f] += cq * pq * (sq.v[f].x * sq.v[f].x + sq.v[f].y * sq.v[f].y);
+        for (int f = 0; f < FPT; ++f) rate[f] = rfma(rmul(cq, pq), cnorm2(sq.v[f]), rate[f]);
     }
     const R vh = __ldg(m.v + row) * hh;
     Pack<R, FPT> out;
 #pragma unroll
     for (int f = 0; f < FPT; ++f) {
         R sh, ch;
-        sincos_r(R(0.5) * (vh + rate[f]), &sh, &ch);
+        sincos_r(R(0.5) * radd(vh, rate[f]), &sh, &ch);
         const C e = cmk<C>(R(-2) * sh * sh, R(2) * sh * ch);
         const C w = cadd(cscale(cadd(e, cmk<C>(R(1), R(0))), damp), e);
         out.v[f] = cadd(s.v[f], cmul(s.v[f], w));
@@ -786,6 +798,11 @@ constexpr int kTileCopyWarps = 3;     // copy warp c owns ring slot c (at most 3
 constexpr int kTileThreads = 32 * (kTileComputeWarps + kTileCopyWarps);
 constexpr int kMaxSlots = kTileCopyWarps;
 constexpr int kHaloRegs = 3;          // halo rows per copy-warp lane held ahead (96 per tile)
+// single-field tiles: 512 rows of one complex64 field (8-byte rows), one row
+// per compute thread; the slot header holds the tile's 16 slice offsets and
+// widths (bulk-copied) and, at byte 128, the mesh and local tile index
+constexpr int kTile1Rows = 512;
+constexpr int kTile1HdrBytes = 256;
 
 // Static per-tile descriptor (two int4): {e0, ne, ovf, nh} (ovf: offset of
 // the halo rows beyond the first 96 in the overflow list) and
@@ -1118,6 +1135,11 @@ __device__ __forceinline__ StageCoef<float> lds_stage_coef(uint32_t addr) {
     return c;
 }
 
+__device__ __forceinline__ int lds_i32(uint32_t addr) {
+    int v;
+    asm volatile("ld.shared.s32 %0, [%1];" : "=r"(v) : "r"(addr));
+    return v;
+}
 __device__ __forceinline__ uint32_t lds_u16(uint32_t addr) {
     unsigned short v;
     asm volatile("ld.shared.u16 %0, [%1];" : "=h"(v) : "r"(addr));
@@ -1278,6 +1300,117 @@ __device__ __forceinline__ void tile_compute(const MeshView<float> *sv, const St
     stg_c2(dst + (size_t)row * 16 + 2 * c2, out[2], out[3]);
 }
 
+__device__ __forceinline__ void cp_async8(uint32_t dst, const void *src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(dst), "l"(src) : "memory");
+}
+
+// Copy warp, single-field tiles: fill `slot` for stage k.  Halo rows are
+// 8-byte cp.async copies (one lane per row); the tile's g, psi and b_{k+2}
+// rows (an even count: the field buffers are padded to whole slices), SELL
+// entries and slice table are bulk copies.
+__device__ __forceinline__ void tile_fill1(const int *entry, const MeshView<float> *sv, const StageCoef<float> *scoef,
+                                           int k, char *slot, uint32_t bar, const MarchParams<float> &P) {
+    const int lane = threadIdx.x & 31;
+    const int4 dsc = *reinterpret_cast<const int4 *>(entry + 96);
+    const int mi = entry[101], tl = entry[102];
+    const MeshView<float> &m = sv[mi];
+    const int flags = scoef[mi].flags;
+    const int r0 = tl * kTile1Rows, nrows = min(kTile1Rows, m.n0 - r0), nrows_pad = (nrows + 1) & ~1;
+    const int e0 = dsc.x, ne = dsc.y, ovf = dsc.z, nh = dsc.w;
+    const float2 *g = (flags & kGisPsi) ? m.psi : m.b[(k + 1) % 3];
+    const uint32_t base = smem_u32(slot);
+#pragma unroll
+    for (int u = 0; u < kHaloRegs; ++u) {
+        const int r = lane + 32 * u;
+        if (r < nh) cp_async8(base + unsigned(kTile1Rows + r) * 8u, g + DECBPM_IDX(entry[r], m.n0, P.status));
+    }
+    for (int j = lane + 32 * kHaloRegs; j < nh; j += 32) {      // rows beyond the 96 held ahead
+        const int q = DECBPM_IDX(__ldg(m.halo_ovf + ovf + j - 32 * kHaloRegs), m.n0, P.status);
+        cp_async8(base + unsigned(kTile1Rows + j) * 8u, g + q);
+    }
+    cp_async_arrive(bar);
+    const unsigned row_bytes = unsigned(nrows_pad) * 8u;
+    const unsigned total = row_bytes * (1u + ((flags & kGisPsi) ? 0u : 1u) + ((flags & kHasH) ? 1u : 0u)) +
+                           unsigned(ne) * 6u + 128u;
+    __syncwarp();
+    if (lane == 0) {
+        asm volatile("st.shared.v2.s32 [%0], {%1, %2};" ::"r"(base + P.off_hdr + 128), "r"(mi), "r"(tl) : "memory");
+        mbar_arrive_expect_tx(bar, total);
+    }
+    __syncwarp();
+    const int s0 = tl * (kTile1Rows / 32);
+    if (lane == 0) bulk_g2s(base, g + r0, row_bytes, bar);
+    if (lane == 1 && !(flags & kGisPsi)) bulk_g2s(base + P.off_psi, m.psi + r0, row_bytes, bar);
+    if (lane == 2 && (flags & kHasH)) bulk_g2s(base + P.off_h, m.b[(k + 2) % 3] + r0, row_bytes, bar);
+    if (lane == 3 && ne > 0) bulk_g2s(base + P.off_lcol, m.lcol + e0, unsigned(ne) * 2u, bar);
+    if (lane == 4 && ne > 0) bulk_g2s(base + P.off_x, m.xval + e0, unsigned(ne) * 4u, bar);
+    if (lane == 5) bulk_g2s(base + P.off_hdr, m.slice_ptr + s0, 64u, bar);
+    if (lane == 6) bulk_g2s(base + P.off_hdr + 64, m.slice_w + s0, 64u, bar);
+}
+
+__device__ __forceinline__ float2 lds_f2(uint32_t addr) {
+    float2 v;
+    asm volatile("ld.shared.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "r"(addr));
+    return v;
+}
+
+// Compute warps, single-field tiles: thread t owns row t of the tile; the
+// same operations in the same order as the row kernel's (one value per
+// thread), so the fields are bit for bit the row kernel's.
+__device__ __forceinline__ void tile_compute1(const MeshView<float> *sv, const StageCoef<float> *scoef, int k,
+                                              const char *slot, float h_post, int kerr_mode,
+                                              const MarchParams<float> &P) {
+    const int t = threadIdx.x;                          // compute threads are 0..511
+    const uint32_t base = smem_u32(slot);
+    int mi, tl;
+    asm volatile("ld.shared.v2.s32 {%0, %1}, [%2];" : "=r"(mi), "=r"(tl) : "r"(base + P.off_hdr + 128));
+    const MeshView<float> &m = sv[mi];
+    const StageCoef<float> sc = scoef[mi];
+    const int row = tl * kTile1Rows + t;
+    if (row >= m.n0) return;
+    const int sl = t >> 5;
+    const int sp0 = lds_i32(base + P.off_hdr);
+    const int es = lds_i32(base + P.off_hdr + 4 * sl) - sp0 + (t & 31);
+    const int width = lds_i32(base + P.off_hdr + 64 + 4 * sl);
+    if (width > 0 && es + 32 * (width - 1) >= P.slot_entries) {   // cannot happen with consistent maps
+        atomicCAS(P.status, 0, -8);                                 // DECBPM_ERR_DEVICE_CHECK
+        return;
+    }
+    const float2 gp = lds_f2(base + 8u * unsigned(t));
+    const float2 ps = (sc.flags & kGisPsi) ? gp : lds_f2(base + P.off_psi + 8u * unsigned(t));
+    const bool hasH = (sc.flags & kHasH) != 0;
+    const float2 hh = hasH ? lds_f2(base + P.off_h + 8u * unsigned(t)) : make_float2(0.f, 0.f);
+    const uint32_t lc = base + P.off_lcol + 2u * unsigned(es), xs = base + P.off_x + 4u * unsigned(es);
+    float2 acc = cmk<float2>(0.f, 0.f);
+    for (int j = 0; j < width; ++j) {
+        const uint32_t off = DECBPM_IDX(lds_u16(lc + 64u * j), uint32_t(P.off_psi), P.status);
+        const float x = lds_f32(xs + 128u * j);
+        const float2 gq = lds_f2(base + off);
+        acc = cfma(x, csub(gp, gq), acc);
+    }
+    float2 out;
+    if (sc.flags & kFinal) {                       // double-float final stage (the row kernel's)
+        out = final_combine(sc.alpha, sc.alpha_lo, sc.beta, ps, acc, gp, hh, hasH);
+    } else {
+        out = cadd(cmul(sc.alpha, ps), cmul(sc.beta, csub(acc, gp)));
+        if (hasH) out = csub(out, hh);
+    }
+    float2 *dst;
+    if (sc.flags & kFinal) {
+        if (kerr_mode == 0) {
+            float em, phi;
+            diag_factors(__ldg(m.sigma + row), h_post, em, phi);
+            out = diag_apply(out, __ldg(m.v + row), __ldg(m.chib + row), h_post, em, phi);
+            dst = m.psi;
+        } else {
+            dst = m.b[0];        // element-averaged Kerr needs the neighbours' |S|^2: park S in b[0]
+        }
+    } else {
+        dst = m.b[k % 3];
+    }
+    dst[row] = out;
+}
+
 // The whole launch as seen by one role: a copy warp (COPIER), a compute
 // warp, or (dataflow march only) the publisher warp (PUBLISHER).  All roles
 // take the same grid barriers; each role's registers are live only in its own
@@ -1286,17 +1419,18 @@ __device__ __forceinline__ void tile_compute(const MeshView<float> *sv, const St
 // waits (see FlowRange) and keeps grid barriers only around the passes over
 // all rows (the first half step's diagonal flow, the element-averaged Kerr
 // flow).
-template <bool COPIER, bool FLOW, bool PUBLISHER = false>
+template <bool COPIER, bool FLOW, bool PUBLISHER = false, bool ONE = false>
 __device__ __forceinline__ void tile_march_role(int copier, const MarchParams<float> &P, char *s_ring,
                                                 const int32_t *s_begin, const int32_t *s_tbeg,
                                                 const MeshView<float> *s_view, StageCoef<float> *s_coef,
                                                 unsigned long long *s_full, unsigned long long *s_empty, int *s_look,
                                                 unsigned *s_done) {
-    constexpr int FPT = Geo<float, 16>::FPT;
+    using GR = Geo<float, ONE ? 1 : 16>;            // rows of the passes over all items
+    constexpr int FPT = GR::FPT;
     const int lane = threadIdx.x & 31;
     unsigned long long target = 0;
     const float h = P.h, hh = P.h * 0.5f;
-    const int bl = Geo<float, 16>::TPR_LOG2 + Geo<float, 16>::FPT_LOG2;
+    const int bl = GR::TPR_LOG2 + GR::FPT_LOG2;
     const unsigned D = unsigned(P.n_slots);
     unsigned seq = 0;                                      // tiles filled / consumed so far by this CTA
     LookCursor cur{0, 0, TileRange{}};
@@ -1402,8 +1536,12 @@ __device__ __forceinline__ void tile_march_role(int copier, const MarchParams<fl
                     }
                     if (ok && q >= D) ok = mbar_wait(smem_u32(&s_empty[sl]), ((q / D) - 1u) & 1u, P.status, P.timeout_ns);
                     if (ok) {
-                        tile_fill<FLOW>(entry, s_view, s_coef, k, s_ring + (size_t)sl * P.slot_bytes,
-                                        smem_u32(&s_full[sl]), P);
+                        if constexpr (ONE)
+                            tile_fill1(entry, s_view, s_coef, k, s_ring + (size_t)sl * P.slot_bytes,
+                                       smem_u32(&s_full[sl]), P);
+                        else
+                            tile_fill<FLOW>(entry, s_view, s_coef, k, s_ring + (size_t)sl * P.slot_bytes,
+                                            smem_u32(&s_full[sl]), P);
                         __syncwarp();
                         if constexpr (FLOW) {
                             const int t = flow_next_n(fcur, P, int(D));
@@ -1415,8 +1553,12 @@ __device__ __forceinline__ void tile_march_role(int copier, const MarchParams<fl
                 } else {
                     ok = mbar_wait(smem_u32(&s_full[sl]), (q / D) & 1u, P.status, P.timeout_ns);
                     if (ok) {
-                        tile_compute<FLOW>(s_view, s_coef, k, s_ring + (size_t)sl * P.slot_bytes,
-                                           h_post, P.kerr_mode, P);
+                        if constexpr (ONE)
+                            tile_compute1(s_view, s_coef, k, s_ring + (size_t)sl * P.slot_bytes, h_post,
+                                          P.kerr_mode, P);
+                        else
+                            tile_compute<FLOW>(s_view, s_coef, k, s_ring + (size_t)sl * P.slot_bytes,
+                                               h_post, P.kerr_mode, P);
                         __syncwarp();
                         if (lane == 0) {
                             mbar_arrive(smem_u32(&s_empty[sl]));
@@ -1447,7 +1589,7 @@ __device__ __forceinline__ void tile_march_role(int copier, const MarchParams<fl
     }
 }
 
-template <bool FLOW>
+template <bool FLOW, bool ONE = false>
 __device__ __forceinline__ void tile_march_body(const MarchParams<float> &P) {
     extern __shared__ __align__(128) char s_ring[];
     __shared__ int32_t s_begin[kMaxMeshes + 1];
@@ -1475,15 +1617,22 @@ __device__ __forceinline__ void tile_march_body(const MarchParams<float> &P) {
             tile_march_role<false, true, true>(0, P, s_ring, s_begin, s_tbeg, s_view, s_coef, s_full, s_empty, s_look,
                                                &s_done);
     } else if (warp >= kTileComputeWarps) {
-        tile_march_role<true, FLOW>(warp - kTileComputeWarps, P, s_ring, s_begin, s_tbeg, s_view, s_coef, s_full,
-                                    s_empty, s_look, &s_done);
+        tile_march_role<true, FLOW, false, ONE>(warp - kTileComputeWarps, P, s_ring, s_begin, s_tbeg, s_view, s_coef,
+                                                s_full, s_empty, s_look, &s_done);
         cp_async_wait<0>();           // no look-ahead copy may land after the CTA exits
     } else {
-        tile_march_role<false, FLOW>(0, P, s_ring, s_begin, s_tbeg, s_view, s_coef, s_full, s_empty, s_look, &s_done);
+        tile_march_role<false, FLOW, false, ONE>(0, P, s_ring, s_begin, s_tbeg, s_view, s_coef, s_full, s_empty,
+                                                 s_look, &s_done);
     }
 }
 
 __global__ void __launch_bounds__(kTileThreads, 1) march_tile_kernel(MarchParams<float> P) { tile_march_body<false>(P); }
+
+// The same march for one complex64 field per vertex: 512-row tiles of 8-byte
+// rows (tile_fill1 / tile_compute1).
+__global__ void __launch_bounds__(kTileThreads, 1) march_tile1_kernel(MarchParams<float> P) {
+    tile_march_body<false, true>(P);
+}
 
 // The dataflow march: the tile-staged kernel without grid barriers between
 // stages, plus a publisher warp.
@@ -1534,11 +1683,6 @@ __device__ __forceinline__ void sts_c2(uint32_t addr, cf2 a, cf2 b) {
 }
 __device__ __forceinline__ void sts_i32(uint32_t addr, int v) {
     asm volatile("st.shared.s32 [%0], %1;" ::"r"(addr), "r"(v) : "memory");
-}
-__device__ __forceinline__ int lds_i32(uint32_t addr) {
-    int v;
-    asm volatile("ld.shared.s32 %0, [%1];" : "=r"(v) : "r"(addr));
-    return v;
 }
 // The compute warps form two groups of 8 that take alternate tiles, so one
 // group's phase barrier overlaps the other group's work.  Barriers of one

@@ -537,6 +537,48 @@ def test_every_launch_shape_gives_the_same_fields(B):
             plan.set_shape(kernel="flow", tile_slots=3, walk_skip=-1)
 
 
+@pytest.mark.parametrize("kerr", ["lumped", "element"])
+def test_single_field_tile_kernel_matches_row_kernel(kerr):
+    """Complex64 plans of one field per mesh can run the single-field
+    tile-staged kernel (512-row tiles staged in shared memory, one row per
+    thread; the autotuner's choice, the row kernel by default): bit for bit
+    the row kernel's fields, on meshes of uneven size
+    and degree (several tiles with ragged last tiles, a mesh below one tile,
+    a single triangle), with 3 and 2 ring slots, over three launches
+    (diagnostics every 3 of 7 steps); and the oracle within the FP32 bars."""
+    specs = [(6000, 81), (1500, 82), (300, 83), (3, 84), (40000, 85)]
+    meshes, opss, sigs, psis = [], [], [], []
+    for n, seed in specs:
+        if n == 3:
+            coords = np.array([[0.0, 0.0], [1.0, 0.0], [0.2, 0.9]])
+            tris = np.array([[0, 1, 2]], dtype=np.int32)
+        else:
+            coords, tris = W.mesh_disk_graded(4.0, n, 3.0, interfaces=(1.0,), seed=seed, grade_from=1.0)
+        V, chi = W.step_index_materials(coords, tris)
+        sigma = W.absorber_profile(coords, 4.0, 20.0)
+        meshes.append(api.Mesh(coords, tris, V, chi, sigma))
+        opss.append(dec.Operators(coords, tris, V, chi))
+        sigs.append(sigma)
+        psis.append(W.hg_superpositions(coords, 1, np.random.default_rng(seed)) * 2.0)
+    plan = api.Plan(meshes, [1] * len(specs), "c64")
+    cfg = plan.config()
+    assert cfg["fused_kernel"] == 0 and cfg["tile_rows"] == 512 and cfg["tile_slots"] >= 2
+    dz = 2e-3
+    plan.set_shape("rows", ctas_per_sm=2)
+    ref = [to_dev(p, torch.complex64) for p in psis]
+    plan.propagate(ref, dz, 7, diag_every=3, kerr=kerr)
+    for slots in range(cfg["tile_slots"], 1, -1):
+        plan.set_shape("tile", tile_slots=slots)
+        assert plan.config()["fused_kernel"] == 1
+        out = [to_dev(p, torch.complex64) for p in psis]
+        plan.propagate(out, dz, 7, diag_every=3, kerr=kerr)
+        for x, y in zip(out, ref):
+            assert torch.equal(x, y), slots
+    for ops, sigma, p0, t in zip(opss[:4], sigs, psis, out):
+        want = bpm.propagate(ops, (1.0,), p0, dz, 7, sigma, kerr=kerr)
+        assert rel(ops, from_dev(t), want) <= 1e-4
+
+
 @pytest.mark.parametrize("precision,B", [("c64", 1), ("c128", 1), ("c64", 4)])
 def test_row_kernel_metadata_cache(precision, B):
     """Single-mesh plans cache each CTA's warp-item metadata (columns,
