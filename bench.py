@@ -36,12 +36,13 @@ FALLBACK_HBM_GBS = 6400.0
 METRIC = "vertex-steps/s (complex field) + % HBM roofline, FP32/batched vs plain FP64 on GPU"
 UNIT = "vertex-steps/s"
 
-# DRAM bytes (read + write) per algorithmic byte of the march kernel on this
-# workload, from the one-pass ncu capture of this bench's own launches, valid
-# for the kernel source whose hash is recorded with it; traffic is reported as
-# null otherwise.
-TRAFFIC_RATIO = 0.9350
-TRAFFIC_SRC_HASH = "0991449c659d59fc"
+# DRAM bytes (read + write) per algorithmic byte of the march kernels on this
+# workload, from an ncu capture of this bench's own launches (the
+# autotuner's 3-step trial launches), valid for the kernel source whose hash
+# is recorded with them; traffic is reported as null for another source or
+# kernel.
+TRAFFIC_RATIO = {"march_tile_kernel": 0.9351, "march_flow_kernel": 0.9633}
+TRAFFIC_SRC_HASH = "3c92bbc47eabbabe"
 
 
 def kernel_source_hash() -> str:
@@ -235,17 +236,18 @@ def run_ours(args, rank, world, local_rank):
     alg_step = algorithmic_bytes_per_step(infos, fields, degrees)
     peak, peak_kind = hbm_peak()
     achieved = alg_step * args.steps / (march_ms * 1e-3) / 1e9
-    traffic = None
-    if TRAFFIC_RATIO is not None and TRAFFIC_SRC_HASH == kernel_source_hash():
-        traffic = TRAFFIC_RATIO * alg_step * args.steps
     value = units_per_step * args.steps * world / (ms * 1e-3)
     e2e_value = units_per_step * args.steps * world / (e2e_ms * 1e-3)
     # kernels of ours per timed call: permute in / out per mesh, the march
     # kernel, two diagnostic kernels per mesh
     launches = 1 + 4 * len(meshes)
-    fk = cfg.get("fused_kernel", 0) if args.variant == "fused" else {"pairs": 2, "rows": 0}.get(args.variant, 0)
+    fk = cfg.get("fused_kernel", 0) if args.variant == "fused" else {"pairs": 2, "rows": 0, "flow": 3}.get(args.variant, 0)
     tiled = fk >= 1
-    kernel_name = {2: "march_pair_kernel", 1: "march_tile_kernel"}.get(fk, "march_kernel<float,%d>" % cfg["fields_padded"])
+    kernel_name = {3: "march_flow_kernel", 2: "march_pair_kernel", 1: "march_tile_kernel"}.get(
+        fk, "march_kernel<float,%d>" % cfg["fields_padded"])
+    traffic = None
+    if kernel_name in TRAFFIC_RATIO and TRAFFIC_SRC_HASH == kernel_source_hash():
+        traffic = TRAFFIC_RATIO[kernel_name] * alg_step * args.steps
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
@@ -257,8 +259,9 @@ def run_ours(args, rank, world, local_rank):
             "vertices_total": int(sum(i["n_vertices"] for i in infos)), "fields_per_mesh": fields[0],
             "cheb_degree_min": int(min(degrees)), "cheb_degree_max": int(max(degrees)),
             "ordering": "hilbert", "parallelism": "replicas" if world > 1 else "single",
-            "grid": cfg["pair_grid"] if fk == 2 else cfg["tile_grid"] if tiled else cfg["grid"],
-            "block": cfg["tile_block"] if tiled else cfg["block"],
+            "grid": cfg["pair_grid"] if fk == 2 else cfg["flow_grid"] if fk == 3 else cfg["tile_grid"] if tiled else cfg["grid"],
+            # the dataflow kernel has one warp more than the tile-staged kernel (its publisher)
+            "block": cfg["tile_block"] + (32 if fk == 3 else 0) if tiled else cfg["block"],
             "passes_per_step": cfg["passes"] if fk == 2 else None,
             "march_kernel": kernel_name, "tile_slots": cfg["tile_slots_used"] if tiled else 0,
             "forward_walk": cfg["forward_walk"],
@@ -371,7 +374,7 @@ def single_field_runs(api, torch, dev, steps, peak, which=("disk", "vortex")):
         out[name] = {
             "vertices": n0, "steps": steps, "dz": wl.dz, "cheb_degree": M, "value": n0 * steps / (ms * 1e-3),
             "unit": UNIT, "march_ms": march_ms, "kernel": "march_kernel<float,1>" if not cfg["fused_kernel"]
-            else "march_tile_kernel", "autotune": {k: tune[k] for k in ("kernel", "ctas_per_sm", "forward_walk",
+            else "march_tile1_kernel", "autotune": {k: tune[k] for k in ("kernel", "ctas_per_sm", "forward_walk",
                                                                         "values_per_thread", "candidates")},
             "alg_bytes_per_vertex_step": alg / steps / n0, "hbm_alg_frac": alg / (march_ms * 1e-3) / 1e9 / peak,
             "working_set_mb": round((n0 * (8 * info["mean_degree"] + 8) + 4 * 8 * n0 + 12 * n0) / 1e6, 1),
