@@ -475,8 +475,7 @@ int decbpm_propagate_batch(const decbpm_mesh_t *meshes, int32_t n_meshes, const 
  * at this call, else DECBPM_ERR_INVALID_ARG) and psi_dev are the caller's.
  * No diagnostics are returned.  The first call on a device looks up the
  * array's device address (cudaGetSymbolAddress, with that device current) and
- * keeps it for the process; make that first call before any stream capture.
- * A cudaDeviceReset drops the module, so the kept address is stale after it:
+ * keeps it for the process.  A cudaDeviceReset drops the module, so the kept address is stale after it:
  * do not call this entry point after resetting the device.  All calls share
  * the one array, which keeps the last call's contents (the call clears what
  * must start at zero), so calls that can overlap on the GPU (on different
