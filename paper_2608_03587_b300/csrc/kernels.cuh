@@ -291,23 +291,25 @@ __device__ __forceinline__ bool grid_barrier(unsigned long long *bar, unsigned l
     __syncthreads();
     if (threadIdx.x == 0) {
         target += gridDim.x + extra;
-        __threadfence();
-        atomicAdd(bar, 1ull);
+        // the arrival releases this CTA's writes (seen by thread 0 through the
+        // CTA barrier), the acquiring load of the count the other CTAs' ones
+        asm volatile("red.release.gpu.global.add.u64 [%0], %1;" ::"l"(bar), "l"(1ull) : "memory");
         int ok = 1;
-        const long long t0 = global_ns();
-        unsigned spins = 0;
-        while (ld_acquire_u64(bar) < target) {
-            if ((++spins & 63u) == 0) {
-                if (*(volatile int *)status != 0) { ok = 0; break; }
-                if (global_ns() - t0 > timeout_ns) {
-                    atomicCAS(status, 0, -4);
-                    ok = 0;
-                    break;
+        if (ld_acquire_u64(bar) < target) {
+            const long long t0 = global_ns();
+            for (unsigned spins = 1;; ++spins) {
+                __nanosleep(32);
+                if (ld_acquire_u64(bar) >= target) break;
+                if ((spins & 63u) == 0) {
+                    if (*(volatile int *)status != 0) { ok = 0; break; }
+                    if (global_ns() - t0 > timeout_ns) {
+                        atomicCAS(status, 0, -4);
+                        ok = 0;
+                        break;
+                    }
                 }
             }
-            __nanosleep(32);
         }
-        __threadfence();
         s_ok = ok;
     }
     __syncthreads();
