@@ -284,6 +284,8 @@ typedef struct {
                               than the tile-staged kernel's: a publisher of tile completions) */
     int32_t flow_skip;     /* dataflow kernel: a reversed walk starts this many tiles before the previous
                               walk's end */
+    int32_t flow_ranges;   /* dataflow kernel: 1 = the tile-staged kernel's contiguous ranges of the active
+                              tiles per CTA, 0 = fixed per-CTA chunks of every mesh */
     int32_t tile_rows;     /* rows per tile of the tile-staged kernel: 128 (16 fields, march_tile_kernel),
                               512 (one field, march_tile1_kernel), 0: none */
     int32_t meta_items;    /* row kernel, single-mesh plans: warp items per CTA whose operator metadata
@@ -298,6 +300,7 @@ int decbpm_plan_get_config(decbpm_plan_t plan, decbpm_plan_config *cfg);
  * (1..1000) at step dz on the plan's internal buffers, for every candidate:
  * the stage-pair kernel with 3 or 2 ring slots, the tile-staged kernel
  * with 3 or 2 ring slots and the dataflow kernel with walk skips 4, 8 and 16
+ * (per-CTA chunks) or 8 (contiguous ranges)
  * (complex64 plans with 9..16 fields), the row kernel
  * with 1..max co-resident CTAs per SM and (complex64 plans with 4+ fields) 4 or
  * 2 complex values per thread, each with and without the reverse walk
@@ -323,13 +326,14 @@ typedef struct {
     int32_t walk_skip;     /* dataflow kernel: see decbpm_plan_config.flow_skip (0: the default, 8) */
     int32_t no_meta_cache; /* row kernel: 1 reads the operator metadata every stage (see
                               decbpm_plan_config.meta_items); 0: cached where it fits */
+    int32_t flow_ranges;   /* dataflow kernel: see decbpm_plan_config.flow_ranges */
 } decbpm_tune_result;
 int decbpm_plan_autotune(decbpm_plan_t plan, double dz, int32_t kerr_mode, int32_t trial_steps, void *stream,
                          decbpm_tune_result *out);
 /* Apply a launch shape without timing (for example one that decbpm_plan_autotune
  * returned in an earlier process): variant (PAIRS, FUSED = tile-staged, FLOW,
  * ROWS), ctas_per_sm, values_per_thread and no_meta_cache (ROWS), tile_slots
- * (PAIRS, FUSED, FLOW), walk_skip (FLOW), forward_walk; ms_per_step,
+ * (PAIRS, FUSED, FLOW), walk_skip and flow_ranges (FLOW), forward_walk; ms_per_step,
  * candidates and from_cache are ignored.  Shapes the
  * plan cannot run return DECBPM_ERR_UNSUPPORTED or DECBPM_ERR_INVALID_ARG. */
 int decbpm_plan_set_shape(decbpm_plan_t plan, const decbpm_tune_result *shape);

@@ -80,7 +80,8 @@ class PlanConfig(ctypes.Structure):
                 ("tile_slots_used", ctypes.c_int32), ("forward_walk", ctypes.c_int32), ("pair_slots", ctypes.c_int32),
                 ("pair_slot_bytes", ctypes.c_int32), ("pair_grid", ctypes.c_int32), ("passes", ctypes.c_int32),
                 ("values_per_thread", ctypes.c_int32), ("rows_per_item", ctypes.c_int32),
-                ("flow_grid", ctypes.c_int32), ("flow_skip", ctypes.c_int32), ("tile_rows", ctypes.c_int32),
+                ("flow_grid", ctypes.c_int32), ("flow_skip", ctypes.c_int32), ("flow_ranges", ctypes.c_int32),
+                ("tile_rows", ctypes.c_int32),
                 ("meta_items", ctypes.c_int32)]
 
     def as_dict(self):
@@ -91,7 +92,7 @@ class TuneResult(ctypes.Structure):
     _fields_ = [("variant", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32), ("tile_slots", ctypes.c_int32),
                 ("forward_walk", ctypes.c_int32), ("ms_per_step", ctypes.c_double), ("candidates", ctypes.c_int32),
                 ("from_cache", ctypes.c_int32), ("values_per_thread", ctypes.c_int32), ("walk_skip", ctypes.c_int32),
-                ("no_meta_cache", ctypes.c_int32)]
+                ("no_meta_cache", ctypes.c_int32), ("flow_ranges", ctypes.c_int32)]
 
     def as_dict(self):
         d = {k: getattr(self, k) for k, _ in self._fields_}

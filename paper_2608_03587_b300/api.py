@@ -267,13 +267,13 @@ class Plan:
         return r.as_dict()
 
     def set_shape(self, kernel="rows", ctas_per_sm=1, tile_slots=0, forward_walk=0, values_per_thread=0,
-                  walk_skip=0, no_meta_cache=0):
+                  walk_skip=0, no_meta_cache=0, flow_ranges=0):
         """decbpm_plan_set_shape: apply a launch shape without timing (kernel
         "pairs", "tile", "flow" or "rows"; e.g. the dict autotune() returned)."""
         var = {"pairs": L.VARIANT_PAIRS, "tile": L.VARIANT_FUSED, "flow": L.VARIANT_FLOW, "rows": L.VARIANT_ROWS}[kernel]
         r = L.TuneResult(variant=var, ctas_per_sm=int(ctas_per_sm), tile_slots=int(tile_slots),
                          forward_walk=int(forward_walk), values_per_thread=int(values_per_thread),
-                         walk_skip=int(walk_skip), no_meta_cache=int(no_meta_cache))
+                         walk_skip=int(walk_skip), no_meta_cache=int(no_meta_cache), flow_ranges=int(flow_ranges))
         L.check(_lib().decbpm_plan_set_shape(self._h, ctypes.byref(r)))
 
     def config(self) -> dict:

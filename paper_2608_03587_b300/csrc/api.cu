@@ -506,6 +506,7 @@ struct decbpm_plan_s {
     int meta_grid = 0, meta_fpt = 0, meta_on = -1, meta_items = 0;
     size_t meta_dyn = 0;
     int flow_skip = kDefaultFlowSkip;
+    int flow_ranges = 0;                         // dataflow kernel: 1 = contiguous ranges, 0 = chunk lists
     // graphs: key -> exec
     std::map<std::tuple<double, int64_t, int32_t, int32_t, double, int32_t>, cudaGraphExec_t> graphs;
     bool graphs_ok = true;
@@ -1158,6 +1159,7 @@ static int launch_march(decbpm_plan_t P, cudaStream_t s, int n_steps, int kerr_m
                 mp.cta_cnt = P->cta_cnt;
                 mp.active_meshes = P->active_meshes;
                 mp.flow_skip = P->flow_skip;
+                mp.flow_ranges = P->flow_ranges;
                 CK(cudaMemsetAsync(P->tile_done, 0, sizeof(unsigned) * size_t(P->total_tiles), s));
                 cfg.gridDim = dim3(P->flow_grid);
                 cfg.blockDim = dim3(kFlowThreads);
@@ -1885,7 +1887,7 @@ static int soliton_impl(decbpm_mesh_t mesh, decbpm_plan_t P, const decbpm_solito
 // plan's internal buffers (zeroed first: their contents are scratch between
 // calls).  The winner is cached for the process, keyed by the meshes'
 // content fingerprints, the field counts, the precision, dz and kerr_mode.
-struct TuneChoice { int rows, per_sm, slots, forward, pair, fpt; double ms; int flow, skip, nometa; };
+struct TuneChoice { int rows, per_sm, slots, forward, pair, fpt; double ms; int flow, skip, nometa, ranges; };
 static std::mutex g_tune_mutex;
 static std::map<std::string, TuneChoice> g_tune_cache;
 
@@ -1924,6 +1926,7 @@ static void apply_choice(decbpm_plan_t P, const TuneChoice &c) {
     P->tune_flow = c.flow;
     P->tune_meta = c.nometa ? 0 : 1;
     P->flow_skip = c.skip > 0 ? c.skip : kDefaultFlowSkip;
+    P->flow_ranges = c.ranges;
     P->tune_slots = c.slots;
     P->forward_walk = c.forward;
     P->grid = P->num_sms * c.per_sm;
@@ -1938,6 +1941,7 @@ static decbpm_tune_result tune_result(const TuneChoice &c, int trial_steps, int 
                                                                                      : DECBPM_VARIANT_FUSED;
     r.walk_skip = c.flow ? c.skip : 0;
     r.no_meta_cache = c.nometa;
+    r.flow_ranges = c.flow ? c.ranges : 0;
     r.ctas_per_sm = c.rows ? c.per_sm : 1;
     r.tile_slots = c.slots;
     r.forward_walk = c.forward;
@@ -1978,9 +1982,11 @@ static int autotune_impl(decbpm_plan_t P, double dz, int kerr_mode, int trial_st
             for (int sl = P->pair_slots; sl >= 2; --sl) cand.push_back({0, 1, sl, fw, 1, fpt0, 0.0, 0, 0});
         if (P->tile_mode)
             for (int sl = P->n_slots; sl >= 2; --sl) cand.push_back({0, P->max_per_sm, sl, fw, 0, fpt0, 0.0, 0, 0});
-        if (P->flow_mode)         // the skip only shapes reversed walks
+        if (P->flow_mode) {       // the skip only shapes reversed walks
             for (int skip : (fw == 0 ? std::vector<int>{4, 8, 16} : std::vector<int>{kDefaultFlowSkip}))
                 cand.push_back({0, P->max_per_sm, P->n_slots, fw, 0, fpt0, 0.0, 1, skip});
+            cand.push_back({0, P->max_per_sm, P->n_slots, fw, 0, fpt0, 0.0, 1, kDefaultFlowSkip, 0, 1});
+        }
         std::vector<int> fpts = {fpt0};
         if (fpt0 == 4 && fpt_allowed(P->precision, P->bpad, 2)) fpts.push_back(2);
         for (int fpt : fpts) {
@@ -2688,6 +2694,7 @@ int decbpm_plan_set_shape(decbpm_plan_t P, const decbpm_tune_result *shape) {
         c.fpt = default_fpt(P->precision, P->bpad);
         c.flow = shape->variant == DECBPM_VARIANT_FLOW ? 1 : 0;
         c.skip = c.flow ? (shape->walk_skip > 0 ? shape->walk_skip : kDefaultFlowSkip) : 0;
+        c.ranges = c.flow && shape->flow_ranges ? 1 : 0;
     } else if (shape->variant == DECBPM_VARIANT_ROWS) {
         if (!fpt_allowed(P->precision, P->bpad, c.fpt))
             return fail(DECBPM_ERR_UNSUPPORTED, "values_per_thread %d is not built for this plan", c.fpt);
@@ -2741,6 +2748,7 @@ int decbpm_plan_get_config(decbpm_plan_t P, decbpm_plan_config *cfg) {
     cfg->tile_rows = P->tile_mode ? (P->tile_one ? kTile1Rows : kTileRows) : 0;
     cfg->flow_grid = P->flow_mode ? P->flow_grid : 0;
     cfg->flow_skip = P->flow_skip;
+    cfg->flow_ranges = P->flow_ranges;
     cfg->meta_items = 0;
     if (cfg->fused_kernel == 0) {
         const void *fn = march_kernel_ptr(P->precision, P->bpad, P->fpt);

@@ -265,7 +265,8 @@ template <typename R> struct MarchParams {
     const int32_t *cta_cnt;      // [grid * n_meshes]: tiles of the CTA in meshes 0..j
     const int32_t *active_meshes;// [S]: meshes with M > S-1-s (a prefix)
     int32_t flow_skip;           // reversed walks start this many tiles before the previous stage's end
-    int32_t pad_flow;
+    int32_t flow_ranges;         // 1: tiles assigned as the tile-staged kernel does (contiguous ranges of
+                                 // the active tiles) instead of the per-CTA chunk lists
 };
 
 // ------------------------------------------------------------ grid barrier
@@ -799,6 +800,7 @@ constexpr int kTileComputeWarps = 16;
 constexpr int kTileCopyWarps = 3;     // copy warp c owns ring slot c (at most 3 slots)
 constexpr int kTileThreads = 32 * (kTileComputeWarps + kTileCopyWarps);
 constexpr int kMaxSlots = kTileCopyWarps;
+constexpr int kDoneSets = kMaxSlots;     // dataflow march: completion counters (one per item residue)
 constexpr int kHaloRegs = 3;          // halo rows per copy-warp lane held ahead (96 per tile)
 // single-field tiles: 512 rows of one complex64 field (8-byte rows), one row
 // per compute thread; the slot header holds the tile's 16 slice offsets and
@@ -925,23 +927,35 @@ struct LookCursor {
 // (epoch, position) item of any CTA depends only on finished items of the
 // previous epoch, all CTAs being co-resident (cooperative launch); every wait
 // is bounded.
+// The assignment of tiles to CTAs does not enter the dependency rule (a tile
+// waits for its neighbours' previous stage whichever CTAs ran them), so the
+// walk may also take the tile-staged kernel's contiguous ranges of the active
+// tiles (flow_ranges; tiles = nullptr): a CTA then re-reads the rows it wrote
+// last, at the cost of waits where a joining mesh shifts the ranges.
 struct FlowRange {
     int base, n, skip;
     bool rev;
     const int32_t *tiles;
     __device__ int at(int i) const {
         const int p = rev ? n - 1 - (i + skip) % n : i;
-        return __ldg(tiles + base + p);
+        return tiles ? __ldg(tiles + base + p) : base + p;
     }
 };
 __device__ __forceinline__ FlowRange flow_range(const MarchParams<float> &P, int step, int s) {
-    const int a = __ldg(P.active_meshes + s);
     FlowRange R;
-    R.base = __ldg(P.cta_ptr + blockIdx.x);
-    R.n = __ldg(P.cta_cnt + blockIdx.x * P.n_meshes + a - 1);
+    if (P.flow_ranges) {
+        const int n_act = __ldg(P.active_tiles + s);
+        R.base = int((long long)n_act * blockIdx.x / gridDim.x);
+        R.n = int((long long)n_act * (blockIdx.x + 1) / gridDim.x) - R.base;
+        R.tiles = nullptr;
+    } else {
+        const int a = __ldg(P.active_meshes + s);
+        R.base = __ldg(P.cta_ptr + blockIdx.x);
+        R.n = __ldg(P.cta_cnt + blockIdx.x * P.n_meshes + a - 1);
+        R.tiles = P.cta_tiles;
+    }
     R.skip = P.flow_skip;
     R.rev = P.forward_walk == 0 && (((step & P.S) ^ s) & 1);     // parity of the epoch step * S + s
-    R.tiles = P.cta_tiles;
     return R;
 }
 struct FlowCursor {
@@ -1439,7 +1453,7 @@ __device__ __forceinline__ void tile_march_role(int copier, const MarchParams<fl
     FlowCursor fcur{0, 0, 0, FlowRange{}};
     if constexpr (FLOW) fcur.R = flow_range(P, 0, 0);
     else cur.R = tile_range(P, 0);
-    unsigned seen = 0;           // publisher: compute-warp tile completions seen (and fenced) so far
+    unsigned seen = 0;           // publisher: items before this one are known finished (and fenced)
     int *ring = s_look + copier * (kLookAhead * kLookInts);
     if constexpr (COPIER) {
         fence_proxy_async_global();
@@ -1498,17 +1512,21 @@ __device__ __forceinline__ void tile_march_role(int copier, const MarchParams<fl
             for (int i = 0; i < n_tiles && ok; ++i) {
                 const unsigned q = seq + unsigned(i), sl = q % D;
                 if constexpr (PUBLISHER) {
-                    // tile q is finished once all compute warps counted it; one fence
-                    // covers every tile seen finished so far (counts compared modulo 2^32)
-                    const unsigned need = (q + 1u) * unsigned(kTileComputeWarps);
-                    if (int(seen - need) < 0) {
-                        unsigned c = ld_acquire_cta_shared(s_done);
-                        if (int(c - need) < 0) {
+                    // Item j is finished once every compute warp counted it in
+                    // s_done[j % kDoneSets]: a warp starts item j + kDoneSets only after all
+                    // warps finished item j (the ring has at most kDoneSets slots), so that
+                    // counter then holds exactly kTileComputeWarps (j / kDoneSets + 1)
+                    // (compared modulo 2^32).  One fence covers every item seen finished.
+                    auto finished = [&](unsigned j) {
+                        const unsigned c = ld_acquire_cta_shared(s_done + j % kDoneSets);
+                        return int(c - (j / kDoneSets + 1u) * unsigned(kTileComputeWarps)) >= 0;
+                    };
+                    if (int(q - seen) >= 0) {                 // q is not known finished yet
+                        if (!finished(q)) {
                             const long long t0 = global_ns();
                             for (unsigned spins = 1;; ++spins) {
                                 __nanosleep(64);
-                                c = ld_acquire_cta_shared(s_done);
-                                if (int(c - need) >= 0) break;
+                                if (finished(q)) break;
                                 if ((spins & 63u) == 0) {
                                     if (*(volatile int *)P.status != 0) { ok = false; break; }
                                     if (global_ns() - t0 > P.timeout_ns) {
@@ -1519,7 +1537,8 @@ __device__ __forceinline__ void tile_march_role(int copier, const MarchParams<fl
                                 }
                             }
                         }
-                        seen = c;
+                        seen = q + 1u;                          // and the next ones already done
+                        while (seen - q < unsigned(kDoneSets) && finished(seen)) ++seen;
                         fence_acq_rel_gpu();
                     }
                     if (ok && lane == 0) st_relaxed_u32(P.tile_done + FR.at(i), epoch + 1u);
@@ -1561,10 +1580,13 @@ __device__ __forceinline__ void tile_march_role(int copier, const MarchParams<fl
                         else
                             tile_compute<FLOW>(s_view, s_coef, k, s_ring + (size_t)sl * P.slot_bytes,
                                                h_post, P.kerr_mode, P);
+                        // dataflow: the rows just stored are read next by bulk copies (async
+                        // proxy), possibly of another CTA right after the counter says so
+                        if constexpr (FLOW) fence_proxy_async_global();
                         __syncwarp();
                         if (lane == 0) {
                             mbar_arrive(smem_u32(&s_empty[sl]));
-                            if constexpr (FLOW) red_release_cta_shared(s_done, 1u);
+                            if constexpr (FLOW) red_release_cta_shared(s_done + q % kDoneSets, 1u);
                         }
                     }
                 }
@@ -1600,7 +1622,8 @@ __device__ __forceinline__ void tile_march_body(const MarchParams<float> &P) {
     __shared__ StageCoef<float> s_coef[kMaxMeshes];
     __shared__ __align__(8) unsigned long long s_full[kMaxSlots], s_empty[kMaxSlots];
     __shared__ __align__(16) int s_look[kTileCopyWarps * kLookAhead * kLookInts];
-    __shared__ unsigned s_done;                       // dataflow march: tiles x compute warps finished
+    __shared__ unsigned s_done[kDoneSets];            // dataflow march: finished items x compute warps,
+                                                      // per item residue mod kDoneSets
     for (int i = threadIdx.x; i < P.n_meshes; i += blockDim.x) {
         s_begin[i] = P.meshes[i].item_begin;
         s_tbeg[i] = P.meshes[i].tile_begin;
@@ -1610,21 +1633,21 @@ __device__ __forceinline__ void tile_march_body(const MarchParams<float> &P) {
         mbar_init(smem_u32(&s_full[threadIdx.x]), 1);
         mbar_init(smem_u32(&s_empty[threadIdx.x]), kTileComputeWarps);
     }
-    if (threadIdx.x == 0) s_done = 0;
+    if (threadIdx.x < kDoneSets) s_done[threadIdx.x] = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     __syncthreads();
     const int warp = threadIdx.x >> 5;
     if (warp >= kTileComputeWarps + kTileCopyWarps) {
         if constexpr (FLOW)
             tile_march_role<false, true, true>(0, P, s_ring, s_begin, s_tbeg, s_view, s_coef, s_full, s_empty, s_look,
-                                               &s_done);
+                                               s_done);
     } else if (warp >= kTileComputeWarps) {
         tile_march_role<true, FLOW, false, ONE>(warp - kTileComputeWarps, P, s_ring, s_begin, s_tbeg, s_view, s_coef,
-                                                s_full, s_empty, s_look, &s_done);
+                                                s_full, s_empty, s_look, s_done);
         cp_async_wait<0>();           // no look-ahead copy may land after the CTA exits
     } else {
         tile_march_role<false, FLOW, false, ONE>(0, P, s_ring, s_begin, s_tbeg, s_view, s_coef, s_full, s_empty,
-                                                 s_look, &s_done);
+                                                 s_look, s_done);
     }
 }
 

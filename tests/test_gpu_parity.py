@@ -389,7 +389,8 @@ def test_dataflow_kernel_matches_tile_kernel(kerr):
     kernel's fields bit for bit: meshes of uneven size and degree (meshes
     join the march at different stages), 9..16 fields, a mesh below one tile
     and a single triangle, three launches (diagnostics every 3 of 7 steps),
-    walk skips from 1 to beyond a CTA's share and either walk.  Repeated runs
+    walk skips from 1 to beyond a CTA's share, either walk, per-CTA chunks or
+    the tile kernel's contiguous ranges.  Repeated runs
     of one shape are bitwise equal too (the waits order every read after the
     write it needs, whatever the timing)."""
     specs = [(600, 16, 51), (2500, 9, 52), (5000, 12, 53), (90, 16, 54), (40, 16, 55), (3, 16, 56),
@@ -412,13 +413,15 @@ def test_dataflow_kernel_matches_tile_kernel(kerr):
     ref = [to_dev(p, torch.complex64) for p in psis]
     plan.set_shape("tile", tile_slots=3)
     plan.propagate(ref, dz, 7, diag_every=3, kerr=kerr)
-    for slots, skip, fw, reps in ((3, 8, 0, 3), (2, 8, 0, 1), (3, 1, 0, 1), (3, 4000, 0, 1), (3, 8, 1, 1)):
-        plan.set_shape("flow", tile_slots=slots, walk_skip=skip, forward_walk=fw)
+    for slots, skip, fw, reps, ranges in ((3, 8, 0, 3, 0), (2, 8, 0, 1, 0), (3, 1, 0, 1, 0), (3, 4000, 0, 1, 0),
+                                          (3, 8, 1, 1, 0), (3, 8, 0, 2, 1), (3, 8, 1, 1, 1), (2, 1, 0, 1, 1)):
+        plan.set_shape("flow", tile_slots=slots, walk_skip=skip, forward_walk=fw, flow_ranges=ranges)
+        assert plan.config()["flow_ranges"] == ranges
         for _ in range(reps):
             out = [to_dev(p, torch.complex64) for p in psis]
             plan.propagate(out, dz, 7, diag_every=3, kerr=kerr)
             for x, y in zip(out, ref):
-                assert torch.equal(x, y), (slots, skip, fw)
+                assert torch.equal(x, y), (slots, skip, fw, ranges)
     # the explicit variant runs it whatever shape the plan holds
     plan.set_shape("tile", tile_slots=3)
     out = [to_dev(p, torch.complex64) for p in psis]
@@ -428,8 +431,9 @@ def test_dataflow_kernel_matches_tile_kernel(kerr):
 
 
 def test_dataflow_kernel_full_bench_batch():
-    """The bench workload at full size: a 3-step launch of the dataflow kernel
-    against the tile-staged kernel, bit for bit."""
+    """The bench workload at full size: 3-step launches of the dataflow kernel
+    (per-CTA chunks and contiguous ranges, several walks) against the
+    tile-staged kernel, bit for bit."""
     wl = W.batched_fibers(n_meshes=16, fields_per_mesh=16, n_min=20_000, ratio=25.0, seed=4)
     meshes = [api.Mesh.from_workload(m, p=wl.p) for m in wl.meshes]
     plan = api.Plan(meshes, [16] * len(meshes), "c64")
@@ -441,6 +445,15 @@ def test_dataflow_kernel_full_bench_batch():
     plan.propagate(b, wl.dz, 3)
     for x, y in zip(a, b):
         assert torch.equal(x, y)
+    # the tile kernel's contiguous ranges: a tile's own rows may come from
+    # another CTA's stores of the stage just before (ordering of the async-proxy
+    # bulk reads after the completion counters), several walks, repeated
+    for skip, fw in ((16, 0), (8, 0), (4, 0), (8, 1), (16, 0)):
+        plan.set_shape("flow", tile_slots=3, walk_skip=skip, forward_walk=fw, flow_ranges=1)
+        c = [to_dev(p, torch.complex64) for p in wl.psi0]
+        plan.propagate(c, wl.dz, 3)
+        for x, y in zip(c, b):
+            assert torch.equal(x, y), (skip, fw)
 
 
 @pytest.mark.parametrize("precision", ["c64", "c128"])
@@ -480,7 +493,7 @@ def test_autotuner_picks_a_shape_without_changing_results(precision):
             assert torch.equal(x, y)
     again = api.Plan(meshes, [p.shape[1] for p in psis], precision).autotune(dz, trial_steps=2)
     assert again["from_cache"] == 1
-    keys = ("kernel", "ctas_per_sm", "tile_slots", "forward_walk", "walk_skip")
+    keys = ("kernel", "ctas_per_sm", "tile_slots", "forward_walk", "walk_skip", "flow_ranges")
     assert {k: again[k] for k in keys} == {k: tune[k] for k in keys}
     with pytest.raises(L.DecbpmError):
         plan.autotune(dz, trial_steps=0)
