@@ -37,12 +37,15 @@ METRIC = "vertex-steps/s (complex field) + % HBM roofline, FP32/batched vs plain
 UNIT = "vertex-steps/s"
 
 # DRAM bytes (read + write) per algorithmic byte of the march kernels on this
-# workload, from an ncu capture of this bench's own launches (the
+# workload (the dataflow kernel per tile assignment, walk skip and reversed
+# walk, the shapes that were captured), from an ncu capture of this bench's own launches (the
 # autotuner's 3-step trial launches), valid for the kernel source whose hash
 # is recorded with them; traffic is reported as null for another source or
 # kernel.
-TRAFFIC_RATIO = {"march_tile_kernel": 0.9351, "march_flow_kernel": 0.9610}
-TRAFFIC_SRC_HASH = "2587ed276f6dbf72"
+TRAFFIC_RATIO = {"march_tile_kernel": 0.9351,
+                 "march_flow_kernel:chunks:skip4:rev": 0.9606, "march_flow_kernel:chunks:skip8:rev": 0.9769,
+                 "march_flow_kernel:chunks:skip16:rev": 0.9893, "march_flow_kernel:ranges:skip8:rev": 0.9836}
+TRAFFIC_SRC_HASH = "3ecf38a16d1e13d4"
 
 
 def kernel_source_hash() -> str:
@@ -246,8 +249,12 @@ def run_ours(args, rank, world, local_rank):
     kernel_name = {3: "march_flow_kernel", 2: "march_pair_kernel", 1: "march_tile_kernel"}.get(
         fk, "march_kernel<float,%d>" % cfg["fields_padded"])
     traffic = None
-    if kernel_name in TRAFFIC_RATIO and TRAFFIC_SRC_HASH == kernel_source_hash():
-        traffic = TRAFFIC_RATIO[kernel_name] * alg_step * args.steps
+    traffic_key = kernel_name
+    if fk == 3:
+        traffic_key += ":%s:skip%d:%s" % ("ranges" if cfg.get("flow_ranges") else "chunks", cfg.get("flow_skip", 0),
+                                          "fwd" if cfg.get("forward_walk") else "rev")
+    if traffic_key in TRAFFIC_RATIO and TRAFFIC_SRC_HASH == kernel_source_hash():
+        traffic = TRAFFIC_RATIO[traffic_key] * alg_step * args.steps
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
@@ -266,8 +273,9 @@ def run_ours(args, rank, world, local_rank):
             "march_kernel": kernel_name, "tile_slots": cfg["tile_slots_used"] if tiled else 0,
             "forward_walk": cfg["forward_walk"],
             "autotune": None if tune is None else {k: tune[k] for k in ("kernel", "ctas_per_sm", "tile_slots",
-                                                                        "forward_walk", "values_per_thread",
-                                                                        "ms_per_step", "candidates")},
+                                                                        "forward_walk", "walk_skip", "flow_ranges",
+                                                                        "values_per_thread", "ms_per_step",
+                                                                        "candidates")},
             "autotune_s": round(tune_s, 2),
             "cuda_graph": bool(cfg["graphs"]),
             "l2": "working set %.2f GB > 126 MB L2; no flush" % (units_per_step * 8 * 4 / 1e9),
