@@ -430,6 +430,33 @@ def test_dataflow_kernel_matches_tile_kernel(kerr):
         assert torch.equal(x, y)
 
 
+def test_dataflow_kernel_repeated_launches_are_bitwise_stable():
+    """Ordering check of the dataflow kernel's completion protocol: many
+    launches of a plan whose meshes join the march at different stages,
+    cycling the ring slots, walk skips, walk direction and tile assignment,
+    each bit for bit the tile-staged kernel's fields (a tile published before
+    all its rows were stored would show up as a last-bit difference)."""
+    specs = [(600, 16, 51), (2500, 9, 52), (5000, 12, 53), (90, 16, 54), (40, 16, 55), (20000, 16, 57),
+             (9000, 10, 58)]
+    meshes, psis = [], []
+    for n, B, seed in specs:
+        coords, tris = W.mesh_disk_graded(4.0, n, 3.0, interfaces=(1.0,), seed=seed, grade_from=1.0)
+        V, chi = W.step_index_materials(coords, tris)
+        meshes.append(api.Mesh(coords, tris, V, chi, W.absorber_profile(coords, 4.0, 20.0)))
+        psis.append(W.hg_superpositions(coords, B, np.random.default_rng(seed)) * 2.0)
+    plan = api.Plan(meshes, [p.shape[1] for p in psis], "c64")
+    plan.set_shape("tile", tile_slots=3)
+    ref = [to_dev(p, torch.complex64) for p in psis]
+    plan.propagate(ref, 2e-3, 40)
+    for rep in range(16):
+        plan.set_shape("flow", tile_slots=3 if rep % 2 else 2, walk_skip=1 + rep % 9, forward_walk=int(rep % 3 == 0),
+                       flow_ranges=rep % 2)
+        out = [to_dev(p, torch.complex64) for p in psis]
+        plan.propagate(out, 2e-3, 40)
+        for x, y in zip(out, ref):
+            assert torch.equal(x, y), rep
+
+
 def test_dataflow_kernel_full_bench_batch():
     """The bench workload at full size: 3-step launches of the dataflow kernel
     (per-CTA chunks and contiguous ranges, several walks) against the
