@@ -1887,7 +1887,11 @@ static int soliton_impl(decbpm_mesh_t mesh, decbpm_plan_t P, const decbpm_solito
 // plan's internal buffers (zeroed first: their contents are scratch between
 // calls).  The winner is cached for the process, keyed by the meshes'
 // content fingerprints, the field counts, the precision, dz and kerr_mode.
-struct TuneChoice { int rows, per_sm, slots, forward, pair, fpt; double ms; int flow, skip, nometa, ranges; };
+struct TuneChoice {
+    int rows = 0, per_sm = 0, slots = 0, forward = 0, pair = 0, fpt = 0;
+    double ms = 0.0;
+    int flow = 0, skip = 0, nometa = 0, ranges = 0;
+};
 static std::mutex g_tune_mutex;
 static std::map<std::string, TuneChoice> g_tune_cache;
 
