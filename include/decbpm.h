@@ -497,6 +497,14 @@ int decbpm_propagate_noalloc(decbpm_mesh_t mesh, const decbpm_params *params, vo
  * exits normally and the context stays usable) and DECBPM_OK when it is 0.   */
 int decbpm_selftest_barrier(int32_t missing_arrivals, int64_t timeout_ns, void *stream);
 
+/* Index-check self test: one tiny kernel passes an out-of-range index (n for
+ * an n-element buffer) through the march kernels' gather-index check and
+ * writes back what the check returned; the index is not used to access
+ * memory.  The bounds-check build (libdecbpm_checked.so) returns
+ * DECBPM_ERR_DEVICE_CHECK (the check fired and replaced the index by 0), the
+ * default build DECBPM_OK (no check compiled in).                            */
+int decbpm_selftest_bounds_check(void *stream);
+
 #ifdef __cplusplus
 }
 #endif

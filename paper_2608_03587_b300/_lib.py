@@ -165,6 +165,7 @@ SIGNATURES = {
     "decbpm_plan_set_shape": (_i32, [_vp, ctypes.POINTER(TuneResult)]),
     "decbpm_plan_last_march_ms": (_i32, [_vp, ctypes.POINTER(ctypes.c_double)]),
     "decbpm_selftest_barrier": (_i32, [_i32, _i64, _vp]),
+    "decbpm_selftest_bounds_check": (_i32, [_vp]),
     "decbpm_mesh_set_potential": (_i32, [_vp, _c_double_p]),
     "decbpm_vjp": (_i32, [_vp, ctypes.POINTER(Params), _vp, _vp, _vp, _vp, _vp, _i64, _i32, _vp]),
     "decbpm_mesh_set_potential_offset": (_i32, [_vp, _vp, _vp]),

@@ -2811,6 +2811,32 @@ int decbpm_selftest_barrier(int32_t missing_arrivals, int64_t timeout_ns, void *
     return st;
 }
 
+int decbpm_selftest_bounds_check(void *stream) {
+    clear_error();
+    cudaStream_t s = (cudaStream_t)stream;
+    int *buf = nullptr;                       // [status, returned index]
+    CK(cudaMalloc(&buf, 2 * sizeof(int)));
+    cudaError_t e = cudaMemsetAsync(buf, 0, 2 * sizeof(int), s);
+    const int n = 1000;
+    if (e == cudaSuccess) {
+        index_check_selftest_kernel<<<1, 32, 0, s>>>(n, buf, buf + 1);
+        e = cudaGetLastError();
+    }
+    int h[2] = {0, 0};
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e == cudaSuccess) e = cudaMemcpy(h, buf, 2 * sizeof(int), cudaMemcpyDeviceToHost);
+    cudaFree(buf);
+    if (e != cudaSuccess) return fail(DECBPM_ERR_CUDA, "self test: %s", cudaGetErrorString(e));
+#ifdef DECBPM_BOUNDS_CHECK
+    if (h[0] != DECBPM_ERR_DEVICE_CHECK || h[1] != 0)
+        return fail(DECBPM_ERR_CUDA, "index check did not fire (status %d, index %d)", h[0], h[1]);
+    return fail(DECBPM_ERR_DEVICE_CHECK, "index %d of a %d-element buffer reported (as requested)", n, n);
+#else
+    if (h[0] != 0 || h[1] != n) return fail(DECBPM_ERR_CUDA, "unexpected status %d, index %d", h[0], h[1]);
+    return DECBPM_OK;
+#endif
+}
+
 int decbpm_propagate_batch(const decbpm_mesh_t *meshes, int32_t n_meshes, const int32_t *fields_per_mesh,
                            const decbpm_params *params, void *const *psi_dev, void *stream, decbpm_diag *diag_out) {
     NvtxRange nvtx_("decbpm_propagate_batch");

@@ -2218,6 +2218,14 @@ __global__ void barrier_selftest_kernel(unsigned long long *bar, int *status, lo
     grid_barrier(bar, target, status, timeout_ns, extra);
 }
 
+// Passes the index n of an n-element buffer through the march kernels' index
+// check and writes back what it returned (the index is never used to access
+// memory): the bounds-check build records DECBPM_ERR_DEVICE_CHECK and returns
+// 0, the default build returns n unchanged.
+__global__ void index_check_selftest_kernel(int n, int *status, int *out) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) out[0] = DECBPM_IDX(n, n, status);
+}
+
 // ------------------------------------------------------------ permutation
 // internal[new][f] = user[perm[new]][f] for f < B, 0 for the padding fields.
 template <typename C>

@@ -83,6 +83,28 @@ def run_cases() -> dict:
 
 
 @pytest.mark.skipif(not torch.cuda.is_available(), reason="no CUDA device")
+def test_index_check_fires_only_in_the_checked_build():
+    """decbpm_selftest_bounds_check passes an out-of-range index through the
+    march kernels' index check (never using it to access memory): the default
+    build returns it unchanged (DECBPM_OK); the checked build, in a child
+    process, reports DECBPM_ERR_DEVICE_CHECK and the context stays usable."""
+    if L.CHECKED:
+        pytest.skip("this process already loaded the bounds-check build")
+    lib = L.load()
+    assert lib.decbpm_selftest_bounds_check(None) == L.OK
+    code = ("import sys; sys.path.insert(0, %r)\n"
+            "from paper_2608_03587_b300 import _lib as L\n"
+            "import torch\n"
+            "lib = L.load(); rc = lib.decbpm_selftest_bounds_check(None)\n"
+            "x = torch.ones(4, device='cuda') * 2; torch.cuda.synchronize()\n"
+            "print('rc', rc, float(x.sum()))\n") % ROOT
+    res = subprocess.run([sys.executable, "-c", code], env=dict(os.environ, DECBPM_BOUNDS_CHECK="1"), cwd=ROOT,
+                         capture_output=True, text=True, timeout=600)
+    assert res.returncode == 0, res.stdout[-2000:] + res.stderr[-2000:]
+    assert "rc %d 8.0" % L.ERR_DEVICE_CHECK in res.stdout, res.stdout
+
+
+@pytest.mark.skipif(not torch.cuda.is_available(), reason="no CUDA device")
 def test_bounds_checked_build_gives_the_same_fields():
     if L.CHECKED:
         pytest.skip("this process already loaded the bounds-check build")
