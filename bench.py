@@ -305,7 +305,7 @@ def run_ours(args, rank, world, local_rank):
             line["adjoint"] = adjoint_run(api, torch, dev)
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args, wl)
-        line["cpu_baseline_all_cores"] = cpu_baseline_all_cores(wl, args.cpu_meshes, 16)
+        line["cpu_baseline_all_cores"] = cpu_baseline_all_cores(wl, args.cpu_meshes, 16, n_steps=args.cpu_steps)
     return line
 
 
@@ -501,10 +501,10 @@ def oracle_sample(wl, n_meshes, n_steps):
 
 
 def cpu_baseline(args, wl):
-    units, secs = oracle_sample(wl, args.cpu_meshes, 1)
+    units, secs = oracle_sample(wl, args.cpu_meshes, args.cpu_steps)
     return {"value": units / secs, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": "first field of the %d smallest fibers, 1 step each (%d vertex-steps, %.1f s); "
-                      "numpy/scipy single thread" % (args.cpu_meshes, units, secs)}
+            "sample": "first field of the %d smallest fibers, %d steps each (%d vertex-steps, %.1f s); "
+                      "numpy/scipy single thread" % (args.cpu_meshes, args.cpu_steps, units, secs)}
 
 
 def _oracle_task(task):
@@ -518,9 +518,9 @@ def _oracle_task(task):
     return coords.shape[0] * n_steps, time.perf_counter() - t, os.getpid()
 
 
-def cpu_baseline_all_cores(wl, n_meshes, n_fields, cores=None):
+def cpu_baseline_all_cores(wl, n_meshes, n_fields, cores=None, n_steps=1):
     """The oracle on every host core: independent (mesh, field) marches of the
-    n_meshes smallest fibers (n_fields fields each, one step), one process per
+    n_meshes smallest fibers (n_fields fields each, n_steps steps), one process per
     core (spawn start: the parent already holds a CUDA context), one thread
     per process.  Throughput = all vertex-steps / the largest per-process march
     time (process start-up and assembly excluded, as the GPU's setup is)."""
@@ -531,7 +531,7 @@ def cpu_baseline_all_cores(wl, n_meshes, n_fields, cores=None):
     for i in order:
         m = wl.meshes[i]
         for b in range(min(n_fields, wl.psi0[i].shape[1])):
-            tasks.append((m.coords, m.cells, m.V_cell, m.chi_cell, m.sigma, wl.p, wl.psi0[i][:, b], wl.dz, 1))
+            tasks.append((m.coords, m.cells, m.V_cell, m.chi_cell, m.sigma, wl.p, wl.psi0[i][:, b], wl.dz, n_steps))
     workers = max(1, min(cores, len(tasks)))
     for var in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
         os.environ[var] = "1"
@@ -543,8 +543,8 @@ def cpu_baseline_all_cores(wl, n_meshes, n_fields, cores=None):
             busy[pid] = busy.get(pid, 0.0) + sec
     wall = max(busy.values())
     return {"value": units / wall, "unit": UNIT, "cores": workers, "kind": "oracle",
-            "sample": "%d fields x 1 step on the %d smallest fibers (%d vertex-steps), one process per core, "
-                      "slowest process %.1f s" % (len(tasks), n_meshes, units, wall)}
+            "sample": "%d fields x %d steps on the %d smallest fibers (%d vertex-steps), one process per core, "
+                      "slowest process %.1f s" % (len(tasks), n_steps, n_meshes, units, wall)}
 
 
 def run_reference(args, rank, world):
@@ -585,6 +585,7 @@ def main():
     ap.add_argument("--fiber-min", type=int, default=20_000, help="vertices of the smallest fiber")
     ap.add_argument("--fiber-ratio", type=float, default=25.0, help="largest / smallest fiber size")
     ap.add_argument("--cpu-meshes", type=int, default=8)
+    ap.add_argument("--cpu-steps", type=int, default=3, help="oracle steps per field of the CPU baselines")
     ap.add_argument("--ref-meshes", type=int, default=4)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
