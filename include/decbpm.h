@@ -450,7 +450,10 @@ int decbpm_bessel_i_scaled(double a, double tol, int32_t n_max, double *out, int
  * of exp(-i a x) evaluated on the complex spectrum (degree from the Bernstein
  * ellipse of the Gershgorin box of A~), D_h the exact flow with the complex
  * v and chib (their imaginary parts damp the intensity by a Bernoulli
- * equation); unfused FP64 launches.  Every other split-step entry point
+ * equation); FP64, one persistent launch per step block where one thread per
+ * row fits the grid (up to about 220k vertices on 148 SMs), else one launch
+ * per Chebyshev term (params->variant = DECBPM_VARIANT_PLAIN forces the
+ * latter).  Every other split-step entry point
  * (plans, batches, complex64, the adjoint, the soliton solver, the
  * allocation-free call) returns DECBPM_ERR_UNSUPPORTED.  pml = NULL or
  * sigma_max = 0 removes the layer.  2D meshes only. */

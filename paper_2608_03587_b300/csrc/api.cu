@@ -499,6 +499,8 @@ struct decbpm_plan_s {
     int32_t *cta_tiles = nullptr, *cta_ptr = nullptr, *cta_cnt = nullptr, *active_meshes = nullptr;
     int cta_cnt_cap = 0, active_meshes_cap = 0;
     int tune_flow = 0;                           // 1: FUSED runs the dataflow kernel
+    PmlStage *pml_st = nullptr;                  // stage table of the fused PML march
+    int pml_st_cap = 0;
     int tune_meta = 1;                           // row kernel, single-mesh plans: cache the item metadata
     // the last metadata-cache decision (row_meta_cache), so launches recorded
     // into a graph make no attribute or occupancy call
@@ -2243,7 +2245,72 @@ static int propagate_plain_pml(decbpm_mesh_t m, const decbpm_params *prm, void *
     int point = 0;
     auto d2 = [](cd z) { return make_double2(z.real(), z.imag()); };
     CK(cudaEventRecord(P->ev0, s));
-    for (int64_t step = 0; step < prm->n_steps; ++step) {
+    // One persistent launch per step block (pml_march_kernel) where the grid
+    // covers every row with one thread (compiled for 6 CTAs of 256 per SM):
+    // it saves the per-term launches of small meshes; larger meshes would
+    // give a thread two rows per stage, and run one launch per term instead.
+    int pml_occ = 0;
+    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&pml_occ, (const void *)pml_march_kernel, 256, 0));
+    const bool pml_fused = prm->variant != DECBPM_VARIANT_PLAIN && prm->n_steps > 0 && pml_occ >= 1 &&
+                           int64_t(P->num_sms) * std::min(pml_occ, 6) * 256 >= n0;
+    if (pml_fused) {
+        // the stage table in the plan's PML workspace
+        std::vector<PmlStage> st(M);
+        for (int k = M - 1; k >= 0; --k) {
+            cd alpha = coef[k], beta = (k == 0) ? 1.0 : 2.0;
+            int g_psi = 0, has_h = 1;
+            if (k == M - 1) { g_psi = 1; beta = 2.0 * coef[M]; has_h = 0; }
+            else if (k == M - 2) { alpha = coef[k] - coef[M]; has_h = 0; }
+            st[k] = PmlStage{d2(alpha), d2(beta), g_psi, has_h};
+        }
+        if (M > P->pml_st_cap) {
+            TRY(P->mem.alloc(&P->pml_st, size_t(M)));
+            P->pml_st_cap = M;
+        }
+        CK(cudaMemcpyAsync(P->pml_st, st.data(), sizeof(PmlStage) * M, cudaMemcpyHostToDevice, s));
+        const int grid = std::min(P->num_sms * std::min(pml_occ, 6), std::max(1, G));
+        CK(cudaMemsetAsync(P->status, 0, sizeof(int), s));
+        for (int64_t done = 0; done < prm->n_steps;) {
+            const int64_t nb = std::min<int64_t>(every, prm->n_steps - done);
+            if (nb > 0x7fffffff) return fail(DECBPM_ERR_INVALID_ARG, "step block too long");
+            PmlMarchParams mp{};
+            mp.o = po;
+            mp.psi = psi;
+            mp.b[0] = b[0]; mp.b[1] = b[1]; mp.b[2] = b[2];
+            mp.st = P->pml_st;
+            mp.M = M;
+            mp.n_steps = int32_t(nb);
+            mp.pre_half = 1;
+            mp.post_half = 1;
+            mp.c = c;
+            mp.rinv = 1.0 / r;
+            mp.h = prm->dz;
+            mp.barrier = P->barrier;
+            mp.status = P->status;
+            mp.timeout_ns = kBarrierTimeoutNs;
+            CK(cudaMemsetAsync(P->barrier, 0, sizeof(unsigned long long), s));
+            cudaLaunchConfig_t cfg = {};
+            cfg.gridDim = dim3(grid);
+            cfg.blockDim = dim3(256);
+            cfg.stream = s;
+            cudaLaunchAttribute attr[1];
+            attr[0].id = cudaLaunchAttributeCooperative;
+            attr[0].val.cooperative = 1;
+            cfg.attrs = attr;
+            cfg.numAttrs = 1;
+            void *args[] = {&mp};
+            CK(cudaLaunchKernelExC(&cfg, (const void *)pml_march_kernel, args));
+            done += nb;
+            if (done >= prm->n_steps) CK(cudaEventRecord(P->ev1, s));
+            TRY(launch_diag<double>(P, s, DECBPM_KERR_LUMPED, point++));
+        }
+        int status = 0;
+        CK(cudaMemcpyAsync(&status, P->status, sizeof(int), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        if (status == DECBPM_ERR_TIMEOUT) return fail(DECBPM_ERR_TIMEOUT, "grid barrier timed out in the PML march");
+        if (status != 0) return fail(status, "device reported status %d", status);
+    }
+    for (int64_t step = 0; step < prm->n_steps && !pml_fused; ++step) {
         const bool block_start = (step % every) == 0;
         const bool block_end = ((step + 1) % every) == 0 || step + 1 == prm->n_steps;
         if (block_start) pml_diag_kernel<<<G, T, 0, s>>>(psi, m->pml_v, m->pml_chib, m->sig64, 0.5 * prm->dz, n0);

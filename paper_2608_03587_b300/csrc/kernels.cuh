@@ -2635,11 +2635,10 @@ __global__ void rk_rhs_pml_kernel(PmlOps o, const double2 *__restrict__ y, doubl
 // Clenshaw stage on the stretched operator X~ = (A~ - c) / r,
 //   out = alpha y + beta (X~ g) - (h ? h : 0),   (A~ g)_p = sum_q a_pq (g_p - g_q),
 // with complex a_pq; g = NULL stands for a zero b.
-__global__ void pml_stage_kernel(PmlOps o, const double2 *__restrict__ y, const double2 *__restrict__ g,
-                                 const double2 *__restrict__ hh, double2 *__restrict__ out, double c, double rinv,
-                                 double2 alpha, double2 beta) {
-    const int p = blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= o.n0) return;
+__device__ __forceinline__ void pml_stage_row(const PmlOps &o, const double2 *__restrict__ y,
+                                              const double2 *__restrict__ g, const double2 *__restrict__ hh,
+                                              double2 *__restrict__ out, double c, double rinv, double2 alpha,
+                                              double2 beta, int p) {
     const double2 yp = y[p];
     double2 acc = cmul(alpha, yp);
     if (g) {
@@ -2650,17 +2649,22 @@ __global__ void pml_stage_kernel(PmlOps o, const double2 *__restrict__ y, const 
     if (hh) acc = csub(acc, hh[p]);
     out[p] = acc;
 }
+__global__ void pml_stage_kernel(PmlOps o, const double2 *__restrict__ y, const double2 *__restrict__ g,
+                                 const double2 *__restrict__ hh, double2 *__restrict__ out, double c, double rinv,
+                                 double2 alpha, double2 beta) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= o.n0) return;
+    pml_stage_row(o, y, g, hh, out, c, rinv, alpha, beta, p);
+}
 
 // Exact flow over h of dpsi/dz = i (v + chib |psi|^2) psi - sigma psi with the
 // complex lumped v and chib of the stretched metric: the intensity solves
 // dI/dz = -alpha I - beta I^2, alpha = 2 (Im v + sigma), beta = 2 Im chib:
 //   I(h) = I0 e^{-alpha h} / D,  D = 1 + beta I0 q,  q = (1 - e^{-alpha h}) / alpha,
 // and the phase is Re v h + Re chib ln(D) / beta (-> Re chib I0 q as beta I0 q -> 0).
-__global__ void pml_diag_kernel(double2 *__restrict__ psi, const double2 *__restrict__ v,
-                                const double2 *__restrict__ chib, const double *__restrict__ sigma, double h,
-                                int32_t n0) {
-    const int p = blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= n0) return;
+__device__ __forceinline__ void pml_diag_row(double2 *__restrict__ psi, const double2 *__restrict__ v,
+                                             const double2 *__restrict__ chib, const double *__restrict__ sigma,
+                                             double h, int p) {
     const double2 y = psi[p];
     const double I0 = y.x * y.x + y.y * y.y;
     const double alpha = 2.0 * (v[p].y + sigma[p]), beta = 2.0 * chib[p].y;
@@ -2673,6 +2677,55 @@ __global__ void pml_diag_kernel(double2 *__restrict__ psi, const double2 *__rest
     double sn, cs;
     sincos(theta, &sn, &cs);
     psi[p] = make_double2(amp * (y.x * cs - y.y * sn), amp * (y.x * sn + y.y * cs));
+}
+__global__ void pml_diag_kernel(double2 *__restrict__ psi, const double2 *__restrict__ v,
+                                const double2 *__restrict__ chib, const double *__restrict__ sigma, double h,
+                                int32_t n0) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n0) return;
+    pml_diag_row(psi, v, chib, sigma, h, p);
+}
+
+// The split-step march with the layer as one persistent cooperative launch
+// per step block: the same stages and diagonal flows as pml_stage_kernel /
+// pml_diag_kernel, rows strided over the grid, a bounded grid barrier after
+// each.  Stage k's coefficients, and whether its g is psi (the top stage)
+// and whether it subtracts b_{k+2}, come from a host-built table.
+struct PmlStage {
+    double2 alpha, beta;
+    int32_t g_psi, has_h;
+};
+struct PmlMarchParams {
+    PmlOps o;
+    double2 *psi, *b[3];
+    const PmlStage *st;
+    int32_t M, n_steps, pre_half, post_half;
+    double c, rinv, h;
+    unsigned long long *barrier;
+    int *status;
+    long long timeout_ns;
+};
+__global__ void __launch_bounds__(256, 6) pml_march_kernel(PmlMarchParams P) {
+    unsigned long long target = 0;
+    const int stride = int(gridDim.x * blockDim.x);
+    const int p0 = int(blockIdx.x * blockDim.x + threadIdx.x);
+    for (int step = 0; step < P.n_steps; ++step) {
+        if (step == 0 && P.pre_half) {
+            for (int p = p0; p < P.o.n0; p += stride) pml_diag_row(P.psi, P.o.v, P.o.chib, P.o.sigma, 0.5 * P.h, p);
+            if (!grid_barrier(P.barrier, target, P.status, P.timeout_ns)) return;
+        }
+        for (int k = P.M - 1; k >= 0; --k) {
+            const PmlStage sc = P.st[k];
+            const double2 *g = sc.g_psi ? P.psi : P.b[(k + 1) % 3];
+            const double2 *hh = sc.has_h ? P.b[(k + 2) % 3] : nullptr;
+            double2 *out = (k == 0) ? P.psi : P.b[k % 3];
+            for (int p = p0; p < P.o.n0; p += stride) pml_stage_row(P.o, P.psi, g, hh, out, P.c, P.rinv, sc.alpha, sc.beta, p);
+            if (!grid_barrier(P.barrier, target, P.status, P.timeout_ns)) return;
+        }
+        const double hd = (step == P.n_steps - 1 && P.post_half) ? 0.5 * P.h : P.h;
+        for (int p = p0; p < P.o.n0; p += stride) pml_diag_row(P.psi, P.o.v, P.o.chib, P.o.sigma, hd, p);
+        if (!grid_barrier(P.barrier, target, P.status, P.timeout_ns)) return;
+    }
 }
 
 struct RkCombine {

@@ -47,7 +47,9 @@ def test_split_step_with_pml_matches_oracle(amp, dz, n, every):
     spectrum, degree set by the Bernstein ellipse of its Gershgorin box, and
     the exact diagonal flow with complex lumped v and chib, against the
     oracle's Strang march on the same operators (Taylor action, no merging
-    of half steps) <= 1e-12; an outgoing beam loses power to the layer."""
+    of half steps) <= 1e-12, both as one persistent launch per step block and
+    as one launch per Chebyshev term; an outgoing beam loses power to the
+    layer."""
     coords, tris = W.mesh_disk_graded(4.0, 1500, 2.0, interfaces=(1.0,), seed=91, grade_from=1.0)
     V, chi = W.step_index_materials(coords, tris)
     ops = pml.StretchedOperators(coords, tris, V, chi, **LAYER)
@@ -61,6 +63,14 @@ def test_split_step_with_pml_matches_oracle(amp, dz, n, every):
     assert bpm.relative_error(ops, t.cpu().numpy(), ref) <= 1e-12
     P = d["power"][:, 0]
     assert np.all(np.isfinite(P)) and np.all(P <= bpm.power(ops, psi0) * (1 + 1e-12))
+    # the same march as one launch per Chebyshev term (PLAIN; also the default
+    # on meshes too large for one row per thread) instead of the persistent
+    # kernel: the same stages, rounding-level agreement
+    u = torch.from_numpy(psi0).to(DEV)
+    d2 = api.propagate(mesh, u, dz, n, diag_every=every, variant="plain")
+    assert bpm.relative_error(ops, u.cpu().numpy(), ref) <= 1e-12
+    assert bpm.relative_error(ops, u.cpu().numpy(), t.cpu().numpy()) <= 1e-13
+    assert np.allclose(d2["power"], d["power"], rtol=1e-12, atol=0)
 
 
 def test_split_step_with_pml_absorbs_an_outgoing_beam():
