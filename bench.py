@@ -45,7 +45,7 @@ UNIT = "vertex-steps/s"
 TRAFFIC_RATIO = {"march_tile_kernel": 0.9351,
                  "march_flow_kernel:chunks:skip4:rev": 0.9606, "march_flow_kernel:chunks:skip8:rev": 0.9769,
                  "march_flow_kernel:chunks:skip16:rev": 0.9893, "march_flow_kernel:ranges:skip8:rev": 0.9836}
-TRAFFIC_SRC_HASH = "e37935f336112bef"
+TRAFFIC_SRC_HASH = "e53dc444bebfa3ea"
 
 
 def kernel_source_hash() -> str:
@@ -303,6 +303,8 @@ def run_ours(args, rank, world, local_rank):
         line["single_field"] = single_field_runs(api, torch, dev, args.side_steps, peak, side)
         if "adjoint" in side:
             line["adjoint"] = adjoint_run(api, torch, dev)
+        if "pml" in side:
+            line["pml"] = pml_run(api, torch, dev)
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args, wl)
         line["cpu_baseline_all_cores"] = cpu_baseline_all_cores(wl, args.cpu_meshes, 16, n_steps=args.cpu_steps)
@@ -389,6 +391,41 @@ def single_field_runs(api, torch, dev, steps, peak, which=("disk", "vortex")):
             "fp32_vs_fp64": err, "fp64_value": n0 * steps / (res["c128"][1] * 1e-3),
             "fp64_cheb_degree": res["c128"][3]}
         mesh.close()
+    return out
+
+
+def pml_run(api, torch, dev, steps=20):
+    """The split-step march on the complex-stretched operators of a PML: a
+    200k-vertex graded step-index fiber with the layer from r = 3 to 4
+    (sigma_max 4, quadratic), 16 Hermite-Gauss superpositions, dz = 5e-4,
+    complex64 and complex128, each through decbpm_propagate (persistent march
+    or per-term launches, by the library's size rule), with the complex64
+    fields' error against complex128 (*0-weighted, max over fields)."""
+    from paper_2608_03587_b300 import workloads as W
+    coords, tris = W.mesh_disk_graded(4.0, 200000, 2.0, interfaces=(1.0,), seed=91, grade_from=1.0)
+    V, chi = W.step_index_materials(coords, tris)
+    mesh = api.Mesh(coords, tris, V, chi)
+    api.set_pml(mesh, r_inner=3.0, r_outer=4.0, sigma_max=4.0, order=2)
+    B, dz = 16, 5e-4
+    psi0 = np.ascontiguousarray(W.hg_superpositions(coords, B, np.random.default_rng(91), power=4.0))
+    n0 = coords.shape[0]
+    out = {"vertices": int(n0), "fields": B, "steps": steps, "dz": dz}
+    res = {}
+    for prec, dt in (("c64", torch.complex64), ("c128", torch.complex128)):
+        psi = torch.from_numpy(psi0).to(dev, dt).contiguous()
+        api.propagate(mesh, psi.clone(), dz, 2)                          # warm-up
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        api.propagate(mesh, psi, dz, steps)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        res[prec] = psi
+        out[prec] = {"value": n0 * B * steps / (ms * 1e-3), "unit": UNIT, "ms": ms}
+    out["fp32_vs_fp64"] = float(np.max(star0_rel_error(api, mesh, res["c64"], res["c128"])))
+    out["fp32_speedup"] = out["c64"]["value"] / out["c128"]["value"]
+    mesh.close()
     return out
 
 
@@ -591,8 +628,8 @@ def main():
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-side", action="store_true", help="skip the single-field and adjoint side runs")
     ap.add_argument("--side-steps", type=int, default=200, help="steps of the single-field side runs")
-    ap.add_argument("--side-workloads", default="disk,vortex,adjoint",
-                    help="side runs to make: any of disk (200k single field), vortex (1M), adjoint (300k PCF)")
+    ap.add_argument("--side-workloads", default="disk,vortex,adjoint,pml",
+                    help="side runs to make: any of disk (200k single field), vortex (1M), adjoint (300k PCF), pml (200k fiber with a PML, 16 fields)")
     ap.add_argument("--variant", choices=["fused", "rows", "pairs", "flow"], default="fused",
                     help="fused: the autotuner's choice; pairs: the stage-pair kernel; rows: the row kernel")
     args = ap.parse_args()

@@ -223,8 +223,11 @@ int decbpm_bessel_coefficients(double a, double tol, int32_t max_terms, double *
  *   n_diag = n_steps / diag_every (+1 if n_steps % diag_every != 0), or 1 if diag_every == 0.
  * Workspaces (internal-order field copy, three Clenshaw buffers, barrier
  * words) are allocated on first use and cached in the handle.
+ * On a mesh with a PML (decbpm_mesh_set_pml) the march runs on the
+ * stretched operators, complex64 or complex128, lumped Kerr, p_1 only.
  * Errors: INVALID_ARG, NONFINITE (field became non-finite), TIMEOUT, CUDA, OOM,
- * UNSUPPORTED (n_fields > 64, or the PLAIN variant with C64).               */
+ * UNSUPPORTED (n_fields > 64, the PLAIN variant with C64 or several fields
+ * on a mesh without a layer, element Kerr or p_2.. with a layer).          */
 int decbpm_propagate(decbpm_mesh_t mesh, const decbpm_params *params, void *psi_dev, int64_t n_fields,
                      void *stream, decbpm_diag *diag_out);
 
@@ -444,19 +447,23 @@ int decbpm_bessel_i_scaled(double a, double tol, int32_t n_max, double *out, int
  * inner product of *1 (Eq. 9) takes the tensor (r~/(s r)) e_r e_r^T +
  * (s r/r~) e_t e_t^T, s = 1 + i sigma, and *0 the factor s r~ / r; v and chib
  * keep their lumped definitions with the stretched *0.  FP64, assembled on the
- * host.  Once set, the mesh runs with decbpm_rk45 (lumped Kerr) and with
- * decbpm_propagate for one complex128 field, lumped Kerr and p_1 only: the
- * Strang split-step on the stretched operators, E_h by the Chebyshev series
- * of exp(-i a x) evaluated on the complex spectrum (degree from the Bernstein
- * ellipse of the Gershgorin box of A~), D_h the exact flow with the complex
- * v and chib (their imaginary parts damp the intensity by a Bernoulli
- * equation); FP64, one persistent launch per step block where one thread per
- * row fits the grid (up to about 220k vertices on 148 SMs), else one launch
- * per Chebyshev term (params->variant = DECBPM_VARIANT_PLAIN forces the
- * latter).  Every other split-step entry point
- * (plans, batches, complex64, the adjoint, the soliton solver, the
- * allocation-free call) returns DECBPM_ERR_UNSUPPORTED.  pml = NULL or
- * sigma_max = 0 removes the layer.  2D meshes only. */
+ * host (the split-step's weights a_pq / r are also kept in FP32, with FP32
+ * copies of v and chib).  Once set, the mesh runs with decbpm_rk45 (lumped
+ * Kerr) and with decbpm_propagate for any number of fields (1..64, layout
+ * as without a layer), complex64 or complex128, lumped Kerr and p_1 only:
+ * the Strang split-step on the stretched operators, E_h by the Chebyshev
+ * series of exp(-i a x) evaluated on the complex spectrum (degree from the
+ * Bernstein ellipse of the Gershgorin box of A~), D_h the exact flow with
+ * the complex v and chib (their imaginary parts damp the intensity by a
+ * Bernoulli equation).  One persistent launch per step block where one
+ * thread per (vertex, field) element fits the grid (up to about 220k
+ * elements on 148 SMs), else one launch per Chebyshev term and per flow
+ * (params->variant = DECBPM_VARIANT_PLAIN forces the latter); complex64
+ * rounds the last stage of each step once (double-float FP32 sums).
+ * Every other split-step entry point (plans, batches over meshes, the
+ * host-buffer call, the adjoint, the soliton solver, the allocation-free
+ * call) returns DECBPM_ERR_UNSUPPORTED.  pml = NULL or sigma_max = 0
+ * removes the layer.  2D meshes only. */
 typedef struct { double x0, y0, r_inner, r_outer, sigma_max; int32_t order; } decbpm_pml;
 int decbpm_mesh_set_pml(decbpm_mesh_t mesh, const decbpm_pml *pml);
 

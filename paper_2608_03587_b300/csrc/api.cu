@@ -118,6 +118,10 @@ struct decbpm_mesh_s {
     double2 *pml_a = nullptr, *pml_v = nullptr, *pml_chib = nullptr;
     // Gershgorin region of A~ (the union of the discs |z - sum_q a_pq| <= sum_q |a_pq|) as a box
     double pml_re_lo = 0, pml_re_hi = 0, pml_im_lo = 0, pml_im_hi = 0;
+    // the split-step's scaled weights x_pq = a_pq / r (r, c: half width and
+    // centre of the box's real extent) in both precisions, and v, chib in FP32
+    double2 *pml_x64 = nullptr;
+    float2 *pml_x32 = nullptr, *pml_v32 = nullptr, *pml_chib32 = nullptr;
     // tile maps of the tile-staged march (built on first use): 128-row tiles
     // of 16 fields (t16) and 512-row tiles of one field (t1)
     TileMaps t16, t1;
@@ -499,8 +503,8 @@ struct decbpm_plan_s {
     int32_t *cta_tiles = nullptr, *cta_ptr = nullptr, *cta_cnt = nullptr, *active_meshes = nullptr;
     int cta_cnt_cap = 0, active_meshes_cap = 0;
     int tune_flow = 0;                           // 1: FUSED runs the dataflow kernel
-    PmlStage *pml_st = nullptr;                  // stage table of the fused PML march
-    int pml_st_cap = 0;
+    char *pml_st = nullptr;                      // stage table of the fused PML march
+    size_t pml_st_bytes = 0;
     int tune_meta = 1;                           // row kernel, single-mesh plans: cache the item metadata
     // the last metadata-cache decision (row_meta_cache), so launches recorded
     // into a graph make no attribute or occupancy call
@@ -2162,32 +2166,56 @@ static int set_pml_impl(decbpm_mesh_t M, const decbpm_pml *o) {
         im_hi = std::max(im_hi, z.imag() + rad);
     }
     M->pml_re_lo = re_lo; M->pml_re_hi = re_hi; M->pml_im_lo = im_lo; M->pml_im_hi = im_hi;
+    const double rr = 0.5 * (re_hi - re_lo);
+    const double rinv = rr > 0 ? 1.0 / rr : 0.0;       // an empty box is refused by the split-step
+    std::vector<double2> x64(a_sell.size());
+    std::vector<float2> x32(a_sell.size()), v32(n0), c32(n0);
+    for (size_t i = 0; i < a_sell.size(); ++i) {
+        x64[i] = make_double2(a_sell[i].x * rinv, a_sell[i].y * rinv);
+        x32[i] = make_float2(float(x64[i].x), float(x64[i].y));
+    }
+    for (int64_t i = 0; i < n0; ++i) {
+        v32[i] = make_float2(float(vv[i].x), float(vv[i].y));
+        c32[i] = make_float2(float(cc[i].x), float(cc[i].y));
+    }
     if (!M->pml_a) {
         TRY(M->mem.alloc(&M->pml_a, a_sell.size()));
         TRY(M->mem.alloc(&M->pml_v, size_t(n0)));
         TRY(M->mem.alloc(&M->pml_chib, size_t(n0)));
+        TRY(M->mem.alloc(&M->pml_x64, a_sell.size()));
+        TRY(M->mem.alloc(&M->pml_x32, a_sell.size()));
+        TRY(M->mem.alloc(&M->pml_v32, size_t(n0)));
+        TRY(M->mem.alloc(&M->pml_chib32, size_t(n0)));
     }
     CK(cudaMemcpy(M->pml_a, a_sell.data(), sizeof(double2) * a_sell.size(), cudaMemcpyHostToDevice));
     CK(cudaMemcpy(M->pml_v, vv.data(), sizeof(double2) * n0, cudaMemcpyHostToDevice));
     CK(cudaMemcpy(M->pml_chib, cc.data(), sizeof(double2) * n0, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(M->pml_x64, x64.data(), sizeof(double2) * x64.size(), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(M->pml_x32, x32.data(), sizeof(float2) * x32.size(), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(M->pml_v32, v32.data(), sizeof(float2) * n0, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(M->pml_chib32, c32.data(), sizeof(float2) * n0, cudaMemcpyHostToDevice));
     M->pml_on = true;
     return DECBPM_OK;
 }
 
 // ============================================================== split-step with a PML
-// The Strang march on the complex-stretched operators (one complex128 field,
-// lumped Kerr, p_1 only), unfused: one stage launch per Chebyshev term and a
-// launch per diagonal flow.  E_h = exp(-i h p1 A~) is the Chebyshev series of
-// exp(-i a x), a = h p1 r, in x = (lambda - c) / r over the real extent
-// [c - r, c + r] of the Gershgorin region of A~; the series of this entire
-// function converges on the complex spectrum too, and its degree is the
-// smallest M whose tail sum_{k>M} 2 |J_k(a)| rho_e^k is below tol, rho_e the
-// largest Bernstein-ellipse parameter of the region's box (so the truncation
-// holds on every eigenvalue the box contains).
-static int propagate_plain_pml(decbpm_mesh_t m, const decbpm_params *prm, void *psi_dev, cudaStream_t s,
-                               decbpm_diag *diag_out) {
+// The Strang march on the complex-stretched operators (one mesh, any number
+// of fields, complex64 or complex128, lumped Kerr, p_1 only).
+// E_h = exp(-i h p1 A~) is the Chebyshev series of exp(-i a x), a = h p1 r,
+// in x = (lambda - c) / r over the real extent [c - r, c + r] of the
+// Gershgorin region of A~; the series of this entire function converges on
+// the complex spectrum too, and its degree is the smallest M whose tail
+// sum_{k>M} 2 |J_k(a)| rho_e^k is below tol, rho_e the largest
+// Bernstein-ellipse parameter of the region's box (so the truncation holds on
+// every eigenvalue the box contains).  The stages run as one persistent
+// launch per step block (pml_march_kernel) where one thread per (vertex,
+// field) element fits the grid, else one launch per Chebyshev term and per
+// diagonal flow.
+template <typename R>
+static int propagate_pml(decbpm_mesh_t m, const decbpm_params *prm, void *psi_dev, int64_t n_fields, cudaStream_t s,
+                         decbpm_diag *diag_out) {
     using cd = std::complex<double>;
-    if (prm->precision != DECBPM_C128) return fail(DECBPM_ERR_UNSUPPORTED, "with a PML the split-step runs complex128");
+    using C = typename CT<R>::c2;
     if (prm->kerr_mode != DECBPM_KERR_LUMPED) return fail(DECBPM_ERR_UNSUPPORTED, "with a PML the split-step takes lumped Kerr");
     if (m->A.p.size() != 1) return fail(DECBPM_ERR_UNSUPPORTED, "with a PML the split-step takes p_1 only");
     const int n0 = int(m->A.n0);
@@ -2229,62 +2257,90 @@ static int propagate_plain_pml(decbpm_mesh_t m, const decbpm_params *prm, void *
         coef[k] = std::pow(cd(0.0, -1.0), k) * jk;
     }
     const double theta0 = -prm->dz * p1 * c;        // exp(-i h p1 lambda) = e^{i theta0} sum_k coef_k T_k(x)
+    const R cs = R(c / r);
+    // Stage table: b_k = a_k psi + 2 X~ b_{k+1} - b_{k+2}, the top two stages
+    // folded (as in the march without a layer).  A constant field is mapped
+    // exactly to -c' by the kernel's X~, so the lambda = 0 mode sees the
+    // recurrence at x = -c' with the stored (rounded) coefficients: its FP64
+    // value is set against the exact e^{-i theta0} through alpha_lo on the
+    // last stage, leaving the smooth part of the field no systematic per-step
+    // gain or phase error from coefficient rounding.
+    auto mk = [](cd z) { C w; w.x = R(z.real()); w.y = R(z.imag()); return w; };   // host code: no cmk
+    auto up = [](C z) { return cd(double(z.x), double(z.y)); };
+    std::vector<PmlStage<R>> st(M);
+    for (int k = M - 1; k >= 0; --k) {
+        cd alpha = coef[k], beta = (k == 0) ? 1.0 : 2.0;
+        int g_psi = 0, has_h = 1;
+        if (k == M - 1) { g_psi = 1; beta = 2.0 * coef[M]; has_h = 0; }
+        else if (k == M - 2) { alpha = coef[k] - coef[M]; has_h = 0; }
+        st[k] = PmlStage<R>{mk(alpha), mk(beta), mk(0.0), g_psi, has_h, k == 0 ? 1 : 0};
+    }
+    {
+        cd bk1 = 0, bk2 = 0, Sv = 0;
+        const double x0 = -double(cs);
+        for (int k = M - 1; k >= 0; --k) {
+            const cd g = st[k].g_psi ? 1.0 : bk1;
+            cd o = up(st[k].alpha) + up(st[k].beta) * (x0 * g);
+            if (st[k].has_h) o -= bk2;
+            if (k == 0) Sv = o;
+            bk2 = bk1;
+            bk1 = o;
+        }
+        st[0].alpha_lo = mk(std::exp(cd(0.0, -theta0)) - Sv);
+    }
     decbpm_plan_t P = nullptr;
-    TRY(single_plan(m, 1, DECBPM_C128, &P));
-    if (P->order.empty()) TRY(plan_configure<double>(P, prm->dz, default_tol(prm)));   // buffers and the device view
-    MeshView<double> mv{};
-    CK(cudaMemcpy(&mv, P->views, sizeof(mv), cudaMemcpyDeviceToHost));
-    const PmlOps po{mv.slice_ptr, mv.slice_w, mv.col, m->pml_a, m->pml_v, m->pml_chib, m->sig64, n0};
-    double2 *psi = (double2 *)P->psi[0];
-    double2 *b[3] = {(double2 *)P->b0[0], (double2 *)P->b1[0], (double2 *)P->b2[0]};
+    TRY(single_plan(m, n_fields, prm->precision, &P));
+    if (P->order.empty()) TRY(plan_configure<R>(P, prm->dz, default_tol(prm)));   // buffers and the device view
+    PmlStepOps<R> po{};
+    po.slice_ptr = m->slice_ptr; po.slice_w = m->slice_w; po.col = m->col;
+    if constexpr (sizeof(R) == 4) {
+        po.x = m->pml_x32; po.v = m->pml_v32; po.chib = m->pml_chib32; po.sigma = m->sig32;
+    } else {
+        po.x = m->pml_x64; po.v = m->pml_v; po.chib = m->pml_chib; po.sigma = m->sig64;
+    }
+    po.status = P->status;
+    po.cs = cs;
+    po.n0 = n0;
+    po.bpad_log2 = P->bpad_log2;
+    C *psi = (C *)P->psi[0];
+    C *b[3] = {(C *)P->b0[0], (C *)P->b1[0], (C *)P->b2[0]};
     const int n_points = n_diag_points(prm);
     TRY(ensure_diag_host(P, n_points));
-    const int T = 256, G = (n0 + T - 1) / T;
-    permute_in_kernel<double2><<<std::min(G, 4 * P->num_sms), T, 0, s>>>((const double2 *)psi_dev, psi, m->perm, n0, 1, 1);
+    const int64_t n_elem = int64_t(n0) << P->bpad_log2;
+    if (n_elem > 0x7fffffff) return fail(DECBPM_ERR_UNSUPPORTED, "mesh x fields too large for the PML march");
+    const int T = 256, G = int((n_elem + T - 1) / T);
+    permute_in_kernel<C><<<std::min(G, 4 * P->num_sms), T, 0, s>>>((const C *)psi_dev, psi, m->perm, n0,
+                                                                   int32_t(n_fields), P->bpad);
     const int64_t every = prm->diag_every > 0 ? prm->diag_every : std::max<int64_t>(prm->n_steps, 1);
     int point = 0;
-    auto d2 = [](cd z) { return make_double2(z.real(), z.imag()); };
+    CK(cudaMemsetAsync(P->status, 0, sizeof(int), s));
     CK(cudaEventRecord(P->ev0, s));
-    // One persistent launch per step block (pml_march_kernel) where the grid
-    // covers every row with one thread (compiled for 6 CTAs of 256 per SM):
-    // it saves the per-term launches of small meshes; larger meshes would
-    // give a thread two rows per stage, and run one launch per term instead.
     int pml_occ = 0;
-    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&pml_occ, (const void *)pml_march_kernel, 256, 0));
+    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&pml_occ, (const void *)pml_march_kernel<R>, 256, 0));
     const bool pml_fused = prm->variant != DECBPM_VARIANT_PLAIN && prm->n_steps > 0 && pml_occ >= 1 &&
-                           int64_t(P->num_sms) * std::min(pml_occ, 6) * 256 >= n0;
+                           int64_t(P->num_sms) * std::min(pml_occ, 6) * 256 >= n_elem;
     if (pml_fused) {
         // the stage table in the plan's PML workspace
-        std::vector<PmlStage> st(M);
-        for (int k = M - 1; k >= 0; --k) {
-            cd alpha = coef[k], beta = (k == 0) ? 1.0 : 2.0;
-            int g_psi = 0, has_h = 1;
-            if (k == M - 1) { g_psi = 1; beta = 2.0 * coef[M]; has_h = 0; }
-            else if (k == M - 2) { alpha = coef[k] - coef[M]; has_h = 0; }
-            st[k] = PmlStage{d2(alpha), d2(beta), g_psi, has_h};
+        const size_t st_bytes = sizeof(PmlStage<R>) * size_t(M);
+        if (st_bytes > P->pml_st_bytes) {
+            TRY(P->mem.alloc(&P->pml_st, st_bytes));
+            P->pml_st_bytes = st_bytes;
         }
-        if (M > P->pml_st_cap) {
-            TRY(P->mem.alloc(&P->pml_st, size_t(M)));
-            P->pml_st_cap = M;
-        }
-        CK(cudaMemcpyAsync(P->pml_st, st.data(), sizeof(PmlStage) * M, cudaMemcpyHostToDevice, s));
+        CK(cudaMemcpyAsync(P->pml_st, st.data(), st_bytes, cudaMemcpyHostToDevice, s));
         const int grid = std::min(P->num_sms * std::min(pml_occ, 6), std::max(1, G));
-        CK(cudaMemsetAsync(P->status, 0, sizeof(int), s));
         for (int64_t done = 0; done < prm->n_steps;) {
             const int64_t nb = std::min<int64_t>(every, prm->n_steps - done);
             if (nb > 0x7fffffff) return fail(DECBPM_ERR_INVALID_ARG, "step block too long");
-            PmlMarchParams mp{};
+            PmlMarchParams<R> mp{};
             mp.o = po;
             mp.psi = psi;
             mp.b[0] = b[0]; mp.b[1] = b[1]; mp.b[2] = b[2];
-            mp.st = P->pml_st;
+            mp.st = reinterpret_cast<const PmlStage<R> *>(P->pml_st);
             mp.M = M;
             mp.n_steps = int32_t(nb);
             mp.pre_half = 1;
             mp.post_half = 1;
-            mp.c = c;
-            mp.rinv = 1.0 / r;
-            mp.h = prm->dz;
+            mp.h = R(prm->dz);
             mp.barrier = P->barrier;
             mp.status = P->status;
             mp.timeout_ns = kBarrierTimeoutNs;
@@ -2299,44 +2355,42 @@ static int propagate_plain_pml(decbpm_mesh_t m, const decbpm_params *prm, void *
             cfg.attrs = attr;
             cfg.numAttrs = 1;
             void *args[] = {&mp};
-            CK(cudaLaunchKernelExC(&cfg, (const void *)pml_march_kernel, args));
+            CK(cudaLaunchKernelExC(&cfg, (const void *)pml_march_kernel<R>, args));
             done += nb;
             if (done >= prm->n_steps) CK(cudaEventRecord(P->ev1, s));
-            TRY(launch_diag<double>(P, s, DECBPM_KERR_LUMPED, point++));
+            TRY(launch_diag<R>(P, s, DECBPM_KERR_LUMPED, point++));
         }
-        int status = 0;
-        CK(cudaMemcpyAsync(&status, P->status, sizeof(int), cudaMemcpyDeviceToHost, s));
-        CK(cudaStreamSynchronize(s));
-        if (status == DECBPM_ERR_TIMEOUT) return fail(DECBPM_ERR_TIMEOUT, "grid barrier timed out in the PML march");
-        if (status != 0) return fail(status, "device reported status %d", status);
     }
+    const R h = R(prm->dz), hh2 = R(0.5 * prm->dz);
     for (int64_t step = 0; step < prm->n_steps && !pml_fused; ++step) {
         const bool block_start = (step % every) == 0;
         const bool block_end = ((step + 1) % every) == 0 || step + 1 == prm->n_steps;
-        if (block_start) pml_diag_kernel<<<G, T, 0, s>>>(psi, m->pml_v, m->pml_chib, m->sig64, 0.5 * prm->dz, n0);
+        if (block_start) pml_diag_kernel<R><<<G, T, 0, s>>>(po, psi, hh2);
         for (int k = M - 1; k >= 0; --k) {
-            cd alpha = coef[k], beta = (k == 0) ? 1.0 : 2.0;
-            const double2 *g = b[(k + 1) % 3], *hh = b[(k + 2) % 3];
-            if (k == M - 1) { g = psi; beta = 2.0 * coef[M]; hh = nullptr; }
-            else if (k == M - 2) { alpha = coef[k] - coef[M]; hh = nullptr; }
-            double2 *outp = (k == 0) ? psi : b[k % 3];
-            pml_stage_kernel<<<G, T, 0, s>>>(po, psi, g, hh, outp, c, 1.0 / r, d2(alpha), d2(beta));
+            const C *g = st[k].g_psi ? psi : b[(k + 1) % 3];
+            const C *hv = st[k].has_h ? b[(k + 2) % 3] : nullptr;
+            C *outp = (k == 0) ? psi : b[k % 3];
+            pml_stage_kernel<R><<<G, T, 0, s>>>(po, psi, g, hv, outp, st[k]);
         }
-        pml_diag_kernel<<<G, T, 0, s>>>(psi, m->pml_v, m->pml_chib, m->sig64, block_end ? 0.5 * prm->dz : prm->dz, n0);
+        pml_diag_kernel<R><<<G, T, 0, s>>>(po, psi, block_end ? hh2 : h);
         if (block_end) {
             if (step + 1 == prm->n_steps) CK(cudaEventRecord(P->ev1, s));
-            TRY(launch_diag<double>(P, s, DECBPM_KERR_LUMPED, point++));
+            TRY(launch_diag<R>(P, s, DECBPM_KERR_LUMPED, point++));
         }
     }
     if (prm->n_steps == 0) {
         CK(cudaEventRecord(P->ev1, s));
-        TRY(launch_diag<double>(P, s, DECBPM_KERR_LUMPED, point++));
+        TRY(launch_diag<R>(P, s, DECBPM_KERR_LUMPED, point++));
     }
     const double ph = std::fmod(double(prm->n_steps) * theta0, 2.0 * M_PI);
-    permute_out_kernel<double2><<<std::min(G, 4 * P->num_sms), T, 0, s>>>(psi, (double2 *)psi_dev, m->perm, n0, 1, 1,
-                                                                         std::cos(ph), std::sin(ph));
+    permute_out_kernel<C><<<std::min(G, 4 * P->num_sms), T, 0, s>>>(psi, (C *)psi_dev, m->perm, n0, int32_t(n_fields),
+                                                                    P->bpad, std::cos(ph), std::sin(ph));
     CK(cudaGetLastError());
+    int status = 0;
+    CK(cudaMemcpyAsync(&status, P->status, sizeof(int), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
+    if (status == DECBPM_ERR_TIMEOUT) return fail(DECBPM_ERR_TIMEOUT, "grid barrier timed out in the PML march");
+    if (status != 0) return fail(status, "device reported status %d", status);
     return finish_diag(P, prm, n_points, diag_out);
 }
 
@@ -2493,8 +2547,10 @@ int decbpm_propagate(decbpm_mesh_t mesh, const decbpm_params *params, void *psi_
     if (!mesh || !psi_dev) return fail(DECBPM_ERR_INVALID_ARG, "mesh and psi_dev are required");
     TRY(check_params(params));
     if (mesh->pml_on) {
-        if (n_fields != 1) return fail(DECBPM_ERR_UNSUPPORTED, "with a PML the split-step runs one field");
-        return propagate_plain_pml(mesh, params, psi_dev, (cudaStream_t)stream, diag_out);
+        if (n_fields < 1) return fail(DECBPM_ERR_INVALID_ARG, "n_fields must be >= 1");
+        return params->precision == DECBPM_C64
+                   ? propagate_pml<float>(mesh, params, psi_dev, n_fields, (cudaStream_t)stream, diag_out)
+                   : propagate_pml<double>(mesh, params, psi_dev, n_fields, (cudaStream_t)stream, diag_out);
     }
     if (params->variant == DECBPM_VARIANT_PLAIN) {
         if (n_fields != 1) return fail(DECBPM_ERR_UNSUPPORTED, "the plain variant runs one field");

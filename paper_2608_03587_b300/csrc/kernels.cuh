@@ -2631,99 +2631,168 @@ __global__ void rk_rhs_pml_kernel(PmlOps o, const double2 *__restrict__ y, doubl
     k[p] = make_double2(gi - sg * yp.x, -gr - sg * yp.y);  // -i (g) - sigma y
 }
 
-// Split-step march with the layer (FP64, one field, internal order): one
-// Clenshaw stage on the stretched operator X~ = (A~ - c) / r,
-//   out = alpha y + beta (X~ g) - (h ? h : 0),   (A~ g)_p = sum_q a_pq (g_p - g_q),
-// with complex a_pq; g = NULL stands for a zero b.
-__device__ __forceinline__ void pml_stage_row(const PmlOps &o, const double2 *__restrict__ y,
-                                              const double2 *__restrict__ g, const double2 *__restrict__ hh,
-                                              double2 *__restrict__ out, double c, double rinv, double2 alpha,
-                                              double2 beta, int p) {
-    const double2 yp = y[p];
-    double2 acc = cmul(alpha, yp);
-    if (g) {
-        const double2 ag = pml_a_row(o, g, p), gp = g[p];
-        const double2 xg = make_double2((ag.x - c * gp.x) * rinv, (ag.y - c * gp.y) * rinv);
-        acc = cadd(acc, cmul(beta, xg));
+// Split-step march with the layer: one Clenshaw stage on the stretched
+// operator X~ = (A~ - c) / r in the scaled form
+//   (X~ g)_p = sum_q x_pq (g_p - g_q) - c' g_p,   x_pq = a_pq / r,  c' = c / r,
+// with complex x_pq, for every field of the padded layout [vertex][bpad]
+// (element i = p bpad + f): out = alpha y + beta (X~ g) - (has_h ? h : 0),
+// plus alpha_lo y on the last stage.  The neighbour sum is formed first and
+// c' g_p subtracted once, so a smooth field's small Laplacian is not summed
+// at the rounding scale of r |g|; a constant field gets X~ 1 = -c' exactly.
+template <typename R> struct PmlStepOps {
+    const int32_t *slice_ptr, *slice_w, *col;
+    const typename CT<R>::c2 *x, *v, *chib;
+    const R *sigma;
+    int *status;                // the bounds-check build's report of a bad column
+    R cs;                       // c' = c / r
+    int32_t n0, bpad_log2;
+};
+template <typename R> struct PmlStage {
+    typename CT<R>::c2 alpha, beta, alpha_lo;
+    int32_t g_psi, has_h, final_stage;
+};
+__device__ __forceinline__ float log1p_r(float x) { return log1pf(x); }
+__device__ __forceinline__ double log1p_r(double x) { return log1p(x); }
+__device__ __forceinline__ float sqrt_r(float x) { return sqrtf(x); }
+__device__ __forceinline__ double sqrt_r(double x) { return sqrt(x); }
+
+// sum_q x_pq (g_p - g_q) over row p's SELL entries, field f
+template <typename R>
+__device__ __forceinline__ typename CT<R>::c2 pml_x_sum(const PmlStepOps<R> &o, const typename CT<R>::c2 *__restrict__ g,
+                                                        typename CT<R>::c2 gp, int p, int f) {
+    const int s = p >> 5, base = o.slice_ptr[s] + (p & 31), w = o.slice_w[s];
+    R sr = 0, si = 0;
+    for (int j = 0; j < w; ++j) {
+        const typename CT<R>::c2 a = o.x[base + 32 * j];
+        const int q = DECBPM_IDX(o.col[base + 32 * j], o.n0, o.status);
+        const typename CT<R>::c2 gq = g[((size_t)q << o.bpad_log2) + f];
+        const R dr = gp.x - gq.x, di = gp.y - gq.y;
+        sr = fma(a.x, dr, fma(-a.y, di, sr));
+        si = fma(a.x, di, fma(a.y, dr, si));
     }
-    if (hh) acc = csub(acc, hh[p]);
-    out[p] = acc;
+    return cmk<typename CT<R>::c2>(sr, si);
 }
-__global__ void pml_stage_kernel(PmlOps o, const double2 *__restrict__ y, const double2 *__restrict__ g,
-                                 const double2 *__restrict__ hh, double2 *__restrict__ out, double c, double rinv,
-                                 double2 alpha, double2 beta) {
-    const int p = blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= o.n0) return;
-    pml_stage_row(o, y, g, hh, out, c, rinv, alpha, beta, p);
+
+// The last stage in complex64: S = alpha y + alpha_lo y + beta (sum - c' g_p) - h
+// in double-float FP32 arithmetic (error-free products by FMA, TwoSum
+// accumulation) and rounded once, so that its roundings do not act as a
+// per-step gain on a stationary field.
+__device__ __forceinline__ float2 pml_final_combine(const PmlStage<float> &st, float2 y, float2 sum, float cs,
+                                                    float2 gp, float2 hh, bool has_h) {
+    DF dr{0.f, 0.f}, di{0.f, 0.f};
+    df_add(dr, sum.x, 0.f); df_prod(dr, -cs, gp.x);
+    df_add(di, sum.y, 0.f); df_prod(di, -cs, gp.y);
+    DF re{0.f, 0.f}, im{0.f, 0.f};
+    df_prod(re, st.alpha.x, y.x);    df_prod(re, -st.alpha.y, y.y);
+    df_prod(im, st.alpha.x, y.y);    df_prod(im, st.alpha.y, y.x);
+    df_prod(re, st.alpha_lo.x, y.x); df_prod(re, -st.alpha_lo.y, y.y);
+    df_prod(im, st.alpha_lo.x, y.y); df_prod(im, st.alpha_lo.y, y.x);
+    df_prod(re, st.beta.x, dr.hi);   df_prod(re, -st.beta.y, di.hi);
+    df_prod(im, st.beta.x, di.hi);   df_prod(im, st.beta.y, dr.hi);
+    df_prod(re, st.beta.x, dr.lo);   df_prod(re, -st.beta.y, di.lo);
+    df_prod(im, st.beta.x, di.lo);   df_prod(im, st.beta.y, dr.lo);
+    if (has_h) { df_add(re, -hh.x, 0.f); df_add(im, -hh.y, 0.f); }
+    return make_float2(__fadd_rn(re.hi, re.lo), __fadd_rn(im.hi, im.lo));
+}
+
+template <typename R>
+__device__ __forceinline__ void pml_stage_row(const PmlStepOps<R> &o, const typename CT<R>::c2 *__restrict__ y,
+                                              const typename CT<R>::c2 *__restrict__ g,
+                                              const typename CT<R>::c2 *__restrict__ hh,
+                                              typename CT<R>::c2 *__restrict__ out, const PmlStage<R> &st, int i) {
+    using C = typename CT<R>::c2;
+    const int p = i >> o.bpad_log2, f = i & ((1 << o.bpad_log2) - 1);
+    const C yp = y[i], gp = g[i];
+    const C sum = pml_x_sum(o, g, gp, p, f);
+    const C hv = hh ? hh[i] : cmk<C>(R(0), R(0));
+    if constexpr (sizeof(R) == 4) {
+        if (st.final_stage) {
+            out[i] = pml_final_combine(st, yp, sum, o.cs, gp, hv, hh != nullptr);
+            return;
+        }
+    }
+    const C xg = cmk<C>(sum.x - o.cs * gp.x, sum.y - o.cs * gp.y);
+    C acc = cmul(st.alpha, yp);
+    if (st.final_stage) acc = cadd(acc, cmul(st.alpha_lo, yp));
+    acc = cadd(acc, cmul(st.beta, xg));
+    if (hh) acc = csub(acc, hv);
+    out[i] = acc;
+}
+template <typename R>
+__global__ void pml_stage_kernel(PmlStepOps<R> o, const typename CT<R>::c2 *__restrict__ y,
+                                 const typename CT<R>::c2 *__restrict__ g, const typename CT<R>::c2 *__restrict__ hh,
+                                 typename CT<R>::c2 *__restrict__ out, PmlStage<R> st) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (o.n0 << o.bpad_log2)) return;
+    pml_stage_row(o, y, g, hh, out, st, i);
 }
 
 // Exact flow over h of dpsi/dz = i (v + chib |psi|^2) psi - sigma psi with the
-// complex lumped v and chib of the stretched metric: the intensity solves
-// dI/dz = -alpha I - beta I^2, alpha = 2 (Im v + sigma), beta = 2 Im chib:
+// complex lumped v and chib of the stretched metric, for element i = p bpad + f:
+// the intensity solves dI/dz = -alpha I - beta I^2, alpha = 2 (Im v + sigma),
+// beta = 2 Im chib:
 //   I(h) = I0 e^{-alpha h} / D,  D = 1 + beta I0 q,  q = (1 - e^{-alpha h}) / alpha,
 // and the phase is Re v h + Re chib ln(D) / beta (-> Re chib I0 q as beta I0 q -> 0).
-__device__ __forceinline__ void pml_diag_row(double2 *__restrict__ psi, const double2 *__restrict__ v,
-                                             const double2 *__restrict__ chib, const double *__restrict__ sigma,
-                                             double h, int p) {
-    const double2 y = psi[p];
-    const double I0 = y.x * y.x + y.y * y.y;
-    const double alpha = 2.0 * (v[p].y + sigma[p]), beta = 2.0 * chib[p].y;
-    const double ah = alpha * h;
-    const double q = ah != 0.0 ? -expm1(-ah) / alpha : h;
-    const double x = beta * I0 * q;
-    const double ratio = x != 0.0 ? log1p(x) / x : 1.0;
-    const double theta = v[p].x * h + chib[p].x * I0 * q * ratio;
-    const double amp = sqrt(exp(-ah) / (1.0 + x));
-    double sn, cs;
-    sincos(theta, &sn, &cs);
-    psi[p] = make_double2(amp * (y.x * cs - y.y * sn), amp * (y.x * sn + y.y * cs));
+template <typename R>
+__device__ __forceinline__ void pml_diag_row(const PmlStepOps<R> &o, typename CT<R>::c2 *__restrict__ psi, R h, int i) {
+    const int p = i >> o.bpad_log2;
+    const typename CT<R>::c2 y = psi[i], v = o.v[p], cb = o.chib[p];
+    const R I0 = y.x * y.x + y.y * y.y;
+    const R alpha = R(2) * (v.y + o.sigma[p]), beta = R(2) * cb.y;
+    const R ah = alpha * h;
+    const R q = ah != R(0) ? -expm1_r(-ah) / alpha : h;
+    const R x = beta * I0 * q;
+    const R ratio = x != R(0) ? log1p_r(x) / x : R(1);
+    const R theta = v.x * h + cb.x * I0 * q * ratio;
+    const R amp = sqrt_r(exp_r(-ah) / (R(1) + x));
+    R sn, cs;
+    sincos_r(theta, &sn, &cs);
+    psi[i] = cmk<typename CT<R>::c2>(amp * (y.x * cs - y.y * sn), amp * (y.x * sn + y.y * cs));
 }
-__global__ void pml_diag_kernel(double2 *__restrict__ psi, const double2 *__restrict__ v,
-                                const double2 *__restrict__ chib, const double *__restrict__ sigma, double h,
-                                int32_t n0) {
-    const int p = blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= n0) return;
-    pml_diag_row(psi, v, chib, sigma, h, p);
+template <typename R>
+__global__ void pml_diag_kernel(PmlStepOps<R> o, typename CT<R>::c2 *__restrict__ psi, R h) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (o.n0 << o.bpad_log2)) return;
+    pml_diag_row(o, psi, h, i);
 }
 
 // The split-step march with the layer as one persistent cooperative launch
 // per step block: the same stages and diagonal flows as pml_stage_kernel /
-// pml_diag_kernel, rows strided over the grid, a bounded grid barrier after
-// each.  Stage k's coefficients, and whether its g is psi (the top stage)
-// and whether it subtracts b_{k+2}, come from a host-built table.
-struct PmlStage {
-    double2 alpha, beta;
-    int32_t g_psi, has_h;
-};
-struct PmlMarchParams {
-    PmlOps o;
-    double2 *psi, *b[3];
-    const PmlStage *st;
+// pml_diag_kernel, elements strided over the grid, a bounded grid barrier
+// after each.  Stage k's coefficients, and whether its g is psi (the top
+// stage) and whether it subtracts b_{k+2}, come from a host-built table.
+template <typename R> struct PmlMarchParams {
+    PmlStepOps<R> o;
+    typename CT<R>::c2 *psi, *b[3];
+    const PmlStage<R> *st;
     int32_t M, n_steps, pre_half, post_half;
-    double c, rinv, h;
+    R h;
     unsigned long long *barrier;
     int *status;
     long long timeout_ns;
 };
-__global__ void __launch_bounds__(256, 6) pml_march_kernel(PmlMarchParams P) {
+template <typename R>
+__global__ void __launch_bounds__(256, 6) pml_march_kernel(PmlMarchParams<R> P) {
+    using C = typename CT<R>::c2;
     unsigned long long target = 0;
     const int stride = int(gridDim.x * blockDim.x);
-    const int p0 = int(blockIdx.x * blockDim.x + threadIdx.x);
+    const int i0 = int(blockIdx.x * blockDim.x + threadIdx.x);
+    const int n = P.o.n0 << P.o.bpad_log2;
     for (int step = 0; step < P.n_steps; ++step) {
         if (step == 0 && P.pre_half) {
-            for (int p = p0; p < P.o.n0; p += stride) pml_diag_row(P.psi, P.o.v, P.o.chib, P.o.sigma, 0.5 * P.h, p);
+            for (int i = i0; i < n; i += stride) pml_diag_row(P.o, P.psi, R(0.5) * P.h, i);
             if (!grid_barrier(P.barrier, target, P.status, P.timeout_ns)) return;
         }
         for (int k = P.M - 1; k >= 0; --k) {
-            const PmlStage sc = P.st[k];
-            const double2 *g = sc.g_psi ? P.psi : P.b[(k + 1) % 3];
-            const double2 *hh = sc.has_h ? P.b[(k + 2) % 3] : nullptr;
-            double2 *out = (k == 0) ? P.psi : P.b[k % 3];
-            for (int p = p0; p < P.o.n0; p += stride) pml_stage_row(P.o, P.psi, g, hh, out, P.c, P.rinv, sc.alpha, sc.beta, p);
+            const PmlStage<R> sc = P.st[k];
+            const C *g = sc.g_psi ? P.psi : P.b[(k + 1) % 3];
+            const C *hh = sc.has_h ? P.b[(k + 2) % 3] : nullptr;
+            C *out = (k == 0) ? P.psi : P.b[k % 3];
+            for (int i = i0; i < n; i += stride) pml_stage_row(P.o, P.psi, g, hh, out, sc, i);
             if (!grid_barrier(P.barrier, target, P.status, P.timeout_ns)) return;
         }
-        const double hd = (step == P.n_steps - 1 && P.post_half) ? 0.5 * P.h : P.h;
-        for (int p = p0; p < P.o.n0; p += stride) pml_diag_row(P.psi, P.o.v, P.o.chib, P.o.sigma, hd, p);
+        const R hd = (step == P.n_steps - 1 && P.post_half) ? R(0.5) * P.h : P.h;
+        for (int i = i0; i < n; i += stride) pml_diag_row(P.o, P.psi, hd, i);
         if (!grid_barrier(P.barrier, target, P.status, P.timeout_ns)) return;
     }
 }

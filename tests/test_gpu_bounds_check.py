@@ -6,7 +6,8 @@ of bounds.  On consistent meshes no check fires, and the fields it produces
 are bit for bit those of the default build, in every march kernel: the row
 kernel (complex64 at 2 and 4 values per thread, complex128, one field), the
 tile-staged kernel, the dataflow kernel (its dependency lists are checked
-too) and the stage-pair kernel, with lumped and element-averaged Kerr.
+too) and the stage-pair kernel, with lumped and element-averaged Kerr, and
+the march with a PML (persistent and per-term launches, both precisions).
 
 The checked library is loaded in a child process (DECBPM_BOUNDS_CHECK=1 in
 its environment); the parent runs the same cases on the default library."""
@@ -79,6 +80,17 @@ def run_cases() -> dict:
     x = torch.from_numpy(np.ascontiguousarray(psis[2][:, 0])).to(DEV, torch.complex128)
     api.propagate(meshes[2], x, dz, n, kerr="element")
     out["single_c128"] = x.cpu().numpy()
+    # the march on the complex-stretched operators of a PML, three fields
+    coords, tris = W.mesh_disk_graded(4.0, 2500, 3.0, interfaces=(1.0,), seed=57, grade_from=1.0)
+    V, chi = W.step_index_materials(coords, tris)
+    mp = api.Mesh(coords, tris, V, chi)
+    api.set_pml(mp, r_inner=3.0, r_outer=4.0, sigma_max=4.0)
+    p3 = np.ascontiguousarray(W.hg_superpositions(coords, 3, np.random.default_rng(57)) * 2.0)
+    for prec, dt in (("c64", torch.complex64), ("c128", torch.complex128)):
+        for variant in ("fused", "plain"):
+            x = torch.from_numpy(p3).to(DEV, dt)
+            api.propagate(mp, x, dz, n, diag_every=3, variant=variant)
+            out["pml_%s_%s" % (prec, variant)] = x.cpu().numpy()
     return out
 
 
