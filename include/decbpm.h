@@ -244,7 +244,10 @@ int decbpm_diagnostics(decbpm_mesh_t mesh, const void *psi_dev, int64_t n_fields
  * A plan binds n_meshes mesh handles, each carrying fields_per_mesh[i] fields
  * (all <= 64), at one precision.  It owns the workspaces and a CUDA graph per
  * step block.  All meshes advance the same n_steps with the same dz; each
- * mesh uses its own Chebyshev degree.                                       */
+ * mesh uses its own Chebyshev degree.  In complex64 a mesh with more than 16
+ * fields runs as field groups of at most 16 (decbpm_plan_config.field_groups;
+ * so do decbpm_propagate, decbpm_propagate_host and decbpm_propagate_batch):
+ * the same stages on each group, the caller's layout unchanged.             */
 int decbpm_plan_create(const decbpm_mesh_t *meshes, int32_t n_meshes, const int32_t *fields_per_mesh,
                        int32_t precision, decbpm_plan_t *out);
 int decbpm_plan_destroy(decbpm_plan_t plan);
@@ -263,7 +266,8 @@ int32_t decbpm_plan_degree(decbpm_plan_t plan, int32_t mesh_index, double dz, in
 typedef struct {
     int32_t grid;          /* CTAs of the persistent cooperative launch (all co-resident) */
     int32_t block;         /* threads per CTA */
-    int32_t fields_padded; /* fields per vertex in the internal layout (power of two >= max fields) */
+    int32_t fields_padded; /* fields per vertex in the internal layout (power of two >= max fields of an
+                              entry, see field_groups) */
     int32_t graphs;        /* 1 if step blocks are replayed from captured CUDA graphs */
     int32_t stages;        /* grid-wide stages per step for the last configured dz (max degree) */
     int32_t n_meshes;
@@ -295,6 +299,10 @@ typedef struct {
                               (columns, weights, slice widths) a launch caches in shared memory once, so
                               that no stage reads it from L2 again; 0: not cached (several meshes, the
                               cache switched off, or it does not fit with the launch's CTAs per SM) */
+    int32_t field_groups;  /* plan entries the march runs: n_meshes, or more when a complex64 plan has more
+                              than 16 fields on a mesh and runs it as field groups of at most 16 fields
+                              (balanced sizes, consecutive, sharing the mesh's operator) so that every entry
+                              fits the tile-staged kernels; the caller's layout and records are unchanged */
 } decbpm_plan_config;
 int decbpm_plan_get_config(decbpm_plan_t plan, decbpm_plan_config *cfg);
 

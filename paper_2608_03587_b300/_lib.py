@@ -82,7 +82,7 @@ class PlanConfig(ctypes.Structure):
                 ("values_per_thread", ctypes.c_int32), ("rows_per_item", ctypes.c_int32),
                 ("flow_grid", ctypes.c_int32), ("flow_skip", ctypes.c_int32), ("flow_ranges", ctypes.c_int32),
                 ("tile_rows", ctypes.c_int32),
-                ("meta_items", ctypes.c_int32)]
+                ("meta_items", ctypes.c_int32), ("field_groups", ctypes.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -439,9 +439,21 @@ static int mesh_upload(decbpm_mesh_t M) {
 }
 
 // ============================================================== plans
+// Fields per entry of a field group: the tile-staged kernels' row width.
+constexpr int kGroupFields = 16;
+
 struct decbpm_plan_s {
+    // plan entries: meshes, fields per entry, and (below) one set of field
+    // buffers each.  A complex64 plan with more than kGroupFields fields on
+    // a mesh runs that mesh as consecutive entries of at most kGroupFields
+    // fields (field groups) that share its operator, so every entry fits the
+    // tile-staged kernels; user_* is the caller's view (its meshes and field
+    // counts), ent_user / ent_f0 map an entry to the caller's mesh and to its
+    // first field there.  Without groups entries and caller meshes coincide.
     std::vector<decbpm_mesh_t> meshes;
     std::vector<int32_t> B;
+    std::vector<decbpm_mesh_t> user_meshes;
+    std::vector<int32_t> user_B, ent_user, ent_f0;
     int bpad = 1, bpad_log2 = 0, precision = DECBPM_C64, fpt = 1;
     int device = 0, num_sms = 0;
     int block = 256, grid = 0;
@@ -534,7 +546,8 @@ static const TileMaps &tile_maps(decbpm_plan_t P, decbpm_mesh_t m) { return P->t
 
 static int reject_pml(decbpm_mesh_t m);        // meshes with a PML run decbpm_propagate (one C128 field) and RK45 only
 extern "C" {
-static int single_plan(decbpm_mesh_t mesh, int64_t n_fields, int32_t precision, decbpm_plan_t *P);
+static int single_plan(decbpm_mesh_t mesh, int64_t n_fields, int32_t precision, decbpm_plan_t *P,
+                       bool field_groups = false);
 }
 static int reject_pml_plan(decbpm_plan_t P);
 
@@ -806,7 +819,7 @@ static int setup_pairs(decbpm_plan_t P) {
 }
 
 static int plan_create_impl(const decbpm_mesh_t *meshes, int32_t n, const int32_t *fields, int32_t precision,
-                            decbpm_plan_t *out) {
+                            decbpm_plan_t *out, bool field_groups = false) {
     if (!out) return fail(DECBPM_ERR_INVALID_ARG, "out is NULL");
     *out = nullptr;
     if (!meshes || !fields || n < 1 || n > kMaxMeshes)
@@ -820,8 +833,29 @@ static int plan_create_impl(const decbpm_mesh_t *meshes, int32_t n, const int32_
         maxB = std::max(maxB, int(fields[i]));
     }
     auto P = std::make_unique<decbpm_plan_s>();
-    P->meshes.assign(meshes, meshes + n);
-    P->B.assign(fields, fields + n);
+    P->user_meshes.assign(meshes, meshes + n);
+    P->user_B.assign(fields, fields + n);
+    // entries: field groups of balanced sizes where they apply (and fit the
+    // kernels' mesh table), else one entry per mesh
+    auto make_entries = [&](bool split) {
+        P->meshes.clear(); P->B.clear(); P->ent_user.clear(); P->ent_f0.clear();
+        for (int i = 0; i < n; ++i) {
+            const int g = split ? (fields[i] + kGroupFields - 1) / kGroupFields : 1;
+            const int base = fields[i] / g, rem = fields[i] % g;
+            for (int k = 0, f0 = 0; k < g; ++k) {
+                const int b = base + (k < rem ? 1 : 0);
+                P->meshes.push_back(meshes[i]);
+                P->B.push_back(b);
+                P->ent_user.push_back(i);
+                P->ent_f0.push_back(f0);
+                f0 += b;
+            }
+        }
+    };
+    make_entries(field_groups && precision == DECBPM_C64 && maxB > kGroupFields);
+    if (int(P->meshes.size()) > kMaxMeshes) make_entries(false);
+    maxB = *std::max_element(P->B.begin(), P->B.end());
+    const int ne = int(P->meshes.size());
     P->precision = precision;
     P->bpad_log2 = ilog2(maxB);
     P->bpad = 1 << P->bpad_log2;
@@ -830,9 +864,10 @@ static int plan_create_impl(const decbpm_mesh_t *meshes, int32_t n, const int32_
     CK(cudaGetDevice(&P->device));
     CK(cudaDeviceGetAttribute(&P->num_sms, cudaDevAttrMultiProcessorCount, P->device));
     const size_t cs = csize(precision);
-    for (int i = 0; i < n; ++i) {
+    P->user.assign(size_t(n), nullptr);
+    for (int i = 0; i < ne; ++i) {
         // rows rounded up to a SELL slice: the single-field tiles bulk-copy an even row count
-        const size_t elems = size_t((meshes[i]->A.n0 + kSlice - 1) / kSlice * kSlice) * P->bpad;
+        const size_t elems = size_t((P->meshes[i]->A.n0 + kSlice - 1) / kSlice * kSlice) * P->bpad;
         void *a, *b, *c, *d;
         char *t;
         TRY(P->mem.alloc(&t, elems * cs)); a = t;
@@ -840,20 +875,19 @@ static int plan_create_impl(const decbpm_mesh_t *meshes, int32_t n, const int32_
         TRY(P->mem.alloc(&t, elems * cs)); c = t;
         TRY(P->mem.alloc(&t, elems * cs)); d = t;
         P->psi.push_back(a); P->b0.push_back(b); P->b1.push_back(c); P->b2.push_back(d);
-        P->user.push_back(nullptr);
         // deterministic diagnostic grid: depends on n0 and the SM count only
         const int rows_per_block = std::max(1, kDiagThreads >> P->bpad_log2);
-        P->diag_blocks.push_back(int(std::min<int64_t>(2 * P->num_sms, (meshes[i]->A.n0 + rows_per_block - 1) / rows_per_block)));
+        P->diag_blocks.push_back(int(std::min<int64_t>(2 * P->num_sms, (P->meshes[i]->A.n0 + rows_per_block - 1) / rows_per_block)));
     }
     char *t;
-    TRY(P->mem.alloc(&t, precision == DECBPM_C64 ? sizeof(MeshView<float>) * n : sizeof(MeshView<double>) * n));
+    TRY(P->mem.alloc(&t, precision == DECBPM_C64 ? sizeof(MeshView<float>) * ne : sizeof(MeshView<double>) * ne));
     P->views = t;
     TRY(P->mem.alloc(&P->barrier, 1));
     TRY(P->mem.alloc(&P->status, 1));
     CK(cudaMemset(P->status, 0, sizeof(int)));
     int maxdb = *std::max_element(P->diag_blocks.begin(), P->diag_blocks.end());
     TRY(P->mem.alloc(&P->partial, size_t(maxdb) * P->bpad * kDiagQ));
-    TRY(P->mem.alloc(&P->diag_dev, size_t(n) * P->bpad * kDiagQ));
+    TRY(P->mem.alloc(&P->diag_dev, size_t(ne) * P->bpad * kDiagQ));
     CK(cudaStreamCreateWithFlags(&P->cap_stream, cudaStreamNonBlocking));
     CK(cudaEventCreate(&P->ev0));
     CK(cudaEventCreate(&P->ev1));
@@ -1292,8 +1326,9 @@ static int plan_propagate_impl(decbpm_plan_t P, const decbpm_params *prm, void *
     for (int i = 0; i < n; ++i) {
         const int64_t n0 = P->meshes[i]->A.n0;
         const int blocks = int(std::min<int64_t>(4 * P->num_sms, (n0 * P->bpad + 255) / 256));
-        permute_in_kernel<C><<<blocks, 256, 0, s>>>((const C *)psi_dev[i], (C *)P->psi[i], P->meshes[i]->perm,
-                                                     int32_t(n0), P->B[i], P->bpad);
+        const int u = P->ent_user[i];
+        permute_in_kernel<C><<<blocks, 256, 0, s>>>((const C *)psi_dev[u], (C *)P->psi[i], P->meshes[i]->perm,
+                                                     int32_t(n0), P->B[i], P->bpad, P->user_B[u], P->ent_f0[i]);
     }
     CK(cudaGetLastError());
     // capture the march + diagnostics once per parameter set, replay afterwards
@@ -1329,8 +1364,10 @@ static int plan_propagate_impl(decbpm_plan_t P, const decbpm_params *prm, void *
         const int64_t n0 = P->meshes[i]->A.n0;
         const int blocks = int(std::min<int64_t>(4 * P->num_sms, (n0 * P->B[i] + 255) / 256));
         const double ph = std::fmod(double(prm->n_steps) * P->theta0[i], 2.0 * M_PI);
-        permute_out_kernel<C><<<blocks, 256, 0, s>>>((const C *)P->psi[i], (C *)psi_dev[i], P->meshes[i]->perm,
-                                                      int32_t(n0), P->B[i], P->bpad, std::cos(ph), std::sin(ph));
+        const int u = P->ent_user[i];
+        permute_out_kernel<C><<<blocks, 256, 0, s>>>((const C *)P->psi[i], (C *)psi_dev[u], P->meshes[i]->perm,
+                                                      int32_t(n0), P->B[i], P->bpad, std::cos(ph), std::sin(ph),
+                                                      P->user_B[u], P->ent_f0[i]);
     }
     CK(cudaGetLastError());
     CK(cudaStreamSynchronize(s));
@@ -1347,7 +1384,7 @@ static int plan_propagate_dispatch(decbpm_plan_t P, const decbpm_params *prm, vo
     if (!P) return fail(DECBPM_ERR_INVALID_ARG, "plan is NULL");
     TRY(reject_pml_plan(P));
     if (!psi_dev) return fail(DECBPM_ERR_INVALID_ARG, "psi_dev is NULL");
-    for (size_t i = 0; i < P->meshes.size(); ++i)
+    for (size_t i = 0; i < P->user_meshes.size(); ++i)
         if (!psi_dev[i]) return fail(DECBPM_ERR_INVALID_ARG, "psi_dev[%zu] is NULL", i);
     if (prm->precision != P->precision) return fail(DECBPM_ERR_INVALID_ARG, "params precision differs from the plan's");
     if (prm->variant == DECBPM_VARIANT_PLAIN) return fail(DECBPM_ERR_UNSUPPORTED, "plans run the fused variants only");
@@ -2529,13 +2566,18 @@ int decbpm_mesh_info(decbpm_mesh_t m, decbpm_mesh_info_t *info) {
     return DECBPM_OK;
 }
 
-static int single_plan(decbpm_mesh_t mesh, int64_t n_fields, int32_t precision, decbpm_plan_t *P) {
+static int single_plan(decbpm_mesh_t mesh, int64_t n_fields, int32_t precision, decbpm_plan_t *P,
+                       bool field_groups) {
     if (n_fields < 1 || n_fields > kMaxFields) return fail(DECBPM_ERR_UNSUPPORTED, "n_fields must be in 1..%d", kMaxFields);
-    auto key = std::make_pair(int(n_fields), int(precision));
+    // field groups (complex64, > kGroupFields fields) only for the forward
+    // march's entry points; the adjoint, the PML march and the diagnostics
+    // work on one entry
+    field_groups = field_groups && precision == DECBPM_C64 && n_fields > kGroupFields;
+    auto key = std::make_pair(int(n_fields), int(precision) | (field_groups ? 0x100 : 0));
     auto it = mesh->plans.find(key);
     if (it != mesh->plans.end()) { *P = it->second; return DECBPM_OK; }
     int32_t nf = int32_t(n_fields);
-    TRY(plan_create_impl(&mesh, 1, &nf, precision, P));
+    TRY(plan_create_impl(&mesh, 1, &nf, precision, P, field_groups));
     mesh->plans[key] = *P;
     return DECBPM_OK;
 }
@@ -2558,7 +2600,7 @@ int decbpm_propagate(decbpm_mesh_t mesh, const decbpm_params *params, void *psi_
         return propagate_plain(mesh, params, psi_dev, (cudaStream_t)stream, diag_out);
     }
     decbpm_plan_t P;
-    TRY(single_plan(mesh, n_fields, params->precision, &P));
+    TRY(single_plan(mesh, n_fields, params->precision, &P, true));
     void *ptrs[1] = {psi_dev};
     return plan_propagate_dispatch(P, params, ptrs, stream, diag_out);
 }
@@ -2571,7 +2613,7 @@ int decbpm_propagate_host(decbpm_mesh_t mesh, const decbpm_params *params, void 
     TRY(reject_pml(mesh));
     TRY(check_params(params));
     decbpm_plan_t P;
-    TRY(single_plan(mesh, n_fields, params->precision, &P));
+    TRY(single_plan(mesh, n_fields, params->precision, &P, true));
     const size_t bytes = size_t(mesh->A.n0) * n_fields * csize(params->precision);
     if (!P->user[0]) {
         char *t;
@@ -2619,7 +2661,7 @@ int decbpm_diagnostics(decbpm_mesh_t mesh, const void *psi_dev, int64_t n_fields
 int decbpm_plan_create(const decbpm_mesh_t *meshes, int32_t n_meshes, const int32_t *fields_per_mesh, int32_t precision,
                        decbpm_plan_t *out) {
     clear_error();
-    return plan_create_impl(meshes, n_meshes, fields_per_mesh, precision, out);
+    return plan_create_impl(meshes, n_meshes, fields_per_mesh, precision, out, true);
 }
 
 int decbpm_plan_destroy(decbpm_plan_t plan) {
@@ -2643,9 +2685,9 @@ int decbpm_plan_propagate_host(decbpm_plan_t P, const decbpm_params *params, voi
     TRY(reject_pml_plan(P));
     cudaStream_t s = (cudaStream_t)stream;
     const size_t cs = csize(P->precision);
-    for (size_t i = 0; i < P->meshes.size(); ++i) {
+    for (size_t i = 0; i < P->user_meshes.size(); ++i) {
         if (!psi_host[i]) return fail(DECBPM_ERR_INVALID_ARG, "psi_host[%zu] is NULL", i);
-        const size_t bytes = size_t(P->meshes[i]->A.n0) * P->B[i] * cs;
+        const size_t bytes = size_t(P->user_meshes[i]->A.n0) * P->user_B[i] * cs;
         if (!P->user[i]) {
             char *t;
             TRY(P->mem.alloc(&t, bytes));
@@ -2654,8 +2696,8 @@ int decbpm_plan_propagate_host(decbpm_plan_t P, const decbpm_params *params, voi
         CK(cudaMemcpyAsync(P->user[i], psi_host[i], bytes, cudaMemcpyHostToDevice, s));
     }
     TRY(plan_propagate_dispatch(P, params, P->user.data(), stream, diag_out));
-    for (size_t i = 0; i < P->meshes.size(); ++i) {
-        const size_t bytes = size_t(P->meshes[i]->A.n0) * P->B[i] * cs;
+    for (size_t i = 0; i < P->user_meshes.size(); ++i) {
+        const size_t bytes = size_t(P->user_meshes[i]->A.n0) * P->user_B[i] * cs;
         CK(cudaMemcpyAsync(psi_host[i], P->user[i], bytes, cudaMemcpyDeviceToHost, s));
     }
     CK(cudaStreamSynchronize(s));
@@ -2663,10 +2705,11 @@ int decbpm_plan_propagate_host(decbpm_plan_t P, const decbpm_params *params, voi
 }
 
 int32_t decbpm_plan_degree(decbpm_plan_t P, int32_t i, double dz, int32_t precision, double cheb_tol) {
-    if (!P || i < 0 || i >= int32_t(P->meshes.size()) || !(dz > 0)) return 0;
+    if (!P || i < 0 || i >= int32_t(P->user_meshes.size()) || !(dz > 0)) return 0;
     Cheb cb;
     const double tol = cheb_tol > 0 ? cheb_tol : (precision == DECBPM_C64 ? 1e-9 : 1e-16);
-    if (cheb_coefficients(P->meshes[i]->A.p, P->meshes[i]->A.rho, dz, tol, cb) != DECBPM_OK) return 0;
+    const decbpm_mesh_t m = P->user_meshes[i];
+    if (cheb_coefficients(m->A.p, m->A.rho, dz, tol, cb) != DECBPM_OK) return 0;
     return cb.M;
 }
 
@@ -2856,7 +2899,8 @@ int decbpm_plan_get_config(decbpm_plan_t P, decbpm_plan_config *cfg) {
     cfg->fields_padded = P->bpad;
     cfg->graphs = (P->graphs_ok && !P->graphs.empty()) ? 1 : 0;
     cfg->stages = P->S;
-    cfg->n_meshes = int32_t(P->meshes.size());
+    cfg->n_meshes = int32_t(P->user_meshes.size());
+    cfg->field_groups = int32_t(P->meshes.size());
     cfg->tile_slots = P->tile_mode ? P->n_slots : 0;
     cfg->tile_slot_bytes = P->tile_mode ? P->slot_bytes : 0;
     cfg->tile_grid = P->tile_mode ? P->tile_grid : 0;
@@ -2966,7 +3010,7 @@ int decbpm_propagate_batch(const decbpm_mesh_t *meshes, int32_t n_meshes, const 
     clear_error();
     TRY(check_params(params));
     decbpm_plan_t P = nullptr;
-    TRY(plan_create_impl(meshes, n_meshes, fields_per_mesh, params->precision, &P));
+    TRY(plan_create_impl(meshes, n_meshes, fields_per_mesh, params->precision, &P, true));
     if (P->meshes.size() && reject_pml_plan(P) != DECBPM_OK) { delete P; return DECBPM_ERR_UNSUPPORTED; }
     int rc = plan_propagate_dispatch(P, params, psi_dev, stream, diag_out);
     delete P;

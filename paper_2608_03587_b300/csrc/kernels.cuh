@@ -2227,26 +2227,32 @@ __global__ void index_check_selftest_kernel(int n, int *status, int *out) {
 }
 
 // ------------------------------------------------------------ permutation
-// internal[new][f] = user[perm[new]][f] for f < B, 0 for the padding fields.
+// internal[new][f] = user[perm[new]][f0 + f] for f < B, 0 for the padding
+// fields; the caller's rows hold ustride fields (ustride = 0: B), of which
+// this buffer takes B from f0 on (one field group of a wider mesh).
 template <typename C>
 __global__ void permute_in_kernel(const C *__restrict__ user, C *__restrict__ internal, const int32_t *__restrict__ perm,
-                                  int32_t n0, int32_t B, int32_t bpad) {
+                                  int32_t n0, int32_t B, int32_t bpad, int32_t ustride = 0, int32_t f0 = 0) {
     const long long n = (long long)n0 * bpad;
+    const int us = ustride > 0 ? ustride : B;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
         const int r = int(i / bpad), f = int(i % bpad);
         C val;
-        if (f < B) val = user[(size_t)perm[r] * B + f];
+        if (f < B) val = user[(size_t)perm[r] * us + f0 + f];
         else { val.x = 0; val.y = 0; }
         internal[i] = val;
     }
 }
 
-// user[perm[new]][f] = phase * internal[new][f]; phase (FP64) is the global
-// factor exp(i n theta0) that the step coefficients leave out.
+// user[perm[new]][f0 + f] = phase * internal[new][f] for f < B; phase (FP64)
+// is the global factor exp(i n theta0) that the step coefficients leave out;
+// ustride and f0 as in permute_in_kernel.
 template <typename C>
 __global__ void permute_out_kernel(const C *__restrict__ internal, C *__restrict__ user, const int32_t *__restrict__ perm,
-                                   int32_t n0, int32_t B, int32_t bpad, double phase_re, double phase_im) {
+                                   int32_t n0, int32_t B, int32_t bpad, double phase_re, double phase_im,
+                                   int32_t ustride = 0, int32_t f0 = 0) {
     const long long n = (long long)n0 * B;
+    const int us = ustride > 0 ? ustride : B;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
         const int r = int(i / B), f = int(i % B);
         const C a = internal[(size_t)r * bpad + f];
@@ -2254,7 +2260,7 @@ __global__ void permute_out_kernel(const C *__restrict__ internal, C *__restrict
         C o;
         o.x = decltype(a.x)(ar * phase_re - ai * phase_im);
         o.y = decltype(a.x)(ar * phase_im + ai * phase_re);
-        user[(size_t)perm[r] * B + f] = o;
+        user[(size_t)perm[r] * us + f0 + f] = o;
     }
 }
 

@@ -182,7 +182,7 @@ def test_fp64_soliton_1d_full_run():
 
 
 # ------------------------------------------------------------------ FP32
-@pytest.mark.parametrize("B", [1, 2, 16])
+@pytest.mark.parametrize("B", [1, 2, 16, 20, 64])
 def test_fp32_one_step_from_oracle_state(fiber, B):
     coords, tris, V, chi, sigma, ops, mesh = fiber
     psi0 = launch(coords, B, seed=7)
@@ -575,6 +575,66 @@ def test_every_launch_shape_gives_the_same_fields(B):
     else:
         with pytest.raises(L.DecbpmError):
             plan.set_shape(kernel="flow", tile_slots=3, walk_skip=-1)
+
+
+def _group_sizes(B, g=16):
+    n = -(-B // g)
+    return [B // n + (1 if k < B % n else 0) for k in range(n)]
+
+
+@pytest.mark.parametrize("kerr", ["lumped", "element"])
+def test_field_groups_equal_their_groups_as_meshes(kerr):
+    """A complex64 plan with more than 16 fields on a mesh runs that mesh as
+    field groups of at most 16 (balanced, consecutive, sharing the operator):
+    meshes with 20, 4 and 33 fields make 2 + 1 + 3 entries of padded width 16,
+    on the tile-staged kernel.  Fields and diagnostic records are bit for bit
+    those of a plan that lists each group as a mesh of its own, through the
+    host-buffer call too; one mesh with 32 fields through decbpm_propagate
+    equals its two halves propagated separately."""
+    specs = [(2000, 20, 61), (600, 4, 62), (5000, 33, 63)]
+    meshes, psis = [], []
+    for nv, B, seed in specs:
+        coords, tris = W.mesh_disk_graded(4.0, nv, 3.0, interfaces=(1.0,), seed=seed, grade_from=1.0)
+        V, chi = W.step_index_materials(coords, tris)
+        sigma = W.absorber_profile(coords, 4.0, 20.0)
+        meshes.append(api.Mesh(coords, tris, V, chi, sigma))
+        psis.append(np.ascontiguousarray(W.hg_superpositions(coords, B, np.random.default_rng(seed)) * 2.0))
+    dz, n, every = 2e-3, 7, 3
+    plan = api.Plan(meshes, [p.shape[1] for p in psis], "c64")
+    cfg = plan.config()
+    assert (cfg["field_groups"], cfg["n_meshes"], cfg["fields_padded"], cfg["fused_kernel"]) == (6, 3, 16, 1)
+    t = [to_dev(p, torch.complex64) for p in psis]
+    d = plan.propagate(t, dz, n, diag_every=every, kerr=kerr)
+    gm, gp = [], []
+    for m, p in zip(meshes, psis):
+        f0 = 0
+        for b in _group_sizes(p.shape[1]):
+            gm.append(m)
+            gp.append(np.ascontiguousarray(p[:, f0:f0 + b]))
+            f0 += b
+    ref_plan = api.Plan(gm, [p.shape[1] for p in gp], "c64")
+    assert ref_plan.config()["field_groups"] == 6
+    r = [to_dev(p, torch.complex64) for p in gp]
+    dr = ref_plan.propagate(r, dz, n, diag_every=every, kerr=kerr)
+    k = 0
+    for i, p in enumerate(psis):
+        g = len(_group_sizes(p.shape[1]))
+        assert torch.equal(t[i], torch.cat(r[k:k + g], dim=1)), i
+        k += g
+    assert d.shape == dr.shape == (3, 57) and np.array_equal(d, dr)
+    h = [torch.from_numpy(p.astype(np.complex64)).pin_memory() for p in psis]
+    dh = plan.propagate_host(h, dz, n, diag_every=every, kerr=kerr)
+    for i in range(len(psis)):
+        assert torch.equal(h[i], t[i].cpu()), i
+    assert np.array_equal(dh, d)
+    # one mesh, 32 fields: the single-mesh entry point groups them too
+    m, p32 = meshes[2], np.ascontiguousarray(psis[2][:, :32])
+    a = to_dev(p32, torch.complex64)
+    api.propagate(m, a, dz, n, kerr=kerr)
+    halves = [to_dev(np.ascontiguousarray(p32[:, j:j + 16]), torch.complex64) for j in (0, 16)]
+    for x in halves:
+        api.propagate(m, x, dz, n, kerr=kerr)
+    assert torch.equal(a, torch.cat(halves, dim=1))
 
 
 @pytest.mark.parametrize("kerr", ["lumped", "element"])
