@@ -305,6 +305,8 @@ def run_ours(args, rank, world, local_rank):
             line["adjoint"] = adjoint_run(api, torch, dev)
         if "pml" in side:
             line["pml"] = pml_run(api, torch, dev)
+        if "element" in side:
+            line["element_kerr"] = element_kerr_run(plan, wl, torch, dev, args.steps, units_per_step, ms, args.variant)
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args, wl)
         line["cpu_baseline_all_cores"] = cpu_baseline_all_cores(wl, args.cpu_meshes, 16, n_steps=args.cpu_steps)
@@ -392,6 +394,25 @@ def single_field_runs(api, torch, dev, steps, peak, which=("disk", "vortex")):
             "fp64_cheb_degree": res["c128"][3]}
         mesh.close()
     return out
+
+
+def element_kerr_run(plan, wl, torch, dev, steps, units_per_step, lumped_ms, variant):
+    """The timed batch with the element-averaged Kerr term (Eq. 14: the phase
+    from Q^T D Q of the intensities, one more neighbour pass per step after
+    the last Clenshaw stage) instead of the lumped one: the same plan and
+    launch shape, K steps from the launch fields (a CUDA graph replay, timed
+    on its own after a capture call)."""
+    psis = [torch.from_numpy(p).to(dev, torch.complex64).contiguous() for p in wl.psi0]
+    plan.propagate(psis, wl.dz, steps, kerr="element", variant=variant)       # capture
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    plan.propagate(psis, wl.dz, steps, kerr="element", variant=variant)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    return {"value": units_per_step * steps / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms / steps,
+            "march_ms": plan.last_march_ms(), "time_vs_lumped": ms / lumped_ms}
 
 
 def pml_run(api, torch, dev, steps=20):
@@ -628,8 +649,9 @@ def main():
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-side", action="store_true", help="skip the single-field and adjoint side runs")
     ap.add_argument("--side-steps", type=int, default=200, help="steps of the single-field side runs")
-    ap.add_argument("--side-workloads", default="disk,vortex,adjoint,pml",
-                    help="side runs to make: any of disk (200k single field), vortex (1M), adjoint (300k PCF), pml (200k fiber with a PML, 16 fields)")
+    ap.add_argument("--side-workloads", default="disk,vortex,adjoint,pml,element",
+                    help="side runs to make: any of disk (200k single field), vortex (1M), adjoint (300k PCF), "
+                         "pml (200k fiber with a PML, 16 fields), element (the batch with element-averaged Kerr)")
     ap.add_argument("--variant", choices=["fused", "rows", "pairs", "flow"], default="fused",
                     help="fused: the autotuner's choice; pairs: the stage-pair kernel; rows: the row kernel")
     args = ap.parse_args()
