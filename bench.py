@@ -45,7 +45,7 @@ UNIT = "vertex-steps/s"
 TRAFFIC_RATIO = {"march_tile_kernel": 0.9351,
                  "march_flow_kernel:chunks:skip4:rev": 0.9606, "march_flow_kernel:chunks:skip8:rev": 0.9769,
                  "march_flow_kernel:chunks:skip16:rev": 0.9893, "march_flow_kernel:ranges:skip8:rev": 0.9836}
-TRAFFIC_SRC_HASH = "4b940fa411a61562"
+TRAFFIC_SRC_HASH = "cf49133647858336"
 
 
 def kernel_source_hash() -> str:

@@ -468,9 +468,9 @@ int decbpm_bessel_i_scaled(double a, double tol, int32_t n_max, double *out, int
  * elements on 148 SMs), else one launch per Chebyshev term and per flow
  * (params->variant = DECBPM_VARIANT_PLAIN forces the latter); complex64
  * rounds the last stage of each step once (double-float FP32 sums).
- * Every other split-step entry point (plans, batches over meshes, the
- * host-buffer call, the adjoint, the soliton solver, the allocation-free
- * call) returns DECBPM_ERR_UNSUPPORTED.  pml = NULL or sigma_max = 0
+ * decbpm_propagate_host runs the same march from host buffers.  Every other
+ * split-step entry point (plans, batches over meshes, the adjoint, the
+ * soliton solver, the allocation-free call) returns DECBPM_ERR_UNSUPPORTED.  pml = NULL or sigma_max = 0
  * removes the layer.  2D meshes only. */
 typedef struct { double x0, y0, r_inner, r_outer, sigma_max; int32_t order; } decbpm_pml;
 int decbpm_mesh_set_pml(decbpm_mesh_t mesh, const decbpm_pml *pml);

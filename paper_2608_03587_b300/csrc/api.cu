@@ -2610,10 +2610,10 @@ int decbpm_propagate_host(decbpm_mesh_t mesh, const decbpm_params *params, void 
     NvtxRange nvtx_("decbpm_propagate_host");
     clear_error();
     if (!mesh || !psi_host) return fail(DECBPM_ERR_INVALID_ARG, "mesh and psi_host are required");
-    TRY(reject_pml(mesh));
     TRY(check_params(params));
     decbpm_plan_t P;
-    TRY(single_plan(mesh, n_fields, params->precision, &P, true));
+    // the staging buffer lives in the plan the march uses (the PML march runs one entry)
+    TRY(single_plan(mesh, n_fields, params->precision, &P, !mesh->pml_on));
     const size_t bytes = size_t(mesh->A.n0) * n_fields * csize(params->precision);
     if (!P->user[0]) {
         char *t;
@@ -2622,8 +2622,14 @@ int decbpm_propagate_host(decbpm_mesh_t mesh, const decbpm_params *params, void 
     }
     cudaStream_t s = (cudaStream_t)stream;
     CK(cudaMemcpyAsync(P->user[0], psi_host, bytes, cudaMemcpyHostToDevice, s));
-    int rc = params->variant == DECBPM_VARIANT_PLAIN ? propagate_plain(mesh, params, P->user[0], s, diag_out)
-                                                     : plan_propagate_dispatch(P, params, P->user.data(), stream, diag_out);
+    int rc;
+    if (mesh->pml_on)
+        rc = params->precision == DECBPM_C64 ? propagate_pml<float>(mesh, params, P->user[0], n_fields, s, diag_out)
+                                             : propagate_pml<double>(mesh, params, P->user[0], n_fields, s, diag_out);
+    else if (params->variant == DECBPM_VARIANT_PLAIN)
+        rc = propagate_plain(mesh, params, P->user[0], s, diag_out);
+    else
+        rc = plan_propagate_dispatch(P, params, P->user.data(), stream, diag_out);
     if (rc != DECBPM_OK) return rc;
     CK(cudaMemcpyAsync(psi_host, P->user[0], bytes, cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));

@@ -176,17 +176,20 @@ def test_split_step_with_pml_complex64_matches_oracle(B):
 
 def test_pml_mesh_limits_and_removal():
     """With a layer the split-step runs one mesh with any number of fields in
-    complex64 or complex128 and lumped Kerr (decbpm_propagate) besides
-    decbpm_rk45; plans and element Kerr are refused; removing the layer
-    restores everything."""
+    complex64 or complex128 and lumped Kerr (decbpm_propagate, and from host
+    buffers with the same bits) besides decbpm_rk45; plans and element Kerr
+    are refused; removing the layer restores everything."""
     coords, tris = W.mesh_disk_graded(4.0, 600, 2.0, interfaces=(1.0,), seed=92, grade_from=1.0)
     V, chi = W.step_index_materials(coords, tris)
     mesh = api.Mesh(coords, tris, V, chi)
     x = torch.from_numpy(np.exp(-(coords[:, 0] ** 2 + coords[:, 1] ** 2)).astype(np.complex128)).to(DEV)
     api.set_pml(mesh, r_inner=3.0, r_outer=4.0, sigma_max=4.0)
     for y in (x.clone(), x.clone().to(torch.complex64), torch.stack([x, 2 * x], dim=1).contiguous()):
+        h = y.cpu().pin_memory()
         api.propagate(mesh, y, 1e-3, 2)
         assert torch.isfinite(torch.view_as_real(y)).all()
+        api.propagate_host(mesh, h, 1e-3, 2)                            # host buffers: the same march
+        assert torch.equal(h, y.cpu())
     for bad in (lambda: api.propagate(mesh, x.clone(), 1e-3, 2, kerr="element"),
                 lambda: api.Plan([mesh], [1], "c128").propagate([x.clone()], 1e-3, 2)):
         with pytest.raises(L.DecbpmError) as e:
