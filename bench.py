@@ -37,14 +37,17 @@ METRIC = "vertex-steps/s (complex field) + % HBM roofline, FP32/batched vs plain
 UNIT = "vertex-steps/s"
 
 # DRAM bytes (read + write) per algorithmic byte of the march kernels on this
-# workload (the dataflow kernel per tile assignment, walk skip and reversed
-# walk, the shapes that were captured), from an ncu capture of this bench's own launches (the
-# autotuner's 3-step trial launches), valid for the kernel source whose hash
-# is recorded with them; traffic is reported as null for another source or
-# kernel.
-TRAFFIC_RATIO = {"march_tile_kernel": 0.9351,
-                 "march_flow_kernel:chunks:skip4:rev": 0.9606, "march_flow_kernel:chunks:skip8:rev": 0.9769,
-                 "march_flow_kernel:chunks:skip16:rev": 0.9893, "march_flow_kernel:ranges:skip8:rev": 0.9836}
+# workload, per launch shape (the tile-staged kernel per ring slots and walk
+# direction; the dataflow kernel per tile assignment, walk skip and walk
+# direction), from an ncu capture of this bench's own launches (all of the
+# autotuner's 3-step trial launches of these two kernels), valid for the
+# kernel source whose hash is recorded with them; traffic is reported as
+# null for another source, kernel or shape.
+TRAFFIC_RATIO = {"march_tile_kernel:slots3:rev": 0.9351, "march_tile_kernel:slots2:rev": 0.9344,
+                 "march_tile_kernel:slots3:fwd": 0.9879, "march_tile_kernel:slots2:fwd": 0.9875,
+                 "march_flow_kernel:chunks:skip4:rev": 0.9624, "march_flow_kernel:chunks:skip8:rev": 0.9776,
+                 "march_flow_kernel:chunks:skip16:rev": 0.9892, "march_flow_kernel:ranges:skip8:rev": 0.9835,
+                 "march_flow_kernel:chunks:skip8:fwd": 0.9940, "march_flow_kernel:ranges:skip8:fwd": 0.9898}
 TRAFFIC_SRC_HASH = "cf49133647858336"
 
 
@@ -250,9 +253,11 @@ def run_ours(args, rank, world, local_rank):
         fk, "march_kernel<float,%d>" % cfg["fields_padded"])
     traffic = None
     traffic_key = kernel_name
+    walk = "fwd" if cfg.get("forward_walk") else "rev"
     if fk == 3:
-        traffic_key += ":%s:skip%d:%s" % ("ranges" if cfg.get("flow_ranges") else "chunks", cfg.get("flow_skip", 0),
-                                          "fwd" if cfg.get("forward_walk") else "rev")
+        traffic_key += ":%s:skip%d:%s" % ("ranges" if cfg.get("flow_ranges") else "chunks", cfg.get("flow_skip", 0), walk)
+    elif fk == 1:
+        traffic_key += ":slots%d:%s" % (cfg.get("tile_slots_used", 0), walk)
     if traffic_key in TRAFFIC_RATIO and TRAFFIC_SRC_HASH == kernel_source_hash():
         traffic = TRAFFIC_RATIO[traffic_key] * alg_step * args.steps
     line = {
