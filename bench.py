@@ -137,6 +137,19 @@ def build_workload(args, rank: int):
                             ratio=args.fiber_ratio, seed=shard_seed(rank))
 
 
+def traffic_shape_key(kernel_name, fused_kernel, cfg):
+    """Key of TRAFFIC_RATIO for the launch shape a plan's config describes:
+    the tile-staged kernel by ring slots and walk direction, the dataflow
+    kernel by tile assignment, walk skip and walk direction."""
+    walk = "fwd" if cfg.get("forward_walk") else "rev"
+    if fused_kernel == 3:
+        return "%s:%s:skip%d:%s" % (kernel_name, "ranges" if cfg.get("flow_ranges") else "chunks",
+                                    cfg.get("flow_skip", 0), walk)
+    if fused_kernel == 1:
+        return "%s:slots%d:%s" % (kernel_name, cfg.get("tile_slots_used", 0), walk)
+    return kernel_name
+
+
 def algorithmic_bytes_per_step(mesh_infos, fields, degrees, scalar_bytes=8):
     """Bytes the degree-M Clenshaw chain must move per z-step (all meshes):
     per vertex-field, M * (S_op / B + 4 s) + 3 r / B with S_op = (4 + r) d + 4 + r
@@ -252,12 +265,7 @@ def run_ours(args, rank, world, local_rank):
     kernel_name = {3: "march_flow_kernel", 2: "march_pair_kernel", 1: "march_tile_kernel"}.get(
         fk, "march_kernel<float,%d>" % cfg["fields_padded"])
     traffic = None
-    traffic_key = kernel_name
-    walk = "fwd" if cfg.get("forward_walk") else "rev"
-    if fk == 3:
-        traffic_key += ":%s:skip%d:%s" % ("ranges" if cfg.get("flow_ranges") else "chunks", cfg.get("flow_skip", 0), walk)
-    elif fk == 1:
-        traffic_key += ":slots%d:%s" % (cfg.get("tile_slots_used", 0), walk)
+    traffic_key = traffic_shape_key(kernel_name, fk, cfg)
     if traffic_key in TRAFFIC_RATIO and TRAFFIC_SRC_HASH == kernel_source_hash():
         traffic = TRAFFIC_RATIO[traffic_key] * alg_step * args.steps
     line = {

@@ -63,3 +63,23 @@ def test_cpu_baseline_on_all_cores_counts_every_march():
     r = bench.cpu_baseline_all_cores(wl, 2, 2, cores=2)
     assert r["cores"] == 2 and r["kind"] == "oracle" and r["value"] > 0
     assert "%d vertex-steps" % sum(m.n_vertices * 2 for m in wl.meshes) in r["sample"]
+
+
+def test_traffic_ratio_covers_every_autotuned_tile_and_dataflow_shape():
+    """Every tile-staged and dataflow launch shape the autotuner can keep on
+    the bench batch (ring slots 3 or 2 and either walk; per-CTA chunks with
+    skips 4, 8, 16 reversed or 8 forward, contiguous ranges either way) maps
+    to a captured DRAM-traffic ratio, and every stored ratio to such a shape."""
+    import bench
+    keys = set()
+    for fw in (0, 1):
+        for slots in (3, 2):
+            keys.add(bench.traffic_shape_key("march_tile_kernel", 1,
+                                             {"forward_walk": fw, "tile_slots_used": slots}))
+        for skip in ((4, 8, 16) if fw == 0 else (8,)):
+            keys.add(bench.traffic_shape_key("march_flow_kernel", 3,
+                                             {"forward_walk": fw, "flow_ranges": 0, "flow_skip": skip}))
+        keys.add(bench.traffic_shape_key("march_flow_kernel", 3, {"forward_walk": fw, "flow_ranges": 1, "flow_skip": 8}))
+    assert keys == set(bench.TRAFFIC_RATIO)
+    assert all(0.9 < r < 1.05 for r in bench.TRAFFIC_RATIO.values())
+    assert bench.traffic_shape_key("march_kernel<float,16>", 0, {}) not in bench.TRAFFIC_RATIO
