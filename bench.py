@@ -48,7 +48,7 @@ TRAFFIC_RATIO = {"march_tile_kernel:slots3:rev": 0.9351, "march_tile_kernel:slot
                  "march_flow_kernel:chunks:skip4:rev": 0.9624, "march_flow_kernel:chunks:skip8:rev": 0.9776,
                  "march_flow_kernel:chunks:skip16:rev": 0.9892, "march_flow_kernel:ranges:skip8:rev": 0.9835,
                  "march_flow_kernel:chunks:skip8:fwd": 0.9940, "march_flow_kernel:ranges:skip8:fwd": 0.9898}
-TRAFFIC_SRC_HASH = "cf49133647858336"
+TRAFFIC_SRC_HASH = "1bbcca780702978b"
 
 
 def kernel_source_hash() -> str:
@@ -317,7 +317,7 @@ def run_ours(args, rank, world, local_rank):
         if "adjoint" in side:
             line["adjoint"] = adjoint_run(api, torch, dev)
         if "pml" in side:
-            line["pml"] = pml_run(api, torch, dev)
+            line["pml"] = pml_run(api, torch, dev, peak)
         if "element" in side:
             line["element_kerr"] = element_kerr_run(plan, wl, torch, dev, args.steps, units_per_step, ms, args.variant)
     if rank == 0 and not args.no_cpu_baseline:
@@ -428,13 +428,28 @@ def element_kerr_run(plan, wl, torch, dev, steps, units_per_step, lumped_ms, var
             "march_ms": plan.last_march_ms(), "time_vs_lumped": ms / lumped_ms}
 
 
-def pml_run(api, torch, dev, steps=20):
+def pml_alg_bytes_per_vertex_field_step(M, mean_degree, B, real_bytes):
+    """Bytes the march on the stretched operators must move per vertex-field
+    and z-step: per stage the complex weights and columns of the row's SELL
+    entries ((4 + 2 r) per entry, shared by the B fields) and four field
+    accesses (g, psi and b_{k+2} read, the stage's output written, s = 2 r
+    each); per step the diagonal flow's read and write of psi and its complex
+    v, chib and real sigma (5 r per vertex)."""
+    r = real_bytes
+    s = 2 * r
+    return M * ((4.0 + 2.0 * r) * mean_degree / B + 4.0 * s) + 2.0 * s + 5.0 * r / B
+
+
+def pml_run(api, torch, dev, peak, steps=20):
     """The split-step march on the complex-stretched operators of a PML: a
     200k-vertex graded step-index fiber with the layer from r = 3 to 4
     (sigma_max 4, quadratic), 16 Hermite-Gauss superpositions, dz = 5e-4,
     complex64 and complex128, each through decbpm_propagate (persistent march
     or per-term launches, by the library's size rule), with the complex64
-    fields' error against complex128 (*0-weighted, max over fields)."""
+    fields' error against complex128 (*0-weighted, max over fields), the
+    Chebyshev degree on the stretched spectrum and the whole call's rate as a
+    fraction of the HBM roof (algorithmic bytes of the march; the working
+    set, about 0.6 GB in complex64, exceeds L2)."""
     from paper_2608_03587_b300 import workloads as W
     coords, tris = W.mesh_disk_graded(4.0, 200000, 2.0, interfaces=(1.0,), seed=91, grade_from=1.0)
     V, chi = W.step_index_materials(coords, tris)
@@ -443,6 +458,7 @@ def pml_run(api, torch, dev, steps=20):
     B, dz = 16, 5e-4
     psi0 = np.ascontiguousarray(W.hg_superpositions(coords, B, np.random.default_rng(91), power=4.0))
     n0 = coords.shape[0]
+    info = mesh.info()
     out = {"vertices": int(n0), "fields": B, "steps": steps, "dz": dz}
     res = {}
     for prec, dt in (("c64", torch.complex64), ("c128", torch.complex128)):
@@ -456,7 +472,10 @@ def pml_run(api, torch, dev, steps=20):
         torch.cuda.synchronize()
         ms = e0.elapsed_time(e1)
         res[prec] = psi
-        out[prec] = {"value": n0 * B * steps / (ms * 1e-3), "unit": UNIT, "ms": ms}
+        M = api.pml_degree(mesh, dz, prec)
+        alg = pml_alg_bytes_per_vertex_field_step(M, info["mean_degree"], B, 4 if prec == "c64" else 8) * n0 * B * steps
+        out[prec] = {"value": n0 * B * steps / (ms * 1e-3), "unit": UNIT, "ms": ms, "cheb_degree": M,
+                     "hbm_alg_frac": alg / (ms * 1e-3) / 1e9 / peak}
     out["fp32_vs_fp64"] = float(np.max(star0_rel_error(api, mesh, res["c64"], res["c128"])))
     out["fp32_speedup"] = out["c64"]["value"] / out["c128"]["value"]
     mesh.close()

@@ -474,6 +474,10 @@ int decbpm_bessel_i_scaled(double a, double tol, int32_t n_max, double *out, int
  * removes the layer.  2D meshes only. */
 typedef struct { double x0, y0, r_inner, r_outer, sigma_max; int32_t order; } decbpm_pml;
 int decbpm_mesh_set_pml(decbpm_mesh_t mesh, const decbpm_pml *pml);
+/* Chebyshev degree M of the split-step on the stretched operators for step
+ * dz at precision's default tolerance (or cheb_tol > 0): M grid-wide stages
+ * per step.  Host only; 0 if the mesh has no layer or an argument is bad. */
+int32_t decbpm_mesh_pml_degree(decbpm_mesh_t mesh, double dz, int32_t precision, double cheb_tol);
 
 /* One-shot convenience: plan_create + plan_propagate + plan_destroy. */
 int decbpm_propagate_batch(const decbpm_mesh_t *meshes, int32_t n_meshes, const int32_t *fields_per_mesh,

@@ -173,6 +173,7 @@ SIGNATURES = {
     "decbpm_soliton": (_i32, [_vp, ctypes.POINTER(SolitonOpts), _vp, _vp, ctypes.POINTER(SolitonStats)]),
     "decbpm_bessel_i_scaled": (_i32, [_dbl, _dbl, _i32, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_i32)]),
     "decbpm_mesh_set_pml": (_i32, [_vp, ctypes.POINTER(Pml)]),
+    "decbpm_mesh_pml_degree": (_i32, [_vp, _dbl, _i32, _dbl]),
     "decbpm_rk45": (_i32, [_vp, _dbl, _i32, ctypes.POINTER(Rk45Opts), _vp, _vp, ctypes.POINTER(Rk45Stats)]),
     "decbpm_propagate_noalloc": (_i32, [_vp, ctypes.POINTER(Params), _vp, _i64, _vp]),
     "decbpm_propagate_batch": (_i32, [ctypes.POINTER(_vp), _i32, _c_int32_p, ctypes.POINTER(Params),

@@ -456,7 +456,8 @@ def bessel_i_scaled(a, tol=1e-17):
 def set_pml(mesh: Mesh, r_inner=None, r_outer=None, sigma_max=0.0, order=2, center=(0.0, 0.0)):
     """decbpm_mesh_set_pml: radial complex-stretching layer beyond r_inner
     (sigma_max = 0 or r_inner = None removes it).  A mesh with a layer runs
-    with rk45 only."""
+    with rk45 and with propagate / propagate_host (the split-step on the
+    stretched operators, lumped Kerr, p_1)."""
     lib = _lib()
     if r_inner is None or sigma_max == 0.0:
         L.check(lib.decbpm_mesh_set_pml(mesh.handle, None))
@@ -464,3 +465,11 @@ def set_pml(mesh: Mesh, r_inner=None, r_outer=None, sigma_max=0.0, order=2, cent
     o = L.Pml(x0=float(center[0]), y0=float(center[1]), r_inner=float(r_inner), r_outer=float(r_outer),
               sigma_max=float(sigma_max), order=int(order))
     L.check(lib.decbpm_mesh_set_pml(mesh.handle, ctypes.byref(o)))
+
+
+
+def pml_degree(mesh: Mesh, dz, precision="c64", cheb_tol=0.0) -> int:
+    """decbpm_mesh_pml_degree: Chebyshev degree of the march on the stretched
+    operators for step dz (0 without a layer)."""
+    prec = L.C64 if precision in ("c64", L.C64) else L.C128
+    return int(_lib().decbpm_mesh_pml_degree(mesh.handle, float(dz), prec, float(cheb_tol)))

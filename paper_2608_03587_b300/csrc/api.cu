@@ -2248,14 +2248,19 @@ static int set_pml_impl(decbpm_mesh_t M, const decbpm_pml *o) {
 // launch per step block (pml_march_kernel) where one thread per (vertex,
 // field) element fits the grid, else one launch per Chebyshev term and per
 // diagonal flow.
-template <typename R>
-static int propagate_pml(decbpm_mesh_t m, const decbpm_params *prm, void *psi_dev, int64_t n_fields, cudaStream_t s,
-                         decbpm_diag *diag_out) {
+// The Chebyshev series of E_h on the stretched operator's spectral box:
+// centre c and half width r of the box's real extent, degree M, the
+// coefficients coef_k of exp(-i a x) (a = h p1 r) and the phase theta0 the
+// series leaves out: exp(-i h p1 lambda) = e^{i theta0} sum_k coef_k T_k(x).
+struct PmlSeries {
+    double c = 0, r = 0, theta0 = 0;
+    int M = 0;
+    std::vector<std::complex<double>> coef;
+};
+static int pml_series(decbpm_mesh_t m, double dz, double tol, PmlSeries &out) {
     using cd = std::complex<double>;
-    using C = typename CT<R>::c2;
-    if (prm->kerr_mode != DECBPM_KERR_LUMPED) return fail(DECBPM_ERR_UNSUPPORTED, "with a PML the split-step takes lumped Kerr");
+    if (!m->pml_on) return fail(DECBPM_ERR_INVALID_ARG, "the mesh has no PML");
     if (m->A.p.size() != 1) return fail(DECBPM_ERR_UNSUPPORTED, "with a PML the split-step takes p_1 only");
-    const int n0 = int(m->A.n0);
     const double p1 = m->A.p[0];
     const double lo = m->pml_re_lo, hi = m->pml_re_hi;
     const double c = 0.5 * (lo + hi), r = 0.5 * (hi - lo);
@@ -2272,8 +2277,7 @@ static int propagate_pml(decbpm_mesh_t m, const decbpm_params *prm, void *psi_de
         rho_e = std::max({rho_e, bern(cd(t, ylo)), bern(cd(t, yhi)), bern(cd(-1.0, u)), bern(cd(1.0, u))});
     }
     rho_e *= 1.01;
-    const double a = prm->dz * p1 * r;
-    const double tol = default_tol(prm);
+    const double a = dz * p1 * r;
     int kmax = int(std::fabs(a) * rho_e + 60 + 12 * std::cbrt(std::fabs(a) + 1.0));
     int M = 0;
     std::vector<double> J;
@@ -2288,12 +2292,30 @@ static int propagate_pml(decbpm_mesh_t m, const decbpm_params *prm, void *psi_de
         if (M < kmax - 20) break;
     }
     M = std::max(M, 2);
-    std::vector<cd> coef(M + 1);
+    out.coef.assign(M + 1, 0.0);
     for (int k = 0; k <= M; ++k) {
         const double jk = J[k] * ((a < 0 && (k & 1)) ? -1.0 : 1.0) * (k == 0 ? 1.0 : 2.0);
-        coef[k] = std::pow(cd(0.0, -1.0), k) * jk;
+        out.coef[k] = std::pow(cd(0.0, -1.0), k) * jk;
     }
-    const double theta0 = -prm->dz * p1 * c;        // exp(-i h p1 lambda) = e^{i theta0} sum_k coef_k T_k(x)
+    out.c = c;
+    out.r = r;
+    out.M = M;
+    out.theta0 = -dz * p1 * c;
+    return DECBPM_OK;
+}
+
+template <typename R>
+static int propagate_pml(decbpm_mesh_t m, const decbpm_params *prm, void *psi_dev, int64_t n_fields, cudaStream_t s,
+                         decbpm_diag *diag_out) {
+    using cd = std::complex<double>;
+    using C = typename CT<R>::c2;
+    if (prm->kerr_mode != DECBPM_KERR_LUMPED) return fail(DECBPM_ERR_UNSUPPORTED, "with a PML the split-step takes lumped Kerr");
+    const int n0 = int(m->A.n0);
+    PmlSeries ser;
+    TRY(pml_series(m, prm->dz, default_tol(prm), ser));
+    const double c = ser.c, r = ser.r, theta0 = ser.theta0;
+    const int M = ser.M;
+    const std::vector<cd> &coef = ser.coef;
     const R cs = R(c / r);
     // Stage table: b_k = a_k psi + 2 X~ b_{k+1} - b_{k+2}, the top two stages
     // folded (as in the march without a layer).  A constant field is mapped
@@ -2896,6 +2918,18 @@ int decbpm_mesh_set_pml(decbpm_mesh_t mesh, const decbpm_pml *pml) {
         return DECBPM_OK;
     }
     return set_pml_impl(mesh, pml);
+}
+
+int32_t decbpm_mesh_pml_degree(decbpm_mesh_t mesh, double dz, int32_t precision, double cheb_tol) {
+    if (!mesh || !mesh->pml_on || !(dz > 0) || !std::isfinite(dz)) return 0;
+    if (precision != DECBPM_C64 && precision != DECBPM_C128) return 0;
+    decbpm_params prm{};
+    prm.dz = dz;
+    prm.precision = precision;
+    prm.cheb_tol = cheb_tol;
+    PmlSeries ser;
+    if (pml_series(mesh, dz, default_tol(&prm), ser) != DECBPM_OK) return 0;
+    return ser.M;
 }
 
 int decbpm_plan_get_config(decbpm_plan_t P, decbpm_plan_config *cfg) {

@@ -183,7 +183,10 @@ def test_pml_mesh_limits_and_removal():
     V, chi = W.step_index_materials(coords, tris)
     mesh = api.Mesh(coords, tris, V, chi)
     x = torch.from_numpy(np.exp(-(coords[:, 0] ** 2 + coords[:, 1] ** 2)).astype(np.complex128)).to(DEV)
+    assert api.pml_degree(mesh, 1e-3, "c128") == 0                     # no layer yet
     api.set_pml(mesh, r_inner=3.0, r_outer=4.0, sigma_max=4.0)
+    m64, m32 = api.pml_degree(mesh, 1e-3, "c128"), api.pml_degree(mesh, 1e-3, "c64")
+    assert m64 >= m32 >= 2 and api.pml_degree(mesh, 2e-3, "c128") > m64
     for y in (x.clone(), x.clone().to(torch.complex64), torch.stack([x, 2 * x], dim=1).contiguous()):
         h = y.cpu().pin_memory()
         api.propagate(mesh, y, 1e-3, 2)
@@ -197,6 +200,7 @@ def test_pml_mesh_limits_and_removal():
     with pytest.raises(L.DecbpmError):
         api.set_pml(mesh, r_inner=4.0, r_outer=3.0, sigma_max=1.0)        # bad geometry
     api.set_pml(mesh, None)
+    assert api.pml_degree(mesh, 1e-3, "c128") == 0
     z = x.to(torch.complex64)
     api.propagate(mesh, z, 1e-3, 2)                                     # every split-step path runs again
     assert torch.isfinite(torch.view_as_real(z)).all()
